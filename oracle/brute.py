@@ -1,0 +1,318 @@
+"""Brute-force GKR prover and verifier in pure Python (TEST INFRASTRUCTURE ONLY).
+
+This is the pin of the C oracle: an independent, exponential-time
+implementation on Python integers and ``hashlib`` that shares no code with
+``sisu_oracle.c``.  It runs the layer sumcheck of GKR (Sec. 2.2) as a
+*generic* sumcheck over all variables (copy bits b, then x, then y) of
+
+    f(b, x, y) = eq(z_b, b) * sum_g w(g) eq(x, in1 g) eq(y, in2 g) op_g(V~(b,x), V~(b,y)),
+
+each round polynomial evaluated by enumerating every boolean value of the
+still-free variables, and every multilinear extension evaluated as the
+explicit sum  V~(p) = sum_j eq(p, bits(j)) V[j]  over the whole table.
+Only micro circuits (a few hundred hypercube points) are feasible.
+
+The transcript and proof conventions are the project's own (the paper fixes
+none): SHA-256 Fiat-Shamir with statement digests over 1024-byte chunks.
+"""
+from __future__ import annotations
+
+import hashlib
+import struct
+
+P = 0x30644E72E131A029B85045B68181585D2833E84879B9709143E1F593F0000001
+DOMAIN = b"SISU-GKR-v1"
+CHUNK = 1024
+
+
+def H(*parts: bytes) -> bytes:
+    return hashlib.sha256(b"".join(parts)).digest()
+
+
+def digest(data: bytes) -> bytes:
+    """Binary Merkle tree over 1024-byte chunks, then a length-binding hash."""
+    if not data:
+        root = H(b"\x02")
+    else:
+        level = [H(data[i:i + CHUNK], b"\x00") for i in range(0, len(data), CHUNK)]
+        while len(level) > 1:
+            nxt = [H(level[i], level[i + 1], b"\x01") for i in range(0, len(level) - 1, 2)]
+            if len(level) % 2:
+                nxt.append(level[-1])
+            level = nxt
+        root = level[0]
+    return H(root, struct.pack("<Q", len(data)), b"\x03")
+
+
+def fe(x: int) -> bytes:
+    return (x % P).to_bytes(32, "little")
+
+
+class Transcript:
+    def __init__(self, domain, d, c, s, dig_w, dig_in, dig_out):
+        dom = DOMAIN if domain is None else domain
+        self.st = H(dom, b"\x00", struct.pack("<II", d, c),
+                    b"".join(struct.pack("<I", v) for v in s), dig_w, dig_in, dig_out)
+
+    def absorb(self, tag: bytes, elems):
+        self.st = H(self.st, tag, b"".join(fe(e) for e in elems))
+
+    def challenge(self) -> int:
+        ctr = 0
+        while True:
+            h = H(self.st, b"C", struct.pack("<I", ctr))
+            x = int.from_bytes(h, "little") % (1 << 254)
+            if x < P:
+                self.st = h
+                return x
+            ctr += 1
+
+
+def log2_ceil(v: int) -> int:
+    s = 0
+    while (1 << s) < v:
+        s += 1
+    return s
+
+
+class Padded:
+    """Circuit padded to power-of-two widths and copy count (absent gates = 2)."""
+
+    def __init__(self, circ):
+        self.d = circ.depth
+        self.Creal = circ.n_copies
+        self.c = log2_ceil(circ.n_copies)
+        self.C = 1 << self.c
+        self.wreal = list(circ.widths)
+        self.s = [log2_ceil(w) for w in circ.widths]
+        self.W = [1 << s for s in self.s]
+        self.type, self.in1, self.in2 = [], [], []
+        for i in range(self.d):
+            t = [int(v) for v in circ.types[i]] + [2] * (self.W[i] - self.wreal[i])
+            a = [int(v) for v in circ.in1[i]] + [0] * (self.W[i] - self.wreal[i])
+            b = [int(v) for v in circ.in2[i]] + [0] * (self.W[i] - self.wreal[i])
+            self.type.append(t); self.in1.append(a); self.in2.append(b)
+
+    def wiring_bytes(self) -> bytes:
+        out = bytearray()
+        for i in range(self.d):
+            for g in range(self.W[i]):
+                out += struct.pack("<BII", self.type[i][g], self.in1[i][g], self.in2[i][g])
+        return bytes(out)
+
+
+def evaluate(pc: Padded, inputs):
+    """inputs: ints, n_copies x widths[d] row-major. Returns padded layers."""
+    d = pc.d
+    V = [None] * (d + 1)
+    V[d] = [0] * (pc.C * pc.W[d])
+    for b in range(pc.Creal):
+        for x in range(pc.wreal[d]):
+            V[d][b * pc.W[d] + x] = inputs[b * pc.wreal[d] + x] % P
+    for i in range(d - 1, -1, -1):
+        V[i] = [0] * (pc.C * pc.W[i])
+        for b in range(pc.C):
+            row = V[i + 1][b * pc.W[i + 1]:(b + 1) * pc.W[i + 1]]
+            for g in range(pc.W[i]):
+                t = pc.type[i][g]
+                u, v = row[pc.in1[i][g]], row[pc.in2[i][g]]
+                V[i][b * pc.W[i] + g] = (u + v) % P if t == 0 else (u * v) % P if t == 1 else 0
+    return V
+
+
+def bits_msb(v: int, m: int):
+    return [(v >> (m - 1 - k)) & 1 for k in range(m)]
+
+
+def eq(p, q) -> int:
+    acc = 1
+    for a, b in zip(p, q):
+        acc = acc * (a * b + (1 - a) * (1 - b)) % P
+    return acc
+
+
+def mle(table, point) -> int:
+    """sum_j eq(point, bits(j)) table[j] (the first coordinate is the top bit)."""
+    m = len(point)
+    return sum(eq(point, bits_msb(j, m)) * table[j] for j in range(1 << m)) % P
+
+
+def interpolate(g, x: int) -> int:
+    n = len(g)
+    acc = 0
+    for i in range(n):
+        num, den = 1, 1
+        for j in range(n):
+            if j != i:
+                num = num * (x - j) % P
+                den = den * (i - j) % P
+        acc = (acc + g[i] * num * pow(den, P - 2, P)) % P
+    return acc
+
+
+def _layer_function(pc: Padded, i: int, V_next, zb, omega):
+    """f(b, x, y) for layer i, as a function of a full point."""
+    c, s, W = pc.c, pc.s[i + 1], pc.W[i]
+    gates = [(pc.type[i][g], bits_msb(pc.in1[i][g], s), bits_msb(pc.in2[i][g], s), omega[g])
+             for g in range(W) if pc.type[i][g] != 2]
+    memo = {}
+
+    def Vt(point):
+        key = tuple(point)
+        if key not in memo:
+            memo[key] = mle(V_next, point)
+        return memo[key]
+
+    def f(point):
+        b, x, y = point[:c], point[c:c + s], point[c + s:]
+        vx, vy = Vt(b + x), Vt(b + y)
+        acc = 0
+        for t, a1, a2, w in gates:
+            op = (vx + vy) if t == 0 else vx * vy
+            acc += w * eq(x, a1) * eq(y, a2) * op
+        return eq(zb, b) * acc % P
+
+    return f, Vt
+
+
+def prove(circ, inputs, domain: bytes | None = None, check: bool = True,
+          statement_inputs=None) -> bytes:
+    """Proof bytes, every round polynomial by brute-force enumeration.
+
+    ``statement_inputs`` (tests only) puts other inputs into the transcript's
+    statement than the ones evaluated, which yields a proof that is
+    consistent in every round but false at the input check.
+    """
+    pc = Padded(circ)
+    d, c = pc.d, pc.c
+    V = evaluate(pc, inputs)
+    Vs = V[d] if statement_inputs is None else evaluate(pc, statement_inputs)[d]
+    tr = Transcript(domain, d, c, pc.s, digest(pc.wiring_bytes()),
+                    digest(b"".join(fe(v) for v in Vs)),
+                    digest(b"".join(fe(v) for v in V[0])))
+    out = bytearray(b"SISUGKR1" + struct.pack("<II", d, c) + b"".join(struct.pack("<I", v) for v in pc.s))
+    zb = [tr.challenge() for _ in range(c)]
+    zg = [tr.challenge() for _ in range(pc.s[0])]
+    claim = mle(V[0], zb + zg)
+    alpha = beta = None
+    prx = pry = None
+    for i in range(d):
+        s = pc.s[i + 1]
+        if i == 0:
+            omega = [eq(zg, bits_msb(g, pc.s[0])) for g in range(pc.W[0])]
+        else:
+            omega = [(alpha * eq(prx, bits_msb(g, pc.s[i])) + beta * eq(pry, bits_msb(g, pc.s[i]))) % P
+                     for g in range(pc.W[i])]
+        f, Vt = _layer_function(pc, i, V[i + 1], zb, omega)
+        nvars = c + 2 * s
+        bound = []
+        for k in range(nvars):
+            nodes = 4 if k < c else 3
+            rest = nvars - k - 1
+            g = []
+            for t in range(nodes):
+                g.append(sum(f(bound + [t] + bits_msb(u, rest)) for u in range(1 << rest)) % P)
+            if check:
+                assert (g[0] + g[1]) % P == claim, f"layer {i} round {k}: g(0)+g(1) != claim"
+            out += b"".join(fe(v) for v in g)
+            tr.absorb(b"R", g)
+            r = tr.challenge()
+            claim = interpolate(g, r)
+            bound.append(r)
+        rb, rx, ry = bound[:c], bound[c:c + s], bound[c + s:]
+        vx, vy = Vt(rb + rx), Vt(rb + ry)
+        if check:
+            assert claim == f(bound), f"layer {i}: final identity fails"
+        out += fe(vx) + fe(vy)
+        tr.absorb(b"V", [vx, vy])
+        if i + 1 < d:
+            alpha, beta = tr.challenge(), tr.challenge()
+            claim = (alpha * vx + beta * vy) % P
+            zb, prx, pry = rb, rx, ry
+    return bytes(out)
+
+
+def forge_one_layer(circ, inputs, fake_outputs, domain: bytes | None = None) -> bytes:
+    """A proof for a one-layer circuit that claims ``fake_outputs``.
+
+    Every round message is chosen so that g(0) + g(1) equals the running
+    claim (g = [claim, 0, 0, ...]) and v_x, v_y are the true values of the
+    input layer at the final point, so only the verifier's final per-layer
+    identity can expose it.  Tests only.
+    """
+    pc = Padded(circ)
+    assert pc.d == 1
+    c, s = pc.c, pc.s[1]
+    V = evaluate(pc, inputs)
+    V0 = [0] * (pc.C * pc.W[0])
+    for b in range(pc.Creal):
+        for g in range(pc.wreal[0]):
+            V0[b * pc.W[0] + g] = fake_outputs[b * pc.wreal[0] + g]
+    tr = Transcript(domain, 1, c, pc.s, digest(pc.wiring_bytes()),
+                    digest(b"".join(fe(v) for v in V[1])), digest(b"".join(fe(v) for v in V0)))
+    out = bytearray(b"SISUGKR1" + struct.pack("<II", 1, c) + b"".join(struct.pack("<I", v) for v in pc.s))
+    zb = [tr.challenge() for _ in range(c)]
+    zg = [tr.challenge() for _ in range(pc.s[0])]
+    claim = mle(V0, zb + zg)
+    bound = []
+    for k in range(c + 2 * s):
+        g = [claim] + [0] * (3 if k < c else 2)
+        out += b"".join(fe(v) for v in g)
+        tr.absorb(b"R", g)
+        r = tr.challenge()
+        claim = interpolate(g, r)
+        bound.append(r)
+    rb, rx, ry = bound[:c], bound[c:c + s], bound[c + s:]
+    vx, vy = mle(V[1], rb + rx), mle(V[1], rb + ry)
+    out += fe(vx) + fe(vy)
+    return bytes(out)
+
+
+def forge_vy_one_layer(circ, inputs, domain: bytes | None = None) -> bytes:
+    """A proof for a one-layer circuit whose v_y is false.
+
+    The copy and x phases are honest; the y-phase messages are g = [claim,
+    0, 0] and v_y is solved from the final per-layer identity (affine in
+    v_y), so every check passes except the input check on v_y.  Tests only.
+    """
+    pc = Padded(circ)
+    assert pc.d == 1
+    c, s = pc.c, pc.s[1]
+    V = evaluate(pc, inputs)
+    tr = Transcript(domain, 1, c, pc.s, digest(pc.wiring_bytes()),
+                    digest(b"".join(fe(v) for v in V[1])), digest(b"".join(fe(v) for v in V[0])))
+    out = bytearray(b"SISUGKR1" + struct.pack("<II", 1, c) + b"".join(struct.pack("<I", v) for v in pc.s))
+    zb = [tr.challenge() for _ in range(c)]
+    zg = [tr.challenge() for _ in range(pc.s[0])]
+    claim = mle(V[0], zb + zg)
+    omega = [eq(zg, bits_msb(g, pc.s[0])) for g in range(pc.W[0])]
+    f, Vt = _layer_function(pc, 0, V[1], zb, omega)
+    nvars = c + 2 * s
+    bound = []
+    for k in range(nvars):
+        if k < c + s:
+            nodes, rest = (4 if k < c else 3), nvars - k - 1
+            g = [sum(f(bound + [t] + bits_msb(u, rest)) for u in range(1 << rest)) % P for t in range(nodes)]
+        else:
+            g = [claim, 0, 0]
+        out += b"".join(fe(v) for v in g)
+        tr.absorb(b"R", g)
+        r = tr.challenge()
+        claim = interpolate(g, r)
+        bound.append(r)
+    rb, rx, ry = bound[:c], bound[c:c + s], bound[c + s:]
+    vx = Vt(rb + rx)
+    e = eq(zb, rb)
+    A = B = 0
+    for g in range(pc.W[0]):
+        t = pc.type[0][g]
+        if t == 2:
+            continue
+        w = omega[g] * eq(rx, bits_msb(pc.in1[0][g], s)) * eq(ry, bits_msb(pc.in2[0][g], s)) % P
+        if t == 0:
+            A, B = (A + w * vx) % P, (B + w) % P
+        else:
+            B = (B + w * vx) % P
+    vy = (claim - e * A) * pow(e * B % P, P - 2, P) % P
+    out += fe(vx) + fe(vy)
+    return bytes(out)

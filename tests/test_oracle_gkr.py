@@ -1,0 +1,194 @@
+"""Pins of the oracle's evaluator, multilinear extensions, prover and verifier.
+
+- Multilinear extensions (Sec. 2.2): folding equals the explicit eq-sum and
+  reproduces the table at boolean points.
+- Evaluator (the layer relation of Sec. 2.2): closed forms on doubling and
+  squaring circuits.
+- Prover: byte-identical to the brute-force generic sumcheck of
+  ``oracle/brute.py`` (which asserts g(0)+g(1) = claim every round, the check
+  of Sec. 3.2.1, and the final identity of every layer) on micro circuits,
+  including padded widths and copy counts (Sec. 2.2 padding), all-add,
+  all-mul and in1 = in2 wiring.
+- Verifier: accepts honest proofs, rejects tampered proofs, outputs, inputs,
+  wiring and domains.
+"""
+import random
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import brute
+from oracle.binding import ERR_REJECT, ints_to_bytes, bytes_to_ints
+
+P = brute.P
+
+
+def _mk(C, widths, pct=50, seed=9):
+    circ = synth.micro(seed, C, widths, pct)
+    x = synth.inputs_for(circ)
+    return circ, synth.fr_bytes(x), synth.fr_ints(x)
+
+
+# -- multilinear extensions --------------------------------------------------
+
+@pytest.mark.parametrize("m", [0, 1, 2, 3, 5])
+def test_mle_folding_equals_eq_sum(oracle, m):
+    rng = random.Random(m)
+    table = [rng.randrange(P) for _ in range(1 << m)]
+    for _ in range(4):
+        pt = [rng.randrange(P) for _ in range(m)]
+        got = bytes_to_ints(oracle.mle(ints_to_bytes(table), m, ints_to_bytes(pt)))[0]
+        assert got == brute.mle(table, pt)
+
+
+def test_mle_boolean_points_and_linearity(oracle):
+    rng = random.Random(3)
+    m = 4
+    table = [rng.randrange(P) for _ in range(1 << m)]
+    tb = ints_to_bytes(table)
+    for j in range(1 << m):
+        pt = brute.bits_msb(j, m)
+        assert bytes_to_ints(oracle.mle(tb, m, ints_to_bytes(pt)))[0] == table[j]
+    # affine in each coordinate: f(t) = (1 - t) f(0) + t f(1)
+    base = [rng.randrange(P) for _ in range(m)]
+    for k in range(m):
+        f = lambda t: bytes_to_ints(oracle.mle(tb, m, ints_to_bytes(base[:k] + [t] + base[k + 1:])))[0]
+        t = rng.randrange(P)
+        assert f(t) == ((1 - t) * f(0) + t * f(1)) % P
+
+
+# -- evaluator closed forms ----------------------------------------------------
+
+def _structured(kind, C, W, d):
+    g = np.arange(W, dtype=np.uint32)
+    t = np.full(W, 0 if kind == "double" else 1, dtype=np.uint8)
+    return synth.Circuit([W] * (d + 1), [t] * d, [g] * d, [g] * d, C, name=kind)
+
+
+@pytest.mark.parametrize("kind", ["double", "square"])
+def test_eval_closed_forms(oracle, kind):
+    C, W, d = 3, 5, 4
+    circ = _structured(kind, C, W, d)
+    x = synth.draw_fr_rows(17, b"cf", C, W)
+    outs = bytes_to_ints(oracle.outputs(circ, synth.fr_bytes(x)))
+    ins = synth.fr_ints(x)
+    want = [(v << d) % P for v in ins] if kind == "double" else [pow(v, 1 << d, P) for v in ins]
+    assert outs == want
+
+
+def test_eval_matches_bruteforce_layers(oracle):
+    circ, xb, xi = _mk(3, [6, 3, 7], 50, seed=4)
+    pc = brute.Padded(circ)
+    V = brute.evaluate(pc, xi)
+    for layer in range(circ.depth + 1):
+        assert bytes_to_ints(oracle.eval_layer(circ, xb, layer)) == V[layer]
+
+
+# -- prover vs brute force -----------------------------------------------------
+
+MICRO = [
+    (1, [1, 1], 50), (1, [2, 2], 50), (1, [4, 4, 4], 50), (2, [2, 2, 2], 50),
+    (4, [4, 4, 4], 50), (4, [4, 2, 8], 100), (4, [4, 4, 4], 0), (8, [8, 8], 50),
+    (3, [3, 5, 2], 50), (5, [2, 3, 3], 60), (2, [1, 2, 1], 50), (8, [2, 4, 2, 4], 50),
+    (2, [8, 8], 100), (16, [2, 2], 50),
+]
+
+
+@pytest.mark.parametrize("C,widths,pct", MICRO)
+def test_prover_matches_bruteforce(oracle, C, widths, pct):
+    circ, xb, xi = _mk(C, widths, pct)
+    p1 = oracle.prove(circ, xb)
+    p2 = brute.prove(circ, xi)
+    assert len(p1) == oracle.proof_len(circ)
+    assert p1 == p2
+    assert oracle.verify(circ, xb, oracle.outputs(circ, xb), p1) == 0
+
+
+def test_in1_equals_in2_and_domain(oracle):
+    circ, xb, xi = _mk(4, [4, 4, 4], 50, seed=21)
+    for i in range(circ.depth):
+        circ.in2[i] = circ.in1[i].copy()
+    dom = b"another-domain"
+    p1 = oracle.prove(circ, xb, dom)
+    assert p1 == brute.prove(circ, xi, dom)
+    outs = oracle.outputs(circ, xb)
+    assert oracle.verify(circ, xb, outs, p1, dom) == 0
+    assert oracle.verify(circ, xb, outs, p1) == ERR_REJECT
+
+
+def test_proof_length_formula(oracle):
+    for C, widths in [(16, [1024] * 9), (1024, [4096] * 21), (32768, [1024] * 25), (3, [3, 5, 2])]:
+        circ = synth.Circuit(widths, [np.zeros(w, np.uint8) for w in widths[:-1]],
+                             [np.zeros(w, np.uint32) for w in widths[:-1]],
+                             [np.zeros(w, np.uint32) for w in widths[:-1]], C)
+        d = len(widths) - 1
+        c = brute.log2_ceil(C)
+        s = [brute.log2_ceil(w) for w in widths]
+        assert oracle.proof_len(circ) == 8 + 4 * (d + 3) + 32 * sum(4 * c + 6 * s[i + 1] + 2 for i in range(d))
+    assert oracle.proof_len(synth.tiny()) == 20020
+
+
+# -- verifier: tampering -------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def tiny_case(oracle):
+    circ = synth.uniform_circuit(1, 4, [64] * 5, 50)
+    xb = synth.fr_bytes(synth.inputs_for(circ))
+    return circ, xb, oracle.outputs(circ, xb), oracle.prove(circ, xb)
+
+
+def test_verifier_accepts(oracle, tiny_case):
+    circ, xb, outs, proof = tiny_case
+    assert oracle.verify(circ, xb, outs, proof) == 0
+
+
+def test_tampered_elements_rejected(oracle, tiny_case):
+    circ, xb, outs, proof = tiny_case
+    hdr = 8 + 4 * (circ.depth + 3)
+    n = (len(proof) - hdr) // 32
+    rng = random.Random(2)
+    positions = sorted(set([0, 1, 2, 3, n - 1, n - 2] + [rng.randrange(n) for _ in range(40)]))
+    for k in positions:
+        bad = bytearray(proof)
+        bad[hdr + 32 * k + rng.randrange(31)] ^= 1 << rng.randrange(8)
+        assert oracle.verify(circ, xb, outs, bytes(bad)) != 0, k
+    for k in range(hdr):
+        bad = bytearray(proof)
+        bad[k] ^= 0x10
+        assert oracle.verify(circ, xb, outs, bytes(bad)) != 0
+    assert oracle.verify(circ, xb, outs, proof[:-32]) != 0
+    assert oracle.verify(circ, xb, outs, proof + bytes(32)) != 0
+
+
+def test_tampered_statement_rejected(oracle, tiny_case):
+    circ, xb, outs, proof = tiny_case
+    bad_out = bytearray(outs); bad_out[5] ^= 1
+    assert oracle.verify(circ, xb, bytes(bad_out), proof) != 0
+    bad_in = bytearray(xb); bad_in[32 * 7] ^= 1
+    assert oracle.verify(circ, bytes(bad_in), outs, proof) != 0
+    # swapping two wiring entries changes the statement
+    c2 = synth.Circuit(list(circ.widths), [t.copy() for t in circ.types], [a.copy() for a in circ.in1],
+                       [b.copy() for b in circ.in2], circ.n_copies)
+    c2.in1[1][[3, 4]] = c2.in1[1][[4, 3]]
+    assert oracle.verify(c2, xb, outs, proof) != 0
+
+
+def test_non_canonical_inputs_rejected(oracle):
+    circ, xb, xi = _mk(2, [2, 2], 50)
+    bad = bytearray(xb)
+    bad[0:32] = P.to_bytes(32, "little")
+    with pytest.raises(ValueError):
+        oracle.prove(circ, bytes(bad))
+
+
+def test_invalid_circuits_rejected(oracle):
+    good = synth.micro(1, 2, [2, 2])
+    bad_idx = synth.Circuit([2, 2], [np.array([0, 1], np.uint8)], [np.array([0, 2], np.uint32)],
+                            [np.array([0, 1], np.uint32)], 2)
+    bad_type = synth.Circuit([2, 2], [np.array([0, 3], np.uint8)], [np.array([0, 1], np.uint32)],
+                             [np.array([0, 1], np.uint32)], 2)
+    oracle.proof_len(good)
+    for c in (bad_idx, bad_type):
+        with pytest.raises(ValueError):
+            oracle.proof_len(c)

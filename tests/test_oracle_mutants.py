@@ -1,0 +1,150 @@
+"""Planted mistakes in the oracle are caught by its pins.
+
+Each case copies ``oracle/sisu_oracle.c``, plants one plausible mistake (a
+dropped term, a wrong sign, a wrong index, a transposed operand, a wrong
+constant), compiles the copy on the CPU and runs the pin set: Python-integer
+field checks, a FIPS 180 vector, the independent statement digest, the
+brute-force prover and the verifier's accept/reject behaviour.  At least one
+pin must fail for every mutant.
+"""
+import hashlib
+import json
+import os
+import random
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth
+from oracle import Oracle, brute
+from oracle.binding import SRC, ints_to_bytes, bytes_to_ints
+
+P = brute.P
+
+MUTANTS = {
+    "fold_sign": ("T[j * width + x] = fr_add(lo, fr_mul(r, fr_sub(hi, lo)));",
+                  "T[j * width + x] = fr_add(lo, fr_mul(r, fr_sub(lo, hi)));"),
+    "copy_line_sign": ("row[x] = fr_add(lo, fr_mul(tt, fr_sub(hi, lo)));",
+                       "row[x] = fr_add(hi, fr_mul(tt, fr_sub(hi, lo)));"),
+    "copy_drop_add_gates": ("if (ty == 2) continue;\n                S = fr_add(S, fr_mul(omega[g]",
+                            "if (ty != 1) continue;\n                S = fr_add(S, fr_mul(omega[g]"),
+    "eq1_dropped_term": ("return fr_add(fr_mul(a, b), fr_mul(fr_sub(one, a), fr_sub(one, b)));",
+                         "return fr_add(fr_mul(a, b), fr_mul(fr_sub(one, a), b));"),
+    "xphase_wrong_index": ("op_gate(ty, at, A0[cc->in2[i][g]])", "op_gate(ty, at, A0[cc->in1[i][g]])"),
+    "yphase_transposed": ("op_gate(ty, vx, at)", "op_gate(ty, at, at)"),
+    "omega_wrong_point": ("fr_mul(beta, eq_point_index(ry, cc->s[i], g)));\n        /* copy phase */",
+                          "fr_mul(beta, eq_point_index(rx, cc->s[i], g)));\n        /* copy phase */"),
+    "bit_order": ("return (int)((v >> (s - m)) & 1u);", "return (int)((v >> (m - 1)) & 1u);"),
+    "barrett_quotient_word": ("q3[i] = q2[5 + i];", "q3[i] = q2[4 + i];"),
+    "add_no_reduce": ("if (mw_cmp(s.w, MODW, 4) >= 0) mw_sub(s.w, s.w, MODW, 4);\n    return s;",
+                      "if (mw_cmp(s.w, MODW, 4) > 0) mw_sub(s.w, s.w, MODW, 4);\n    return s;"),
+    "sha_rotation": ("uint32_t S1 = rotr(e, 6) ^ rotr(e, 11) ^ rotr(e, 25);",
+                     "uint32_t S1 = rotr(e, 6) ^ rotr(e, 12) ^ rotr(e, 25);"),
+    "challenge_mask": ("hm[31] &= 0x3f;", "hm[31] &= 0x1f;"),
+    "merkle_tag": ("msg[64] = 0x01;", "msg[64] = 0x00;"),
+    "verifier_skips_final": ("if (!fr_eq(claim, fr_mul(e, sum))) { ok = 0; break; }",
+                             "if (0) { ok = 0; break; }"),
+    "verifier_skips_input": ("if (!fr_eq(vy, mle_by_folding(Vin, c + s, pt))) { ok = 0; break; }",
+                             "if (0) { ok = 0; break; }"),
+    "interp_wrong_node": ("num = fr_mul(num, fr_sub(x, fr_u64((uint64_t)j)));",
+                          "num = fr_mul(num, fr_sub(x, fr_u64((uint64_t)j + 1)));"),
+}
+
+
+def _pins(o: Oracle) -> list:
+    """Names of the pins that fail for this build of the oracle."""
+    failed = []
+    rng = random.Random(1)
+    a = [rng.randrange(P) for _ in range(64)] + [P - 1, 0, 1]
+    b = [rng.randrange(P) for _ in range(64)] + [P - 1, P - 1, P - 1]
+    try:
+        for op, fn in ((0, lambda x, y: (x + y) % P), (1, lambda x, y: (x - y) % P), (2, lambda x, y: x * y % P)):
+            if bytes_to_ints(o.fr_op(op, ints_to_bytes(a), ints_to_bytes(b))) != [fn(x, y) for x, y in zip(a, b)]:
+                failed.append(f"field{op}")
+    except ValueError:
+        failed.append("field-error")
+    if o.sha256(b"abc") != hashlib.sha256(b"abc").digest():
+        failed.append("sha")
+    data = bytes(range(256)) * 13
+    if o.statement_digest(data) != brute.digest(data):
+        failed.append("digest")
+    for C, widths, pct in ((4, [4, 4, 4], 50), (3, [3, 5, 2], 50), (2, [4, 2, 4], 100)):
+        circ = synth.micro(5, C, widths, pct)
+        x = synth.inputs_for(circ)
+        xb = synth.fr_bytes(x)
+        try:
+            proof = o.prove(circ, xb)
+        except ValueError:
+            failed.append("prove-error")
+            continue
+        if proof != brute.prove(circ, synth.fr_ints(x)):
+            failed.append(f"brute{C}")
+        outs = brute.evaluate(brute.Padded(circ), synth.fr_ints(x))[0]
+        outs_real = b"".join(brute.fe(outs[bb * brute.Padded(circ).W[0] + g])
+                             for bb in range(C) for g in range(widths[0]))
+        if o.verify(circ, xb, outs_real, proof) != 0:
+            failed.append(f"accept{C}")
+        honest = brute.prove(circ, synth.fr_ints(x))
+        hdr = 8 + 4 * (circ.depth + 3)
+        for k in range(0, (len(honest) - hdr) // 32):
+            bad = bytearray(honest)
+            bad[hdr + 32 * k] ^= 1
+            if o.verify(circ, xb, outs_real, bytes(bad)) == 0:
+                failed.append(f"reject{C}")
+                break
+        # an honest-looking proof over other inputs than the statement's
+        fake = synth.fr_ints(x)
+        fake[1] = (fake[1] + 1) % P
+        forged = brute.prove(circ, fake, statement_inputs=synth.fr_ints(x))
+        fake_outs = brute.evaluate(brute.Padded(circ), fake)[0]
+        fake_real = b"".join(brute.fe(fake_outs[bb * brute.Padded(circ).W[0] + g])
+                             for bb in range(C) for g in range(widths[0]))
+        if o.verify(circ, xb, fake_real, forged) == 0:
+            failed.append(f"forged-inputs{C}")
+    # round-consistent proof of false outputs for a one-layer circuit
+    circ = synth.micro(6, 4, [4, 4], 50)
+    x = synth.fr_ints(synth.inputs_for(circ))
+    outs = brute.evaluate(brute.Padded(circ), x)[0]
+    outs[0] = (outs[0] + 1) % P
+    forged = brute.forge_one_layer(circ, x, outs)
+    if o.verify(circ, ints_to_bytes(x), ints_to_bytes(outs), forged) == 0:
+        failed.append("forged-final")
+    # consistent proof whose v_y is false at the input layer
+    outs = brute.evaluate(brute.Padded(circ), x)[0]
+    forged = brute.forge_vy_one_layer(circ, x)
+    if o.verify(circ, ints_to_bytes(x), ints_to_bytes(outs), forged) == 0:
+        failed.append("forged-vy")
+    return failed
+
+
+def test_unmutated_oracle_passes_all_pins(oracle):
+    assert _pins(oracle) == []
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_mistake_is_caught(tmp_path, name):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation site for {name} not unique"
+    path = tmp_path / "mutant.c"
+    path.write_text(src.replace(old, new))
+    lib = str(tmp_path / f"libmutant_{name}.so")
+    subprocess.check_call(["gcc", "-O1", "-std=c11", "-w", "-shared", "-fPIC", "-o", lib, str(path)])
+    # A mutant may loop for ever (a wrong Barrett quotient leaves a huge
+    # remainder to subtract): run its pins in a child process with a limit.
+    try:
+        res = subprocess.run([sys.executable, os.path.abspath(__file__), lib], capture_output=True,
+                             text=True, timeout=45)
+        failed = json.loads(res.stdout.strip().splitlines()[-1]) if res.returncode == 0 else ["crash"]
+    except subprocess.TimeoutExpired:
+        failed = ["timeout"]
+    assert failed, f"mutant {name} passed every pin"
+
+
+if __name__ == "__main__":
+    print(json.dumps(_pins(Oracle(sys.argv[1]))))
