@@ -1,0 +1,325 @@
+#!/usr/bin/env python3
+"""Benchmark of the data-parallel GKR prover: gates proved per second.
+
+One step = the whole hot path over one batch of synthetic input: forward
+evaluation of every layer from device-resident inputs, statement digests,
+transcript, and the GKR layer sumcheck of every layer (copy phase, Libra's
+x and y phases), ending with the proof bytes on the host.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload medium|tiny|slot]
+
+With N > 1 (launched by torchrun, one rank per GPU) every rank proves its
+own instance of the workload: independent proofs, no data-path collective
+("replicas", weak scaling).  ``--impl reference`` times the CPU oracle (the
+plain C implementation the tests check against) on a bounded sample of the
+same workload, on rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "gates proved/sec (field mults/s vs roofline); batched proofs/sec and p99 latency vs plain"
+UNIT = "gates/s"
+# Roofline of the integer pipe (the binding unit of this path: exact
+# 256-bit modular products on 32-bit multiply-adds, no tensor cores):
+# 148 SMs x 64 32-bit multiply-adds per SM per clock x 2032 MHz.  One
+# Montgomery product of 8-limb operands (CIOS) is 2*64 multiply halves for
+# a*b plus 8 + 2*64 for the reduction = 264 multiply-adds.
+SMS, IMAD_PER_SM_CLK, SM_MAX_MHZ = 148, 64, 2032.0
+IMAD_PER_FR_MUL = 264
+ALU_PEAK_TIMAD = SMS * IMAD_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
+# DRAM traffic (read + write bytes) per launch of the dominant kernel from
+# an ncu capture (profiles/); None when not captured for the current build.
+DOMINANT_TRAFFIC_BYTES = None
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def workload(name: str):
+    import synth
+    return {"tiny": synth.tiny, "medium": synth.medium, "slot": synth.slot}[name]()
+
+
+def describe(circ) -> str:
+    return (f"{circ.name}: {circ.n_copies} copies x {circ.widths[0]} gates x {circ.depth} layers, "
+            f"{circ.meta.get('pct_mul')}% mul, {circ.meta.get('wiring')} wiring, seed {circ.seed}")
+
+
+def gates_of(circ) -> int:
+    return circ.n_copies * circ.gates_per_copy()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+
+FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class Clocks:
+    def __init__(self, gpu: str | None):
+        self.f = tempfile.TemporaryFile(mode="w+")
+        cmd = ["nvidia-smi", f"--query-gpu={FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if gpu:
+            cmd += ["-i", gpu]
+        try:
+            self.p = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        self.t0 = self.t1 = None
+
+    def mark(self, start: bool):
+        if start:
+            self.t0 = time.time()
+        else:
+            self.t1 = time.time()
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.seek(0)
+        rows = []
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                ts = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                rows.append((ts, float(parts[2]), float(parts[3]), parts[6:10]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        inside = [r for r in rows if self.t0 and self.t1 and self.t0 - 1 <= r[0] <= self.t1 + 1] or rows
+        sm = sorted(r[1] for r in inside)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in inside for k in range(4) if r[3][k].lower().startswith("active")})
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[2] for r in inside), "reasons": reasons,
+                "samples": len(inside)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline leg and reference arm)
+
+def oracle_sample(layers: int, copies: int):
+    """The workload's first ``layers`` layers with ``copies`` copies."""
+    import synth
+    return synth.uniform_circuit(2, copies, [4096] * (layers + 1), 50,
+                                 name=f"medium-shaped sample: {copies} copies x 4096 gates x {layers} layers")
+
+
+def time_oracle(circ):
+    import synth
+    from oracle import Oracle
+    o = Oracle()
+    xb = synth.fr_bytes(synth.inputs_for(circ))
+    o.proof_len(circ)
+    t0 = time.perf_counter()
+    o.prove(circ, xb)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline():
+    circ = oracle_sample(2, 1024)
+    secs = time_oracle(circ)
+    return {"value": gates_of(circ) / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{circ.name} (one proof incl. evaluation, {gates_of(circ)} gates, {secs:.1f} s, "
+                      f"single-threaded C oracle on the host)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    circ_full = workload(args.workload)
+    circ = oracle_sample(1, 256)
+    for _ in range(args.warmup):
+        time_oracle(circ)
+    total = 0.0
+    for _ in range(args.steps):
+        total += time_oracle(circ)
+    value = args.steps * gates_of(circ) / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic", "config": {"workload": describe(circ_full), "sample": circ.name},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{circ.name} per step ({gates_of(circ)} gates)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# the CUDA path
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2404_10404_b300 as S
+    import synth
+    from paper_2404_10404_b300.build import build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    build()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    circ = workload(args.workload)
+    gates = gates_of(circ)
+    t0 = time.time()
+    xb = synth.fr_bytes(synth.inputs_for(circ))
+    log(f"[bench] {circ.name}: inputs drawn in {time.time() - t0:.1f} s")
+    host = torch.frombuffer(bytearray(xb), dtype=torch.uint8).pin_memory()
+    inputs = host.to(dev)
+    stream = torch.cuda.Stream(device=dev)
+    gc = S.Circuit.from_spec(circ)
+    ev = S.Eval(gc, inputs, stream)
+    buf = ctypes.create_string_buffer(gc.proof_len)
+
+    def step(src):
+        ev.update(src, stream)
+        return S.prove(gc, ev, None, stream, out=buf)
+
+    proof = step(inputs)
+    parity = None
+    gold_path = os.path.join(ROOT, "tests", "golden", "oracle_full_size.json")
+    if os.path.exists(gold_path):
+        g = json.load(open(gold_path)).get(args.workload)
+        if g:
+            parity = hashlib.sha256(proof).hexdigest() == g["proof_sha256"]
+    for _ in range(max(0, args.warmup - 1)):
+        step(inputs)
+
+    # integer-pipe microbenchmark (reported beside the derived peak)
+    ms_lo, ops_lo = S.microbench(0, SMS * 8, 256, 256, stream.cuda_stream)
+    ms_fr, ops_fr = S.microbench(2, SMS * 8, 256, 64, stream.cuda_stream)
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = Clocks(uuid)
+    time.sleep(0.5)
+    S.profile_enable(1 << S.PROF_COPY_ROUND)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    launches0 = S.kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks.mark(True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step(inputs)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks.mark(False)
+    if world > 1:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches = S.kernel_launches() - launches0
+    prof_ms, prof_n, prof_work = S.profile_read(S.PROF_COPY_ROUND)
+    S.profile_enable(0)
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * args.steps * gates / (ms / 1e3)
+
+    # end to end through the public API: host inputs (pinned) in, proof out
+    torch.cuda.synchronize(dev)
+    w0 = time.perf_counter()
+    for _ in range(args.steps):
+        step(host)
+    torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - w0
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * args.steps * gates / e2e_s, "unit": UNIT, "h2d_bytes_per_step": len(xb),
+           "d2h_bytes_per_step": gc.proof_len}
+
+    # per-kernel breakdown of one step (untimed pass)
+    S.profile_enable(0x1FF)
+    step(inputs)
+    torch.cuda.synchronize(dev)
+    breakdown = {}
+    for k, name in S.PROF_KINDS.items():
+        kms, kn, kw = S.profile_read(k)
+        breakdown[name] = {"ms": round(kms, 4), "launches": kn, "fr_mults": kw}
+    S.profile_enable(0)
+
+    achieved = prof_work * IMAD_PER_FR_MUL / (prof_ms / 1e3) / 1e12 if prof_ms else None
+    roofline = {"bound": "alu", "kernel": "k_copy_round (copy-phase round)", "achieved": achieved,
+                "peak": ALU_PEAK_TIMAD, "unit": "TIMAD/s", "frac": achieved / ALU_PEAK_TIMAD if achieved else None,
+                "traffic": DOMINANT_TRAFFIC_BYTES,
+                "per_launch_ms": prof_ms / prof_n if prof_n else None, "launches_timed": prof_n,
+                "fr_mults_per_launch": prof_work / prof_n if prof_n else None,
+                "peak_source": "derived: 148 SMs x 64 IMAD/clk x 2032 MHz; 264 IMAD per 8x32-bit Montgomery product",
+                "imad_measured_tops": ops_lo / (ms_lo / 1e3) / 1e12,
+                "fr_mul_measured_gops": ops_fr / (ms_fr / 1e3) / 1e9}
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": describe(circ), "n_copies": circ.n_copies, "width": circ.widths[0],
+                       "depth": circ.depth, "gates_per_step": gates, "proof_bytes": gc.proof_len,
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2: the resident layer values are "
+                             f"{gc.eval_bytes / 2**30:.1f} GiB, every step re-evaluates and re-reads them"},
+            "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
+            "parity": {"proof_matches_oracle_sha256": parity},
+            "breakdown_ms_per_step": breakdown}
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["tiny", "medium", "slot"], default="medium")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

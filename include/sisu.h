@@ -1,0 +1,187 @@
+/*
+ * sisu.h - C ABI of the B300-native data-parallel GKR prover.
+ *
+ * The library proves the evaluation of a layered arithmetic circuit made of
+ * many identical sub-circuit copies (data-parallel GKR, paper Sec. 2.2; the
+ * workload of Sec. 3.2 and Sec. 4.1: one copy per validator check) over the
+ * BN254 scalar field r (Sec. 4.1).  Each layer is reduced to the next by the
+ * GKR layer sumcheck (Sec. 2.2) with Libra's linear-time two-phase prover
+ * (Sec. 2.3), preceded by a phase over the copy variables; Fiat-Shamir
+ * challenges come from a SHA-256 transcript.
+ *
+ * Conventions shared by every call
+ *   - Field elements cross the boundary as 32-byte little-endian canonical
+ *     integers in [0, r), r = 0x30644e72e131a029b85045b68181585d
+ *                             2833e84879b9709143e1f593f0000001.
+ *     An element >= r is rejected with SISU_ERR_NOT_CANONICAL.
+ *   - Layer 0 holds the outputs, layer d the inputs (Sec. 2.2).  Gate g of
+ *     gate layer i (0 <= i < d) reads gates in1[g] and in2[g] of layer i+1
+ *     and adds (type 0) or multiplies (type 1) them.  All copies share the
+ *     wiring.  Widths and the copy count need not be powers of two: they are
+ *     padded with absent gates of value 0 and zero inputs (Sec. 2.2).
+ *   - Tables of values are copy-major: element (b, g) at index b*width + g.
+ *   - "stream" is a cudaStream_t (NULL = the legacy default stream).  Device
+ *     pointers must be 16-byte aligned.
+ *   - Every call returns SISU_OK (0) or a negative SISU_ERR_* code; the
+ *     calling thread's last error message is sisu_last_error().  No call
+ *     aborts or exits.  Handles are not thread-safe: one thread (or one
+ *     stream) at a time per handle.
+ */
+#ifndef SISU_H
+#define SISU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SISU_OK 0
+#define SISU_ERR_INVALID_ARG (-1)  /* null pointer, zero size, bad gate type */
+#define SISU_ERR_INDEX_OOB (-2)    /* in1/in2 not below the next layer's width */
+#define SISU_ERR_NOT_CANONICAL (-3) /* a field element >= r */
+#define SISU_ERR_OOM (-4)          /* device or host allocation failed */
+#define SISU_ERR_CUDA (-5)         /* a CUDA runtime call failed */
+#define SISU_ERR_TIMEOUT (-6)      /* a bounded device wait gave up */
+#define SISU_ERR_REJECT (-7)       /* sisu_gkr_verify: the proof is invalid */
+#define SISU_ERR_ZERO_INVERSE (-8) /* sisu_fr_batch inverse: a zero input */
+#define SISU_ERR_TOO_LARGE (-9)    /* sizes beyond the library's limits */
+#define SISU_ERR_BUFFER (-10)      /* caller buffer too small */
+
+/* Limits: d <= 64 gate layers, widths <= 2^24, copies <= 2^24,
+ * copies x width <= 2^32 per layer (padded sizes). */
+#define SISU_MAX_LAYERS 64u
+#define SISU_MAX_WIDTH (1u << 24)
+#define SISU_MAX_COPIES (1u << 24)
+
+typedef struct sisu_circuit sisu_circuit;       /* device wiring + gate lists */
+typedef struct sisu_eval sisu_eval;             /* resident values of all layers */
+typedef struct sisu_transcript sisu_transcript; /* Fiat-Shamir domain */
+
+/* One gate layer i: `width` gates; type[g] in {0 add, 1 mul}; in1[g],
+ * in2[g] index gates of layer i+1 (Sec. 2.2, the add_i / mult_i wiring). */
+typedef struct {
+  uint32_t width;
+  const uint8_t* type;
+  const uint32_t* in1;
+  const uint32_t* in2;
+} sisu_layer;
+
+/* ---- circuits (Sec. 2.2: layered circuit, identical copies) ---------------
+ * Copies the wiring (the caller may free its arrays afterwards), validates
+ * it, uploads it to the current device and builds the per-layer gate lists
+ * the prover uses (gates grouped by type, and indexed by in1 and by in2).
+ * layers[0..n_gate_layers-1] are gate layers 0..d-1; input_width is the
+ * width of layer d.  Errors: INVALID_ARG, INDEX_OOB, TOO_LARGE, OOM, CUDA. */
+int sisu_circuit_create(const sisu_layer* layers, uint32_t n_gate_layers, uint32_t input_width,
+                        uint32_t n_copies, sisu_circuit** out);
+/* The same circuit held on the host only, for sisu_gkr_verify and
+ * sisu_circuit_info on machines without a GPU (no CUDA call is made);
+ * sisu_circuit_eval on such a handle returns INVALID_ARG. */
+int sisu_circuit_create_host(const sisu_layer* layers, uint32_t n_gate_layers, uint32_t input_width,
+                             uint32_t n_copies, sisu_circuit** out);
+void sisu_circuit_destroy(sisu_circuit* circ);
+
+/* Padded shape: log2 of the copy count, log2 widths of layers 0..d (array
+ * of d+1), proof length in bytes, and the device bytes one sisu_eval holds.
+ * Any output pointer may be NULL. */
+int sisu_circuit_info(const sisu_circuit* circ, uint32_t* depth, uint32_t* log_copies,
+                      uint32_t* log_widths, size_t* proof_len, size_t* eval_bytes);
+
+/* ---- forward evaluation (the layer relation of Sec. 2.2) -------------------
+ * inputs: n_copies x input_width elements (32 B each), host or device
+ * memory (inputs_on_device != 0).  Every layer's values stay resident on
+ * the device in the returned handle.  The call returns once the work is
+ * enqueued on `stream` and the inputs were found canonical (one wait).
+ * Errors: INVALID_ARG, NOT_CANONICAL, OOM, CUDA. */
+int sisu_circuit_eval(const sisu_circuit* circ, const uint8_t* inputs, int inputs_on_device,
+                      void* stream, sisu_eval** out);
+/* Re-evaluate into an existing handle (no allocation); same rules. */
+int sisu_eval_update(sisu_eval* ev, const uint8_t* inputs, int inputs_on_device, void* stream);
+/* Outputs (layer 0), n_copies x width_0 elements, to host memory (blocks)
+ * or device memory (out_on_device != 0, enqueued on `stream`).
+ * Errors: INVALID_ARG, BUFFER (cap too small), CUDA. */
+int sisu_eval_outputs(const sisu_eval* ev, uint8_t* out, size_t cap, int out_on_device,
+                      void* stream);
+/* One whole padded layer (2^c x 2^s_layer elements, canonical) to host
+ * memory; for tests and inspection.  Blocks. */
+int sisu_eval_layer(const sisu_eval* ev, uint32_t layer, uint8_t* out, size_t cap, void* stream);
+void sisu_eval_destroy(sisu_eval* ev);
+
+/* ---- transcript domain ----------------------------------------------------
+ * The Fiat-Shamir domain string (<= 256 bytes); NULL/0 selects the default
+ * "SISU-GKR-v1".  Errors: INVALID_ARG, OOM. */
+int sisu_transcript_create(const uint8_t* domain, size_t len, sisu_transcript** out);
+void sisu_transcript_destroy(sisu_transcript* tr);
+
+/* ---- proving (Sec. 2.2 GKR, Sec. 2.3 Libra two-phase sumcheck) -----------
+ * Proves that `ev` holds the evaluation of `circ`.  Every step runs on the
+ * device, enqueued on `stream`, with challenges kept in device memory; the
+ * call blocks once at the end to copy the proof out.  Deterministic: the
+ * same (circuit, inputs, domain) give the same bytes.
+ * Proof layout: "SISUGKR1" || u32le d || u32le c || u32le s_0..s_d, then for
+ * each layer i = 0..d-1: c x 4 elements (copy rounds, evaluations at
+ * t = 0..3) || s_{i+1} x 3 (x rounds, t = 0..2) || s_{i+1} x 3 (y rounds) ||
+ * v_x || v_y.
+ * sisu_gkr_prove allocates *proof (free it with sisu_free);
+ * sisu_gkr_prove_into writes into the caller's buffer of `cap` bytes.
+ * The first proof on an eval handle allocates the prover's workspace
+ * (about copies/2 x max width x 32 bytes), kept until sisu_eval_destroy.
+ * Errors: INVALID_ARG, BUFFER, OOM, CUDA. */
+int sisu_gkr_prove(const sisu_circuit* circ, sisu_eval* ev, const sisu_transcript* tr, void* stream,
+                   uint8_t** proof, size_t* proof_len);
+int sisu_gkr_prove_into(const sisu_circuit* circ, sisu_eval* ev, const sisu_transcript* tr,
+                        void* stream, uint8_t* proof, size_t cap, size_t* proof_len);
+
+/* Host verifier: replays the transcript, checks g(0) + g(1) = claim in
+ * every round (Sec. 3.2.1), the final identity of every layer by summing
+ * the wiring predicates, the output claim from `outputs` and the input
+ * claims from `inputs` (both host memory, unpadded, copy-major).
+ * Returns SISU_OK or SISU_ERR_REJECT (or INVALID_ARG / NOT_CANONICAL). */
+int sisu_gkr_verify(const sisu_circuit* circ, const uint8_t* inputs, const uint8_t* outputs,
+                    const uint8_t* proof, size_t proof_len, const uint8_t* domain, size_t dlen);
+
+/* ---- field core (Sec. 4.1, BN254 scalar field) ----------------------------
+ * Elementwise on device arrays of n canonical elements, enqueued on
+ * `stream` and awaited: op 0 a+b, 1 a-b, 2 a*b, 3 a^-1 (batched inversion:
+ * Montgomery's trick per thread, one Fermat exponentiation per batch; a
+ * zero input yields 0 and SISU_ERR_ZERO_INVERSE), 4 a*b + (1-a)(1-b).
+ * b is ignored for op 3.  Errors: INVALID_ARG, NOT_CANONICAL, ZERO_INVERSE. */
+int sisu_fr_batch(int op, const uint8_t* a, const uint8_t* b, uint8_t* out, size_t n, void* stream);
+
+/* Merkle statement digest of device bytes (the transcript's digest of
+ * wiring, inputs and outputs): SHA-256 tree over 1024-byte chunks, leaf =
+ * H(chunk || 0x00), node = H(left || right || 0x01), odd last node moved
+ * up, digest = H(root || u64le len || 0x03).  out: 32 host bytes. */
+int sisu_statement_digest(const uint8_t* data, size_t len, uint8_t* out, void* stream);
+
+/* Integer-pipe microbenchmarks used for the roofline: kind 0 = independent
+ * 32-bit multiply-add chains (mad.lo), kind 1 = mad.hi chains, kind 2 =
+ * Montgomery products.  Reports the elapsed milliseconds and the number of
+ * operations (multiply-adds, or field products for kind 2). */
+int sisu_microbench(int kind, uint32_t blocks, uint32_t threads, uint32_t iters, void* stream,
+                    double* ms, double* ops);
+
+/* Per-kernel timing with CUDA events on the launching stream.  Bit k of
+ * kind_mask enables kind k: 0 copy-phase round, 1 copy-phase fold, 2 layer
+ * evaluation, 3 x/y-phase round, 4 statement digests, 5 layer init, 6 x/y
+ * phase init, 7 transcript-only kernels, 8 input conversion; 0 disables.
+ * sisu_profile_read waits for the recorded events of one kind and returns
+ * their summed milliseconds, the launch count and the algorithmic field
+ * products of those launches (per copy-phase pair: 5 per mul gate, 2 per
+ * add gate, 4 for the copy weights), then forgets them. */
+int sisu_profile_enable(uint32_t kind_mask);
+int sisu_profile_read(uint32_t kind, double* ms, uint64_t* launches, double* fr_mults);
+
+/* Number of kernels this library launched so far in this process. */
+uint64_t sisu_kernel_launches(void);
+
+void sisu_free(void* p);
+const char* sisu_last_error(void);
+const char* sisu_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SISU_H */

@@ -1,0 +1,325 @@
+"""Python binding of libsisu.so, the B300-native data-parallel GKR prover.
+
+Argument marshalling only: every step of evaluation and proving runs in the
+library's CUDA kernels behind the C ABI declared in ``include/sisu.h``.
+The library is loaded on first use.  Importing this package does not import
+torch; device buffers are passed as
+objects with ``data_ptr()`` (torch CUDA tensors) or as raw integer pointers.
+If the library has not been built the import fails with an error that says
+how to build it: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsisu.so")
+
+OK = 0
+ERRORS = {
+    -1: "INVALID_ARG", -2: "INDEX_OOB", -3: "NOT_CANONICAL", -4: "OOM", -5: "CUDA",
+    -6: "TIMEOUT", -7: "REJECT", -8: "ZERO_INVERSE", -9: "TOO_LARGE", -10: "BUFFER",
+}
+FR_ADD, FR_SUB, FR_MUL, FR_INV, FR_EQ1 = 0, 1, 2, 3, 4
+ENTRY_POINTS = [
+    "sisu_circuit_create", "sisu_circuit_create_host", "sisu_circuit_destroy", "sisu_circuit_info", "sisu_circuit_eval",
+    "sisu_eval_update", "sisu_eval_outputs", "sisu_eval_layer", "sisu_eval_destroy",
+    "sisu_transcript_create", "sisu_transcript_destroy", "sisu_gkr_prove", "sisu_gkr_prove_into",
+    "sisu_gkr_verify", "sisu_fr_batch", "sisu_statement_digest", "sisu_microbench",
+    "sisu_kernel_launches", "sisu_free", "sisu_last_error", "sisu_version",
+    "sisu_profile_enable", "sisu_profile_read",
+]
+PROF_COPY_ROUND, PROF_COPY_FOLD, PROF_EVAL, PROF_GATE_ROUND, PROF_DIGEST = 0, 1, 2, 3, 4
+PROF_LAYER_INIT, PROF_PHASE_INIT, PROF_TRANSCRIPT, PROF_INPUTS = 5, 6, 7, 8
+PROF_KINDS = {0: "copy_round", 1: "copy_fold", 2: "eval_layer", 3: "gate_round", 4: "digest",
+              5: "layer_init", 6: "phase_init", 7: "transcript", 8: "inputs"}
+
+
+class SisuError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _Layer(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_uint32), ("type", ctypes.POINTER(ctypes.c_uint8)),
+                ("in1", ctypes.POINTER(ctypes.c_uint32)), ("in2", ctypes.POINTER(ctypes.c_uint32))]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -m paper_2404_10404_b300.build` (needs nvcc, sm_103a)")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, sz, u32, u8p = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint32, ctypes.c_void_p
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "sisu_circuit_create": ([ctypes.POINTER(_Layer), u32, u32, u32, pp], ctypes.c_int),
+        "sisu_circuit_create_host": ([ctypes.POINTER(_Layer), u32, u32, u32, pp], ctypes.c_int),
+        "sisu_circuit_destroy": ([vp], None),
+        "sisu_circuit_info": ([vp, ctypes.POINTER(u32), ctypes.POINTER(u32), ctypes.POINTER(u32),
+                               ctypes.POINTER(sz), ctypes.POINTER(sz)], ctypes.c_int),
+        "sisu_circuit_eval": ([vp, u8p, ctypes.c_int, vp, pp], ctypes.c_int),
+        "sisu_eval_update": ([vp, u8p, ctypes.c_int, vp], ctypes.c_int),
+        "sisu_eval_outputs": ([vp, u8p, sz, ctypes.c_int, vp], ctypes.c_int),
+        "sisu_eval_layer": ([vp, u32, u8p, sz, vp], ctypes.c_int),
+        "sisu_eval_destroy": ([vp], None),
+        "sisu_transcript_create": ([u8p, sz, pp], ctypes.c_int),
+        "sisu_transcript_destroy": ([vp], None),
+        "sisu_gkr_prove": ([vp, vp, vp, vp, pp, ctypes.POINTER(sz)], ctypes.c_int),
+        "sisu_gkr_prove_into": ([vp, vp, vp, vp, u8p, sz, ctypes.POINTER(sz)], ctypes.c_int),
+        "sisu_gkr_verify": ([vp, u8p, u8p, u8p, sz, u8p, sz], ctypes.c_int),
+        "sisu_fr_batch": ([ctypes.c_int, vp, vp, vp, sz, vp], ctypes.c_int),
+        "sisu_statement_digest": ([vp, sz, u8p, vp], ctypes.c_int),
+        "sisu_microbench": ([ctypes.c_int, u32, u32, u32, vp, ctypes.POINTER(ctypes.c_double),
+                             ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+        "sisu_kernel_launches": ([], ctypes.c_uint64),
+        "sisu_free": ([vp], None),
+        "sisu_last_error": ([], ctypes.c_char_p),
+        "sisu_version": ([], ctypes.c_char_p),
+        "sisu_profile_enable": ([u32], ctypes.c_int),
+        "sisu_profile_read": ([u32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64),
+                               ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+_lib_handle = None
+
+
+def _lib_get():
+    global _lib_handle
+    if _lib_handle is None:
+        _lib_handle = _load()
+    return _lib_handle
+
+
+class _LazyLib:
+    def __getattr__(self, name):
+        return getattr(_lib_get(), name)
+
+
+_lib = _LazyLib()
+
+
+def _check(rc: int):
+    if rc != OK:
+        raise SisuError(rc, _lib.sisu_last_error().decode(errors="replace"))
+
+
+def _ptr(buf):
+    """(pointer, on_device, keepalive) for bytes, numpy arrays, torch tensors or ints."""
+    if buf is None:
+        return None, 0, None
+    if isinstance(buf, int):
+        return buf, 1, None
+    if hasattr(buf, "data_ptr") and hasattr(buf, "is_cuda"):
+        return buf.data_ptr(), int(bool(buf.is_cuda)), buf
+    if isinstance(buf, (bytes, bytearray)):
+        arr = np.frombuffer(bytes(buf), dtype=np.uint8)
+        return arr.ctypes.data, 0, arr
+    arr = np.ascontiguousarray(buf)
+    return arr.ctypes.data, 0, arr
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def library_path() -> str:
+    return LIB_PATH
+
+
+def version() -> str:
+    return _lib.sisu_version().decode()
+
+
+def kernel_launches() -> int:
+    return int(_lib.sisu_kernel_launches())
+
+
+class Circuit:
+    """A layered circuit on the device (``sisu_circuit_create``).
+
+    ``widths[i]`` gates in layer i (0 = outputs, d = inputs); ``types``,
+    ``in1``, ``in2`` per gate layer; ``n_copies`` identical copies.
+    """
+
+    def __init__(self, widths, types, in1, in2, n_copies: int, host_only: bool = False):
+        d = len(widths) - 1
+        self._keep = []
+        layers = (_Layer * d)()
+        for i in range(d):
+            t = np.ascontiguousarray(types[i], dtype=np.uint8)
+            a = np.ascontiguousarray(in1[i], dtype=np.uint32)
+            b = np.ascontiguousarray(in2[i], dtype=np.uint32)
+            if not (len(t) == len(a) == len(b) == int(widths[i])):
+                raise SisuError(-1, f"layer {i}: wiring arrays must have {widths[i]} entries")
+            self._keep += [t, a, b]
+            layers[i] = _Layer(int(widths[i]), t.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                               a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                               b.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)))
+        h = ctypes.c_void_p()
+        create = _lib.sisu_circuit_create_host if host_only else _lib.sisu_circuit_create
+        _check(create(layers, d, int(widths[d]), int(n_copies), ctypes.byref(h)))
+        self._keep = None
+        self.h = h
+        self.widths = [int(w) for w in widths]
+        self.n_copies = int(n_copies)
+        dep, lc = ctypes.c_uint32(), ctypes.c_uint32()
+        lw = (ctypes.c_uint32 * (d + 1))()
+        pl, eb = ctypes.c_size_t(), ctypes.c_size_t()
+        _check(_lib.sisu_circuit_info(h, ctypes.byref(dep), ctypes.byref(lc), lw, ctypes.byref(pl),
+                                      ctypes.byref(eb)))
+        self.depth = int(dep.value)
+        self.log_copies = int(lc.value)
+        self.log_widths = list(lw)
+        self.proof_len = int(pl.value)
+        self.eval_bytes = int(eb.value)
+
+    @classmethod
+    def from_spec(cls, spec, host_only: bool = False):
+        """From any object with widths, types, in1, in2 and n_copies."""
+        return cls(spec.widths, spec.types, spec.in1, spec.in2, spec.n_copies, host_only=host_only)
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            _lib.sisu_circuit_destroy(self.h)
+            self.h = None
+
+
+class Eval:
+    """Resident values of every layer (``sisu_circuit_eval``)."""
+
+    def __init__(self, circ: Circuit, inputs, stream=None):
+        p, on_dev, keep = _ptr(inputs)
+        h = ctypes.c_void_p()
+        _check(_lib.sisu_circuit_eval(circ.h, p, on_dev, _stream(stream), ctypes.byref(h)))
+        del keep
+        self.h = h
+        self.circ = circ
+
+    def update(self, inputs, stream=None):
+        p, on_dev, keep = _ptr(inputs)
+        _check(_lib.sisu_eval_update(self.h, p, on_dev, _stream(stream)))
+        del keep
+
+    def outputs(self, stream=None) -> bytes:
+        n = 32 * self.circ.n_copies * self.circ.widths[0]
+        buf = ctypes.create_string_buffer(n)
+        _check(_lib.sisu_eval_outputs(self.h, ctypes.cast(buf, ctypes.c_void_p), n, 0, _stream(stream)))
+        return buf.raw
+
+    def outputs_to(self, dev_buf, stream=None):
+        p, _, keep = _ptr(dev_buf)
+        n = 32 * self.circ.n_copies * self.circ.widths[0]
+        _check(_lib.sisu_eval_outputs(self.h, p, n, 1, _stream(stream)))
+
+    def layer(self, l: int, stream=None) -> bytes:
+        n = 32 << (self.circ.log_copies + self.circ.log_widths[l])
+        buf = ctypes.create_string_buffer(n)
+        _check(_lib.sisu_eval_layer(self.h, l, ctypes.cast(buf, ctypes.c_void_p), n, _stream(stream)))
+        return buf.raw
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            _lib.sisu_eval_destroy(self.h)
+            self.h = None
+
+
+class Transcript:
+    """Fiat-Shamir domain (``sisu_transcript_create``); None = default."""
+
+    def __init__(self, domain: bytes | None = None):
+        h = ctypes.c_void_p()
+        dom = bytes(domain) if domain else None
+        buf = ctypes.create_string_buffer(dom) if dom else None
+        _check(_lib.sisu_transcript_create(ctypes.cast(buf, ctypes.c_void_p) if buf else None,
+                                           len(dom) if dom else 0, ctypes.byref(h)))
+        self.h = h
+        self.domain = dom
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            _lib.sisu_transcript_destroy(self.h)
+            self.h = None
+
+
+def prove(circ: Circuit, ev: Eval, transcript: Transcript | None = None, stream=None, out=None) -> bytes:
+    """Proof bytes (``sisu_gkr_prove_into``); ``out`` may be a reusable
+    ctypes buffer of at least ``circ.proof_len`` bytes."""
+    n = circ.proof_len
+    buf = out if out is not None else ctypes.create_string_buffer(n)
+    ln = ctypes.c_size_t()
+    _check(_lib.sisu_gkr_prove_into(circ.h, ev.h, transcript.h if transcript else None, _stream(stream),
+                                    ctypes.cast(buf, ctypes.c_void_p), n, ctypes.byref(ln)))
+    return buf.raw[:ln.value]
+
+
+def prove_alloc(circ: Circuit, ev: Eval, transcript: Transcript | None = None, stream=None) -> bytes:
+    """Proof bytes through ``sisu_gkr_prove`` (library-allocated buffer)."""
+    p = ctypes.c_void_p()
+    ln = ctypes.c_size_t()
+    _check(_lib.sisu_gkr_prove(circ.h, ev.h, transcript.h if transcript else None, _stream(stream),
+                               ctypes.byref(p), ctypes.byref(ln)))
+    try:
+        return ctypes.string_at(p, ln.value)
+    finally:
+        _lib.sisu_free(p)
+
+
+def verify(circ: Circuit, inputs: bytes, outputs: bytes, proof: bytes, domain: bytes | None = None) -> int:
+    """SISU_OK (0) or a negative code, SISU_ERR_REJECT (-7) for a bad proof."""
+    ib, ob, pb = (np.frombuffer(bytes(x), dtype=np.uint8) for x in (inputs, outputs, proof))
+    db = np.frombuffer(bytes(domain), dtype=np.uint8) if domain else None
+    return int(_lib.sisu_gkr_verify(circ.h, ib.ctypes.data, ob.ctypes.data, pb.ctypes.data, len(pb),
+                                    db.ctypes.data if db is not None else None, len(db) if db is not None else 0))
+
+
+def fr_batch(op: int, a, b, out, n: int, stream=None):
+    """Elementwise field op on device arrays of n canonical elements."""
+    pa, _, ka = _ptr(a)
+    pb, _, kb = _ptr(b)
+    po, _, ko = _ptr(out)
+    _check(_lib.sisu_fr_batch(op, pa, pb, po, n, _stream(stream)))
+
+
+def statement_digest(data, length: int, stream=None) -> bytes:
+    p, _, keep = _ptr(data)
+    out = ctypes.create_string_buffer(32)
+    _check(_lib.sisu_statement_digest(p, length, ctypes.cast(out, ctypes.c_void_p), _stream(stream)))
+    return out.raw
+
+
+def microbench(kind: int, blocks: int, threads: int, iters: int, stream=None):
+    """(milliseconds, operations) of an integer-pipe microbenchmark."""
+    ms, ops = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.sisu_microbench(kind, blocks, threads, iters, _stream(stream), ctypes.byref(ms), ctypes.byref(ops)))
+    return ms.value, ops.value
+
+
+def profile_enable(kind_mask: int):
+    """Time the launches of the kernel kinds in the mask with CUDA events."""
+    _check(_lib.sisu_profile_enable(kind_mask))
+
+
+def profile_read(kind: int):
+    """(milliseconds, launches, algorithmic field products) since the last read."""
+    ms, n, w = ctypes.c_double(), ctypes.c_uint64(), ctypes.c_double()
+    _check(_lib.sisu_profile_read(kind, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(w)))
+    return ms.value, int(n.value), w.value
+
+
+def last_error() -> str:
+    return _lib.sisu_last_error().decode(errors="replace")

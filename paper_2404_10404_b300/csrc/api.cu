@@ -1,0 +1,786 @@
+// C ABI of the data-parallel GKR prover: handles, evaluation and the
+// prover's launch sequence.  Everything in a proof runs on the device,
+// stream-ordered, with challenges in device memory; the host waits once,
+// for the proof bytes.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <memory>
+#include <new>
+
+#include "../../include/sisu.h"
+#include "internal.h"
+
+using namespace sisu;
+
+namespace sisu {
+static std::atomic<uint64_t> g_launches{0};
+uint64_t launches_add(uint64_t n) { return g_launches.fetch_add(n) + n; }
+}  // namespace sisu
+
+// ---------------------------------------------------------------------------
+// errors
+
+static thread_local char g_err[512] = "";
+
+static int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+static int cuda_fail(cudaError_t e, const char* what) {
+  return fail(SISU_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                   \
+  do {                                                   \
+    cudaError_t e_ = (cudaError_t)(call);                \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what);   \
+  } while (0)
+
+static uint32_t ceil_log2(uint64_t v) {
+  uint32_t s = 0;
+  while ((1ull << s) < v) ++s;
+  return s;
+}
+
+namespace sisu {
+size_t HostCircuit::proof_len() const {
+  size_t n = 8 + 4 * ((size_t)d + 3);
+  for (uint32_t i = 0; i < d; ++i) n += 32 * (4 * (size_t)c + 6 * (size_t)s[i + 1] + 2);
+  return n;
+}
+}  // namespace sisu
+
+// ---------------------------------------------------------------------------
+// per-kernel timing with CUDA events (diagnostics; off unless enabled)
+
+namespace {
+struct ProfRec {
+  cudaEvent_t a, b;
+  double work;
+  uint32_t kind;
+};
+uint32_t g_prof_mask = 0;
+std::vector<ProfRec> g_prof;
+std::vector<cudaEvent_t> g_event_pool;
+
+cudaEvent_t pool_event() {
+  if (!g_event_pool.empty()) {
+    cudaEvent_t e = g_event_pool.back();
+    g_event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Times one launch when its kind is enabled: returns the index of the record.
+struct ProfScope {
+  long idx = -1;
+  cudaStream_t st;
+  ProfScope(uint32_t kind, double work, cudaStream_t s) : st(s) {
+    if (!(g_prof_mask & (1u << kind))) return;
+    ProfRec r{pool_event(), pool_event(), work, kind};
+    cudaEventRecord(r.a, st);
+    g_prof.push_back(r);
+    idx = (long)g_prof.size() - 1;
+  }
+  ~ProfScope() {
+    if (idx >= 0) cudaEventRecord(g_prof[idx].b, st);
+  }
+};
+}  // namespace
+
+enum : uint32_t {
+  kProfCopyRound = 0, kProfCopyFold = 1, kProfEval = 2, kProfGateRound = 3, kProfDigest = 4,
+  kProfLayerInit = 5, kProfPhaseInit = 6, kProfTranscript = 7, kProfInputs = 8
+};
+
+extern "C" int sisu_profile_enable(uint32_t kind_mask) {
+  g_prof_mask = kind_mask;
+  return SISU_OK;
+}
+
+extern "C" int sisu_profile_read(uint32_t kind, double* ms, uint64_t* launches, double* fr_mults) {
+  double t = 0, w = 0;
+  uint64_t n = 0;
+  std::vector<ProfRec> keep;
+  for (ProfRec& r : g_prof) {
+    if (r.kind != kind) {
+      keep.push_back(r);
+      continue;
+    }
+    cudaError_t e = cudaEventSynchronize(r.b);
+    if (e != cudaSuccess) return cuda_fail(e, "profile events");
+    float x = 0;
+    cudaEventElapsedTime(&x, r.a, r.b);
+    t += x;
+    w += r.work;
+    ++n;
+    g_event_pool.push_back(r.a);
+    g_event_pool.push_back(r.b);
+  }
+  g_prof.swap(keep);
+  if (ms) *ms = t;
+  if (launches) *launches = n;
+  if (fr_mults) *fr_mults = w;
+  return SISU_OK;
+}
+
+// ---------------------------------------------------------------------------
+// handles
+
+struct sisu_circuit {
+  HostCircuit hc;
+  std::vector<DevLayer> L;  // device views, gate layers 0..d-1
+  void* dev = nullptr;      // one allocation holding every device array
+  int device = 0;
+  ~sisu_circuit() {
+    if (dev) cudaFree(dev);
+  }
+};
+
+struct Workspace {
+  void* dev = nullptr;
+  uint32_t *T = nullptr, *E = nullptr, *om = nullptr, *At = nullptr, *H1 = nullptr, *H2 = nullptr,
+           *Ay = nullptr, *Q = nullptr, *partials = nullptr, *dscratch = nullptr;
+  DevState* S = nullptr;
+  uint8_t* proof = nullptr;
+  uint8_t* host = nullptr;  // pinned: proof bytes followed by the error word
+  size_t proof_len = 0;
+  ~Workspace() {
+    if (dev) cudaFree(dev);
+    if (host) cudaFreeHost(host);
+  }
+};
+
+struct sisu_eval {
+  const sisu_circuit* circ = nullptr;
+  std::vector<uint32_t*> V;  // layers 0..d, Montgomery, padded
+  void* dev = nullptr;
+  uint32_t* stage = nullptr;  // padded-input staging (only when padding is needed)
+  uint32_t* flag = nullptr;   // device error word
+  uint32_t* host_flag = nullptr;
+  std::unique_ptr<Workspace> ws;
+  ~sisu_eval() {
+    ws.reset();
+    if (stage) cudaFree(stage);
+    if (dev) cudaFree(dev);
+    if (host_flag) cudaFreeHost(host_flag);
+  }
+};
+
+struct sisu_transcript {
+  uint8_t domain[kMaxDomain];
+  uint32_t len;
+};
+
+static const char kDefaultDomain[] = "SISU-GKR-v1";
+
+// ---------------------------------------------------------------------------
+// circuit creation
+
+// Wiring bytes: for each gate layer i and padded gate g:
+//   u8 type || u32le in1 || u32le in2   (type 2 = absent padding gate)
+static void wiring_digest(const HostCircuit& hc, uint32_t out[8]) {
+  size_t n = 0;
+  for (uint32_t i = 0; i < hc.d; ++i) n += (size_t)hc.W[i] * 9;
+  std::vector<uint8_t> buf(n);
+  uint8_t* p = buf.data();
+  auto put = [&](uint32_t v) {
+    p[0] = (uint8_t)v; p[1] = (uint8_t)(v >> 8); p[2] = (uint8_t)(v >> 16); p[3] = (uint8_t)(v >> 24);
+    p += 4;
+  };
+  for (uint32_t i = 0; i < hc.d; ++i)
+    for (uint32_t g = 0; g < hc.W[i]; ++g) {
+      *p++ = hc.type[i][g];
+      put(hc.in1[i][g]);
+      put(hc.in2[i][g]);
+    }
+  host_statement_digest(buf.data(), n, out);
+}
+
+static int circuit_create(const sisu_layer* layers, uint32_t n_gate_layers, uint32_t input_width,
+                          uint32_t n_copies, bool on_device, sisu_circuit** out) {
+  if (!out) return fail(SISU_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!layers || n_gate_layers == 0) return fail(SISU_ERR_INVALID_ARG, "need at least one gate layer");
+  if (n_gate_layers > SISU_MAX_LAYERS) return fail(SISU_ERR_TOO_LARGE, "more than %u layers", SISU_MAX_LAYERS);
+  if (n_copies == 0 || input_width == 0) return fail(SISU_ERR_INVALID_ARG, "zero copies or zero input width");
+  if (n_copies > SISU_MAX_COPIES) return fail(SISU_ERR_TOO_LARGE, "more than 2^24 copies");
+  const uint32_t d = n_gate_layers;
+  std::unique_ptr<sisu_circuit> cc(new (std::nothrow) sisu_circuit());
+  if (!cc) return fail(SISU_ERR_OOM, "host allocation");
+  HostCircuit& hc = cc->hc;
+  hc.d = d;
+  hc.Creal = n_copies;
+  hc.c = ceil_log2(n_copies);
+  hc.C = 1u << hc.c;
+  hc.s.resize(d + 1);
+  hc.W.resize(d + 1);
+  hc.wreal.resize(d + 1);
+  for (uint32_t i = 0; i <= d; ++i) {
+    uint32_t w = i < d ? layers[i].width : input_width;
+    if (w == 0) return fail(SISU_ERR_INVALID_ARG, "layer %u has zero width", i);
+    if (w > SISU_MAX_WIDTH) return fail(SISU_ERR_TOO_LARGE, "layer %u wider than 2^24", i);
+    hc.wreal[i] = w;
+    hc.s[i] = ceil_log2(w);
+    hc.W[i] = 1u << hc.s[i];
+    if (hc.c + hc.s[i] > 32) return fail(SISU_ERR_TOO_LARGE, "copies x width of layer %u above 2^32", i);
+  }
+  hc.type.resize(d);
+  hc.in1.resize(d);
+  hc.in2.resize(d);
+  for (uint32_t i = 0; i < d; ++i) {
+    const sisu_layer& ly = layers[i];
+    if (!ly.type || !ly.in1 || !ly.in2) return fail(SISU_ERR_INVALID_ARG, "layer %u: NULL wiring array", i);
+    hc.type[i].assign(hc.W[i], 2);
+    hc.in1[i].assign(hc.W[i], 0);
+    hc.in2[i].assign(hc.W[i], 0);
+    for (uint32_t g = 0; g < ly.width; ++g) {
+      if (ly.type[g] > 1) return fail(SISU_ERR_INVALID_ARG, "layer %u gate %u: type %u", i, g, ly.type[g]);
+      if (ly.in1[g] >= hc.wreal[i + 1] || ly.in2[g] >= hc.wreal[i + 1])
+        return fail(SISU_ERR_INDEX_OOB, "layer %u gate %u: input index beyond width %u", i, g, hc.wreal[i + 1]);
+      hc.type[i][g] = ly.type[g];
+      hc.in1[i][g] = ly.in1[g];
+      hc.in2[i][g] = ly.in2[g];
+    }
+  }
+  wiring_digest(hc, hc.wiring_digest);
+  if (!on_device) {
+    *out = cc.release();
+    return SISU_OK;
+  }
+
+  // Device arrays per layer: gate_io (W_i x 8 B), sgate (n_i x 16 B),
+  // off1/off2 ((W_{i+1}+1) x 4 B), pos1/pos2 (n_i x 4 B).
+  struct Lay {
+    std::vector<uint2> io;
+    std::vector<uint4> sg;
+    std::vector<uint32_t> off1, pos1, off2, pos2;
+    uint32_t nmul, ntot;
+  };
+  std::vector<Lay> H(d);
+  size_t bytes = 0;
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  for (uint32_t i = 0; i < d; ++i) {
+    Lay& l = H[i];
+    const uint32_t W = hc.W[i], Wn = hc.W[i + 1];
+    l.io.resize(W);
+    std::vector<uint32_t> muls, adds;
+    for (uint32_t g = 0; g < W; ++g) {
+      l.io[g] = make_uint2(hc.in1[i][g] | ((uint32_t)hc.type[i][g] << 30), hc.in2[i][g]);
+      if (hc.type[i][g] == 1) muls.push_back(g);
+      else if (hc.type[i][g] == 0) adds.push_back(g);
+    }
+    // each type group sorted by in1 (then g) for locality of the row gathers
+    auto by_in1 = [&](uint32_t a, uint32_t b) {
+      return hc.in1[i][a] != hc.in1[i][b] ? hc.in1[i][a] < hc.in1[i][b] : a < b;
+    };
+    std::sort(muls.begin(), muls.end(), by_in1);
+    std::sort(adds.begin(), adds.end(), by_in1);
+    l.nmul = (uint32_t)muls.size();
+    l.ntot = (uint32_t)(muls.size() + adds.size());
+    l.sg.resize(l.ntot);
+    for (uint32_t q = 0; q < l.ntot; ++q) {
+      uint32_t g = q < l.nmul ? muls[q] : adds[q - l.nmul];
+      l.sg[q] = make_uint4(hc.in1[i][g], hc.in2[i][g], g, 0);
+    }
+    auto csr = [&](int which, std::vector<uint32_t>& off, std::vector<uint32_t>& pos) {
+      off.assign(Wn + 1, 0);
+      pos.resize(l.ntot);
+      for (uint32_t q = 0; q < l.ntot; ++q) ++off[(which ? l.sg[q].y : l.sg[q].x) + 1];
+      for (uint32_t x = 0; x < Wn; ++x) off[x + 1] += off[x];
+      std::vector<uint32_t> fill(off.begin(), off.end() - 1);
+      for (uint32_t q = 0; q < l.ntot; ++q) pos[fill[which ? l.sg[q].y : l.sg[q].x]++] = q;
+    };
+    csr(0, l.off1, l.pos1);
+    csr(1, l.off2, l.pos2);
+    bytes += al(l.io.size() * 8) + al(l.sg.size() * 16 + 16) + 2 * al(l.off1.size() * 4) + 2 * al(l.pos1.size() * 4 + 4);
+  }
+  CK(cudaGetDevice(&cc->device), "cudaGetDevice");
+  cudaError_t e = cudaMalloc(&cc->dev, bytes);
+  if (e != cudaSuccess) return fail(SISU_ERR_OOM, "device allocation of %zu bytes for the wiring", bytes);
+  uint8_t* p = (uint8_t*)cc->dev;
+  cc->L.resize(d);
+  auto up = [&](const void* src, size_t n, size_t reserve) -> void* {
+    void* dst = p;
+    if (n) {
+      cudaError_t e2 = cudaMemcpy(dst, src, n, cudaMemcpyHostToDevice);
+      if (e2 != cudaSuccess) return nullptr;
+    }
+    p += al(reserve);
+    return dst;
+  };
+  for (uint32_t i = 0; i < d; ++i) {
+    Lay& l = H[i];
+    DevLayer& D = cc->L[i];
+    D.gate_io = (const uint2*)up(l.io.data(), l.io.size() * 8, l.io.size() * 8);
+    D.sgate = (const uint4*)up(l.sg.data(), l.sg.size() * 16, l.sg.size() * 16 + 16);
+    D.off1 = (const uint32_t*)up(l.off1.data(), l.off1.size() * 4, l.off1.size() * 4);
+    D.pos1 = (const uint32_t*)up(l.pos1.data(), l.pos1.size() * 4, l.pos1.size() * 4 + 4);
+    D.off2 = (const uint32_t*)up(l.off2.data(), l.off2.size() * 4, l.off2.size() * 4);
+    D.pos2 = (const uint32_t*)up(l.pos2.data(), l.pos2.size() * 4, l.pos2.size() * 4 + 4);
+    if (!D.gate_io || !D.sgate || !D.off1 || !D.pos1 || !D.off2 || !D.pos2)
+      return fail(SISU_ERR_CUDA, "upload of the wiring failed");
+    D.nmul = l.nmul;
+    D.ntot = l.ntot;
+  }
+  *out = cc.release();
+  return SISU_OK;
+}
+
+extern "C" int sisu_circuit_create(const sisu_layer* layers, uint32_t n_gate_layers, uint32_t input_width,
+                                   uint32_t n_copies, sisu_circuit** out) {
+  return circuit_create(layers, n_gate_layers, input_width, n_copies, true, out);
+}
+
+extern "C" int sisu_circuit_create_host(const sisu_layer* layers, uint32_t n_gate_layers, uint32_t input_width,
+                                        uint32_t n_copies, sisu_circuit** out) {
+  return circuit_create(layers, n_gate_layers, input_width, n_copies, false, out);
+}
+
+static bool has_device(const sisu_circuit* circ) { return circ && circ->dev; }
+
+extern "C" void sisu_circuit_destroy(sisu_circuit* circ) { delete circ; }
+
+extern "C" int sisu_circuit_info(const sisu_circuit* circ, uint32_t* depth, uint32_t* log_copies,
+                                 uint32_t* log_widths, size_t* proof_len, size_t* eval_bytes) {
+  if (!circ) return fail(SISU_ERR_INVALID_ARG, "circuit is NULL");
+  const HostCircuit& hc = circ->hc;
+  if (depth) *depth = hc.d;
+  if (log_copies) *log_copies = hc.c;
+  if (log_widths)
+    for (uint32_t i = 0; i <= hc.d; ++i) log_widths[i] = hc.s[i];
+  if (proof_len) *proof_len = hc.proof_len();
+  if (eval_bytes) {
+    size_t n = 0;
+    for (uint32_t i = 0; i <= hc.d; ++i) n += ((size_t)hc.C << hc.s[i]) * 32;
+    *eval_bytes = n;
+  }
+  return SISU_OK;
+}
+
+// ---------------------------------------------------------------------------
+// evaluation
+
+static int eval_run(sisu_eval* ev, const uint8_t* inputs, int on_device, cudaStream_t st) {
+  const sisu_circuit* cc = ev->circ;
+  const HostCircuit& hc = cc->hc;
+  const uint32_t d = hc.d;
+  const size_t in_bytes = (size_t)hc.Creal * hc.wreal[d] * 32;
+  const bool padded = hc.Creal != hc.C || hc.wreal[d] != hc.W[d];
+  const uint32_t* src;
+  if (on_device) {
+    if (((uintptr_t)inputs & 15) != 0) return fail(SISU_ERR_INVALID_ARG, "device inputs not 16-byte aligned");
+    src = (const uint32_t*)inputs;
+  } else {
+    uint32_t* dst = padded ? ev->stage : ev->V[d];
+    CK(cudaMemcpyAsync(dst, inputs, in_bytes, cudaMemcpyHostToDevice, st), "input copy");
+    src = dst;
+  }
+  CK(cudaMemsetAsync(ev->flag, 0, 4, st), "memset");
+  {
+    ProfScope ps(kProfInputs, (double)((size_t)hc.C << hc.s[d]), st);
+    CK(launch_inputs_to_mont(src, ev->V[d], hc.c, hc.s[d], hc.Creal, hc.wreal[d], ev->flag, st), "input conversion");
+  }
+  for (int i = (int)d - 1; i >= 0; --i) {
+    ProfScope ps(kProfEval, (double)hc.C * cc->L[i].nmul, st);
+    CK(launch_eval_layer(ev->V[i + 1], ev->V[i], cc->L[i].gate_io, hc.c, hc.s[i], hc.s[i + 1], st), "eval layer");
+  }
+  CK(cudaMemcpyAsync(ev->host_flag, ev->flag, 4, cudaMemcpyDeviceToHost, st), "flag copy");
+  CK(cudaStreamSynchronize(st), "eval");
+  if (*ev->host_flag & 1u) return fail(SISU_ERR_NOT_CANONICAL, "an input element is not below r");
+  return SISU_OK;
+}
+
+extern "C" int sisu_circuit_eval(const sisu_circuit* circ, const uint8_t* inputs, int inputs_on_device,
+                                 void* stream, sisu_eval** out) {
+  if (!out) return fail(SISU_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!circ || !inputs) return fail(SISU_ERR_INVALID_ARG, "NULL circuit or inputs");
+  if (!has_device(circ)) return fail(SISU_ERR_INVALID_ARG, "circuit was created for host verification only");
+  const HostCircuit& hc = circ->hc;
+  std::unique_ptr<sisu_eval> ev(new (std::nothrow) sisu_eval());
+  if (!ev) return fail(SISU_ERR_OOM, "host allocation");
+  ev->circ = circ;
+  size_t total = 0;
+  std::vector<size_t> offs(hc.d + 1);
+  for (uint32_t i = 0; i <= hc.d; ++i) {
+    offs[i] = total;
+    total += ((size_t)hc.C << hc.s[i]) * 32;
+  }
+  if (cudaMalloc(&ev->dev, total + 256) != cudaSuccess)
+    return fail(SISU_ERR_OOM, "device allocation of %zu bytes for the layer values", total);
+  ev->V.resize(hc.d + 1);
+  for (uint32_t i = 0; i <= hc.d; ++i) ev->V[i] = (uint32_t*)((uint8_t*)ev->dev + offs[i]);
+  ev->flag = (uint32_t*)((uint8_t*)ev->dev + total);
+  const bool padded = hc.Creal != hc.C || hc.wreal[hc.d] != hc.W[hc.d];
+  if (padded && !inputs_on_device) {
+    if (cudaMalloc(&ev->stage, (size_t)hc.Creal * hc.wreal[hc.d] * 32) != cudaSuccess)
+      return fail(SISU_ERR_OOM, "device allocation for the input staging");
+  }
+  CK(cudaMallocHost(&ev->host_flag, 4), "cudaMallocHost");
+  int rc = eval_run(ev.get(), inputs, inputs_on_device, (cudaStream_t)stream);
+  if (rc != SISU_OK) return rc;
+  *out = ev.release();
+  return SISU_OK;
+}
+
+extern "C" int sisu_eval_update(sisu_eval* ev, const uint8_t* inputs, int inputs_on_device, void* stream) {
+  if (!ev || !inputs) return fail(SISU_ERR_INVALID_ARG, "NULL eval or inputs");
+  const HostCircuit& hc = ev->circ->hc;
+  const bool padded = hc.Creal != hc.C || hc.wreal[hc.d] != hc.W[hc.d];
+  if (padded && !inputs_on_device && !ev->stage) {
+    if (cudaMalloc(&ev->stage, (size_t)hc.Creal * hc.wreal[hc.d] * 32) != cudaSuccess)
+      return fail(SISU_ERR_OOM, "device allocation for the input staging");
+  }
+  return eval_run(ev, inputs, inputs_on_device, (cudaStream_t)stream);
+}
+
+extern "C" int sisu_eval_outputs(const sisu_eval* ev, uint8_t* out, size_t cap, int out_on_device, void* stream) {
+  if (!ev || !out) return fail(SISU_ERR_INVALID_ARG, "NULL eval or output");
+  const HostCircuit& hc = ev->circ->hc;
+  const size_t n = (size_t)hc.Creal * hc.wreal[0] * 32;
+  if (cap < n) return fail(SISU_ERR_BUFFER, "output buffer of %zu bytes, need %zu", cap, n);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (out_on_device) {
+    if (((uintptr_t)out & 15) != 0) return fail(SISU_ERR_INVALID_ARG, "device output not 16-byte aligned");
+    CK(launch_layer_to_canonical(ev->V[0], (uint32_t*)out, hc.c, hc.s[0], hc.Creal, hc.wreal[0], st), "outputs");
+    return SISU_OK;
+  }
+  uint32_t* tmp = nullptr;
+  CK(cudaMallocAsync(&tmp, n, st), "cudaMallocAsync");
+  int rc = launch_layer_to_canonical(ev->V[0], tmp, hc.c, hc.s[0], hc.Creal, hc.wreal[0], st);
+  if (rc == 0) rc = cudaMemcpyAsync(out, tmp, n, cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(tmp, st);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (rc) return cuda_fail((cudaError_t)rc, "outputs");
+  if (e) return cuda_fail(e, "outputs");
+  return SISU_OK;
+}
+
+extern "C" int sisu_eval_layer(const sisu_eval* ev, uint32_t layer, uint8_t* out, size_t cap, void* stream) {
+  if (!ev || !out) return fail(SISU_ERR_INVALID_ARG, "NULL eval or output");
+  const HostCircuit& hc = ev->circ->hc;
+  if (layer > hc.d) return fail(SISU_ERR_INVALID_ARG, "layer %u beyond depth %u", layer, hc.d);
+  const size_t n = ((size_t)hc.C << hc.s[layer]) * 32;
+  if (cap < n) return fail(SISU_ERR_BUFFER, "buffer of %zu bytes, need %zu", cap, n);
+  cudaStream_t st = (cudaStream_t)stream;
+  uint32_t* tmp = nullptr;
+  CK(cudaMallocAsync(&tmp, n, st), "cudaMallocAsync");
+  int rc = launch_layer_to_canonical(ev->V[layer], tmp, hc.c, hc.s[layer], hc.C, hc.W[layer], st);
+  if (rc == 0) rc = cudaMemcpyAsync(out, tmp, n, cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(tmp, st);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (rc) return cuda_fail((cudaError_t)rc, "layer copy");
+  if (e) return cuda_fail(e, "layer copy");
+  return SISU_OK;
+}
+
+extern "C" void sisu_eval_destroy(sisu_eval* ev) { delete ev; }
+
+// ---------------------------------------------------------------------------
+// transcript domain
+
+extern "C" int sisu_transcript_create(const uint8_t* domain, size_t len, sisu_transcript** out) {
+  if (!out) return fail(SISU_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (len > kMaxDomain) return fail(SISU_ERR_INVALID_ARG, "domain longer than %u bytes", kMaxDomain);
+  if (len && !domain) return fail(SISU_ERR_INVALID_ARG, "NULL domain with nonzero length");
+  sisu_transcript* t = new (std::nothrow) sisu_transcript();
+  if (!t) return fail(SISU_ERR_OOM, "host allocation");
+  if (!domain || len == 0) {
+    t->len = (uint32_t)strlen(kDefaultDomain);
+    memcpy(t->domain, kDefaultDomain, t->len);
+  } else {
+    t->len = (uint32_t)len;
+    memcpy(t->domain, domain, len);
+  }
+  *out = t;
+  return SISU_OK;
+}
+
+extern "C" void sisu_transcript_destroy(sisu_transcript* tr) { delete tr; }
+
+// ---------------------------------------------------------------------------
+// proving
+
+static int workspace_alloc(sisu_eval* ev) {
+  const HostCircuit& hc = ev->circ->hc;
+  const sisu_circuit* cc = ev->circ;
+  uint32_t wmax_next = 1, wmax = 1, nmax = 1;
+  for (uint32_t i = 0; i < hc.d; ++i) {
+    wmax_next = std::max(wmax_next, hc.W[i + 1]);
+    nmax = std::max(nmax, cc->L[i].ntot);
+  }
+  for (uint32_t i = 0; i <= hc.d; ++i) wmax = std::max(wmax, hc.W[i]);
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t half = hc.C >= 2 ? (size_t)(hc.C / 2) * wmax_next * 32 : 32;
+  const size_t dig = std::max(digest_scratch_words((size_t)hc.C * hc.W[hc.d] * 32),
+                              digest_scratch_words((size_t)hc.C * hc.W[0] * 32)) * 4;
+  size_t sizes[12] = {half,
+                      (size_t)hc.C * 32,
+                      (size_t)nmax * 32,
+                      (size_t)wmax_next * 32,
+                      (size_t)wmax_next * 32,
+                      (size_t)wmax_next * 32,
+                      (size_t)wmax_next * 32,
+                      (size_t)wmax * 32,
+                      (size_t)kMaxPartials * 4 * 32,
+                      dig,
+                      sizeof(DevState),
+                      hc.proof_len()};
+  size_t total = 0;
+  for (size_t s : sizes) total += al(s);
+  std::unique_ptr<Workspace> ws(new (std::nothrow) Workspace());
+  if (!ws) return fail(SISU_ERR_OOM, "host allocation");
+  if (cudaMalloc(&ws->dev, total) != cudaSuccess)
+    return fail(SISU_ERR_OOM, "device allocation of %zu bytes for the prover workspace", total);
+  uint8_t* p = (uint8_t*)ws->dev;
+  void* ptrs[12];
+  for (int k = 0; k < 12; ++k) {
+    ptrs[k] = p;
+    p += al(sizes[k]);
+  }
+  ws->T = (uint32_t*)ptrs[0];
+  ws->E = (uint32_t*)ptrs[1];
+  ws->om = (uint32_t*)ptrs[2];
+  ws->At = (uint32_t*)ptrs[3];
+  ws->H1 = (uint32_t*)ptrs[4];
+  ws->H2 = (uint32_t*)ptrs[5];
+  ws->Ay = (uint32_t*)ptrs[6];
+  ws->Q = (uint32_t*)ptrs[7];
+  ws->partials = (uint32_t*)ptrs[8];
+  ws->dscratch = (uint32_t*)ptrs[9];
+  ws->S = (DevState*)ptrs[10];
+  ws->proof = (uint8_t*)ptrs[11];
+  ws->proof_len = hc.proof_len();
+  if (cudaMallocHost(&ws->host, ws->proof_len + 16) != cudaSuccess)
+    return fail(SISU_ERR_OOM, "pinned host allocation");
+  // the proof header is fixed by the circuit
+  std::vector<uint8_t> hdr(8 + 4 * ((size_t)hc.d + 3));
+  memcpy(hdr.data(), "SISUGKR1", 8);
+  auto put = [&](size_t at, uint32_t v) {
+    hdr[at] = (uint8_t)v; hdr[at + 1] = (uint8_t)(v >> 8); hdr[at + 2] = (uint8_t)(v >> 16); hdr[at + 3] = (uint8_t)(v >> 24);
+  };
+  put(8, hc.d);
+  put(12, hc.c);
+  for (uint32_t i = 0; i <= hc.d; ++i) put(16 + 4 * (size_t)i, hc.s[i]);
+  CK(cudaMemcpy(ws->proof, hdr.data(), hdr.size(), cudaMemcpyHostToDevice), "header upload");
+  CK(cudaMemset(ws->S, 0, sizeof(DevState)), "memset");
+  ev->ws = std::move(ws);
+  return SISU_OK;
+}
+
+// Enqueue one whole proof on `st` (no host synchronisation).
+static int enqueue_prove(const sisu_circuit* cc, sisu_eval* ev, const sisu_transcript* tr, cudaStream_t st) {
+  const HostCircuit& hc = cc->hc;
+  Workspace& w = *ev->ws;
+  const uint32_t d = hc.d, c = hc.c;
+  // statement digests of the inputs and outputs (the wiring's is cached)
+  {
+    ProfScope ps(kProfDigest, 0, st);
+    CK(launch_digest_table(ev->V[d], (size_t)hc.C << hc.s[d], w.dscratch, w.S->dig_in, st), "input digest");
+    CK(launch_digest_table(ev->V[0], (size_t)hc.C << hc.s[0], w.dscratch, w.S->dig_out, st), "output digest");
+  }
+  InitParams ip;
+  memset(&ip, 0, sizeof ip);
+  if (tr) {
+    memcpy(ip.domain, tr->domain, tr->len);
+    ip.dlen = tr->len;
+  } else {
+    ip.dlen = (uint32_t)strlen(kDefaultDomain);
+    memcpy(ip.domain, kDefaultDomain, ip.dlen);
+  }
+  ip.d = d;
+  ip.c = c;
+  for (uint32_t i = 0; i <= d; ++i) ip.s[i] = hc.s[i];
+  memcpy(ip.wiring, hc.wiring_digest, 32);
+  {
+    ProfScope ps(kProfTranscript, 0, st);
+    CK(launch_transcript_init(ip, w.S, st), "transcript init");
+  }
+
+  size_t off = 8 + 4 * ((size_t)d + 3);
+  for (uint32_t i = 0; i < d; ++i) {
+    const DevLayer& L = cc->L[i];
+    const uint32_t s = hc.s[i + 1], Wn = hc.W[i + 1], sn = hc.s[i + 1];
+    {
+      ProfScope ps(kProfLayerInit, (double)hc.C * c + (double)L.ntot * (i == 0 ? hc.s[0] : 2.0 * hc.s[i] + 2), st);
+      CK(launch_layer_init(w.S, i, c, hc.s[i], L, w.E, w.om, st), "layer init");
+    }
+    // copy phase: c rounds, each followed by the fold of its challenge
+    const uint32_t* A = ev->V[i + 1];
+    const double per_pair = 5.0 * L.nmul + 2.0 * (L.ntot - L.nmul) + 4.0;
+    for (uint32_t k = 0; k < c; ++k) {
+      const uint32_t* tab = k == 0 ? ev->V[i + 1] : w.T;
+      const uint32_t h = hc.C >> (k + 1);
+      {
+        ProfScope ps(kProfCopyRound, per_pair * h, st);
+        CK(launch_copy_round(tab, sn, h, w.E, w.om, L, w.partials, w.S, w.proof, off + 32 * 4 * (size_t)k, k, st),
+           "copy round");
+      }
+      {
+        ProfScope ps(kProfCopyFold, (double)h * Wn + h, st);
+        CK(launch_copy_fold(tab, w.T, sn, h, w.E, w.S, k, st), "copy fold");
+      }
+      A = w.T;
+    }
+    const size_t offx = off + 32 * 4 * (size_t)c;
+    const size_t offy = offx + 32 * 3 * (size_t)s;
+    const size_t offv = offy + 32 * 3 * (size_t)s;
+    // phase over x
+    {
+      ProfScope ps(kProfPhaseInit, (double)L.ntot + 2.0 * Wn, st);
+      CK(launch_xinit(A, w.E, w.om, L, Wn, w.At, w.H1, w.H2, w.Ay, st), "x init");
+    }
+    for (uint32_t k = 0; k < s; ++k) {
+      ProfScope ps(kProfGateRound, (double)(Wn >> k) / 2 * (k ? 9.0 : 3.0), st);
+      CK(launch_gate_round(w.At, w.H1, w.H2, Wn >> k, 0, k, w.partials, w.S, w.proof, offx + 96 * (size_t)k, st),
+         "x round");
+    }
+    // phase over y
+    {
+      ProfScope ps(kProfPhaseInit, (double)Wn * s + L.ntot + 3.0 * Wn, st);
+      CK(launch_eq_rx(w.S, s, Wn, w.Q, w.At, st), "eq(r_x)");
+      CK(launch_yinit(w.E, w.om, w.Q, L, Wn, w.H1, w.H2, w.S, st), "y init");
+    }
+    for (uint32_t k = 0; k < s; ++k) {
+      ProfScope ps(kProfGateRound, (double)(Wn >> k) / 2 * (k ? 9.0 : 3.0), st);
+      CK(launch_gate_round(w.Ay, w.H1, w.H2, Wn >> k, 1, k, w.partials, w.S, w.proof, offy + 96 * (size_t)k, st),
+         "y round");
+    }
+    {
+      ProfScope ps(kProfTranscript, 0, st);
+      CK(launch_layer_end(w.S, w.Ay, s, w.proof, offv, i + 1 == d, st), "layer end");
+    }
+    off = offv + 64;
+  }
+  return SISU_OK;
+}
+
+extern "C" int sisu_gkr_prove_into(const sisu_circuit* circ, sisu_eval* ev, const sisu_transcript* tr, void* stream,
+                                   uint8_t* proof, size_t cap, size_t* proof_len) {
+  if (!circ || !ev || !proof) return fail(SISU_ERR_INVALID_ARG, "NULL circuit, eval or proof buffer");
+  if (ev->circ != circ) return fail(SISU_ERR_INVALID_ARG, "eval handle belongs to another circuit");
+  const size_t n = circ->hc.proof_len();
+  if (proof_len) *proof_len = n;
+  if (cap < n) return fail(SISU_ERR_BUFFER, "proof buffer of %zu bytes, need %zu", cap, n);
+  if (!ev->ws) {
+    int rc = workspace_alloc(ev);
+    if (rc) return rc;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  Workspace& w = *ev->ws;
+  int rc = enqueue_prove(circ, ev, tr, st);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(w.host, w.proof, n, cudaMemcpyDeviceToHost, st), "proof copy");
+  CK(cudaMemcpyAsync(w.host + ((n + 3) & ~(size_t)3), &w.S->error, 4, cudaMemcpyDeviceToHost, st), "flag copy");
+  CK(cudaStreamSynchronize(st), "prove");
+  uint32_t err;
+  memcpy(&err, w.host + ((n + 3) & ~(size_t)3), 4);
+  if (err) return fail(SISU_ERR_CUDA, "device-side check failed (code %u)", err);
+  memcpy(proof, w.host, n);
+  return SISU_OK;
+}
+
+extern "C" int sisu_gkr_prove(const sisu_circuit* circ, sisu_eval* ev, const sisu_transcript* tr, void* stream,
+                              uint8_t** proof, size_t* proof_len) {
+  if (!proof || !circ) return fail(SISU_ERR_INVALID_ARG, "NULL proof pointer or circuit");
+  *proof = nullptr;
+  const size_t n = circ->hc.proof_len();
+  uint8_t* buf = (uint8_t*)malloc(n);
+  if (!buf) return fail(SISU_ERR_OOM, "host allocation of %zu bytes", n);
+  int rc = sisu_gkr_prove_into(circ, ev, tr, stream, buf, n, proof_len);
+  if (rc) {
+    free(buf);
+    return rc;
+  }
+  *proof = buf;
+  return SISU_OK;
+}
+
+extern "C" int sisu_gkr_verify(const sisu_circuit* circ, const uint8_t* inputs, const uint8_t* outputs,
+                               const uint8_t* proof, size_t proof_len, const uint8_t* domain, size_t dlen) {
+  if (!circ || !inputs || !outputs || !proof) return fail(SISU_ERR_INVALID_ARG, "NULL argument");
+  if (dlen > kMaxDomain) return fail(SISU_ERR_INVALID_ARG, "domain longer than %u bytes", kMaxDomain);
+  const uint8_t* dom = domain;
+  size_t dl = dlen;
+  if (!domain || dlen == 0) {
+    dom = (const uint8_t*)kDefaultDomain;
+    dl = strlen(kDefaultDomain);
+  }
+  int rc = host_verify(circ->hc, inputs, outputs, proof, proof_len, dom, dl);
+  if (rc == SISU_ERR_REJECT) return fail(rc, "proof rejected");
+  if (rc == SISU_ERR_NOT_CANONICAL) return fail(rc, "an input or output element is not below r");
+  return rc;
+}
+
+// ---------------------------------------------------------------------------
+// field core, digests, microbenchmarks
+
+extern "C" int sisu_fr_batch(int op, const uint8_t* a, const uint8_t* b, uint8_t* out, size_t n, void* stream) {
+  if (op < 0 || op > 4) return fail(SISU_ERR_INVALID_ARG, "op %d", op);
+  if (!a || !out || (op != 3 && !b)) return fail(SISU_ERR_INVALID_ARG, "NULL operand");
+  if (n == 0) return SISU_OK;
+  if ((((uintptr_t)a | (uintptr_t)out | (uintptr_t)(b ? b : a)) & 15) != 0)
+    return fail(SISU_ERR_INVALID_ARG, "device arrays must be 16-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  uint32_t *flag = nullptr, host_flag = 0;
+  CK(cudaMallocAsync(&flag, 4, st), "cudaMallocAsync");
+  CK(cudaMemsetAsync(flag, 0, 4, st), "memset");
+  int rc = launch_fr_batch(op, (const uint32_t*)a, (const uint32_t*)(b ? b : a), (uint32_t*)out, n, flag, st);
+  if (rc == 0) rc = cudaMemcpyAsync(&host_flag, flag, 4, cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(flag, st);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (rc) return cuda_fail((cudaError_t)rc, "field op");
+  if (e) return cuda_fail(e, "field op");
+  if (host_flag & 1u) return fail(SISU_ERR_NOT_CANONICAL, "an operand is not below r");
+  if (host_flag & 2u) return fail(SISU_ERR_ZERO_INVERSE, "inverse of zero");
+  return SISU_OK;
+}
+
+extern "C" int sisu_statement_digest(const uint8_t* data, size_t len, uint8_t* out, void* stream) {
+  if (!out || (len && !data)) return fail(SISU_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t words = digest_scratch_words(len) + 8;
+  uint32_t* scratch = nullptr;
+  CK(cudaMallocAsync(&scratch, words * 4, st), "cudaMallocAsync");
+  uint32_t h[8];
+  int rc = launch_digest_bytes(data, len, scratch, scratch + words - 8, st);
+  if (rc == 0) rc = cudaMemcpyAsync(h, scratch + words - 8, 32, cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(scratch, st);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (rc) return cuda_fail((cudaError_t)rc, "digest");
+  if (e) return cuda_fail(e, "digest");
+  for (int i = 0; i < 8; ++i) {
+    out[4 * i] = (uint8_t)(h[i] >> 24); out[4 * i + 1] = (uint8_t)(h[i] >> 16);
+    out[4 * i + 2] = (uint8_t)(h[i] >> 8); out[4 * i + 3] = (uint8_t)h[i];
+  }
+  return SISU_OK;
+}
+
+extern "C" int sisu_microbench(int kind, uint32_t blocks, uint32_t threads, uint32_t iters, void* stream, double* ms,
+                               double* ops) {
+  if (kind < 0 || kind > 2 || !blocks || !threads || threads > 1024 || !ms || !ops)
+    return fail(SISU_ERR_INVALID_ARG, "bad microbenchmark arguments");
+  int rc = run_microbench(kind, blocks, threads, iters, stream, ms, ops);
+  if (rc) return cuda_fail((cudaError_t)rc, "microbenchmark");
+  return SISU_OK;
+}
+
+extern "C" uint64_t sisu_kernel_launches(void) { return launches_add(0); }
+extern "C" void sisu_free(void* p) { free(p); }
+extern "C" const char* sisu_last_error(void) { return g_err; }
+extern "C" const char* sisu_version(void) { return "sisu-b300 0.1 (sm_103a)"; }

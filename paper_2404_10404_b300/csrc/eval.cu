@@ -1,0 +1,237 @@
+// Forward evaluation of the circuit and Merkle statement digests.
+//
+// Data layout in HBM: layer l's values are a copy-major table of
+// 2^c x 2^s_l elements, element (b, g) at index b * 2^s_l + g, each element
+// 32 bytes (8 limbs, Montgomery form) so that one element is two 128-bit
+// accesses and a gathered element touches exactly one 32-byte sector.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "internal.h"
+#include "launch.cuh"
+#include "sha256.cuh"
+
+namespace sisu {
+
+// ---------------------------------------------------------------------------
+// inputs: canonical -> Montgomery, zero padding, canonicity check
+
+__global__ void k_inputs_to_mont(const uint32_t* in, uint32_t* V, uint32_t c, uint32_t s, uint32_t Creal,
+                                 uint32_t wreal, uint32_t* err) {
+  const size_t total = (size_t)1 << (c + s);
+  const uint32_t mask = (1u << s) - 1u;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    uint32_t b = (uint32_t)(idx >> s), x = (uint32_t)(idx & mask);
+    Fr v = fr_zero();
+    if (b < Creal && x < wreal) {
+      Fr raw = fr_load(in, (size_t)b * wreal + x);
+      if (!fr_lt_modulus(raw)) {
+        atomicOr(err, 1u);
+        raw = fr_zero();
+      }
+      v = fr_from_canonical(raw);
+    }
+    fr_store(V, idx, v);
+  }
+}
+
+int launch_inputs_to_mont(const uint32_t* in, uint32_t* V, uint32_t c, uint32_t s, uint32_t Creal,
+                          uint32_t wreal, uint32_t* err, void* stream) {
+  size_t n = (size_t)1 << (c + s);
+  k_inputs_to_mont<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(in, V, c, s, Creal, wreal, err);
+  return post_launch();
+}
+
+// Montgomery layer -> canonical, unpadded (n_copies x width)
+__global__ void k_layer_to_canonical(const uint32_t* V, uint32_t* out, uint32_t s, uint32_t Creal, uint32_t wreal) {
+  const size_t total = (size_t)Creal * wreal;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    size_t b = idx / wreal, x = idx % wreal;
+    fr_store(out, idx, fr_to_canonical(fr_load(V, (b << s) + x)));
+  }
+}
+
+int launch_layer_to_canonical(const uint32_t* V, uint32_t* out, uint32_t c, uint32_t s, uint32_t Creal,
+                              uint32_t wreal, void* stream) {
+  (void)c;
+  size_t n = (size_t)Creal * wreal;
+  k_layer_to_canonical<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(V, out, s, Creal, wreal);
+  return post_launch();
+}
+
+// ---------------------------------------------------------------------------
+// forward evaluation of one layer (Sec. 2.2): V_i(b, g) = op_g(V_{i+1}(b, in1 g), V_{i+1}(b, in2 g))
+
+__global__ void k_eval_layer(const uint32_t* __restrict__ Vn, uint32_t* __restrict__ V,
+                             const uint2* __restrict__ gates, uint32_t c, uint32_t s, uint32_t sn) {
+  const size_t total = (size_t)1 << (c + s);
+  const uint32_t mask = (1u << s) - 1u;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    uint32_t b = (uint32_t)(idx >> s), g = (uint32_t)(idx & mask);
+    uint2 gw = gates[g];
+    uint32_t t = gw.x >> 30;
+    Fr out = fr_zero();
+    if (t != 2u) {
+      const uint32_t* row = Vn + (((size_t)b << sn) << 3);
+      Fr x = fr_load(row, gw.x & 0x3fffffffu), y = fr_load(row, gw.y);
+      out = t == 0u ? fr_add(x, y) : fr_mul(x, y);
+    }
+    fr_store(V, idx, out);
+  }
+}
+
+int launch_eval_layer(const uint32_t* Vn, uint32_t* V, const uint2* gate_io, uint32_t c, uint32_t s,
+                      uint32_t sn, void* stream) {
+  size_t n = (size_t)1 << (c + s);
+  k_eval_layer<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(Vn, V, gate_io, c, s, sn);
+  return post_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Merkle statement digest over 1024-byte chunks (32 field elements each):
+//   leaf = H(chunk || 0x00), node = H(left || right || 0x01),
+//   odd last node moved up, digest = H(root || u64le len || 0x03).
+
+__device__ __forceinline__ void elem_words(const uint32_t* tab, size_t i, uint32_t* w) {
+  Fr v = fr_to_canonical(fr_load(tab, i));
+#pragma unroll
+  for (int k = 0; k < 8; ++k) w[k] = bswap32(v.v[k]);
+}
+
+__global__ void k_digest_leaves_table(const uint32_t* __restrict__ tab, size_t nelem, uint32_t* __restrict__ out) {
+  const size_t nleaf = (nelem + 31) / 32;
+  for (size_t L = blockIdx.x * (size_t)blockDim.x + threadIdx.x; L < nleaf; L += (size_t)gridDim.x * blockDim.x) {
+    const size_t first = L * 32;
+    const uint32_t count = (uint32_t)min((size_t)32, nelem - first);
+    uint32_t h[8], blk[16];
+    sha256_init(h);
+    uint32_t e = 0;
+    for (; e + 1 < count; e += 2) {
+      elem_words(tab, first + e, blk);
+      elem_words(tab, first + e + 1, blk + 8);
+      sha256_compress(h, blk);
+    }
+    const uint64_t bits = ((uint64_t)count * 32 + 1) * 8;
+    if (e < count) {  // one element left: it, the tag and the length fit one block
+      elem_words(tab, first + e, blk);
+      blk[8] = 0x00800000u;
+#pragma unroll
+      for (int k = 9; k < 14; ++k) blk[k] = 0;
+    } else {
+      blk[0] = 0x00800000u;
+#pragma unroll
+      for (int k = 1; k < 14; ++k) blk[k] = 0;
+    }
+    blk[14] = (uint32_t)(bits >> 32);
+    blk[15] = (uint32_t)bits;
+    sha256_compress(h, blk);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) out[L * 8 + k] = h[k];
+  }
+}
+
+__global__ void k_digest_leaves_bytes(const uint8_t* __restrict__ data, size_t len, uint32_t* __restrict__ out) {
+  const size_t nleaf = (len + 1023) / 1024;
+  for (size_t L = blockIdx.x * (size_t)blockDim.x + threadIdx.x; L < nleaf; L += (size_t)gridDim.x * blockDim.x) {
+    size_t off = L * 1024, m = min((size_t)1024, len - off);
+    Sha256Stream h;
+    h.begin();
+    h.bytes(data + off, m);
+    h.byte(0x00);
+    uint32_t o[8];
+    h.end(o);
+    for (int k = 0; k < 8; ++k) out[L * 8 + k] = o[k];
+  }
+}
+
+__global__ void k_digest_level(const uint32_t* __restrict__ src, size_t n, uint32_t* __restrict__ dst) {
+  const size_t m = (n + 1) / 2;
+  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < m; j += (size_t)gridDim.x * blockDim.x) {
+    if (2 * j + 1 < n) {
+      uint32_t h[8], blk[16];
+      sha256_init(h);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        blk[k] = src[16 * j + k];
+        blk[8 + k] = src[16 * j + 8 + k];
+      }
+      sha256_compress(h, blk);
+      blk[0] = 0x01800000u;
+#pragma unroll
+      for (int k = 1; k < 15; ++k) blk[k] = 0;
+      blk[15] = 65 * 8;
+      sha256_compress(h, blk);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) dst[8 * j + k] = h[k];
+    } else {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) dst[8 * j + k] = src[16 * j + k];
+    }
+  }
+}
+
+__global__ void k_digest_final(const uint32_t* root, uint64_t len, int empty, uint32_t* out) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  uint32_t r[8], blk[16], h[8];
+  if (empty) {
+    sha256_init(r);
+    blk[0] = 0x02800000u;
+    for (int k = 1; k < 15; ++k) blk[k] = 0;
+    blk[15] = 8;
+    sha256_compress(r, blk);
+  } else {
+    for (int k = 0; k < 8; ++k) r[k] = root[k];
+  }
+  for (int k = 0; k < 8; ++k) blk[k] = r[k];
+  blk[8] = bswap32((uint32_t)len);
+  blk[9] = bswap32((uint32_t)(len >> 32));
+  blk[10] = 0x03800000u;
+  for (int k = 11; k < 15; ++k) blk[k] = 0;
+  blk[15] = 41 * 8;
+  sha256_init(h);
+  sha256_compress(h, blk);
+  for (int k = 0; k < 8; ++k) out[k] = h[k];
+}
+
+size_t digest_scratch_words(size_t len_bytes) { return 2 * 8 * ((len_bytes + 1023) / 1024) + 16; }
+
+static int digest_tree(size_t nleaf, uint64_t len, uint32_t* scratch, uint32_t* out_words, cudaStream_t st) {
+  uint32_t* a = scratch;
+  uint32_t* b = scratch + 8 * nleaf + 8;
+  size_t n = nleaf;
+  while (n > 1) {
+    size_t m = (n + 1) / 2;
+    k_digest_level<<<grid_for(m, 128), 128, 0, st>>>(a, n, b);
+    if (int e = post_launch()) return e;
+    std::swap(a, b);
+    n = m;
+  }
+  k_digest_final<<<1, 32, 0, st>>>(a, len, nleaf == 0, out_words);
+  return post_launch();
+}
+
+int launch_digest_table(const uint32_t* tab, size_t nelem, uint32_t* scratch, uint32_t* out_words, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  size_t nleaf = (nelem + 31) / 32;
+  if (nleaf) {
+    k_digest_leaves_table<<<grid_for(nleaf, 128, 32), 128, 0, st>>>(tab, nelem, scratch);
+    if (int e = post_launch()) return e;
+  }
+  return digest_tree(nleaf, (uint64_t)nelem * 32, scratch, out_words, st);
+}
+
+int launch_digest_bytes(const uint8_t* data, size_t len, uint32_t* scratch, uint32_t* out_words, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  size_t nleaf = (len + 1023) / 1024;
+  if (nleaf) {
+    k_digest_leaves_bytes<<<grid_for(nleaf, 128, 32), 128, 0, st>>>(data, len, scratch);
+    if (int e = post_launch()) return e;
+  }
+  return digest_tree(nleaf, (uint64_t)len, scratch, out_words, st);
+}
+
+}  // namespace sisu

@@ -1,0 +1,165 @@
+// Field-core batch operations and integer-pipe microbenchmarks.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "internal.h"
+#include "launch.cuh"
+#include "sha256.cuh"
+
+namespace sisu {
+
+// ---------------------------------------------------------------------------
+// field core on device arrays (canonical in and out)
+
+__device__ __forceinline__ Fr fr_one_minus_f(const Fr& z) { return fr_sub(fr_one(), z); }
+
+constexpr int kInvBatch = 8;
+
+__global__ void k_fr_batch(int op, const uint32_t* __restrict__ a, const uint32_t* __restrict__ b,
+                           uint32_t* __restrict__ out, size_t n, uint32_t* flags) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const size_t tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (op != 3) {
+    for (size_t i = tid; i < n; i += stride) {
+      Fr x = fr_load(a, i), y = fr_load(b, i);
+      if (!fr_lt_modulus(x) || !fr_lt_modulus(y)) {
+        atomicOr(flags, 1u);
+        x = fr_zero();
+        y = fr_zero();
+      }
+      x = fr_from_canonical(x);
+      y = fr_from_canonical(y);
+      Fr z;
+      switch (op) {
+        case 0: z = fr_add(x, y); break;
+        case 1: z = fr_sub(x, y); break;
+        case 2: z = fr_mul(x, y); break;
+        default: z = fr_add(fr_mul(x, y), fr_mul(fr_one_minus_f(x), fr_one_minus_f(y))); break;
+      }
+      fr_store(out, i, fr_to_canonical(z));
+    }
+    return;
+  }
+  // batched inversion: Montgomery's trick over kInvBatch consecutive
+  // elements, one Fermat exponentiation per batch; zeros are skipped
+  // (output 0) and reported.
+  const size_t nb = (n + kInvBatch - 1) / kInvBatch;
+  for (size_t bi = tid; bi < nb; bi += stride) {
+    const size_t i0 = bi * kInvBatch;
+    const int cnt = (int)min((size_t)kInvBatch, n - i0);
+    Fr v[kInvBatch], pre[kInvBatch];
+    bool nz[kInvBatch];
+    Fr run = fr_one();  // product of the nonzero entries so far
+    for (int i = 0; i < cnt; ++i) {
+      Fr x = fr_load(a, i0 + i);
+      if (!fr_lt_modulus(x)) {
+        atomicOr(flags, 1u);
+        x = fr_zero();
+      }
+      v[i] = fr_from_canonical(x);
+      nz[i] = !fr_is_zero_lazy(v[i]);
+      if (!nz[i]) atomicOr(flags, 2u);
+      pre[i] = run;
+      if (nz[i]) run = fr_mul(run, v[i]);
+    }
+    Fr inv = fr_inv(run);  // (product of nonzero entries up to the top)^-1
+    for (int i = cnt - 1; i >= 0; --i) {
+      if (nz[i]) {
+        fr_store(out, i0 + i, fr_to_canonical(fr_mul(inv, pre[i])));
+        inv = fr_mul(inv, v[i]);
+      } else {
+        fr_store(out, i0 + i, fr_zero());
+      }
+    }
+  }
+}
+
+int launch_fr_batch(int op, const uint32_t* a, const uint32_t* b, uint32_t* out, size_t n, uint32_t* flags,
+                    void* stream) {
+  size_t work = op == 3 ? (n + kInvBatch - 1) / kInvBatch : n;
+  k_fr_batch<<<grid_for(work, 128), 128, 0, (cudaStream_t)stream>>>(op, a, b, out, n, flags);
+  return post_launch();
+}
+
+// ---------------------------------------------------------------------------
+// integer-pipe microbenchmarks
+
+__global__ void k_mb_madlo(uint32_t iters, uint32_t mul, uint32_t* sink) {
+  uint32_t x[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) x[i] = threadIdx.x + 17u * i;
+  for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+      for (int i = 0; i < 8; ++i) asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(x[i]) : "r"(mul), "r"(it));
+  }
+  uint32_t acc = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) acc ^= x[i];
+  sink[blockIdx.x * blockDim.x + threadIdx.x] = acc;
+}
+
+__global__ void k_mb_madhi(uint32_t iters, uint32_t mul, uint32_t* sink) {
+  uint32_t x[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) x[i] = threadIdx.x + 17u * i;
+  for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+      for (int i = 0; i < 8; ++i) asm volatile("mad.hi.u32 %0, %0, %1, %2;" : "+r"(x[i]) : "r"(mul), "r"(it));
+  }
+  uint32_t acc = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) acc ^= x[i];
+  sink[blockIdx.x * blockDim.x + threadIdx.x] = acc;
+}
+
+__global__ void k_mb_frmul(uint32_t iters, uint32_t* sink) {
+  Fr x = fr_one(), y = fr_r2(), z = fr_one();
+  x.v[0] ^= threadIdx.x;
+  for (uint32_t it = 0; it < iters; ++it) {
+    x = fr_mul(x, y);
+    z = fr_mul(z, x);
+  }
+  uint32_t acc = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) acc ^= x.v[i] ^ z.v[i];
+  sink[blockIdx.x * blockDim.x + threadIdx.x] = acc;
+}
+
+int run_microbench(int kind, uint32_t blocks, uint32_t threads, uint32_t iters, void* stream, double* ms,
+                   double* ops) {
+  cudaStream_t st = (cudaStream_t)stream;
+  uint32_t* sink = nullptr;
+  cudaError_t e = cudaMalloc(&sink, (size_t)blocks * threads * 4);
+  if (e) return (int)e;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  auto launch = [&]() {
+    if (kind == 0) k_mb_madlo<<<blocks, threads, 0, st>>>(iters, 0x9e3779b9u, sink);
+    else if (kind == 1) k_mb_madhi<<<blocks, threads, 0, st>>>(iters, 0x9e3779b9u, sink);
+    else k_mb_frmul<<<blocks, threads, 0, st>>>(iters, sink);
+    launches_add(1);
+  };
+  launch();  // warm-up
+  cudaEventRecord(a, st);
+  launch();
+  cudaEventRecord(b, st);
+  e = cudaEventSynchronize(b);
+  float t = 0;
+  cudaEventElapsedTime(&t, a, b);
+  *ms = t;
+  double per = kind == 2 ? 2.0 : 64.0;
+  *ops = (double)blocks * threads * iters * per;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(sink);
+  if (!e) e = cudaGetLastError();
+  return (int)e;
+}
+
+}  // namespace sisu

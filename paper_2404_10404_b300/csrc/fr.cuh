@@ -1,0 +1,327 @@
+// Field core: the BN254 scalar field F_r (the paper's choice of BN254,
+// Sec. 4.1), for the sm_103a integer pipes.
+//
+// Representation: 8 x 32-bit little-endian limbs in Montgomery form,
+// x_mont = x * 2^256 mod r.  Values are kept *lazily reduced* in [0, 2r):
+// r < 2^254, so 4r < 2^256 and the CIOS product of two values below 2r is
+// again below 2r without a final subtraction.  Additions and subtractions
+// reduce once against 2r.  Canonical form ([0, r), not Montgomery) is used
+// only at the boundary: inputs, proof bytes, transcript hashing.
+//
+// Multiplication is coarsely integrated operand scanning (CIOS, Koc, Acar
+// and Kaliski 1996) written as PTX carry chains.  Every carry chain, with
+// the instruction that consumes its final carry, sits inside one asm block:
+// the carry flag is not preserved between separate asm statements.
+#pragma once
+#include <cstdint>
+
+namespace sisu {
+
+struct Fr {
+  uint32_t v[8];
+};
+
+#ifdef __CUDACC__
+
+#define SISU_FR_CONST(name, a0, a1, a2, a3, a4, a5, a6, a7) \
+  __device__ __forceinline__ Fr name() {                     \
+    Fr o;                                                    \
+    o.v[0] = a0; o.v[1] = a1; o.v[2] = a2; o.v[3] = a3;      \
+    o.v[4] = a4; o.v[5] = a5; o.v[6] = a6; o.v[7] = a7;      \
+    return o;                                                \
+  }
+
+SISU_FR_CONST(fr_zero, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u)
+// Montgomery form of 1: 2^256 mod r
+SISU_FR_CONST(fr_one, 0x4ffffffbu, 0xac96341cu, 0x9f60cd29u, 0x36fc7695u, 0x7879462eu, 0x666ea36fu,
+              0x9a07df2fu, 0x0e0a77c1u)
+// 2^512 mod r: one product with it maps canonical -> Montgomery
+SISU_FR_CONST(fr_r2, 0xae216da7u, 0x1bb8e645u, 0xe35c59e3u, 0x53fe3ab1u, 0x53bb8085u, 0x8c49833du,
+              0x7f4e44a5u, 0x0216d0b1u)
+// the integer 1 (a product with it maps Montgomery -> canonical)
+SISU_FR_CONST(fr_int_one, 1u, 0u, 0u, 0u, 0u, 0u, 0u, 0u)
+SISU_FR_CONST(fr_modulus, 0xf0000001u, 0x43e1f593u, 0x79b97091u, 0x2833e848u, 0x8181585du, 0xb85045b6u,
+              0xe131a029u, 0x30644e72u)
+
+// ---------------------------------------------------------------------------
+// loads and stores of one 32-byte element (two 128-bit accesses)
+
+__device__ __forceinline__ Fr fr_load(const uint32_t* __restrict__ base, size_t idx) {
+  const uint4* p = reinterpret_cast<const uint4*>(base + 8 * idx);
+  uint4 a = p[0], b = p[1];
+  Fr x;
+  x.v[0] = a.x; x.v[1] = a.y; x.v[2] = a.z; x.v[3] = a.w;
+  x.v[4] = b.x; x.v[5] = b.y; x.v[6] = b.z; x.v[7] = b.w;
+  return x;
+}
+
+// through L2 only: for data that other blocks of the same grid wrote
+__device__ __forceinline__ Fr fr_load_cg(const uint32_t* base, size_t idx) {
+  const uint4* p = reinterpret_cast<const uint4*>(base + 8 * idx);
+  uint4 a = __ldcg(p), b = __ldcg(p + 1);
+  Fr x;
+  x.v[0] = a.x; x.v[1] = a.y; x.v[2] = a.z; x.v[3] = a.w;
+  x.v[4] = b.x; x.v[5] = b.y; x.v[6] = b.z; x.v[7] = b.w;
+  return x;
+}
+
+__device__ __forceinline__ void fr_store(uint32_t* __restrict__ base, size_t idx, const Fr& x) {
+  uint4* p = reinterpret_cast<uint4*>(base + 8 * idx);
+  p[0] = make_uint4(x.v[0], x.v[1], x.v[2], x.v[3]);
+  p[1] = make_uint4(x.v[4], x.v[5], x.v[6], x.v[7]);
+}
+
+__device__ __forceinline__ void fr_store_cg(uint32_t* base, size_t idx, const Fr& x) {
+  uint4* p = reinterpret_cast<uint4*>(base + 8 * idx);
+  __stcg(p, make_uint4(x.v[0], x.v[1], x.v[2], x.v[3]));
+  __stcg(p + 1, make_uint4(x.v[4], x.v[5], x.v[6], x.v[7]));
+}
+
+// ---------------------------------------------------------------------------
+// addition and subtraction, inputs and outputs in [0, 2r)
+
+__device__ __forceinline__ Fr fr_add(const Fr& a, const Fr& b) {
+  Fr s = a, d;
+  uint32_t keep;  // all ones when s < 2r
+  asm("{\n\t"
+      ".reg .u32 z;\n\t"
+      "mov.u32 z, 0;\n\t"
+      "add.cc.u32  %0, %0, %17;\n\t"
+      "addc.cc.u32 %1, %1, %18;\n\t"
+      "addc.cc.u32 %2, %2, %19;\n\t"
+      "addc.cc.u32 %3, %3, %20;\n\t"
+      "addc.cc.u32 %4, %4, %21;\n\t"
+      "addc.cc.u32 %5, %5, %22;\n\t"
+      "addc.cc.u32 %6, %6, %23;\n\t"
+      "addc.u32    %7, %7, %24;\n\t"
+      "sub.cc.u32  %8,  %0, 0xe0000002;\n\t"
+      "subc.cc.u32 %9,  %1, 0x87c3eb27;\n\t"
+      "subc.cc.u32 %10, %2, 0xf372e122;\n\t"
+      "subc.cc.u32 %11, %3, 0x5067d090;\n\t"
+      "subc.cc.u32 %12, %4, 0x0302b0ba;\n\t"
+      "subc.cc.u32 %13, %5, 0x70a08b6d;\n\t"
+      "subc.cc.u32 %14, %6, 0xc2634053;\n\t"
+      "subc.cc.u32 %15, %7, 0x60c89ce5;\n\t"
+      "subc.u32    %16, z, z;\n\t"
+      "}"
+      : "+r"(s.v[0]), "+r"(s.v[1]), "+r"(s.v[2]), "+r"(s.v[3]), "+r"(s.v[4]), "+r"(s.v[5]),
+        "+r"(s.v[6]), "+r"(s.v[7]), "=r"(d.v[0]), "=r"(d.v[1]), "=r"(d.v[2]), "=r"(d.v[3]),
+        "=r"(d.v[4]), "=r"(d.v[5]), "=r"(d.v[6]), "=r"(d.v[7]), "=r"(keep)
+      : "r"(b.v[0]), "r"(b.v[1]), "r"(b.v[2]), "r"(b.v[3]), "r"(b.v[4]), "r"(b.v[5]), "r"(b.v[6]),
+        "r"(b.v[7]));
+  Fr r;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) r.v[i] = (s.v[i] & keep) | (d.v[i] & ~keep);
+  return r;
+}
+
+__device__ __forceinline__ Fr fr_sub(const Fr& a, const Fr& b) {
+  Fr d = a;
+  asm("{\n\t"
+      ".reg .u32 z, m, t0, t1, t2, t3, t4, t5, t6, t7;\n\t"
+      "mov.u32 z, 0;\n\t"
+      "sub.cc.u32  %0, %0, %8;\n\t"
+      "subc.cc.u32 %1, %1, %9;\n\t"
+      "subc.cc.u32 %2, %2, %10;\n\t"
+      "subc.cc.u32 %3, %3, %11;\n\t"
+      "subc.cc.u32 %4, %4, %12;\n\t"
+      "subc.cc.u32 %5, %5, %13;\n\t"
+      "subc.cc.u32 %6, %6, %14;\n\t"
+      "subc.cc.u32 %7, %7, %15;\n\t"
+      "subc.u32    m, z, z;\n\t"
+      "and.b32 t0, m, 0xe0000002;\n\t"
+      "and.b32 t1, m, 0x87c3eb27;\n\t"
+      "and.b32 t2, m, 0xf372e122;\n\t"
+      "and.b32 t3, m, 0x5067d090;\n\t"
+      "and.b32 t4, m, 0x0302b0ba;\n\t"
+      "and.b32 t5, m, 0x70a08b6d;\n\t"
+      "and.b32 t6, m, 0xc2634053;\n\t"
+      "and.b32 t7, m, 0x60c89ce5;\n\t"
+      "add.cc.u32  %0, %0, t0;\n\t"
+      "addc.cc.u32 %1, %1, t1;\n\t"
+      "addc.cc.u32 %2, %2, t2;\n\t"
+      "addc.cc.u32 %3, %3, t3;\n\t"
+      "addc.cc.u32 %4, %4, t4;\n\t"
+      "addc.cc.u32 %5, %5, t5;\n\t"
+      "addc.cc.u32 %6, %6, t6;\n\t"
+      "addc.u32    %7, %7, t7;\n\t"
+      "}"
+      : "+r"(d.v[0]), "+r"(d.v[1]), "+r"(d.v[2]), "+r"(d.v[3]), "+r"(d.v[4]), "+r"(d.v[5]),
+        "+r"(d.v[6]), "+r"(d.v[7])
+      : "r"(b.v[0]), "r"(b.v[1]), "r"(b.v[2]), "r"(b.v[3]), "r"(b.v[4]), "r"(b.v[5]), "r"(b.v[6]),
+        "r"(b.v[7]));
+  return d;
+}
+
+__device__ __forceinline__ Fr fr_dbl(const Fr& a) { return fr_add(a, a); }
+
+// ---------------------------------------------------------------------------
+// Montgomery product a * b * 2^-256 mod r, inputs and output in [0, 2r).
+//
+// One CIOS step for limb bi of b: t += a * bi (9 words), m = t0 * (-r^-1),
+// t += m * r, t >>= 32.  With a < 2r and t < 3r at the start of a step the
+// running value stays below 3r (1 + 2^32) < 2^288, so nine words never
+// overflow and no tenth word is needed (this uses r < 2^254).
+
+#define SISU_CIOS_STEP(BI)                                                                   \
+  t8 = 0;                                                                                    \
+  asm("{\n\t"                                                                                \
+      ".reg .u32 m;\n\t"                                                                     \
+      "mad.lo.cc.u32  %0, %9,  %17, %0;\n\t"                                                 \
+      "madc.lo.cc.u32 %1, %10, %17, %1;\n\t"                                                 \
+      "madc.lo.cc.u32 %2, %11, %17, %2;\n\t"                                                 \
+      "madc.lo.cc.u32 %3, %12, %17, %3;\n\t"                                                 \
+      "madc.lo.cc.u32 %4, %13, %17, %4;\n\t"                                                 \
+      "madc.lo.cc.u32 %5, %14, %17, %5;\n\t"                                                 \
+      "madc.lo.cc.u32 %6, %15, %17, %6;\n\t"                                                 \
+      "madc.lo.cc.u32 %7, %16, %17, %7;\n\t"                                                 \
+      "addc.u32       %8, %8, 0;\n\t"                                                        \
+      "mad.hi.cc.u32  %1, %9,  %17, %1;\n\t"                                                 \
+      "madc.hi.cc.u32 %2, %10, %17, %2;\n\t"                                                 \
+      "madc.hi.cc.u32 %3, %11, %17, %3;\n\t"                                                 \
+      "madc.hi.cc.u32 %4, %12, %17, %4;\n\t"                                                 \
+      "madc.hi.cc.u32 %5, %13, %17, %5;\n\t"                                                 \
+      "madc.hi.cc.u32 %6, %14, %17, %6;\n\t"                                                 \
+      "madc.hi.cc.u32 %7, %15, %17, %7;\n\t"                                                 \
+      "madc.hi.u32    %8, %16, %17, %8;\n\t"                                                 \
+      "mul.lo.u32 m, %0, 0xefffffff;\n\t"                                                    \
+      "mad.lo.cc.u32  %0, m, 0xf0000001, %0;\n\t"                                            \
+      "madc.lo.cc.u32 %1, m, 0x43e1f593, %1;\n\t"                                            \
+      "madc.lo.cc.u32 %2, m, 0x79b97091, %2;\n\t"                                            \
+      "madc.lo.cc.u32 %3, m, 0x2833e848, %3;\n\t"                                            \
+      "madc.lo.cc.u32 %4, m, 0x8181585d, %4;\n\t"                                            \
+      "madc.lo.cc.u32 %5, m, 0xb85045b6, %5;\n\t"                                            \
+      "madc.lo.cc.u32 %6, m, 0xe131a029, %6;\n\t"                                            \
+      "madc.lo.cc.u32 %7, m, 0x30644e72, %7;\n\t"                                            \
+      "addc.u32       %8, %8, 0;\n\t"                                                        \
+      "mad.hi.cc.u32  %1, m, 0xf0000001, %1;\n\t"                                            \
+      "madc.hi.cc.u32 %2, m, 0x43e1f593, %2;\n\t"                                            \
+      "madc.hi.cc.u32 %3, m, 0x79b97091, %3;\n\t"                                            \
+      "madc.hi.cc.u32 %4, m, 0x2833e848, %4;\n\t"                                            \
+      "madc.hi.cc.u32 %5, m, 0x8181585d, %5;\n\t"                                            \
+      "madc.hi.cc.u32 %6, m, 0xb85045b6, %6;\n\t"                                            \
+      "madc.hi.cc.u32 %7, m, 0xe131a029, %7;\n\t"                                            \
+      "madc.hi.u32    %8, m, 0x30644e72, %8;\n\t"                                            \
+      "}"                                                                                    \
+      : "+r"(t0), "+r"(t1), "+r"(t2), "+r"(t3), "+r"(t4), "+r"(t5), "+r"(t6), "+r"(t7),      \
+        "+r"(t8)                                                                             \
+      : "r"(a.v[0]), "r"(a.v[1]), "r"(a.v[2]), "r"(a.v[3]), "r"(a.v[4]), "r"(a.v[5]),        \
+        "r"(a.v[6]), "r"(a.v[7]), "r"(BI));                                                  \
+  t0 = t1; t1 = t2; t2 = t3; t3 = t4; t4 = t5; t5 = t6; t6 = t7; t7 = t8;
+
+__device__ __forceinline__ Fr fr_mul(const Fr& a, const Fr& b) {
+  uint32_t t0 = 0, t1 = 0, t2 = 0, t3 = 0, t4 = 0, t5 = 0, t6 = 0, t7 = 0, t8;
+  SISU_CIOS_STEP(b.v[0])
+  SISU_CIOS_STEP(b.v[1])
+  SISU_CIOS_STEP(b.v[2])
+  SISU_CIOS_STEP(b.v[3])
+  SISU_CIOS_STEP(b.v[4])
+  SISU_CIOS_STEP(b.v[5])
+  SISU_CIOS_STEP(b.v[6])
+  SISU_CIOS_STEP(b.v[7])
+  Fr r;
+  r.v[0] = t0; r.v[1] = t1; r.v[2] = t2; r.v[3] = t3;
+  r.v[4] = t4; r.v[5] = t5; r.v[6] = t6; r.v[7] = t7;
+  return r;
+}
+
+__device__ __forceinline__ Fr fr_sqr(const Fr& a) { return fr_mul(a, a); }
+
+// ---------------------------------------------------------------------------
+// comparisons and conversions
+
+// x < r for an integer given as 8 limbs
+__device__ __forceinline__ bool fr_lt_modulus(const Fr& x) {
+  uint32_t borrow;
+  asm("{\n\t"
+      ".reg .u32 z, t;\n\t"
+      "mov.u32 z, 0;\n\t"
+      "sub.cc.u32  t, %1, 0xf0000001;\n\t"
+      "subc.cc.u32 t, %2, 0x43e1f593;\n\t"
+      "subc.cc.u32 t, %3, 0x79b97091;\n\t"
+      "subc.cc.u32 t, %4, 0x2833e848;\n\t"
+      "subc.cc.u32 t, %5, 0x8181585d;\n\t"
+      "subc.cc.u32 t, %6, 0xb85045b6;\n\t"
+      "subc.cc.u32 t, %7, 0xe131a029;\n\t"
+      "subc.cc.u32 t, %8, 0x30644e72;\n\t"
+      "subc.u32    %0, z, z;\n\t"
+      "}"
+      : "=r"(borrow)
+      : "r"(x.v[0]), "r"(x.v[1]), "r"(x.v[2]), "r"(x.v[3]), "r"(x.v[4]), "r"(x.v[5]), "r"(x.v[6]),
+        "r"(x.v[7]));
+  return borrow != 0;
+}
+
+// x - r when x >= r (x < 2r), else x
+__device__ __forceinline__ Fr fr_reduce_once(const Fr& x) {
+  Fr d = x;
+  uint32_t keep;
+  asm("{\n\t"
+      ".reg .u32 z;\n\t"
+      "mov.u32 z, 0;\n\t"
+      "sub.cc.u32  %0, %0, 0xf0000001;\n\t"
+      "subc.cc.u32 %1, %1, 0x43e1f593;\n\t"
+      "subc.cc.u32 %2, %2, 0x79b97091;\n\t"
+      "subc.cc.u32 %3, %3, 0x2833e848;\n\t"
+      "subc.cc.u32 %4, %4, 0x8181585d;\n\t"
+      "subc.cc.u32 %5, %5, 0xb85045b6;\n\t"
+      "subc.cc.u32 %6, %6, 0xe131a029;\n\t"
+      "subc.cc.u32 %7, %7, 0x30644e72;\n\t"
+      "subc.u32    %8, z, z;\n\t"
+      "}"
+      : "+r"(d.v[0]), "+r"(d.v[1]), "+r"(d.v[2]), "+r"(d.v[3]), "+r"(d.v[4]), "+r"(d.v[5]),
+        "+r"(d.v[6]), "+r"(d.v[7]), "=r"(keep));
+  Fr r;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) r.v[i] = (x.v[i] & keep) | (d.v[i] & ~keep);
+  return r;
+}
+
+// Montgomery (lazy) -> canonical integer in [0, r)
+__device__ __forceinline__ Fr fr_to_canonical(const Fr& a) {
+  return fr_reduce_once(fr_mul(a, fr_int_one()));
+}
+
+// canonical integer (< r) -> Montgomery
+__device__ __forceinline__ Fr fr_from_canonical(const Fr& a) { return fr_mul(a, fr_r2()); }
+
+__device__ __forceinline__ bool fr_is_zero_lazy(const Fr& a) {
+  // a in [0, 2r) represents 0 exactly when a == 0 or a == r
+  Fr c = fr_reduce_once(a);
+  uint32_t acc = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) acc |= c.v[i];
+  return acc == 0;
+}
+
+// a^e for a 256-bit exponent given as canonical limbs (square and multiply)
+__device__ __forceinline__ Fr fr_pow(const Fr& a, const Fr& e) {
+  Fr acc = fr_one();
+  for (int i = 255; i >= 0; --i) {
+    acc = fr_sqr(acc);
+    if ((e.v[i >> 5] >> (i & 31)) & 1u) acc = fr_mul(acc, a);
+  }
+  return acc;
+}
+
+// Fermat inverse a^(r-2) (0 maps to 0)
+__device__ __forceinline__ Fr fr_inv(const Fr& a) {
+  Fr e = fr_modulus();
+  e.v[0] -= 2u;  // r - 2 (no borrow: low limb of r is 0xf0000001)
+  return fr_pow(a, e);
+}
+
+// warp-wide sum (result valid in lane 0)
+__device__ __forceinline__ Fr fr_warp_sum(Fr x) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    Fr y;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) y.v[i] = __shfl_down_sync(0xffffffffu, x.v[i], off);
+    x = fr_add(x, y);
+  }
+  return x;
+}
+
+#endif  // __CUDACC__
+}  // namespace sisu

@@ -1,0 +1,118 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "fr.cuh"
+
+#ifndef __CUDACC__
+// CUDA's vector types, for translation units built by the host compiler
+struct uint2 {
+  uint32_t x, y;
+};
+struct uint4 {
+  uint32_t x, y, z, w;
+};
+#endif
+
+namespace sisu {
+
+constexpr uint32_t kMaxLog = 32;         // bound on c and s_i (sizes <= 2^24 in practice)
+constexpr uint32_t kMaxDomain = 256;     // transcript domain bytes
+constexpr uint32_t kMaxPartials = 8192;  // blocks whose partial sums one round reduces
+
+// Device-resident prover state: the transcript and every challenge, so that
+// no host round trip is needed inside a proof.  Challenges are stored in
+// Montgomery form.
+struct DevState {
+  uint32_t st[8];       // transcript state, 32 bytes as big-endian words
+  uint32_t dig_in[8];   // statement digest of the inputs
+  uint32_t dig_out[8];  // statement digest of the outputs
+  uint32_t counter;     // last-block-done counter of the running round
+  uint32_t error;       // nonzero: a device-side check failed
+  uint32_t pad[6];
+  Fr zb[kMaxLog], zg[kMaxLog];             // initial claim point (copy bits, gate bits)
+  Fr rb[kMaxLog], rx[kMaxLog], ry[kMaxLog];  // challenges of the running layer
+  Fr alpha, beta, vx, vy;
+};
+
+struct InitParams {
+  uint8_t domain[kMaxDomain];
+  uint32_t dlen;
+  uint32_t d, c;
+  uint32_t s[65];
+  uint32_t wiring[8];  // statement digest of the wiring (big-endian words)
+};
+
+// Per-layer device views of the circuit.
+struct DevLayer {
+  const uint2* gate_io;  // per padded gate: {in1 | type << 30, in2}; type 2 = absent
+  const uint4* sgate;    // present gates, mul first then add, each sorted by in1: {in1, in2, g, 0}
+  const uint32_t* off1;  // CSR over layer i+1 positions x: sgate positions with in1 == x
+  const uint32_t* pos1;
+  const uint32_t* off2;  // same for in2
+  const uint32_t* pos2;
+  uint32_t nmul, ntot;   // number of mul gates, of present gates
+};
+
+// Host copy of the padded circuit (the verifier and the digests use it).
+struct HostCircuit {
+  uint32_t d = 0, c = 0, C = 0, Creal = 0;
+  std::vector<uint32_t> s, W, wreal;
+  std::vector<std::vector<uint8_t>> type;
+  std::vector<std::vector<uint32_t>> in1, in2;
+  uint32_t wiring_digest[8];
+  size_t proof_len() const;
+};
+
+// ---------------------------------------------------------------------------
+// kernel launch wrappers (kernels.cu); all return cudaError_t as int
+
+uint64_t launches_add(uint64_t n);
+
+int launch_inputs_to_mont(const uint32_t* in, uint32_t* V, uint32_t c, uint32_t s, uint32_t Creal,
+                          uint32_t wreal, uint32_t* err, void* stream);
+int launch_eval_layer(const uint32_t* Vn, uint32_t* V, const uint2* gate_io, uint32_t c, uint32_t s,
+                      uint32_t sn, void* stream);
+int launch_layer_to_canonical(const uint32_t* V, uint32_t* out, uint32_t c, uint32_t s, uint32_t Creal,
+                              uint32_t wreal, void* stream);
+// Merkle statement digest of a Montgomery table (elements converted to
+// canonical bytes on the fly) or of raw device bytes; writes 8 words.
+int launch_digest_table(const uint32_t* tab, size_t nelem, uint32_t* scratch, uint32_t* out_words,
+                        void* stream);
+int launch_digest_bytes(const uint8_t* data, size_t len, uint32_t* scratch, uint32_t* out_words,
+                        void* stream);
+size_t digest_scratch_words(size_t len_bytes);
+
+int launch_transcript_init(const InitParams& p, DevState* S, void* stream);
+int launch_layer_init(DevState* S, uint32_t layer, uint32_t c, uint32_t s_i, const DevLayer& L,
+                      uint32_t* E, uint32_t* omega_s, void* stream);
+int launch_copy_round(const uint32_t* T, uint32_t sn, uint32_t h, const uint32_t* E, const uint32_t* omega_s,
+                      const DevLayer& L, uint32_t* partials, DevState* S, uint8_t* proof, size_t off,
+                      uint32_t k, void* stream);
+int launch_copy_fold(const uint32_t* src, uint32_t* dst, uint32_t sn, uint32_t h, uint32_t* E,
+                     DevState* S, uint32_t k, void* stream);
+int launch_xinit(const uint32_t* Arow, const uint32_t* E, const uint32_t* omega_s, const DevLayer& L,
+                 uint32_t Wn, uint32_t* At, uint32_t* H1, uint32_t* H2, uint32_t* Ay, void* stream);
+int launch_gate_round(uint32_t* A, uint32_t* B1, uint32_t* B2, uint32_t m, int phase, uint32_t k,
+                      uint32_t* partials, DevState* S, uint8_t* proof, size_t off, void* stream);
+int launch_eq_rx(DevState* S, uint32_t s, uint32_t W, uint32_t* Q, const uint32_t* At, void* stream);
+int launch_yinit(const uint32_t* E, const uint32_t* omega_s, const uint32_t* Q, const DevLayer& L,
+                 uint32_t Wn, uint32_t* K1, uint32_t* K2, DevState* S, void* stream);
+int launch_layer_end(DevState* S, const uint32_t* Ay, uint32_t s, uint8_t* proof, size_t off, int last,
+                     void* stream);
+
+int launch_fr_batch(int op, const uint32_t* a, const uint32_t* b, uint32_t* out, size_t n,
+                    uint32_t* flags, void* stream);
+int run_microbench(int kind, uint32_t blocks, uint32_t threads, uint32_t iters, void* stream, double* ms,
+                   double* ops);
+
+// host verifier (verify.cpp)
+int host_verify(const HostCircuit& hc, const uint8_t* inputs, const uint8_t* outputs, const uint8_t* proof,
+                size_t proof_len, const uint8_t* domain, size_t dlen);
+// host Merkle statement digest of bytes (big-endian words out)
+void host_statement_digest(const uint8_t* data, size_t len, uint32_t out[8]);
+
+}  // namespace sisu

@@ -1,0 +1,473 @@
+// Prover kernels: the device transcript, layer initialisation, the copy
+// phase and Libra's two phases of the GKR layer sumcheck.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "internal.h"
+#include "launch.cuh"
+#include "sha256.cuh"
+
+namespace sisu {
+
+// ---------------------------------------------------------------------------
+// small device helpers
+
+__device__ __forceinline__ Fr fr_one_minus(const Fr& z) { return fr_sub(fr_one(), z); }
+
+// eq(r_1..r_s, v) = prod_k (bit_k(v) ? r_k : 1 - r_k), bit 1 = most significant
+__device__ __forceinline__ Fr eq_index(const Fr* r, uint32_t s, uint32_t v) {
+  Fr acc = fr_one();
+  for (uint32_t k = 0; k < s; ++k) {
+    uint32_t bit = (v >> (s - 1 - k)) & 1u;
+    acc = fr_mul(acc, bit ? r[k] : fr_one_minus(r[k]));
+  }
+  return acc;
+}
+
+// x + r (y - x): the multilinear line through two table entries
+__device__ __forceinline__ Fr fold2(const Fr& x, const Fr& y, const Fr& r) {
+  return fr_add(x, fr_mul(r, fr_sub(y, x)));
+}
+
+__device__ __forceinline__ void store_words(uint8_t* base, size_t off, const Fr& canon) {
+  uint32_t* p = reinterpret_cast<uint32_t*>(base + off);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) p[i] = canon.v[i];
+}
+
+// ---------------------------------------------------------------------------
+// Fiat-Shamir transcript (single thread)
+//   absorb:    st = SHA256(st || tag || canonical LE elements)
+//   challenge: h = SHA256(st || 'C' || u32le ctr), x = LE(h) mod 2^254,
+//              accepted (st = h) when x < r.
+
+__device__ void tr_absorb(DevState* S, uint8_t tag, const Fr* canon, int n) {
+  Sha256Stream h;
+  h.begin();
+  h.digest_words(S->st);
+  h.byte(tag);
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < 8; ++k) h.u32le(canon[i].v[k]);
+  uint32_t out[8];
+  h.end(out);
+  for (int i = 0; i < 8; ++i) S->st[i] = out[i];
+}
+
+__device__ Fr tr_challenge(DevState* S) {
+  for (uint32_t ctr = 0; ctr < 4096u; ++ctr) {  // each try fails with probability < 1/4
+    Sha256Stream h;
+    h.begin();
+    h.digest_words(S->st);
+    h.byte('C');
+    h.u32le(ctr);
+    uint32_t o[8];
+    h.end(o);
+    Fr x;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x.v[k] = bswap32(o[k]);
+    x.v[7] &= 0x3fffffffu;
+    if (fr_lt_modulus(x)) {
+      for (int i = 0; i < 8; ++i) S->st[i] = o[i];
+      return fr_from_canonical(x);
+    }
+  }
+  S->error |= 2u;
+  return fr_zero();
+}
+
+// The last block of a round: canonical evaluations into the proof, absorb,
+// squeeze the round's challenge.
+__device__ void round_finalize(DevState* S, const Fr* vals, int n, uint8_t* proof, size_t off, Fr* rslot) {
+  Fr canon[4];
+  for (int i = 0; i < n; ++i) {
+    canon[i] = fr_to_canonical(vals[i]);
+    store_words(proof, off + 32 * (size_t)i, canon[i]);
+  }
+  tr_absorb(S, 'R', canon, n);
+  *rslot = tr_challenge(S);
+}
+
+// Block-wide sum of NV field elements per thread; result in thread 0.
+template <int BD, int NV>
+__device__ __forceinline__ void block_sum(Fr (&v)[NV]) {
+  __shared__ Fr red[NV][BD / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int t = 0; t < NV; ++t) v[t] = fr_warp_sum(v[t]);
+  if (BD > 32) {
+    if (lane == 0)
+#pragma unroll
+      for (int t = 0; t < NV; ++t) red[t][warp] = v[t];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+      for (int t = 0; t < NV; ++t) {
+        Fr x = lane < BD / 32 ? red[t][lane] : fr_zero();
+        v[t] = fr_warp_sum(x);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Writes this block's partial sums; returns true in the last block to
+// finish, which then holds the grid-wide sums in thread 0's v.
+template <int BD, int NV>
+__device__ __forceinline__ bool grid_sum_last_block(Fr (&v)[NV], uint32_t* partials, DevState* S) {
+  __shared__ bool is_last;
+  const uint32_t nblk = gridDim.x * gridDim.y;
+  const uint32_t bid = blockIdx.y * gridDim.x + blockIdx.x;
+  block_sum<BD, NV>(v);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int t = 0; t < NV; ++t) fr_store_cg(partials, (size_t)bid * NV + t, v[t]);
+    __threadfence();
+    uint32_t prev = atomicAdd(&S->counter, 1u);
+    is_last = (prev == nblk - 1);
+  }
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+#pragma unroll
+  for (int t = 0; t < NV; ++t) v[t] = fr_zero();
+  for (uint32_t p = threadIdx.x; p < nblk; p += BD)
+#pragma unroll
+    for (int t = 0; t < NV; ++t) v[t] = fr_add(v[t], fr_load_cg(partials, (size_t)p * NV + t));
+  block_sum<BD, NV>(v);
+  if (threadIdx.x == 0) S->counter = 0;
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// transcript initialisation and the initial claim point z = (z_b, z_g)
+//   st = SHA256(domain || 0x00 || u32le d || u32le c || u32le s_0..s_d ||
+//               Dig(wiring) || Dig(inputs) || Dig(outputs))
+
+__global__ void k_transcript_init(InitParams p, DevState* S) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  Sha256Stream h;
+  h.begin();
+  h.bytes(p.domain, p.dlen);
+  h.byte(0);
+  h.u32le(p.d);
+  h.u32le(p.c);
+  for (uint32_t i = 0; i <= p.d; ++i) h.u32le(p.s[i]);
+  h.digest_words(p.wiring);
+  h.digest_words(S->dig_in);
+  h.digest_words(S->dig_out);
+  uint32_t o[8];
+  h.end(o);
+  for (int i = 0; i < 8; ++i) S->st[i] = o[i];
+  S->counter = 0;
+  S->error = 0;
+  for (uint32_t k = 0; k < p.c; ++k) S->zb[k] = tr_challenge(S);
+  for (uint32_t k = 0; k < p.s[0]; ++k) S->zg[k] = tr_challenge(S);
+}
+
+int launch_transcript_init(const InitParams& p, DevState* S, void* stream) {
+  k_transcript_init<<<1, 32, 0, (cudaStream_t)stream>>>(p, S);
+  return post_launch();
+}
+
+// ---------------------------------------------------------------------------
+// layer initialisation: E = EQ(copy point) over the 2^c copies and the gate
+// weights w(g) over the layer's present gates (in the sorted order):
+//   layer 0:  w(g) = eq(z_g, g)
+//   layer i:  w(g) = alpha eq(r_x, g) + beta eq(r_y, g)   (previous layer's r_x, r_y)
+
+__global__ void k_layer_init(DevState* S, uint32_t layer, uint32_t c, uint32_t si, const uint4* __restrict__ sg,
+                             uint32_t ntot, uint32_t* __restrict__ E, uint32_t* __restrict__ om) {
+  const uint32_t C = 1u << c;
+  const size_t total = (size_t)C + ntot;
+  const Fr* z = layer == 0 ? S->zb : S->rb;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    if (idx < C) {
+      fr_store(E, idx, eq_index(z, c, (uint32_t)idx));
+    } else {
+      uint32_t q = (uint32_t)(idx - C);
+      uint32_t g = sg[q].z;
+      Fr w;
+      if (layer == 0) {
+        w = eq_index(S->zg, si, g);
+      } else {
+        w = fr_add(fr_mul(S->alpha, eq_index(S->rx, si, g)), fr_mul(S->beta, eq_index(S->ry, si, g)));
+      }
+      fr_store(om, q, w);
+    }
+  }
+}
+
+int launch_layer_init(DevState* S, uint32_t layer, uint32_t c, uint32_t s_i, const DevLayer& L, uint32_t* E,
+                      uint32_t* omega_s, void* stream) {
+  size_t n = ((size_t)1 << c) + L.ntot;
+  k_layer_init<<<grid_for(n, 128), 128, 0, (cudaStream_t)stream>>>(S, layer, c, s_i, L.sgate, L.ntot, E, omega_s);
+  return post_launch();
+}
+
+// ---------------------------------------------------------------------------
+// copy-phase round (degree 3 in the bound copy variable):
+//   g(t) = sum_{j < h} E_t(j) sum_g w(g) op_g(T_t(j, in1 g), T_t(j, in2 g)),  t = 0..3
+// with X_t(j) = X(j) + t (X(j + h) - X(j)).  Per pair the gate sum S_j(t)
+// is quadratic in t: S_j(0..2) are summed directly and
+// S_j(3) = S_j(0) - 3 S_j(1) + 3 S_j(2).  A mul gate costs five products
+// (w x_t is affine in t, so w x_2 = 2 w x_1 - w x_0), an add gate two.
+//
+// Grid: blockIdx.x = chunk of the sorted gate list, blockIdx.y strides over
+// pairs; each thread applies E_t(j) to its own partial sums.
+
+template <int BD>
+__global__ void __launch_bounds__(BD) k_copy_round(const uint32_t* __restrict__ T, uint32_t sn, uint32_t h,
+                                                   const uint32_t* __restrict__ E, const uint32_t* __restrict__ om,
+                                                   const uint4* __restrict__ sg, uint32_t nmul, uint32_t ntot,
+                                                   uint32_t G, uint32_t* partials, DevState* S, uint8_t* proof,
+                                                   size_t off, uint32_t k) {
+  const uint32_t g0 = blockIdx.x * G;
+  const uint32_t g1 = min(ntot, g0 + G);
+  Fr acc[4] = {fr_zero(), fr_zero(), fr_zero(), fr_zero()};
+  for (uint32_t j = blockIdx.y; j < h; j += gridDim.y) {
+    const uint32_t* lo = T + (((size_t)j << sn) << 3);
+    const uint32_t* hi = T + (((size_t)(j + h) << sn) << 3);
+    Fr s0 = fr_zero(), s1 = fr_zero(), s2 = fr_zero();
+    for (uint32_t q = g0 + threadIdx.x; q < g1; q += BD) {
+      const uint4 gi = sg[q];
+      const Fr w = fr_load(om, q);
+      const Fr x0 = fr_load(lo, gi.x), x1 = fr_load(hi, gi.x);
+      const Fr y0 = fr_load(lo, gi.y), y1 = fr_load(hi, gi.y);
+      if (q < nmul) {
+        const Fr wx0 = fr_mul(w, x0), wx1 = fr_mul(w, x1);
+        const Fr wx2 = fr_sub(fr_dbl(wx1), wx0);
+        const Fr y2 = fr_sub(fr_dbl(y1), y0);
+        s0 = fr_add(s0, fr_mul(wx0, y0));
+        s1 = fr_add(s1, fr_mul(wx1, y1));
+        s2 = fr_add(s2, fr_mul(wx2, y2));
+      } else {
+        const Fr a0 = fr_mul(w, fr_add(x0, y0)), a1 = fr_mul(w, fr_add(x1, y1));
+        s0 = fr_add(s0, a0);
+        s1 = fr_add(s1, a1);
+        s2 = fr_add(s2, fr_sub(fr_dbl(a1), a0));
+      }
+    }
+    const Fr d21 = fr_sub(s2, s1);
+    const Fr s3 = fr_add(s0, fr_add(d21, fr_dbl(d21)));
+    const Fr e0 = fr_load(E, j), e1 = fr_load(E, j + h);
+    const Fr de = fr_sub(e1, e0);
+    const Fr e2 = fr_add(e1, de), e3 = fr_add(e2, de);
+    acc[0] = fr_add(acc[0], fr_mul(e0, s0));
+    acc[1] = fr_add(acc[1], fr_mul(e1, s1));
+    acc[2] = fr_add(acc[2], fr_mul(e2, s2));
+    acc[3] = fr_add(acc[3], fr_mul(e3, s3));
+  }
+  if (grid_sum_last_block<BD, 4>(acc, partials, S) && threadIdx.x == 0)
+    round_finalize(S, acc, 4, proof, off, &S->rb[k]);
+}
+
+int launch_copy_round(const uint32_t* T, uint32_t sn, uint32_t h, const uint32_t* E, const uint32_t* omega_s,
+                      const DevLayer& L, uint32_t* partials, DevState* S, uint8_t* proof, size_t off, uint32_t k,
+                      void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  const uint32_t ntot = L.ntot;
+  // about eight gates per thread for each pair when one chunk covers the layer
+  int bd = 256;
+  while (bd > 32 && (uint32_t)bd * 8 > ntot) bd >>= 1;
+  const uint32_t target = kSMs * 6;
+  uint32_t chunks = 1, pairblocks;
+  if (h >= target) {
+    pairblocks = target;
+  } else {
+    pairblocks = h;
+    uint32_t want = (target + h - 1) / h;
+    uint32_t maxc = (ntot + bd - 1) / bd;
+    chunks = std::max(1u, std::min(want, maxc));
+  }
+  uint32_t G = (ntot + chunks - 1) / chunks;
+  G = (G + bd - 1) / bd * bd;
+  chunks = (ntot + G - 1) / G;
+  dim3 grid(chunks, pairblocks);
+  switch (bd) {
+    case 256: k_copy_round<256><<<grid, 256, 0, st>>>(T, sn, h, E, omega_s, L.sgate, L.nmul, ntot, G, partials, S, proof, off, k); break;
+    case 128: k_copy_round<128><<<grid, 128, 0, st>>>(T, sn, h, E, omega_s, L.sgate, L.nmul, ntot, G, partials, S, proof, off, k); break;
+    case 64: k_copy_round<64><<<grid, 64, 0, st>>>(T, sn, h, E, omega_s, L.sgate, L.nmul, ntot, G, partials, S, proof, off, k); break;
+    default: k_copy_round<32><<<grid, 32, 0, st>>>(T, sn, h, E, omega_s, L.sgate, L.nmul, ntot, G, partials, S, proof, off, k); break;
+  }
+  return post_launch();
+}
+
+// fold of the copy rows and of E by the round's challenge r = r_b[k]:
+//   dst(j, x) = src(j, x) + r (src(j + h, x) - src(j, x)),  j < h
+// (in place when src == dst: each thread writes only the entry it read)
+__global__ void k_copy_fold(const uint32_t* src, uint32_t* dst, uint32_t sn, uint32_t h, uint32_t* E,
+                            const DevState* S, uint32_t k) {
+  const Fr r = S->rb[k];
+  const size_t nel = (size_t)h << sn;
+  const size_t total = nel + h;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    if (idx < nel) {
+      fr_store(dst, idx, fold2(fr_load(src, idx), fr_load(src, idx + nel), r));
+    } else {
+      size_t j = idx - nel;
+      fr_store(E, j, fold2(fr_load(E, j), fr_load(E, j + h), r));
+    }
+  }
+}
+
+int launch_copy_fold(const uint32_t* src, uint32_t* dst, uint32_t sn, uint32_t h, uint32_t* E, DevState* S,
+                     uint32_t k, void* stream) {
+  size_t n = ((size_t)h << sn) + h;
+  k_copy_fold<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(src, dst, sn, h, E, S, k);
+  return post_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Libra phase 1 (over x) bookkeeping, from the row A = V~(r_b, .) and
+// e = E(r_b):  H1(x) = e sum_{g: in1 g = x} w(g) (mul ? A(in2 g) : 1)
+//              H2(x) = e sum_{g: in1 g = x, add} w(g) A(in2 g)
+// so that sum_y P(r_b, x, y) = A(x) H1(x) + H2(x).
+
+__global__ void k_xinit(const uint32_t* __restrict__ A, const uint32_t* __restrict__ E,
+                        const uint32_t* __restrict__ om, const uint4* __restrict__ sg, uint32_t nmul,
+                        const uint32_t* __restrict__ off1, const uint32_t* __restrict__ pos1, uint32_t Wn,
+                        uint32_t* __restrict__ At, uint32_t* __restrict__ H1, uint32_t* __restrict__ H2,
+                        uint32_t* __restrict__ Ay) {
+  const Fr e = fr_load(E, 0);
+  for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < Wn; x += gridDim.x * blockDim.x) {
+    Fr a1 = fr_zero(), a2 = fr_zero();
+    for (uint32_t p = off1[x], pe = off1[x + 1]; p < pe; ++p) {
+      uint32_t q = pos1[p];
+      uint4 gi = sg[q];
+      Fr w = fr_load(om, q);
+      Fr wa = fr_mul(w, fr_load(A, gi.y));
+      if (q < nmul) {
+        a1 = fr_add(a1, wa);
+      } else {
+        a1 = fr_add(a1, w);
+        a2 = fr_add(a2, wa);
+      }
+    }
+    fr_store(H1, x, fr_mul(e, a1));
+    fr_store(H2, x, fr_mul(e, a2));
+    Fr a = fr_load(A, x);
+    fr_store(At, x, a);
+    fr_store(Ay, x, a);
+  }
+}
+
+int launch_xinit(const uint32_t* Arow, const uint32_t* E, const uint32_t* omega_s, const DevLayer& L, uint32_t Wn,
+                 uint32_t* At, uint32_t* H1, uint32_t* H2, uint32_t* Ay, void* stream) {
+  k_xinit<<<grid_for(Wn, 64), 64, 0, (cudaStream_t)stream>>>(Arow, E, omega_s, L.sgate, L.nmul, L.off1, L.pos1,
+                                                             Wn, At, H1, H2, Ay);
+  return post_launch();
+}
+
+// Libra phase 2 (over y): Q = EQ(r_x); v_x = A(r_x) from the size-2 table.
+__global__ void k_eq_rx(DevState* S, uint32_t s, uint32_t W, uint32_t* __restrict__ Q, const uint32_t* __restrict__ At) {
+  const size_t gid = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  for (size_t x = gid; x < W; x += (size_t)gridDim.x * blockDim.x) fr_store(Q, x, eq_index(S->rx, s, (uint32_t)x));
+  if (gid == 0) S->vx = s == 0 ? fr_load(At, 0) : fold2(fr_load(At, 0), fr_load(At, 1), S->rx[s - 1]);
+}
+
+int launch_eq_rx(DevState* S, uint32_t s, uint32_t W, uint32_t* Q, const uint32_t* At, void* stream) {
+  k_eq_rx<<<grid_for(W, 128), 128, 0, (cudaStream_t)stream>>>(S, s, W, Q, At);
+  return post_launch();
+}
+
+//   K1(y) = e sum_{g: in2 g = y} w(g) Q(in1 g) (mul ? v_x : 1)
+//   K2(y) = e sum_{g: in2 g = y, add} w(g) Q(in1 g) v_x
+// so that sum over boolean x of P(r_b, r_x, y) = A(y) K1(y) + K2(y).
+__global__ void k_yinit(const uint32_t* __restrict__ E, const uint32_t* __restrict__ om, const uint32_t* __restrict__ Q,
+                        const uint4* __restrict__ sg, uint32_t nmul, const uint32_t* __restrict__ off2,
+                        const uint32_t* __restrict__ pos2, uint32_t Wn, uint32_t* __restrict__ K1,
+                        uint32_t* __restrict__ K2, const DevState* S) {
+  const Fr e = fr_load(E, 0);
+  const Fr ev = fr_mul(e, S->vx);
+  for (uint32_t y = blockIdx.x * blockDim.x + threadIdx.x; y < Wn; y += gridDim.x * blockDim.x) {
+    Fr m = fr_zero(), a = fr_zero();
+    for (uint32_t p = off2[y], pe = off2[y + 1]; p < pe; ++p) {
+      uint32_t q = pos2[p];
+      Fr wq = fr_mul(fr_load(om, q), fr_load(Q, sg[q].x));
+      if (q < nmul) m = fr_add(m, wq);
+      else a = fr_add(a, wq);
+    }
+    fr_store(K1, y, fr_add(fr_mul(e, a), fr_mul(ev, m)));
+    fr_store(K2, y, fr_mul(ev, a));
+  }
+}
+
+int launch_yinit(const uint32_t* E, const uint32_t* omega_s, const uint32_t* Q, const DevLayer& L, uint32_t Wn,
+                 uint32_t* K1, uint32_t* K2, DevState* S, void* stream) {
+  k_yinit<<<grid_for(Wn, 64), 64, 0, (cudaStream_t)stream>>>(E, omega_s, Q, L.sgate, L.nmul, L.off2, L.pos2, Wn,
+                                                             K1, K2, S);
+  return post_launch();
+}
+
+// One round of a Libra phase over tables (A, B1, B2) of size m after the
+// fold of the previous round's challenge (when k > 0):
+//   g(t) = sum_{j < m/2} A_t(j) B1_t(j) + B2_t(j),  t = 0, 1, 2.
+template <int BD>
+__global__ void __launch_bounds__(BD) k_gate_round(uint32_t* A, uint32_t* B1, uint32_t* B2, uint32_t m, int phase,
+                                                   uint32_t k, uint32_t* partials, DevState* S, uint8_t* proof,
+                                                   size_t off) {
+  const uint32_t hq = m / 2;
+  Fr* rs = phase == 0 ? S->rx : S->ry;
+  const bool fold = k > 0;
+  Fr r = fr_zero();
+  if (fold) r = rs[k - 1];
+  Fr acc[3] = {fr_zero(), fr_zero(), fr_zero()};
+  for (uint32_t j = blockIdx.x * BD + threadIdx.x; j < hq; j += gridDim.x * BD) {
+    Fr a0, a1, p0, p1, q0, q1;
+    if (fold) {
+      a0 = fold2(fr_load(A, j), fr_load(A, j + m), r);
+      a1 = fold2(fr_load(A, j + hq), fr_load(A, j + hq + m), r);
+      p0 = fold2(fr_load(B1, j), fr_load(B1, j + m), r);
+      p1 = fold2(fr_load(B1, j + hq), fr_load(B1, j + hq + m), r);
+      q0 = fold2(fr_load(B2, j), fr_load(B2, j + m), r);
+      q1 = fold2(fr_load(B2, j + hq), fr_load(B2, j + hq + m), r);
+      fr_store(A, j, a0); fr_store(A, j + hq, a1);
+      fr_store(B1, j, p0); fr_store(B1, j + hq, p1);
+      fr_store(B2, j, q0); fr_store(B2, j + hq, q1);
+    } else {
+      a0 = fr_load(A, j); a1 = fr_load(A, j + hq);
+      p0 = fr_load(B1, j); p1 = fr_load(B1, j + hq);
+      q0 = fr_load(B2, j); q1 = fr_load(B2, j + hq);
+    }
+    const Fr a2 = fr_sub(fr_dbl(a1), a0), p2 = fr_sub(fr_dbl(p1), p0), q2 = fr_sub(fr_dbl(q1), q0);
+    acc[0] = fr_add(acc[0], fr_add(fr_mul(a0, p0), q0));
+    acc[1] = fr_add(acc[1], fr_add(fr_mul(a1, p1), q1));
+    acc[2] = fr_add(acc[2], fr_add(fr_mul(a2, p2), q2));
+  }
+  if (grid_sum_last_block<BD, 3>(acc, partials, S) && threadIdx.x == 0)
+    round_finalize(S, acc, 3, proof, off, &rs[k]);
+}
+
+int launch_gate_round(uint32_t* A, uint32_t* B1, uint32_t* B2, uint32_t m, int phase, uint32_t k, uint32_t* partials,
+                      DevState* S, uint8_t* proof, size_t off, void* stream) {
+  const uint32_t hq = m / 2;
+  unsigned g = grid_for(hq, 128, 8);
+  k_gate_round<128><<<g, 128, 0, (cudaStream_t)stream>>>(A, B1, B2, m, phase, k, partials, S, proof, off);
+  return post_launch();
+}
+
+// end of a layer: v_y, the proof's (v_x, v_y), absorb 'V', next alpha, beta
+__global__ void k_layer_end(DevState* S, const uint32_t* Ay, uint32_t s, uint8_t* proof, size_t off, int last) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  Fr vy = s == 0 ? fr_load(Ay, 0) : fold2(fr_load(Ay, 0), fr_load(Ay, 1), S->ry[s - 1]);
+  S->vy = vy;
+  Fr canon[2] = {fr_to_canonical(S->vx), fr_to_canonical(vy)};
+  store_words(proof, off, canon[0]);
+  store_words(proof, off + 32, canon[1]);
+  tr_absorb(S, 'V', canon, 2);
+  if (!last) {
+    S->alpha = tr_challenge(S);
+    S->beta = tr_challenge(S);
+  }
+}
+
+int launch_layer_end(DevState* S, const uint32_t* Ay, uint32_t s, uint8_t* proof, size_t off, int last,
+                     void* stream) {
+  k_layer_end<<<1, 32, 0, (cudaStream_t)stream>>>(S, Ay, s, proof, off, last);
+  return post_launch();
+}
+
+}  // namespace sisu

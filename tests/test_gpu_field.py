@@ -1,0 +1,87 @@
+"""GPU field core (Sec. 4.1, BN254 scalar field) and device digests, through
+the C ABI, against Python integers and the CPU oracle."""
+import random
+
+import pytest
+
+from gpu_util import bytes_of, from_device, ints_of, to_device
+
+pytestmark = pytest.mark.gpu
+
+P = 0x30644E72E131A029B85045B68181585D2833E84879B9709143E1F593F0000001
+EDGE = [0, 1, 2, 3, P - 1, P - 2, (P - 1) // 2, (P + 1) // 2, 1 << 253, (1 << 254) - P + 7,
+        (1 << 128) - 1, 1 << 64, (1 << 32) - 1, 0xF0000001]
+
+
+@pytest.fixture(scope="module")
+def S():
+    import paper_2404_10404_b300 as S
+    return S
+
+
+def _run(S, op, a, b):
+    n = len(a)
+    da, db, do = to_device(bytes_of(a)), to_device(bytes_of(b)), to_device(bytes(32 * n))
+    S.fr_batch(op, da, db, do, n)
+    return ints_of(from_device(do, 32 * n))
+
+
+@pytest.mark.parametrize("op,fn", [
+    (0, lambda a, b: (a + b) % P), (1, lambda a, b: (a - b) % P), (2, lambda a, b: a * b % P),
+    (4, lambda a, b: (a * b + (1 - a) * (1 - b)) % P)])
+def test_ops_vs_python_ints(S, op, fn):
+    rng = random.Random(op)
+    a = [rng.randrange(P) for _ in range(20000)] + [x for x in EDGE for _ in EDGE]
+    b = [rng.randrange(P) for _ in range(20000)] + [y for _ in EDGE for y in EDGE]
+    assert _run(S, op, a, b) == [fn(x, y) for x, y in zip(a, b)]
+
+
+def test_million_products_vs_oracle(S, oracle):
+    import numpy as np
+    rng = np.random.default_rng(12)
+    n = 1 << 20
+    raw = rng.integers(0, 1 << 63, size=(2, n, 4), dtype=np.uint64)
+    raw[..., 3] &= np.uint64((1 << 61) - 1)  # below 2^253 < r
+    a, b = raw[0].tobytes(), raw[1].tobytes()
+    da, db, do = to_device(a), to_device(b), to_device(bytes(32 * n))
+    S.fr_batch(2, da, db, do, n)
+    got = from_device(do, 32 * n)
+    assert got == oracle.fr_op(2, a, b)
+
+
+def test_batched_inverse(S):
+    rng = random.Random(5)
+    a = [rng.randrange(1, P) for _ in range(1001)] + [1, P - 1, 2]
+    got = _run(S, 3, a, a)
+    assert got == [pow(x, -1, P) for x in a]
+
+
+def test_inverse_of_zero_reported(S):
+    a = [5, 0, 7, 11, 0, 13, 17, 19, 23]
+    da, do = to_device(bytes_of(a)), to_device(bytes(32 * len(a)))
+    with pytest.raises(S.SisuError) as e:
+        S.fr_batch(3, da, da, do, len(a))
+    assert e.value.code == -8
+    got = ints_of(from_device(do, 32 * len(a)))
+    assert got == [pow(x, -1, P) if x else 0 for x in a]
+
+
+def test_non_canonical_rejected(S):
+    for bad in (P, P + 5, (1 << 256) - 1):
+        da, do = to_device(bytes_of([bad, 1])), to_device(bytes(64))
+        with pytest.raises(S.SisuError) as e:
+            S.fr_batch(2, da, da, do, 2)
+        assert e.value.code == -3
+
+
+@pytest.mark.parametrize("n", [0, 1, 31, 1023, 1024, 1025, 4096, 3 * 1024 + 5, 100000])
+def test_device_digest_vs_oracle(S, oracle, n):
+    rng = random.Random(n)
+    data = bytes(rng.getrandbits(8) for _ in range(n))
+    assert S.statement_digest(to_device(data), n) == oracle.statement_digest(data)
+
+
+def test_microbench_runs(S):
+    for kind in (0, 1, 2):
+        ms, ops = S.microbench(kind, 148, 256, 64)
+        assert ms > 0 and ops > 0

@@ -1,0 +1,175 @@
+"""GPU evaluation and proving through the C ABI, byte for byte against the
+CPU oracle (GKR layer sumcheck, Sec. 2.2-2.3; data-parallel copies).
+
+Proofs are deterministic and every element is exact, so parity is byte
+equality of the whole proof.  Small cases call the oracle live; the
+full-size workloads compare with hashes written by
+tests/golden/make_golden.py, which calls only the oracle.
+"""
+import numpy as np
+import pytest
+
+import synth
+from gpu_util import golden, sha, to_device
+
+pytestmark = pytest.mark.gpu
+
+P = synth.FR_MODULUS
+
+
+@pytest.fixture(scope="module")
+def S():
+    import paper_2404_10404_b300 as S
+    return S
+
+
+def _case(S, oracle, circ, domain=None, device_inputs=False):
+    xb = synth.fr_bytes(synth.inputs_for(circ))
+    gc = S.Circuit.from_spec(circ)
+    ev = S.Eval(gc, to_device(xb) if device_inputs else xb)
+    tr = S.Transcript(domain) if domain else None
+    proof = S.prove(gc, ev, tr)
+    want = oracle.prove(circ, xb, domain)
+    assert len(proof) == len(want) == gc.proof_len
+    assert proof == want, _first_diff(proof, want, circ)
+    outs = ev.outputs()
+    assert outs == oracle.outputs(circ, xb)
+    assert S.verify(gc, xb, outs, proof, domain) == 0
+    return gc, ev, xb, proof
+
+
+def _first_diff(a, b, circ):
+    for i, (x, y) in enumerate(zip(a, b)):
+        if x != y:
+            hdr = 8 + 4 * (circ.depth + 3)
+            return f"first differing byte {i} (element {(i - hdr) // 32} after the header)"
+    return "lengths differ"
+
+
+MICRO = [
+    (1, [1, 1], 50), (1, [2, 2], 50), (1, [4, 4, 4], 50), (2, [2, 2, 2], 50), (4, [4, 4, 4], 50),
+    (4, [4, 2, 8], 100), (4, [4, 4, 4], 0), (8, [8, 8], 50), (3, [3, 5, 2], 50), (5, [2, 3, 3], 60),
+    (2, [1, 2, 1], 50), (8, [2, 4, 2, 4], 50), (2, [8, 8], 100), (16, [2, 2], 50), (64, [32, 16, 64], 50),
+]
+
+
+@pytest.mark.parametrize("C,widths,pct", MICRO)
+def test_micro_parity(S, oracle, C, widths, pct):
+    _case(S, oracle, synth.micro(9, C, widths, pct))
+
+
+@pytest.mark.parametrize("C,widths,pct", [
+    (1000, [1000, 1000, 1000], 50),     # padded copies and widths: absent gates, ragged tails
+    (37, [300, 257, 513, 129], 70),
+    (1, [4096, 4096, 4096], 50),        # one copy: the copy phase is empty
+    (4096, [1, 1, 1], 50),              # one gate: x and y phases are empty
+    (2, [2048, 8], 50),                 # fan-in from a narrow layer
+    (256, [16, 2048, 16], 50),
+    (512, [1024] * 4, 100), (512, [1024] * 4, 0),
+])
+def test_shapes_parity(S, oracle, C, widths, pct):
+    _case(S, oracle, synth.micro(11, C, widths, pct))
+
+
+def test_mixing_parity(S, oracle):
+    _case(S, oracle, synth.mixing_circuit(3, 64, 256, 6))
+
+
+def test_in1_equals_in2(S, oracle):
+    circ = synth.micro(21, 16, [64, 64, 64], 50)
+    for i in range(circ.depth):
+        circ.in2[i] = circ.in1[i].copy()
+    _case(S, oracle, circ)
+
+
+def test_domain_and_device_inputs(S, oracle):
+    circ = synth.micro(23, 32, [128, 64, 128], 50)
+    _case(S, oracle, circ, domain=b"custom-domain", device_inputs=True)
+
+
+def test_tiny_parity_and_golden(S, oracle):
+    circ = synth.tiny()
+    gc, ev, xb, proof = _case(S, oracle, circ)
+    g = golden("tiny")
+    if g:
+        assert sha(proof) == g["proof_sha256"]
+
+
+def test_layers_match_oracle(S, oracle):
+    circ = synth.micro(31, 48, [100, 200, 300, 50], 50)
+    xb = synth.fr_bytes(synth.inputs_for(circ))
+    ev = S.Eval(S.Circuit.from_spec(circ), xb)
+    for layer in range(circ.depth + 1):
+        assert ev.layer(layer) == oracle.eval_layer(circ, xb, layer), layer
+
+
+def test_repeat_and_update(S, oracle):
+    """Workspace reuse: several proofs on one handle, then new inputs."""
+    circ = synth.micro(41, 128, [256, 256, 256], 50)
+    x1 = synth.fr_bytes(synth.inputs_for(circ))
+    x2 = synth.fr_bytes(synth.inputs_for(circ, seed=99))
+    gc = S.Circuit.from_spec(circ)
+    ev = S.Eval(gc, x1)
+    p1 = S.prove(gc, ev)
+    assert S.prove(gc, ev) == p1 == S.prove_alloc(gc, ev)
+    ev.update(to_device(x2))
+    assert S.prove(gc, ev) == oracle.prove(circ, x2)
+    ev.update(x1)
+    assert S.prove(gc, ev) == p1
+
+
+def test_errors(S):
+    circ = synth.micro(1, 4, [4, 4])
+    gc = S.Circuit.from_spec(circ)
+    bad = bytearray(synth.fr_bytes(synth.inputs_for(circ)))
+    bad[32:64] = P.to_bytes(32, "little")
+    with pytest.raises(S.SisuError) as e:
+        S.Eval(gc, bytes(bad))
+    assert e.value.code == -3
+    with pytest.raises(S.SisuError) as e:
+        S.Circuit([4, 4], [np.zeros(4, np.uint8)], [np.array([0, 1, 2, 4], np.uint32)],
+                  [np.zeros(4, np.uint32)], 4)
+    assert e.value.code == -2
+    with pytest.raises(S.SisuError) as e:
+        S.Circuit([2, 2], [np.array([0, 5], np.uint8)], [np.zeros(2, np.uint32)], [np.zeros(2, np.uint32)], 4)
+    assert e.value.code == -1
+    with pytest.raises(S.SisuError) as e:
+        S.Circuit([2, 2], [np.zeros(2, np.uint8)], [np.zeros(2, np.uint32)], [np.zeros(2, np.uint32)], 0)
+    assert e.value.code == -1
+    host_only = S.Circuit.from_spec(circ, host_only=True)
+    with pytest.raises(S.SisuError):
+        S.Eval(host_only, synth.fr_bytes(synth.inputs_for(circ)))
+
+
+def test_tampered_gpu_proof_rejected(S):
+    circ = synth.micro(51, 32, [64, 64, 64], 50)
+    xb = synth.fr_bytes(synth.inputs_for(circ))
+    gc = S.Circuit.from_spec(circ)
+    ev = S.Eval(gc, xb)
+    proof = S.prove(gc, ev)
+    outs = ev.outputs()
+    assert S.verify(gc, xb, outs, proof) == 0
+    hdr = 8 + 4 * (circ.depth + 3)
+    for k in range(0, (len(proof) - hdr) // 32, 7):
+        bad = bytearray(proof)
+        bad[hdr + 32 * k + 3] ^= 0x40
+        assert S.verify(gc, xb, outs, bytes(bad)) == -7
+
+
+@pytest.mark.parametrize("name", ["medium", "slot"])
+def test_full_size_golden(S, name):
+    """Full-size workloads, in the launch configuration the benchmark times:
+    proof and outputs equal to the oracle's (stored hashes)."""
+    g = golden(name)
+    if g is None:
+        pytest.skip(f"no oracle record for {name}")
+    circ = {"medium": synth.medium, "slot": synth.slot}[name]()
+    xb = synth.fr_bytes(synth.inputs_for(circ))
+    assert sha(xb) == g["inputs_sha256"]
+    gc = S.Circuit.from_spec(circ)
+    ev = S.Eval(gc, to_device(xb))
+    del xb
+    proof = S.prove(gc, ev)
+    assert len(proof) == g["proof_len"]
+    assert sha(proof) == g["proof_sha256"]
+    assert sha(ev.outputs()) == g["outputs_sha256"]
