@@ -34,8 +34,9 @@
  *     predicates over gates, the output claim from the clear outputs and the
  *     input claims from the clear inputs.
  *   - Transcript: SHA-256 Fiat-Shamir; statement digests are binary Merkle
- *     trees over 1024-byte chunks.  The paper fixes neither; the conventions
- *     below are the project's own (parity unpinned with respect to the paper).
+ *     trees over 1024-byte chunks.  The paper fixes neither: these are the
+ *     project's conventions, pinned by the FIPS 180 vectors and by the
+ *     independent hashlib-based implementation in brute.py.
  */
 #include <stdint.h>
 #include <stdlib.h>
