@@ -49,9 +49,13 @@ def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
-def workload(name: str):
+def workload(name: str, depth: int | None = None):
     import synth
-    return {"tiny": synth.tiny, "medium": synth.medium, "slot": synth.slot}[name]()
+    circ = {"tiny": synth.tiny, "medium": synth.medium, "slot": synth.slot}[name]()
+    if depth:  # the workload's first `depth` layers (for profiler captures)
+        circ = synth.Circuit(circ.widths[:depth + 1], circ.types[:depth], circ.in1[:depth], circ.in2[:depth],
+                             circ.n_copies, name=f"{circ.name}_first{depth}", seed=circ.seed, meta=circ.meta)
+    return circ
 
 
 def describe(circ) -> str:
@@ -192,7 +196,7 @@ def run_ours(args):
         torch.cuda.set_device(0)
     build()
     dev = torch.device("cuda", torch.cuda.current_device())
-    circ = workload(args.workload)
+    circ = workload(args.workload, args.depth)
     gates = gates_of(circ)
     t0 = time.time()
     xb = synth.fr_bytes(synth.inputs_for(circ))
@@ -213,7 +217,7 @@ def run_ours(args):
     gold_path = os.path.join(ROOT, "tests", "golden", "oracle_full_size.json")
     if os.path.exists(gold_path):
         g = json.load(open(gold_path)).get(args.workload)
-        if g:
+        if g and not args.depth:
             parity = hashlib.sha256(proof).hexdigest() == g["proof_sha256"]
     for _ in range(max(0, args.warmup - 1)):
         step(inputs)
@@ -314,6 +318,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["tiny", "medium", "slot"], default="medium")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--depth", type=int, default=None,
+                    help="keep only the workload's first layers (profiler captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

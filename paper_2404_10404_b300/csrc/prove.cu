@@ -37,37 +37,93 @@ __device__ __forceinline__ void store_words(uint8_t* base, size_t off, const Fr&
 }
 
 // ---------------------------------------------------------------------------
-// Fiat-Shamir transcript (single thread)
+// Fiat-Shamir transcript
 //   absorb:    st = SHA256(st || tag || canonical LE elements)
 //   challenge: h = SHA256(st || 'C' || u32le ctr), x = LE(h) mod 2^254,
 //              accepted (st = h) when x < r.
+// The messages have fixed lengths, so every SHA-256 block is assembled word
+// by word at compile time (the element bytes sit one byte after the state,
+// behind the tag: each message word straddles two limbs).
 
-__device__ void tr_absorb(DevState* S, uint8_t tag, const Fr* canon, int n) {
-  Sha256Stream h;
-  h.begin();
-  h.digest_words(S->st);
-  h.byte(tag);
-  for (int i = 0; i < n; ++i)
-    for (int k = 0; k < 8; ++k) h.u32le(canon[i].v[k]);
-  uint32_t out[8];
-  h.end(out);
-  for (int i = 0; i < 8; ++i) S->st[i] = out[i];
+// absorb of N elements, given as 8N big-endian words (ew[8i+j] = bswap(limb j of element i))
+template <int N>
+struct AbsorbMsg {
+  static constexpr int L = 33 + 32 * N;              // message bytes
+  static constexpr int NB = (L + 9 + 63) / 64;       // padded blocks
+  const uint32_t* st;
+  uint32_t tag;
+  const uint32_t* ew;
+  __device__ __forceinline__ uint32_t word(int w) const {
+    if (w < 8) return st[w];
+    if (w == 8) return (tag << 24) | (ew[0] >> 8);
+    if (w < 8 + 8 * N) return (ew[w - 9] << 24) | (ew[w - 8] >> 8);
+    if (w == 8 + 8 * N) return (ew[8 * N - 1] << 24) | 0x00800000u;
+    if (w == 16 * NB - 1) return 8u * L;
+    return 0u;
+  }
+};
+
+template <class Msg>
+__device__ __forceinline__ void sha_message(const Msg& m, uint32_t out[8]) {
+  uint32_t h[8];
+  sha256_init(h);
+#pragma unroll
+  for (int b = 0; b < Msg::NB; ++b) {
+    uint32_t blk[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) blk[k] = m.word(16 * b + k);
+    sha256_compress(h, blk);
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) out[i] = h[i];
 }
 
-__device__ Fr tr_challenge(DevState* S) {
-  for (uint32_t ctr = 0; ctr < 4096u; ++ctr) {  // each try fails with probability < 1/4
-    Sha256Stream h;
-    h.begin();
-    h.digest_words(S->st);
-    h.byte('C');
-    h.u32le(ctr);
+template <int N>
+__device__ __noinline__ void tr_absorb_n(uint32_t* st, uint32_t tag, const Fr* canon) {
+  uint32_t ew[8 * N];
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) ew[8 * i + j] = bswap32(canon[i].v[j]);
+  uint32_t s0[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) s0[i] = st[i];
+  AbsorbMsg<N> m{s0, tag, ew};
+  uint32_t out[8];
+  sha_message(m, out);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) st[i] = out[i];
+}
+
+struct ChallengeMsg {
+  static constexpr int NB = 1;
+  const uint32_t* st;
+  uint32_t ctr;
+  __device__ __forceinline__ uint32_t word(int w) const {
+    if (w < 8) return st[w];
+    if (w == 8) return (uint32_t('C') << 24) | ((ctr & 0xffu) << 16) | (((ctr >> 8) & 0xffu) << 8) | ((ctr >> 16) & 0xffu);
+    if (w == 9) return ((ctr >> 24) << 24) | 0x00800000u;
+    if (w == 15) return 37u * 8u;
+    return 0u;
+  }
+};
+
+// next challenge in Montgomery form; a bounded number of tries (each is
+// rejected with probability below 1/4), then the error flag
+__device__ __noinline__ Fr tr_challenge(DevState* S) {
+  uint32_t s0[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) s0[i] = S->st[i];
+  for (uint32_t ctr = 0; ctr < 4096u; ++ctr) {
+    ChallengeMsg m{s0, ctr};
     uint32_t o[8];
-    h.end(o);
+    sha_message(m, o);
     Fr x;
 #pragma unroll
     for (int k = 0; k < 8; ++k) x.v[k] = bswap32(o[k]);
     x.v[7] &= 0x3fffffffu;
     if (fr_lt_modulus(x)) {
+#pragma unroll
       for (int i = 0; i < 8; ++i) S->st[i] = o[i];
       return fr_from_canonical(x);
     }
@@ -76,16 +132,31 @@ __device__ Fr tr_challenge(DevState* S) {
   return fr_zero();
 }
 
-// The last block of a round: canonical evaluations into the proof, absorb,
-// squeeze the round's challenge.
-__device__ void round_finalize(DevState* S, const Fr* vals, int n, uint8_t* proof, size_t off, Fr* rslot) {
-  Fr canon[4];
-  for (int i = 0; i < n; ++i) {
-    canon[i] = fr_to_canonical(vals[i]);
-    store_words(proof, off + 32 * (size_t)i, canon[i]);
+// The last block of a round, called by the lanes of its warp 0 with the
+// grid-wide sums in lane 0: canonical evaluations (one lane each) into the
+// proof, absorb 'R', squeeze the round's challenge.
+template <int NV>
+__device__ __forceinline__ void round_finalize(DevState* S, const Fr (&v)[NV], uint8_t* proof, size_t off,
+                                               Fr* rslot) {
+  __shared__ Fr sh[NV];
+  const int lane = threadIdx.x & 31;
+  if (lane == 0)
+#pragma unroll
+    for (int t = 0; t < NV; ++t) sh[t] = v[t];
+  __syncwarp();
+  if (lane < NV) {
+    Fr c = fr_to_canonical(sh[lane]);
+    store_words(proof, off + 32 * (size_t)lane, c);
+    sh[lane] = c;
   }
-  tr_absorb(S, 'R', canon, n);
-  *rslot = tr_challenge(S);
+  __syncwarp();
+  if (lane == 0) {
+    Fr canon[NV];
+#pragma unroll
+    for (int t = 0; t < NV; ++t) canon[t] = sh[t];
+    tr_absorb_n<NV>(S->st, 'R', canon);
+    *rslot = tr_challenge(S);
+  }
 }
 
 // Block-wide sum of NV field elements per thread; result in thread 0.
@@ -259,8 +330,7 @@ __global__ void __launch_bounds__(BD) k_copy_round(const uint32_t* __restrict__ 
     acc[2] = fr_add(acc[2], fr_mul(e2, s2));
     acc[3] = fr_add(acc[3], fr_mul(e3, s3));
   }
-  if (grid_sum_last_block<BD, 4>(acc, partials, S) && threadIdx.x == 0)
-    round_finalize(S, acc, 4, proof, off, &S->rb[k]);
+  if (grid_sum_last_block<BD, 4>(acc, partials, S) && threadIdx.x < 32) round_finalize<4>(S, acc, proof, off, &S->rb[k]);
 }
 
 int launch_copy_round(const uint32_t* T, uint32_t sn, uint32_t h, const uint32_t* E, const uint32_t* omega_s,
@@ -437,8 +507,7 @@ __global__ void __launch_bounds__(BD) k_gate_round(uint32_t* A, uint32_t* B1, ui
     acc[1] = fr_add(acc[1], fr_add(fr_mul(a1, p1), q1));
     acc[2] = fr_add(acc[2], fr_add(fr_mul(a2, p2), q2));
   }
-  if (grid_sum_last_block<BD, 3>(acc, partials, S) && threadIdx.x == 0)
-    round_finalize(S, acc, 3, proof, off, &rs[k]);
+  if (grid_sum_last_block<BD, 3>(acc, partials, S) && threadIdx.x < 32) round_finalize<3>(S, acc, proof, off, &rs[k]);
 }
 
 int launch_gate_round(uint32_t* A, uint32_t* B1, uint32_t* B2, uint32_t m, int phase, uint32_t k, uint32_t* partials,
@@ -457,7 +526,7 @@ __global__ void k_layer_end(DevState* S, const uint32_t* Ay, uint32_t s, uint8_t
   Fr canon[2] = {fr_to_canonical(S->vx), fr_to_canonical(vy)};
   store_words(proof, off, canon[0]);
   store_words(proof, off + 32, canon[1]);
-  tr_absorb(S, 'V', canon, 2);
+  tr_absorb_n<2>(S->st, 'V', canon);
   if (!last) {
     S->alpha = tr_challenge(S);
     S->beta = tr_challenge(S);

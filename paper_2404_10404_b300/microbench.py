@@ -1,0 +1,25 @@
+"""Integer-pipe microbenchmarks behind the roofline denominators.
+
+    python -m paper_2404_10404_b300.microbench
+
+Times independent 32-bit multiply-add chains (mad.lo, mad.hi) and chained
+Montgomery products on every SM of cuda:0, and prints one JSON line.
+"""
+import json
+
+import paper_2404_10404_b300 as S
+
+
+def main():
+    import torch
+    torch.cuda.set_device(0)
+    st = torch.cuda.current_stream().cuda_stream
+    out = {}
+    for name, kind, iters in (("mad_lo", 0, 512), ("mad_hi", 1, 512), ("fr_mul", 2, 128)):
+        ms, ops = S.microbench(kind, 148 * 8, 256, iters, st)
+        out[name] = {"ms": ms, "ops": ops, "per_s": ops / (ms / 1e3)}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()
