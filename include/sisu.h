@@ -158,8 +158,10 @@ int sisu_statement_digest(const uint8_t* data, size_t len, uint8_t* out, void* s
 
 /* Integer-pipe microbenchmarks used for the roofline: kind 0 = independent
  * 32-bit multiply-add chains (mad.lo), kind 1 = mad.hi chains, kind 2 =
- * Montgomery products.  Reports the elapsed milliseconds and the number of
- * operations (multiply-adds, or field products for kind 2). */
+ * Montgomery products as the kernels call them, kind 3 = the same products
+ * inlined, kind 4 = 32x32+64-bit mad.wide chains.  Reports the elapsed
+ * milliseconds and the number of operations (multiply-adds, or field
+ * products for kinds 2 and 3). */
 int sisu_microbench(int kind, uint32_t blocks, uint32_t threads, uint32_t iters, void* stream,
                     double* ms, double* ops);
 

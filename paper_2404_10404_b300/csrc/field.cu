@@ -130,6 +130,38 @@ __global__ void k_mb_frmul(uint32_t iters, uint32_t* sink) {
   sink[blockIdx.x * blockDim.x + threadIdx.x] = acc;
 }
 
+__global__ void k_mb_frmul_inline(uint32_t iters, uint32_t* sink) {
+  Fr x = fr_one(), y = fr_r2(), z = fr_one();
+  x.v[0] ^= threadIdx.x;
+  for (uint32_t it = 0; it < iters; ++it) {
+    x = fr_mul_inl(x, y);
+    z = fr_mul_inl(z, x);
+  }
+  uint32_t acc = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) acc ^= x.v[i] ^ z.v[i];
+  sink[blockIdx.x * blockDim.x + threadIdx.x] = acc;
+}
+
+__global__ void k_mb_madwide(uint32_t iters, uint32_t mul, uint32_t* sink) {
+  unsigned long long x[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) x[i] = threadIdx.x + 17u * i;
+  for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        uint32_t lo = (uint32_t)x[i];
+        asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(x[i]) : "r"(lo), "r"(mul));
+      }
+  }
+  unsigned long long acc = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) acc ^= x[i];
+  sink[blockIdx.x * blockDim.x + threadIdx.x] = (uint32_t)(acc ^ (acc >> 32));
+}
+
 int run_microbench(int kind, uint32_t blocks, uint32_t threads, uint32_t iters, void* stream, double* ms,
                    double* ops) {
   cudaStream_t st = (cudaStream_t)stream;
@@ -142,7 +174,9 @@ int run_microbench(int kind, uint32_t blocks, uint32_t threads, uint32_t iters, 
   auto launch = [&]() {
     if (kind == 0) k_mb_madlo<<<blocks, threads, 0, st>>>(iters, 0x9e3779b9u, sink);
     else if (kind == 1) k_mb_madhi<<<blocks, threads, 0, st>>>(iters, 0x9e3779b9u, sink);
-    else k_mb_frmul<<<blocks, threads, 0, st>>>(iters, sink);
+    else if (kind == 2) k_mb_frmul<<<blocks, threads, 0, st>>>(iters, sink);
+    else if (kind == 3) k_mb_frmul_inline<<<blocks, threads, 0, st>>>(iters, sink);
+    else k_mb_madwide<<<blocks, threads, 0, st>>>(iters, 0x9e3779b9u, sink);
     launches_add(1);
   };
   launch();  // warm-up
@@ -153,7 +187,7 @@ int run_microbench(int kind, uint32_t blocks, uint32_t threads, uint32_t iters, 
   float t = 0;
   cudaEventElapsedTime(&t, a, b);
   *ms = t;
-  double per = kind == 2 ? 2.0 : 64.0;
+  double per = (kind == 2 || kind == 3) ? 2.0 : 64.0;
   *ops = (double)blocks * threads * iters * per;
   cudaEventDestroy(a);
   cudaEventDestroy(b);

@@ -209,7 +209,7 @@ __device__ __forceinline__ Fr fr_dbl(const Fr& a) { return fr_add(a, a); }
         "r"(a.v[6]), "r"(a.v[7]), "r"(BI));                                                  \
   t0 = t1; t1 = t2; t2 = t3; t3 = t4; t4 = t5; t5 = t6; t6 = t7; t7 = t8;
 
-__device__ __forceinline__ Fr fr_mul(const Fr& a, const Fr& b) {
+__device__ __forceinline__ Fr fr_mul_inl(const Fr& a, const Fr& b) {
   uint32_t t0 = 0, t1 = 0, t2 = 0, t3 = 0, t4 = 0, t5 = 0, t6 = 0, t7 = 0, t8;
   SISU_CIOS_STEP(b.v[0])
   SISU_CIOS_STEP(b.v[1])
@@ -224,6 +224,14 @@ __device__ __forceinline__ Fr fr_mul(const Fr& a, const Fr& b) {
   r.v[4] = t4; r.v[5] = t5; r.v[6] = t6; r.v[7] = t7;
   return r;
 }
+
+// One out-of-line copy of the product per translation unit: a kernel that
+// inlined every product would hold tens of kilobytes of straight-line code
+// in its inner loop and stall on instruction fetch.  Operands and result
+// travel in registers.
+static __device__ __noinline__ Fr fr_mul_call(Fr a, Fr b) { return fr_mul_inl(a, b); }
+
+__device__ __forceinline__ Fr fr_mul(const Fr& a, const Fr& b) { return fr_mul_call(a, b); }
 
 __device__ __forceinline__ Fr fr_sqr(const Fr& a) { return fr_mul(a, a); }
 

@@ -72,7 +72,7 @@ __device__ __forceinline__ void sha_message(const Msg& m, uint32_t out[8]) {
     uint32_t blk[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) blk[k] = m.word(16 * b + k);
-    sha256_compress(h, blk);
+    sha256_compress_compact(h, blk);
   }
 #pragma unroll
   for (int i = 0; i < 8; ++i) out[i] = h[i];

@@ -87,12 +87,55 @@ __host__ __device__ __forceinline__ void sha256_compress(uint32_t h[8], const ui
   h[0] += a; h[1] += b; h[2] += c; h[3] += d; h[4] += e; h[5] += f; h[6] += g; h[7] += hh;
 }
 
+// The same compression with only 16 rounds unrolled (four passes): a small
+// code footprint for the single-thread transcript, which runs cold at the
+// end of a round kernel.
+__host__ __device__ __forceinline__ void sha256_compress_compact(uint32_t h[8], const uint32_t blk[16]) {
+  uint32_t w[16];
+#ifdef __CUDA_ARCH__
+#pragma unroll
+#endif
+  for (int t = 0; t < 16; ++t) w[t] = blk[t];
+  uint32_t a = h[0], b = h[1], c = h[2], d = h[3], e = h[4], f = h[5], g = h[6], hh = h[7];
+#ifdef __CUDA_ARCH__
+#pragma unroll 1
+#endif
+  for (int r = 0; r < 64; r += 16) {
+#ifdef __CUDA_ARCH__
+#pragma unroll
+#endif
+    for (int k = 0; k < 16; ++k) {
+      uint32_t wt;
+      if (r == 0) {
+        wt = w[k];
+      } else {
+        uint32_t w15 = w[(k + 1) & 15], w2 = w[(k + 14) & 15];
+        uint32_t s0 = sha_rotr(w15, 7) ^ sha_rotr(w15, 18) ^ (w15 >> 3);
+        uint32_t s1 = sha_rotr(w2, 17) ^ sha_rotr(w2, 19) ^ (w2 >> 10);
+        wt = w[k] + s0 + w[(k + 9) & 15] + s1;
+        w[k] = wt;
+      }
+      uint32_t S1 = sha_rotr(e, 6) ^ sha_rotr(e, 11) ^ sha_rotr(e, 25);
+      uint32_t ch = (e & f) ^ (~e & g);
+#ifdef __CUDA_ARCH__
+      uint32_t t1 = hh + S1 + ch + c_sha256_k[r + k] + wt;
+#else
+      uint32_t t1 = hh + S1 + ch + h_sha256_k[r + k] + wt;
+#endif
+      uint32_t S0 = sha_rotr(a, 2) ^ sha_rotr(a, 13) ^ sha_rotr(a, 22);
+      uint32_t maj = (a & b) ^ (a & c) ^ (b & c);
+      hh = g; g = f; f = e; e = d + t1; d = c; c = b; b = a; a = t1 + S0 + maj;
+    }
+  }
+  h[0] += a; h[1] += b; h[2] += c; h[3] += d; h[4] += e; h[5] += f; h[6] += g; h[7] += hh;
+}
+
 // Out-of-line compression for the byte-stream hasher: it is called from
 // many single-thread call sites, where inlining the unrolled rounds would
 // only grow the code.
 #ifdef __CUDACC__
 static __device__ __noinline__ void sha256_compress_call(uint32_t h[8], const uint32_t blk[16]) {
-  sha256_compress(h, blk);
+  sha256_compress_compact(h, blk);
 }
 __host__ __device__ __forceinline__ void sha256_compress_stream(uint32_t h[8], const uint32_t blk[16]) {
 #ifdef __CUDA_ARCH__

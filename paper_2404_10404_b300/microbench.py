@@ -15,7 +15,8 @@ def main():
     torch.cuda.set_device(0)
     st = torch.cuda.current_stream().cuda_stream
     out = {}
-    for name, kind, iters in (("mad_lo", 0, 512), ("mad_hi", 1, 512), ("fr_mul", 2, 128)):
+    for name, kind, iters in (("mad_lo", 0, 512), ("mad_hi", 1, 512), ("fr_mul", 2, 128),
+                              ("fr_mul_inline", 3, 128), ("mad_wide", 4, 512)):
         ms, ops = S.microbench(kind, 148 * 8, 256, iters, st)
         out[name] = {"ms": ms, "ops": ops, "per_s": ops / (ms / 1e3)}
     print(json.dumps(out))
