@@ -159,9 +159,12 @@ int sisu_statement_digest(const uint8_t* data, size_t len, uint8_t* out, void* s
 /* Integer-pipe microbenchmarks used for the roofline: kind 0 = independent
  * 32-bit multiply-add chains (mad.lo), kind 1 = mad.hi chains, kind 2 =
  * Montgomery products as the kernels call them, kind 3 = the same products
- * inlined, kind 4 = 32x32+64-bit mad.wide chains.  Reports the elapsed
+ * inlined, kind 4 = 32x32+64-bit mad.wide chains, kind 5 = Montgomery
+ * products built from 64-bit partial products (mul.wide), kind 6 = kinds 2
+ * and 5 run side by side on the same operands.  Reports the elapsed
  * milliseconds and the number of operations (multiply-adds, or field
- * products for kinds 2 and 3). */
+ * products for kinds 2, 3 and 5); for kind 6, *ops is minus the number of
+ * threads whose two products disagreed (0 when they all agree). */
 int sisu_microbench(int kind, uint32_t blocks, uint32_t threads, uint32_t iters, void* stream,
                     double* ms, double* ops);
 

@@ -640,7 +640,20 @@ static int enqueue_prove(const sisu_circuit* cc, sisu_eval* ev, const sisu_trans
     const size_t offx = off + 32 * 4 * (size_t)c;
     const size_t offy = offx + 32 * 3 * (size_t)s;
     const size_t offv = offy + 32 * 3 * (size_t)s;
-    // phase over x
+    if (Wn <= kTailMaxWidth) {
+      // Libra's two phases and the end of the layer in one cluster launch
+      TailParams tp;
+      tp.A = A; tp.E = w.E; tp.om = w.om; tp.sg = L.sgate;
+      tp.off1 = L.off1; tp.pos1 = L.pos1; tp.off2 = L.off2; tp.pos2 = L.pos2;
+      tp.nmul = L.nmul; tp.Wn = Wn; tp.s = s;
+      tp.At = w.At; tp.H1 = w.H1; tp.H2 = w.H2; tp.Ay = w.Ay; tp.Q = w.Q;
+      tp.S = w.S; tp.proof = w.proof; tp.offx = offx; tp.offy = offy; tp.offv = offv; tp.last = i + 1 == d;
+      ProfScope ps(kProfGateRound, (double)Wn * (6.0 + s) + 2.0 * L.ntot, st);
+      CK(launch_layer_tail(tp, st), "layer tail");
+      off = offv + 64;
+      continue;
+    }
+    // wide layers: one launch per round over the whole GPU
     {
       ProfScope ps(kProfPhaseInit, (double)L.ntot + 2.0 * Wn, st);
       CK(launch_xinit(A, w.E, w.om, L, Wn, w.At, w.H1, w.H2, w.Ay, st), "x init");
@@ -650,7 +663,6 @@ static int enqueue_prove(const sisu_circuit* cc, sisu_eval* ev, const sisu_trans
       CK(launch_gate_round(w.At, w.H1, w.H2, Wn >> k, 0, k, w.partials, w.S, w.proof, offx + 96 * (size_t)k, st),
          "x round");
     }
-    // phase over y
     {
       ProfScope ps(kProfPhaseInit, (double)Wn * s + L.ntot + 3.0 * Wn, st);
       CK(launch_eq_rx(w.S, s, Wn, w.Q, w.At, st), "eq(r_x)");
@@ -773,7 +785,7 @@ extern "C" int sisu_statement_digest(const uint8_t* data, size_t len, uint8_t* o
 
 extern "C" int sisu_microbench(int kind, uint32_t blocks, uint32_t threads, uint32_t iters, void* stream, double* ms,
                                double* ops) {
-  if (kind < 0 || kind > 4 || !blocks || !threads || threads > 1024 || !ms || !ops)
+  if (kind < 0 || kind > 6 || !blocks || !threads || threads > 1024 || !ms || !ops)
     return fail(SISU_ERR_INVALID_ARG, "bad microbenchmark arguments");
   int rc = run_microbench(kind, blocks, threads, iters, stream, ms, ops);
   if (rc) return cuda_fail((cudaError_t)rc, "microbenchmark");

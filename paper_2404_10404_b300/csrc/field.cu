@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "internal.h"
 #include "launch.cuh"
@@ -143,6 +144,36 @@ __global__ void k_mb_frmul_inline(uint32_t iters, uint32_t* sink) {
   sink[blockIdx.x * blockDim.x + threadIdx.x] = acc;
 }
 
+__global__ void k_mb_frmul_wide(uint32_t iters, uint32_t* sink) {
+  Fr x = fr_one(), y = fr_r2(), z = fr_one();
+  x.v[0] ^= threadIdx.x;
+  for (uint32_t it = 0; it < iters; ++it) {
+    x = fr_mul_wide_call(x, y);
+    z = fr_mul_wide_call(z, x);
+  }
+  uint32_t acc = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) acc ^= x.v[i] ^ z.v[i];
+  sink[blockIdx.x * blockDim.x + threadIdx.x] = acc;
+}
+
+// check of the two product formulations against each other (kind 6)
+__global__ void k_mb_frmul_check(uint32_t iters, uint32_t* sink) {
+  Fr x = fr_one(), y = fr_r2(), u = fr_one(), v = fr_r2();
+  x.v[0] ^= threadIdx.x + blockIdx.x * 977u;
+  u = x;
+  uint32_t bad = 0;
+  for (uint32_t it = 0; it < iters; ++it) {
+    x = fr_mul_call(x, y);
+    u = fr_mul_wide_call(u, v);
+    y = fr_add(y, x);
+    v = fr_add(v, u);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) bad |= x.v[i] ^ u.v[i];
+  }
+  sink[blockIdx.x * blockDim.x + threadIdx.x] = bad;
+}
+
 __global__ void k_mb_madwide(uint32_t iters, uint32_t mul, uint32_t* sink) {
   unsigned long long x[8];
 #pragma unroll
@@ -176,7 +207,9 @@ int run_microbench(int kind, uint32_t blocks, uint32_t threads, uint32_t iters, 
     else if (kind == 1) k_mb_madhi<<<blocks, threads, 0, st>>>(iters, 0x9e3779b9u, sink);
     else if (kind == 2) k_mb_frmul<<<blocks, threads, 0, st>>>(iters, sink);
     else if (kind == 3) k_mb_frmul_inline<<<blocks, threads, 0, st>>>(iters, sink);
-    else k_mb_madwide<<<blocks, threads, 0, st>>>(iters, 0x9e3779b9u, sink);
+    else if (kind == 4) k_mb_madwide<<<blocks, threads, 0, st>>>(iters, 0x9e3779b9u, sink);
+    else if (kind == 5) k_mb_frmul_wide<<<blocks, threads, 0, st>>>(iters, sink);
+    else k_mb_frmul_check<<<blocks, threads, 0, st>>>(iters, sink);
     launches_add(1);
   };
   launch();  // warm-up
@@ -187,7 +220,18 @@ int run_microbench(int kind, uint32_t blocks, uint32_t threads, uint32_t iters, 
   float t = 0;
   cudaEventElapsedTime(&t, a, b);
   *ms = t;
-  double per = (kind == 2 || kind == 3) ? 2.0 : 64.0;
+  if (kind == 6 && e == cudaSuccess) {
+    std::vector<uint32_t> h((size_t)blocks * threads);
+    e = cudaMemcpy(h.data(), sink, h.size() * 4, cudaMemcpyDeviceToHost);
+    size_t bad = 0;
+    for (uint32_t x : h) bad += x != 0;
+    *ops = -(double)bad;  // number of threads whose products disagreed (0 = agree)
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(sink);
+    return (int)e;
+  }
+  double per = (kind == 2 || kind == 3 || kind == 5) ? 2.0 : kind == 6 ? 2.0 : 64.0;
   *ops = (double)blocks * threads * iters * per;
   cudaEventDestroy(a);
   cudaEventDestroy(b);

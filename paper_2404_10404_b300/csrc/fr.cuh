@@ -225,6 +225,65 @@ __device__ __forceinline__ Fr fr_mul_inl(const Fr& a, const Fr& b) {
   return r;
 }
 
+// The same CIOS product with every 32x32 partial product formed as one
+// 64-bit multiply (mul.wide.u32) and the carries in pure add chains.
+#define SISU_ROW_ADD(P0, P1, P2, P3, P4, P5, P6, P7)                                          \
+  asm("add.cc.u32  %0, %0, %9;\n\t"                                                          \
+      "addc.cc.u32 %1, %1, %10;\n\t"                                                         \
+      "addc.cc.u32 %2, %2, %11;\n\t"                                                         \
+      "addc.cc.u32 %3, %3, %12;\n\t"                                                         \
+      "addc.cc.u32 %4, %4, %13;\n\t"                                                         \
+      "addc.cc.u32 %5, %5, %14;\n\t"                                                         \
+      "addc.cc.u32 %6, %6, %15;\n\t"                                                         \
+      "addc.cc.u32 %7, %7, %16;\n\t"                                                         \
+      "addc.u32    %8, %8, 0;\n\t"                                                           \
+      "add.cc.u32  %1, %1, %17;\n\t"                                                         \
+      "addc.cc.u32 %2, %2, %18;\n\t"                                                         \
+      "addc.cc.u32 %3, %3, %19;\n\t"                                                         \
+      "addc.cc.u32 %4, %4, %20;\n\t"                                                         \
+      "addc.cc.u32 %5, %5, %21;\n\t"                                                         \
+      "addc.cc.u32 %6, %6, %22;\n\t"                                                         \
+      "addc.cc.u32 %7, %7, %23;\n\t"                                                         \
+      "addc.u32    %8, %8, %24;\n\t"                                                         \
+      : "+r"(t0), "+r"(t1), "+r"(t2), "+r"(t3), "+r"(t4), "+r"(t5), "+r"(t6), "+r"(t7), "+r"(t8) \
+      : "r"((uint32_t)(P0)), "r"((uint32_t)(P1)), "r"((uint32_t)(P2)), "r"((uint32_t)(P3)),     \
+        "r"((uint32_t)(P4)), "r"((uint32_t)(P5)), "r"((uint32_t)(P6)), "r"((uint32_t)(P7)),     \
+        "r"((uint32_t)((P0) >> 32)), "r"((uint32_t)((P1) >> 32)), "r"((uint32_t)((P2) >> 32)), \
+        "r"((uint32_t)((P3) >> 32)), "r"((uint32_t)((P4) >> 32)), "r"((uint32_t)((P5) >> 32)), \
+        "r"((uint32_t)((P6) >> 32)), "r"((uint32_t)((P7) >> 32)))
+
+#define SISU_CIOS_WIDE_STEP(BI)                                                               \
+  {                                                                                          \
+    const uint64_t bi_ = (BI);                                                               \
+    t8 = 0;                                                                                  \
+    SISU_ROW_ADD(a.v[0] * bi_, a.v[1] * bi_, a.v[2] * bi_, a.v[3] * bi_, a.v[4] * bi_,        \
+                 a.v[5] * bi_, a.v[6] * bi_, a.v[7] * bi_);                                  \
+    const uint64_t m_ = (uint32_t)(t0 * SISU_NINV_C);                                        \
+    SISU_ROW_ADD(m_ * 0xf0000001ull, m_ * 0x43e1f593ull, m_ * 0x79b97091ull, m_ * 0x2833e848ull, \
+                 m_ * 0x8181585dull, m_ * 0xb85045b6ull, m_ * 0xe131a029ull, m_ * 0x30644e72ull); \
+    t0 = t1; t1 = t2; t2 = t3; t3 = t4; t4 = t5; t5 = t6; t6 = t7; t7 = t8;                   \
+  }
+
+#define SISU_NINV_C 0xefffffffu
+
+__device__ __forceinline__ Fr fr_mul_wide_inl(const Fr& a, const Fr& b) {
+  uint32_t t0 = 0, t1 = 0, t2 = 0, t3 = 0, t4 = 0, t5 = 0, t6 = 0, t7 = 0, t8;
+  SISU_CIOS_WIDE_STEP(b.v[0])
+  SISU_CIOS_WIDE_STEP(b.v[1])
+  SISU_CIOS_WIDE_STEP(b.v[2])
+  SISU_CIOS_WIDE_STEP(b.v[3])
+  SISU_CIOS_WIDE_STEP(b.v[4])
+  SISU_CIOS_WIDE_STEP(b.v[5])
+  SISU_CIOS_WIDE_STEP(b.v[6])
+  SISU_CIOS_WIDE_STEP(b.v[7])
+  Fr r;
+  r.v[0] = t0; r.v[1] = t1; r.v[2] = t2; r.v[3] = t3;
+  r.v[4] = t4; r.v[5] = t5; r.v[6] = t6; r.v[7] = t7;
+  return r;
+}
+
+static __device__ __noinline__ Fr fr_mul_wide_call(Fr a, Fr b) { return fr_mul_wide_inl(a, b); }
+
 // One out-of-line copy of the product per translation unit: a kernel that
 // inlined every product would hold tens of kilobytes of straight-line code
 // in its inner loop and stall on instruction fetch.  Operands and result

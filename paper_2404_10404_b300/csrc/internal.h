@@ -104,6 +104,25 @@ int launch_yinit(const uint32_t* E, const uint32_t* omega_s, const uint32_t* Q, 
 int launch_layer_end(DevState* S, const uint32_t* Ay, uint32_t s, uint8_t* proof, size_t off, int last,
                      void* stream);
 
+// Libra's two phases of one layer in a single thread-block-cluster launch
+// (tables up to kTailMaxWidth entries): phase-1 init, the x rounds,
+// EQ(r_x), phase-2 init, the y rounds and the end of the layer.
+constexpr uint32_t kTailMaxWidth = 1u << 16;
+struct TailParams {
+  const uint32_t* A;  // row V~(r_b, .) after the copy phase
+  const uint32_t* E;  // E[0] = eq(z_b, r_b)
+  const uint32_t* om; // gate weights, sorted order
+  const uint4* sg;
+  const uint32_t *off1, *pos1, *off2, *pos2;
+  uint32_t nmul, Wn, s;
+  uint32_t *At, *H1, *H2, *Ay, *Q;
+  DevState* S;
+  uint8_t* proof;
+  size_t offx, offy, offv;
+  int last;
+};
+int launch_layer_tail(const TailParams& p, void* stream);
+
 int launch_fr_batch(int op, const uint32_t* a, const uint32_t* b, uint32_t* out, size_t n,
                     uint32_t* flags, void* stream);
 int run_microbench(int kind, uint32_t blocks, uint32_t threads, uint32_t iters, void* stream, double* ms,

@@ -1,5 +1,6 @@
 // Prover kernels: the device transcript, layer initialisation, the copy
 // phase and Libra's two phases of the GKR layer sumcheck.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -536,6 +537,203 @@ __global__ void k_layer_end(DevState* S, const uint32_t* Ay, uint32_t s, uint8_t
 int launch_layer_end(DevState* S, const uint32_t* Ay, uint32_t s, uint8_t* proof, size_t off, int last,
                      void* stream) {
   k_layer_end<<<1, 32, 0, (cudaStream_t)stream>>>(S, Ay, s, proof, off, last);
+  return post_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Libra's two phases of one layer in one launch of a thread-block cluster.
+//
+// Each round is latency-bound (tables of at most a few thousand entries),
+// so a separate launch per round cost more than the round's arithmetic.
+// The cluster's CTAs share every round: each folds and evaluates its pairs,
+// sends its partial sums to CTA 0 through distributed shared memory, CTA 0
+// runs the transcript, and the challenge comes back the same way.  Tables
+// live in global memory and are read through L2 (__ldcg): entries written
+// by another CTA in the previous round are ordered by the cluster barrier.
+
+namespace cg = cooperative_groups;
+constexpr int kTailCTAs = 8;
+constexpr int kTailThreads = 256;
+
+__device__ __forceinline__ Fr fr_ldcg_state(const Fr* p) {
+  const uint4* q = reinterpret_cast<const uint4*>(p);
+  uint4 a = __ldcg(q), b = __ldcg(q + 1);
+  Fr x;
+  x.v[0] = a.x; x.v[1] = a.y; x.v[2] = a.z; x.v[3] = a.w;
+  x.v[4] = b.x; x.v[5] = b.y; x.v[6] = b.z; x.v[7] = b.w;
+  return x;
+}
+
+struct TailShared {
+  Fr part[kTailCTAs][3];  // CTA 0: partial sums of every CTA
+  Fr canon[3];            // CTA 0: canonical round values
+  Fr bcast;               // CTA 0: the round's challenge, read by every CTA
+  Fr vx;                  // CTA 0: v_x, read by every CTA
+  Fr red[3][kTailThreads / 32];
+};
+
+// One round over tables (A, B1, B2) of size m (after the fold of `rprev`
+// when k > 0): g(t) = sum_{j < m/2} A_t(j) B1_t(j) + B2_t(j), t = 0, 1, 2.
+// Returns the round's challenge (Montgomery form) in every thread.
+__device__ Fr tail_round(cg::cluster_group& cl, TailShared& sh, uint32_t* A, uint32_t* B1, uint32_t* B2,
+                         uint32_t m, uint32_t k, const Fr& rprev, DevState* S, uint8_t* proof, size_t off,
+                         Fr* rslot) {
+  const uint32_t rank = cl.block_rank();
+  const uint32_t hq = m / 2;
+  Fr acc[3] = {fr_zero(), fr_zero(), fr_zero()};
+  for (uint32_t j = rank * kTailThreads + threadIdx.x; j < hq; j += kTailCTAs * kTailThreads) {
+    Fr a0, a1, p0, p1, q0, q1;
+    if (k > 0) {
+      a0 = fold2(fr_load_cg(A, j), fr_load_cg(A, j + m), rprev);
+      a1 = fold2(fr_load_cg(A, j + hq), fr_load_cg(A, j + hq + m), rprev);
+      p0 = fold2(fr_load_cg(B1, j), fr_load_cg(B1, j + m), rprev);
+      p1 = fold2(fr_load_cg(B1, j + hq), fr_load_cg(B1, j + hq + m), rprev);
+      q0 = fold2(fr_load_cg(B2, j), fr_load_cg(B2, j + m), rprev);
+      q1 = fold2(fr_load_cg(B2, j + hq), fr_load_cg(B2, j + hq + m), rprev);
+      fr_store(A, j, a0); fr_store(A, j + hq, a1);
+      fr_store(B1, j, p0); fr_store(B1, j + hq, p1);
+      fr_store(B2, j, q0); fr_store(B2, j + hq, q1);
+    } else {
+      a0 = fr_load_cg(A, j); a1 = fr_load_cg(A, j + hq);
+      p0 = fr_load_cg(B1, j); p1 = fr_load_cg(B1, j + hq);
+      q0 = fr_load_cg(B2, j); q1 = fr_load_cg(B2, j + hq);
+    }
+    const Fr a2 = fr_sub(fr_dbl(a1), a0), p2 = fr_sub(fr_dbl(p1), p0), q2 = fr_sub(fr_dbl(q1), q0);
+    acc[0] = fr_add(acc[0], fr_add(fr_mul(a0, p0), q0));
+    acc[1] = fr_add(acc[1], fr_add(fr_mul(a1, p1), q1));
+    acc[2] = fr_add(acc[2], fr_add(fr_mul(a2, p2), q2));
+  }
+  // CTA sum, then into CTA 0's shared memory
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int t = 0; t < 3; ++t) acc[t] = fr_warp_sum(acc[t]);
+  if (lane == 0)
+#pragma unroll
+    for (int t = 0; t < 3; ++t) sh.red[t][warp] = acc[t];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int t = 0; t < 3; ++t) acc[t] = fr_warp_sum(lane < kTailThreads / 32 ? sh.red[t][lane] : fr_zero());
+    if (lane == 0) {
+      Fr* dst = cl.map_shared_rank(&sh.part[0][0], 0);
+#pragma unroll
+      for (int t = 0; t < 3; ++t) dst[rank * 3 + t] = acc[t];
+    }
+  }
+  cl.sync();
+  if (rank == 0 && warp == 0) {
+    if (lane < 3) {
+      Fr v = fr_zero();
+#pragma unroll
+      for (int c = 0; c < kTailCTAs; ++c) v = fr_add(v, sh.part[c][lane]);
+      v = fr_to_canonical(v);
+      store_words(proof, off + 32 * (size_t)lane, v);
+      sh.canon[lane] = v;
+    }
+    __syncwarp();
+    if (lane == 0) {
+      Fr canon[3] = {sh.canon[0], sh.canon[1], sh.canon[2]};
+      tr_absorb_n<3>(S->st, 'R', canon);
+      Fr r = tr_challenge(S);
+      *rslot = r;
+      sh.bcast = r;
+    }
+  }
+  cl.sync();
+  return *cl.map_shared_rank(&sh.bcast, 0);
+}
+
+__global__ void __cluster_dims__(kTailCTAs, 1, 1) __launch_bounds__(kTailThreads) k_layer_tail(TailParams p) {
+  cg::cluster_group cl = cg::this_cluster();
+  __shared__ TailShared sh;
+  const uint32_t rank = cl.block_rank();
+  const uint32_t gtid = rank * kTailThreads + threadIdx.x, gstride = kTailCTAs * kTailThreads;
+  DevState* S = p.S;
+  const Fr e = fr_load(p.E, 0);
+  // Libra phase 1 bookkeeping: H1(x) = e sum_{in1 g = x} w(g) (mul ? A(in2 g) : 1),
+  // H2(x) = e sum_{in1 g = x, add} w(g) A(in2 g)
+  for (uint32_t x = gtid; x < p.Wn; x += gstride) {
+    Fr a1 = fr_zero(), a2 = fr_zero();
+    for (uint32_t q = p.off1[x], qe = p.off1[x + 1]; q < qe; ++q) {
+      uint32_t g = p.pos1[q];
+      Fr w = fr_load(p.om, g);
+      Fr wa = fr_mul(w, fr_load(p.A, p.sg[g].y));
+      if (g < p.nmul) {
+        a1 = fr_add(a1, wa);
+      } else {
+        a1 = fr_add(a1, w);
+        a2 = fr_add(a2, wa);
+      }
+    }
+    fr_store(p.H1, x, fr_mul(e, a1));
+    fr_store(p.H2, x, fr_mul(e, a2));
+    Fr a = fr_load(p.A, x);
+    fr_store(p.At, x, a);
+    fr_store(p.Ay, x, a);
+  }
+  cl.sync();
+  Fr r = fr_zero();
+  for (uint32_t k = 0; k < p.s; ++k)
+    r = tail_round(cl, sh, p.At, p.H1, p.H2, p.Wn >> k, k, r, S, p.proof, p.offx + 96 * (size_t)k, &S->rx[k]);
+  // v_x = A(r_x)
+  if (rank == 0 && threadIdx.x == 0) {
+    Fr vx = p.s == 0 ? fr_load_cg(p.At, 0) : fold2(fr_load_cg(p.At, 0), fr_load_cg(p.At, 1), r);
+    S->vx = vx;
+    sh.vx = vx;
+  }
+  // Q = EQ(r_x) over the Wn positions of layer i+1
+  for (uint32_t x = gtid; x < p.Wn; x += gstride) {
+    Fr acc = fr_one();
+    for (uint32_t k = 0; k < p.s; ++k) {
+      const Fr rk = fr_ldcg_state(&S->rx[k]);
+      uint32_t bit = (x >> (p.s - 1 - k)) & 1u;
+      acc = fr_mul(acc, bit ? rk : fr_sub(fr_one(), rk));
+    }
+    fr_store(p.Q, x, acc);
+  }
+  cl.sync();
+  const Fr vx = *cl.map_shared_rank(&sh.vx, 0);
+  // Libra phase 2 bookkeeping: K1(y) = e sum_{in2 g = y} w(g) Q(in1 g) (mul ? v_x : 1),
+  // K2(y) = e sum_{in2 g = y, add} w(g) Q(in1 g) v_x
+  const Fr ev = fr_mul(e, vx);
+  for (uint32_t y = gtid; y < p.Wn; y += gstride) {
+    Fr mu = fr_zero(), ad = fr_zero();
+    for (uint32_t q = p.off2[y], qe = p.off2[y + 1]; q < qe; ++q) {
+      uint32_t g = p.pos2[q];
+      Fr wq = fr_mul(fr_load(p.om, g), fr_load_cg(p.Q, p.sg[g].x));
+      if (g < p.nmul) mu = fr_add(mu, wq);
+      else ad = fr_add(ad, wq);
+    }
+    fr_store(p.H1, y, fr_add(fr_mul(e, ad), fr_mul(ev, mu)));
+    fr_store(p.H2, y, fr_mul(ev, ad));
+  }
+  cl.sync();
+  for (uint32_t k = 0; k < p.s; ++k)
+    r = tail_round(cl, sh, p.Ay, p.H1, p.H2, p.Wn >> k, k, r, S, p.proof, p.offy + 96 * (size_t)k, &S->ry[k]);
+  // end of the layer: v_y, (v_x, v_y) into the proof, absorb 'V', alpha, beta
+  if (rank == 0 && threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    if (lane < 2) {
+      Fr v = lane == 0 ? vx : (p.s == 0 ? fr_load_cg(p.Ay, 0) : fold2(fr_load_cg(p.Ay, 0), fr_load_cg(p.Ay, 1), r));
+      if (lane == 1) S->vy = v;
+      Fr c = fr_to_canonical(v);
+      store_words(p.proof, p.offv + 32 * (size_t)lane, c);
+      sh.canon[lane] = c;
+    }
+    __syncwarp();
+    if (lane == 0) {
+      Fr canon[2] = {sh.canon[0], sh.canon[1]};
+      tr_absorb_n<2>(S->st, 'V', canon);
+      if (!p.last) {
+        S->alpha = tr_challenge(S);
+        S->beta = tr_challenge(S);
+      }
+    }
+  }
+}
+
+int launch_layer_tail(const TailParams& p, void* stream) {
+  k_layer_tail<<<kTailCTAs, kTailThreads, 0, (cudaStream_t)stream>>>(p);
   return post_launch();
 }
 

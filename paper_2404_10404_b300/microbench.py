@@ -16,7 +16,8 @@ def main():
     st = torch.cuda.current_stream().cuda_stream
     out = {}
     for name, kind, iters in (("mad_lo", 0, 512), ("mad_hi", 1, 512), ("fr_mul", 2, 128),
-                              ("fr_mul_inline", 3, 128), ("mad_wide", 4, 512)):
+                              ("fr_mul_inline", 3, 128), ("mad_wide", 4, 512), ("fr_mul_wide", 5, 128),
+                              ("fr_mul_check", 6, 64)):
         ms, ops = S.microbench(kind, 148 * 8, 256, iters, st)
         out[name] = {"ms": ms, "ops": ops, "per_s": ops / (ms / 1e3)}
     print(json.dumps(out))

@@ -82,6 +82,13 @@ def test_device_digest_vs_oracle(S, oracle, n):
 
 
 def test_microbench_runs(S):
-    for kind in (0, 1, 2):
+    for kind in (0, 1, 2, 3, 4, 5):
         ms, ops = S.microbench(kind, 148, 256, 64)
         assert ms > 0 and ops > 0
+
+
+def test_product_formulations_agree(S):
+    """The carry-chain and the 64-bit-partial-product Montgomery products
+    give identical limbs on chained inputs (every thread of every block)."""
+    ms, bad = S.microbench(6, 148 * 4, 256, 256)
+    assert bad == 0

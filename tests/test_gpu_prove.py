@@ -71,6 +71,13 @@ def test_shapes_parity(S, oracle, C, widths, pct):
     _case(S, oracle, synth.micro(11, C, widths, pct))
 
 
+def test_wide_next_layer_parity(S, oracle):
+    """A layer reading from more than 2^16 gates takes the one-launch-per-
+    round path of Libra's phases instead of the cluster kernel."""
+    _case(S, oracle, synth.micro(13, 2, [1024, 1 << 17], 50))
+    _case(S, oracle, synth.micro(14, 4, [3000, 70000, 5000], 60))
+
+
 def test_mixing_parity(S, oracle):
     _case(S, oracle, synth.mixing_circuit(3, 64, 256, 6))
 
