@@ -26,6 +26,18 @@ __device__ __forceinline__ Fr eq_index(const Fr* r, uint32_t s, uint32_t v) {
   return acc;
 }
 
+// The same product started from the integer 1 instead of Montgomery 1:
+// Montgomery products of a plain value with Montgomery values stay plain,
+// so this returns eq(r, v) in plain (non-Montgomery) form at no extra cost.
+__device__ __forceinline__ Fr eq_index_plain(const Fr* r, uint32_t s, uint32_t v) {
+  Fr acc = fr_int_one();
+  for (uint32_t k = 0; k < s; ++k) {
+    uint32_t bit = (v >> (s - 1 - k)) & 1u;
+    acc = fr_mul(acc, bit ? r[k] : fr_one_minus(r[k]));
+  }
+  return acc;
+}
+
 // x + r (y - x): the multilinear line through two table entries
 __device__ __forceinline__ Fr fold2(const Fr& x, const Fr& y, const Fr& r) {
   return fr_add(x, fr_mul(r, fr_sub(y, x)));
@@ -135,7 +147,9 @@ __device__ __noinline__ Fr tr_challenge(DevState* S) {
 
 // The last block of a round, called by the lanes of its warp 0 with the
 // grid-wide sums in lane 0: canonical evaluations (one lane each) into the
-// proof, absorb 'R', squeeze the round's challenge.
+// proof, absorb 'R', squeeze the round's challenge.  The sums are plain
+// (not Montgomery) values below 2r: the copy weights E and the Libra tables
+// H, K are kept plain, so one conditional subtraction makes them canonical.
 template <int NV>
 __device__ __forceinline__ void round_finalize(DevState* S, const Fr (&v)[NV], uint8_t* proof, size_t off,
                                                Fr* rslot) {
@@ -146,7 +160,7 @@ __device__ __forceinline__ void round_finalize(DevState* S, const Fr (&v)[NV], u
     for (int t = 0; t < NV; ++t) sh[t] = v[t];
   __syncwarp();
   if (lane < NV) {
-    Fr c = fr_to_canonical(sh[lane]);
+    Fr c = fr_reduce_once(sh[lane]);
     store_words(proof, off + 32 * (size_t)lane, c);
     sh[lane] = c;
   }
@@ -256,7 +270,7 @@ __global__ void k_layer_init(DevState* S, uint32_t layer, uint32_t c, uint32_t s
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
        idx += (size_t)gridDim.x * blockDim.x) {
     if (idx < C) {
-      fr_store(E, idx, eq_index(z, c, (uint32_t)idx));
+      fr_store(E, idx, eq_index_plain(z, c, (uint32_t)idx));
     } else {
       uint32_t q = (uint32_t)(idx - C);
       uint32_t g = sg[q].z;
@@ -574,35 +588,43 @@ struct TailShared {
 
 // One round over tables (A, B1, B2) of size m (after the fold of `rprev`
 // when k > 0): g(t) = sum_{j < m/2} A_t(j) B1_t(j) + B2_t(j), t = 0, 1, 2.
-// Returns the round's challenge (Montgomery form) in every thread.
+// A is in Montgomery form and B1, B2 are plain, so the products and the
+// sums are plain.  The round runs in two cluster-wide steps, each thread
+// doing at most a few products: the fold (one product per new table
+// entry), then one product per (pair, t).  Returns the round's challenge
+// (Montgomery form) in every thread.
 __device__ Fr tail_round(cg::cluster_group& cl, TailShared& sh, uint32_t* A, uint32_t* B1, uint32_t* B2,
                          uint32_t m, uint32_t k, const Fr& rprev, DevState* S, uint8_t* proof, size_t off,
                          Fr* rslot) {
   const uint32_t rank = cl.block_rank();
-  const uint32_t hq = m / 2;
-  Fr acc[3] = {fr_zero(), fr_zero(), fr_zero()};
-  for (uint32_t j = rank * kTailThreads + threadIdx.x; j < hq; j += kTailCTAs * kTailThreads) {
-    Fr a0, a1, p0, p1, q0, q1;
-    if (k > 0) {
-      a0 = fold2(fr_load_cg(A, j), fr_load_cg(A, j + m), rprev);
-      a1 = fold2(fr_load_cg(A, j + hq), fr_load_cg(A, j + hq + m), rprev);
-      p0 = fold2(fr_load_cg(B1, j), fr_load_cg(B1, j + m), rprev);
-      p1 = fold2(fr_load_cg(B1, j + hq), fr_load_cg(B1, j + hq + m), rprev);
-      q0 = fold2(fr_load_cg(B2, j), fr_load_cg(B2, j + m), rprev);
-      q1 = fold2(fr_load_cg(B2, j + hq), fr_load_cg(B2, j + hq + m), rprev);
-      fr_store(A, j, a0); fr_store(A, j + hq, a1);
-      fr_store(B1, j, p0); fr_store(B1, j + hq, p1);
-      fr_store(B2, j, q0); fr_store(B2, j + hq, q1);
-    } else {
-      a0 = fr_load_cg(A, j); a1 = fr_load_cg(A, j + hq);
-      p0 = fr_load_cg(B1, j); p1 = fr_load_cg(B1, j + hq);
-      q0 = fr_load_cg(B2, j); q1 = fr_load_cg(B2, j + hq);
+  const uint32_t gtid = rank * kTailThreads + threadIdx.x, gstride = kTailCTAs * kTailThreads;
+  if (k > 0) {
+    // fold of the three tables from 2m to m entries (in place: entry q < m
+    // is written only by the thread that reads q and q + m)
+    for (uint32_t q = gtid; q < 3 * m; q += gstride) {
+      const uint32_t tab = q / m, idx = q - tab * m;
+      uint32_t* T = tab == 0 ? A : tab == 1 ? B1 : B2;
+      fr_store(T, idx, fold2(fr_load_cg(T, idx), fr_load_cg(T, idx + m), rprev));
     }
-    const Fr a2 = fr_sub(fr_dbl(a1), a0), p2 = fr_sub(fr_dbl(p1), p0), q2 = fr_sub(fr_dbl(q1), q0);
-    acc[0] = fr_add(acc[0], fr_add(fr_mul(a0, p0), q0));
-    acc[1] = fr_add(acc[1], fr_add(fr_mul(a1, p1), q1));
-    acc[2] = fr_add(acc[2], fr_add(fr_mul(a2, p2), q2));
+    cl.sync();
   }
+  const uint32_t hq = m / 2;
+  Fr acc0 = fr_zero(), acc1 = fr_zero(), acc2 = fr_zero();
+  for (uint32_t q = gtid; q < 3 * hq; q += gstride) {
+    const uint32_t j = q / 3, t = q - 3 * j;
+    Fr a = fr_load_cg(A, j), p = fr_load_cg(B1, j), c = fr_load_cg(B2, j);
+    if (t > 0) {
+      const Fr da = fr_sub(fr_load_cg(A, j + hq), a), dp = fr_sub(fr_load_cg(B1, j + hq), p),
+               dc = fr_sub(fr_load_cg(B2, j + hq), c);
+      a = fr_add(a, da); p = fr_add(p, dp); c = fr_add(c, dc);
+      if (t == 2) { a = fr_add(a, da); p = fr_add(p, dp); c = fr_add(c, dc); }
+    }
+    const Fr v = fr_add(fr_mul(a, p), c);
+    if (t == 0) acc0 = fr_add(acc0, v);
+    else if (t == 1) acc1 = fr_add(acc1, v);
+    else acc2 = fr_add(acc2, v);
+  }
+  Fr acc[3] = {acc0, acc1, acc2};
   // CTA sum, then into CTA 0's shared memory
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -626,7 +648,7 @@ __device__ Fr tail_round(cg::cluster_group& cl, TailShared& sh, uint32_t* A, uin
       Fr v = fr_zero();
 #pragma unroll
       for (int c = 0; c < kTailCTAs; ++c) v = fr_add(v, sh.part[c][lane]);
-      v = fr_to_canonical(v);
+      v = fr_reduce_once(v);  // plain and below 2r: now canonical
       store_words(proof, off + 32 * (size_t)lane, v);
       sh.canon[lane] = v;
     }
