@@ -78,17 +78,17 @@ struct AbsorbMsg {
 
 template <class Msg>
 __device__ __forceinline__ void sha_message(const Msg& m, uint32_t out[8]) {
-  uint32_t h[8];
-  sha256_init(h);
+  ShaWords8 h;
+  sha256_init(h.w);
 #pragma unroll
   for (int b = 0; b < Msg::NB; ++b) {
-    uint32_t blk[16];
+    ShaWords16 blk;
 #pragma unroll
-    for (int k = 0; k < 16; ++k) blk[k] = m.word(16 * b + k);
-    sha256_compress_compact(h, blk);
+    for (int k = 0; k < 16; ++k) blk.w[k] = m.word(16 * b + k);
+    h = sha256_compress_v(h, blk);
   }
 #pragma unroll
-  for (int i = 0; i < 8; ++i) out[i] = h[i];
+  for (int i = 0; i < 8; ++i) out[i] = h.w[i];
 }
 
 template <int N>
@@ -300,22 +300,30 @@ int launch_layer_init(DevState* S, uint32_t layer, uint32_t c, uint32_t s_i, con
 // S_j(3) = S_j(0) - 3 S_j(1) + 3 S_j(2).  A mul gate costs five products
 // (w x_t is affine in t, so w x_2 = 2 w x_1 - w x_0), an add gate two.
 //
-// Grid: blockIdx.x = chunk of the sorted gate list, blockIdx.y strides over
-// pairs; each thread applies E_t(j) to its own partial sums.
+// Work split: the (pair, gate) items, pair-major, are cut into one
+// contiguous range of equal length per CTA.  A CTA walks its range one pair
+// segment at a time; after each segment it sums S_j(t) over the block and
+// four lanes of warp 0 apply the weights E_t(j) (plain form, so the
+// weighted sums are plain).
 
 template <int BD>
 __global__ void __launch_bounds__(BD) k_copy_round(const uint32_t* __restrict__ T, uint32_t sn, uint32_t h,
                                                    const uint32_t* __restrict__ E, const uint32_t* __restrict__ om,
                                                    const uint4* __restrict__ sg, uint32_t nmul, uint32_t ntot,
-                                                   uint32_t G, uint32_t* partials, DevState* S, uint8_t* proof,
+                                                   uint64_t per_cta, uint32_t* partials, DevState* S, uint8_t* proof,
                                                    size_t off, uint32_t k) {
-  const uint32_t g0 = blockIdx.x * G;
-  const uint32_t g1 = min(ntot, g0 + G);
-  Fr acc[4] = {fr_zero(), fr_zero(), fr_zero(), fr_zero()};
-  for (uint32_t j = blockIdx.y; j < h; j += gridDim.y) {
+  const uint64_t total = (uint64_t)h * ntot;
+  const uint64_t q0 = (uint64_t)blockIdx.x * per_cta;
+  const uint64_t q1 = min(total, q0 + per_cta);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  Fr tot = fr_zero();  // lane t < 4 of warp 0: sum over segments of E_t(j) S_j(t)
+  for (uint64_t seg = q0; seg < q1;) {
+    const uint32_t j = (uint32_t)(seg / ntot);
+    const uint64_t segend = min(q1, (uint64_t)(j + 1) * ntot);
+    const uint32_t g0 = (uint32_t)(seg - (uint64_t)j * ntot), g1 = (uint32_t)(segend - (uint64_t)j * ntot);
     const uint32_t* lo = T + (((size_t)j << sn) << 3);
     const uint32_t* hi = T + (((size_t)(j + h) << sn) << 3);
-    Fr s0 = fr_zero(), s1 = fr_zero(), s2 = fr_zero();
+    Fr s[3] = {fr_zero(), fr_zero(), fr_zero()};
     for (uint32_t q = g0 + threadIdx.x; q < g1; q += BD) {
       const uint4 gi = sg[q];
       const Fr w = fr_load(om, q);
@@ -325,25 +333,45 @@ __global__ void __launch_bounds__(BD) k_copy_round(const uint32_t* __restrict__ 
         const Fr wx0 = fr_mul(w, x0), wx1 = fr_mul(w, x1);
         const Fr wx2 = fr_sub(fr_dbl(wx1), wx0);
         const Fr y2 = fr_sub(fr_dbl(y1), y0);
-        s0 = fr_add(s0, fr_mul(wx0, y0));
-        s1 = fr_add(s1, fr_mul(wx1, y1));
-        s2 = fr_add(s2, fr_mul(wx2, y2));
+        s[0] = fr_add(s[0], fr_mul(wx0, y0));
+        s[1] = fr_add(s[1], fr_mul(wx1, y1));
+        s[2] = fr_add(s[2], fr_mul(wx2, y2));
       } else {
         const Fr a0 = fr_mul(w, fr_add(x0, y0)), a1 = fr_mul(w, fr_add(x1, y1));
-        s0 = fr_add(s0, a0);
-        s1 = fr_add(s1, a1);
-        s2 = fr_add(s2, fr_sub(fr_dbl(a1), a0));
+        s[0] = fr_add(s[0], a0);
+        s[1] = fr_add(s[1], a1);
+        s[2] = fr_add(s[2], fr_sub(fr_dbl(a1), a0));
       }
     }
-    const Fr d21 = fr_sub(s2, s1);
-    const Fr s3 = fr_add(s0, fr_add(d21, fr_dbl(d21)));
-    const Fr e0 = fr_load(E, j), e1 = fr_load(E, j + h);
-    const Fr de = fr_sub(e1, e0);
-    const Fr e2 = fr_add(e1, de), e3 = fr_add(e2, de);
-    acc[0] = fr_add(acc[0], fr_mul(e0, s0));
-    acc[1] = fr_add(acc[1], fr_mul(e1, s1));
-    acc[2] = fr_add(acc[2], fr_mul(e2, s2));
-    acc[3] = fr_add(acc[3], fr_mul(e3, s3));
+    block_sum<BD, 3>(s);  // thread 0 holds S_j(0..2) for this segment
+    if (warp == 0) {
+      Fr sj[3];
+#pragma unroll
+      for (int t = 0; t < 3; ++t)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) sj[t].v[i] = __shfl_sync(0xffffffffu, s[t].v[i], 0);
+      if (lane < 4) {
+        const Fr e0 = fr_load(E, j), e1 = fr_load(E, j + h);
+        const Fr de = fr_sub(e1, e0);
+        Fr et = e0, st;
+        if (lane == 3) {
+          const Fr d21 = fr_sub(sj[2], sj[1]);
+          st = fr_add(sj[0], fr_add(d21, fr_dbl(d21)));  // S(3) = S(0) + 3 (S(2) - S(1))
+        } else {
+          st = lane == 0 ? sj[0] : lane == 1 ? sj[1] : sj[2];
+        }
+        for (int t = 0; t < lane; ++t) et = fr_add(et, de);
+        tot = fr_add(tot, fr_mul(et, st));
+      }
+    }
+    seg = segend;
+  }
+  Fr acc[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc[t].v[i] = __shfl_sync(0xffffffffu, tot.v[i], t);
+    if (threadIdx.x != 0) acc[t] = fr_zero();
   }
   if (grid_sum_last_block<BD, 4>(acc, partials, S) && threadIdx.x < 32) round_finalize<4>(S, acc, proof, off, &S->rb[k]);
 }
@@ -352,30 +380,21 @@ int launch_copy_round(const uint32_t* T, uint32_t sn, uint32_t h, const uint32_t
                       const DevLayer& L, uint32_t* partials, DevState* S, uint8_t* proof, size_t off, uint32_t k,
                       void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
-  const uint32_t ntot = L.ntot;
-  // about eight gates per thread for each pair when one chunk covers the layer
-  int bd = 256;
-  while (bd > 32 && (uint32_t)bd * 8 > ntot) bd >>= 1;
-  const uint32_t target = kSMs * 6;
-  uint32_t chunks = 1, pairblocks;
-  if (h >= target) {
-    pairblocks = target;
-  } else {
-    pairblocks = h;
-    uint32_t want = (target + h - 1) / h;
-    uint32_t maxc = (ntot + bd - 1) / bd;
-    chunks = std::max(1u, std::min(want, maxc));
+  constexpr int BD = 256;
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_copy_round<BD>, BD, 0) != cudaSuccess || n < 1) n = 1;
+    per_sm = n;
   }
-  uint32_t G = (ntot + chunks - 1) / chunks;
-  G = (G + bd - 1) / bd * bd;
-  chunks = (ntot + G - 1) / G;
-  dim3 grid(chunks, pairblocks);
-  switch (bd) {
-    case 256: k_copy_round<256><<<grid, 256, 0, st>>>(T, sn, h, E, omega_s, L.sgate, L.nmul, ntot, G, partials, S, proof, off, k); break;
-    case 128: k_copy_round<128><<<grid, 128, 0, st>>>(T, sn, h, E, omega_s, L.sgate, L.nmul, ntot, G, partials, S, proof, off, k); break;
-    case 64: k_copy_round<64><<<grid, 64, 0, st>>>(T, sn, h, E, omega_s, L.sgate, L.nmul, ntot, G, partials, S, proof, off, k); break;
-    default: k_copy_round<32><<<grid, 32, 0, st>>>(T, sn, h, E, omega_s, L.sgate, L.nmul, ntot, G, partials, S, proof, off, k); break;
-  }
+  const uint64_t total = (uint64_t)h * L.ntot;
+  // equal contiguous ranges, at least four items per thread, one wave of CTAs
+  uint64_t nc = std::min<uint64_t>((uint64_t)kSMs * per_sm, (total + 4 * BD - 1) / (4 * BD));
+  nc = std::max<uint64_t>(1, std::min<uint64_t>(nc, kMaxPartials));
+  const uint64_t per_cta = (total + nc - 1) / nc;
+  nc = (total + per_cta - 1) / per_cta;
+  k_copy_round<BD><<<(unsigned)nc, BD, 0, st>>>(T, sn, h, E, omega_s, L.sgate, L.nmul, L.ntot, per_cta, partials, S,
+                                                proof, off, k);
   return post_launch();
 }
 
