@@ -277,6 +277,9 @@ def run_ours(args):
     S.profile_enable(0x1FF)
     step(inputs)
     torch.cuda.synchronize(dev)
+    rounds = S.profile_launches(S.PROF_COPY_ROUND)
+    per_round = [{"ms": round(m, 4), "fr_mults": w, "gmul_s": round(w / m / 1e6, 2) if m else None}
+                 for m, w in rounds[:max(1, len(rounds) // max(1, circ.depth))]]
     breakdown = {}
     for k, name in S.PROF_KINDS.items():
         kms, kn, kw = S.profile_read(k)
@@ -304,7 +307,7 @@ def run_ours(args):
                              f"{gc.eval_bytes / 2**30:.1f} GiB, every step re-evaluates and re-reads them"},
             "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
             "parity": {"proof_matches_oracle_sha256": parity},
-            "breakdown_ms_per_step": breakdown}
+            "breakdown_ms_per_step": breakdown, "copy_rounds_first_layer": per_round}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)

@@ -178,6 +178,10 @@ int sisu_microbench(int kind, uint32_t blocks, uint32_t threads, uint32_t iters,
  * add gate, 4 for the copy weights), then forgets them. */
 int sisu_profile_enable(uint32_t kind_mask);
 int sisu_profile_read(uint32_t kind, double* ms, uint64_t* launches, double* fr_mults);
+/* The recorded launches of one kind one by one, oldest first, without
+ * forgetting them: up to `cap` milliseconds and field-product counts; *n =
+ * the number recorded. */
+int sisu_profile_launches(uint32_t kind, double* ms, double* fr_mults, size_t cap, size_t* n);
 
 /* Number of kernels this library launched so far in this process. */
 uint64_t sisu_kernel_launches(void);

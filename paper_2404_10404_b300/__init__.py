@@ -30,7 +30,7 @@ ENTRY_POINTS = [
     "sisu_transcript_create", "sisu_transcript_destroy", "sisu_gkr_prove", "sisu_gkr_prove_into",
     "sisu_gkr_verify", "sisu_fr_batch", "sisu_statement_digest", "sisu_microbench",
     "sisu_kernel_launches", "sisu_free", "sisu_last_error", "sisu_version",
-    "sisu_profile_enable", "sisu_profile_read",
+    "sisu_profile_enable", "sisu_profile_read", "sisu_profile_launches",
 ]
 PROF_COPY_ROUND, PROF_COPY_FOLD, PROF_EVAL, PROF_GATE_ROUND, PROF_DIGEST = 0, 1, 2, 3, 4
 PROF_LAYER_INIT, PROF_PHASE_INIT, PROF_TRANSCRIPT, PROF_INPUTS = 5, 6, 7, 8
@@ -83,6 +83,8 @@ def _load():
         "sisu_profile_enable": ([u32], ctypes.c_int),
         "sisu_profile_read": ([u32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64),
                                ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+        "sisu_profile_launches": ([u32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), sz,
+                                   ctypes.POINTER(sz)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -312,6 +314,15 @@ def microbench(kind: int, blocks: int, threads: int, iters: int, stream=None):
 def profile_enable(kind_mask: int):
     """Time the launches of the kernel kinds in the mask with CUDA events."""
     _check(_lib.sisu_profile_enable(kind_mask))
+
+
+def profile_launches(kind: int, cap: int = 4096):
+    """[(milliseconds, field products)] of the recorded launches of one kind."""
+    ms = (ctypes.c_double * cap)()
+    w = (ctypes.c_double * cap)()
+    n = ctypes.c_size_t()
+    _check(_lib.sisu_profile_launches(kind, ms, w, cap, ctypes.byref(n)))
+    return [(ms[i], w[i]) for i in range(min(cap, n.value))]
 
 
 def profile_read(kind: int):

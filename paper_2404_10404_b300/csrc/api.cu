@@ -111,6 +111,24 @@ extern "C" int sisu_profile_enable(uint32_t kind_mask) {
   return SISU_OK;
 }
 
+extern "C" int sisu_profile_launches(uint32_t kind, double* ms, double* fr_mults, size_t cap, size_t* n) {
+  size_t k = 0;
+  for (ProfRec& r : g_prof) {
+    if (r.kind != kind) continue;
+    cudaError_t e = cudaEventSynchronize(r.b);
+    if (e != cudaSuccess) return cuda_fail(e, "profile events");
+    if (k < cap) {
+      float x = 0;
+      cudaEventElapsedTime(&x, r.a, r.b);
+      if (ms) ms[k] = x;
+      if (fr_mults) fr_mults[k] = r.work;
+    }
+    ++k;
+  }
+  if (n) *n = k;
+  return SISU_OK;
+}
+
 extern "C" int sisu_profile_read(uint32_t kind, double* ms, uint64_t* launches, double* fr_mults) {
   double t = 0, w = 0;
   uint64_t n = 0;

@@ -20,6 +20,10 @@ def main():
                               ("fr_mul_check", 6, 64)):
         ms, ops = S.microbench(kind, 148 * 8, 256, iters, st)
         out[name] = {"ms": ms, "ops": ops, "per_s": ops / (ms / 1e3)}
+    # the product rate at the occupancy of the prover kernels (1 and 2 CTAs of 256 per SM)
+    for name, blocks in (("fr_mul_1cta_per_sm", 148), ("fr_mul_2cta_per_sm", 296)):
+        ms, ops = S.microbench(2, blocks, 256, 512, st)
+        out[name] = {"ms": ms, "ops": ops, "per_s": ops / (ms / 1e3)}
     print(json.dumps(out))
 
 
