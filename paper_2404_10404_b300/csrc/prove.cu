@@ -301,10 +301,20 @@ int launch_layer_init(DevState* S, uint32_t layer, uint32_t c, uint32_t s_i, con
 // (w x_t is affine in t, so w x_2 = 2 w x_1 - w x_0), an add gate two.
 //
 // Work split: the (pair, gate) items, pair-major, are cut into one
-// contiguous range of equal length per CTA.  A CTA walks its range one pair
+// contiguous range per CTA of equal cost (a mul gate costs 5 products, an
+// add gate 2; gates are sorted mul first, so equal item counts would leave
+// some CTAs 2.5 times the work of others).  A CTA walks its range one pair
 // segment at a time; after each segment it sums S_j(t) over the block and
 // four lanes of warp 0 apply the weights E_t(j) (plain form, so the
 // weighted sums are plain).
+
+// item position of cost position X (rounded up to a gate boundary)
+__device__ __forceinline__ uint64_t item_at_cost(uint64_t X, uint32_t nmul, uint32_t ntot, uint64_t pair_cost) {
+  const uint64_t j = X / pair_cost, r = X - j * pair_cost;
+  const uint64_t mc = 5ull * nmul;
+  const uint64_t g = r < mc ? (r + 4) / 5 : nmul + (r - mc + 1) / 2;
+  return j * ntot + min(g, (uint64_t)ntot);
+}
 
 template <int BD>
 __global__ void __launch_bounds__(BD) k_copy_round(const uint32_t* __restrict__ T, uint32_t sn, uint32_t h,
@@ -312,9 +322,10 @@ __global__ void __launch_bounds__(BD) k_copy_round(const uint32_t* __restrict__ 
                                                    const uint4* __restrict__ sg, uint32_t nmul, uint32_t ntot,
                                                    uint64_t per_cta, uint32_t* partials, DevState* S, uint8_t* proof,
                                                    size_t off, uint32_t k) {
-  const uint64_t total = (uint64_t)h * ntot;
-  const uint64_t q0 = (uint64_t)blockIdx.x * per_cta;
-  const uint64_t q1 = min(total, q0 + per_cta);
+  const uint64_t pair_cost = 5ull * nmul + 2ull * (ntot - nmul);
+  const uint64_t total_cost = (uint64_t)h * pair_cost;
+  const uint64_t q0 = item_at_cost(min(total_cost, (uint64_t)blockIdx.x * per_cta), nmul, ntot, pair_cost);
+  const uint64_t q1 = item_at_cost(min(total_cost, (uint64_t)(blockIdx.x + 1) * per_cta), nmul, ntot, pair_cost);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   Fr tot = fr_zero();  // lane t < 4 of warp 0: sum over segments of E_t(j) S_j(t)
   for (uint64_t seg = q0; seg < q1;) {
@@ -388,11 +399,14 @@ int launch_copy_round(const uint32_t* T, uint32_t sn, uint32_t h, const uint32_t
     per_sm = n;
   }
   const uint64_t total = (uint64_t)h * L.ntot;
-  // equal contiguous ranges, at least four items per thread, one wave of CTAs
-  uint64_t nc = std::min<uint64_t>((uint64_t)kSMs * per_sm, (total + 4 * BD - 1) / (4 * BD));
+  const uint64_t pair_cost = 5ull * L.nmul + 2ull * (L.ntot - L.nmul);
+  // contiguous ranges of equal cost: one wave of CTAs, and for small rounds
+  // about one item per thread (short serial chains)
+  uint64_t nc = std::min<uint64_t>((uint64_t)kSMs * per_sm, (total + BD - 1) / BD);
   nc = std::max<uint64_t>(1, std::min<uint64_t>(nc, kMaxPartials));
-  const uint64_t per_cta = (total + nc - 1) / nc;
-  nc = (total + per_cta - 1) / per_cta;
+  const uint64_t total_cost = (uint64_t)h * pair_cost;
+  const uint64_t per_cta = (total_cost + nc - 1) / nc;  // cost units per CTA
+  nc = (total_cost + per_cta - 1) / per_cta;
   k_copy_round<BD><<<(unsigned)nc, BD, 0, st>>>(T, sn, h, E, omega_s, L.sgate, L.nmul, L.ntot, per_cta, partials, S,
                                                 proof, off, k);
   return post_launch();
