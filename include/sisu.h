@@ -156,6 +156,26 @@ int sisu_fr_batch(int op, const uint8_t* a, const uint8_t* b, uint8_t* out, size
  * up, digest = H(root || u64le len || 0x03).  out: 32 host bytes. */
 int sisu_statement_digest(const uint8_t* data, size_t len, uint8_t* out, void* stream);
 
+/* The same digest without any allocation, for callers that must not let a
+ * library allocate device memory: a serving loop or framework that owns
+ * all device memory through its own pool (cudaMalloc can synchronise the
+ * device and fragments the pool) or code running while that pool's lock is
+ * held.  (The paper has no counterpart: this is a property of the library.)
+ *   data: device bytes, len <= 67108864 (64 MiB); larger inputs return
+ *         SISU_ERR_TOO_LARGE with a message naming the limit.
+ *   out:  32 device bytes the caller provides, written by work enqueued on
+ *         `stream` (the call does not wait).
+ * Scratch: a fixed 4 MiB array in the library's device memory, which every
+ * GPU that loads the library holds until the process exits.  The first call
+ * on a device looks up that array's device address (cudaGetSymbolAddress)
+ * and caches it, so make the first call on each device before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU (on
+ * different streams, or from different threads) race and must be ordered
+ * by the caller.  Nothing in the array needs to start at zero.  No
+ * cudaMalloc, cudaFree or other allocating routine is called.
+ * Errors: INVALID_ARG, TOO_LARGE, CUDA. */
+int sisu_statement_digest_noalloc(const uint8_t* data, size_t len, uint8_t* out, void* stream);
+
 /* Integer-pipe microbenchmarks used for the roofline: kind 0 = independent
  * 32-bit multiply-add chains (mad.lo), kind 1 = mad.hi chains, kind 2 =
  * Montgomery products as the kernels call them, kind 3 = the same products

@@ -30,7 +30,7 @@ ENTRY_POINTS = [
     "sisu_transcript_create", "sisu_transcript_destroy", "sisu_gkr_prove", "sisu_gkr_prove_into",
     "sisu_gkr_verify", "sisu_fr_batch", "sisu_statement_digest", "sisu_microbench",
     "sisu_kernel_launches", "sisu_free", "sisu_last_error", "sisu_version",
-    "sisu_profile_enable", "sisu_profile_read", "sisu_profile_launches",
+    "sisu_profile_enable", "sisu_profile_read", "sisu_profile_launches", "sisu_statement_digest_noalloc",
 ]
 PROF_COPY_ROUND, PROF_COPY_FOLD, PROF_EVAL, PROF_GATE_ROUND, PROF_DIGEST = 0, 1, 2, 3, 4
 PROF_LAYER_INIT, PROF_PHASE_INIT, PROF_TRANSCRIPT, PROF_INPUTS = 5, 6, 7, 8
@@ -74,6 +74,7 @@ def _load():
         "sisu_gkr_verify": ([vp, u8p, u8p, u8p, sz, u8p, sz], ctypes.c_int),
         "sisu_fr_batch": ([ctypes.c_int, vp, vp, vp, sz, vp], ctypes.c_int),
         "sisu_statement_digest": ([vp, sz, u8p, vp], ctypes.c_int),
+        "sisu_statement_digest_noalloc": ([vp, sz, vp, vp], ctypes.c_int),
         "sisu_microbench": ([ctypes.c_int, u32, u32, u32, vp, ctypes.POINTER(ctypes.c_double),
                              ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
         "sisu_kernel_launches": ([], ctypes.c_uint64),
@@ -302,6 +303,15 @@ def statement_digest(data, length: int, stream=None) -> bytes:
     out = ctypes.create_string_buffer(32)
     _check(_lib.sisu_statement_digest(p, length, ctypes.cast(out, ctypes.c_void_p), _stream(stream)))
     return out.raw
+
+
+def statement_digest_noalloc(data, length: int, out, stream=None):
+    """The statement digest written to the 32-byte device buffer ``out``,
+    using the library's fixed scratch instead of any allocation (inputs up
+    to 64 MiB; see include/sisu.h for who needs this and its limits)."""
+    p, _, keep = _ptr(data)
+    po, _, keep_out = _ptr(out)
+    _check(_lib.sisu_statement_digest_noalloc(p, length, po, _stream(stream)))
 
 
 def microbench(kind: int, blocks: int, threads: int, iters: int, stream=None):

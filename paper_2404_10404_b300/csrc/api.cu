@@ -36,6 +36,10 @@ static int fail(int code, const char* fmt, ...) {
   return code;
 }
 
+namespace sisu {
+int report_error(int code, const char* msg) { return fail(code, "%s", msg); }
+}  // namespace sisu
+
 static int cuda_fail(cudaError_t e, const char* what) {
   return fail(SISU_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }

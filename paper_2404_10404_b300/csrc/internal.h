@@ -71,6 +71,8 @@ struct HostCircuit {
 // kernel launch wrappers (kernels.cu); all return cudaError_t as int
 
 uint64_t launches_add(uint64_t n);
+// sets the calling thread's sisu_last_error() message, returns code
+int report_error(int code, const char* msg);
 
 int launch_inputs_to_mont(const uint32_t* in, uint32_t* V, uint32_t c, uint32_t s, uint32_t Creal,
                           uint32_t wreal, uint32_t* err, void* stream);
