@@ -134,6 +134,21 @@ int sisu_gkr_prove(const sisu_circuit* circ, sisu_eval* ev, const sisu_transcrip
 int sisu_gkr_prove_into(const sisu_circuit* circ, sisu_eval* ev, const sisu_transcript* tr,
                         void* stream, uint8_t* proof, size_t cap, size_t* proof_len);
 
+/* Batched proving (many independent instances): proves every
+ * (circs[i], evals[i]) with one transcript domain, spreading the instances
+ * over `concurrency` library-owned streams (0 = 4) so that one instance's
+ * latency-bound phases overlap the others' arithmetic.  The work starts
+ * after the caller's prior work on `stream`, and the call returns when
+ * every proof is in proofs[i] (caps[i] bytes each; lens[i] = length, may be
+ * NULL).  Each eval handle may appear once.  Proof bytes are identical to
+ * sisu_gkr_prove_into's.  From the second proof on a handle, its launch
+ * sequence is replayed from a CUDA graph (also for sisu_gkr_prove_into),
+ * unless per-kernel profiling is on or SISU_NO_GRAPHS is set.
+ * Errors: as sisu_gkr_prove_into, INVALID_ARG for a repeated handle. */
+int sisu_gkr_prove_batch(const sisu_circuit* const* circs, sisu_eval* const* evals, uint32_t n,
+                         const sisu_transcript* tr, void* stream, uint32_t concurrency, uint8_t* const* proofs,
+                         const size_t* caps, size_t* lens);
+
 /* Host verifier: replays the transcript, checks g(0) + g(1) = claim in
  * every round (Sec. 3.2.1), the final identity of every layer by summing
  * the wiring predicates, the output claim from `outputs` and the input

@@ -31,6 +31,7 @@ ENTRY_POINTS = [
     "sisu_gkr_verify", "sisu_fr_batch", "sisu_statement_digest", "sisu_microbench",
     "sisu_kernel_launches", "sisu_free", "sisu_last_error", "sisu_version",
     "sisu_profile_enable", "sisu_profile_read", "sisu_profile_launches", "sisu_statement_digest_noalloc",
+    "sisu_gkr_prove_batch",
 ]
 PROF_COPY_ROUND, PROF_COPY_FOLD, PROF_EVAL, PROF_GATE_ROUND, PROF_DIGEST = 0, 1, 2, 3, 4
 PROF_LAYER_INIT, PROF_PHASE_INIT, PROF_TRANSCRIPT, PROF_INPUTS = 5, 6, 7, 8
@@ -72,6 +73,8 @@ def _load():
         "sisu_gkr_prove": ([vp, vp, vp, vp, pp, ctypes.POINTER(sz)], ctypes.c_int),
         "sisu_gkr_prove_into": ([vp, vp, vp, vp, u8p, sz, ctypes.POINTER(sz)], ctypes.c_int),
         "sisu_gkr_verify": ([vp, u8p, u8p, u8p, sz, u8p, sz], ctypes.c_int),
+        "sisu_gkr_prove_batch": ([ctypes.POINTER(vp), ctypes.POINTER(vp), u32, vp, vp, u32, ctypes.POINTER(vp),
+                                  ctypes.POINTER(sz), ctypes.POINTER(sz)], ctypes.c_int),
         "sisu_fr_batch": ([ctypes.c_int, vp, vp, vp, sz, vp], ctypes.c_int),
         "sisu_statement_digest": ([vp, sz, u8p, vp], ctypes.c_int),
         "sisu_statement_digest_noalloc": ([vp, sz, vp, vp], ctypes.c_int),
@@ -280,6 +283,22 @@ def prove_alloc(circ: Circuit, ev: Eval, transcript: Transcript | None = None, s
         return ctypes.string_at(p, ln.value)
     finally:
         _lib.sisu_free(p)
+
+
+def prove_batch(circs, evals, transcript: Transcript | None = None, stream=None, concurrency: int = 0):
+    """Proofs of independent instances on concurrent streams (``sisu_gkr_prove_batch``)."""
+    n = len(circs)
+    if n != len(evals):
+        raise SisuError(-1, "circuits and evals differ in number")
+    bufs = [ctypes.create_string_buffer(c.proof_len) for c in circs]
+    ch = (ctypes.c_void_p * n)(*[c.h.value for c in circs])
+    eh = (ctypes.c_void_p * n)(*[e.h.value for e in evals])
+    ph = (ctypes.c_void_p * n)(*[ctypes.cast(b, ctypes.c_void_p).value for b in bufs])
+    caps = (ctypes.c_size_t * n)(*[c.proof_len for c in circs])
+    lens = (ctypes.c_size_t * n)()
+    _check(_lib.sisu_gkr_prove_batch(ch, eh, n, transcript.h if transcript else None, _stream(stream),
+                                     concurrency, ph, caps, lens))
+    return [bufs[i].raw[:lens[i]] for i in range(n)]
 
 
 def verify(circ: Circuit, inputs: bytes, outputs: bytes, proof: bytes, domain: bytes | None = None) -> int:

@@ -11,6 +11,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <new>
 
 #include "../../include/sisu.h"
@@ -180,7 +181,17 @@ struct Workspace {
   uint8_t* proof = nullptr;
   uint8_t* host = nullptr;  // pinned: proof bytes followed by the error word
   size_t proof_len = 0;
+  // the proof's launch sequence captured as a CUDA graph (same circuit,
+  // workspace and transcript domain give the same launches every time)
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  uint8_t gdomain[kMaxDomain];
+  uint32_t gdlen = 0;
+  bool gvalid = false;
+  int proofs = 0;  // proofs enqueued so far on this workspace
   ~Workspace() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
     if (dev) cudaFree(dev);
     if (host) cudaFreeHost(host);
   }
@@ -704,8 +715,76 @@ static int enqueue_prove(const sisu_circuit* cc, sisu_eval* ev, const sisu_trans
   return SISU_OK;
 }
 
-extern "C" int sisu_gkr_prove_into(const sisu_circuit* circ, sisu_eval* ev, const sisu_transcript* tr, void* stream,
-                                   uint8_t* proof, size_t cap, size_t* proof_len) {
+// One whole proof and the copies of its bytes and error word to pinned host
+// memory, enqueued on `st` (no host wait).
+static int enqueue_proof_and_copy(const sisu_circuit* cc, sisu_eval* ev, const sisu_transcript* tr, cudaStream_t st) {
+  Workspace& w = *ev->ws;
+  const size_t n = cc->hc.proof_len();
+  int rc = enqueue_prove(cc, ev, tr, st);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(w.host, w.proof, n, cudaMemcpyDeviceToHost, st), "proof copy");
+  CK(cudaMemcpyAsync(w.host + ((n + 3) & ~(size_t)3), &w.S->error, 4, cudaMemcpyDeviceToHost, st), "flag copy");
+  return SISU_OK;
+}
+
+static bool graphs_enabled() {
+  static int on = -1;
+  if (on < 0) {
+    const char* e = getenv("SISU_NO_GRAPHS");
+    on = (e && e[0] && e[0] != '0') ? 0 : 1;
+  }
+  return on == 1;
+}
+
+// Enqueue a proof on `st`: replay the workspace's graph (captured on the
+// second proof of a handle, when every lazily initialised launch parameter
+// is settled), or launch kernel by kernel while profiling or on the first
+// proof.
+static int launch_proof(const sisu_circuit* cc, sisu_eval* ev, const sisu_transcript* tr, cudaStream_t st) {
+  Workspace& w = *ev->ws;
+  const uint8_t* dom = tr ? tr->domain : (const uint8_t*)kDefaultDomain;
+  const uint32_t dlen = tr ? tr->len : (uint32_t)strlen(kDefaultDomain);
+  if (!graphs_enabled() || g_prof_mask != 0 || w.proofs++ == 0) return enqueue_proof_and_copy(cc, ev, tr, st);
+  if (!w.gvalid || w.gdlen != dlen || memcmp(w.gdomain, dom, dlen) != 0) {
+    if (w.exec) {
+      cudaGraphExecDestroy(w.exec);
+      w.exec = nullptr;
+    }
+    w.gvalid = false;
+    if (!w.cap_stream) CK(cudaStreamCreateWithFlags(&w.cap_stream, cudaStreamNonBlocking), "stream create");
+    CK(cudaStreamBeginCapture(w.cap_stream, cudaStreamCaptureModeThreadLocal), "graph capture");
+    int rc = enqueue_proof_and_copy(cc, ev, tr, w.cap_stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(w.cap_stream, &g);
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "graph capture");
+    e = cudaGraphInstantiate(&w.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+    memcpy(w.gdomain, dom, dlen);
+    w.gdlen = dlen;
+    w.gvalid = true;
+  }
+  CK(cudaGraphLaunch(w.exec, st), "graph launch");
+  return SISU_OK;
+}
+
+// After the proof's stream work completed: check the device error word and
+// copy the bytes out.
+static int finish_proof(const sisu_circuit* cc, sisu_eval* ev, uint8_t* proof) {
+  Workspace& w = *ev->ws;
+  const size_t n = cc->hc.proof_len();
+  uint32_t err;
+  memcpy(&err, w.host + ((n + 3) & ~(size_t)3), 4);
+  if (err) return fail(SISU_ERR_CUDA, "device-side check failed (code %u)", err);
+  memcpy(proof, w.host, n);
+  return SISU_OK;
+}
+
+static int prepare_proof(const sisu_circuit* circ, sisu_eval* ev, uint8_t* proof, size_t cap, size_t* proof_len) {
   if (!circ || !ev || !proof) return fail(SISU_ERR_INVALID_ARG, "NULL circuit, eval or proof buffer");
   if (ev->circ != circ) return fail(SISU_ERR_INVALID_ARG, "eval handle belongs to another circuit");
   const size_t n = circ->hc.proof_len();
@@ -715,17 +794,79 @@ extern "C" int sisu_gkr_prove_into(const sisu_circuit* circ, sisu_eval* ev, cons
     int rc = workspace_alloc(ev);
     if (rc) return rc;
   }
-  cudaStream_t st = (cudaStream_t)stream;
-  Workspace& w = *ev->ws;
-  int rc = enqueue_prove(circ, ev, tr, st);
+  return SISU_OK;
+}
+
+extern "C" int sisu_gkr_prove_into(const sisu_circuit* circ, sisu_eval* ev, const sisu_transcript* tr, void* stream,
+                                   uint8_t* proof, size_t cap, size_t* proof_len) {
+  int rc = prepare_proof(circ, ev, proof, cap, proof_len);
   if (rc) return rc;
-  CK(cudaMemcpyAsync(w.host, w.proof, n, cudaMemcpyDeviceToHost, st), "proof copy");
-  CK(cudaMemcpyAsync(w.host + ((n + 3) & ~(size_t)3), &w.S->error, 4, cudaMemcpyDeviceToHost, st), "flag copy");
+  cudaStream_t st = (cudaStream_t)stream;
+  rc = launch_proof(circ, ev, tr, st);
+  if (rc) return rc;
   CK(cudaStreamSynchronize(st), "prove");
-  uint32_t err;
-  memcpy(&err, w.host + ((n + 3) & ~(size_t)3), 4);
-  if (err) return fail(SISU_ERR_CUDA, "device-side check failed (code %u)", err);
-  memcpy(proof, w.host, n);
+  return finish_proof(circ, ev, proof);
+}
+
+// ---------------------------------------------------------------------------
+// batched proving: independent instances on concurrent streams
+
+namespace {
+std::mutex g_batch_mu;
+std::vector<cudaStream_t> g_batch_streams[256];
+std::vector<cudaEvent_t> g_batch_events[256];
+}  // namespace
+
+extern "C" int sisu_gkr_prove_batch(const sisu_circuit* const* circs, sisu_eval* const* evals, uint32_t n,
+                                    const sisu_transcript* tr, void* stream, uint32_t concurrency,
+                                    uint8_t* const* proofs, const size_t* caps, size_t* lens) {
+  if (n == 0) return SISU_OK;
+  if (!circs || !evals || !proofs || !caps) return fail(SISU_ERR_INVALID_ARG, "NULL array");
+  for (uint32_t i = 0; i < n; ++i)
+    for (uint32_t j = 0; j < i; ++j)
+      if (evals[i] == evals[j]) return fail(SISU_ERR_INVALID_ARG, "eval handle %u appears twice in the batch", i);
+  for (uint32_t i = 0; i < n; ++i) {
+    int rc = prepare_proof(circs[i], evals[i], proofs[i], caps[i], lens ? &lens[i] : nullptr);
+    if (rc) return rc;
+  }
+  const uint32_t K = std::max(1u, std::min(concurrency ? concurrency : 4u, 32u));
+  int dev = 0;
+  CK(cudaGetDevice(&dev), "cudaGetDevice");
+  if (dev < 0 || dev >= 256) return fail(SISU_ERR_CUDA, "device ordinal %d", dev);
+  std::lock_guard<std::mutex> lock(g_batch_mu);
+  auto& pool = g_batch_streams[dev];
+  auto& evs = g_batch_events[dev];
+  while (pool.size() < K) {
+    cudaStream_t s;
+    CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "stream create");
+    pool.push_back(s);
+    cudaEvent_t e;
+    CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event create");
+    evs.push_back(e);
+  }
+  while (evs.size() < K + 1) {
+    cudaEvent_t e;
+    CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event create");
+    evs.push_back(e);
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  // the pool streams start after the caller's prior work on `stream`
+  CK(cudaEventRecord(evs[K], st), "event record");
+  for (uint32_t k = 0; k < K; ++k) CK(cudaStreamWaitEvent(pool[k], evs[K], 0), "stream wait");
+  for (uint32_t i = 0; i < n; ++i) {
+    int rc = launch_proof(circs[i], evals[i], tr, pool[i % K]);
+    if (rc) return rc;
+  }
+  // the caller's stream continues after every instance
+  for (uint32_t k = 0; k < K; ++k) {
+    CK(cudaEventRecord(evs[k], pool[k]), "event record");
+    CK(cudaStreamWaitEvent(st, evs[k], 0), "stream wait");
+  }
+  CK(cudaStreamSynchronize(st), "prove batch");
+  for (uint32_t i = 0; i < n; ++i) {
+    int rc = finish_proof(circs[i], evals[i], proofs[i]);
+    if (rc) return rc;
+  }
   return SISU_OK;
 }
 

@@ -1,0 +1,66 @@
+"""Batched proving of independent instances of uneven size (SURVEY's batched
+configuration, scaled to sizes the oracle finishes quickly): every proof
+equals the oracle's and the single-instance GPU proof, at every concurrency,
+on repeated calls (CUDA-graph replay) and in any order."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    import paper_2404_10404_b300 as S
+    return S
+
+
+def _instances():
+    rng = np.random.default_rng(7)
+    out = []
+    for j in range(7):
+        C = int(2 ** rng.integers(2, 8))
+        W = int(2 ** rng.integers(3, 9))
+        d = int(rng.integers(1, 5))
+        out.append(synth.uniform_circuit(4 * (1 << 32) + j, C, [W] * (d + 1), 60, name=f"b{j}"))
+    out.append(synth.micro(99, 37, [300, 257, 513], 70))  # padded shape in the mix
+    return out
+
+
+@pytest.fixture(scope="module")
+def batch(S, oracle):
+    circs = _instances()
+    xs = [synth.fr_bytes(synth.inputs_for(c)) for c in circs]
+    gcs = [S.Circuit.from_spec(c) for c in circs]
+    evs = [S.Eval(g, x) for g, x in zip(gcs, xs)]
+    want = [oracle.prove(c, x) for c, x in zip(circs, xs)]
+    return circs, xs, gcs, evs, want
+
+
+@pytest.mark.parametrize("k", [1, 3, 8])
+def test_batch_equals_oracle(S, batch, k):
+    circs, xs, gcs, evs, want = batch
+    for _ in range(2):  # second call replays the captured graphs
+        assert S.prove_batch(gcs, evs, concurrency=k) == want
+
+
+def test_batch_equals_single_and_order_free(S, batch):
+    circs, xs, gcs, evs, want = batch
+    singles = [S.prove(g, e) for g, e in zip(gcs, evs)]
+    assert singles == want
+    order = [5, 0, 7, 2, 6, 1, 3, 4]
+    got = S.prove_batch([gcs[i] for i in order], [evs[i] for i in order], concurrency=4)
+    assert got == [want[i] for i in order]
+    for g, x, e, p in zip(gcs, xs, evs, want):
+        assert S.verify(g, x, e.outputs(), p) == 0
+
+
+def test_batch_domain_and_repeat_rejected(S, batch, oracle):
+    circs, xs, gcs, evs, want = batch
+    tr = S.Transcript(b"batch-domain")
+    got = S.prove_batch(gcs[:3], evs[:3], tr, concurrency=2)
+    assert got == [oracle.prove(c, x, b"batch-domain") for c, x in zip(circs[:3], xs[:3])]
+    with pytest.raises(S.SisuError) as e:
+        S.prove_batch([gcs[0], gcs[0]], [evs[0], evs[0]])
+    assert e.value.code == -1
