@@ -364,7 +364,7 @@ def run_batched(args):
             S.prove(g, e, None, stream)
         if tuned is None:  # pick the concurrency on the first wave
             best = None
-            for k in (1, 2, 4, 8, 16):
+            for k in (1, 2, 4, 8, 16, 32):
                 S.prove_batch(gcs, evs, None, stream, k)
                 torch.cuda.synchronize(dev)
                 ev0.record(stream)
@@ -407,13 +407,115 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# served: Poisson arrivals into the continuous-batching server
+
+def run_served(args):
+    import numpy as np
+    import torch
+
+    import paper_2404_10404_b300 as S
+    import synth
+    from paper_2404_10404_b300.build import build
+
+    torch.cuda.set_device(0)
+    build()
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(5)
+    # job templates: instances drawn as in the batched workload; each job is
+    # one template with its own inputs stored once (pinned host memory)
+    templates = [synth.batched_instance(j) for j in range(args.templates)]
+    gcs = [S.Circuit.from_spec(c) for c in templates]
+    pins = []
+    for c in templates:
+        xb = synth.fr_bytes(synth.inputs_for(c))
+        pins.append(torch.frombuffer(bytearray(xb), dtype=torch.uint8).pin_memory())
+    log(f"[bench] served: {len(templates)} templates ready")
+    # plain path, one job at a time: evaluation from pinned host inputs + proof
+    stream = torch.cuda.Stream(device=dev)
+    plain_s, alone = [], []
+    for g, x in zip(gcs, pins):
+        ev = S.Eval(g, x, stream)
+        p = S.prove(g, ev, None, stream)
+        S.prove(g, ev, None, stream)
+        t0 = time.perf_counter()
+        for _ in range(2):
+            ev.update(x, stream)
+            S.prove(g, ev, None, stream)
+        plain_s.append((time.perf_counter() - t0) / 2)
+        alone.append(hashlib.sha256(p).hexdigest())
+        del ev
+    torch.cuda.synchronize(dev)
+    jobs = rng.integers(0, len(templates), size=args.jobs)
+    budget = int(args.budget_gb * 2**30)
+
+    def serve(arrivals):
+        srv = S.Server(budget, args.slots)
+        t0 = time.perf_counter()
+        tickets, lat, done_at, bad = [], {}, {}, 0
+        k = 0
+        while len(lat) < len(jobs):
+            now = time.perf_counter() - t0
+            while k < len(jobs) and arrivals[k] <= now:
+                tickets.append((srv.submit(gcs[jobs[k]], pins[jobs[k]]), k))
+                k += 1
+            for t, jk in tickets:
+                if jk in lat:
+                    continue
+                st, proof, ms = srv.poll(t)
+                if st in (srv.QUEUED, srv.RUNNING):
+                    continue
+                if st != srv.DONE or hashlib.sha256(proof).hexdigest() != alone[jobs[jk]]:
+                    bad += 1
+                lat[jk] = ms
+                done_at[jk] = time.perf_counter() - t0
+            tickets = [(t, jk) for t, jk in tickets if jk not in lat]
+            time.sleep(0.0002)
+        srv.close()
+        ls = np.array([lat[j] for j in range(len(jobs))])
+        span = max(done_at.values()) - float(arrivals[0])
+        return {"p50_ms": float(np.percentile(ls, 50)), "p99_ms": float(np.percentile(ls, 99)),
+                "proofs_per_s": len(jobs) / span, "mismatches": bad}
+
+    def plain_fifo(arrivals):
+        t, ls = 0.0, []
+        for a, j in zip(arrivals, jobs):
+            t = max(t, a) + plain_s[j]
+            ls.append(1e3 * (t - a))
+        ls = np.array(ls)
+        return {"p50_ms": float(np.percentile(ls, 50)), "p99_ms": float(np.percentile(ls, 99)),
+                "proofs_per_s": len(jobs) / (t - float(arrivals[0]))}
+
+    peak = serve(np.zeros(len(jobs)))
+    rate = peak["proofs_per_s"]
+    loads = {}
+    for load in args.loads:
+        gaps = rng.exponential(1.0 / (load * rate), size=len(jobs))
+        arrivals = np.cumsum(gaps) - gaps[0]
+        loads[str(load)] = {"offered_proofs_per_s": load * rate, "served": serve(arrivals),
+                            "plain_one_at_a_time": plain_fifo(arrivals)}
+    line = {"metric": "served p50/p99 proof latency and proofs/sec", "value": peak["proofs_per_s"],
+            "unit": "proofs/s", "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": 1e3 * args.jobs / rate,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"served: {args.jobs} jobs drawn from {len(templates)} instances of the batched "
+                                   f"workload, Poisson arrivals, {args.budget_gb:g} GB budget, {args.slots} slots",
+                       "loads": args.loads},
+            "peak": peak, "plain_peak_proofs_per_s": len(jobs) / float(sum(plain_s[j] for j in jobs)),
+            "by_load": loads, "parity": "each served proof is compared with the same job proved alone"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["tiny", "medium", "slot", "batched"], default="medium")
+    ap.add_argument("--workload", choices=["tiny", "medium", "slot", "batched", "served"], default="medium")
+    ap.add_argument("--jobs", type=int, default=200, help="served: number of jobs")
+    ap.add_argument("--templates", type=int, default=16, help="served: distinct job instances")
+    ap.add_argument("--slots", type=int, default=16, help="served: concurrent jobs")
+    ap.add_argument("--loads", type=float, nargs="+", default=[0.25, 0.5, 0.9], help="served: offered loads")
     ap.add_argument("--instances", type=int, default=64, help="batched: number of instances")
     ap.add_argument("--budget-gb", type=float, default=150.0, help="batched: device memory per wave")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -424,6 +526,8 @@ def main():
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "served":
+        run_served(args)
     else:
         run_ours(args)
 

@@ -149,6 +149,39 @@ int sisu_gkr_prove_batch(const sisu_circuit* const* circs, sisu_eval* const* eva
                          const sisu_transcript* tr, void* stream, uint32_t concurrency, uint8_t* const* proofs,
                          const size_t* caps, size_t* lens);
 
+/* ---- serving (continuous batching of proof jobs) --------------------------
+ * A server owns one device allocation of `budget_bytes` (its memory budget),
+ * `max_active` slots (a stream, an event and a 1 MiB pinned proof buffer
+ * each) and a worker thread.  Jobs queue in arrival order; the worker admits
+ * the head of the queue as soon as a slot is free and the job's footprint
+ * (all layer values plus the prover workspace, see sisu_circuit_info) fits
+ * in the free part of the budget, lays the job out there, and enqueues its
+ * evaluation and proof on the slot's stream.  Admitted jobs run
+ * concurrently, so their rounds interleave on the device; a finished job
+ * frees its slot and memory, which admits the next.  Every proof is byte
+ * for byte the proof sisu_gkr_prove_into gives for the same inputs and
+ * domain (NULL/0 = the default domain).  The server works on the device
+ * that is current at creation.  Per-kernel profiling must be off while a
+ * server runs.
+ * submit: the circuit must outlive the job and the inputs (host or device,
+ *   n_copies x input_width elements) must stay unchanged until the job is
+ *   done; pinned host inputs let the input copy run asynchronously.
+ *   Errors: TOO_LARGE when the footprint exceeds the whole budget.
+ * poll: *status = 0 queued, 1 running, 2 done (the proof is copied out and
+ *   the ticket released), or a negative SISU_ERR_* (e.g. NOT_CANONICAL
+ *   inputs; the ticket is released).  *latency_ms = completion - submission.
+ * pending: queued and running job counts.
+ * destroy: waits for running jobs; queued jobs are dropped. */
+typedef struct sisu_server sisu_server;
+int sisu_server_create(size_t budget_bytes, uint32_t max_active, const uint8_t* domain, size_t dlen,
+                       sisu_server** out);
+int sisu_server_submit(sisu_server* s, const sisu_circuit* circ, const uint8_t* inputs, int inputs_on_device,
+                       uint64_t* ticket);
+int sisu_server_poll(sisu_server* s, uint64_t ticket, int* status, uint8_t* proof, size_t cap, size_t* len,
+                     double* latency_ms);
+int sisu_server_pending(sisu_server* s, uint32_t* queued, uint32_t* running);
+void sisu_server_destroy(sisu_server* s);
+
 /* Host verifier: replays the transcript, checks g(0) + g(1) = claim in
  * every round (Sec. 3.2.1), the final identity of every layer by summing
  * the wiring predicates, the output claim from `outputs` and the input

@@ -31,7 +31,8 @@ ENTRY_POINTS = [
     "sisu_gkr_verify", "sisu_fr_batch", "sisu_statement_digest", "sisu_microbench",
     "sisu_kernel_launches", "sisu_free", "sisu_last_error", "sisu_version",
     "sisu_profile_enable", "sisu_profile_read", "sisu_profile_launches", "sisu_statement_digest_noalloc",
-    "sisu_gkr_prove_batch",
+    "sisu_gkr_prove_batch", "sisu_server_create", "sisu_server_submit", "sisu_server_poll",
+    "sisu_server_pending", "sisu_server_destroy",
 ]
 PROF_COPY_ROUND, PROF_COPY_FOLD, PROF_EVAL, PROF_GATE_ROUND, PROF_DIGEST = 0, 1, 2, 3, 4
 PROF_LAYER_INIT, PROF_PHASE_INIT, PROF_TRANSCRIPT, PROF_INPUTS = 5, 6, 7, 8
@@ -73,6 +74,12 @@ def _load():
         "sisu_gkr_prove": ([vp, vp, vp, vp, pp, ctypes.POINTER(sz)], ctypes.c_int),
         "sisu_gkr_prove_into": ([vp, vp, vp, vp, u8p, sz, ctypes.POINTER(sz)], ctypes.c_int),
         "sisu_gkr_verify": ([vp, u8p, u8p, u8p, sz, u8p, sz], ctypes.c_int),
+        "sisu_server_create": ([sz, u32, vp, sz, pp], ctypes.c_int),
+        "sisu_server_submit": ([vp, vp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+        "sisu_server_poll": ([vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int), vp, sz, ctypes.POINTER(sz),
+                              ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+        "sisu_server_pending": ([vp, ctypes.POINTER(u32), ctypes.POINTER(u32)], ctypes.c_int),
+        "sisu_server_destroy": ([vp], None),
         "sisu_gkr_prove_batch": ([ctypes.POINTER(vp), ctypes.POINTER(vp), u32, vp, vp, u32, ctypes.POINTER(vp),
                                   ctypes.POINTER(sz), ctypes.POINTER(sz)], ctypes.c_int),
         "sisu_fr_batch": ([ctypes.c_int, vp, vp, vp, sz, vp], ctypes.c_int),
@@ -299,6 +306,56 @@ def prove_batch(circs, evals, transcript: Transcript | None = None, stream=None,
     _check(_lib.sisu_gkr_prove_batch(ch, eh, n, transcript.h if transcript else None, _stream(stream),
                                      concurrency, ph, caps, lens))
     return [bufs[i].raw[:lens[i]] for i in range(n)]
+
+
+class Server:
+    """Continuous-batching proof server (``sisu_server_*``)."""
+
+    QUEUED, RUNNING, DONE = 0, 1, 2
+
+    def __init__(self, budget_bytes: int, max_active: int = 8, domain: bytes | None = None):
+        h = ctypes.c_void_p()
+        dom = bytes(domain) if domain else None
+        buf = ctypes.create_string_buffer(dom) if dom else None
+        _check(_lib.sisu_server_create(budget_bytes, max_active, ctypes.cast(buf, ctypes.c_void_p) if buf else None,
+                                       len(dom) if dom else 0, ctypes.byref(h)))
+        self.h = h
+        self._keep = {}
+
+    def submit(self, circ: Circuit, inputs) -> int:
+        """Queue a job; ``inputs`` must stay alive and unchanged until it is done."""
+        p, on_dev, keep = _ptr(inputs)
+        t = ctypes.c_uint64()
+        _check(_lib.sisu_server_submit(self.h, circ.h, p, on_dev, ctypes.byref(t)))
+        self._keep[t.value] = (keep, circ, circ.proof_len)
+        return t.value
+
+    def poll(self, ticket: int):
+        """(status, proof bytes or None, latency ms or None)."""
+        keep, circ, n = self._keep[ticket]
+        st = ctypes.c_int()
+        buf = ctypes.create_string_buffer(n)
+        ln = ctypes.c_size_t()
+        lat = ctypes.c_double()
+        _check(_lib.sisu_server_poll(self.h, ticket, ctypes.byref(st), ctypes.cast(buf, ctypes.c_void_p), n,
+                                     ctypes.byref(ln), ctypes.byref(lat)))
+        if st.value in (self.QUEUED, self.RUNNING):
+            return st.value, None, None
+        del self._keep[ticket]
+        return st.value, (buf.raw[:ln.value] if st.value == self.DONE else None), lat.value
+
+    def pending(self):
+        q, r = ctypes.c_uint32(), ctypes.c_uint32()
+        _check(_lib.sisu_server_pending(self.h, ctypes.byref(q), ctypes.byref(r)))
+        return q.value, r.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.sisu_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
 
 
 def verify(circ: Circuit, inputs: bytes, outputs: bytes, proof: bytes, domain: bytes | None = None) -> int:

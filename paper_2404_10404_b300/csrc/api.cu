@@ -14,8 +14,7 @@
 #include <mutex>
 #include <new>
 
-#include "../../include/sisu.h"
-#include "internal.h"
+#include "handles.h"
 
 using namespace sisu;
 
@@ -162,61 +161,6 @@ extern "C" int sisu_profile_read(uint32_t kind, double* ms, uint64_t* launches, 
 
 // ---------------------------------------------------------------------------
 // handles
-
-struct sisu_circuit {
-  HostCircuit hc;
-  std::vector<DevLayer> L;  // device views, gate layers 0..d-1
-  void* dev = nullptr;      // one allocation holding every device array
-  int device = 0;
-  ~sisu_circuit() {
-    if (dev) cudaFree(dev);
-  }
-};
-
-struct Workspace {
-  void* dev = nullptr;
-  uint32_t *T = nullptr, *E = nullptr, *om = nullptr, *At = nullptr, *H1 = nullptr, *H2 = nullptr,
-           *Ay = nullptr, *Q = nullptr, *partials = nullptr, *dscratch = nullptr;
-  DevState* S = nullptr;
-  uint8_t* proof = nullptr;
-  uint8_t* host = nullptr;  // pinned: proof bytes followed by the error word
-  size_t proof_len = 0;
-  // the proof's launch sequence captured as a CUDA graph (same circuit,
-  // workspace and transcript domain give the same launches every time)
-  cudaStream_t cap_stream = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  uint8_t gdomain[kMaxDomain];
-  uint32_t gdlen = 0;
-  bool gvalid = false;
-  int proofs = 0;  // proofs enqueued so far on this workspace
-  ~Workspace() {
-    if (exec) cudaGraphExecDestroy(exec);
-    if (cap_stream) cudaStreamDestroy(cap_stream);
-    if (dev) cudaFree(dev);
-    if (host) cudaFreeHost(host);
-  }
-};
-
-struct sisu_eval {
-  const sisu_circuit* circ = nullptr;
-  std::vector<uint32_t*> V;  // layers 0..d, Montgomery, padded
-  void* dev = nullptr;
-  uint32_t* stage = nullptr;  // padded-input staging (only when padding is needed)
-  uint32_t* flag = nullptr;   // device error word
-  uint32_t* host_flag = nullptr;
-  std::unique_ptr<Workspace> ws;
-  ~sisu_eval() {
-    ws.reset();
-    if (stage) cudaFree(stage);
-    if (dev) cudaFree(dev);
-    if (host_flag) cudaFreeHost(host_flag);
-  }
-};
-
-struct sisu_transcript {
-  uint8_t domain[kMaxDomain];
-  uint32_t len;
-};
 
 static const char kDefaultDomain[] = "SISU-GKR-v1";
 
@@ -407,7 +351,8 @@ extern "C" int sisu_circuit_info(const sisu_circuit* circ, uint32_t* depth, uint
 // ---------------------------------------------------------------------------
 // evaluation
 
-static int eval_run(sisu_eval* ev, const uint8_t* inputs, int on_device, cudaStream_t st) {
+namespace sisu {
+int eval_enqueue(sisu_eval* ev, const uint8_t* inputs, int on_device, cudaStream_t st) {
   const sisu_circuit* cc = ev->circ;
   const HostCircuit& hc = cc->hc;
   const uint32_t d = hc.d;
@@ -432,6 +377,40 @@ static int eval_run(sisu_eval* ev, const uint8_t* inputs, int on_device, cudaStr
     CK(launch_eval_layer(ev->V[i + 1], ev->V[i], cc->L[i].gate_io, hc.c, hc.s[i], hc.s[i + 1], st), "eval layer");
   }
   CK(cudaMemcpyAsync(ev->host_flag, ev->flag, 4, cudaMemcpyDeviceToHost, st), "flag copy");
+  return SISU_OK;
+}
+
+size_t eval_footprint(const sisu_circuit* cc, bool host_inputs) {
+  const HostCircuit& hc = cc->hc;
+  size_t total = 0;
+  for (uint32_t i = 0; i <= hc.d; ++i) total += ((size_t)hc.C << hc.s[i]) * 32;
+  total += 256;  // flag
+  const bool padded = hc.Creal != hc.C || hc.wreal[hc.d] != hc.W[hc.d];
+  if (padded && host_inputs) total += ((size_t)hc.Creal * hc.wreal[hc.d] * 32 + 255) & ~(size_t)255;
+  return total;
+}
+
+void eval_place(sisu_eval* ev, const sisu_circuit* cc, uint8_t* dev, bool host_inputs, uint32_t* host_flag) {
+  const HostCircuit& hc = cc->hc;
+  ev->circ = cc;
+  ev->placed = true;
+  ev->V.resize(hc.d + 1);
+  size_t off = 0;
+  for (uint32_t i = 0; i <= hc.d; ++i) {
+    ev->V[i] = (uint32_t*)(dev + off);
+    off += ((size_t)hc.C << hc.s[i]) * 32;
+  }
+  ev->flag = (uint32_t*)(dev + off);
+  off += 256;
+  const bool padded = hc.Creal != hc.C || hc.wreal[hc.d] != hc.W[hc.d];
+  ev->stage = (padded && host_inputs) ? (uint32_t*)(dev + off) : nullptr;
+  ev->host_flag = host_flag;
+}
+}  // namespace sisu
+
+static int eval_run(sisu_eval* ev, const uint8_t* inputs, int on_device, cudaStream_t st) {
+  int rc = eval_enqueue(ev, inputs, on_device, st);
+  if (rc) return rc;
   CK(cudaStreamSynchronize(st), "eval");
   if (*ev->host_flag & 1u) return fail(SISU_ERR_NOT_CANONICAL, "an input element is not below r");
   return SISU_OK;
@@ -549,42 +528,45 @@ extern "C" void sisu_transcript_destroy(sisu_transcript* tr) { delete tr; }
 // ---------------------------------------------------------------------------
 // proving
 
-static int workspace_alloc(sisu_eval* ev) {
-  const HostCircuit& hc = ev->circ->hc;
-  const sisu_circuit* cc = ev->circ;
+static void workspace_sizes(const sisu_circuit* cc, size_t sizes[12]) {
+  const HostCircuit& hc = cc->hc;
   uint32_t wmax_next = 1, wmax = 1, nmax = 1;
   for (uint32_t i = 0; i < hc.d; ++i) {
     wmax_next = std::max(wmax_next, hc.W[i + 1]);
     nmax = std::max(nmax, cc->L[i].ntot);
   }
   for (uint32_t i = 0; i <= hc.d; ++i) wmax = std::max(wmax, hc.W[i]);
-  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t half = hc.C >= 2 ? (size_t)(hc.C / 2) * wmax_next * 32 : 32;
   const size_t dig = std::max(digest_scratch_words((size_t)hc.C * hc.W[hc.d] * 32),
                               digest_scratch_words((size_t)hc.C * hc.W[0] * 32)) * 4;
-  size_t sizes[12] = {half,
-                      (size_t)hc.C * 32,
-                      (size_t)nmax * 32,
-                      (size_t)wmax_next * 32,
-                      (size_t)wmax_next * 32,
-                      (size_t)wmax_next * 32,
-                      (size_t)wmax_next * 32,
-                      (size_t)wmax * 32,
-                      (size_t)kMaxPartials * 4 * 32,
-                      dig,
-                      sizeof(DevState),
-                      hc.proof_len()};
-  size_t total = 0;
-  for (size_t s : sizes) total += al(s);
-  std::unique_ptr<Workspace> ws(new (std::nothrow) Workspace());
-  if (!ws) return fail(SISU_ERR_OOM, "host allocation");
-  if (cudaMalloc(&ws->dev, total) != cudaSuccess)
-    return fail(SISU_ERR_OOM, "device allocation of %zu bytes for the prover workspace", total);
-  uint8_t* p = (uint8_t*)ws->dev;
+  const size_t v[12] = {half, (size_t)hc.C * 32, (size_t)nmax * 32, (size_t)wmax_next * 32, (size_t)wmax_next * 32,
+                        (size_t)wmax_next * 32, (size_t)wmax_next * 32, (size_t)wmax * 32,
+                        (size_t)kMaxPartials * 4 * 32, dig, sizeof(DevState), hc.proof_len()};
+  for (int k = 0; k < 12; ++k) sizes[k] = v[k];
+}
+
+static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+namespace sisu {
+size_t workspace_footprint(const sisu_circuit* cc) {
+  size_t sizes[12], total = 0;
+  workspace_sizes(cc, sizes);
+  for (size_t x : sizes) total += al256(x);
+  return total;
+}
+
+// Lay out the workspace in `dev` (workspace_footprint bytes) with the pinned
+// proof bytes at `host` (proof_len + 16 bytes), header and state set on `st`.
+static int workspace_init(sisu_eval* ev, Workspace* ws, uint8_t* dev, uint8_t* host, cudaStream_t st) {
+  const sisu_circuit* cc = ev->circ;
+  const HostCircuit& hc = cc->hc;
+  size_t sizes[12];
+  workspace_sizes(cc, sizes);
+  uint8_t* p = dev;
   void* ptrs[12];
   for (int k = 0; k < 12; ++k) {
     ptrs[k] = p;
-    p += al(sizes[k]);
+    p += al256(sizes[k]);
   }
   ws->T = (uint32_t*)ptrs[0];
   ws->E = (uint32_t*)ptrs[1];
@@ -599,8 +581,7 @@ static int workspace_alloc(sisu_eval* ev) {
   ws->S = (DevState*)ptrs[10];
   ws->proof = (uint8_t*)ptrs[11];
   ws->proof_len = hc.proof_len();
-  if (cudaMallocHost(&ws->host, ws->proof_len + 16) != cudaSuccess)
-    return fail(SISU_ERR_OOM, "pinned host allocation");
+  ws->host = host;
   // the proof header is fixed by the circuit
   std::vector<uint8_t> hdr(8 + 4 * ((size_t)hc.d + 3));
   memcpy(hdr.data(), "SISUGKR1", 8);
@@ -610,8 +591,38 @@ static int workspace_alloc(sisu_eval* ev) {
   put(8, hc.d);
   put(12, hc.c);
   for (uint32_t i = 0; i <= hc.d; ++i) put(16 + 4 * (size_t)i, hc.s[i]);
-  CK(cudaMemcpy(ws->proof, hdr.data(), hdr.size(), cudaMemcpyHostToDevice), "header upload");
-  CK(cudaMemset(ws->S, 0, sizeof(DevState)), "memset");
+  // staged through the pinned proof buffer so that the copy can stay asynchronous
+  memcpy(host, hdr.data(), hdr.size());
+  CK(cudaMemcpyAsync(ws->proof, host, hdr.size(), cudaMemcpyHostToDevice, st), "header upload");
+  CK(cudaMemsetAsync(ws->S, 0, sizeof(DevState), st), "memset");
+  return SISU_OK;
+}
+
+int workspace_place(sisu_eval* ev, uint8_t* dev, uint8_t* host_pinned, cudaStream_t st) {
+  std::unique_ptr<Workspace> ws(new (std::nothrow) Workspace());
+  if (!ws) return fail(SISU_ERR_OOM, "host allocation");
+  ws->owns_host = false;
+  int rc = workspace_init(ev, ws.get(), dev, host_pinned, st);
+  if (rc) return rc;
+  ev->ws = std::move(ws);
+  return SISU_OK;
+}
+}  // namespace sisu
+
+static int workspace_alloc(sisu_eval* ev) {
+  const sisu_circuit* cc = ev->circ;
+  std::unique_ptr<Workspace> ws(new (std::nothrow) Workspace());
+  if (!ws) return fail(SISU_ERR_OOM, "host allocation");
+  const size_t total = workspace_footprint(cc);
+  if (cudaMalloc(&ws->dev, total) != cudaSuccess)
+    return fail(SISU_ERR_OOM, "device allocation of %zu bytes for the prover workspace", total);
+  uint8_t* host = nullptr;
+  if (cudaMallocHost(&host, cc->hc.proof_len() + 16) != cudaSuccess)
+    return fail(SISU_ERR_OOM, "pinned host allocation");
+  ws->owns_host = true;
+  int rc = workspace_init(ev, ws.get(), (uint8_t*)ws->dev, host, 0);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(0), "workspace init");
   ev->ws = std::move(ws);
   return SISU_OK;
 }
@@ -717,6 +728,7 @@ static int enqueue_prove(const sisu_circuit* cc, sisu_eval* ev, const sisu_trans
 
 // One whole proof and the copies of its bytes and error word to pinned host
 // memory, enqueued on `st` (no host wait).
+int sisu::proof_enqueue(const sisu_circuit* cc, sisu_eval* ev, const sisu_transcript* tr, cudaStream_t st);
 static int enqueue_proof_and_copy(const sisu_circuit* cc, sisu_eval* ev, const sisu_transcript* tr, cudaStream_t st) {
   Workspace& w = *ev->ws;
   const size_t n = cc->hc.proof_len();
@@ -772,6 +784,10 @@ static int launch_proof(const sisu_circuit* cc, sisu_eval* ev, const sisu_transc
   return SISU_OK;
 }
 
+int sisu::proof_enqueue(const sisu_circuit* cc, sisu_eval* ev, const sisu_transcript* tr, cudaStream_t st) {
+  return enqueue_proof_and_copy(cc, ev, tr, st);
+}
+
 // After the proof's stream work completed: check the device error word and
 // copy the bytes out.
 static int finish_proof(const sisu_circuit* cc, sisu_eval* ev, uint8_t* proof) {
@@ -783,6 +799,8 @@ static int finish_proof(const sisu_circuit* cc, sisu_eval* ev, uint8_t* proof) {
   memcpy(proof, w.host, n);
   return SISU_OK;
 }
+
+int sisu::proof_finish(const sisu_circuit* cc, sisu_eval* ev, uint8_t* proof) { return finish_proof(cc, ev, proof); }
 
 static int prepare_proof(const sisu_circuit* circ, sisu_eval* ev, uint8_t* proof, size_t cap, size_t* proof_len) {
   if (!circ || !ev || !proof) return fail(SISU_ERR_INVALID_ARG, "NULL circuit, eval or proof buffer");

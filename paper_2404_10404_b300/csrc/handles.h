@@ -1,0 +1,90 @@
+// Handle types of the C ABI and the internal entry points that the prover,
+// the batch call and the server share.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <memory>
+#include <vector>
+
+#include "../../include/sisu.h"
+#include "internal.h"
+
+using sisu::DevLayer;
+using sisu::DevState;
+using sisu::HostCircuit;
+using sisu::kMaxDomain;
+
+struct sisu_circuit {
+  HostCircuit hc;
+  std::vector<DevLayer> L;  // device views, gate layers 0..d-1
+  void* dev = nullptr;      // one allocation holding every device array
+  int device = 0;
+  ~sisu_circuit() {
+    if (dev) cudaFree(dev);
+  }
+};
+
+struct Workspace {
+  void* dev = nullptr;  // owned allocation (null when placed in caller memory)
+  uint32_t *T = nullptr, *E = nullptr, *om = nullptr, *At = nullptr, *H1 = nullptr, *H2 = nullptr,
+           *Ay = nullptr, *Q = nullptr, *partials = nullptr, *dscratch = nullptr;
+  DevState* S = nullptr;
+  uint8_t* proof = nullptr;
+  uint8_t* host = nullptr;  // pinned: proof bytes followed by the error word
+  bool owns_host = true;    // false when the pinned bytes belong to the caller
+  size_t proof_len = 0;
+  // the proof's launch sequence captured as a CUDA graph (same circuit,
+  // workspace and transcript domain give the same launches every time)
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  uint8_t gdomain[kMaxDomain];
+  uint32_t gdlen = 0;
+  bool gvalid = false;
+  int proofs = 0;  // proofs enqueued so far on this workspace
+  ~Workspace() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (dev) cudaFree(dev);
+    if (host && owns_host) cudaFreeHost(host);
+  }
+};
+
+struct sisu_eval {
+  const sisu_circuit* circ = nullptr;
+  std::vector<uint32_t*> V;  // layers 0..d, Montgomery, padded
+  void* dev = nullptr;        // owned allocation (null when placed in caller memory)
+  uint32_t* stage = nullptr;  // padded-input staging (only when padding is needed)
+  uint32_t* flag = nullptr;   // device error word
+  uint32_t* host_flag = nullptr;
+  std::unique_ptr<Workspace> ws;
+  bool placed = false;         // layers, flag and staging live in caller memory
+  ~sisu_eval() {
+    ws.reset();
+    if (stage && !placed) cudaFree(stage);
+    if (dev) cudaFree(dev);
+    if (host_flag && !placed) cudaFreeHost(host_flag);
+  }
+};
+
+struct sisu_transcript {
+  uint8_t domain[kMaxDomain];
+  uint32_t len;
+};
+
+
+namespace sisu {
+// device bytes of one evaluation (layers, flag, staging for padded host
+// inputs) and of one prover workspace
+size_t eval_footprint(const sisu_circuit* cc, bool host_inputs);
+size_t workspace_footprint(const sisu_circuit* cc);
+// lay out an evaluation / a workspace in caller memory (256-byte aligned)
+void eval_place(sisu_eval* ev, const sisu_circuit* cc, uint8_t* dev, bool host_inputs, uint32_t* host_flag);
+int workspace_place(sisu_eval* ev, uint8_t* dev, uint8_t* host_pinned, cudaStream_t st);
+// enqueue the evaluation (no wait; the canonicity flag is checked later)
+int eval_enqueue(sisu_eval* ev, const uint8_t* inputs, int on_device, cudaStream_t st);
+// enqueue one proof plus the copies of its bytes and error word to host
+int proof_enqueue(const sisu_circuit* cc, sisu_eval* ev, const sisu_transcript* tr, cudaStream_t st);
+// after the stream work: check the error word, copy the proof out
+int proof_finish(const sisu_circuit* cc, sisu_eval* ev, uint8_t* proof);
+int report_error(int code, const char* msg);
+}  // namespace sisu

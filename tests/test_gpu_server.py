@@ -1,0 +1,88 @@
+"""Continuous-batching proof server: jobs admitted by device-memory
+footprint, running concurrently on the server's streams, each result equal
+to the proof of the same job alone (and to the oracle's)."""
+import time
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    import paper_2404_10404_b300 as S
+    return S
+
+
+def _jobs():
+    rng = np.random.default_rng(3)
+    specs = []
+    for j in range(5):
+        C = int(2 ** rng.integers(2, 7))
+        W = int(2 ** rng.integers(3, 8))
+        d = int(rng.integers(1, 4))
+        specs.append(synth.uniform_circuit(5 * (1 << 32) + j, C, [W] * (d + 1), 60, name=f"s{j}"))
+    specs.append(synth.micro(77, 20, [100, 300, 60], 50))
+    return specs
+
+
+def _drain(srv, tickets, timeout=120):
+    out = {}
+    t0 = time.time()
+    while len(out) < len(tickets):
+        for t in tickets:
+            if t in out:
+                continue
+            st, proof, lat = srv.poll(t)
+            if st not in (srv.QUEUED, srv.RUNNING):
+                out[t] = (st, proof, lat)
+        assert time.time() - t0 < timeout, "server did not finish"
+        time.sleep(0.001)
+    return out
+
+
+def test_served_equals_alone_and_oracle(S, oracle):
+    specs = _jobs()
+    gcs = [S.Circuit.from_spec(c) for c in specs]
+    inputs = [synth.fr_bytes(synth.inputs_for(c, seed=1000 + k)) for k, c in enumerate(specs)]
+    alone = []
+    for g, x in zip(gcs, inputs):
+        alone.append(S.prove(g, S.Eval(g, x)))
+    for c, x, p in zip(specs, inputs, alone):
+        assert p == oracle.prove(c, x)
+    # a budget that holds about two of the larger jobs: queueing and reuse of memory
+    fp = max(g.eval_bytes for g in gcs) * 3
+    srv = S.Server(budget_bytes=max(fp, 8 << 20), max_active=3)
+    order = [k % len(specs) for k in range(3 * len(specs))]
+    tickets = [srv.submit(gcs[k], inputs[k]) for k in order]
+    res = _drain(srv, tickets)
+    for t, k in zip(tickets, order):
+        st, proof, lat = res[t]
+        assert st == srv.DONE and proof == alone[k] and lat > 0
+    assert srv.pending() == (0, 0)
+    srv.close()
+
+
+def test_server_errors(S):
+    specs = _jobs()[:2]
+    gcs = [S.Circuit.from_spec(c) for c in specs]
+    good = synth.fr_bytes(synth.inputs_for(specs[0]))
+    bad = bytearray(synth.fr_bytes(synth.inputs_for(specs[1])))
+    bad[0:32] = synth.FR_MODULUS.to_bytes(32, "little")
+    srv = S.Server(budget_bytes=1 << 30, max_active=2)
+    t_bad = srv.submit(gcs[1], bytes(bad))
+    t_good = srv.submit(gcs[0], good)
+    res = _drain(srv, [t_bad, t_good])
+    assert res[t_bad][0] == -3
+    assert res[t_good][0] == srv.DONE
+    assert res[t_good][1] == S.prove(gcs[0], S.Eval(gcs[0], good))
+    tiny = S.Server(budget_bytes=1 << 20, max_active=1)
+    big = S.Circuit.from_spec(synth.micro(5, 64, [1024, 1024], 50))
+    with pytest.raises(S.SisuError) as e:
+        tiny.submit(big, synth.fr_bytes(synth.inputs_for(synth.micro(5, 64, [1024, 1024], 50))))
+    assert e.value.code == -9
+    srv.close()
+    tiny.close()
