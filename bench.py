@@ -233,7 +233,7 @@ def run_ours(args):
         pass
     clocks = Clocks(uuid)
     time.sleep(0.5)
-    S.profile_enable(1 << S.PROF_COPY_ROUND)
+    # timed region: no per-kernel events, so the proofs replay their CUDA graphs
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
@@ -250,14 +250,21 @@ def run_ours(args):
         dist.barrier()
     ms = ev0.elapsed_time(ev1)
     launches = S.kernel_launches() - launches0
-    prof_ms, prof_n, prof_work = S.profile_read(S.PROF_COPY_ROUND)
-    S.profile_enable(0)
     clk = clocks.stop()
     if world > 1:
         t = torch.tensor([ms], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     value = world * args.steps * gates / (ms / 1e3)
+    # roofline of the dominant kernel: its launches timed with CUDA events on
+    # the launching stream over further steps right after the timed region
+    # (per-launch events need launch-by-launch issue instead of graph replay)
+    S.profile_enable(1 << S.PROF_COPY_ROUND)
+    for _ in range(min(args.steps, 10)):
+        step(inputs)
+    torch.cuda.synchronize(dev)
+    prof_ms, prof_n, prof_work = S.profile_read(S.PROF_COPY_ROUND)
+    S.profile_enable(0)
 
     # end to end through the public API: host inputs (pinned) in, proof out
     torch.cuda.synchronize(dev)
@@ -287,6 +294,7 @@ def run_ours(args):
     S.profile_enable(0)
 
     achieved = prof_work * IMAD_PER_FR_MUL / (prof_ms / 1e3) / 1e12 if prof_ms else None
+    # kernel launches counted inside the timed region (graph replay launches the same kernels)
     roofline = {"bound": "alu", "kernel": "k_copy_round (copy-phase round)", "achieved": achieved,
                 "peak": ALU_PEAK_TIMAD, "unit": "TIMAD/s", "frac": achieved / ALU_PEAK_TIMAD if achieved else None,
                 "traffic": DOMINANT_TRAFFIC_BYTES,

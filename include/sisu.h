@@ -251,7 +251,8 @@ int sisu_profile_read(uint32_t kind, double* ms, uint64_t* launches, double* fr_
  * the number recorded. */
 int sisu_profile_launches(uint32_t kind, double* ms, double* fr_mults, size_t cap, size_t* n);
 
-/* Number of kernels this library launched so far in this process. */
+/* Number of kernels this library launched so far in this process (a CUDA
+ * graph replay counts the kernels it runs). */
 uint64_t sisu_kernel_launches(void);
 
 void sisu_free(void* p);

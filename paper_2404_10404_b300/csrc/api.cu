@@ -765,7 +765,11 @@ static int launch_proof(const sisu_circuit* cc, sisu_eval* ev, const sisu_transc
     w.gvalid = false;
     if (!w.cap_stream) CK(cudaStreamCreateWithFlags(&w.cap_stream, cudaStreamNonBlocking), "stream create");
     CK(cudaStreamBeginCapture(w.cap_stream, cudaStreamCaptureModeThreadLocal), "graph capture");
+    const uint64_t before = launches_add(0);
     int rc = enqueue_proof_and_copy(cc, ev, tr, w.cap_stream);
+    // captured kernels are launched by each replay, not now
+    w.graph_kernels = launches_add(0) - before;
+    launches_add((uint64_t)0 - w.graph_kernels);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(w.cap_stream, &g);
     if (rc) {
@@ -781,6 +785,7 @@ static int launch_proof(const sisu_circuit* cc, sisu_eval* ev, const sisu_transc
     w.gvalid = true;
   }
   CK(cudaGraphLaunch(w.exec, st), "graph launch");
+  launches_add(w.graph_kernels);
   return SISU_OK;
 }
 

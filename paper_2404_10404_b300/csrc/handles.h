@@ -40,7 +40,8 @@ struct Workspace {
   uint8_t gdomain[kMaxDomain];
   uint32_t gdlen = 0;
   bool gvalid = false;
-  int proofs = 0;  // proofs enqueued so far on this workspace
+  uint64_t graph_kernels = 0;  // kernel nodes in the captured graph
+  int proofs = 0;              // proofs enqueued so far on this workspace
   ~Workspace() {
     if (exec) cudaGraphExecDestroy(exec);
     if (cap_stream) cudaStreamDestroy(cap_stream);
