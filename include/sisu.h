@@ -194,8 +194,10 @@ int sisu_gkr_verify(const sisu_circuit* circ, const uint8_t* inputs, const uint8
  * Elementwise on device arrays of n canonical elements, enqueued on
  * `stream` and awaited: op 0 a+b, 1 a-b, 2 a*b, 3 a^-1 (batched inversion:
  * Montgomery's trick per thread, one Fermat exponentiation per batch; a
- * zero input yields 0 and SISU_ERR_ZERO_INVERSE), 4 a*b + (1-a)(1-b).
- * b is ignored for op 3.  Errors: INVALID_ARG, NOT_CANONICAL, ZERO_INVERSE. */
+ * zero input yields 0 and SISU_ERR_ZERO_INVERSE), 4 a*b + (1-a)(1-b),
+ * 5 out[i] = sum of a[j]*b[j] for j from 64*floor(i/64) to i (the lazily
+ * reduced dot product the copy-phase rounds use: full 512-bit products
+ * summed exactly, one reduction per sum).  b is ignored for op 3.  Errors: INVALID_ARG, NOT_CANONICAL, ZERO_INVERSE. */
 int sisu_fr_batch(int op, const uint8_t* a, const uint8_t* b, uint8_t* out, size_t n, void* stream);
 
 /* Merkle statement digest of device bytes (the transcript's digest of
@@ -229,9 +231,10 @@ int sisu_statement_digest_noalloc(const uint8_t* data, size_t len, uint8_t* out,
  * Montgomery products as the kernels call them, kind 3 = the same products
  * inlined, kind 4 = 32x32+64-bit mad.wide chains, kind 5 = Montgomery
  * products built from 64-bit partial products (mul.wide), kind 6 = kinds 2
- * and 5 run side by side on the same operands.  Reports the elapsed
- * milliseconds and the number of operations (multiply-adds, or field
- * products for kinds 2, 3 and 5); for kind 6, *ops is minus the number of
+ * and 5 run side by side on the same operands, kind 7 = full 512-bit
+ * products added into one 544-bit accumulator (no reduction).  Reports the
+ * elapsed milliseconds and the number of operations (multiply-adds, or
+ * field products for kinds 2, 3, 5 and 7); for kind 6, *ops is minus the number of
  * threads whose two products disagreed (0 when they all agree). */
 int sisu_microbench(int kind, uint32_t blocks, uint32_t threads, uint32_t iters, void* stream,
                     double* ms, double* ops);

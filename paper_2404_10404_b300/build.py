@@ -21,7 +21,7 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU = ["eval.cu", "prove.cu", "field.cu", "api.cu", "noalloc.cu", "server.cu"]
 CPP = ["verify.cpp"]
-HEADERS = ["fr.cuh", "sha256.cuh", "internal.h", "launch.cuh", "handles.h"]
+HEADERS = ["fr.cuh", "fr_wide.cuh", "sha256.cuh", "internal.h", "launch.cuh", "handles.h"]
 
 
 def _stale(target: str, deps) -> bool:

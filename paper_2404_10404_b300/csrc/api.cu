@@ -929,7 +929,7 @@ extern "C" int sisu_gkr_verify(const sisu_circuit* circ, const uint8_t* inputs, 
 // field core, digests, microbenchmarks
 
 extern "C" int sisu_fr_batch(int op, const uint8_t* a, const uint8_t* b, uint8_t* out, size_t n, void* stream) {
-  if (op < 0 || op > 4) return fail(SISU_ERR_INVALID_ARG, "op %d", op);
+  if (op < 0 || op > 5) return fail(SISU_ERR_INVALID_ARG, "op %d", op);
   if (!a || !out || (op != 3 && !b)) return fail(SISU_ERR_INVALID_ARG, "NULL operand");
   if (n == 0) return SISU_OK;
   if ((((uintptr_t)a | (uintptr_t)out | (uintptr_t)(b ? b : a)) & 15) != 0)
@@ -971,7 +971,7 @@ extern "C" int sisu_statement_digest(const uint8_t* data, size_t len, uint8_t* o
 
 extern "C" int sisu_microbench(int kind, uint32_t blocks, uint32_t threads, uint32_t iters, void* stream, double* ms,
                                double* ops) {
-  if (kind < 0 || kind > 6 || !blocks || !threads || threads > 1024 || !ms || !ops)
+  if (kind < 0 || kind > 7 || !blocks || !threads || threads > 1024 || !ms || !ops)
     return fail(SISU_ERR_INVALID_ARG, "bad microbenchmark arguments");
   int rc = run_microbench(kind, blocks, threads, iters, stream, ms, ops);
   if (rc) return cuda_fail((cudaError_t)rc, "microbenchmark");

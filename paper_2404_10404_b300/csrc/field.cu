@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "fr_wide.cuh"
 #include "internal.h"
 #include "launch.cuh"
 #include "sha256.cuh"
@@ -36,7 +37,23 @@ __global__ void k_fr_batch(int op, const uint32_t* __restrict__ a, const uint32_
         case 0: z = fr_add(x, y); break;
         case 1: z = fr_sub(x, y); break;
         case 2: z = fr_mul(x, y); break;
-        default: z = fr_add(fr_mul(x, y), fr_mul(fr_one_minus_f(x), fr_one_minus_f(y))); break;
+        case 4: z = fr_add(fr_mul(x, y), fr_mul(fr_one_minus_f(x), fr_one_minus_f(y))); break;
+        default: {
+          // op 5: sum of a_j b_j over j from the start of i's aligned run of
+          // 64 up to i, through the 544-bit accumulator (one reduction)
+          FrAcc acc = fracc_zero();
+          for (size_t j = i & ~(size_t)63; j <= i; ++j) {
+            Fr u = fr_load(a, j), v = fr_load(b, j);
+            if (!fr_lt_modulus(u) || !fr_lt_modulus(v)) {
+              atomicOr(flags, 1u);
+              u = fr_zero();
+              v = fr_zero();
+            }
+            fracc_mac(acc, fr_from_canonical(u), fr_from_canonical(v));
+          }
+          z = fr_mul(fr_redc288(acc), fr_mont_2_32());
+          break;
+        }
       }
       fr_store(out, i, fr_to_canonical(z));
     }
@@ -174,6 +191,23 @@ __global__ void k_mb_frmul_check(uint32_t iters, uint32_t* sink) {
   sink[blockIdx.x * blockDim.x + threadIdx.x] = bad;
 }
 
+// 512-bit products added into one 544-bit accumulator (kind 7)
+__global__ void k_mb_frmac(uint32_t iters, uint32_t* sink) {
+  Fr x = fr_one(), y = fr_r2();
+  x.v[0] ^= threadIdx.x;
+  FrAcc acc = fracc_zero();
+  for (uint32_t it = 0; it < iters; ++it) {
+    fracc_mac(acc, x, y);
+    fracc_mac(acc, y, x);
+    x.v[1] ^= acc.v[4];
+  }
+  const Fr r = fr_redc288(acc);
+  uint32_t o = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) o ^= r.v[i];
+  sink[blockIdx.x * blockDim.x + threadIdx.x] = o;
+}
+
 __global__ void k_mb_madwide(uint32_t iters, uint32_t mul, uint32_t* sink) {
   unsigned long long x[8];
 #pragma unroll
@@ -209,6 +243,7 @@ int run_microbench(int kind, uint32_t blocks, uint32_t threads, uint32_t iters, 
     else if (kind == 3) k_mb_frmul_inline<<<blocks, threads, 0, st>>>(iters, sink);
     else if (kind == 4) k_mb_madwide<<<blocks, threads, 0, st>>>(iters, 0x9e3779b9u, sink);
     else if (kind == 5) k_mb_frmul_wide<<<blocks, threads, 0, st>>>(iters, sink);
+    else if (kind == 7) k_mb_frmac<<<blocks, threads, 0, st>>>(iters, sink);
     else k_mb_frmul_check<<<blocks, threads, 0, st>>>(iters, sink);
     launches_add(1);
   };
@@ -231,7 +266,7 @@ int run_microbench(int kind, uint32_t blocks, uint32_t threads, uint32_t iters, 
     cudaFree(sink);
     return (int)e;
   }
-  double per = (kind == 2 || kind == 3 || kind == 5) ? 2.0 : kind == 6 ? 2.0 : 64.0;
+  double per = (kind == 2 || kind == 3 || kind == 5 || kind == 7) ? 2.0 : kind == 6 ? 2.0 : 64.0;
   *ops = (double)blocks * threads * iters * per;
   cudaEventDestroy(a);
   cudaEventDestroy(b);

@@ -1,0 +1,549 @@
+// Lazily reduced sums of field products (BN254 F_r, Montgomery form).
+//
+// A sum of many products a_i b_i needs only one Montgomery reduction when
+// the full 512-bit products are added up first: the accumulator holds the
+// exact integer T = sum a_i b_i in 17 words (544 bits), and one reduction at
+// the end maps it into the field.  A full product costs 64 mad.lo and 64
+// mad.hi, against 128 + 128 (+ 8 for the quotient digits) for a Montgomery
+// product, so a dot product of n terms costs about half as much.
+//
+// The final reduction divides by 2^288 instead of 2^256 (nine quotient
+// digits instead of eight), which keeps it exact for large sums: with
+// m < 2^288 the result (T + m r) / 2^288 is below T / 2^288 + r, so any
+// T < r 2^288 reduces to a value below 2r.  Operands below 2r give products
+// below 4 r^2 < 2^510, so about 2^32 terms fit.  For Montgomery operands
+// a = a' 2^256, b = b' 2^256 the result is a'b' 2^224 mod r: the Montgomery
+// form of a'b' times 2^-32.  The caller multiplies by the Montgomery form
+// of 2^32 once to undo that factor (or leaves it in a value that is scaled
+// back later).
+#pragma once
+#include "fr.cuh"
+
+namespace sisu {
+
+struct FrAcc {
+  uint32_t v[17];  // little-endian words of a 544-bit integer
+};
+
+#ifdef __CUDACC__
+
+__device__ __forceinline__ FrAcc fracc_zero() {
+  FrAcc z;
+#pragma unroll
+  for (int i = 0; i < 17; ++i) z.v[i] = 0;
+  return z;
+}
+
+// Montgomery form of 2^32 (2^288 mod r): a product with it undoes the
+// 2^-32 that fr_redc288 leaves
+SISU_FR_CONST(fr_mont_2_32, 0x15b8b9dau, 0x93e78865u, 0xb05ea154u, 0x16df2426u, 0x302ab839u, 0x1271b743u,
+              0xec6c226eu, 0x06bc037eu)
+
+// acc += a * b (the full 512-bit product, no reduction)
+__device__ __forceinline__ void fracc_mac_inl(FrAcc& acc, const Fr& a, const Fr& b) {
+  uint32_t p[16];
+  // row 0: p[0..8] = a * b_0
+#pragma unroll
+  for (int k = 0; k < 8; ++k) p[k] = a.v[k] * b.v[0];
+  p[8] = __umulhi(a.v[7], b.v[0]);
+
+  asm("mad.hi.cc.u32  %0, %8, %15, %0;\n\t"
+      "madc.hi.cc.u32 %1, %9, %15, %1;\n\t"
+      "madc.hi.cc.u32 %2, %10, %15, %2;\n\t"
+      "madc.hi.cc.u32 %3, %11, %15, %3;\n\t"
+      "madc.hi.cc.u32 %4, %12, %15, %4;\n\t"
+      "madc.hi.cc.u32 %5, %13, %15, %5;\n\t"
+      "madc.hi.cc.u32 %6, %14, %15, %6;\n\t"
+      "addc.u32       %7, %7, 0;"
+      : "+r"(p[1]), "+r"(p[2]), "+r"(p[3]), "+r"(p[4]), "+r"(p[5]), "+r"(p[6]), "+r"(p[7]), "+r"(p[8])
+      : "r"(a.v[0]), "r"(a.v[1]), "r"(a.v[2]), "r"(a.v[3]), "r"(a.v[4]), "r"(a.v[5]), "r"(a.v[6]), "r"(b.v[0]));
+  // rows 1..7: p[i..i+8] += a * b_i (the top word of a row starts at 0)
+  p[9] = 0;
+  asm("mad.lo.cc.u32  %0, %9, %17, %0;\n\t"
+      "madc.lo.cc.u32 %1, %10, %17, %1;\n\t"
+      "madc.lo.cc.u32 %2, %11, %17, %2;\n\t"
+      "madc.lo.cc.u32 %3, %12, %17, %3;\n\t"
+      "madc.lo.cc.u32 %4, %13, %17, %4;\n\t"
+      "madc.lo.cc.u32 %5, %14, %17, %5;\n\t"
+      "madc.lo.cc.u32 %6, %15, %17, %6;\n\t"
+      "madc.lo.cc.u32 %7, %16, %17, %7;\n\t"
+      "addc.u32       %8, %8, 0;\n\t"
+      "mad.hi.cc.u32  %1, %9, %17, %1;\n\t"
+      "madc.hi.cc.u32 %2, %10, %17, %2;\n\t"
+      "madc.hi.cc.u32 %3, %11, %17, %3;\n\t"
+      "madc.hi.cc.u32 %4, %12, %17, %4;\n\t"
+      "madc.hi.cc.u32 %5, %13, %17, %5;\n\t"
+      "madc.hi.cc.u32 %6, %14, %17, %6;\n\t"
+      "madc.hi.cc.u32 %7, %15, %17, %7;\n\t"
+      "madc.hi.u32    %8, %16, %17, %8;"
+      : "+r"(p[1]), "+r"(p[2]), "+r"(p[3]), "+r"(p[4]), "+r"(p[5]), "+r"(p[6]), "+r"(p[7]), "+r"(p[8]), "+r"(p[9])
+      : "r"(a.v[0]), "r"(a.v[1]), "r"(a.v[2]), "r"(a.v[3]), "r"(a.v[4]), "r"(a.v[5]), "r"(a.v[6]), "r"(a.v[7]), "r"(b.v[1]));
+  p[10] = 0;
+  asm("mad.lo.cc.u32  %0, %9, %17, %0;\n\t"
+      "madc.lo.cc.u32 %1, %10, %17, %1;\n\t"
+      "madc.lo.cc.u32 %2, %11, %17, %2;\n\t"
+      "madc.lo.cc.u32 %3, %12, %17, %3;\n\t"
+      "madc.lo.cc.u32 %4, %13, %17, %4;\n\t"
+      "madc.lo.cc.u32 %5, %14, %17, %5;\n\t"
+      "madc.lo.cc.u32 %6, %15, %17, %6;\n\t"
+      "madc.lo.cc.u32 %7, %16, %17, %7;\n\t"
+      "addc.u32       %8, %8, 0;\n\t"
+      "mad.hi.cc.u32  %1, %9, %17, %1;\n\t"
+      "madc.hi.cc.u32 %2, %10, %17, %2;\n\t"
+      "madc.hi.cc.u32 %3, %11, %17, %3;\n\t"
+      "madc.hi.cc.u32 %4, %12, %17, %4;\n\t"
+      "madc.hi.cc.u32 %5, %13, %17, %5;\n\t"
+      "madc.hi.cc.u32 %6, %14, %17, %6;\n\t"
+      "madc.hi.cc.u32 %7, %15, %17, %7;\n\t"
+      "madc.hi.u32    %8, %16, %17, %8;"
+      : "+r"(p[2]), "+r"(p[3]), "+r"(p[4]), "+r"(p[5]), "+r"(p[6]), "+r"(p[7]), "+r"(p[8]), "+r"(p[9]), "+r"(p[10])
+      : "r"(a.v[0]), "r"(a.v[1]), "r"(a.v[2]), "r"(a.v[3]), "r"(a.v[4]), "r"(a.v[5]), "r"(a.v[6]), "r"(a.v[7]), "r"(b.v[2]));
+  p[11] = 0;
+  asm("mad.lo.cc.u32  %0, %9, %17, %0;\n\t"
+      "madc.lo.cc.u32 %1, %10, %17, %1;\n\t"
+      "madc.lo.cc.u32 %2, %11, %17, %2;\n\t"
+      "madc.lo.cc.u32 %3, %12, %17, %3;\n\t"
+      "madc.lo.cc.u32 %4, %13, %17, %4;\n\t"
+      "madc.lo.cc.u32 %5, %14, %17, %5;\n\t"
+      "madc.lo.cc.u32 %6, %15, %17, %6;\n\t"
+      "madc.lo.cc.u32 %7, %16, %17, %7;\n\t"
+      "addc.u32       %8, %8, 0;\n\t"
+      "mad.hi.cc.u32  %1, %9, %17, %1;\n\t"
+      "madc.hi.cc.u32 %2, %10, %17, %2;\n\t"
+      "madc.hi.cc.u32 %3, %11, %17, %3;\n\t"
+      "madc.hi.cc.u32 %4, %12, %17, %4;\n\t"
+      "madc.hi.cc.u32 %5, %13, %17, %5;\n\t"
+      "madc.hi.cc.u32 %6, %14, %17, %6;\n\t"
+      "madc.hi.cc.u32 %7, %15, %17, %7;\n\t"
+      "madc.hi.u32    %8, %16, %17, %8;"
+      : "+r"(p[3]), "+r"(p[4]), "+r"(p[5]), "+r"(p[6]), "+r"(p[7]), "+r"(p[8]), "+r"(p[9]), "+r"(p[10]), "+r"(p[11])
+      : "r"(a.v[0]), "r"(a.v[1]), "r"(a.v[2]), "r"(a.v[3]), "r"(a.v[4]), "r"(a.v[5]), "r"(a.v[6]), "r"(a.v[7]), "r"(b.v[3]));
+  p[12] = 0;
+  asm("mad.lo.cc.u32  %0, %9, %17, %0;\n\t"
+      "madc.lo.cc.u32 %1, %10, %17, %1;\n\t"
+      "madc.lo.cc.u32 %2, %11, %17, %2;\n\t"
+      "madc.lo.cc.u32 %3, %12, %17, %3;\n\t"
+      "madc.lo.cc.u32 %4, %13, %17, %4;\n\t"
+      "madc.lo.cc.u32 %5, %14, %17, %5;\n\t"
+      "madc.lo.cc.u32 %6, %15, %17, %6;\n\t"
+      "madc.lo.cc.u32 %7, %16, %17, %7;\n\t"
+      "addc.u32       %8, %8, 0;\n\t"
+      "mad.hi.cc.u32  %1, %9, %17, %1;\n\t"
+      "madc.hi.cc.u32 %2, %10, %17, %2;\n\t"
+      "madc.hi.cc.u32 %3, %11, %17, %3;\n\t"
+      "madc.hi.cc.u32 %4, %12, %17, %4;\n\t"
+      "madc.hi.cc.u32 %5, %13, %17, %5;\n\t"
+      "madc.hi.cc.u32 %6, %14, %17, %6;\n\t"
+      "madc.hi.cc.u32 %7, %15, %17, %7;\n\t"
+      "madc.hi.u32    %8, %16, %17, %8;"
+      : "+r"(p[4]), "+r"(p[5]), "+r"(p[6]), "+r"(p[7]), "+r"(p[8]), "+r"(p[9]), "+r"(p[10]), "+r"(p[11]), "+r"(p[12])
+      : "r"(a.v[0]), "r"(a.v[1]), "r"(a.v[2]), "r"(a.v[3]), "r"(a.v[4]), "r"(a.v[5]), "r"(a.v[6]), "r"(a.v[7]), "r"(b.v[4]));
+  p[13] = 0;
+  asm("mad.lo.cc.u32  %0, %9, %17, %0;\n\t"
+      "madc.lo.cc.u32 %1, %10, %17, %1;\n\t"
+      "madc.lo.cc.u32 %2, %11, %17, %2;\n\t"
+      "madc.lo.cc.u32 %3, %12, %17, %3;\n\t"
+      "madc.lo.cc.u32 %4, %13, %17, %4;\n\t"
+      "madc.lo.cc.u32 %5, %14, %17, %5;\n\t"
+      "madc.lo.cc.u32 %6, %15, %17, %6;\n\t"
+      "madc.lo.cc.u32 %7, %16, %17, %7;\n\t"
+      "addc.u32       %8, %8, 0;\n\t"
+      "mad.hi.cc.u32  %1, %9, %17, %1;\n\t"
+      "madc.hi.cc.u32 %2, %10, %17, %2;\n\t"
+      "madc.hi.cc.u32 %3, %11, %17, %3;\n\t"
+      "madc.hi.cc.u32 %4, %12, %17, %4;\n\t"
+      "madc.hi.cc.u32 %5, %13, %17, %5;\n\t"
+      "madc.hi.cc.u32 %6, %14, %17, %6;\n\t"
+      "madc.hi.cc.u32 %7, %15, %17, %7;\n\t"
+      "madc.hi.u32    %8, %16, %17, %8;"
+      : "+r"(p[5]), "+r"(p[6]), "+r"(p[7]), "+r"(p[8]), "+r"(p[9]), "+r"(p[10]), "+r"(p[11]), "+r"(p[12]), "+r"(p[13])
+      : "r"(a.v[0]), "r"(a.v[1]), "r"(a.v[2]), "r"(a.v[3]), "r"(a.v[4]), "r"(a.v[5]), "r"(a.v[6]), "r"(a.v[7]), "r"(b.v[5]));
+  p[14] = 0;
+  asm("mad.lo.cc.u32  %0, %9, %17, %0;\n\t"
+      "madc.lo.cc.u32 %1, %10, %17, %1;\n\t"
+      "madc.lo.cc.u32 %2, %11, %17, %2;\n\t"
+      "madc.lo.cc.u32 %3, %12, %17, %3;\n\t"
+      "madc.lo.cc.u32 %4, %13, %17, %4;\n\t"
+      "madc.lo.cc.u32 %5, %14, %17, %5;\n\t"
+      "madc.lo.cc.u32 %6, %15, %17, %6;\n\t"
+      "madc.lo.cc.u32 %7, %16, %17, %7;\n\t"
+      "addc.u32       %8, %8, 0;\n\t"
+      "mad.hi.cc.u32  %1, %9, %17, %1;\n\t"
+      "madc.hi.cc.u32 %2, %10, %17, %2;\n\t"
+      "madc.hi.cc.u32 %3, %11, %17, %3;\n\t"
+      "madc.hi.cc.u32 %4, %12, %17, %4;\n\t"
+      "madc.hi.cc.u32 %5, %13, %17, %5;\n\t"
+      "madc.hi.cc.u32 %6, %14, %17, %6;\n\t"
+      "madc.hi.cc.u32 %7, %15, %17, %7;\n\t"
+      "madc.hi.u32    %8, %16, %17, %8;"
+      : "+r"(p[6]), "+r"(p[7]), "+r"(p[8]), "+r"(p[9]), "+r"(p[10]), "+r"(p[11]), "+r"(p[12]), "+r"(p[13]), "+r"(p[14])
+      : "r"(a.v[0]), "r"(a.v[1]), "r"(a.v[2]), "r"(a.v[3]), "r"(a.v[4]), "r"(a.v[5]), "r"(a.v[6]), "r"(a.v[7]), "r"(b.v[6]));
+  p[15] = 0;
+  asm("mad.lo.cc.u32  %0, %9, %17, %0;\n\t"
+      "madc.lo.cc.u32 %1, %10, %17, %1;\n\t"
+      "madc.lo.cc.u32 %2, %11, %17, %2;\n\t"
+      "madc.lo.cc.u32 %3, %12, %17, %3;\n\t"
+      "madc.lo.cc.u32 %4, %13, %17, %4;\n\t"
+      "madc.lo.cc.u32 %5, %14, %17, %5;\n\t"
+      "madc.lo.cc.u32 %6, %15, %17, %6;\n\t"
+      "madc.lo.cc.u32 %7, %16, %17, %7;\n\t"
+      "addc.u32       %8, %8, 0;\n\t"
+      "mad.hi.cc.u32  %1, %9, %17, %1;\n\t"
+      "madc.hi.cc.u32 %2, %10, %17, %2;\n\t"
+      "madc.hi.cc.u32 %3, %11, %17, %3;\n\t"
+      "madc.hi.cc.u32 %4, %12, %17, %4;\n\t"
+      "madc.hi.cc.u32 %5, %13, %17, %5;\n\t"
+      "madc.hi.cc.u32 %6, %14, %17, %6;\n\t"
+      "madc.hi.cc.u32 %7, %15, %17, %7;\n\t"
+      "madc.hi.u32    %8, %16, %17, %8;"
+      : "+r"(p[7]), "+r"(p[8]), "+r"(p[9]), "+r"(p[10]), "+r"(p[11]), "+r"(p[12]), "+r"(p[13]), "+r"(p[14]), "+r"(p[15])
+      : "r"(a.v[0]), "r"(a.v[1]), "r"(a.v[2]), "r"(a.v[3]), "r"(a.v[4]), "r"(a.v[5]), "r"(a.v[6]), "r"(a.v[7]), "r"(b.v[7]));
+  // acc += p
+  asm("add.cc.u32  %0, %0, %17;\n\t"
+      "addc.cc.u32 %1, %1, %18;\n\t"
+      "addc.cc.u32 %2, %2, %19;\n\t"
+      "addc.cc.u32 %3, %3, %20;\n\t"
+      "addc.cc.u32 %4, %4, %21;\n\t"
+      "addc.cc.u32 %5, %5, %22;\n\t"
+      "addc.cc.u32 %6, %6, %23;\n\t"
+      "addc.cc.u32 %7, %7, %24;\n\t"
+      "addc.cc.u32 %8, %8, %25;\n\t"
+      "addc.cc.u32 %9, %9, %26;\n\t"
+      "addc.cc.u32 %10, %10, %27;\n\t"
+      "addc.cc.u32 %11, %11, %28;\n\t"
+      "addc.cc.u32 %12, %12, %29;\n\t"
+      "addc.cc.u32 %13, %13, %30;\n\t"
+      "addc.cc.u32 %14, %14, %31;\n\t"
+      "addc.cc.u32 %15, %15, %32;\n\t"
+      "addc.u32    %16, %16, 0;"
+      : "+r"(acc.v[0]), "+r"(acc.v[1]), "+r"(acc.v[2]), "+r"(acc.v[3]), "+r"(acc.v[4]), "+r"(acc.v[5]), "+r"(acc.v[6]), "+r"(acc.v[7]), "+r"(acc.v[8]), "+r"(acc.v[9]), "+r"(acc.v[10]), "+r"(acc.v[11]), "+r"(acc.v[12]), "+r"(acc.v[13]), "+r"(acc.v[14]), "+r"(acc.v[15]), "+r"(acc.v[16])
+      : "r"(p[0]), "r"(p[1]), "r"(p[2]), "r"(p[3]), "r"(p[4]), "r"(p[5]), "r"(p[6]), "r"(p[7]), "r"(p[8]), "r"(p[9]), "r"(p[10]), "r"(p[11]), "r"(p[12]), "r"(p[13]), "r"(p[14]), "r"(p[15]));
+}
+
+// x += y (544-bit integers; the sum must fit)
+__device__ __forceinline__ void fracc_add(FrAcc& x, const FrAcc& y) {
+
+  asm("add.cc.u32  %0, %0, %17;\n\t"
+      "addc.cc.u32 %1, %1, %18;\n\t"
+      "addc.cc.u32 %2, %2, %19;\n\t"
+      "addc.cc.u32 %3, %3, %20;\n\t"
+      "addc.cc.u32 %4, %4, %21;\n\t"
+      "addc.cc.u32 %5, %5, %22;\n\t"
+      "addc.cc.u32 %6, %6, %23;\n\t"
+      "addc.cc.u32 %7, %7, %24;\n\t"
+      "addc.cc.u32 %8, %8, %25;\n\t"
+      "addc.cc.u32 %9, %9, %26;\n\t"
+      "addc.cc.u32 %10, %10, %27;\n\t"
+      "addc.cc.u32 %11, %11, %28;\n\t"
+      "addc.cc.u32 %12, %12, %29;\n\t"
+      "addc.cc.u32 %13, %13, %30;\n\t"
+      "addc.cc.u32 %14, %14, %31;\n\t"
+      "addc.cc.u32 %15, %15, %32;\n\t"
+      "addc.u32    %16, %16, %33;"
+      : "+r"(x.v[0]), "+r"(x.v[1]), "+r"(x.v[2]), "+r"(x.v[3]), "+r"(x.v[4]), "+r"(x.v[5]), "+r"(x.v[6]), "+r"(x.v[7]), "+r"(x.v[8]), "+r"(x.v[9]), "+r"(x.v[10]), "+r"(x.v[11]), "+r"(x.v[12]), "+r"(x.v[13]), "+r"(x.v[14]), "+r"(x.v[15]), "+r"(x.v[16])
+      : "r"(y.v[0]), "r"(y.v[1]), "r"(y.v[2]), "r"(y.v[3]), "r"(y.v[4]), "r"(y.v[5]), "r"(y.v[6]), "r"(y.v[7]), "r"(y.v[8]), "r"(y.v[9]), "r"(y.v[10]), "r"(y.v[11]), "r"(y.v[12]), "r"(y.v[13]), "r"(y.v[14]), "r"(y.v[15]), "r"(y.v[16]));
+}
+
+// T * 2^-288 mod r, in [0, 2r), for T < r 2^288: nine Montgomery steps, each
+// adding the multiple m r of r that zeroes the lowest remaining word, with
+// the carries rippling to the top word.  The result is the top eight words.
+__device__ __forceinline__ Fr fr_redc288(const FrAcc& acc) {
+  uint32_t t[17];
+#pragma unroll
+  for (int i = 0; i < 17; ++i) t[i] = acc.v[i];
+  // step 0: zero t[0]
+  asm("{\n\t"
+      ".reg .u32 m;\n\t"
+      "mul.lo.u32 m, %0, 0xefffffff;\n\t"
+      "mad.lo.cc.u32  %0, m, 0xf0000001, %0;\n\t"
+      "madc.lo.cc.u32 %1, m, 0x43e1f593, %1;\n\t"
+      "madc.lo.cc.u32 %2, m, 0x79b97091, %2;\n\t"
+      "madc.lo.cc.u32 %3, m, 0x2833e848, %3;\n\t"
+      "madc.lo.cc.u32 %4, m, 0x8181585d, %4;\n\t"
+      "madc.lo.cc.u32 %5, m, 0xb85045b6, %5;\n\t"
+      "madc.lo.cc.u32 %6, m, 0xe131a029, %6;\n\t"
+      "madc.lo.cc.u32 %7, m, 0x30644e72, %7;\n\t"
+      "addc.cc.u32    %8, %8, 0;\n\t"
+      "addc.cc.u32    %9, %9, 0;\n\t"
+      "addc.cc.u32    %10, %10, 0;\n\t"
+      "addc.cc.u32    %11, %11, 0;\n\t"
+      "addc.cc.u32    %12, %12, 0;\n\t"
+      "addc.cc.u32    %13, %13, 0;\n\t"
+      "addc.cc.u32    %14, %14, 0;\n\t"
+      "addc.cc.u32    %15, %15, 0;\n\t"
+      "addc.u32       %16, %16, 0;\n\t"
+      "mad.hi.cc.u32  %1, m, 0xf0000001, %1;\n\t"
+      "madc.hi.cc.u32 %2, m, 0x43e1f593, %2;\n\t"
+      "madc.hi.cc.u32 %3, m, 0x79b97091, %3;\n\t"
+      "madc.hi.cc.u32 %4, m, 0x2833e848, %4;\n\t"
+      "madc.hi.cc.u32 %5, m, 0x8181585d, %5;\n\t"
+      "madc.hi.cc.u32 %6, m, 0xb85045b6, %6;\n\t"
+      "madc.hi.cc.u32 %7, m, 0xe131a029, %7;\n\t"
+      "madc.hi.cc.u32 %8, m, 0x30644e72, %8;\n\t"
+      "addc.cc.u32    %9, %9, 0;\n\t"
+      "addc.cc.u32    %10, %10, 0;\n\t"
+      "addc.cc.u32    %11, %11, 0;\n\t"
+      "addc.cc.u32    %12, %12, 0;\n\t"
+      "addc.cc.u32    %13, %13, 0;\n\t"
+      "addc.cc.u32    %14, %14, 0;\n\t"
+      "addc.cc.u32    %15, %15, 0;\n\t"
+      "addc.u32       %16, %16, 0;\n\t"
+      "}"
+      : "+r"(t[0]), "+r"(t[1]), "+r"(t[2]), "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]), "+r"(t[7]), "+r"(t[8]), "+r"(t[9]), "+r"(t[10]), "+r"(t[11]), "+r"(t[12]), "+r"(t[13]), "+r"(t[14]), "+r"(t[15]), "+r"(t[16]));
+  // step 1: zero t[1]
+  asm("{\n\t"
+      ".reg .u32 m;\n\t"
+      "mul.lo.u32 m, %0, 0xefffffff;\n\t"
+      "mad.lo.cc.u32  %0, m, 0xf0000001, %0;\n\t"
+      "madc.lo.cc.u32 %1, m, 0x43e1f593, %1;\n\t"
+      "madc.lo.cc.u32 %2, m, 0x79b97091, %2;\n\t"
+      "madc.lo.cc.u32 %3, m, 0x2833e848, %3;\n\t"
+      "madc.lo.cc.u32 %4, m, 0x8181585d, %4;\n\t"
+      "madc.lo.cc.u32 %5, m, 0xb85045b6, %5;\n\t"
+      "madc.lo.cc.u32 %6, m, 0xe131a029, %6;\n\t"
+      "madc.lo.cc.u32 %7, m, 0x30644e72, %7;\n\t"
+      "addc.cc.u32    %8, %8, 0;\n\t"
+      "addc.cc.u32    %9, %9, 0;\n\t"
+      "addc.cc.u32    %10, %10, 0;\n\t"
+      "addc.cc.u32    %11, %11, 0;\n\t"
+      "addc.cc.u32    %12, %12, 0;\n\t"
+      "addc.cc.u32    %13, %13, 0;\n\t"
+      "addc.cc.u32    %14, %14, 0;\n\t"
+      "addc.u32       %15, %15, 0;\n\t"
+      "mad.hi.cc.u32  %1, m, 0xf0000001, %1;\n\t"
+      "madc.hi.cc.u32 %2, m, 0x43e1f593, %2;\n\t"
+      "madc.hi.cc.u32 %3, m, 0x79b97091, %3;\n\t"
+      "madc.hi.cc.u32 %4, m, 0x2833e848, %4;\n\t"
+      "madc.hi.cc.u32 %5, m, 0x8181585d, %5;\n\t"
+      "madc.hi.cc.u32 %6, m, 0xb85045b6, %6;\n\t"
+      "madc.hi.cc.u32 %7, m, 0xe131a029, %7;\n\t"
+      "madc.hi.cc.u32 %8, m, 0x30644e72, %8;\n\t"
+      "addc.cc.u32    %9, %9, 0;\n\t"
+      "addc.cc.u32    %10, %10, 0;\n\t"
+      "addc.cc.u32    %11, %11, 0;\n\t"
+      "addc.cc.u32    %12, %12, 0;\n\t"
+      "addc.cc.u32    %13, %13, 0;\n\t"
+      "addc.cc.u32    %14, %14, 0;\n\t"
+      "addc.u32       %15, %15, 0;\n\t"
+      "}"
+      : "+r"(t[1]), "+r"(t[2]), "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]), "+r"(t[7]), "+r"(t[8]), "+r"(t[9]), "+r"(t[10]), "+r"(t[11]), "+r"(t[12]), "+r"(t[13]), "+r"(t[14]), "+r"(t[15]), "+r"(t[16]));
+  // step 2: zero t[2]
+  asm("{\n\t"
+      ".reg .u32 m;\n\t"
+      "mul.lo.u32 m, %0, 0xefffffff;\n\t"
+      "mad.lo.cc.u32  %0, m, 0xf0000001, %0;\n\t"
+      "madc.lo.cc.u32 %1, m, 0x43e1f593, %1;\n\t"
+      "madc.lo.cc.u32 %2, m, 0x79b97091, %2;\n\t"
+      "madc.lo.cc.u32 %3, m, 0x2833e848, %3;\n\t"
+      "madc.lo.cc.u32 %4, m, 0x8181585d, %4;\n\t"
+      "madc.lo.cc.u32 %5, m, 0xb85045b6, %5;\n\t"
+      "madc.lo.cc.u32 %6, m, 0xe131a029, %6;\n\t"
+      "madc.lo.cc.u32 %7, m, 0x30644e72, %7;\n\t"
+      "addc.cc.u32    %8, %8, 0;\n\t"
+      "addc.cc.u32    %9, %9, 0;\n\t"
+      "addc.cc.u32    %10, %10, 0;\n\t"
+      "addc.cc.u32    %11, %11, 0;\n\t"
+      "addc.cc.u32    %12, %12, 0;\n\t"
+      "addc.cc.u32    %13, %13, 0;\n\t"
+      "addc.u32       %14, %14, 0;\n\t"
+      "mad.hi.cc.u32  %1, m, 0xf0000001, %1;\n\t"
+      "madc.hi.cc.u32 %2, m, 0x43e1f593, %2;\n\t"
+      "madc.hi.cc.u32 %3, m, 0x79b97091, %3;\n\t"
+      "madc.hi.cc.u32 %4, m, 0x2833e848, %4;\n\t"
+      "madc.hi.cc.u32 %5, m, 0x8181585d, %5;\n\t"
+      "madc.hi.cc.u32 %6, m, 0xb85045b6, %6;\n\t"
+      "madc.hi.cc.u32 %7, m, 0xe131a029, %7;\n\t"
+      "madc.hi.cc.u32 %8, m, 0x30644e72, %8;\n\t"
+      "addc.cc.u32    %9, %9, 0;\n\t"
+      "addc.cc.u32    %10, %10, 0;\n\t"
+      "addc.cc.u32    %11, %11, 0;\n\t"
+      "addc.cc.u32    %12, %12, 0;\n\t"
+      "addc.cc.u32    %13, %13, 0;\n\t"
+      "addc.u32       %14, %14, 0;\n\t"
+      "}"
+      : "+r"(t[2]), "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]), "+r"(t[7]), "+r"(t[8]), "+r"(t[9]), "+r"(t[10]), "+r"(t[11]), "+r"(t[12]), "+r"(t[13]), "+r"(t[14]), "+r"(t[15]), "+r"(t[16]));
+  // step 3: zero t[3]
+  asm("{\n\t"
+      ".reg .u32 m;\n\t"
+      "mul.lo.u32 m, %0, 0xefffffff;\n\t"
+      "mad.lo.cc.u32  %0, m, 0xf0000001, %0;\n\t"
+      "madc.lo.cc.u32 %1, m, 0x43e1f593, %1;\n\t"
+      "madc.lo.cc.u32 %2, m, 0x79b97091, %2;\n\t"
+      "madc.lo.cc.u32 %3, m, 0x2833e848, %3;\n\t"
+      "madc.lo.cc.u32 %4, m, 0x8181585d, %4;\n\t"
+      "madc.lo.cc.u32 %5, m, 0xb85045b6, %5;\n\t"
+      "madc.lo.cc.u32 %6, m, 0xe131a029, %6;\n\t"
+      "madc.lo.cc.u32 %7, m, 0x30644e72, %7;\n\t"
+      "addc.cc.u32    %8, %8, 0;\n\t"
+      "addc.cc.u32    %9, %9, 0;\n\t"
+      "addc.cc.u32    %10, %10, 0;\n\t"
+      "addc.cc.u32    %11, %11, 0;\n\t"
+      "addc.cc.u32    %12, %12, 0;\n\t"
+      "addc.u32       %13, %13, 0;\n\t"
+      "mad.hi.cc.u32  %1, m, 0xf0000001, %1;\n\t"
+      "madc.hi.cc.u32 %2, m, 0x43e1f593, %2;\n\t"
+      "madc.hi.cc.u32 %3, m, 0x79b97091, %3;\n\t"
+      "madc.hi.cc.u32 %4, m, 0x2833e848, %4;\n\t"
+      "madc.hi.cc.u32 %5, m, 0x8181585d, %5;\n\t"
+      "madc.hi.cc.u32 %6, m, 0xb85045b6, %6;\n\t"
+      "madc.hi.cc.u32 %7, m, 0xe131a029, %7;\n\t"
+      "madc.hi.cc.u32 %8, m, 0x30644e72, %8;\n\t"
+      "addc.cc.u32    %9, %9, 0;\n\t"
+      "addc.cc.u32    %10, %10, 0;\n\t"
+      "addc.cc.u32    %11, %11, 0;\n\t"
+      "addc.cc.u32    %12, %12, 0;\n\t"
+      "addc.u32       %13, %13, 0;\n\t"
+      "}"
+      : "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]), "+r"(t[7]), "+r"(t[8]), "+r"(t[9]), "+r"(t[10]), "+r"(t[11]), "+r"(t[12]), "+r"(t[13]), "+r"(t[14]), "+r"(t[15]), "+r"(t[16]));
+  // step 4: zero t[4]
+  asm("{\n\t"
+      ".reg .u32 m;\n\t"
+      "mul.lo.u32 m, %0, 0xefffffff;\n\t"
+      "mad.lo.cc.u32  %0, m, 0xf0000001, %0;\n\t"
+      "madc.lo.cc.u32 %1, m, 0x43e1f593, %1;\n\t"
+      "madc.lo.cc.u32 %2, m, 0x79b97091, %2;\n\t"
+      "madc.lo.cc.u32 %3, m, 0x2833e848, %3;\n\t"
+      "madc.lo.cc.u32 %4, m, 0x8181585d, %4;\n\t"
+      "madc.lo.cc.u32 %5, m, 0xb85045b6, %5;\n\t"
+      "madc.lo.cc.u32 %6, m, 0xe131a029, %6;\n\t"
+      "madc.lo.cc.u32 %7, m, 0x30644e72, %7;\n\t"
+      "addc.cc.u32    %8, %8, 0;\n\t"
+      "addc.cc.u32    %9, %9, 0;\n\t"
+      "addc.cc.u32    %10, %10, 0;\n\t"
+      "addc.cc.u32    %11, %11, 0;\n\t"
+      "addc.u32       %12, %12, 0;\n\t"
+      "mad.hi.cc.u32  %1, m, 0xf0000001, %1;\n\t"
+      "madc.hi.cc.u32 %2, m, 0x43e1f593, %2;\n\t"
+      "madc.hi.cc.u32 %3, m, 0x79b97091, %3;\n\t"
+      "madc.hi.cc.u32 %4, m, 0x2833e848, %4;\n\t"
+      "madc.hi.cc.u32 %5, m, 0x8181585d, %5;\n\t"
+      "madc.hi.cc.u32 %6, m, 0xb85045b6, %6;\n\t"
+      "madc.hi.cc.u32 %7, m, 0xe131a029, %7;\n\t"
+      "madc.hi.cc.u32 %8, m, 0x30644e72, %8;\n\t"
+      "addc.cc.u32    %9, %9, 0;\n\t"
+      "addc.cc.u32    %10, %10, 0;\n\t"
+      "addc.cc.u32    %11, %11, 0;\n\t"
+      "addc.u32       %12, %12, 0;\n\t"
+      "}"
+      : "+r"(t[4]), "+r"(t[5]), "+r"(t[6]), "+r"(t[7]), "+r"(t[8]), "+r"(t[9]), "+r"(t[10]), "+r"(t[11]), "+r"(t[12]), "+r"(t[13]), "+r"(t[14]), "+r"(t[15]), "+r"(t[16]));
+  // step 5: zero t[5]
+  asm("{\n\t"
+      ".reg .u32 m;\n\t"
+      "mul.lo.u32 m, %0, 0xefffffff;\n\t"
+      "mad.lo.cc.u32  %0, m, 0xf0000001, %0;\n\t"
+      "madc.lo.cc.u32 %1, m, 0x43e1f593, %1;\n\t"
+      "madc.lo.cc.u32 %2, m, 0x79b97091, %2;\n\t"
+      "madc.lo.cc.u32 %3, m, 0x2833e848, %3;\n\t"
+      "madc.lo.cc.u32 %4, m, 0x8181585d, %4;\n\t"
+      "madc.lo.cc.u32 %5, m, 0xb85045b6, %5;\n\t"
+      "madc.lo.cc.u32 %6, m, 0xe131a029, %6;\n\t"
+      "madc.lo.cc.u32 %7, m, 0x30644e72, %7;\n\t"
+      "addc.cc.u32    %8, %8, 0;\n\t"
+      "addc.cc.u32    %9, %9, 0;\n\t"
+      "addc.cc.u32    %10, %10, 0;\n\t"
+      "addc.u32       %11, %11, 0;\n\t"
+      "mad.hi.cc.u32  %1, m, 0xf0000001, %1;\n\t"
+      "madc.hi.cc.u32 %2, m, 0x43e1f593, %2;\n\t"
+      "madc.hi.cc.u32 %3, m, 0x79b97091, %3;\n\t"
+      "madc.hi.cc.u32 %4, m, 0x2833e848, %4;\n\t"
+      "madc.hi.cc.u32 %5, m, 0x8181585d, %5;\n\t"
+      "madc.hi.cc.u32 %6, m, 0xb85045b6, %6;\n\t"
+      "madc.hi.cc.u32 %7, m, 0xe131a029, %7;\n\t"
+      "madc.hi.cc.u32 %8, m, 0x30644e72, %8;\n\t"
+      "addc.cc.u32    %9, %9, 0;\n\t"
+      "addc.cc.u32    %10, %10, 0;\n\t"
+      "addc.u32       %11, %11, 0;\n\t"
+      "}"
+      : "+r"(t[5]), "+r"(t[6]), "+r"(t[7]), "+r"(t[8]), "+r"(t[9]), "+r"(t[10]), "+r"(t[11]), "+r"(t[12]), "+r"(t[13]), "+r"(t[14]), "+r"(t[15]), "+r"(t[16]));
+  // step 6: zero t[6]
+  asm("{\n\t"
+      ".reg .u32 m;\n\t"
+      "mul.lo.u32 m, %0, 0xefffffff;\n\t"
+      "mad.lo.cc.u32  %0, m, 0xf0000001, %0;\n\t"
+      "madc.lo.cc.u32 %1, m, 0x43e1f593, %1;\n\t"
+      "madc.lo.cc.u32 %2, m, 0x79b97091, %2;\n\t"
+      "madc.lo.cc.u32 %3, m, 0x2833e848, %3;\n\t"
+      "madc.lo.cc.u32 %4, m, 0x8181585d, %4;\n\t"
+      "madc.lo.cc.u32 %5, m, 0xb85045b6, %5;\n\t"
+      "madc.lo.cc.u32 %6, m, 0xe131a029, %6;\n\t"
+      "madc.lo.cc.u32 %7, m, 0x30644e72, %7;\n\t"
+      "addc.cc.u32    %8, %8, 0;\n\t"
+      "addc.cc.u32    %9, %9, 0;\n\t"
+      "addc.u32       %10, %10, 0;\n\t"
+      "mad.hi.cc.u32  %1, m, 0xf0000001, %1;\n\t"
+      "madc.hi.cc.u32 %2, m, 0x43e1f593, %2;\n\t"
+      "madc.hi.cc.u32 %3, m, 0x79b97091, %3;\n\t"
+      "madc.hi.cc.u32 %4, m, 0x2833e848, %4;\n\t"
+      "madc.hi.cc.u32 %5, m, 0x8181585d, %5;\n\t"
+      "madc.hi.cc.u32 %6, m, 0xb85045b6, %6;\n\t"
+      "madc.hi.cc.u32 %7, m, 0xe131a029, %7;\n\t"
+      "madc.hi.cc.u32 %8, m, 0x30644e72, %8;\n\t"
+      "addc.cc.u32    %9, %9, 0;\n\t"
+      "addc.u32       %10, %10, 0;\n\t"
+      "}"
+      : "+r"(t[6]), "+r"(t[7]), "+r"(t[8]), "+r"(t[9]), "+r"(t[10]), "+r"(t[11]), "+r"(t[12]), "+r"(t[13]), "+r"(t[14]), "+r"(t[15]), "+r"(t[16]));
+  // step 7: zero t[7]
+  asm("{\n\t"
+      ".reg .u32 m;\n\t"
+      "mul.lo.u32 m, %0, 0xefffffff;\n\t"
+      "mad.lo.cc.u32  %0, m, 0xf0000001, %0;\n\t"
+      "madc.lo.cc.u32 %1, m, 0x43e1f593, %1;\n\t"
+      "madc.lo.cc.u32 %2, m, 0x79b97091, %2;\n\t"
+      "madc.lo.cc.u32 %3, m, 0x2833e848, %3;\n\t"
+      "madc.lo.cc.u32 %4, m, 0x8181585d, %4;\n\t"
+      "madc.lo.cc.u32 %5, m, 0xb85045b6, %5;\n\t"
+      "madc.lo.cc.u32 %6, m, 0xe131a029, %6;\n\t"
+      "madc.lo.cc.u32 %7, m, 0x30644e72, %7;\n\t"
+      "addc.cc.u32    %8, %8, 0;\n\t"
+      "addc.u32       %9, %9, 0;\n\t"
+      "mad.hi.cc.u32  %1, m, 0xf0000001, %1;\n\t"
+      "madc.hi.cc.u32 %2, m, 0x43e1f593, %2;\n\t"
+      "madc.hi.cc.u32 %3, m, 0x79b97091, %3;\n\t"
+      "madc.hi.cc.u32 %4, m, 0x2833e848, %4;\n\t"
+      "madc.hi.cc.u32 %5, m, 0x8181585d, %5;\n\t"
+      "madc.hi.cc.u32 %6, m, 0xb85045b6, %6;\n\t"
+      "madc.hi.cc.u32 %7, m, 0xe131a029, %7;\n\t"
+      "madc.hi.cc.u32 %8, m, 0x30644e72, %8;\n\t"
+      "addc.u32       %9, %9, 0;\n\t"
+      "}"
+      : "+r"(t[7]), "+r"(t[8]), "+r"(t[9]), "+r"(t[10]), "+r"(t[11]), "+r"(t[12]), "+r"(t[13]), "+r"(t[14]), "+r"(t[15]), "+r"(t[16]));
+  // step 8: zero t[8]
+  asm("{\n\t"
+      ".reg .u32 m;\n\t"
+      "mul.lo.u32 m, %0, 0xefffffff;\n\t"
+      "mad.lo.cc.u32  %0, m, 0xf0000001, %0;\n\t"
+      "madc.lo.cc.u32 %1, m, 0x43e1f593, %1;\n\t"
+      "madc.lo.cc.u32 %2, m, 0x79b97091, %2;\n\t"
+      "madc.lo.cc.u32 %3, m, 0x2833e848, %3;\n\t"
+      "madc.lo.cc.u32 %4, m, 0x8181585d, %4;\n\t"
+      "madc.lo.cc.u32 %5, m, 0xb85045b6, %5;\n\t"
+      "madc.lo.cc.u32 %6, m, 0xe131a029, %6;\n\t"
+      "madc.lo.cc.u32 %7, m, 0x30644e72, %7;\n\t"
+      "addc.u32       %8, %8, 0;\n\t"
+      "mad.hi.cc.u32  %1, m, 0xf0000001, %1;\n\t"
+      "madc.hi.cc.u32 %2, m, 0x43e1f593, %2;\n\t"
+      "madc.hi.cc.u32 %3, m, 0x79b97091, %3;\n\t"
+      "madc.hi.cc.u32 %4, m, 0x2833e848, %4;\n\t"
+      "madc.hi.cc.u32 %5, m, 0x8181585d, %5;\n\t"
+      "madc.hi.cc.u32 %6, m, 0xb85045b6, %6;\n\t"
+      "madc.hi.cc.u32 %7, m, 0xe131a029, %7;\n\t"
+      "madc.hi.u32    %8, m, 0x30644e72, %8;\n\t"
+      "}"
+      : "+r"(t[8]), "+r"(t[9]), "+r"(t[10]), "+r"(t[11]), "+r"(t[12]), "+r"(t[13]), "+r"(t[14]), "+r"(t[15]), "+r"(t[16]));
+  Fr o;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) o.v[i] = t[9 + i];
+  return o;
+}
+
+// one out-of-line copy per translation unit (see fr_mul_call); operands and
+// result travel in registers
+static __device__ __noinline__ FrAcc fracc_mac_call(FrAcc acc, Fr a, Fr b) {
+  fracc_mac_inl(acc, a, b);
+  return acc;
+}
+
+__device__ __forceinline__ void fracc_mac(FrAcc& acc, const Fr& a, const Fr& b) { acc = fracc_mac_call(acc, a, b); }
+
+#endif  // __CUDACC__
+}  // namespace sisu

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 
+#include "fr_wide.cuh"
 #include "internal.h"
 #include "launch.cuh"
 #include "sha256.cuh"
@@ -296,9 +297,16 @@ int launch_layer_init(DevState* S, uint32_t layer, uint32_t c, uint32_t s_i, con
 // copy-phase round (degree 3 in the bound copy variable):
 //   g(t) = sum_{j < h} E_t(j) sum_g w(g) op_g(T_t(j, in1 g), T_t(j, in2 g)),  t = 0..3
 // with X_t(j) = X(j) + t (X(j + h) - X(j)).  Per pair the gate sum S_j(t)
-// is quadratic in t: S_j(0..2) are summed directly and
-// S_j(3) = S_j(0) - 3 S_j(1) + 3 S_j(2).  A mul gate costs five products
-// (w x_t is affine in t, so w x_2 = 2 w x_1 - w x_0), an add gate two.
+// is quadratic in t, S_j(t) = S_j(0) + (S_j(1) - S_j(0) - c_j) t + c_j t^2,
+// so S_j(0), S_j(1) and the t^2 coefficient c_j fix it:
+//   S_j(2) = 2 S_j(1) - S_j(0) + 2 c_j,  S_j(3) = 3 S_j(1) - 2 S_j(0) + 6 c_j.
+// A mul gate w x_t y_t adds w x_0 y_0, w x_1 y_1 and (w x_1 - w x_0)(y_1 - y_0)
+// (its t^2 coefficient); an add gate w (x_t + y_t) is affine in t and adds
+// only to the first two.  The three sums are lazily reduced: each thread
+// adds full 512-bit products (fracc_mac) and reduces once per pair segment,
+// so a mul gate costs two Montgomery products and three full products, an
+// add gate two full products.  The reduction leaves a factor 2^-32 in every
+// sum, undone by one product per CTA at the end.
 //
 // Work split: the (pair, gate) items, pair-major, are cut into one
 // contiguous range per CTA of equal cost (a mul gate costs 5 products, an
@@ -334,7 +342,7 @@ __global__ void __launch_bounds__(BD) k_copy_round(const uint32_t* __restrict__ 
     const uint32_t g0 = (uint32_t)(seg - (uint64_t)j * ntot), g1 = (uint32_t)(segend - (uint64_t)j * ntot);
     const uint32_t* lo = T + (((size_t)j << sn) << 3);
     const uint32_t* hi = T + (((size_t)(j + h) << sn) << 3);
-    Fr s[3] = {fr_zero(), fr_zero(), fr_zero()};
+    FrAcc a0 = fracc_zero(), a1 = fracc_zero(), ac = fracc_zero();
     for (uint32_t q = g0 + threadIdx.x; q < g1; q += BD) {
       const uint4 gi = sg[q];
       const Fr w = fr_load(om, q);
@@ -342,19 +350,16 @@ __global__ void __launch_bounds__(BD) k_copy_round(const uint32_t* __restrict__ 
       const Fr y0 = fr_load(lo, gi.y), y1 = fr_load(hi, gi.y);
       if (q < nmul) {
         const Fr wx0 = fr_mul(w, x0), wx1 = fr_mul(w, x1);
-        const Fr wx2 = fr_sub(fr_dbl(wx1), wx0);
-        const Fr y2 = fr_sub(fr_dbl(y1), y0);
-        s[0] = fr_add(s[0], fr_mul(wx0, y0));
-        s[1] = fr_add(s[1], fr_mul(wx1, y1));
-        s[2] = fr_add(s[2], fr_mul(wx2, y2));
+        fracc_mac(a0, wx0, y0);
+        fracc_mac(a1, wx1, y1);
+        fracc_mac(ac, fr_sub(wx1, wx0), fr_sub(y1, y0));
       } else {
-        const Fr a0 = fr_mul(w, fr_add(x0, y0)), a1 = fr_mul(w, fr_add(x1, y1));
-        s[0] = fr_add(s[0], a0);
-        s[1] = fr_add(s[1], a1);
-        s[2] = fr_add(s[2], fr_sub(fr_dbl(a1), a0));
+        fracc_mac(a0, w, fr_add(x0, y0));
+        fracc_mac(a1, w, fr_add(x1, y1));
       }
     }
-    block_sum<BD, 3>(s);  // thread 0 holds S_j(0..2) for this segment
+    Fr s[3] = {fr_redc288(a0), fr_redc288(a1), fr_redc288(ac)};
+    block_sum<BD, 3>(s);  // thread 0 holds 2^-32 (S_j(0), S_j(1), c_j) for this segment
     if (warp == 0) {
       Fr sj[3];
 #pragma unroll
@@ -365,11 +370,13 @@ __global__ void __launch_bounds__(BD) k_copy_round(const uint32_t* __restrict__ 
         const Fr e0 = fr_load(E, j), e1 = fr_load(E, j + h);
         const Fr de = fr_sub(e1, e0);
         Fr et = e0, st;
-        if (lane == 3) {
-          const Fr d21 = fr_sub(sj[2], sj[1]);
-          st = fr_add(sj[0], fr_add(d21, fr_dbl(d21)));  // S(3) = S(0) + 3 (S(2) - S(1))
+        const Fr d = fr_sub(sj[1], sj[0]);
+        if (lane == 2) {
+          st = fr_add(fr_add(sj[1], d), fr_dbl(sj[2]));  // S(1) + (S(1) - S(0)) + 2c
+        } else if (lane == 3) {
+          st = fr_add(sj[1], fr_dbl(fr_add(d, fr_add(sj[2], fr_dbl(sj[2])))));  // S(1) + 2 (S(1) - S(0) + 3c)
         } else {
-          st = lane == 0 ? sj[0] : lane == 1 ? sj[1] : sj[2];
+          st = lane == 0 ? sj[0] : sj[1];
         }
         for (int t = 0; t < lane; ++t) et = fr_add(et, de);
         tot = fr_add(tot, fr_mul(et, st));
@@ -377,6 +384,7 @@ __global__ void __launch_bounds__(BD) k_copy_round(const uint32_t* __restrict__ 
     }
     seg = segend;
   }
+  if (warp == 0 && lane < 4) tot = fr_mul(tot, fr_mont_2_32());  // undo the reductions' 2^-32
   Fr acc[4];
 #pragma unroll
   for (int t = 0; t < 4; ++t) {

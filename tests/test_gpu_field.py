@@ -82,7 +82,7 @@ def test_device_digest_vs_oracle(S, oracle, n):
 
 
 def test_microbench_runs(S):
-    for kind in (0, 1, 2, 3, 4, 5):
+    for kind in (0, 1, 2, 3, 4, 5, 7):
         ms, ops = S.microbench(kind, 148, 256, 64)
         assert ms > 0 and ops > 0
 
@@ -92,3 +92,21 @@ def test_product_formulations_agree(S):
     give identical limbs on chained inputs (every thread of every block)."""
     ms, bad = S.microbench(6, 148 * 4, 256, 256)
     assert bad == 0
+
+
+def test_lazy_dot_products_vs_python_ints(S):
+    """op 5: prefix sums of products within aligned runs of 64, through the
+    544-bit accumulator and one reduction per sum."""
+    rng = random.Random(55)
+    n = 64 * 40 + 17  # ragged last run
+    a = [rng.randrange(P) for _ in range(n)]
+    b = [rng.randrange(P) for _ in range(n)]
+    a[:len(EDGE)] = EDGE
+    b[64:64 + len(EDGE)] = EDGE
+    a[128:192] = [P - 1] * 64  # the largest canonical operands in a full run
+    b[128:192] = [P - 1] * 64
+    want, run = [], 0
+    for i in range(n):
+        run = (0 if i % 64 == 0 else run) + a[i] * b[i]
+        want.append(run % P)
+    assert _run(S, 5, a, b) == want
