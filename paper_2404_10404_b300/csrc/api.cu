@@ -690,7 +690,7 @@ static int enqueue_prove(const sisu_circuit* cc, sisu_eval* ev, const sisu_trans
       tp.A = A; tp.E = w.E; tp.om = w.om; tp.sg = L.sgate;
       tp.off1 = L.off1; tp.pos1 = L.pos1; tp.off2 = L.off2; tp.pos2 = L.pos2;
       tp.nmul = L.nmul; tp.Wn = Wn; tp.s = s;
-      tp.At = w.At; tp.H1 = w.H1; tp.H2 = w.H2; tp.Ay = w.Ay; tp.Q = w.Q;
+      tp.At = w.At; tp.H1 = w.H1; tp.H2 = w.H2; tp.Ay = w.Ay;
       tp.S = w.S; tp.proof = w.proof; tp.offx = offx; tp.offy = offy; tp.offv = offv; tp.last = i + 1 == d;
       ProfScope ps(kProfGateRound, (double)Wn * (6.0 + s) + 2.0 * L.ntot, st);
       CK(launch_layer_tail(tp, st), "layer tail");

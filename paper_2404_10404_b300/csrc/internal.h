@@ -117,7 +117,7 @@ struct TailParams {
   const uint4* sg;
   const uint32_t *off1, *pos1, *off2, *pos2;
   uint32_t nmul, Wn, s;
-  uint32_t *At, *H1, *H2, *Ay, *Q;
+  uint32_t *At, *H1, *H2, *Ay;
   DevState* S;
   uint8_t* proof;
   size_t offx, offy, offv;

@@ -216,6 +216,15 @@ __device__ __forceinline__ bool grid_sum_last_block(Fr (&v)[NV], uint32_t* parti
   __syncthreads();
   if (!is_last) return false;
   __threadfence();
+  if (nblk <= 32) {  // one partial per lane of warp 0
+    if (threadIdx.x < 32) {
+#pragma unroll
+      for (int t = 0; t < NV; ++t)
+        v[t] = fr_warp_sum(threadIdx.x < nblk ? fr_load_cg(partials, (size_t)threadIdx.x * NV + t) : fr_zero());
+    }
+    if (threadIdx.x == 0) S->counter = 0;
+    return true;
+  }
 #pragma unroll
   for (int t = 0; t < NV; ++t) v[t] = fr_zero();
   for (uint32_t p = threadIdx.x; p < nblk; p += BD)
@@ -308,13 +317,16 @@ int launch_layer_init(DevState* S, uint32_t layer, uint32_t c, uint32_t s_i, con
 // add gate two full products.  The reduction leaves a factor 2^-32 in every
 // sum, undone by one product per CTA at the end.
 //
-// Work split: the (pair, gate) items, pair-major, are cut into one
-// contiguous range per CTA of equal cost (a mul gate costs 5 products, an
-// add gate 2; gates are sorted mul first, so equal item counts would leave
-// some CTAs 2.5 times the work of others).  A CTA walks its range one pair
-// segment at a time; after each segment it sums S_j(t) over the block and
-// four lanes of warp 0 apply the weights E_t(j) (plain form, so the
-// weighted sums are plain).
+// Work split: the (pair, gate) items, pair-major, are cut into ranges of
+// equal cost (a mul gate costs 5 products, an add gate 2; gates are sorted
+// mul first, so equal item counts would leave some CTAs 2.5 times the work
+// of others).  With more pairs than CTAs each CTA takes one contiguous
+// range and walks it one pair segment at a time; with fewer (the late,
+// latency-bound rounds) each pair gets m CTAs and every range lies inside
+// one pair, so no CTA pays the per-segment reduction twice.  After each
+// segment the CTA sums S_j(t) over the block and four lanes of warp 0 apply
+// the weights E_t(j) (plain form, so the weighted sums are plain); the two
+// weights are fetched with cp.async while the segment's items run.
 
 // item position of cost position X (rounded up to a gate boundary)
 __device__ __forceinline__ uint64_t item_at_cost(uint64_t X, uint32_t nmul, uint32_t ntot, uint64_t pair_cost) {
@@ -328,17 +340,36 @@ template <int BD>
 __global__ void __launch_bounds__(BD) k_copy_round(const uint32_t* __restrict__ T, uint32_t sn, uint32_t h,
                                                    const uint32_t* __restrict__ E, const uint32_t* __restrict__ om,
                                                    const uint4* __restrict__ sg, uint32_t nmul, uint32_t ntot,
-                                                   uint64_t per_cta, uint32_t* partials, DevState* S, uint8_t* proof,
-                                                   size_t off, uint32_t k) {
+                                                   uint64_t per_cta, uint32_t m, uint32_t* partials, DevState* S,
+                                                   uint8_t* proof, size_t off, uint32_t k) {
+  __shared__ __align__(16) uint32_t sh_e[16];  // E(j), E(j + h) of the current segment
   const uint64_t pair_cost = 5ull * nmul + 2ull * (ntot - nmul);
-  const uint64_t total_cost = (uint64_t)h * pair_cost;
-  const uint64_t q0 = item_at_cost(min(total_cost, (uint64_t)blockIdx.x * per_cta), nmul, ntot, pair_cost);
-  const uint64_t q1 = item_at_cost(min(total_cost, (uint64_t)(blockIdx.x + 1) * per_cta), nmul, ntot, pair_cost);
+  uint64_t c0, c1;  // the CTA's cost range
+  if (m) {
+    const uint32_t j = blockIdx.x / m, sub = blockIdx.x - j * m;
+    const uint64_t base = (uint64_t)j * pair_cost;
+    c0 = base + min(pair_cost, (uint64_t)sub * per_cta);
+    c1 = base + min(pair_cost, (uint64_t)(sub + 1) * per_cta);
+  } else {
+    const uint64_t total_cost = (uint64_t)h * pair_cost;
+    c0 = min(total_cost, (uint64_t)blockIdx.x * per_cta);
+    c1 = min(total_cost, (uint64_t)(blockIdx.x + 1) * per_cta);
+  }
+  const uint64_t q0 = item_at_cost(c0, nmul, ntot, pair_cost);
+  const uint64_t q1 = item_at_cost(c1, nmul, ntot, pair_cost);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   Fr tot = fr_zero();  // lane t < 4 of warp 0: sum over segments of E_t(j) S_j(t)
   for (uint64_t seg = q0; seg < q1;) {
     const uint32_t j = (uint32_t)(seg / ntot);
     const uint64_t segend = min(q1, (uint64_t)(j + 1) * ntot);
+    if (threadIdx.x < 4) {  // E(j) -> sh_e[0..7], E(j + h) -> sh_e[8..15], 16 bytes a thread
+      __syncwarp(0xfu);     // the previous segment's reads of sh_e are done
+      const uint32_t* src = E + 8 * (size_t)(threadIdx.x < 2 ? j : j + h) + 4 * (threadIdx.x & 1);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n\tcp.async.commit_group;" ::"r"(
+                       (uint32_t)__cvta_generic_to_shared(sh_e + 4 * threadIdx.x)),
+                   "l"(src)
+                   : "memory");
+    }
     const uint32_t g0 = (uint32_t)(seg - (uint64_t)j * ntot), g1 = (uint32_t)(segend - (uint64_t)j * ntot);
     const uint32_t* lo = T + (((size_t)j << sn) << 3);
     const uint32_t* hi = T + (((size_t)(j + h) << sn) << 3);
@@ -367,7 +398,14 @@ __global__ void __launch_bounds__(BD) k_copy_round(const uint32_t* __restrict__ 
 #pragma unroll
         for (int i = 0; i < 8; ++i) sj[t].v[i] = __shfl_sync(0xffffffffu, s[t].v[i], 0);
       if (lane < 4) {
-        const Fr e0 = fr_load(E, j), e1 = fr_load(E, j + h);
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncwarp(0xfu);  // every lane sees all four copies
+        Fr e0, e1;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          e0.v[i] = sh_e[i];
+          e1.v[i] = sh_e[8 + i];
+        }
         const Fr de = fr_sub(e1, e0);
         Fr et = e0, st;
         const Fr d = fr_sub(sj[1], sj[0]);
@@ -413,10 +451,18 @@ int launch_copy_round(const uint32_t* T, uint32_t sn, uint32_t h, const uint32_t
   uint64_t nc = std::min<uint64_t>((uint64_t)kSMs * per_sm, (total + BD - 1) / BD);
   nc = std::max<uint64_t>(1, std::min<uint64_t>(nc, kMaxPartials));
   const uint64_t total_cost = (uint64_t)h * pair_cost;
-  const uint64_t per_cta = (total_cost + nc - 1) / nc;  // cost units per CTA
-  nc = (total_cost + per_cta - 1) / per_cta;
-  k_copy_round<BD><<<(unsigned)nc, BD, 0, st>>>(T, sn, h, E, omega_s, L.sgate, L.nmul, L.ntot, per_cta, partials, S,
-                                                proof, off, k);
+  uint64_t per_cta;
+  uint32_t m = 0;
+  if (h <= nc) {  // m CTAs per pair, each range inside one pair
+    m = (uint32_t)(nc / h);
+    per_cta = (pair_cost + m - 1) / m;
+    nc = (uint64_t)h * m;
+  } else {
+    per_cta = (total_cost + nc - 1) / nc;  // cost units per CTA
+    nc = (total_cost + per_cta - 1) / per_cta;
+  }
+  k_copy_round<BD><<<(unsigned)nc, BD, 0, st>>>(T, sn, h, E, omega_s, L.sgate, L.nmul, L.ntot, per_cta, m, partials,
+                                                S, proof, off, k);
   return post_launch();
 }
 
@@ -625,6 +671,8 @@ struct TailShared {
   Fr bcast;               // CTA 0: the round's challenge, read by every CTA
   Fr vx;                  // CTA 0: v_x, read by every CTA
   Fr red[3][kTailThreads / 32];
+  Fr rx[2][16];           // r_x,k and 1 - r_x,k
+  Fr eqh[256], eql[256];  // eq(r_x, x) = eqh[x >> sl] eql[x mod 2^sl]
 };
 
 // One round over tables (A, B1, B2) of size m (after the fold of `rprev`
@@ -744,26 +792,34 @@ __global__ void __cluster_dims__(kTailCTAs, 1, 1) __launch_bounds__(kTailThreads
     S->vx = vx;
     sh.vx = vx;
   }
-  // Q = EQ(r_x) over the Wn positions of layer i+1
-  for (uint32_t x = gtid; x < p.Wn; x += gstride) {
-    Fr acc = fr_one();
-    for (uint32_t k = 0; k < p.s; ++k) {
-      const Fr rk = fr_ldcg_state(&S->rx[k]);
-      uint32_t bit = (x >> (p.s - 1 - k)) & 1u;
-      acc = fr_mul(acc, bit ? rk : fr_sub(fr_one(), rk));
-    }
-    fr_store(p.Q, x, acc);
+  // eq(r_x, x) over the Wn positions of layer i+1, as the product of two
+  // half tables over the high sh and the low sl bits of x (r_x,0 binds the
+  // most significant bit), which every CTA builds in its own shared memory
+  const uint32_t sl = p.s / 2, shb = p.s - sl, lmask = (1u << sl) - 1;
+  if (threadIdx.x < p.s) {
+    const Fr rk = fr_ldcg_state(&S->rx[threadIdx.x]);
+    sh.rx[1][threadIdx.x] = rk;
+    sh.rx[0][threadIdx.x] = fr_sub(fr_one(), rk);
   }
-  cl.sync();
+  __syncthreads();
+  for (uint32_t u = threadIdx.x; u < (1u << shb) + (1u << sl); u += kTailThreads) {
+    const bool hi = u < (1u << shb);
+    const uint32_t v = hi ? u : u - (1u << shb), nb = hi ? shb : sl, k0 = hi ? 0 : shb;
+    Fr acc = fr_one();
+    for (uint32_t b = 0; b < nb; ++b) acc = fr_mul(acc, sh.rx[(v >> (nb - 1 - b)) & 1u][k0 + b]);
+    (hi ? sh.eqh : sh.eql)[v] = acc;
+  }
+  cl.sync();  // the half tables, and v_x from CTA 0
   const Fr vx = *cl.map_shared_rank(&sh.vx, 0);
   // Libra phase 2 bookkeeping: K1(y) = e sum_{in2 g = y} w(g) Q(in1 g) (mul ? v_x : 1),
-  // K2(y) = e sum_{in2 g = y, add} w(g) Q(in1 g) v_x
+  // K2(y) = e sum_{in2 g = y, add} w(g) Q(in1 g) v_x,  Q = eq(r_x, .)
   const Fr ev = fr_mul(e, vx);
   for (uint32_t y = gtid; y < p.Wn; y += gstride) {
     Fr mu = fr_zero(), ad = fr_zero();
     for (uint32_t q = p.off2[y], qe = p.off2[y + 1]; q < qe; ++q) {
       uint32_t g = p.pos2[q];
-      Fr wq = fr_mul(fr_load(p.om, g), fr_load_cg(p.Q, p.sg[g].x));
+      const uint32_t x1 = p.sg[g].x;
+      Fr wq = fr_mul(fr_load(p.om, g), fr_mul(sh.eqh[x1 >> sl], sh.eql[x1 & lmask]));
       if (g < p.nmul) mu = fr_add(mu, wq);
       else ad = fr_add(ad, wq);
     }
@@ -793,6 +849,7 @@ __global__ void __cluster_dims__(kTailCTAs, 1, 1) __launch_bounds__(kTailThreads
       }
     }
   }
+  cl.sync();  // no CTA leaves while another may still read its shared memory
 }
 
 int launch_layer_tail(const TailParams& p, void* stream) {
