@@ -13,7 +13,9 @@ explicit sum  V~(p) = sum_j eq(p, bits(j)) V[j]  over the whole table.
 Only micro circuits (a few hundred hypercube points) are feasible.
 
 The transcript and proof conventions are the project's own (the paper fixes
-none): SHA-256 Fiat-Shamir with statement digests over 1024-byte chunks.
+none): Fiat-Shamir on the SHA-256 compression function, with statement
+digests (full SHA-256) over 1024-byte chunks.  The compression function is
+written out here from FIPS 180-4 and checked against ``hashlib``.
 """
 from __future__ import annotations
 
@@ -27,6 +29,59 @@ CHUNK = 1024
 
 def H(*parts: bytes) -> bytes:
     return hashlib.sha256(b"".join(parts)).digest()
+
+
+def _iroot(n: int, k: int) -> int:
+    """floor(n^(1/k)) for a non-negative integer n."""
+    lo, hi = 0, 1 << (n.bit_length() // k + 1)
+    while hi - lo > 1:
+        mid = (lo + hi) // 2
+        if mid ** k <= n:
+            lo = mid
+        else:
+            hi = mid
+    return lo
+
+
+def _primes(n: int):
+    out, v = [], 2
+    while len(out) < n:
+        if all(v % q for q in out if q * q <= v):
+            out.append(v)
+        v += 1
+    return out
+
+
+# FIPS 180-4 Sec. 4.2.2 and 5.3.3: the first 32 fraction bits of the cube
+# roots of the first 64 primes and of the square roots of the first 8
+_PR = _primes(64)
+SHA_K = [_iroot(p << 96, 3) & 0xFFFFFFFF for p in _PR]
+SHA_IV = [_iroot(p << 64, 2) & 0xFFFFFFFF for p in _PR[:8]]
+
+
+def _rotr(x: int, n: int) -> int:
+    return ((x >> n) | (x << (32 - n))) & 0xFFFFFFFF
+
+
+def compress(h: bytes, block: bytes) -> bytes:
+    """SHA-256 compression function (FIPS 180-4 Sec. 6.2.2, steps 1-4) of a
+    32-byte chaining value (big-endian words) and one 64-byte block."""
+    assert len(h) == 32 and len(block) == 64
+    w = list(struct.unpack(">16I", block))
+    for t in range(16, 64):
+        s0 = _rotr(w[t - 15], 7) ^ _rotr(w[t - 15], 18) ^ (w[t - 15] >> 3)
+        s1 = _rotr(w[t - 2], 17) ^ _rotr(w[t - 2], 19) ^ (w[t - 2] >> 10)
+        w.append((w[t - 16] + s0 + w[t - 7] + s1) & 0xFFFFFFFF)
+    hv = list(struct.unpack(">8I", h))
+    a, b, c, d, e, f, g, hh = hv
+    for t in range(64):
+        S1 = _rotr(e, 6) ^ _rotr(e, 11) ^ _rotr(e, 25)
+        ch = (e & f) ^ (~e & g)
+        t1 = (hh + S1 + ch + SHA_K[t] + w[t]) & 0xFFFFFFFF
+        S0 = _rotr(a, 2) ^ _rotr(a, 13) ^ _rotr(a, 22)
+        maj = (a & b) ^ (a & c) ^ (b & c)
+        hh, g, f, e, d, c, b, a = g, f, e, (d + t1) & 0xFFFFFFFF, c, b, a, (t1 + S0 + maj) & 0xFFFFFFFF
+    return struct.pack(">8I", *[(x + y) & 0xFFFFFFFF for x, y in zip(hv, (a, b, c, d, e, f, g, hh))])
 
 
 def digest(data: bytes) -> bytes:
@@ -49,22 +104,41 @@ def fe(x: int) -> bytes:
 
 
 class Transcript:
+    """State: a SHA-256 chaining value.  absorb tweaks it with the tag and
+    the element count and compresses the elements 64 bytes at a time;
+    the first challenge after an absorb reads the state itself, later ones
+    compress a squeeze block first.  A challenge is x 2^-256 mod r for the
+    state's low 254 bits x (rejected and squeezed again when x >= r)."""
+
     def __init__(self, domain, d, c, s, dig_w, dig_in, dig_out):
         dom = DOMAIN if domain is None else domain
         self.st = H(dom, b"\x00", struct.pack("<II", d, c),
                     b"".join(struct.pack("<I", v) for v in s), dig_w, dig_in, dig_out)
+        self.fresh = True
 
     def absorb(self, tag: bytes, elems):
-        self.st = H(self.st, tag, b"".join(fe(e) for e in elems))
+        msg = b"".join(fe(e) for e in elems)
+        msg += bytes(-len(msg) % 64)
+        tweak = 256 * tag[0] + len(elems)
+        h = self.st[:28] + (int.from_bytes(self.st[28:], "big") ^ tweak).to_bytes(4, "big")
+        for i in range(0, len(msg), 64):
+            h = compress(h, msg[i:i + 64])
+        self.st, self.fresh = h, True
+
+    def _squeeze(self, ctr: int):
+        self.st = compress(self.st, b"C" + struct.pack("<I", ctr) + bytes(59))
 
     def challenge(self) -> int:
         ctr = 0
+        if not self.fresh:
+            self._squeeze(ctr)
+            ctr += 1
+        self.fresh = False
         while True:
-            h = H(self.st, b"C", struct.pack("<I", ctr))
-            x = int.from_bytes(h, "little") % (1 << 254)
+            x = int.from_bytes(self.st, "little") % (1 << 254)
             if x < P:
-                self.st = h
-                return x
+                return x * pow(2, -256, P) % P
+            self._squeeze(ctr)
             ctr += 1
 
 

@@ -363,15 +363,23 @@ static int statement_digest(const uint8_t *data, size_t len, uint8_t out[32]) {
 }
 
 /* ------------------------------------------------------------------ */
-/* Fiat-Shamir transcript.                                              */
+/* Fiat-Shamir transcript (the paper fixes no hash; this is our reading).*/
+/* The state st is a SHA-256 chaining value (32 bytes, big-endian        */
+/* words) and F(h, B) is the SHA-256 compression function (FIPS 180-4    */
+/* Sec. 6.2.2) of chaining value h and a 64-byte block B.                */
 /*   init:      st = SHA256(domain || 0x00 || u32le d || u32le c ||     */
 /*                          u32le s_0..s_d || Dig(wiring) ||            */
-/*                          Dig(inputs) || Dig(outputs))                */
-/*   absorb:    st = SHA256(st || tag || canonical LE elements)         */
-/*   challenge: for ctr = 0, 1, ...: h = SHA256(st || 'C' || u32le ctr);*/
-/*              x = LE(h) mod 2^254; if x < r: st = h, return x.        */
+/*                          Dig(inputs) || Dig(outputs)); fresh         */
+/*   absorb:    h = st with word 7 xor (256 tag + n); for every 64-byte */
+/*              block B of the n canonical LE elements, zero-padded to  */
+/*              a multiple of 64 bytes: h = F(h, B).  st = h; fresh     */
+/*   challenge: ctr = 0; unless fresh: st = F(st, Q(ctr++)); then while */
+/*              x = LE(st) mod 2^254 is not below r: st = F(st,         */
+/*              Q(ctr++)).  Not fresh any more.  The challenge is       */
+/*              x 2^-256 mod r (x read as a Montgomery form).           */
+/*              Q(c) = 'C' || u32le c || 59 zero bytes.                 */
 
-typedef struct { uint8_t st[32]; } transcript;
+typedef struct { uint8_t st[32]; int fresh; } transcript;
 
 static const char DEFAULT_DOMAIN[] = "SISU-GKR-v1";
 
@@ -395,32 +403,57 @@ static void tr_init(transcript *t, const uint8_t *domain, size_t dlen, uint32_t 
     sha_update(&h, di, 32);
     sha_update(&h, dout, 32);
     sha_end(&h, t->st);
+    t->fresh = 1;
+}
+
+/* st = F(st, blk), with st as 32 big-endian bytes */
+static void tr_compress(uint8_t st[32], const uint8_t blk[64]) {
+    uint32_t h[8];
+    for (int i = 0; i < 8; ++i)
+        h[i] = ((uint32_t)st[4 * i] << 24) | ((uint32_t)st[4 * i + 1] << 16) |
+               ((uint32_t)st[4 * i + 2] << 8) | st[4 * i + 3];
+    sha_block(h, blk);
+    for (int i = 0; i < 8; ++i) {
+        st[4 * i] = (uint8_t)(h[i] >> 24); st[4 * i + 1] = (uint8_t)(h[i] >> 16);
+        st[4 * i + 2] = (uint8_t)(h[i] >> 8); st[4 * i + 3] = (uint8_t)h[i];
+    }
 }
 
 static void tr_absorb(transcript *t, uint8_t tag, const fr *e, int n) {
-    sha_ctx h;
-    uint8_t b[32];
-    sha_begin(&h);
-    sha_update(&h, t->st, 32);
-    sha_update(&h, &tag, 1);
-    for (int i = 0; i < n; ++i) { fr_to_bytes(b, e[i]); sha_update(&h, b, 32); }
-    sha_end(&h, t->st);
+    uint8_t msg[32 * 8] = {0};
+    size_t len = 32 * (size_t)n, nb = (len + 63) / 64;
+    for (int i = 0; i < n; ++i) fr_to_bytes(msg + 32 * i, e[i]);
+    t->st[30] ^= tag;           /* word 7 xor (256 tag + n) */
+    t->st[31] ^= (uint8_t)n;
+    for (size_t b = 0; b < nb; ++b) tr_compress(t->st, msg + 64 * b);
+    t->fresh = 1;
+}
+
+/* 2^-256 mod r */
+static fr r_inverse(void) {
+    fr x = fr_u64(2);
+    for (int i = 0; i < 8; ++i) x = fr_mul(x, x); /* 2^(2^8) */
+    return fr_inv(x);
+}
+
+static void tr_squeeze(transcript *t, uint32_t ctr) {
+    uint8_t q[64] = {0};
+    q[0] = 'C';
+    put_u32(q + 1, ctr);
+    tr_compress(t->st, q);
 }
 
 static fr tr_challenge(transcript *t) {
-    for (uint32_t ctr = 0;; ++ctr) {
-        uint8_t msg[37], h[32], hm[32];
-        memcpy(msg, t->st, 32);
-        msg[32] = 'C';
-        put_u32(msg + 33, ctr);
-        sha256(msg, 37, h);
-        memcpy(hm, h, 32);
+    uint32_t ctr = 0;
+    if (!t->fresh) tr_squeeze(t, ctr++);
+    t->fresh = 0;
+    for (;;) {
+        uint8_t hm[32];
+        for (int i = 0; i < 32; ++i) hm[i] = t->st[i];
         hm[31] &= 0x3f; /* mod 2^254 */
         fr x;
-        if (fr_from_bytes(&x, hm) == SO_OK) {
-            memcpy(t->st, h, 32);
-            return x;
-        }
+        if (fr_from_bytes(&x, hm) == SO_OK) return fr_mul(x, r_inverse());
+        tr_squeeze(t, ctr++);
     }
 }
 

@@ -51,95 +51,70 @@ __device__ __forceinline__ void store_words(uint8_t* base, size_t off, const Fr&
 }
 
 // ---------------------------------------------------------------------------
-// Fiat-Shamir transcript
-//   absorb:    st = SHA256(st || tag || canonical LE elements)
-//   challenge: h = SHA256(st || 'C' || u32le ctr), x = LE(h) mod 2^254,
-//              accepted (st = h) when x < r.
-// The messages have fixed lengths, so every SHA-256 block is assembled word
-// by word at compile time (the element bytes sit one byte after the state,
-// behind the tag: each message word straddles two limbs).
+// Fiat-Shamir transcript on the SHA-256 compression function F (the paper
+// fixes no hash; this convention is the project's own):
+//   absorb:    h = st with word 7 xor (256 tag + n); h = F(h, B) for every
+//              64-byte block B of the n canonical LE elements (zero-padded
+//              to whole blocks); st = h.
+//   challenge: unless the state is fresh from an absorb (or from the
+//              initial hash), st = F(st, Q(ctr++)) first; then while
+//              x = LE(st) mod 2^254 >= r, st = F(st, Q(ctr++)).  The
+//              challenge is the field element whose Montgomery form is x
+//              (x 2^-256 mod r), so it needs no conversion.
+//              Q(c) = 'C' || u32le c || 59 zero bytes.
+// A round thus costs two compressions (absorb of three or four elements)
+// where a full SHA-256 of the message and a separate challenge hash took
+// four, and the hash runs on the critical path of every round.
 
-// absorb of N elements, given as 8N big-endian words (ew[8i+j] = bswap(limb j of element i))
+// absorb of N canonical elements (N <= 4)
 template <int N>
-struct AbsorbMsg {
-  static constexpr int L = 33 + 32 * N;              // message bytes
-  static constexpr int NB = (L + 9 + 63) / 64;       // padded blocks
-  const uint32_t* st;
-  uint32_t tag;
-  const uint32_t* ew;
-  __device__ __forceinline__ uint32_t word(int w) const {
-    if (w < 8) return st[w];
-    if (w == 8) return (tag << 24) | (ew[0] >> 8);
-    if (w < 8 + 8 * N) return (ew[w - 9] << 24) | (ew[w - 8] >> 8);
-    if (w == 8 + 8 * N) return (ew[8 * N - 1] << 24) | 0x00800000u;
-    if (w == 16 * NB - 1) return 8u * L;
-    return 0u;
-  }
-};
-
-template <class Msg>
-__device__ __forceinline__ void sha_message(const Msg& m, uint32_t out[8]) {
+__device__ __noinline__ void tr_absorb_n(uint32_t* st, uint32_t tag, const Fr* canon) {
+  constexpr int NB = (8 * N + 15) / 16;  // blocks
   ShaWords8 h;
-  sha256_init(h.w);
 #pragma unroll
-  for (int b = 0; b < Msg::NB; ++b) {
+  for (int i = 0; i < 8; ++i) h.w[i] = st[i];
+  h.w[7] ^= (tag << 8) | (uint32_t)N;
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
     ShaWords16 blk;
 #pragma unroll
-    for (int k = 0; k < 16; ++k) blk.w[k] = m.word(16 * b + k);
+    for (int k = 0; k < 16; ++k) {
+      const int w = 16 * b + k;  // message word: limb w % 8 of element w / 8, byte-swapped
+      blk.w[k] = w < 8 * N ? bswap32(canon[w >> 3].v[w & 7]) : 0u;
+    }
     h = sha256_compress_v(h, blk);
   }
 #pragma unroll
-  for (int i = 0; i < 8; ++i) out[i] = h.w[i];
+  for (int i = 0; i < 8; ++i) st[i] = h.w[i];
 }
 
-template <int N>
-__device__ __noinline__ void tr_absorb_n(uint32_t* st, uint32_t tag, const Fr* canon) {
-  uint32_t ew[8 * N];
+__device__ __forceinline__ ShaWords8 tr_squeeze(const ShaWords8& h, uint32_t ctr) {
+  ShaWords16 q;
 #pragma unroll
-  for (int i = 0; i < N; ++i)
-#pragma unroll
-    for (int j = 0; j < 8; ++j) ew[8 * i + j] = bswap32(canon[i].v[j]);
-  uint32_t s0[8];
-#pragma unroll
-  for (int i = 0; i < 8; ++i) s0[i] = st[i];
-  AbsorbMsg<N> m{s0, tag, ew};
-  uint32_t out[8];
-  sha_message(m, out);
-#pragma unroll
-  for (int i = 0; i < 8; ++i) st[i] = out[i];
+  for (int k = 0; k < 16; ++k) q.w[k] = 0;
+  q.w[0] = (uint32_t('C') << 24) | ((ctr & 0xffu) << 16) | (((ctr >> 8) & 0xffu) << 8) | ((ctr >> 16) & 0xffu);
+  q.w[1] = (ctr >> 24) << 24;
+  return sha256_compress_v(h, q);
 }
 
-struct ChallengeMsg {
-  static constexpr int NB = 1;
-  const uint32_t* st;
-  uint32_t ctr;
-  __device__ __forceinline__ uint32_t word(int w) const {
-    if (w < 8) return st[w];
-    if (w == 8) return (uint32_t('C') << 24) | ((ctr & 0xffu) << 16) | (((ctr >> 8) & 0xffu) << 8) | ((ctr >> 16) & 0xffu);
-    if (w == 9) return ((ctr >> 24) << 24) | 0x00800000u;
-    if (w == 15) return 37u * 8u;
-    return 0u;
-  }
-};
-
-// next challenge in Montgomery form; a bounded number of tries (each is
-// rejected with probability below 1/4), then the error flag
-__device__ __noinline__ Fr tr_challenge(DevState* S) {
-  uint32_t s0[8];
+// next challenge (Montgomery form); `fresh`: the state comes straight from
+// an absorb or the initial hash.  A bounded number of tries (each rejected
+// with probability below 1/4), then the error flag.
+__device__ __noinline__ Fr tr_challenge(DevState* S, bool fresh) {
+  ShaWords8 h;
 #pragma unroll
-  for (int i = 0; i < 8; ++i) s0[i] = S->st[i];
-  for (uint32_t ctr = 0; ctr < 4096u; ++ctr) {
-    ChallengeMsg m{s0, ctr};
-    uint32_t o[8];
-    sha_message(m, o);
+  for (int i = 0; i < 8; ++i) h.w[i] = S->st[i];
+  uint32_t ctr = 0;
+  if (!fresh) h = tr_squeeze(h, ctr++);
+  for (; ctr < 4096u; h = tr_squeeze(h, ctr++)) {
     Fr x;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) x.v[k] = bswap32(o[k]);
+    for (int k = 0; k < 8; ++k) x.v[k] = bswap32(h.w[k]);
     x.v[7] &= 0x3fffffffu;
     if (fr_lt_modulus(x)) {
 #pragma unroll
-      for (int i = 0; i < 8; ++i) S->st[i] = o[i];
-      return fr_from_canonical(x);
+      for (int i = 0; i < 8; ++i) S->st[i] = h.w[i];
+      return x;
     }
   }
   S->error |= 2u;
@@ -171,7 +146,7 @@ __device__ __forceinline__ void round_finalize(DevState* S, const Fr (&v)[NV], u
 #pragma unroll
     for (int t = 0; t < NV; ++t) canon[t] = sh[t];
     tr_absorb_n<NV>(S->st, 'R', canon);
-    *rslot = tr_challenge(S);
+    *rslot = tr_challenge(S, true);
   }
 }
 
@@ -257,8 +232,9 @@ __global__ void k_transcript_init(InitParams p, DevState* S) {
   for (int i = 0; i < 8; ++i) S->st[i] = o[i];
   S->counter = 0;
   S->error = 0;
-  for (uint32_t k = 0; k < p.c; ++k) S->zb[k] = tr_challenge(S);
-  for (uint32_t k = 0; k < p.s[0]; ++k) S->zg[k] = tr_challenge(S);
+  // the first challenge reads the fresh initial state
+  for (uint32_t k = 0; k < p.c; ++k) S->zb[k] = tr_challenge(S, k == 0);
+  for (uint32_t k = 0; k < p.s[0]; ++k) S->zg[k] = tr_challenge(S, p.c == 0 && k == 0);
 }
 
 int launch_transcript_init(const InitParams& p, DevState* S, void* stream) {
@@ -630,8 +606,8 @@ __global__ void k_layer_end(DevState* S, const uint32_t* Ay, uint32_t s, uint8_t
   store_words(proof, off + 32, canon[1]);
   tr_absorb_n<2>(S->st, 'V', canon);
   if (!last) {
-    S->alpha = tr_challenge(S);
-    S->beta = tr_challenge(S);
+    S->alpha = tr_challenge(S, true);
+    S->beta = tr_challenge(S, false);
   }
 }
 
@@ -745,7 +721,7 @@ __device__ Fr tail_round(cg::cluster_group& cl, TailShared& sh, uint32_t* A, uin
     if (lane == 0) {
       Fr canon[3] = {sh.canon[0], sh.canon[1], sh.canon[2]};
       tr_absorb_n<3>(S->st, 'R', canon);
-      Fr r = tr_challenge(S);
+      Fr r = tr_challenge(S, true);
       *rslot = r;
       sh.bcast = r;
     }
@@ -844,8 +820,8 @@ __global__ void __cluster_dims__(kTailCTAs, 1, 1) __launch_bounds__(kTailThreads
       Fr canon[2] = {sh.canon[0], sh.canon[1]};
       tr_absorb_n<2>(S->st, 'V', canon);
       if (!p.last) {
-        S->alpha = tr_challenge(S);
-        S->beta = tr_challenge(S);
+        S->alpha = tr_challenge(S, true);
+        S->beta = tr_challenge(S, false);
       }
     }
   }

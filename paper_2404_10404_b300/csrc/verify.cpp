@@ -199,40 +199,53 @@ struct Lagrange {
   }
 };
 
+// Fiat-Shamir transcript on the SHA-256 compression function: absorb
+// tweaks word 7 of the state with 256 tag + n and compresses the elements'
+// canonical LE bytes 64 at a time (zero-padded); the first challenge after
+// an absorb or the initial hash reads the state, later ones first compress
+// Q(ctr) = 'C' || u32le ctr || 0^59; a challenge is the element whose
+// Montgomery form is LE(st) mod 2^254 (squeezed again while >= r).
 struct Transcript {
   uint32_t st[8];
+  bool fresh = true;
   void absorb(uint8_t tag, const HF* e, int n) {
-    Sha256Stream h;
-    h.begin();
-    h.digest_words(st);
-    h.byte(tag);
-    uint8_t b[32];
-    for (int i = 0; i < n; ++i) {
-      store(b, e[i]);
-      h.bytes(b, 32);
+    uint8_t msg[32 * 4] = {0};
+    const int nb = (32 * n + 63) / 64;
+    for (int i = 0; i < n; ++i) store(msg + 32 * i, e[i]);
+    st[7] ^= ((uint32_t)tag << 8) | (uint32_t)n;
+    for (int b = 0; b < nb; ++b) {
+      uint32_t blk[16];
+      const uint8_t* p = msg + 64 * b;
+      for (int k = 0; k < 16; ++k)
+        blk[k] = ((uint32_t)p[4 * k] << 24) | ((uint32_t)p[4 * k + 1] << 16) | ((uint32_t)p[4 * k + 2] << 8) | p[4 * k + 3];
+      sha256_compress(st, blk);
     }
-    h.end(st);
+    fresh = true;
+  }
+  void squeeze(uint32_t ctr) {
+    uint32_t q[16] = {0};
+    q[0] = (uint32_t('C') << 24) | ((ctr & 0xffu) << 16) | (((ctr >> 8) & 0xffu) << 8) | ((ctr >> 16) & 0xffu);
+    q[1] = (ctr >> 24) << 24;
+    sha256_compress(st, q);
   }
   HF challenge() {
-    for (uint32_t ctr = 0;; ++ctr) {
-      Sha256Stream h;
-      h.begin();
-      h.digest_words(st);
-      h.byte('C');
-      h.u32le(ctr);
-      uint32_t o[8];
-      h.end(o);
+    uint32_t ctr = 0;
+    if (!fresh) squeeze(ctr++);
+    fresh = false;
+    for (;; squeeze(ctr++)) {
       uint8_t b[32];
       for (int i = 0; i < 8; ++i) {
-        b[4 * i] = (uint8_t)(o[i] >> 24); b[4 * i + 1] = (uint8_t)(o[i] >> 16);
-        b[4 * i + 2] = (uint8_t)(o[i] >> 8); b[4 * i + 3] = (uint8_t)o[i];
+        b[4 * i] = (uint8_t)(st[i] >> 24); b[4 * i + 1] = (uint8_t)(st[i] >> 16);
+        b[4 * i + 2] = (uint8_t)(st[i] >> 8); b[4 * i + 3] = (uint8_t)st[i];
       }
       b[31] &= 0x3f;
       HF x;
-      if (load(b, &x)) {
-        memcpy(st, o, 32);
-        return x;
+      for (int i = 0; i < 4; ++i) {
+        uint64_t v = 0;
+        for (int k = 7; k >= 0; --k) v = (v << 8) | b[8 * i + k];
+        x.w[i] = v;
       }
+      if (!geq_mod(x.w)) return x;  // x is the Montgomery form
     }
   }
 };

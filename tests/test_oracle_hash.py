@@ -76,3 +76,50 @@ def test_statement_digest_structure(oracle):
     ls = [H(three[i:i + 1024], b"\x00") for i in (0, 1024, 2048)]
     root = H(H(ls[0], ls[1], b"\x01"), ls[2], b"\x01")
     assert oracle.statement_digest(three) == H(root, (2500).to_bytes(8, "little"), b"\x03")
+
+
+def _sha256_by_compress(m: bytes) -> bytes:
+    # FIPS 180-4 Sec. 5.1.1 padding, then the compression function block by block
+    padded = m + b"\x80" + bytes(-(len(m) + 9) % 64) + (8 * len(m)).to_bytes(8, "big")
+    h = b"".join(v.to_bytes(4, "big") for v in brute.SHA_IV)
+    for i in range(0, len(padded), 64):
+        h = brute.compress(h, padded[i:i + 64])
+    return h
+
+
+def test_python_compression_function_matches_hashlib():
+    """The transcript's compression function (the pure-Python one; the C
+    oracle's is pinned through its full SHA-256 above) chained over the
+    FIPS padding is SHA-256."""
+    rng = random.Random(9)
+    for m, d in _fips_vectors():
+        assert _sha256_by_compress(m) == d
+    for n in list(range(0, 130)) + [rng.randrange(200, 3000) for _ in range(20)]:
+        m = bytes(rng.getrandbits(8) for _ in range(n))
+        assert _sha256_by_compress(m) == hashlib.sha256(m).digest(), n
+
+
+def test_python_constants_match_fips_table():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "sha256_constants.txt")) if l[:1] in "KH"]
+    assert brute.SHA_K == [int(x, 16) for r in rows if r[0] == "K" for x in r[1:]]
+    assert brute.SHA_IV == [int(x, 16) for r in rows if r[0] == "H" for x in r[1:]]
+
+
+def test_transcript_challenges_are_uniform_field_elements():
+    """Every challenge is below r, consecutive challenges differ, and a
+    different tag or element count changes the state."""
+    t = brute.Transcript(None, 1, 2, [3, 3], b"\x01" * 32, b"\x02" * 32, b"\x03" * 32)
+    seen = set()
+    for i in range(200):
+        if i % 3 == 0:
+            t.absorb(b"R", [i, 2 * i])
+        x = t.challenge()
+        assert 0 <= x < brute.P and x not in seen
+        seen.add(x)
+    a = brute.Transcript(None, 1, 2, [3, 3], b"\x01" * 32, b"\x02" * 32, b"\x03" * 32)
+    b = brute.Transcript(None, 1, 2, [3, 3], b"\x01" * 32, b"\x02" * 32, b"\x03" * 32)
+    c = brute.Transcript(None, 1, 2, [3, 3], b"\x01" * 32, b"\x02" * 32, b"\x03" * 32)
+    a.absorb(b"R", [5, 6])
+    b.absorb(b"V", [5, 6])
+    c.absorb(b"R", [5, 6, 0])
+    assert len({a.st, b.st, c.st}) == 3
