@@ -174,13 +174,18 @@ __device__ __forceinline__ void block_sum(Fr (&v)[NV]) {
 }
 
 // Writes this block's partial sums; returns true in the last block to
-// finish, which then holds the grid-wide sums in thread 0's v.
-template <int BD, int NV>
+// finish, which then holds the grid-wide sums in thread 0's v.  With
+// kInThread0 the block's sums are already in thread 0 (the other threads'
+// v are ignored), so the block reduction is skipped.  The last block sums
+// the partials with one warp per value (NV <= BD / 32).
+template <int BD, int NV, bool kInThread0 = false>
 __device__ __forceinline__ bool grid_sum_last_block(Fr (&v)[NV], uint32_t* partials, DevState* S) {
+  static_assert(NV <= BD / 32, "one warp per value");
   __shared__ bool is_last;
+  __shared__ Fr tot[NV];
   const uint32_t nblk = gridDim.x * gridDim.y;
   const uint32_t bid = blockIdx.y * gridDim.x + blockIdx.x;
-  block_sum<BD, NV>(v);
+  if (!kInThread0) block_sum<BD, NV>(v);
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int t = 0; t < NV; ++t) fr_store_cg(partials, (size_t)bid * NV + t, v[t]);
@@ -191,22 +196,19 @@ __device__ __forceinline__ bool grid_sum_last_block(Fr (&v)[NV], uint32_t* parti
   __syncthreads();
   if (!is_last) return false;
   __threadfence();
-  if (nblk <= 32) {  // one partial per lane of warp 0
-    if (threadIdx.x < 32) {
-#pragma unroll
-      for (int t = 0; t < NV; ++t)
-        v[t] = fr_warp_sum(threadIdx.x < nblk ? fr_load_cg(partials, (size_t)threadIdx.x * NV + t) : fr_zero());
-    }
-    if (threadIdx.x == 0) S->counter = 0;
-    return true;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (warp < NV) {  // warp t sums value t over every block's partial
+    Fr x = fr_zero();
+    for (uint32_t p = lane; p < nblk; p += 32) x = fr_add(x, fr_load_cg(partials, (size_t)p * NV + warp));
+    x = fr_warp_sum(x);
+    if (lane == 0) tot[warp] = x;
   }
+  __syncthreads();
+  if (threadIdx.x == 0) {
 #pragma unroll
-  for (int t = 0; t < NV; ++t) v[t] = fr_zero();
-  for (uint32_t p = threadIdx.x; p < nblk; p += BD)
-#pragma unroll
-    for (int t = 0; t < NV; ++t) v[t] = fr_add(v[t], fr_load_cg(partials, (size_t)p * NV + t));
-  block_sum<BD, NV>(v);
-  if (threadIdx.x == 0) S->counter = 0;
+    for (int t = 0; t < NV; ++t) v[t] = tot[t];
+    S->counter = 0;
+  }
   return true;
 }
 
@@ -406,7 +408,8 @@ __global__ void __launch_bounds__(BD) k_copy_round(const uint32_t* __restrict__ 
     for (int i = 0; i < 8; ++i) acc[t].v[i] = __shfl_sync(0xffffffffu, tot.v[i], t);
     if (threadIdx.x != 0) acc[t] = fr_zero();
   }
-  if (grid_sum_last_block<BD, 4>(acc, partials, S) && threadIdx.x < 32) round_finalize<4>(S, acc, proof, off, &S->rb[k]);
+  if (grid_sum_last_block<BD, 4, true>(acc, partials, S) && threadIdx.x < 32)
+    round_finalize<4>(S, acc, proof, off, &S->rb[k]);
 }
 
 int launch_copy_round(const uint32_t* T, uint32_t sn, uint32_t h, const uint32_t* E, const uint32_t* omega_s,
