@@ -97,13 +97,13 @@ __device__ __forceinline__ ShaWords8 tr_squeeze(const ShaWords8& h, uint32_t ctr
   return sha256_compress_v(h, q);
 }
 
-// next challenge (Montgomery form); `fresh`: the state comes straight from
-// an absorb or the initial hash.  A bounded number of tries (each rejected
-// with probability below 1/4), then the error flag.
-__device__ __noinline__ Fr tr_challenge(DevState* S, bool fresh) {
+// next challenge (Montgomery form) from the state st; `fresh`: the state
+// comes straight from an absorb or the initial hash.  A bounded number of
+// tries (each rejected with probability below 1/4), then the error flag.
+__device__ __noinline__ Fr tr_challenge_st(uint32_t* st, uint32_t* error, bool fresh) {
   ShaWords8 h;
 #pragma unroll
-  for (int i = 0; i < 8; ++i) h.w[i] = S->st[i];
+  for (int i = 0; i < 8; ++i) h.w[i] = st[i];
   uint32_t ctr = 0;
   if (!fresh) h = tr_squeeze(h, ctr++);
   for (; ctr < 4096u; h = tr_squeeze(h, ctr++)) {
@@ -113,13 +113,15 @@ __device__ __noinline__ Fr tr_challenge(DevState* S, bool fresh) {
     x.v[7] &= 0x3fffffffu;
     if (fr_lt_modulus(x)) {
 #pragma unroll
-      for (int i = 0; i < 8; ++i) S->st[i] = h.w[i];
+      for (int i = 0; i < 8; ++i) st[i] = h.w[i];
       return x;
     }
   }
-  S->error |= 2u;
+  atomicOr(error, 2u);
   return fr_zero();
 }
+
+__device__ __forceinline__ Fr tr_challenge(DevState* S, bool fresh) { return tr_challenge_st(S->st, &S->error, fresh); }
 
 // The last block of a round, called by the lanes of its warp 0 with the
 // grid-wide sums in lane 0: canonical evaluations (one lane each) into the
@@ -296,9 +298,11 @@ int launch_layer_init(DevState* S, uint32_t layer, uint32_t c, uint32_t s_i, con
 // sum, undone by one product per CTA at the end.
 //
 // Work split: the (pair, gate) items, pair-major, are cut into ranges of
-// equal cost (a mul gate costs 5 products, an add gate 2; gates are sorted
-// mul first, so equal item counts would leave some CTAs 2.5 times the work
-// of others).  With more pairs than CTAs each CTA takes one contiguous
+// equal cost (gates are sorted mul first, so equal item counts would leave
+// some CTAs twice the work of others).  The weights kCostMul : kCostAdd are
+// the measured times of the two kinds of item on B300 (a mul item, two
+// Montgomery and three full products, takes about 2.2 times an add item,
+// two full products).  With more pairs than CTAs each CTA takes one contiguous
 // range and walks it one pair segment at a time; with fewer (the late,
 // latency-bound rounds) each pair gets m CTAs and every range lies inside
 // one pair, so no CTA pays the per-segment reduction twice.  After each
@@ -306,11 +310,17 @@ int launch_layer_init(DevState* S, uint32_t layer, uint32_t c, uint32_t s_i, con
 // the weights E_t(j) (plain form, so the weighted sums are plain); the two
 // weights are fetched with cp.async while the segment's items run.
 
+constexpr uint64_t kCostMul = 9, kCostAdd = 4;
+
+__host__ __device__ __forceinline__ uint64_t copy_pair_cost(uint32_t nmul, uint32_t ntot) {
+  return kCostMul * nmul + kCostAdd * (ntot - nmul);
+}
+
 // item position of cost position X (rounded up to a gate boundary)
 __device__ __forceinline__ uint64_t item_at_cost(uint64_t X, uint32_t nmul, uint32_t ntot, uint64_t pair_cost) {
   const uint64_t j = X / pair_cost, r = X - j * pair_cost;
-  const uint64_t mc = 5ull * nmul;
-  const uint64_t g = r < mc ? (r + 4) / 5 : nmul + (r - mc + 1) / 2;
+  const uint64_t mc = kCostMul * nmul;
+  const uint64_t g = r < mc ? (r + kCostMul - 1) / kCostMul : nmul + (r - mc + kCostAdd - 1) / kCostAdd;
   return j * ntot + min(g, (uint64_t)ntot);
 }
 
@@ -321,7 +331,7 @@ __global__ void __launch_bounds__(BD) k_copy_round(const uint32_t* __restrict__ 
                                                    uint64_t per_cta, uint32_t m, uint32_t* partials, DevState* S,
                                                    uint8_t* proof, size_t off, uint32_t k) {
   __shared__ __align__(16) uint32_t sh_e[16];  // E(j), E(j + h) of the current segment
-  const uint64_t pair_cost = 5ull * nmul + 2ull * (ntot - nmul);
+  const uint64_t pair_cost = copy_pair_cost(nmul, ntot);
   uint64_t c0, c1;  // the CTA's cost range
   if (m) {
     const uint32_t j = blockIdx.x / m, sub = blockIdx.x - j * m;
@@ -424,7 +434,7 @@ int launch_copy_round(const uint32_t* T, uint32_t sn, uint32_t h, const uint32_t
     per_sm = n;
   }
   const uint64_t total = (uint64_t)h * L.ntot;
-  const uint64_t pair_cost = 5ull * L.nmul + 2ull * (L.ntot - L.nmul);
+  const uint64_t pair_cost = copy_pair_cost(L.nmul, L.ntot);
   // contiguous ranges of equal cost: one wave of CTAs, and for small rounds
   // about one item per thread (short serial chains)
   uint64_t nc = std::min<uint64_t>((uint64_t)kSMs * per_sm, (total + BD - 1) / BD);
@@ -635,20 +645,12 @@ namespace cg = cooperative_groups;
 constexpr int kTailCTAs = 8;
 constexpr int kTailThreads = 256;
 
-__device__ __forceinline__ Fr fr_ldcg_state(const Fr* p) {
-  const uint4* q = reinterpret_cast<const uint4*>(p);
-  uint4 a = __ldcg(q), b = __ldcg(q + 1);
-  Fr x;
-  x.v[0] = a.x; x.v[1] = a.y; x.v[2] = a.z; x.v[3] = a.w;
-  x.v[4] = b.x; x.v[5] = b.y; x.v[6] = b.z; x.v[7] = b.w;
-  return x;
-}
-
 struct TailShared {
-  Fr part[kTailCTAs][3];  // CTA 0: partial sums of every CTA
-  Fr canon[3];            // CTA 0: canonical round values
-  Fr bcast;               // CTA 0: the round's challenge, read by every CTA
+  Fr part[kTailCTAs][3];  // partial sums of every CTA (each CTA sends its own to all)
+  Fr canon[3];            // canonical round values
+  Fr bcast;               // the round's challenge, for every thread of the CTA
   Fr vx;                  // CTA 0: v_x, read by every CTA
+  uint32_t st[8];         // this CTA's copy of the transcript state
   Fr red[3][kTailThreads / 32];
   Fr rx[2][16];           // r_x,k and 1 - r_x,k
   Fr eqh[256], eql[256];  // eq(r_x, x) = eqh[x >> sl] eql[x mod 2^sl]
@@ -659,7 +661,10 @@ struct TailShared {
 // A is in Montgomery form and B1, B2 are plain, so the products and the
 // sums are plain.  The round runs in two cluster-wide steps, each thread
 // doing at most a few products: the fold (one product per new table
-// entry), then one product per (pair, t).  Returns the round's challenge
+// entry), then one product per (pair, t).  Every CTA sends its partial sums
+// to every CTA and then runs the transcript on its own copy of the state,
+// so the challenge needs no further barrier; CTA 0 alone writes the proof
+// bytes and the challenge (rslot).  Returns the round's challenge
 // (Montgomery form) in every thread.
 __device__ Fr tail_round(cg::cluster_group& cl, TailShared& sh, uint32_t* A, uint32_t* B1, uint32_t* B2,
                          uint32_t m, uint32_t k, const Fr& rprev, DevState* S, uint8_t* proof, size_t off,
@@ -703,34 +708,38 @@ __device__ Fr tail_round(cg::cluster_group& cl, TailShared& sh, uint32_t* A, uin
   __syncthreads();
   if (warp == 0) {
 #pragma unroll
-    for (int t = 0; t < 3; ++t) acc[t] = fr_warp_sum(lane < kTailThreads / 32 ? sh.red[t][lane] : fr_zero());
-    if (lane == 0) {
-      Fr* dst = cl.map_shared_rank(&sh.part[0][0], 0);
+    for (int t = 0; t < 3; ++t) {
+      acc[t] = fr_warp_sum(lane < kTailThreads / 32 ? sh.red[t][lane] : fr_zero());
+#pragma unroll
+      for (int i = 0; i < 8; ++i) acc[t].v[i] = __shfl_sync(0xffffffffu, acc[t].v[i], 0);
+    }
+    if (lane < kTailCTAs) {  // lane d sends this CTA's sums to CTA d
+      Fr* dst = cl.map_shared_rank(&sh.part[0][0], lane);
 #pragma unroll
       for (int t = 0; t < 3; ++t) dst[rank * 3 + t] = acc[t];
     }
   }
   cl.sync();
-  if (rank == 0 && warp == 0) {
+  if (warp == 0) {
     if (lane < 3) {
       Fr v = fr_zero();
 #pragma unroll
       for (int c = 0; c < kTailCTAs; ++c) v = fr_add(v, sh.part[c][lane]);
       v = fr_reduce_once(v);  // plain and below 2r: now canonical
-      store_words(proof, off + 32 * (size_t)lane, v);
+      if (rank == 0) store_words(proof, off + 32 * (size_t)lane, v);
       sh.canon[lane] = v;
     }
     __syncwarp();
     if (lane == 0) {
       Fr canon[3] = {sh.canon[0], sh.canon[1], sh.canon[2]};
-      tr_absorb_n<3>(S->st, 'R', canon);
-      Fr r = tr_challenge(S, true);
-      *rslot = r;
+      tr_absorb_n<3>(sh.st, 'R', canon);
+      const Fr r = tr_challenge_st(sh.st, &S->error, true);
+      if (rank == 0) *rslot = r;
       sh.bcast = r;
     }
   }
-  cl.sync();
-  return *cl.map_shared_rank(&sh.bcast, 0);
+  __syncthreads();
+  return sh.bcast;
 }
 
 __global__ void __cluster_dims__(kTailCTAs, 1, 1) __launch_bounds__(kTailThreads) k_layer_tail(TailParams p) {
@@ -740,6 +749,7 @@ __global__ void __cluster_dims__(kTailCTAs, 1, 1) __launch_bounds__(kTailThreads
   const uint32_t gtid = rank * kTailThreads + threadIdx.x, gstride = kTailCTAs * kTailThreads;
   DevState* S = p.S;
   const Fr e = fr_load(p.E, 0);
+  if (threadIdx.x < 8) sh.st[threadIdx.x] = S->st[threadIdx.x];  // ordered by the cluster barrier below
   // Libra phase 1 bookkeeping: H1(x) = e sum_{in1 g = x} w(g) (mul ? A(in2 g) : 1),
   // H2(x) = e sum_{in1 g = x, add} w(g) A(in2 g)
   for (uint32_t x = gtid; x < p.Wn; x += gstride) {
@@ -763,8 +773,13 @@ __global__ void __cluster_dims__(kTailCTAs, 1, 1) __launch_bounds__(kTailThreads
   }
   cl.sync();
   Fr r = fr_zero();
-  for (uint32_t k = 0; k < p.s; ++k)
+  for (uint32_t k = 0; k < p.s; ++k) {
     r = tail_round(cl, sh, p.At, p.H1, p.H2, p.Wn >> k, k, r, S, p.proof, p.offx + 96 * (size_t)k, &S->rx[k]);
+    if (threadIdx.x == 0) {  // r_x,k and 1 - r_x,k for eq(r_x, .)
+      sh.rx[1][k] = r;
+      sh.rx[0][k] = fr_sub(fr_one(), r);
+    }
+  }
   // v_x = A(r_x)
   if (rank == 0 && threadIdx.x == 0) {
     Fr vx = p.s == 0 ? fr_load_cg(p.At, 0) : fold2(fr_load_cg(p.At, 0), fr_load_cg(p.At, 1), r);
@@ -775,11 +790,6 @@ __global__ void __cluster_dims__(kTailCTAs, 1, 1) __launch_bounds__(kTailThreads
   // half tables over the high sh and the low sl bits of x (r_x,0 binds the
   // most significant bit), which every CTA builds in its own shared memory
   const uint32_t sl = p.s / 2, shb = p.s - sl, lmask = (1u << sl) - 1;
-  if (threadIdx.x < p.s) {
-    const Fr rk = fr_ldcg_state(&S->rx[threadIdx.x]);
-    sh.rx[1][threadIdx.x] = rk;
-    sh.rx[0][threadIdx.x] = fr_sub(fr_one(), rk);
-  }
   __syncthreads();
   for (uint32_t u = threadIdx.x; u < (1u << shb) + (1u << sl); u += kTailThreads) {
     const bool hi = u < (1u << shb);
@@ -821,11 +831,13 @@ __global__ void __cluster_dims__(kTailCTAs, 1, 1) __launch_bounds__(kTailThreads
     __syncwarp();
     if (lane == 0) {
       Fr canon[2] = {sh.canon[0], sh.canon[1]};
-      tr_absorb_n<2>(S->st, 'V', canon);
+      tr_absorb_n<2>(sh.st, 'V', canon);
       if (!p.last) {
-        S->alpha = tr_challenge(S, true);
-        S->beta = tr_challenge(S, false);
+        S->alpha = tr_challenge_st(sh.st, &S->error, true);
+        S->beta = tr_challenge_st(sh.st, &S->error, false);
       }
+#pragma unroll
+      for (int i = 0; i < 8; ++i) S->st[i] = sh.st[i];
     }
   }
   cl.sync();  // no CTA leaves while another may still read its shared memory
