@@ -197,7 +197,9 @@ int sisu_gkr_verify(const sisu_circuit* circ, const uint8_t* inputs, const uint8
  * zero input yields 0 and SISU_ERR_ZERO_INVERSE), 4 a*b + (1-a)(1-b),
  * 5 out[i] = sum of a[j]*b[j] for j from 64*floor(i/64) to i (the lazily
  * reduced dot product the copy-phase rounds use: full 512-bit products
- * summed exactly, one reduction per sum).  b is ignored for op 3.  Errors: INVALID_ARG, NOT_CANONICAL, ZERO_INVERSE. */
+ * summed exactly, one reduction per sum), 6 a[i]*b[0] (the product by
+ * one fixed multiplier that folds a table by a challenge: eight 32x256-bit
+ * rows and a two-word reduction).  b is ignored for op 3.  Errors: INVALID_ARG, NOT_CANONICAL, ZERO_INVERSE. */
 int sisu_fr_batch(int op, const uint8_t* a, const uint8_t* b, uint8_t* out, size_t n, void* stream);
 
 /* Merkle statement digest of device bytes (the transcript's digest of

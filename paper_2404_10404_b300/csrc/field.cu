@@ -38,6 +38,16 @@ __global__ void k_fr_batch(int op, const uint32_t* __restrict__ a, const uint32_
         case 1: z = fr_sub(x, y); break;
         case 2: z = fr_mul(x, y); break;
         case 4: z = fr_add(fr_mul(x, y), fr_mul(fr_one_minus_f(x), fr_one_minus_f(y))); break;
+        case 6: {  // a * b[0] by the fixed-multiplier product
+          Fr b0 = fr_load(b, 0);
+          if (!fr_lt_modulus(b0)) b0 = fr_zero();  // reported through element 0
+          const Fr r = fr_from_canonical(b0);
+          Fr K[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) K[u] = fr_fixed_coeff(r, u);
+          z = fr_mul_fixed(x, K);
+          break;
+        }
         default: {
           // op 5: sum of a_j b_j over j from the start of i's aligned run of
           // 64 up to i, through the 544-bit accumulator (one reduction)

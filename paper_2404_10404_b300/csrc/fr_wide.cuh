@@ -545,5 +545,113 @@ static __device__ __noinline__ FrAcc fracc_mac_call(FrAcc acc, Fr a, Fr b) {
 
 __device__ __forceinline__ void fracc_mac(FrAcc& acc, const Fr& a, const Fr& b) { acc = fracc_mac_call(acc, a, b); }
 
+// ---------------------------------------------------------------------------
+// Products with one fixed multiplier (the fold of a table by a challenge).
+//
+// For a fixed rho (Montgomery form r) and K_i = rho 2^(32 i + 64) mod p,
+// i = 0..7, the Montgomery form of D rho for d = D 2^256 (limbs d_i) is
+//   sum_i d_i K_i  2^-64 mod p,
+// because sum_i d_i K_i = d rho 2^64.  The sum is eight 32 x 256-bit rows
+// added at the same offset (64 mad.lo and 64 mad.hi into ten words, below
+// 8 2^32 2p < 2^291) and the factor 2^-64 is two Montgomery steps, whose
+// result is below 2^291 / 2^64 + p < 2p.  That is 82 mad.lo and 80 mad.hi
+// where a Montgomery product needs 136 and 128.  K_i = MontMul(r, X_i) for
+// the plain constants X_i = 2^(32 i + 64) mod p.
+
+// K_i for 0 <= i < 8 from the Montgomery form r of rho
+__device__ __forceinline__ Fr fr_fixed_coeff(const Fr& r, int i) {
+  Fr x = fr_zero();
+  if (i < 6) {
+    x.v[i + 2] = 1u;  // 2^(32 i + 64) < p
+  } else {
+    x = i == 6 ? fr_one() : fr_mont_2_32();  // 2^256 mod p, 2^288 mod p
+  }
+  return fr_mul(r, x);
+}
+
+// d rho (Montgomery forms, d < 2p) given K[0..7] from fr_fixed_coeff
+__device__ __forceinline__ Fr fr_mul_fixed(const Fr& d, const Fr* K8) {
+  uint32_t a[10];
+#pragma unroll
+  for (int i = 0; i < 10; ++i) a[i] = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const Fr K = K8[i];
+    const uint32_t di = d.v[i];
+    asm("mad.lo.cc.u32  %0, %11, %10, %0;\n\t"
+        "madc.lo.cc.u32 %1, %12, %10, %1;\n\t"
+        "madc.lo.cc.u32 %2, %13, %10, %2;\n\t"
+        "madc.lo.cc.u32 %3, %14, %10, %3;\n\t"
+        "madc.lo.cc.u32 %4, %15, %10, %4;\n\t"
+        "madc.lo.cc.u32 %5, %16, %10, %5;\n\t"
+        "madc.lo.cc.u32 %6, %17, %10, %6;\n\t"
+        "madc.lo.cc.u32 %7, %18, %10, %7;\n\t"
+        "addc.cc.u32    %8, %8, 0;\n\t"
+        "addc.u32       %9, %9, 0;\n\t"
+        "mad.hi.cc.u32  %1, %11, %10, %1;\n\t"
+        "madc.hi.cc.u32 %2, %12, %10, %2;\n\t"
+        "madc.hi.cc.u32 %3, %13, %10, %3;\n\t"
+        "madc.hi.cc.u32 %4, %14, %10, %4;\n\t"
+        "madc.hi.cc.u32 %5, %15, %10, %5;\n\t"
+        "madc.hi.cc.u32 %6, %16, %10, %6;\n\t"
+        "madc.hi.cc.u32 %7, %17, %10, %7;\n\t"
+        "madc.hi.cc.u32 %8, %18, %10, %8;\n\t"
+        "addc.u32       %9, %9, 0;"
+        : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]), "+r"(a[6]), "+r"(a[7]), "+r"(a[8]), "+r"(a[9])
+        : "r"(di), "r"(K.v[0]), "r"(K.v[1]), "r"(K.v[2]), "r"(K.v[3]), "r"(K.v[4]), "r"(K.v[5]), "r"(K.v[6]), "r"(K.v[7]));
+  }
+  // two Montgomery steps: divide by 2^64
+  asm("{\n\t"
+      ".reg .u32 m;\n\t"
+      "mul.lo.u32 m, %0, 0xefffffff;\n\t"
+      "mad.lo.cc.u32  %0, m, 0xf0000001, %0;\n\t"
+      "madc.lo.cc.u32 %1, m, 0x43e1f593, %1;\n\t"
+      "madc.lo.cc.u32 %2, m, 0x79b97091, %2;\n\t"
+      "madc.lo.cc.u32 %3, m, 0x2833e848, %3;\n\t"
+      "madc.lo.cc.u32 %4, m, 0x8181585d, %4;\n\t"
+      "madc.lo.cc.u32 %5, m, 0xb85045b6, %5;\n\t"
+      "madc.lo.cc.u32 %6, m, 0xe131a029, %6;\n\t"
+      "madc.lo.cc.u32 %7, m, 0x30644e72, %7;\n\t"
+      "addc.cc.u32    %8, %8, 0;\n\t"
+      "addc.u32       %9, %9, 0;\n\t"
+      "mad.hi.cc.u32  %1, m, 0xf0000001, %1;\n\t"
+      "madc.hi.cc.u32 %2, m, 0x43e1f593, %2;\n\t"
+      "madc.hi.cc.u32 %3, m, 0x79b97091, %3;\n\t"
+      "madc.hi.cc.u32 %4, m, 0x2833e848, %4;\n\t"
+      "madc.hi.cc.u32 %5, m, 0x8181585d, %5;\n\t"
+      "madc.hi.cc.u32 %6, m, 0xb85045b6, %6;\n\t"
+      "madc.hi.cc.u32 %7, m, 0xe131a029, %7;\n\t"
+      "madc.hi.cc.u32 %8, m, 0x30644e72, %8;\n\t"
+      "addc.u32       %9, %9, 0;\n\t"
+      "}"
+      : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]), "+r"(a[6]), "+r"(a[7]), "+r"(a[8]), "+r"(a[9]));
+  asm("{\n\t"
+      ".reg .u32 m;\n\t"
+      "mul.lo.u32 m, %0, 0xefffffff;\n\t"
+      "mad.lo.cc.u32  %0, m, 0xf0000001, %0;\n\t"
+      "madc.lo.cc.u32 %1, m, 0x43e1f593, %1;\n\t"
+      "madc.lo.cc.u32 %2, m, 0x79b97091, %2;\n\t"
+      "madc.lo.cc.u32 %3, m, 0x2833e848, %3;\n\t"
+      "madc.lo.cc.u32 %4, m, 0x8181585d, %4;\n\t"
+      "madc.lo.cc.u32 %5, m, 0xb85045b6, %5;\n\t"
+      "madc.lo.cc.u32 %6, m, 0xe131a029, %6;\n\t"
+      "madc.lo.cc.u32 %7, m, 0x30644e72, %7;\n\t"
+      "addc.u32       %8, %8, 0;\n\t"
+      "mad.hi.cc.u32  %1, m, 0xf0000001, %1;\n\t"
+      "madc.hi.cc.u32 %2, m, 0x43e1f593, %2;\n\t"
+      "madc.hi.cc.u32 %3, m, 0x79b97091, %3;\n\t"
+      "madc.hi.cc.u32 %4, m, 0x2833e848, %4;\n\t"
+      "madc.hi.cc.u32 %5, m, 0x8181585d, %5;\n\t"
+      "madc.hi.cc.u32 %6, m, 0xb85045b6, %6;\n\t"
+      "madc.hi.cc.u32 %7, m, 0xe131a029, %7;\n\t"
+      "madc.hi.u32    %8, m, 0x30644e72, %8;\n\t"
+      "}"
+      : "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]), "+r"(a[6]), "+r"(a[7]), "+r"(a[8]), "+r"(a[9]));
+  Fr o;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) o.v[i] = a[2 + i];
+  return o;
+}
+
 #endif  // __CUDACC__
 }  // namespace sisu

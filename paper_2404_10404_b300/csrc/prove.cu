@@ -457,20 +457,27 @@ int launch_copy_round(const uint32_t* T, uint32_t sn, uint32_t h, const uint32_t
 
 // fold of the copy rows and of E by the round's challenge r = r_b[k]:
 //   dst(j, x) = src(j, x) + r (src(j + h, x) - src(j, x)),  j < h
-// (in place when src == dst: each thread writes only the entry it read)
-__global__ void k_copy_fold(const uint32_t* src, uint32_t* dst, uint32_t sn, uint32_t h, uint32_t* E,
-                            const DevState* S, uint32_t k) {
-  const Fr r = S->rb[k];
+// (in place when src == dst: each thread writes only the entry it read).
+// Every entry is multiplied by the same r, so the product is the
+// fixed-multiplier form (fr_mul_fixed: eight row products and a two-word
+// reduction, 40% fewer multiply-adds than a Montgomery product), with the
+// eight coefficients built once per CTA in shared memory (read by broadcast
+// loads, so the kernel fits four CTAs per SM: the fold streams HBM and
+// needs the warps to keep loads in flight).
+__global__ void __launch_bounds__(256, 4) k_copy_fold(const uint32_t* src, uint32_t* dst, uint32_t sn, uint32_t h,
+                                                   uint32_t* E, const DevState* S, uint32_t k) {
+  __shared__ Fr shK[8];
+  if (threadIdx.x < 8) shK[threadIdx.x] = fr_fixed_coeff(S->rb[k], (int)threadIdx.x);
+  __syncthreads();
   const size_t nel = (size_t)h << sn;
   const size_t total = nel + h;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
        idx += (size_t)gridDim.x * blockDim.x) {
-    if (idx < nel) {
-      fr_store(dst, idx, fold2(fr_load(src, idx), fr_load(src, idx + nel), r));
-    } else {
-      size_t j = idx - nel;
-      fr_store(E, j, fold2(fr_load(E, j), fr_load(E, j + h), r));
-    }
+    const bool row = idx < nel;
+    const uint32_t* base = row ? src : E;
+    const size_t i0 = row ? idx : idx - nel, i1 = row ? idx + nel : idx - nel + h;
+    const Fr x = fr_load(base, i0), y = fr_load(base, i1);
+    fr_store(row ? dst : E, i0, fr_add(x, fr_mul_fixed(fr_sub(y, x), shK)));
   }
 }
 

@@ -110,3 +110,13 @@ def test_lazy_dot_products_vs_python_ints(S):
         run = (0 if i % 64 == 0 else run) + a[i] * b[i]
         want.append(run % P)
     assert _run(S, 5, a, b) == want
+
+
+@pytest.mark.parametrize("fixed", [1, 2, P - 1, (1 << 253) + 12345, 0xF0000001, None])
+def test_fixed_multiplier_products_vs_python_ints(S, fixed):
+    """op 6: a[i] * b[0] through the fixed-multiplier product (the fold's)."""
+    rng = random.Random(66 if fixed is None else fixed % 1000)
+    b0 = rng.randrange(P) if fixed is None else fixed
+    a = [rng.randrange(P) for _ in range(3000)] + EDGE
+    b = [b0] + [0] * (len(a) - 1)
+    assert _run(S, 6, a, b) == [x * b0 % P for x in a]
