@@ -268,11 +268,13 @@ static int circuit_create(const sisu_layer* layers, uint32_t n_gate_layers, uint
     std::sort(adds.begin(), adds.end(), by_in1);
     l.nmul = (uint32_t)muls.size();
     l.ntot = (uint32_t)(muls.size() + adds.size());
-    l.sg.resize(l.ntot);
+    l.sg.resize(W);  // present gates, then the absent (padding) gates
     for (uint32_t q = 0; q < l.ntot; ++q) {
       uint32_t g = q < l.nmul ? muls[q] : adds[q - l.nmul];
       l.sg[q] = make_uint4(hc.in1[i][g], hc.in2[i][g], g, 0);
     }
+    for (uint32_t g = 0, q = l.ntot; g < W; ++g)
+      if (hc.type[i][g] == 2) l.sg[q++] = make_uint4(0, 0, g, 0);
     auto csr = [&](int which, std::vector<uint32_t>& off, std::vector<uint32_t>& pos) {
       off.assign(Wn + 1, 0);
       pos.resize(l.ntot);
@@ -374,7 +376,7 @@ int eval_enqueue(sisu_eval* ev, const uint8_t* inputs, int on_device, cudaStream
   }
   for (int i = (int)d - 1; i >= 0; --i) {
     ProfScope ps(kProfEval, (double)hc.C * cc->L[i].nmul, st);
-    CK(launch_eval_layer(ev->V[i + 1], ev->V[i], cc->L[i].gate_io, hc.c, hc.s[i], hc.s[i + 1], st), "eval layer");
+    CK(launch_eval_layer(ev->V[i + 1], ev->V[i], cc->L[i], hc.c, hc.s[i], hc.s[i + 1], st), "eval layer");
   }
   CK(cudaMemcpyAsync(ev->host_flag, ev->flag, 4, cudaMemcpyDeviceToHost, st), "flag copy");
   return SISU_OK;
@@ -528,7 +530,9 @@ extern "C" void sisu_transcript_destroy(sisu_transcript* tr) { delete tr; }
 // ---------------------------------------------------------------------------
 // proving
 
-static void workspace_sizes(const sisu_circuit* cc, size_t sizes[12]) {
+constexpr int kWsRegions = 13;
+
+static void workspace_sizes(const sisu_circuit* cc, size_t sizes[kWsRegions]) {
   const HostCircuit& hc = cc->hc;
   uint32_t wmax_next = 1, wmax = 1, nmax = 1;
   for (uint32_t i = 0; i < hc.d; ++i) {
@@ -539,17 +543,20 @@ static void workspace_sizes(const sisu_circuit* cc, size_t sizes[12]) {
   const size_t half = hc.C >= 2 ? (size_t)(hc.C / 2) * wmax_next * 32 : 32;
   const size_t dig = std::max(digest_scratch_words((size_t)hc.C * hc.W[hc.d] * 32),
                               digest_scratch_words((size_t)hc.C * hc.W[0] * 32)) * 4;
-  const size_t v[12] = {half, (size_t)hc.C * 32, (size_t)nmax * 32, (size_t)wmax_next * 32, (size_t)wmax_next * 32,
-                        (size_t)wmax_next * 32, (size_t)wmax_next * 32, (size_t)wmax * 32,
-                        (size_t)kMaxPartials * 4 * 32, dig, sizeof(DevState), hc.proof_len()};
-  for (int k = 0; k < 12; ++k) sizes[k] = v[k];
+  uint32_t smax = 0;
+  for (uint32_t i = 0; i < hc.d; ++i) smax = std::max(smax, hc.s[i]);
+  const size_t v[kWsRegions] = {half, (size_t)hc.C * 32, (size_t)nmax * 32, (size_t)wmax_next * 32,
+                                (size_t)wmax_next * 32, (size_t)wmax_next * 32, (size_t)wmax_next * 32,
+                                (size_t)wmax * 32, (size_t)kMaxPartials * 4 * 32, dig, sizeof(DevState),
+                                hc.proof_len(), eq_half_words(hc.c, smax) * 4};
+  for (int k = 0; k < kWsRegions; ++k) sizes[k] = v[k];
 }
 
 static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 namespace sisu {
 size_t workspace_footprint(const sisu_circuit* cc) {
-  size_t sizes[12], total = 0;
+  size_t sizes[kWsRegions], total = 0;
   workspace_sizes(cc, sizes);
   for (size_t x : sizes) total += al256(x);
   return total;
@@ -560,11 +567,11 @@ size_t workspace_footprint(const sisu_circuit* cc) {
 static int workspace_init(sisu_eval* ev, Workspace* ws, uint8_t* dev, uint8_t* host, cudaStream_t st) {
   const sisu_circuit* cc = ev->circ;
   const HostCircuit& hc = cc->hc;
-  size_t sizes[12];
+  size_t sizes[kWsRegions];
   workspace_sizes(cc, sizes);
   uint8_t* p = dev;
-  void* ptrs[12];
-  for (int k = 0; k < 12; ++k) {
+  void* ptrs[kWsRegions];
+  for (int k = 0; k < kWsRegions; ++k) {
     ptrs[k] = p;
     p += al256(sizes[k]);
   }
@@ -580,6 +587,7 @@ static int workspace_init(sisu_eval* ev, Workspace* ws, uint8_t* dev, uint8_t* h
   ws->dscratch = (uint32_t*)ptrs[9];
   ws->S = (DevState*)ptrs[10];
   ws->proof = (uint8_t*)ptrs[11];
+  ws->eqh = (uint32_t*)ptrs[12];
   ws->proof_len = hc.proof_len();
   ws->host = host;
   // the proof header is fixed by the circuit
@@ -662,7 +670,7 @@ static int enqueue_prove(const sisu_circuit* cc, sisu_eval* ev, const sisu_trans
     const uint32_t s = hc.s[i + 1], Wn = hc.W[i + 1], sn = hc.s[i + 1];
     {
       ProfScope ps(kProfLayerInit, (double)hc.C * c + (double)L.ntot * (i == 0 ? hc.s[0] : 2.0 * hc.s[i] + 2), st);
-      CK(launch_layer_init(w.S, i, c, hc.s[i], L, w.E, w.om, st), "layer init");
+      CK(launch_layer_init(w.S, i, c, hc.s[i], L, w.E, w.om, w.eqh, st), "layer init");
     }
     // copy phase: c rounds, each followed by the fold of its challenge
     const uint32_t* A = ev->V[i + 1];

@@ -64,30 +64,36 @@ int launch_layer_to_canonical(const uint32_t* V, uint32_t* out, uint32_t c, uint
 
 // ---------------------------------------------------------------------------
 // forward evaluation of one layer (Sec. 2.2): V_i(b, g) = op_g(V_{i+1}(b, in1 g), V_{i+1}(b, in2 g))
+//
+// Threads walk each copy's gates in the sorted order (mul gates, add gates,
+// then the absent padding gates, whose value is 0), so a warp holds one kind
+// of gate: with the wiring order nearly every warp mixed the two and all of
+// it waited for the Montgomery products of its mul lanes.  The outputs go
+// to each gate's own position (one 32-byte sector per element).
 
 __global__ void k_eval_layer(const uint32_t* __restrict__ Vn, uint32_t* __restrict__ V,
-                             const uint2* __restrict__ gates, uint32_t c, uint32_t s, uint32_t sn) {
+                             const uint4* __restrict__ sg, uint32_t nmul, uint32_t ntot, uint32_t c, uint32_t s,
+                             uint32_t sn) {
   const size_t total = (size_t)1 << (c + s);
   const uint32_t mask = (1u << s) - 1u;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
        idx += (size_t)gridDim.x * blockDim.x) {
-    uint32_t b = (uint32_t)(idx >> s), g = (uint32_t)(idx & mask);
-    uint2 gw = gates[g];
-    uint32_t t = gw.x >> 30;
+    const uint32_t b = (uint32_t)(idx >> s), q = (uint32_t)(idx & mask);
+    const uint4 gi = sg[q];
     Fr out = fr_zero();
-    if (t != 2u) {
+    if (q < ntot) {
       const uint32_t* row = Vn + (((size_t)b << sn) << 3);
-      Fr x = fr_load(row, gw.x & 0x3fffffffu), y = fr_load(row, gw.y);
-      out = t == 0u ? fr_add(x, y) : fr_mul(x, y);
+      const Fr x = fr_load(row, gi.x), y = fr_load(row, gi.y);
+      out = q < nmul ? fr_mul(x, y) : fr_add(x, y);
     }
-    fr_store(V, idx, out);
+    fr_store(V, ((size_t)b << s) + gi.z, out);
   }
 }
 
-int launch_eval_layer(const uint32_t* Vn, uint32_t* V, const uint2* gate_io, uint32_t c, uint32_t s,
-                      uint32_t sn, void* stream) {
+int launch_eval_layer(const uint32_t* Vn, uint32_t* V, const DevLayer& L, uint32_t c, uint32_t s, uint32_t sn,
+                      void* stream) {
   size_t n = (size_t)1 << (c + s);
-  k_eval_layer<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(Vn, V, gate_io, c, s, sn);
+  k_eval_layer<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(Vn, V, L.sgate, L.nmul, L.ntot, c, s, sn);
   return post_launch();
 }
 

@@ -49,7 +49,8 @@ struct InitParams {
 // Per-layer device views of the circuit.
 struct DevLayer {
   const uint2* gate_io;  // per padded gate: {in1 | type << 30, in2}; type 2 = absent
-  const uint4* sgate;    // present gates, mul first then add, each sorted by in1: {in1, in2, g, 0}
+  const uint4* sgate;    // present gates, mul first then add, each sorted by in1: {in1, in2, g, 0};
+                         // then the absent gates {0, 0, g, 0} (W_i entries in all)
   const uint32_t* off1;  // CSR over layer i+1 positions x: sgate positions with in1 == x
   const uint32_t* pos1;
   const uint32_t* off2;  // same for in2
@@ -76,8 +77,8 @@ int report_error(int code, const char* msg);
 
 int launch_inputs_to_mont(const uint32_t* in, uint32_t* V, uint32_t c, uint32_t s, uint32_t Creal,
                           uint32_t wreal, uint32_t* err, void* stream);
-int launch_eval_layer(const uint32_t* Vn, uint32_t* V, const uint2* gate_io, uint32_t c, uint32_t s,
-                      uint32_t sn, void* stream);
+int launch_eval_layer(const uint32_t* Vn, uint32_t* V, const DevLayer& L, uint32_t c, uint32_t s, uint32_t sn,
+                      void* stream);
 int launch_layer_to_canonical(const uint32_t* V, uint32_t* out, uint32_t c, uint32_t s, uint32_t Creal,
                               uint32_t wreal, void* stream);
 // Merkle statement digest of a Montgomery table (elements converted to
@@ -89,8 +90,11 @@ int launch_digest_bytes(const uint8_t* data, size_t len, uint32_t* scratch, uint
 size_t digest_scratch_words(size_t len_bytes);
 
 int launch_transcript_init(const InitParams& p, DevState* S, void* stream);
-int launch_layer_init(DevState* S, uint32_t layer, uint32_t c, uint32_t s_i, const DevLayer& L,
-                      uint32_t* E, uint32_t* omega_s, void* stream);
+int launch_layer_init(DevState* S, uint32_t layer, uint32_t c, uint32_t s_i, const DevLayer& L, uint32_t* E,
+                      uint32_t* omega_s, uint32_t* eqh, void* stream);
+// words of the eq half-table scratch of launch_layer_init (copy bits c,
+// largest layer log-width smax)
+size_t eq_half_words(uint32_t c, uint32_t smax);
 int launch_copy_round(const uint32_t* T, uint32_t sn, uint32_t h, const uint32_t* E, const uint32_t* omega_s,
                       const DevLayer& L, uint32_t* partials, DevState* S, uint8_t* proof, size_t off,
                       uint32_t k, void* stream);

@@ -27,18 +27,6 @@ __device__ __forceinline__ Fr eq_index(const Fr* r, uint32_t s, uint32_t v) {
   return acc;
 }
 
-// The same product started from the integer 1 instead of Montgomery 1:
-// Montgomery products of a plain value with Montgomery values stay plain,
-// so this returns eq(r, v) in plain (non-Montgomery) form at no extra cost.
-__device__ __forceinline__ Fr eq_index_plain(const Fr* r, uint32_t s, uint32_t v) {
-  Fr acc = fr_int_one();
-  for (uint32_t k = 0; k < s; ++k) {
-    uint32_t bit = (v >> (s - 1 - k)) & 1u;
-    acc = fr_mul(acc, bit ? r[k] : fr_one_minus(r[k]));
-  }
-  return acc;
-}
-
 // x + r (y - x): the multilinear line through two table entries
 __device__ __forceinline__ Fr fold2(const Fr& x, const Fr& y, const Fr& r) {
   return fr_add(x, fr_mul(r, fr_sub(y, x)));
@@ -251,34 +239,83 @@ int launch_transcript_init(const InitParams& p, DevState* S, void* stream) {
 // weights w(g) over the layer's present gates (in the sorted order):
 //   layer 0:  w(g) = eq(z_g, g)
 //   layer i:  w(g) = alpha eq(r_x, g) + beta eq(r_y, g)   (previous layer's r_x, r_y)
+//
+// Each eq over n bits is the product of two half tables, over the high
+// n - n/2 and the low n/2 bits of the index (bit 1 of the point binds the
+// most significant index bit).  A first launch builds the half tables (at
+// most n/2 + 1 products an entry, alpha and beta folded into the high
+// halves), a second combines them: one product per E entry, one or two per
+// gate weight, where a direct product over all bits took n.
 
-__global__ void k_layer_init(DevState* S, uint32_t layer, uint32_t c, uint32_t si, const uint4* __restrict__ sg,
-                             uint32_t ntot, uint32_t* __restrict__ E, uint32_t* __restrict__ om) {
+__host__ __device__ inline uint32_t eq_half_entries(uint32_t n) { return (1u << (n - n / 2)) + (1u << (n / 2)); }
+
+// entry v of the table over bits k0 .. k0 + nb - 1 of point P, started from init
+__device__ __forceinline__ Fr eq_half_entry(const Fr* P, uint32_t k0, uint32_t nb, uint32_t v, Fr acc) {
+  for (uint32_t b = 0; b < nb; ++b) {
+    const Fr pk = P[k0 + b];
+    acc = fr_mul(acc, ((v >> (nb - 1 - b)) & 1u) ? pk : fr_one_minus(pk));
+  }
+  return acc;
+}
+
+// Half tables, in order: E high (plain: started from the integer 1), E low;
+// then layer 0: z_g high, low; layer i: alpha r_x high, r_x low, beta r_y
+// high, r_y low.
+__global__ void k_eq_halves(DevState* S, uint32_t layer, uint32_t c, uint32_t si, uint32_t* __restrict__ tab) {
+  const uint32_t nE = eq_half_entries(c), nW = eq_half_entries(si);
+  const uint32_t total = nE + (layer == 0 ? nW : 2 * nW);
+  for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    const bool isE = idx < nE;
+    const uint32_t n = isE ? c : si;
+    uint32_t u = isE ? idx : (idx - nE) % nW;
+    const uint32_t which = isE ? 0 : (idx - nE) / nW;  // 0: z_g or r_x, 1: r_y
+    const uint32_t nh = n - n / 2, hsize = 1u << nh;
+    const bool hi = u < hsize;
+    if (!hi) u -= hsize;
+    const Fr* P = isE ? (layer == 0 ? S->zb : S->rb) : layer == 0 ? S->zg : which == 0 ? S->rx : S->ry;
+    Fr init = fr_one();
+    if (hi) init = isE ? fr_int_one() : layer == 0 ? fr_one() : which == 0 ? S->alpha : S->beta;
+    fr_store(tab, idx, eq_half_entry(P, hi ? 0 : nh, hi ? nh : n / 2, u, init));
+  }
+}
+
+__global__ void k_layer_init(uint32_t layer, uint32_t c, uint32_t si, const uint4* __restrict__ sg, uint32_t ntot,
+                             const uint32_t* __restrict__ tab, uint32_t* __restrict__ E, uint32_t* __restrict__ om) {
   const uint32_t C = 1u << c;
   const size_t total = (size_t)C + ntot;
-  const Fr* z = layer == 0 ? S->zb : S->rb;
+  const uint32_t nE = eq_half_entries(c), nW = eq_half_entries(si);
+  const uint32_t cl = c / 2, sl = si / 2;
+  const uint32_t* Eh = tab;
+  const uint32_t* El = tab + 8 * ((size_t)1 << (c - cl));
+  const uint32_t* Xh = tab + 8 * (size_t)nE;
+  const uint32_t* Xl = Xh + 8 * ((size_t)1 << (si - sl));
+  const uint32_t* Yh = Xh + 8 * (size_t)nW;
+  const uint32_t* Yl = Yh + 8 * ((size_t)1 << (si - sl));
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
        idx += (size_t)gridDim.x * blockDim.x) {
     if (idx < C) {
-      fr_store(E, idx, eq_index_plain(z, c, (uint32_t)idx));
+      const uint32_t v = (uint32_t)idx;
+      fr_store(E, idx, fr_mul(fr_load(Eh, v >> cl), fr_load(El, v & ((1u << cl) - 1))));  // plain
     } else {
-      uint32_t q = (uint32_t)(idx - C);
-      uint32_t g = sg[q].z;
-      Fr w;
-      if (layer == 0) {
-        w = eq_index(S->zg, si, g);
-      } else {
-        w = fr_add(fr_mul(S->alpha, eq_index(S->rx, si, g)), fr_mul(S->beta, eq_index(S->ry, si, g)));
-      }
+      const uint32_t q = (uint32_t)(idx - C), g = sg[q].z, gh = g >> sl, gl = g & ((1u << sl) - 1);
+      Fr w = fr_mul(fr_load(Xh, gh), fr_load(Xl, gl));
+      if (layer != 0) w = fr_add(w, fr_mul(fr_load(Yh, gh), fr_load(Yl, gl)));
       fr_store(om, q, w);
     }
   }
 }
 
+size_t eq_half_words(uint32_t c, uint32_t smax) { return 8 * ((size_t)eq_half_entries(c) + 2 * eq_half_entries(smax)); }
+
 int launch_layer_init(DevState* S, uint32_t layer, uint32_t c, uint32_t s_i, const DevLayer& L, uint32_t* E,
-                      uint32_t* omega_s, void* stream) {
+                      uint32_t* omega_s, uint32_t* eqh, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  const uint32_t nh = eq_half_entries(c) + (layer == 0 ? 1 : 2) * eq_half_entries(s_i);
+  k_eq_halves<<<grid_for(nh, 128), 128, 0, st>>>(S, layer, c, s_i, eqh);
+  const int rc = post_launch();
+  if (rc) return rc;
   size_t n = ((size_t)1 << c) + L.ntot;
-  k_layer_init<<<grid_for(n, 128), 128, 0, (cudaStream_t)stream>>>(S, layer, c, s_i, L.sgate, L.ntot, E, omega_s);
+  k_layer_init<<<grid_for(n, 128), 128, 0, st>>>(layer, c, s_i, L.sgate, L.ntot, eqh, E, omega_s);
   return post_launch();
 }
 
