@@ -41,8 +41,11 @@ SMS, IMAD_PER_SM_CLK, SM_MAX_MHZ = 148, 64, 2032.0
 IMAD_PER_FR_MUL = 264
 ALU_PEAK_TIMAD = SMS * IMAD_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
 # DRAM traffic (read + write bytes) per launch of the dominant kernel from
-# an ncu capture (profiles/); None when not captured for the current build.
-DOMINANT_TRAFFIC_BYTES = None
+# an ncu capture (profiles/copy_round_medium.md): the mean over the ten copy
+# rounds of a medium layer (every layer has the same shape, so this is the
+# mean over all 200 launches of a step); None when not captured for the
+# current build of the kernel.
+DOMINANT_TRAFFIC_BYTES = 29.88e6
 
 
 def log(*a):

@@ -521,7 +521,9 @@ __global__ void __launch_bounds__(256, 4) k_copy_fold(const uint32_t* src, uint3
 int launch_copy_fold(const uint32_t* src, uint32_t* dst, uint32_t sn, uint32_t h, uint32_t* E, DevState* S,
                      uint32_t k, void* stream) {
   size_t n = ((size_t)h << sn) + h;
-  k_copy_fold<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(src, dst, sn, h, E, S, k);
+  // one resident wave (four CTAs per SM), so each CTA builds the eight
+  // coefficients once for many entries
+  k_copy_fold<<<grid_for(n, 256, 4), 256, 0, (cudaStream_t)stream>>>(src, dst, sn, h, E, S, k);
   return post_launch();
 }
 
