@@ -42,9 +42,9 @@ __global__ void k_fr_batch(int op, const uint32_t* __restrict__ a, const uint32_
           Fr b0 = fr_load(b, 0);
           if (!fr_lt_modulus(b0)) b0 = fr_zero();  // reported through element 0
           const Fr r = fr_from_canonical(b0);
-          Fr K[8];
+          __align__(16) uint32_t K[64];
 #pragma unroll
-          for (int u = 0; u < 8; ++u) K[u] = fr_fixed_coeff(r, u);
+          for (int u = 0; u < 8; ++u) fr_store(K, u, fr_fixed_coeff(r, u));
           z = fr_mul_fixed(x, K);
           break;
         }

@@ -569,14 +569,25 @@ __device__ __forceinline__ Fr fr_fixed_coeff(const Fr& r, int i) {
   return fr_mul(r, x);
 }
 
-// d rho (Montgomery forms, d < 2p) given K[0..7] from fr_fixed_coeff
-__device__ __forceinline__ Fr fr_mul_fixed(const Fr& d, const Fr* K8) {
+// coefficient i of a table of eight (8 words each, 16-byte aligned)
+__device__ __forceinline__ Fr fr_coeff_load(const uint32_t* K8, int i) {
+  const uint4* p = reinterpret_cast<const uint4*>(K8 + 8 * i);
+  const uint4 lo = p[0], hi = p[1];
+  Fr k;
+  k.v[0] = lo.x; k.v[1] = lo.y; k.v[2] = lo.z; k.v[3] = lo.w;
+  k.v[4] = hi.x; k.v[5] = hi.y; k.v[6] = hi.z; k.v[7] = hi.w;
+  return k;
+}
+
+// d rho (Montgomery forms, d < 2p) given the coefficients K_0..K_7 of
+// fr_fixed_coeff as 64 words (16-byte aligned)
+__device__ __forceinline__ Fr fr_mul_fixed(const Fr& d, const uint32_t* K8) {
   uint32_t a[10];
 #pragma unroll
   for (int i = 0; i < 10; ++i) a[i] = 0;
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
-    const Fr K = K8[i];
+    const Fr K = fr_coeff_load(K8, i);
     const uint32_t di = d.v[i];
     asm("mad.lo.cc.u32  %0, %11, %10, %0;\n\t"
         "madc.lo.cc.u32 %1, %12, %10, %1;\n\t"

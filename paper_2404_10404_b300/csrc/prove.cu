@@ -503,8 +503,8 @@ int launch_copy_round(const uint32_t* T, uint32_t sn, uint32_t h, const uint32_t
 // needs the warps to keep loads in flight).
 __global__ void __launch_bounds__(256, 4) k_copy_fold(const uint32_t* src, uint32_t* dst, uint32_t sn, uint32_t h,
                                                    uint32_t* E, const DevState* S, uint32_t k) {
-  __shared__ Fr shK[8];
-  if (threadIdx.x < 8) shK[threadIdx.x] = fr_fixed_coeff(S->rb[k], (int)threadIdx.x);
+  __shared__ __align__(16) uint32_t shK[64];
+  if (threadIdx.x < 8) fr_store(shK, threadIdx.x, fr_fixed_coeff(S->rb[k], (int)threadIdx.x));
   __syncthreads();
   const size_t nel = (size_t)h << sn;
   const size_t total = nel + h;
