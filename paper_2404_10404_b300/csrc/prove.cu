@@ -54,8 +54,16 @@ __device__ __forceinline__ void store_words(uint8_t* base, size_t off, const Fr&
 // where a full SHA-256 of the message and a separate challenge hash took
 // four, and the hash runs on the critical path of every round.
 
+// The compression runs out of line in one of two forms: kSmall for the
+// transcripts at the end of a round kernel, where the code is cold, the
+// unrolled form in the cluster kernel of Libra's phases, where it is warm.
+template <bool kSmall>
+__device__ __forceinline__ ShaWords8 tr_compress(const ShaWords8& h, const ShaWords16& blk) {
+  return kSmall ? sha256_compress_small_v(h, blk) : sha256_compress_v(h, blk);
+}
+
 // absorb of N canonical elements (N <= 4)
-template <int N>
+template <int N, bool kSmall>
 __device__ __noinline__ void tr_absorb_n(uint32_t* st, uint32_t tag, const Fr* canon) {
   constexpr int NB = (8 * N + 15) / 16;  // blocks
   ShaWords8 h;
@@ -70,31 +78,33 @@ __device__ __noinline__ void tr_absorb_n(uint32_t* st, uint32_t tag, const Fr* c
       const int w = 16 * b + k;  // message word: limb w % 8 of element w / 8, byte-swapped
       blk.w[k] = w < 8 * N ? bswap32(canon[w >> 3].v[w & 7]) : 0u;
     }
-    h = sha256_compress_v(h, blk);
+    h = tr_compress<kSmall>(h, blk);
   }
 #pragma unroll
   for (int i = 0; i < 8; ++i) st[i] = h.w[i];
 }
 
+template <bool kSmall>
 __device__ __forceinline__ ShaWords8 tr_squeeze(const ShaWords8& h, uint32_t ctr) {
   ShaWords16 q;
 #pragma unroll
   for (int k = 0; k < 16; ++k) q.w[k] = 0;
   q.w[0] = (uint32_t('C') << 24) | ((ctr & 0xffu) << 16) | (((ctr >> 8) & 0xffu) << 8) | ((ctr >> 16) & 0xffu);
   q.w[1] = (ctr >> 24) << 24;
-  return sha256_compress_v(h, q);
+  return tr_compress<kSmall>(h, q);
 }
 
 // next challenge (Montgomery form) from the state st; `fresh`: the state
 // comes straight from an absorb or the initial hash.  A bounded number of
 // tries (each rejected with probability below 1/4), then the error flag.
+template <bool kSmall>
 __device__ __noinline__ Fr tr_challenge_st(uint32_t* st, uint32_t* error, bool fresh) {
   ShaWords8 h;
 #pragma unroll
   for (int i = 0; i < 8; ++i) h.w[i] = st[i];
   uint32_t ctr = 0;
-  if (!fresh) h = tr_squeeze(h, ctr++);
-  for (; ctr < 4096u; h = tr_squeeze(h, ctr++)) {
+  if (!fresh) h = tr_squeeze<kSmall>(h, ctr++);
+  for (; ctr < 4096u; h = tr_squeeze<kSmall>(h, ctr++)) {
     Fr x;
 #pragma unroll
     for (int k = 0; k < 8; ++k) x.v[k] = bswap32(h.w[k]);
@@ -109,7 +119,10 @@ __device__ __noinline__ Fr tr_challenge_st(uint32_t* st, uint32_t* error, bool f
   return fr_zero();
 }
 
-__device__ __forceinline__ Fr tr_challenge(DevState* S, bool fresh) { return tr_challenge_st(S->st, &S->error, fresh); }
+// the transcripts of the round kernels (cold code)
+__device__ __forceinline__ Fr tr_challenge(DevState* S, bool fresh) {
+  return tr_challenge_st<true>(S->st, &S->error, fresh);
+}
 
 // The last block of a round, called by the lanes of its warp 0 with the
 // grid-wide sums in lane 0: canonical evaluations (one lane each) into the
@@ -135,7 +148,7 @@ __device__ __forceinline__ void round_finalize(DevState* S, const Fr (&v)[NV], u
     Fr canon[NV];
 #pragma unroll
     for (int t = 0; t < NV; ++t) canon[t] = sh[t];
-    tr_absorb_n<NV>(S->st, 'R', canon);
+    tr_absorb_n<NV, true>(S->st, 'R', canon);
     *rslot = tr_challenge(S, true);
   }
 }
@@ -663,7 +676,7 @@ __global__ void k_layer_end(DevState* S, const uint32_t* Ay, uint32_t s, uint8_t
   Fr canon[2] = {fr_to_canonical(S->vx), fr_to_canonical(vy)};
   store_words(proof, off, canon[0]);
   store_words(proof, off + 32, canon[1]);
-  tr_absorb_n<2>(S->st, 'V', canon);
+  tr_absorb_n<2, true>(S->st, 'V', canon);
   if (!last) {
     S->alpha = tr_challenge(S, true);
     S->beta = tr_challenge(S, false);
@@ -778,8 +791,8 @@ __device__ Fr tail_round(cg::cluster_group& cl, TailShared& sh, uint32_t* A, uin
     __syncwarp();
     if (lane == 0) {
       Fr canon[3] = {sh.canon[0], sh.canon[1], sh.canon[2]};
-      tr_absorb_n<3>(sh.st, 'R', canon);
-      const Fr r = tr_challenge_st(sh.st, &S->error, true);
+      tr_absorb_n<3, false>(sh.st, 'R', canon);
+      const Fr r = tr_challenge_st<false>(sh.st, &S->error, true);
       if (rank == 0) *rslot = r;
       sh.bcast = r;
     }
@@ -877,10 +890,10 @@ __global__ void __cluster_dims__(kTailCTAs, 1, 1) __launch_bounds__(kTailThreads
     __syncwarp();
     if (lane == 0) {
       Fr canon[2] = {sh.canon[0], sh.canon[1]};
-      tr_absorb_n<2>(sh.st, 'V', canon);
+      tr_absorb_n<2, false>(sh.st, 'V', canon);
       if (!p.last) {
-        S->alpha = tr_challenge_st(sh.st, &S->error, true);
-        S->beta = tr_challenge_st(sh.st, &S->error, false);
+        S->alpha = tr_challenge_st<false>(sh.st, &S->error, true);
+        S->beta = tr_challenge_st<false>(sh.st, &S->error, false);
       }
 #pragma unroll
       for (int i = 0; i < 8; ++i) S->st[i] = sh.st[i];

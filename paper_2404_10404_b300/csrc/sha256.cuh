@@ -141,10 +141,18 @@ struct ShaWords16 {
 
 #ifdef __CUDACC__
 // One out-of-line copy of the fully unrolled compression per translation
-// unit for the single-thread transcript (on one thread the unrolled rounds
-// run about 1.4x faster than the compact loop).
+// unit for the single-thread transcript: with its code in the instruction
+// caches the unrolled rounds run about 1.4x faster than the compact loop.
 static __device__ __noinline__ ShaWords8 sha256_compress_v(ShaWords8 h, ShaWords16 blk) {
   sha256_compress(h.w, blk.w);
+  return h;
+}
+// The compact loop (a quarter of the code) for a transcript that runs cold,
+// once at the end of a kernel whose main loop evicted it: there fetching
+// the unrolled code costs more than the loop saves (measured in the
+// copy-phase rounds).
+static __device__ __noinline__ ShaWords8 sha256_compress_small_v(ShaWords8 h, ShaWords16 blk) {
+  sha256_compress_compact(h.w, blk.w);
   return h;
 }
 #endif
