@@ -120,10 +120,11 @@ void sisu_transcript_destroy(sisu_transcript* tr);
  * device, enqueued on `stream`, with challenges kept in device memory; the
  * call blocks once at the end to copy the proof out.  Deterministic: the
  * same (circuit, inputs, domain) give the same bytes.
- * Proof layout: "SISUGKR1" || u32le d || u32le c || u32le s_0..s_d, then for
- * each layer i = 0..d-1: c x 4 elements (copy rounds, evaluations at
- * t = 0..3) || s_{i+1} x 3 (x rounds, t = 0..2) || s_{i+1} x 3 (y rounds) ||
- * v_x || v_y.
+ * Proof layout: "SISUGKR2" || u32le d || u32le c || u32le s_0..s_d, then for
+ * each layer i = 0..d-1: c x 3 elements (copy rounds: the round
+ * polynomial at t = 0, 2, 3) || s_{i+1} x 2 (x rounds, t = 0, 2) ||
+ * s_{i+1} x 2 (y rounds) || v_x || v_y.  A round leaves out g(1): the
+ * verifier takes it as the running claim minus g(0).
  * sisu_gkr_prove allocates *proof (free it with sisu_free);
  * sisu_gkr_prove_into writes into the caller's buffer of `cap` bytes.
  * The first proof on an eval handle allocates the prover's workspace

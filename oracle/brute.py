@@ -264,7 +264,7 @@ def prove(circ, inputs, domain: bytes | None = None, check: bool = True,
     tr = Transcript(domain, d, c, pc.s, digest(pc.wiring_bytes()),
                     digest(b"".join(fe(v) for v in Vs)),
                     digest(b"".join(fe(v) for v in V[0])))
-    out = bytearray(b"SISUGKR1" + struct.pack("<II", d, c) + b"".join(struct.pack("<I", v) for v in pc.s))
+    out = bytearray(b"SISUGKR2" + struct.pack("<II", d, c) + b"".join(struct.pack("<I", v) for v in pc.s))
     zb = [tr.challenge() for _ in range(c)]
     zg = [tr.challenge() for _ in range(pc.s[0])]
     claim = mle(V[0], zb + zg)
@@ -288,8 +288,9 @@ def prove(circ, inputs, domain: bytes | None = None, check: bool = True,
                 g.append(sum(f(bound + [t] + bits_msb(u, rest)) for u in range(1 << rest)) % P)
             if check:
                 assert (g[0] + g[1]) % P == claim, f"layer {i} round {k}: g(0)+g(1) != claim"
-            out += b"".join(fe(v) for v in g)
-            tr.absorb(b"R", g)
+            sent = [g[0]] + g[2:]  # g(1) = claim - g(0) is left to the verifier
+            out += b"".join(fe(v) for v in sent)
+            tr.absorb(b"R", sent)
             r = tr.challenge()
             claim = interpolate(g, r)
             bound.append(r)
@@ -324,15 +325,16 @@ def forge_one_layer(circ, inputs, fake_outputs, domain: bytes | None = None) -> 
             V0[b * pc.W[0] + g] = fake_outputs[b * pc.wreal[0] + g]
     tr = Transcript(domain, 1, c, pc.s, digest(pc.wiring_bytes()),
                     digest(b"".join(fe(v) for v in V[1])), digest(b"".join(fe(v) for v in V0)))
-    out = bytearray(b"SISUGKR1" + struct.pack("<II", 1, c) + b"".join(struct.pack("<I", v) for v in pc.s))
+    out = bytearray(b"SISUGKR2" + struct.pack("<II", 1, c) + b"".join(struct.pack("<I", v) for v in pc.s))
     zb = [tr.challenge() for _ in range(c)]
     zg = [tr.challenge() for _ in range(pc.s[0])]
     claim = mle(V0, zb + zg)
     bound = []
     for k in range(c + 2 * s):
-        g = [claim] + [0] * (3 if k < c else 2)
-        out += b"".join(fe(v) for v in g)
-        tr.absorb(b"R", g)
+        g = [claim] + [0] * (3 if k < c else 2)  # g(1) = claim - g(0) = 0
+        sent = [g[0]] + g[2:]
+        out += b"".join(fe(v) for v in sent)
+        tr.absorb(b"R", sent)
         r = tr.challenge()
         claim = interpolate(g, r)
         bound.append(r)
@@ -355,7 +357,7 @@ def forge_vy_one_layer(circ, inputs, domain: bytes | None = None) -> bytes:
     V = evaluate(pc, inputs)
     tr = Transcript(domain, 1, c, pc.s, digest(pc.wiring_bytes()),
                     digest(b"".join(fe(v) for v in V[1])), digest(b"".join(fe(v) for v in V[0])))
-    out = bytearray(b"SISUGKR1" + struct.pack("<II", 1, c) + b"".join(struct.pack("<I", v) for v in pc.s))
+    out = bytearray(b"SISUGKR2" + struct.pack("<II", 1, c) + b"".join(struct.pack("<I", v) for v in pc.s))
     zb = [tr.challenge() for _ in range(c)]
     zg = [tr.challenge() for _ in range(pc.s[0])]
     claim = mle(V[0], zb + zg)
@@ -369,8 +371,9 @@ def forge_vy_one_layer(circ, inputs, domain: bytes | None = None) -> bytes:
             g = [sum(f(bound + [t] + bits_msb(u, rest)) for u in range(1 << rest)) % P for t in range(nodes)]
         else:
             g = [claim, 0, 0]
-        out += b"".join(fe(v) for v in g)
-        tr.absorb(b"R", g)
+        sent = [g[0]] + g[2:]
+        out += b"".join(fe(v) for v in sent)
+        tr.absorb(b"R", sent)
         r = tr.challenge()
         claim = interpolate(g, r)
         bound.append(r)

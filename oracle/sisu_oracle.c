@@ -546,7 +546,7 @@ uint32_t so_circuit_log_width(const so_circuit *cc, uint32_t i) { return cc->s[i
 
 size_t so_proof_len(const so_circuit *cc) {
     size_t n = 8 + 4 * ((size_t)cc->d + 3);
-    for (uint32_t i = 0; i < cc->d; ++i) n += 32 * (4 * (size_t)cc->c + 6 * (size_t)cc->s[i + 1] + 2);
+    for (uint32_t i = 0; i < cc->d; ++i) n += 32 * (3 * (size_t)cc->c + 4 * (size_t)cc->s[i + 1] + 2);
     return n;
 }
 
@@ -650,7 +650,7 @@ static void put_fr(writer *w, fr x) {
 }
 
 static void put_hdr(writer *w, const so_circuit *cc) {
-    static const char magic[8] = {'S', 'I', 'S', 'U', 'G', 'K', 'R', '1'};
+    static const char magic[8] = {'S', 'I', 'S', 'U', 'G', 'K', 'R', '2'};
     uint8_t u[4];
     if (w->cap >= 8) memcpy(w->buf, magic, 8);
     w->len = 8;
@@ -743,6 +743,16 @@ static void absorb_and_put(transcript *tr, writer *w, uint8_t tag, const fr *e, 
     tr_absorb(tr, tag, e, n);
 }
 
+/* A round message: the round polynomial's values at t = 0, 2, ..., n - 1
+ * (n = 4 in the copy phase, 3 in the x and y phases).  g(1) is left out:
+ * the verifier takes it as claim - g(0), the sumcheck's own relation. */
+static void send_round(transcript *tr, writer *w, const fr *g, int n) {
+    fr sent[3];
+    sent[0] = g[0];
+    for (int t = 2; t < n; ++t) sent[t - 1] = g[t];
+    absorb_and_put(tr, w, 'R', sent, n - 1);
+}
+
 int so_prove(const so_circuit *cc, const uint8_t *inputs, const uint8_t *domain, size_t dlen,
              uint8_t *proof, size_t cap, size_t *len_out) {
     uint32_t d = cc->d, c = cc->c;
@@ -778,7 +788,7 @@ int so_prove(const so_circuit *cc, const uint8_t *inputs, const uint8_t *domain,
         for (uint32_t k = 1; k <= c; ++k) {
             fr g4[4];
             copy_round(cc, i, T, n, omega, zb, rb, k, g4);
-            absorb_and_put(&tr, &w, 'R', g4, 4);
+            send_round(&tr, &w, g4, 4);
             rb[k - 1] = tr_challenge(&tr);
             fold_rows(T, n, Wn, rb[k - 1]);
             n /= 2;
@@ -795,7 +805,7 @@ int so_prove(const so_circuit *cc, const uint8_t *inputs, const uint8_t *domain,
         for (uint32_t k = 1; k <= s; ++k) {
             fr g3[3];
             gate_round(cc, i, 1, A, A0, omega, pre, e, fr_zero(), k, g3);
-            absorb_and_put(&tr, &w, 'R', g3, 3);
+            send_round(&tr, &w, g3, 3);
             rx[k - 1] = tr_challenge(&tr);
             fold_rows(A, (size_t)1 << (s - k + 1), 1, rx[k - 1]);
             for (uint32_t g = 0; g < W; ++g)
@@ -808,7 +818,7 @@ int so_prove(const so_circuit *cc, const uint8_t *inputs, const uint8_t *domain,
         for (uint32_t k = 1; k <= s; ++k) {
             fr g3[3];
             gate_round(cc, i, 2, A, A0, omega, pre, e, vx, k, g3);
-            absorb_and_put(&tr, &w, 'R', g3, 3);
+            send_round(&tr, &w, g3, 3);
             ry[k - 1] = tr_challenge(&tr);
             fold_rows(A, (size_t)1 << (s - k + 1), 1, ry[k - 1]);
             for (uint32_t g = 0; g < W; ++g)
@@ -896,20 +906,25 @@ int so_verify(const so_circuit *cc, const uint8_t *inputs, const uint8_t *output
     int ok = 1;
     for (uint32_t i = 0; i < d && ok; ++i) {
         uint32_t W = cc->W[i], s = cc->s[i + 1];
+        /* each round: g(0), g(2)[, g(3)] from the proof, g(1) = claim - g(0) */
         for (uint32_t k = 0; k < c && ok; ++k) {
-            fr g[4];
-            for (int t = 0; t < 4; ++t) g[t] = get_fr(&rd);
-            if (rd.bad || !fr_eq(fr_add(g[0], g[1]), claim)) { ok = 0; break; }
-            tr_absorb(&tr, 'R', g, 4);
+            fr g[4], sent[3];
+            for (int t = 0; t < 3; ++t) sent[t] = get_fr(&rd);
+            if (rd.bad) { ok = 0; break; }
+            g[0] = sent[0]; g[2] = sent[1]; g[3] = sent[2];
+            g[1] = fr_sub(claim, g[0]);
+            tr_absorb(&tr, 'R', sent, 3);
             rb[k] = tr_challenge(&tr);
             claim = interpolate(g, 4, rb[k]);
         }
         for (int phase = 0; phase < 2 && ok; ++phase)
             for (uint32_t k = 0; k < s && ok; ++k) {
-                fr g[3];
-                for (int t = 0; t < 3; ++t) g[t] = get_fr(&rd);
-                if (rd.bad || !fr_eq(fr_add(g[0], g[1]), claim)) { ok = 0; break; }
-                tr_absorb(&tr, 'R', g, 3);
+                fr g[3], sent[2];
+                for (int t = 0; t < 2; ++t) sent[t] = get_fr(&rd);
+                if (rd.bad) { ok = 0; break; }
+                g[0] = sent[0]; g[2] = sent[1];
+                g[1] = fr_sub(claim, g[0]);
+                tr_absorb(&tr, 'R', sent, 2);
                 fr r = tr_challenge(&tr);
                 if (phase == 0) rx[k] = r; else ry[k] = r;
                 claim = interpolate(g, 3, r);

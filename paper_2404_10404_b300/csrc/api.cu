@@ -59,7 +59,7 @@ static uint32_t ceil_log2(uint64_t v) {
 namespace sisu {
 size_t HostCircuit::proof_len() const {
   size_t n = 8 + 4 * ((size_t)d + 3);
-  for (uint32_t i = 0; i < d; ++i) n += 32 * (4 * (size_t)c + 6 * (size_t)s[i + 1] + 2);
+  for (uint32_t i = 0; i < d; ++i) n += 32 * (3 * (size_t)c + 4 * (size_t)s[i + 1] + 2);
   return n;
 }
 }  // namespace sisu
@@ -592,7 +592,7 @@ static int workspace_init(sisu_eval* ev, Workspace* ws, uint8_t* dev, uint8_t* h
   ws->host = host;
   // the proof header is fixed by the circuit
   std::vector<uint8_t> hdr(8 + 4 * ((size_t)hc.d + 3));
-  memcpy(hdr.data(), "SISUGKR1", 8);
+  memcpy(hdr.data(), "SISUGKR2", 8);
   auto put = [&](size_t at, uint32_t v) {
     hdr[at] = (uint8_t)v; hdr[at + 1] = (uint8_t)(v >> 8); hdr[at + 2] = (uint8_t)(v >> 16); hdr[at + 3] = (uint8_t)(v >> 24);
   };
@@ -680,7 +680,7 @@ static int enqueue_prove(const sisu_circuit* cc, sisu_eval* ev, const sisu_trans
       const uint32_t h = hc.C >> (k + 1);
       {
         ProfScope ps(kProfCopyRound, per_pair * h, st);
-        CK(launch_copy_round(tab, sn, h, w.E, w.om, L, w.partials, w.S, w.proof, off + 32 * 4 * (size_t)k, k, st),
+        CK(launch_copy_round(tab, sn, h, w.E, w.om, L, w.partials, w.S, w.proof, off + 32 * 3 * (size_t)k, k, st),
            "copy round");
       }
       {
@@ -689,9 +689,9 @@ static int enqueue_prove(const sisu_circuit* cc, sisu_eval* ev, const sisu_trans
       }
       A = w.T;
     }
-    const size_t offx = off + 32 * 4 * (size_t)c;
-    const size_t offy = offx + 32 * 3 * (size_t)s;
-    const size_t offv = offy + 32 * 3 * (size_t)s;
+    const size_t offx = off + 32 * 3 * (size_t)c;  // a copy round sends 3 values, an x/y round 2
+    const size_t offy = offx + 32 * 2 * (size_t)s;
+    const size_t offv = offy + 32 * 2 * (size_t)s;
     if (Wn <= kTailMaxWidth) {
       // Libra's two phases and the end of the layer in one cluster launch
       TailParams tp;
@@ -712,7 +712,7 @@ static int enqueue_prove(const sisu_circuit* cc, sisu_eval* ev, const sisu_trans
     }
     for (uint32_t k = 0; k < s; ++k) {
       ProfScope ps(kProfGateRound, (double)(Wn >> k) / 2 * (k ? 9.0 : 3.0), st);
-      CK(launch_gate_round(w.At, w.H1, w.H2, Wn >> k, 0, k, w.partials, w.S, w.proof, offx + 96 * (size_t)k, st),
+      CK(launch_gate_round(w.At, w.H1, w.H2, Wn >> k, 0, k, w.partials, w.S, w.proof, offx + 64 * (size_t)k, st),
          "x round");
     }
     {
@@ -722,7 +722,7 @@ static int enqueue_prove(const sisu_circuit* cc, sisu_eval* ev, const sisu_trans
     }
     for (uint32_t k = 0; k < s; ++k) {
       ProfScope ps(kProfGateRound, (double)(Wn >> k) / 2 * (k ? 9.0 : 3.0), st);
-      CK(launch_gate_round(w.Ay, w.H1, w.H2, Wn >> k, 1, k, w.partials, w.S, w.proof, offy + 96 * (size_t)k, st),
+      CK(launch_gate_round(w.Ay, w.H1, w.H2, Wn >> k, 1, k, w.partials, w.S, w.proof, offy + 64 * (size_t)k, st),
          "y round");
     }
     {

@@ -125,30 +125,34 @@ __device__ __forceinline__ Fr tr_challenge(DevState* S, bool fresh) {
 }
 
 // The last block of a round, called by the lanes of its warp 0 with the
-// grid-wide sums in lane 0: canonical evaluations (one lane each) into the
-// proof, absorb 'R', squeeze the round's challenge.  The sums are plain
-// (not Montgomery) values below 2r: the copy weights E and the Libra tables
-// H, K are kept plain, so one conditional subtraction makes them canonical.
+// grid-wide sums g(0..NV-1) in lane 0: the round message g(0), g(2), ...,
+// g(NV-1) (g(1) is left out: the verifier takes it as the claim minus g(0))
+// as canonical values into the proof, one lane each, then absorb 'R' and
+// squeeze the round's challenge.  The sums are plain (not Montgomery)
+// values below 2r: the copy weights E and the Libra tables H, K are kept
+// plain, so one conditional subtraction makes them canonical.
 template <int NV>
 __device__ __forceinline__ void round_finalize(DevState* S, const Fr (&v)[NV], uint8_t* proof, size_t off,
                                                Fr* rslot) {
   __shared__ Fr sh[NV];
   const int lane = threadIdx.x & 31;
-  if (lane == 0)
+  if (lane == 0) {
+    sh[0] = v[0];
 #pragma unroll
-    for (int t = 0; t < NV; ++t) sh[t] = v[t];
+    for (int t = 2; t < NV; ++t) sh[t - 1] = v[t];
+  }
   __syncwarp();
-  if (lane < NV) {
+  if (lane < NV - 1) {
     Fr c = fr_reduce_once(sh[lane]);
     store_words(proof, off + 32 * (size_t)lane, c);
     sh[lane] = c;
   }
   __syncwarp();
   if (lane == 0) {
-    Fr canon[NV];
+    Fr canon[NV - 1];
 #pragma unroll
-    for (int t = 0; t < NV; ++t) canon[t] = sh[t];
-    tr_absorb_n<NV, true>(S->st, 'R', canon);
+    for (int t = 0; t < NV - 1; ++t) canon[t] = sh[t];
+    tr_absorb_n<NV - 1, true>(S->st, 'R', canon);
     *rslot = tr_challenge(S, true);
   }
 }
@@ -705,7 +709,7 @@ constexpr int kTailCTAs = 8;
 constexpr int kTailThreads = 256;
 
 struct TailShared {
-  Fr part[kTailCTAs][3];  // partial sums of every CTA (each CTA sends its own to all)
+  Fr part[kTailCTAs][2];  // partial sums g(0), g(2) of every CTA (each CTA sends its own to all)
   Fr canon[3];            // canonical round values
   Fr bcast;               // the round's challenge, for every thread of the CTA
   Fr vx;                  // CTA 0: v_x, read by every CTA
@@ -716,7 +720,8 @@ struct TailShared {
 };
 
 // One round over tables (A, B1, B2) of size m (after the fold of `rprev`
-// when k > 0): g(t) = sum_{j < m/2} A_t(j) B1_t(j) + B2_t(j), t = 0, 1, 2.
+// when k > 0): g(t) = sum_{j < m/2} A_t(j) B1_t(j) + B2_t(j) for t = 0 and
+// t = 2, the round message (g(1) is the claim minus g(0), for the verifier).
 // A is in Montgomery form and B1, B2 are plain, so the products and the
 // sums are plain.  The round runs in two cluster-wide steps, each thread
 // doing at most a few products: the fold (one product per new table
@@ -741,33 +746,31 @@ __device__ Fr tail_round(cg::cluster_group& cl, TailShared& sh, uint32_t* A, uin
     cl.sync();
   }
   const uint32_t hq = m / 2;
-  Fr acc0 = fr_zero(), acc1 = fr_zero(), acc2 = fr_zero();
-  for (uint32_t q = gtid; q < 3 * hq; q += gstride) {
-    const uint32_t j = q / 3, t = q - 3 * j;
+  Fr acc0 = fr_zero(), acc2 = fr_zero();
+  for (uint32_t q = gtid; q < 2 * hq; q += gstride) {
+    const uint32_t j = q >> 1;
     Fr a = fr_load_cg(A, j), p = fr_load_cg(B1, j), c = fr_load_cg(B2, j);
-    if (t > 0) {
-      const Fr da = fr_sub(fr_load_cg(A, j + hq), a), dp = fr_sub(fr_load_cg(B1, j + hq), p),
-               dc = fr_sub(fr_load_cg(B2, j + hq), c);
-      a = fr_add(a, da); p = fr_add(p, dp); c = fr_add(c, dc);
-      if (t == 2) { a = fr_add(a, da); p = fr_add(p, dp); c = fr_add(c, dc); }
+    if (q & 1) {  // t = 2: X_2 = 2 X(j + m/2) - X(j)
+      a = fr_sub(fr_dbl(fr_load_cg(A, j + hq)), a);
+      p = fr_sub(fr_dbl(fr_load_cg(B1, j + hq)), p);
+      c = fr_sub(fr_dbl(fr_load_cg(B2, j + hq)), c);
     }
     const Fr v = fr_add(fr_mul(a, p), c);
-    if (t == 0) acc0 = fr_add(acc0, v);
-    else if (t == 1) acc1 = fr_add(acc1, v);
-    else acc2 = fr_add(acc2, v);
+    if (q & 1) acc2 = fr_add(acc2, v);
+    else acc0 = fr_add(acc0, v);
   }
-  Fr acc[3] = {acc0, acc1, acc2};
-  // CTA sum, then into CTA 0's shared memory
+  Fr acc[2] = {acc0, acc2};
+  // CTA sum, then to every CTA's shared memory
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int t = 0; t < 3; ++t) acc[t] = fr_warp_sum(acc[t]);
+  for (int t = 0; t < 2; ++t) acc[t] = fr_warp_sum(acc[t]);
   if (lane == 0)
 #pragma unroll
-    for (int t = 0; t < 3; ++t) sh.red[t][warp] = acc[t];
+    for (int t = 0; t < 2; ++t) sh.red[t][warp] = acc[t];
   __syncthreads();
   if (warp == 0) {
 #pragma unroll
-    for (int t = 0; t < 3; ++t) {
+    for (int t = 0; t < 2; ++t) {
       acc[t] = fr_warp_sum(lane < kTailThreads / 32 ? sh.red[t][lane] : fr_zero());
 #pragma unroll
       for (int i = 0; i < 8; ++i) acc[t].v[i] = __shfl_sync(0xffffffffu, acc[t].v[i], 0);
@@ -775,12 +778,12 @@ __device__ Fr tail_round(cg::cluster_group& cl, TailShared& sh, uint32_t* A, uin
     if (lane < kTailCTAs) {  // lane d sends this CTA's sums to CTA d
       Fr* dst = cl.map_shared_rank(&sh.part[0][0], lane);
 #pragma unroll
-      for (int t = 0; t < 3; ++t) dst[rank * 3 + t] = acc[t];
+      for (int t = 0; t < 2; ++t) dst[rank * 2 + t] = acc[t];
     }
   }
   cl.sync();
   if (warp == 0) {
-    if (lane < 3) {
+    if (lane < 2) {  // the message g(0), g(2)
       Fr v = fr_zero();
 #pragma unroll
       for (int c = 0; c < kTailCTAs; ++c) v = fr_add(v, sh.part[c][lane]);
@@ -790,8 +793,8 @@ __device__ Fr tail_round(cg::cluster_group& cl, TailShared& sh, uint32_t* A, uin
     }
     __syncwarp();
     if (lane == 0) {
-      Fr canon[3] = {sh.canon[0], sh.canon[1], sh.canon[2]};
-      tr_absorb_n<3, false>(sh.st, 'R', canon);
+      Fr canon[2] = {sh.canon[0], sh.canon[1]};
+      tr_absorb_n<2, false>(sh.st, 'R', canon);
       const Fr r = tr_challenge_st<false>(sh.st, &S->error, true);
       if (rank == 0) *rslot = r;
       sh.bcast = r;
@@ -833,7 +836,7 @@ __global__ void __cluster_dims__(kTailCTAs, 1, 1) __launch_bounds__(kTailThreads
   cl.sync();
   Fr r = fr_zero();
   for (uint32_t k = 0; k < p.s; ++k) {
-    r = tail_round(cl, sh, p.At, p.H1, p.H2, p.Wn >> k, k, r, S, p.proof, p.offx + 96 * (size_t)k, &S->rx[k]);
+    r = tail_round(cl, sh, p.At, p.H1, p.H2, p.Wn >> k, k, r, S, p.proof, p.offx + 64 * (size_t)k, &S->rx[k]);
     if (threadIdx.x == 0) {  // r_x,k and 1 - r_x,k for eq(r_x, .)
       sh.rx[1][k] = r;
       sh.rx[0][k] = fr_sub(fr_one(), r);
@@ -876,7 +879,7 @@ __global__ void __cluster_dims__(kTailCTAs, 1, 1) __launch_bounds__(kTailThreads
   }
   cl.sync();
   for (uint32_t k = 0; k < p.s; ++k)
-    r = tail_round(cl, sh, p.Ay, p.H1, p.H2, p.Wn >> k, k, r, S, p.proof, p.offy + 96 * (size_t)k, &S->ry[k]);
+    r = tail_round(cl, sh, p.Ay, p.H1, p.H2, p.Wn >> k, k, r, S, p.proof, p.offy + 64 * (size_t)k, &S->ry[k]);
   // end of the layer: v_y, (v_x, v_y) into the proof, absorb 'V', alpha, beta
   if (rank == 0 && threadIdx.x < 32) {
     const int lane = threadIdx.x;

@@ -337,7 +337,7 @@ int host_verify(const HostCircuit& hc, const uint8_t* inputs, const uint8_t* out
   // header
   {
     std::vector<uint8_t> hdr(8 + 4 * ((size_t)d + 3));
-    memcpy(hdr.data(), "SISUGKR1", 8);
+    memcpy(hdr.data(), "SISUGKR2", 8);
     auto put = [&](size_t at, uint32_t v) {
       for (int k = 0; k < 4; ++k) hdr[at + k] = (uint8_t)(v >> (8 * k));
     };
@@ -387,22 +387,25 @@ int host_verify(const HostCircuit& hc, const uint8_t* inputs, const uint8_t* out
   for (uint32_t i = 0; i < d; ++i) {
     const uint32_t s = hc.s[i + 1], W = hc.W[i];
     std::vector<HF> rb(c), rx(s), ry(s);
+    // each round sends g(0), g(2)[, g(3)]; g(1) = claim - g(0)
     for (uint32_t k = 0; k < c; ++k) {
-      HF g[4];
-      for (auto& v : g)
+      HF g[4], sent[3];
+      for (auto& v : sent)
         if (!next(&v)) return SISU_ERR_REJECT;
-      if (!eq(add(g[0], g[1]), claim)) return SISU_ERR_REJECT;
-      tr.absorb('R', g, 4);
+      g[0] = sent[0]; g[2] = sent[1]; g[3] = sent[2];
+      g[1] = sub(claim, g[0]);
+      tr.absorb('R', sent, 3);
       rb[k] = tr.challenge();
       claim = lag.at(g, 4, rb[k]);
     }
     for (int phase = 0; phase < 2; ++phase)
       for (uint32_t k = 0; k < s; ++k) {
-        HF g[3];
-        for (auto& v : g)
+        HF g[3], sent[2];
+        for (auto& v : sent)
           if (!next(&v)) return SISU_ERR_REJECT;
-        if (!eq(add(g[0], g[1]), claim)) return SISU_ERR_REJECT;
-        tr.absorb('R', g, 3);
+        g[0] = sent[0]; g[2] = sent[1];
+        g[1] = sub(claim, g[0]);
+        tr.absorb('R', sent, 2);
         HF r = tr.challenge();
         (phase == 0 ? rx : ry)[k] = r;
         claim = lag.at(g, 3, r);

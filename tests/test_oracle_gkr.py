@@ -6,7 +6,8 @@
   squaring circuits.
 - Prover: byte-identical to the brute-force generic sumcheck of
   ``oracle/brute.py`` (which asserts g(0)+g(1) = claim every round, the check
-  of Sec. 3.2.1, and the final identity of every layer) on micro circuits,
+  of Sec. 3.2.1, before leaving g(1) out of the message, and the final
+  identity of every layer) on micro circuits,
   including padded widths and copy counts (Sec. 2.2 padding), all-add,
   all-mul and in1 = in2 wiring.
 - Verifier: accepts honest proofs, rejects tampered proofs, outputs, inputs,
@@ -125,8 +126,10 @@ def test_proof_length_formula(oracle):
         d = len(widths) - 1
         c = brute.log2_ceil(C)
         s = [brute.log2_ceil(w) for w in widths]
-        assert oracle.proof_len(circ) == 8 + 4 * (d + 3) + 32 * sum(4 * c + 6 * s[i + 1] + 2 for i in range(d))
-    assert oracle.proof_len(synth.tiny()) == 20020
+        # per layer: 3 values per copy round, 2 per x and y round (g(1) left
+        # out), then v_x and v_y
+        assert oracle.proof_len(circ) == 8 + 4 * (d + 3) + 32 * sum(3 * c + 4 * s[i + 1] + 2 for i in range(d))
+    assert oracle.proof_len(synth.tiny()) == 13876
 
 
 # -- verifier: tampering -------------------------------------------------------

@@ -51,6 +51,10 @@ MUTANTS = {
                              "if (0) { ok = 0; break; }"),
     "verifier_skips_input": ("if (!fr_eq(vy, mle_by_folding(Vin, c + s, pt))) { ok = 0; break; }",
                              "if (0) { ok = 0; break; }"),
+    "verifier_g1_sign": ("g[0] = sent[0]; g[2] = sent[1]; g[3] = sent[2];\n            g[1] = fr_sub(claim, g[0]);",
+                         "g[0] = sent[0]; g[2] = sent[1]; g[3] = sent[2];\n            g[1] = fr_sub(g[0], claim);"),
+    "prover_sends_g1": ("sent[0] = g[0];\n    for (int t = 2; t < n; ++t) sent[t - 1] = g[t];",
+                        "sent[0] = g[0];\n    for (int t = 2; t < n; ++t) sent[t - 1] = g[t - 1];"),
     "interp_wrong_node": ("num = fr_mul(num, fr_sub(x, fr_u64((uint64_t)j)));",
                           "num = fr_mul(num, fr_sub(x, fr_u64((uint64_t)j + 1)));"),
 }
