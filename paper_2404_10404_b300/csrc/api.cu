@@ -541,8 +541,8 @@ static void workspace_sizes(const sisu_circuit* cc, size_t sizes[kWsRegions]) {
   }
   for (uint32_t i = 0; i <= hc.d; ++i) wmax = std::max(wmax, hc.W[i]);
   const size_t half = hc.C >= 2 ? (size_t)(hc.C / 2) * wmax_next * 32 : 32;
-  const size_t dig = std::max(digest_scratch_words((size_t)hc.C * hc.W[hc.d] * 32),
-                              digest_scratch_words((size_t)hc.C * hc.W[0] * 32)) * 4;
+  const size_t dig = (digest_scratch_words((size_t)hc.C * hc.W[hc.d] * 32) +
+                      digest_scratch_words((size_t)hc.C * hc.W[0] * 32)) * 4;
   uint32_t smax = 0;
   for (uint32_t i = 0; i < hc.d; ++i) smax = std::max(smax, hc.s[i]);
   const size_t v[kWsRegions] = {half, (size_t)hc.C * 32, (size_t)nmax * 32, (size_t)wmax_next * 32,
@@ -643,8 +643,9 @@ static int enqueue_prove(const sisu_circuit* cc, sisu_eval* ev, const sisu_trans
   // statement digests of the inputs and outputs (the wiring's is cached)
   {
     ProfScope ps(kProfDigest, 0, st);
-    CK(launch_digest_table(ev->V[d], (size_t)hc.C << hc.s[d], w.dscratch, w.S->dig_in, st), "input digest");
-    CK(launch_digest_table(ev->V[0], (size_t)hc.C << hc.s[0], w.dscratch, w.S->dig_out, st), "output digest");
+    CK(launch_digest_tables2(ev->V[d], (size_t)hc.C << hc.s[d], ev->V[0], (size_t)hc.C << hc.s[0], w.dscratch,
+                             w.S->dig_in, w.S->dig_out, st),
+       "statement digests");
   }
   InitParams ip;
   memset(&ip, 0, sizeof ip);

@@ -108,35 +108,46 @@ __device__ __forceinline__ void elem_words(const uint32_t* tab, size_t i, uint32
   for (int k = 0; k < 8; ++k) w[k] = bswap32(v.v[k]);
 }
 
-__global__ void k_digest_leaves_table(const uint32_t* __restrict__ tab, size_t nelem, uint32_t* __restrict__ out) {
-  const size_t nleaf = (nelem + 31) / 32;
-  for (size_t L = blockIdx.x * (size_t)blockDim.x + threadIdx.x; L < nleaf; L += (size_t)gridDim.x * blockDim.x) {
-    const size_t first = L * 32;
-    const uint32_t count = (uint32_t)min((size_t)32, nelem - first);
-    uint32_t h[8], blk[16];
-    sha256_init(h);
-    uint32_t e = 0;
-    for (; e + 1 < count; e += 2) {
-      elem_words(tab, first + e, blk);
-      elem_words(tab, first + e + 1, blk + 8);
-      sha256_compress(h, blk);
-    }
-    const uint64_t bits = ((uint64_t)count * 32 + 1) * 8;
-    if (e < count) {  // one element left: it, the tag and the length fit one block
-      elem_words(tab, first + e, blk);
-      blk[8] = 0x00800000u;
-#pragma unroll
-      for (int k = 9; k < 14; ++k) blk[k] = 0;
-    } else {
-      blk[0] = 0x00800000u;
-#pragma unroll
-      for (int k = 1; k < 14; ++k) blk[k] = 0;
-    }
-    blk[14] = (uint32_t)(bits >> 32);
-    blk[15] = (uint32_t)bits;
+// leaf L of a table of nelem elements: H(32 canonical elements || 0x00)
+__device__ __forceinline__ void digest_leaf_table(const uint32_t* __restrict__ tab, size_t nelem, size_t L,
+                                                  uint32_t* __restrict__ out) {
+  const size_t first = L * 32;
+  const uint32_t count = (uint32_t)min((size_t)32, nelem - first);
+  uint32_t h[8], blk[16];
+  sha256_init(h);
+  uint32_t e = 0;
+  for (; e + 1 < count; e += 2) {
+    elem_words(tab, first + e, blk);
+    elem_words(tab, first + e + 1, blk + 8);
     sha256_compress(h, blk);
+  }
+  const uint64_t bits = ((uint64_t)count * 32 + 1) * 8;
+  if (e < count) {  // one element left: it, the tag and the length fit one block
+    elem_words(tab, first + e, blk);
+    blk[8] = 0x00800000u;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) out[L * 8 + k] = h[k];
+    for (int k = 9; k < 14; ++k) blk[k] = 0;
+  } else {
+    blk[0] = 0x00800000u;
+#pragma unroll
+    for (int k = 1; k < 14; ++k) blk[k] = 0;
+  }
+  blk[14] = (uint32_t)(bits >> 32);
+  blk[15] = (uint32_t)bits;
+  sha256_compress(h, blk);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) out[L * 8 + k] = h[k];
+}
+
+// The leaves of two tables in one launch (the statement's inputs and
+// outputs): one grid over both, so neither digest leaves SMs idle in its
+// last wave.
+__global__ void k_digest_leaves_table2(const uint32_t* __restrict__ ta, size_t na, uint32_t* __restrict__ oa,
+                                       const uint32_t* __restrict__ tb, size_t nb, uint32_t* __restrict__ ob) {
+  const size_t la = (na + 31) / 32, lb = (nb + 31) / 32;
+  for (size_t L = blockIdx.x * (size_t)blockDim.x + threadIdx.x; L < la + lb; L += (size_t)gridDim.x * blockDim.x) {
+    if (L < la) digest_leaf_table(ta, na, L, oa);
+    else digest_leaf_table(tb, nb, L - la, ob);
   }
 }
 
@@ -154,34 +165,49 @@ __global__ void k_digest_leaves_bytes(const uint8_t* __restrict__ data, size_t l
   }
 }
 
-__global__ void k_digest_level(const uint32_t* __restrict__ src, size_t n, uint32_t* __restrict__ dst) {
-  const size_t m = (n + 1) / 2;
-  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < m; j += (size_t)gridDim.x * blockDim.x) {
-    if (2 * j + 1 < n) {
-      uint32_t h[8], blk[16];
-      sha256_init(h);
+// node j of the next level over n nodes: H(left || right || 0x01), or the
+// odd last node moved up
+__device__ __forceinline__ void digest_node(const uint32_t* __restrict__ src, size_t n, size_t j,
+                                            uint32_t* __restrict__ dst) {
+  if (2 * j + 1 < n) {
+    uint32_t h[8], blk[16];
+    sha256_init(h);
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        blk[k] = src[16 * j + k];
-        blk[8 + k] = src[16 * j + 8 + k];
-      }
-      sha256_compress(h, blk);
-      blk[0] = 0x01800000u;
-#pragma unroll
-      for (int k = 1; k < 15; ++k) blk[k] = 0;
-      blk[15] = 65 * 8;
-      sha256_compress(h, blk);
-#pragma unroll
-      for (int k = 0; k < 8; ++k) dst[8 * j + k] = h[k];
-    } else {
-#pragma unroll
-      for (int k = 0; k < 8; ++k) dst[8 * j + k] = src[16 * j + k];
+    for (int k = 0; k < 8; ++k) {
+      blk[k] = src[16 * j + k];
+      blk[8 + k] = src[16 * j + 8 + k];
     }
+    sha256_compress(h, blk);
+    blk[0] = 0x01800000u;
+#pragma unroll
+    for (int k = 1; k < 15; ++k) blk[k] = 0;
+    blk[15] = 65 * 8;
+    sha256_compress(h, blk);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) dst[8 * j + k] = h[k];
+  } else {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) dst[8 * j + k] = src[16 * j + k];
   }
 }
 
-__global__ void k_digest_final(const uint32_t* root, uint64_t len, int empty, uint32_t* out) {
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+__global__ void k_digest_level(const uint32_t* __restrict__ src, size_t n, uint32_t* __restrict__ dst) {
+  const size_t m = (n + 1) / 2;
+  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < m; j += (size_t)gridDim.x * blockDim.x)
+    digest_node(src, n, j, dst);
+}
+
+// one level of two trees (a tree already at its root has no nodes to add)
+__global__ void k_digest_level2(const uint32_t* __restrict__ sa, size_t na, uint32_t* __restrict__ da,
+                                const uint32_t* __restrict__ sb, size_t nb, uint32_t* __restrict__ db) {
+  const size_t ma = na > 1 ? (na + 1) / 2 : 0, mb = nb > 1 ? (nb + 1) / 2 : 0;
+  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < ma + mb; j += (size_t)gridDim.x * blockDim.x) {
+    if (j < ma) digest_node(sa, na, j, da);
+    else digest_node(sb, nb, j - ma, db);
+  }
+}
+
+__device__ __forceinline__ void digest_finish(const uint32_t* root, uint64_t len, int empty, uint32_t* out) {
   uint32_t r[8], blk[16], h[8];
   if (empty) {
     sha256_init(r);
@@ -203,6 +229,18 @@ __global__ void k_digest_final(const uint32_t* root, uint64_t len, int empty, ui
   for (int k = 0; k < 8; ++k) out[k] = h[k];
 }
 
+__global__ void k_digest_final(const uint32_t* root, uint64_t len, int empty, uint32_t* out) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  digest_finish(root, len, empty, out);
+}
+
+__global__ void k_digest_final2(const uint32_t* ra, uint64_t la, int ea, uint32_t* oa, const uint32_t* rb,
+                                uint64_t lb, int eb, uint32_t* ob) {
+  if (blockIdx.x != 0 || threadIdx.x >= 2) return;
+  if (threadIdx.x == 0) digest_finish(ra, la, ea, oa);
+  else digest_finish(rb, lb, eb, ob);
+}
+
 size_t digest_scratch_words(size_t len_bytes) { return 2 * 8 * ((len_bytes + 1023) / 1024) + 16; }
 
 static int digest_tree(size_t nleaf, uint64_t len, uint32_t* scratch, uint32_t* out_words, cudaStream_t st) {
@@ -220,14 +258,35 @@ static int digest_tree(size_t nleaf, uint64_t len, uint32_t* scratch, uint32_t* 
   return post_launch();
 }
 
-int launch_digest_table(const uint32_t* tab, size_t nelem, uint32_t* scratch, uint32_t* out_words, void* stream) {
+int launch_digest_tables2(const uint32_t* ta, size_t na, const uint32_t* tb, size_t nb, uint32_t* scratch,
+                          uint32_t* out_a, uint32_t* out_b, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
-  size_t nleaf = (nelem + 31) / 32;
-  if (nleaf) {
-    k_digest_leaves_table<<<grid_for(nleaf, 128, 32), 128, 0, st>>>(tab, nelem, scratch);
+  const size_t la = (na + 31) / 32, lb = (nb + 31) / 32;
+  // each tree ping-pongs between two halves of its own scratch
+  uint32_t* a0 = scratch;
+  uint32_t* a1 = a0 + 8 * la + 8;
+  uint32_t* b0 = scratch + digest_scratch_words(na * 32);
+  uint32_t* b1 = b0 + 8 * lb + 8;
+  if (la + lb) {
+    k_digest_leaves_table2<<<grid_for(la + lb, 128, 32), 128, 0, st>>>(ta, na, a0, tb, nb, b0);
     if (int e = post_launch()) return e;
   }
-  return digest_tree(nleaf, (uint64_t)nelem * 32, scratch, out_words, st);
+  size_t n_a = la, n_b = lb;
+  while (n_a > 1 || n_b > 1) {
+    const size_t m = (n_a > 1 ? (n_a + 1) / 2 : 0) + (n_b > 1 ? (n_b + 1) / 2 : 0);
+    k_digest_level2<<<grid_for(m, 128), 128, 0, st>>>(a0, n_a, a1, b0, n_b, b1);
+    if (int e = post_launch()) return e;
+    if (n_a > 1) {
+      std::swap(a0, a1);
+      n_a = (n_a + 1) / 2;
+    }
+    if (n_b > 1) {
+      std::swap(b0, b1);
+      n_b = (n_b + 1) / 2;
+    }
+  }
+  k_digest_final2<<<1, 32, 0, st>>>(a0, (uint64_t)na * 32, la == 0, out_a, b0, (uint64_t)nb * 32, lb == 0, out_b);
+  return post_launch();
 }
 
 int launch_digest_bytes(const uint8_t* data, size_t len, uint32_t* scratch, uint32_t* out_words, void* stream) {

@@ -81,10 +81,12 @@ int launch_eval_layer(const uint32_t* Vn, uint32_t* V, const DevLayer& L, uint32
                       void* stream);
 int launch_layer_to_canonical(const uint32_t* V, uint32_t* out, uint32_t c, uint32_t s, uint32_t Creal,
                               uint32_t wreal, void* stream);
-// Merkle statement digest of a Montgomery table (elements converted to
-// canonical bytes on the fly) or of raw device bytes; writes 8 words.
-int launch_digest_table(const uint32_t* tab, size_t nelem, uint32_t* scratch, uint32_t* out_words,
-                        void* stream);
+// Merkle statement digests (8 words each): of two Montgomery tables at
+// once, elements converted to canonical bytes on the fly, the launches
+// shared by both trees (scratch: digest_scratch_words(na * 32) +
+// digest_scratch_words(nb * 32) words); or of raw device bytes.
+int launch_digest_tables2(const uint32_t* ta, size_t na, const uint32_t* tb, size_t nb, uint32_t* scratch,
+                          uint32_t* out_a, uint32_t* out_b, void* stream);
 int launch_digest_bytes(const uint8_t* data, size_t len, uint32_t* scratch, uint32_t* out_words,
                         void* stream);
 size_t digest_scratch_words(size_t len_bytes);
