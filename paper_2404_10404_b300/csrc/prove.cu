@@ -708,6 +708,8 @@ namespace cg = cooperative_groups;
 constexpr int kTailCTAs = 8;
 constexpr int kTailThreads = 256;
 
+constexpr uint32_t kSoloMax = 256;  // table entries at which CTA 0 finishes a phase alone
+
 struct TailShared {
   Fr part[kTailCTAs][2];  // partial sums g(0), g(2) of every CTA (each CTA sends its own to all)
   Fr canon[3];            // canonical round values
@@ -717,6 +719,7 @@ struct TailShared {
   Fr red[3][kTailThreads / 32];
   Fr rx[2][16];           // r_x,k and 1 - r_x,k
   Fr eqh[256], eql[256];  // eq(r_x, x) = eqh[x >> sl] eql[x mod 2^sl]
+  Fr solo[3][kSoloMax];   // CTA 0: the tables of a phase's last rounds
 };
 
 // One round over tables (A, B1, B2) of size m (after the fold of `rprev`
@@ -804,6 +807,74 @@ __device__ Fr tail_round(cg::cluster_group& cl, TailShared& sh, uint32_t* A, uin
   return sh.bcast;
 }
 
+// The last rounds of a phase, k = k0 .. s-1, by CTA 0 alone (call it from
+// CTA 0 only): once the tables have at most kSoloMax entries the cluster's
+// barriers and partial-sum exchange cost more than the work, so the tables
+// move to CTA 0's shared memory and its threads fold, evaluate and reduce
+// with block barriers.  On entry the tables as round k0 - 1 left them (or
+// as the phase's bookkeeping wrote them, k0 = 0) are in global memory and
+// r is r_{k0-1}.  Records every challenge in rslot[k] and in the slot
+// rhist[k] of shared memory (when not null), and returns the last one; the
+// final two entries of the first table stay in sh.solo[0][0..1].
+__device__ Fr tail_solo(TailShared& sh, const uint32_t* A, const uint32_t* B1, const uint32_t* B2, uint32_t Wn,
+                        uint32_t s, uint32_t k0, Fr r, DevState* S, uint8_t* proof, size_t off, Fr* rslot,
+                        Fr (*rhist)[16]) {
+  const uint32_t n0 = k0 == 0 ? Wn : Wn >> (k0 - 1);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (uint32_t e = threadIdx.x; e < 3 * n0; e += kTailThreads) {
+    const uint32_t tab = e / n0, idx = e - tab * n0;
+    sh.solo[tab][idx] = fr_load_cg(tab == 0 ? A : tab == 1 ? B1 : B2, idx);
+  }
+  __syncthreads();
+  for (uint32_t k = k0; k < s; ++k) {
+    const uint32_t m = Wn >> k, hq = m / 2;
+    if (k > 0) {  // fold from 2m to m entries in place (entry idx < m: read and written by one thread)
+      for (uint32_t e = threadIdx.x; e < 3 * m; e += kTailThreads) {
+        const uint32_t tab = e / m, idx = e - tab * m;
+        sh.solo[tab][idx] = fold2(sh.solo[tab][idx], sh.solo[tab][idx + m], r);
+      }
+      __syncthreads();
+    }
+    Fr acc[2] = {fr_zero(), fr_zero()};
+    for (uint32_t q = threadIdx.x; q < 2 * hq; q += kTailThreads) {
+      const uint32_t j = q >> 1;
+      Fr a = sh.solo[0][j], pp = sh.solo[1][j], c = sh.solo[2][j];
+      if (q & 1) {  // t = 2
+        a = fr_sub(fr_dbl(sh.solo[0][j + hq]), a);
+        pp = fr_sub(fr_dbl(sh.solo[1][j + hq]), pp);
+        c = fr_sub(fr_dbl(sh.solo[2][j + hq]), c);
+      }
+      acc[q & 1] = fr_add(acc[q & 1], fr_add(fr_mul(a, pp), c));
+    }
+#pragma unroll
+    for (int t = 0; t < 2; ++t) acc[t] = fr_warp_sum(acc[t]);
+    if (lane == 0)
+#pragma unroll
+      for (int t = 0; t < 2; ++t) sh.red[t][warp] = acc[t];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+      for (int t = 0; t < 2; ++t) acc[t] = fr_warp_sum(lane < kTailThreads / 32 ? sh.red[t][lane] : fr_zero());
+      if (lane == 0) {
+        Fr canon[2] = {fr_reduce_once(acc[0]), fr_reduce_once(acc[1])};  // plain, below 2r
+        store_words(proof, off + 64 * (size_t)k, canon[0]);
+        store_words(proof, off + 64 * (size_t)k + 32, canon[1]);
+        tr_absorb_n<2, false>(sh.st, 'R', canon);
+        const Fr rk = tr_challenge_st<false>(sh.st, &S->error, true);
+        rslot[k] = rk;
+        if (rhist) {
+          rhist[1][k] = rk;
+          rhist[0][k] = fr_sub(fr_one(), rk);
+        }
+        sh.bcast = rk;
+      }
+    }
+    __syncthreads();
+    r = sh.bcast;
+  }
+  return r;
+}
+
 __global__ void __cluster_dims__(kTailCTAs, 1, 1) __launch_bounds__(kTailThreads) k_layer_tail(TailParams p) {
   cg::cluster_group cl = cg::this_cluster();
   __shared__ TailShared sh;
@@ -834,19 +905,35 @@ __global__ void __cluster_dims__(kTailCTAs, 1, 1) __launch_bounds__(kTailThreads
     fr_store(p.Ay, x, a);
   }
   cl.sync();
+  // rounds k < k0 over the cluster, k >= k0 by CTA 0 alone (tables of at
+  // most kSoloMax entries)
+  uint32_t k0 = 0;
+  while (k0 < p.s && (p.Wn >> (k0 == 0 ? 0 : k0 - 1)) > kSoloMax) ++k0;
   Fr r = fr_zero();
-  for (uint32_t k = 0; k < p.s; ++k) {
+  for (uint32_t k = 0; k < k0; ++k) {
     r = tail_round(cl, sh, p.At, p.H1, p.H2, p.Wn >> k, k, r, S, p.proof, p.offx + 64 * (size_t)k, &S->rx[k]);
     if (threadIdx.x == 0) {  // r_x,k and 1 - r_x,k for eq(r_x, .)
       sh.rx[1][k] = r;
       sh.rx[0][k] = fr_sub(fr_one(), r);
     }
   }
-  // v_x = A(r_x)
-  if (rank == 0 && threadIdx.x == 0) {
-    Fr vx = p.s == 0 ? fr_load_cg(p.At, 0) : fold2(fr_load_cg(p.At, 0), fr_load_cg(p.At, 1), r);
-    S->vx = vx;
-    sh.vx = vx;
+  if (rank == 0) {
+    r = tail_solo(sh, p.At, p.H1, p.H2, p.Wn, p.s, k0, r, S, p.proof, p.offx, S->rx, sh.rx);
+    if (threadIdx.x == 0) {  // v_x = A(r_x)
+      const Fr vx = p.s == 0 ? sh.solo[0][0] : fold2(sh.solo[0][0], sh.solo[0][1], r);
+      S->vx = vx;
+      sh.vx = vx;
+    }
+  }
+  cl.sync();  // CTA 0's late challenges and transcript state, for every CTA
+  if (rank != 0) {
+    const TailShared* s0 = cl.map_shared_rank(&sh, 0);
+    for (uint32_t k = k0 + threadIdx.x; k < p.s; k += kTailThreads) {
+      sh.rx[0][k] = s0->rx[0][k];
+      sh.rx[1][k] = s0->rx[1][k];
+    }
+    if (threadIdx.x < 8) sh.st[threadIdx.x] = s0->st[threadIdx.x];
+    r = s0->bcast;
   }
   // eq(r_x, x) over the Wn positions of layer i+1, as the product of two
   // half tables over the high sh and the low sl bits of x (r_x,0 binds the
@@ -878,13 +965,14 @@ __global__ void __cluster_dims__(kTailCTAs, 1, 1) __launch_bounds__(kTailThreads
     fr_store(p.H2, y, fr_mul(ev, ad));
   }
   cl.sync();
-  for (uint32_t k = 0; k < p.s; ++k)
+  for (uint32_t k = 0; k < k0; ++k)
     r = tail_round(cl, sh, p.Ay, p.H1, p.H2, p.Wn >> k, k, r, S, p.proof, p.offy + 64 * (size_t)k, &S->ry[k]);
+  if (rank == 0) r = tail_solo(sh, p.Ay, p.H1, p.H2, p.Wn, p.s, k0, r, S, p.proof, p.offy, S->ry, nullptr);
   // end of the layer: v_y, (v_x, v_y) into the proof, absorb 'V', alpha, beta
   if (rank == 0 && threadIdx.x < 32) {
     const int lane = threadIdx.x;
     if (lane < 2) {
-      Fr v = lane == 0 ? vx : (p.s == 0 ? fr_load_cg(p.Ay, 0) : fold2(fr_load_cg(p.Ay, 0), fr_load_cg(p.Ay, 1), r));
+      Fr v = lane == 0 ? vx : (p.s == 0 ? sh.solo[0][0] : fold2(sh.solo[0][0], sh.solo[0][1], r));
       if (lane == 1) S->vy = v;
       Fr c = fr_to_canonical(v);
       store_words(p.proof, p.offv + 32 * (size_t)lane, c);
