@@ -45,7 +45,7 @@ ALU_PEAK_TIMAD = SMS * IMAD_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
 # rounds of a medium layer (every layer has the same shape, so this is the
 # mean over all 200 launches of a step); None when not captured for the
 # current build of the kernel.
-DOMINANT_TRAFFIC_BYTES = None
+DOMINANT_TRAFFIC_BYTES = 29.86e6
 
 
 def log(*a):
