@@ -31,16 +31,24 @@ def _u8(b):
 class _CircuitHandle:
     def __init__(self, lib, circ):
         self.lib = lib
-        widths, types, in1, in2 = circ.flat()
-        self._keep = (widths, types, in1, in2)
         err = ctypes.c_int(0)
-        self.h = lib.so_circuit_new(
-            ctypes.c_uint32(circ.depth),
-            widths.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
-            types.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
-            in1.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
-            in2.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
-            ctypes.c_uint32(circ.n_copies), ctypes.byref(err))
+        u32 = ctypes.POINTER(ctypes.c_uint32)
+        if getattr(circ, "accumulates", False):  # accumulation gates: entry lists
+            widths, cnt, outs, types, in1, in2 = circ.flat_entries()
+            self._keep = (widths, cnt, outs, types, in1, in2)
+            self.h = lib.so_circuit_new_entries(
+                ctypes.c_uint32(circ.depth), widths.ctypes.data_as(u32), cnt.ctypes.data_as(u32),
+                outs.ctypes.data_as(u32), types.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                in1.ctypes.data_as(u32), in2.ctypes.data_as(u32), ctypes.c_uint32(circ.n_copies),
+                ctypes.byref(err))
+        else:
+            widths, types, in1, in2 = circ.flat()
+            self._keep = (widths, types, in1, in2)
+            self.h = lib.so_circuit_new(
+                ctypes.c_uint32(circ.depth), widths.ctypes.data_as(u32),
+                types.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                in1.ctypes.data_as(u32), in2.ctypes.data_as(u32),
+                ctypes.c_uint32(circ.n_copies), ctypes.byref(err))
         if not self.h:
             raise ValueError(f"oracle rejected the circuit (code {err.value})")
 
@@ -58,6 +66,9 @@ class Oracle:
         vp, u8p, u32p, sz = ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint8), ctypes.POINTER(ctypes.c_uint32), ctypes.c_size_t
         lib.so_circuit_new.restype = vp
         lib.so_circuit_new.argtypes = [ctypes.c_uint32, u32p, u8p, u32p, u32p, ctypes.c_uint32, ctypes.POINTER(ctypes.c_int)]
+        lib.so_circuit_new_entries.restype = vp
+        lib.so_circuit_new_entries.argtypes = [ctypes.c_uint32, u32p, u32p, u32p, u8p, u32p, u32p, ctypes.c_uint32,
+                                               ctypes.POINTER(ctypes.c_int)]
         lib.so_circuit_free.argtypes = [vp]
         lib.so_proof_len.restype = sz
         lib.so_proof_len.argtypes = [vp]

@@ -150,7 +150,12 @@ def log2_ceil(v: int) -> int:
 
 
 class Padded:
-    """Circuit padded to power-of-two widths and copy count (absent gates = 2)."""
+    """Circuit padded to power-of-two widths and copy count.
+
+    Layer i is a list of fan-in-2 entries (out, type, in1, in2): gate g's
+    value is the sum of op(V(in1), V(in2)) over the entries with out = g
+    (Sec. 3.4.3, accumulation gates); a plain gate is one entry and a
+    padding gate has none."""
 
     def __init__(self, circ):
         self.d = circ.depth
@@ -160,18 +165,29 @@ class Padded:
         self.wreal = list(circ.widths)
         self.s = [log2_ceil(w) for w in circ.widths]
         self.W = [1 << s for s in self.s]
-        self.type, self.in1, self.in2 = [], [], []
+        self.entries = []
         for i in range(self.d):
-            t = [int(v) for v in circ.types[i]] + [2] * (self.W[i] - self.wreal[i])
-            a = [int(v) for v in circ.in1[i]] + [0] * (self.W[i] - self.wreal[i])
-            b = [int(v) for v in circ.in2[i]] + [0] * (self.W[i] - self.wreal[i])
-            self.type.append(t); self.in1.append(a); self.in2.append(b)
+            outs = [int(o) for o in circ.layer_outs(i)]
+            ent = [(o, int(t), int(a), int(b)) for o, t, a, b in zip(outs, circ.types[i], circ.in1[i], circ.in2[i])]
+            self.entries.append(sorted(ent, key=lambda e: e[0]))  # stable: order within a gate kept
 
     def wiring_bytes(self) -> bytes:
+        """Per padded gate: its one entry as u8 type || u32 in1 || u32 in2;
+        no entry as (2, 0, 0); k >= 2 entries as u8 3 || u32 k || k records."""
         out = bytearray()
         for i in range(self.d):
-            for g in range(self.W[i]):
-                out += struct.pack("<BII", self.type[i][g], self.in1[i][g], self.in2[i][g])
+            by_gate = [[] for _ in range(self.W[i])]
+            for o, t, a, b in self.entries[i]:
+                by_gate[o].append((t, a, b))
+            for recs in by_gate:
+                if not recs:
+                    out += struct.pack("<BII", 2, 0, 0)
+                elif len(recs) == 1:
+                    out += struct.pack("<BII", *recs[0])
+                else:
+                    out += struct.pack("<BI", 3, len(recs))
+                    for r in recs:
+                        out += struct.pack("<BII", *r)
         return bytes(out)
 
 
@@ -187,10 +203,10 @@ def evaluate(pc: Padded, inputs):
         V[i] = [0] * (pc.C * pc.W[i])
         for b in range(pc.C):
             row = V[i + 1][b * pc.W[i + 1]:(b + 1) * pc.W[i + 1]]
-            for g in range(pc.W[i]):
-                t = pc.type[i][g]
-                u, v = row[pc.in1[i][g]], row[pc.in2[i][g]]
-                V[i][b * pc.W[i] + g] = (u + v) % P if t == 0 else (u * v) % P if t == 1 else 0
+            for g, t, a1, a2 in pc.entries[i]:
+                u, v = row[a1], row[a2]
+                k = b * pc.W[i] + g
+                V[i][k] = (V[i][k] + ((u + v) if t == 0 else u * v)) % P
     return V
 
 
@@ -226,9 +242,8 @@ def interpolate(g, x: int) -> int:
 
 def _layer_function(pc: Padded, i: int, V_next, zb, omega):
     """f(b, x, y) for layer i, as a function of a full point."""
-    c, s, W = pc.c, pc.s[i + 1], pc.W[i]
-    gates = [(pc.type[i][g], bits_msb(pc.in1[i][g], s), bits_msb(pc.in2[i][g], s), omega[g])
-             for g in range(W) if pc.type[i][g] != 2]
+    c, s = pc.c, pc.s[i + 1]
+    gates = [(t, bits_msb(a1, s), bits_msb(a2, s), omega[g]) for g, t, a1, a2 in pc.entries[i]]
     memo = {}
 
     def Vt(point):
@@ -381,11 +396,8 @@ def forge_vy_one_layer(circ, inputs, domain: bytes | None = None) -> bytes:
     vx = Vt(rb + rx)
     e = eq(zb, rb)
     A = B = 0
-    for g in range(pc.W[0]):
-        t = pc.type[0][g]
-        if t == 2:
-            continue
-        w = omega[g] * eq(rx, bits_msb(pc.in1[0][g], s)) * eq(ry, bits_msb(pc.in2[0][g], s)) % P
+    for g, t, a1, a2 in pc.entries[0]:
+        w = omega[g] * eq(rx, bits_msb(a1, s)) * eq(ry, bits_msb(a2, s)) % P
         if t == 0:
             A, B = (A + w * vx) % P, (B + w) % P
         else:

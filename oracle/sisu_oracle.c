@@ -458,15 +458,23 @@ static fr tr_challenge(transcript *t) {
 }
 
 /* ------------------------------------------------------------------ */
-/* Circuits.  Gate types: 0 add, 1 mul, 2 absent (padding, value 0).    */
+/* Circuits.  Gate layer i is a list of ne[i] fan-in-2 entries (out, type,*/
+/* in1, in2), type 0 add or 1 mul, sorted by output gate: gate g's value  */
+/* is the sum of op(V_{i+1}(in1), V_{i+1}(in2)) over its entries (Sec.    */
+/* 3.4.3, accumulation gates).  A plain gate has one entry; a gate with   */
+/* none, such as a padding gate, is 0.                                     */
 
 typedef struct so_circuit {
     uint32_t d, c, C, Creal;
     uint32_t s[SO_MAX_DEPTH + 1], W[SO_MAX_DEPTH + 1], wreal[SO_MAX_DEPTH + 1];
+    uint32_t ne[SO_MAX_DEPTH];
+    uint32_t *out[SO_MAX_DEPTH];
     uint8_t *type[SO_MAX_DEPTH];
     uint32_t *in1[SO_MAX_DEPTH], *in2[SO_MAX_DEPTH];
     uint8_t wiring_digest[32];
 } so_circuit;
+
+static fr op_gate(uint8_t t, fr a, fr b) { return t == 0 ? fr_add(a, b) : fr_mul(a, b); }
 
 static uint32_t ceil_log2(uint64_t v) {
     uint32_t s = 0;
@@ -476,29 +484,51 @@ static uint32_t ceil_log2(uint64_t v) {
 
 void so_circuit_free(so_circuit *cc) {
     if (!cc) return;
-    for (uint32_t i = 0; i < cc->d; ++i) { free(cc->type[i]); free(cc->in1[i]); free(cc->in2[i]); }
+    for (uint32_t i = 0; i < cc->d; ++i) {
+        free(cc->out[i]); free(cc->type[i]); free(cc->in1[i]); free(cc->in2[i]);
+    }
     free(cc);
 }
 
-/* Wiring bytes: for i = 0..d-1, g = 0..W_i-1: u8 type || u32le in1 || u32le in2. */
+/* Wiring bytes: for i = 0..d-1 and each padded gate g = 0..W_i-1 in turn,
+ *   one entry:   u8 type || u32le in1 || u32le in2
+ *   no entry:    u8 2 || u32le 0 || u32le 0         (a padding gate)
+ *   k >= 2:      u8 3 || u32le k, then k times u8 type || u32le in1 || u32le in2
+ * The first byte of a record tells which form follows. */
 static int wiring_digest(so_circuit *cc) {
     size_t n = 0;
-    for (uint32_t i = 0; i < cc->d; ++i) n += (size_t)cc->W[i] * 9;
+    for (uint32_t i = 0; i < cc->d; ++i) n += (size_t)cc->W[i] * 9 + (size_t)cc->ne[i] * 9;
     uint8_t *buf = (uint8_t *)malloc(n ? n : 1), *p = buf;
     if (!buf) return SO_ERR_OOM;
-    for (uint32_t i = 0; i < cc->d; ++i)
+    for (uint32_t i = 0; i < cc->d; ++i) {
+        uint32_t e = 0;
         for (uint32_t g = 0; g < cc->W[i]; ++g) {
-            *p++ = cc->type[i][g];
-            put_u32(p, cc->in1[i][g]); p += 4;
-            put_u32(p, cc->in2[i][g]); p += 4;
+            uint32_t e1 = e;
+            while (e1 < cc->ne[i] && cc->out[i][e1] == g) ++e1;
+            uint32_t k = e1 - e;
+            if (k == 0) {
+                *p++ = 2; put_u32(p, 0); p += 4; put_u32(p, 0); p += 4;
+            } else if (k == 1) {
+                *p++ = cc->type[i][e]; put_u32(p, cc->in1[i][e]); p += 4; put_u32(p, cc->in2[i][e]); p += 4;
+            } else {
+                *p++ = 3; put_u32(p, k); p += 4;
+                for (uint32_t q = e; q < e1; ++q) {
+                    *p++ = cc->type[i][q]; put_u32(p, cc->in1[i][q]); p += 4; put_u32(p, cc->in2[i][q]); p += 4;
+                }
+            }
+            e = e1;
         }
-    int rc = statement_digest(buf, n, cc->wiring_digest);
+    }
+    int rc = statement_digest(buf, (size_t)(p - buf), cc->wiring_digest);
     free(buf);
     return rc;
 }
 
-so_circuit *so_circuit_new(uint32_t d, const uint32_t *widths, const uint8_t *types,
-                           const uint32_t *in1, const uint32_t *in2, uint32_t n_copies, int *err) {
+/* Shared constructor: layer i gets cnt[i] entries (outs, types, in1, in2
+ * concatenated over the layers), kept in order of output gate (stable). */
+static so_circuit *circuit_from_entries(uint32_t d, const uint32_t *widths, const uint32_t *cnt,
+                                        const uint32_t *outs, const uint8_t *types, const uint32_t *in1,
+                                        const uint32_t *in2, uint32_t n_copies, int *err) {
     if (!mu_ready) init_mu();
     if (!sha_ready) sha_init_constants();
     *err = SO_ERR_ARG;
@@ -518,26 +548,58 @@ so_circuit *so_circuit_new(uint32_t d, const uint32_t *widths, const uint8_t *ty
     }
     size_t off = 0;
     for (uint32_t i = 0; i < d; ++i) {
-        cc->type[i] = (uint8_t *)calloc(cc->W[i], 1);
-        cc->in1[i] = (uint32_t *)calloc(cc->W[i], 4);
-        cc->in2[i] = (uint32_t *)calloc(cc->W[i], 4);
+        uint32_t n = cnt[i];
         cc->d = i + 1; /* so that so_circuit_free releases what exists */
-        if (!cc->type[i] || !cc->in1[i] || !cc->in2[i]) { so_circuit_free(cc); *err = SO_ERR_OOM; return NULL; }
-        for (uint32_t g = 0; g < cc->W[i]; ++g) {
-            if (g < widths[i]) {
-                uint8_t t = types[off + g];
-                uint32_t a = in1[off + g], b = in2[off + g];
-                if (t > 1 || a >= widths[i + 1] || b >= widths[i + 1]) { so_circuit_free(cc); return NULL; }
-                cc->type[i][g] = t; cc->in1[i][g] = a; cc->in2[i][g] = b;
-            } else {
-                cc->type[i][g] = 2;
-            }
+        cc->ne[i] = n;
+        cc->out[i] = (uint32_t *)calloc(n ? n : 1, 4);
+        cc->type[i] = (uint8_t *)calloc(n ? n : 1, 1);
+        cc->in1[i] = (uint32_t *)calloc(n ? n : 1, 4);
+        cc->in2[i] = (uint32_t *)calloc(n ? n : 1, 4);
+        if (!cc->out[i] || !cc->type[i] || !cc->in1[i] || !cc->in2[i]) {
+            so_circuit_free(cc); *err = SO_ERR_OOM; return NULL;
         }
-        off += widths[i];
+        uint32_t k = 0;
+        for (uint32_t g = 0; g < widths[i]; ++g) /* stable by output gate */
+            for (uint32_t e = 0; e < n; ++e) {
+                if (outs[off + e] >= widths[i]) { so_circuit_free(cc); return NULL; }
+                if (outs[off + e] != g) continue;
+                uint8_t t = types[off + e];
+                uint32_t a = in1[off + e], b = in2[off + e];
+                if (t > 1 || a >= widths[i + 1] || b >= widths[i + 1]) { so_circuit_free(cc); return NULL; }
+                cc->out[i][k] = g; cc->type[i][k] = t; cc->in1[i][k] = a; cc->in2[i][k] = b;
+                ++k;
+            }
+        off += n;
     }
     cc->d = d;
     if (wiring_digest(cc) != SO_OK) { so_circuit_free(cc); *err = SO_ERR_OOM; return NULL; }
     *err = SO_OK;
+    return cc;
+}
+
+so_circuit *so_circuit_new_entries(uint32_t d, const uint32_t *widths, const uint32_t *cnt, const uint32_t *outs,
+                                   const uint8_t *types, const uint32_t *in1, const uint32_t *in2,
+                                   uint32_t n_copies, int *err) {
+    *err = SO_ERR_ARG;
+    if (!cnt || !outs || !types || !in1 || !in2) return NULL;
+    return circuit_from_entries(d, widths, cnt, outs, types, in1, in2, n_copies, err);
+}
+
+so_circuit *so_circuit_new(uint32_t d, const uint32_t *widths, const uint8_t *types,
+                           const uint32_t *in1, const uint32_t *in2, uint32_t n_copies, int *err) {
+    /* one entry per gate: entry e of layer i belongs to gate e */
+    *err = SO_ERR_ARG;
+    if (d < 1 || d > SO_MAX_DEPTH || !widths) return NULL;
+    size_t total = 0;
+    uint32_t cnt[SO_MAX_DEPTH];
+    for (uint32_t i = 0; i < d; ++i) { cnt[i] = widths[i]; total += widths[i]; }
+    uint32_t *outs = (uint32_t *)malloc(total ? total * 4 : 4);
+    if (!outs) { *err = SO_ERR_OOM; return NULL; }
+    size_t off = 0;
+    for (uint32_t i = 0; i < d; ++i)
+        for (uint32_t g = 0; g < widths[i]; ++g) outs[off++] = g;
+    so_circuit *cc = circuit_from_entries(d, widths, cnt, outs, types, in1, in2, n_copies, err);
+    free(outs);
     return cc;
 }
 
@@ -569,12 +631,10 @@ static int eval_all(const so_circuit *cc, const uint8_t *inputs, fr **V) {
         for (uint32_t b = 0; b < cc->C; ++b) {
             const fr *in = V[i + 1] + (size_t)b * Wn;
             fr *out = V[i] + (size_t)b * W;
-            for (uint32_t g = 0; g < W; ++g) {
-                uint8_t t = cc->type[i][g];
-                if (t == 0) out[g] = fr_add(in[cc->in1[i][g]], in[cc->in2[i][g]]);
-                else if (t == 1) out[g] = fr_mul(in[cc->in1[i][g]], in[cc->in2[i][g]]);
-                else out[g] = fr_zero();
-            }
+            for (uint32_t g = 0; g < W; ++g) out[g] = fr_zero();
+            for (uint32_t e = 0; e < cc->ne[i]; ++e) /* each entry adds to its gate */
+                out[cc->out[i][e]] = fr_add(out[cc->out[i][e]],
+                                            op_gate(cc->type[i][e], in[cc->in1[i][e]], in[cc->in2[i][e]]));
         }
     }
     return SO_OK;
@@ -604,7 +664,6 @@ static fr eq_point_index(const fr *r, uint32_t s, uint32_t v) {
     return acc;
 }
 
-static fr op_gate(uint8_t t, fr a, fr b) { return t == 0 ? fr_add(a, b) : fr_mul(a, b); }
 
 /* MLE of a table of 2^m entries at point r (r_1 binds the top index bit). */
 static fr mle_by_folding(const fr *T, uint32_t m, const fr *r) {
@@ -670,7 +729,7 @@ static void put_hdr(writer *w, const so_circuit *cc) {
  * with T_t(j, x) = T(j, x) + t (T(j + n/2, x) - T(j, x)). */
 static void copy_round(const so_circuit *cc, uint32_t i, const fr *T, size_t n, const fr *omega,
                        const fr *zb, const fr *rb, uint32_t k, fr out[4]) {
-    uint32_t c = cc->c, W = cc->W[i], Wn = cc->W[i + 1];
+    uint32_t c = cc->c, Wn = cc->W[i + 1];
     size_t h = n / 2;
     fr prefix = fr_u64(1);
     for (uint32_t m = 1; m < k; ++m) prefix = fr_mul(prefix, eq1(zb[m - 1], rb[m - 1]));
@@ -687,11 +746,9 @@ static void copy_round(const so_circuit *cc, uint32_t i, const fr *T, size_t n, 
                 row[x] = fr_add(lo, fr_mul(tt, fr_sub(hi, lo)));
             }
             fr S = fr_zero();
-            for (uint32_t g = 0; g < W; ++g) {
-                uint8_t ty = cc->type[i][g];
-                if (ty == 2) continue;
-                S = fr_add(S, fr_mul(omega[g], op_gate(ty, row[cc->in1[i][g]], row[cc->in2[i][g]])));
-            }
+            for (uint32_t e = 0; e < cc->ne[i]; ++e) /* entry e weighs w(out e) */
+                S = fr_add(S, fr_mul(omega[cc->out[i][e]],
+                                     op_gate(cc->type[i][e], row[cc->in1[i][e]], row[cc->in2[i][e]])));
             fr E = fr_mul(fr_mul(prefix, eq1(zb[k - 1], tt)), suffix);
             out[t] = fr_add(out[t], fr_mul(E, S));
         }
@@ -711,27 +768,27 @@ static void fold_rows(fr *T, size_t n, uint32_t width, fr r) {
 /* Phase over one gate input (Libra's phase 1 when which = 1, phase 2 when
  * which = 2), round k of s.  A is the row V~(r_b, .) folded by
  * r_1..r_{k-1} (size 2^(s-k+1)); A0 is the unfolded row; pre[g] holds
- * eq((r_1..r_{k-1}), top k-1 bits of the bound input of gate g) times, in
- * phase 2, eq(r_x, in1 g).
- * Phase 1: g(t) = e sum_g w(g) pre(g) eq1(t, bit_k(in1 g))
- *                 * op_g(A_t(lo(in1 g)), A0(in2 g))
- * Phase 2: g(t) = e sum_g w(g) pre(g) eq1(t, bit_k(in2 g))
- *                 * op_g(v_x, A_t(lo(in2 g))). */
+ * eq((r_1..r_{k-1}), top k-1 bits of the bound input of entry q) times,
+ * in phase 2, eq(r_x, in1 q).  Sums run over the entries q (a plain gate
+ * is one entry), each weighted by w of its output gate:
+ * Phase 1: g(t) = e sum_q w(out q) pre(q) eq1(t, bit_k(in1 q))
+ *                 * op_q(A_t(lo(in1 q)), A0(in2 q))
+ * Phase 2: g(t) = e sum_q w(out q) pre(q) eq1(t, bit_k(in2 q))
+ *                 * op_q(v_x, A_t(lo(in2 q))). */
 static void gate_round(const so_circuit *cc, uint32_t i, int which, const fr *A, const fr *A0,
                        const fr *omega, const fr *pre, fr e, fr vx, uint32_t k, fr out[3]) {
-    uint32_t s = cc->s[i + 1], W = cc->W[i];
+    uint32_t s = cc->s[i + 1];
     size_t m = (size_t)1 << (s - k + 1), h = m / 2;
     uint32_t lomask = (uint32_t)(h - 1);
     for (int t = 0; t < 3; ++t) {
         fr tt = fr_u64((uint64_t)t), S = fr_zero();
-        for (uint32_t g = 0; g < W; ++g) {
-            uint8_t ty = cc->type[i][g];
-            if (ty == 2) continue;
-            uint32_t v = which == 1 ? cc->in1[i][g] : cc->in2[i][g];
+        for (uint32_t q = 0; q < cc->ne[i]; ++q) {
+            uint8_t ty = cc->type[i][q];
+            uint32_t v = which == 1 ? cc->in1[i][q] : cc->in2[i][q];
             uint32_t lo = v & lomask;
             fr at = fr_add(A[lo], fr_mul(tt, fr_sub(A[lo + h], A[lo])));
-            fr val = which == 1 ? op_gate(ty, at, A0[cc->in2[i][g]]) : op_gate(ty, vx, at);
-            fr coeff = fr_mul(fr_mul(omega[g], pre[g]), eq1(tt, fr_u64((uint64_t)bit_msb(v, s, k))));
+            fr val = which == 1 ? op_gate(ty, at, A0[cc->in2[i][q]]) : op_gate(ty, vx, at);
+            fr coeff = fr_mul(fr_mul(omega[cc->out[i][q]], pre[q]), eq1(tt, fr_u64((uint64_t)bit_msb(v, s, k))));
             S = fr_add(S, fr_mul(coeff, val));
         }
         out[t] = fr_mul(e, S);
@@ -797,32 +854,33 @@ int so_prove(const so_circuit *cc, const uint8_t *inputs, const uint8_t *domain,
         for (uint32_t m = 0; m < c; ++m) e = fr_mul(e, eq1(zb[m], rb[m]));
         /* A0 = V~(r_b, .), the copy-bound row */
         fr *A0 = (fr *)malloc(Wn * sizeof(fr)), *A = (fr *)malloc(Wn * sizeof(fr));
-        fr *pre = (fr *)malloc(W * sizeof(fr));
+        uint32_t ne = cc->ne[i];
+        fr *pre = (fr *)malloc((ne ? ne : 1) * sizeof(fr)); /* one per entry */
         memcpy(A0, T, Wn * sizeof(fr));
         /* phase over x */
         memcpy(A, A0, Wn * sizeof(fr));
-        for (uint32_t g = 0; g < W; ++g) pre[g] = fr_u64(1);
+        for (uint32_t q = 0; q < ne; ++q) pre[q] = fr_u64(1);
         for (uint32_t k = 1; k <= s; ++k) {
             fr g3[3];
             gate_round(cc, i, 1, A, A0, omega, pre, e, fr_zero(), k, g3);
             send_round(&tr, &w, g3, 3);
             rx[k - 1] = tr_challenge(&tr);
             fold_rows(A, (size_t)1 << (s - k + 1), 1, rx[k - 1]);
-            for (uint32_t g = 0; g < W; ++g)
-                pre[g] = fr_mul(pre[g], eq1(rx[k - 1], fr_u64((uint64_t)bit_msb(cc->in1[i][g], s, k))));
+            for (uint32_t q = 0; q < ne; ++q)
+                pre[q] = fr_mul(pre[q], eq1(rx[k - 1], fr_u64((uint64_t)bit_msb(cc->in1[i][q], s, k))));
         }
         fr vx = A[0];
         /* phase over y */
         memcpy(A, A0, Wn * sizeof(fr));
-        for (uint32_t g = 0; g < W; ++g) pre[g] = eq_point_index(rx, s, cc->in1[i][g]);
+        for (uint32_t q = 0; q < ne; ++q) pre[q] = eq_point_index(rx, s, cc->in1[i][q]);
         for (uint32_t k = 1; k <= s; ++k) {
             fr g3[3];
             gate_round(cc, i, 2, A, A0, omega, pre, e, vx, k, g3);
             send_round(&tr, &w, g3, 3);
             ry[k - 1] = tr_challenge(&tr);
             fold_rows(A, (size_t)1 << (s - k + 1), 1, ry[k - 1]);
-            for (uint32_t g = 0; g < W; ++g)
-                pre[g] = fr_mul(pre[g], eq1(ry[k - 1], fr_u64((uint64_t)bit_msb(cc->in2[i][g], s, k))));
+            for (uint32_t q = 0; q < ne; ++q)
+                pre[q] = fr_mul(pre[q], eq1(ry[k - 1], fr_u64((uint64_t)bit_msb(cc->in2[i][q], s, k))));
         }
         fr vy = A[0];
         fr vv[2] = {vx, vy};
@@ -905,7 +963,7 @@ int so_verify(const so_circuit *cc, const uint8_t *inputs, const uint8_t *output
     fr claim = mle_by_folding(Vout, c + cc->s[0], pt);
     int ok = 1;
     for (uint32_t i = 0; i < d && ok; ++i) {
-        uint32_t W = cc->W[i], s = cc->s[i + 1];
+        uint32_t s = cc->s[i + 1];
         /* each round: g(0), g(2)[, g(3)] from the proof, g(1) = claim - g(0) */
         for (uint32_t k = 0; k < c && ok; ++k) {
             fr g[4], sent[3];
@@ -932,17 +990,17 @@ int so_verify(const so_circuit *cc, const uint8_t *inputs, const uint8_t *output
         if (!ok) break;
         fr vx = get_fr(&rd), vy = get_fr(&rd);
         if (rd.bad) { ok = 0; break; }
-        /* final identity: claim = eq(z_b, r_b) sum_g w(g) eq(r_x, in1 g)
-         *                         eq(r_y, in2 g) op_g(v_x, v_y) */
+        /* final identity: claim = eq(z_b, r_b) sum_q w(out q) eq(r_x, in1 q)
+         *                         eq(r_y, in2 q) op_q(v_x, v_y) over the entries q */
         fr e = fr_u64(1), sum = fr_zero();
         for (uint32_t m = 0; m < c; ++m) e = fr_mul(e, eq1(zb[m], rb[m]));
-        for (uint32_t g = 0; g < W; ++g) {
-            uint8_t ty = cc->type[i][g];
-            if (ty == 2) continue;
+        for (uint32_t q = 0; q < cc->ne[i]; ++q) {
+            uint8_t ty = cc->type[i][q];
+            uint32_t g = cc->out[i][q];
             fr om = i == 0 ? eq_point_index(zg, cc->s[0], g)
                            : fr_add(fr_mul(alpha, eq_point_index(prx, cc->s[i], g)),
                                     fr_mul(beta, eq_point_index(pry, cc->s[i], g)));
-            fr pred = fr_mul(eq_point_index(rx, s, cc->in1[i][g]), eq_point_index(ry, s, cc->in2[i][g]));
+            fr pred = fr_mul(eq_point_index(rx, s, cc->in1[i][q]), eq_point_index(ry, s, cc->in2[i][q]));
             sum = fr_add(sum, fr_mul(fr_mul(om, pred), op_gate(ty, vx, vy)));
         }
         if (!fr_eq(claim, fr_mul(e, sum))) { ok = 0; break; }

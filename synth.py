@@ -115,6 +115,12 @@ class Circuit:
     ``widths[i]`` is the number of gates of layer i (0 = outputs,
     d = inputs); ``types[i]``, ``in1[i]``, ``in2[i]`` describe layer i < d.
     Widths need not be powers of two: the prover pads (Sec. 2.2).
+
+    Accumulation gates (Sec. 3.4.3): when ``outs`` is given and
+    ``outs[i]`` is not None, layer i is a list of fan-in-2 entries:
+    ``types[i]``, ``in1[i]``, ``in2[i]`` and ``outs[i]`` have one element
+    per entry, and gate g's value is the sum over the entries with
+    ``outs[i] == g`` (a gate with no entry is 0).
     """
     widths: list
     types: list
@@ -124,6 +130,17 @@ class Circuit:
     name: str = ""
     seed: int = 0
     meta: dict = field(default_factory=dict)
+    outs: list | None = None
+
+    def layer_outs(self, i: int):
+        """Output gate of every entry of layer i (one entry per gate when plain)."""
+        if self.outs is not None and self.outs[i] is not None:
+            return np.asarray(self.outs[i], dtype=np.uint32)
+        return np.arange(self.widths[i], dtype=np.uint32)
+
+    @property
+    def accumulates(self) -> bool:
+        return self.outs is not None and any(o is not None for o in self.outs)
 
     @property
     def depth(self) -> int:
@@ -135,6 +152,16 @@ class Circuit:
     def flat(self):
         """Concatenated (widths, types, in1, in2) arrays for C callers."""
         return (np.ascontiguousarray(self.widths, dtype=np.uint32),
+                np.ascontiguousarray(np.concatenate(self.types), dtype=np.uint8),
+                np.ascontiguousarray(np.concatenate(self.in1), dtype=np.uint32),
+                np.ascontiguousarray(np.concatenate(self.in2), dtype=np.uint32))
+
+    def flat_entries(self):
+        """(widths, entries per layer, outs, types, in1, in2), concatenated."""
+        outs = [self.layer_outs(i) for i in range(self.depth)]
+        return (np.ascontiguousarray(self.widths, dtype=np.uint32),
+                np.ascontiguousarray([len(o) for o in outs], dtype=np.uint32),
+                np.ascontiguousarray(np.concatenate(outs), dtype=np.uint32),
                 np.ascontiguousarray(np.concatenate(self.types), dtype=np.uint8),
                 np.ascontiguousarray(np.concatenate(self.in1), dtype=np.uint32),
                 np.ascontiguousarray(np.concatenate(self.in2), dtype=np.uint32))
@@ -233,6 +260,30 @@ def batched_instance(j: int) -> Circuit:
 def micro(seed: int, n_copies: int, widths, pct_mul: int = 50) -> Circuit:
     return uniform_circuit(seed, n_copies, widths, pct_mul,
                            name=f"micro_s{seed}_C{n_copies}_W{'-'.join(map(str, widths))}")
+
+
+def accumulation_circuit(seed: int, n_copies: int, widths, max_entries: int = 4, pct_mul: int = 50,
+                         name: str = "") -> Circuit:
+    """Layers of accumulation gates (Sec. 3.4.3) with uniform wiring: gate g
+    of layer i gets U{0..max_entries} fan-in-2 entries (so some gates are
+    plain, some are 0), each entry mul with probability pct_mul % and its two
+    inputs uniform over layer i+1.  Entries are listed by gate."""
+    d = len(widths) - 1
+    types, in1, in2, outs = [], [], [], []
+    for i in range(d):
+        cnt = splitmix_words(stream_seed(seed, b"acc-count", i), 0, widths[i]) >> np.uint64(32)
+        cnt = ((cnt * np.uint64(max_entries + 1)) >> np.uint64(32)).astype(np.int64)
+        ne = int(cnt.sum())
+        u = splitmix_words(stream_seed(seed, b"acc-wiring", i), 0, 3 * max(ne, 1)).reshape(-1, 3)[:ne]
+        hi = u >> np.uint64(32)
+        types.append((((hi[:, 0] * np.uint64(100)) >> np.uint64(32)) < np.uint64(pct_mul)).astype(np.uint8))
+        in1.append(((hi[:, 1] * np.uint64(widths[i + 1])) >> np.uint64(32)).astype(np.uint32))
+        in2.append(((hi[:, 2] * np.uint64(widths[i + 1])) >> np.uint64(32)).astype(np.uint32))
+        outs.append(np.repeat(np.arange(widths[i], dtype=np.uint32), cnt))
+    return Circuit(list(widths), types, in1, in2, n_copies,
+                   name=name or f"acc_s{seed}_C{n_copies}_W{'-'.join(map(str, widths))}", seed=seed,
+                   meta={"pct_mul": pct_mul, "wiring": f"accumulation, U{{0..{max_entries}}} entries a gate"},
+                   outs=outs)
 
 
 def fr_bytes(elems: np.ndarray) -> bytes:

@@ -195,3 +195,76 @@ def test_invalid_circuits_rejected(oracle):
     for c in (bad_idx, bad_type):
         with pytest.raises(ValueError):
             oracle.proof_len(c)
+
+
+# --- accumulation gates (Sec. 3.4.3) ---------------------------------------
+
+def _acc(widths, C, layers):
+    """Circuit from per-layer entry lists [(out, type, in1, in2), ...]."""
+    outs = [np.array([e[0] for e in L], np.uint32) for L in layers]
+    types = [np.array([e[1] for e in L], np.uint8) for L in layers]
+    in1 = [np.array([e[2] for e in L], np.uint32) for L in layers]
+    in2 = [np.array([e[3] for e in L], np.uint32) for L in layers]
+    return synth.Circuit(list(widths), types, in1, in2, C, outs=outs)
+
+
+def test_accumulation_gate_closed_forms(oracle):
+    """The paper's example: one gate of two add entries sums four inputs in
+    one layer; a mul and an add entry give x0 x1 + x2 + x3; a gate with no
+    entry is 0."""
+    rng = random.Random(3)
+    circ = _acc([3, 4], 2, [[(0, 0, 0, 1), (0, 0, 2, 3), (1, 1, 0, 1), (1, 0, 2, 3)]])
+    x = [rng.randrange(P) for _ in range(8)]
+    out = bytes_to_ints(oracle.outputs(circ, ints_to_bytes(x)))
+    for b in range(2):
+        v = x[4 * b:4 * b + 4]
+        assert out[3 * b:3 * b + 3] == [sum(v) % P, (v[0] * v[1] + v[2] + v[3]) % P, 0]
+
+
+def test_accumulation_with_one_entry_a_gate_is_the_plain_circuit(oracle):
+    """Writing every gate as a single entry changes nothing: same wiring
+    digest, same proof bytes."""
+    plain = synth.micro(17, 4, [6, 5, 7], 50)
+    layers = [[(g, int(plain.types[i][g]), int(plain.in1[i][g]), int(plain.in2[i][g]))
+               for g in range(plain.widths[i])] for i in range(plain.depth)]
+    acc = _acc(plain.widths, 4, layers)
+    assert acc.accumulates
+    xb = synth.fr_bytes(synth.inputs_for(plain))
+    assert oracle.wiring_digest(acc) == oracle.wiring_digest(plain)
+    assert oracle.prove(acc, xb) == oracle.prove(plain, xb)
+
+
+@pytest.mark.parametrize("seed,C,widths,k", [(1, 2, [3, 4, 5], 3), (2, 4, [4, 4, 4], 4), (3, 3, [5, 2, 3, 4], 2),
+                                             (4, 1, [2, 2], 5), (5, 8, [6, 3, 8], 3)])
+def test_accumulation_prover_matches_bruteforce(oracle, seed, C, widths, k):
+    circ = synth.accumulation_circuit(seed, C, widths, k)
+    x = synth.inputs_for(circ)
+    xb = synth.fr_bytes(x)
+    proof = oracle.prove(circ, xb)
+    assert proof == brute.prove(circ, synth.fr_ints(x))
+    assert oracle.wiring_digest(circ) == brute.digest(brute.Padded(circ).wiring_bytes())
+    V = brute.evaluate(brute.Padded(circ), synth.fr_ints(x))
+    pc = brute.Padded(circ)
+    for layer in range(circ.depth + 1):
+        want = b"".join(brute.fe(V[layer][b * pc.W[layer] + g]) for b in range(pc.C) for g in range(pc.W[layer]))
+        assert oracle.eval_layer(circ, xb, layer) == want
+    outs = oracle.outputs(circ, xb)
+    assert oracle.verify(circ, xb, outs, proof) == 0
+    bad = bytearray(outs)
+    bad[0] ^= 1
+    assert oracle.verify(circ, xb, bytes(bad), proof) == ERR_REJECT
+    hdr = 8 + 4 * (circ.depth + 3)
+    for kk in range(0, (len(proof) - hdr) // 32, 5):
+        t = bytearray(proof)
+        t[hdr + 32 * kk + 1] ^= 2
+        assert oracle.verify(circ, xb, outs, bytes(t)) == ERR_REJECT
+
+
+def test_accumulation_wiring_is_bound(oracle):
+    """Moving one entry to another gate, or swapping two entries' order
+    inside a gate with different types, changes the wiring digest."""
+    base = _acc([2, 4], 1, [[(0, 0, 0, 1), (0, 1, 2, 3), (1, 0, 1, 2)]])
+    moved = _acc([2, 4], 1, [[(0, 0, 0, 1), (1, 1, 2, 3), (1, 0, 1, 2)]])
+    swapped = _acc([2, 4], 1, [[(0, 1, 2, 3), (0, 0, 0, 1), (1, 0, 1, 2)]])
+    d = {oracle.wiring_digest(c) for c in (base, moved, swapped)}
+    assert len(d) == 3

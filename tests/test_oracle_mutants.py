@@ -31,11 +31,12 @@ MUTANTS = {
                   "T[j * width + x] = fr_add(lo, fr_mul(r, fr_sub(lo, hi)));"),
     "copy_line_sign": ("row[x] = fr_add(lo, fr_mul(tt, fr_sub(hi, lo)));",
                        "row[x] = fr_add(hi, fr_mul(tt, fr_sub(hi, lo)));"),
-    "copy_drop_add_gates": ("if (ty == 2) continue;\n                S = fr_add(S, fr_mul(omega[g]",
-                            "if (ty != 1) continue;\n                S = fr_add(S, fr_mul(omega[g]"),
+    "copy_drop_add_gates": ("/* entry e weighs w(out e) */\n                S = fr_add(S,",
+                            "/* entry e weighs w(out e) */\n                if (cc->type[i][e]) S = fr_add(S,"),
+    "eval_overwrites": ("out[cc->out[i][e]] = fr_add(out[cc->out[i][e]],", "out[cc->out[i][e]] = fr_add(fr_zero(),"),
     "eq1_dropped_term": ("return fr_add(fr_mul(a, b), fr_mul(fr_sub(one, a), fr_sub(one, b)));",
                          "return fr_add(fr_mul(a, b), fr_mul(fr_sub(one, a), b));"),
-    "xphase_wrong_index": ("op_gate(ty, at, A0[cc->in2[i][g]])", "op_gate(ty, at, A0[cc->in1[i][g]])"),
+    "xphase_wrong_index": ("op_gate(ty, at, A0[cc->in2[i][q]])", "op_gate(ty, at, A0[cc->in1[i][q]])"),
     "yphase_transposed": ("op_gate(ty, vx, at)", "op_gate(ty, at, at)"),
     "omega_wrong_point": ("fr_mul(beta, eq_point_index(ry, cc->s[i], g)));\n        /* copy phase */",
                           "fr_mul(beta, eq_point_index(rx, cc->s[i], g)));\n        /* copy phase */"),
@@ -123,6 +124,14 @@ def _pins(o: Oracle) -> list:
     forged = brute.forge_vy_one_layer(circ, x)
     if o.verify(circ, ints_to_bytes(x), ints_to_bytes(outs), forged) == 0:
         failed.append("forged-vy")
+    # accumulation gates (Sec. 3.4.3): several entries summed into a gate
+    acc = synth.accumulation_circuit(7, 2, [3, 4, 4], 3)
+    xa = synth.inputs_for(acc)
+    try:
+        if o.prove(acc, synth.fr_bytes(xa)) != brute.prove(acc, synth.fr_ints(xa)):
+            failed.append("brute-acc")
+    except ValueError:
+        failed.append("prove-acc-error")
     return failed
 
 
