@@ -39,7 +39,7 @@ extern "C" {
 
 #define SISU_OK 0
 #define SISU_ERR_INVALID_ARG (-1)  /* null pointer, zero size, bad gate type */
-#define SISU_ERR_INDEX_OOB (-2)    /* in1/in2 not below the next layer's width */
+#define SISU_ERR_INDEX_OOB (-2)    /* in1/in2 not below the next layer's width, or an entry's gate not below its layer's */
 #define SISU_ERR_NOT_CANONICAL (-3) /* a field element >= r */
 #define SISU_ERR_OOM (-4)          /* device or host allocation failed */
 #define SISU_ERR_CUDA (-5)         /* a CUDA runtime call failed */
@@ -81,6 +81,29 @@ int sisu_circuit_create(const sisu_layer* layers, uint32_t n_gate_layers, uint32
  * sisu_circuit_eval on such a handle returns INVALID_ARG. */
 int sisu_circuit_create_host(const sisu_layer* layers, uint32_t n_gate_layers, uint32_t input_width,
                              uint32_t n_copies, sisu_circuit** out);
+
+/* Accumulation gates (Sec. 3.4.3): gate layer i given as `n_entries`
+ * fan-in-2 entries; entry e adds op_e(V_{i+1}(in1[e]), V_{i+1}(in2[e]))
+ * (type[e] in {0 add, 1 mul}) to gate out[e] < width.  A gate's value is
+ * the sum of its entries, 0 when it has none; entries of one gate may mix
+ * types.  The order of a gate's entries is kept (it is part of the wiring
+ * the transcript binds).  A circuit whose every gate has exactly one entry
+ * is the same circuit as through sisu_circuit_create: same proofs. */
+typedef struct {
+  uint32_t width;      /* gates of the layer */
+  uint32_t n_entries;  /* entries of the layer */
+  const uint32_t* out; /* gate of each entry */
+  const uint8_t* type;
+  const uint32_t* in1;
+  const uint32_t* in2;
+} sisu_acc_layer;
+
+/* As sisu_circuit_create / sisu_circuit_create_host, from entry lists.
+ * Errors: INVALID_ARG, INDEX_OOB, TOO_LARGE, OOM, CUDA. */
+int sisu_circuit_create_acc(const sisu_acc_layer* layers, uint32_t n_gate_layers, uint32_t input_width,
+                            uint32_t n_copies, sisu_circuit** out);
+int sisu_circuit_create_acc_host(const sisu_acc_layer* layers, uint32_t n_gate_layers, uint32_t input_width,
+                                 uint32_t n_copies, sisu_circuit** out);
 void sisu_circuit_destroy(sisu_circuit* circ);
 
 /* Padded shape: log2 of the copy count, log2 widths of layers 0..d (array

@@ -25,7 +25,8 @@ ERRORS = {
 }
 FR_ADD, FR_SUB, FR_MUL, FR_INV, FR_EQ1 = 0, 1, 2, 3, 4
 ENTRY_POINTS = [
-    "sisu_circuit_create", "sisu_circuit_create_host", "sisu_circuit_destroy", "sisu_circuit_info", "sisu_circuit_eval",
+    "sisu_circuit_create", "sisu_circuit_create_host", "sisu_circuit_create_acc", "sisu_circuit_create_acc_host",
+    "sisu_circuit_destroy", "sisu_circuit_info", "sisu_circuit_eval",
     "sisu_eval_update", "sisu_eval_outputs", "sisu_eval_layer", "sisu_eval_destroy",
     "sisu_transcript_create", "sisu_transcript_destroy", "sisu_gkr_prove", "sisu_gkr_prove_into",
     "sisu_gkr_verify", "sisu_fr_batch", "sisu_statement_digest", "sisu_microbench",
@@ -51,6 +52,12 @@ class _Layer(ctypes.Structure):
                 ("in1", ctypes.POINTER(ctypes.c_uint32)), ("in2", ctypes.POINTER(ctypes.c_uint32))]
 
 
+class _AccLayer(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_uint32), ("n_entries", ctypes.c_uint32),
+                ("out", ctypes.POINTER(ctypes.c_uint32)), ("type", ctypes.POINTER(ctypes.c_uint8)),
+                ("in1", ctypes.POINTER(ctypes.c_uint32)), ("in2", ctypes.POINTER(ctypes.c_uint32))]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing: build it with "
@@ -61,6 +68,8 @@ def _load():
     sig = {
         "sisu_circuit_create": ([ctypes.POINTER(_Layer), u32, u32, u32, pp], ctypes.c_int),
         "sisu_circuit_create_host": ([ctypes.POINTER(_Layer), u32, u32, u32, pp], ctypes.c_int),
+        "sisu_circuit_create_acc": ([ctypes.POINTER(_AccLayer), u32, u32, u32, pp], ctypes.c_int),
+        "sisu_circuit_create_acc_host": ([ctypes.POINTER(_AccLayer), u32, u32, u32, pp], ctypes.c_int),
         "sisu_circuit_destroy": ([vp], None),
         "sisu_circuit_info": ([vp, ctypes.POINTER(u32), ctypes.POINTER(u32), ctypes.POINTER(u32),
                                ctypes.POINTER(sz), ctypes.POINTER(sz)], ctypes.c_int),
@@ -166,25 +175,39 @@ class Circuit:
     """A layered circuit on the device (``sisu_circuit_create``).
 
     ``widths[i]`` gates in layer i (0 = outputs, d = inputs); ``types``,
-    ``in1``, ``in2`` per gate layer; ``n_copies`` identical copies.
+    ``in1``, ``in2`` per gate layer; ``n_copies`` identical copies.  With
+    ``outs`` (accumulation gates, ``sisu_circuit_create_acc``) the three
+    arrays of a layer list its entries and ``outs[i]`` the gate of each.
     """
 
-    def __init__(self, widths, types, in1, in2, n_copies: int, host_only: bool = False):
+    def __init__(self, widths, types, in1, in2, n_copies: int, host_only: bool = False, outs=None):
         d = len(widths) - 1
         self._keep = []
-        layers = (_Layer * d)()
+        u32p, u8p = ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint8)
+        layers = (_Layer * d)() if outs is None else (_AccLayer * d)()
         for i in range(d):
             t = np.ascontiguousarray(types[i], dtype=np.uint8)
             a = np.ascontiguousarray(in1[i], dtype=np.uint32)
             b = np.ascontiguousarray(in2[i], dtype=np.uint32)
-            if not (len(t) == len(a) == len(b) == int(widths[i])):
-                raise SisuError(-1, f"layer {i}: wiring arrays must have {widths[i]} entries")
-            self._keep += [t, a, b]
-            layers[i] = _Layer(int(widths[i]), t.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
-                               a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
-                               b.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)))
+            if outs is None:
+                if not (len(t) == len(a) == len(b) == int(widths[i])):
+                    raise SisuError(-1, f"layer {i}: wiring arrays must have {widths[i]} entries")
+                self._keep += [t, a, b]
+                layers[i] = _Layer(int(widths[i]), t.ctypes.data_as(u8p), a.ctypes.data_as(u32p),
+                                   b.ctypes.data_as(u32p))
+            else:
+                o = (np.arange(int(widths[i]), dtype=np.uint32) if outs[i] is None
+                     else np.ascontiguousarray(outs[i], dtype=np.uint32))
+                if not (len(t) == len(a) == len(b) == len(o)):
+                    raise SisuError(-1, f"layer {i}: entry arrays of different lengths")
+                self._keep += [t, a, b, o]
+                layers[i] = _AccLayer(int(widths[i]), len(o), o.ctypes.data_as(u32p), t.ctypes.data_as(u8p),
+                                      a.ctypes.data_as(u32p), b.ctypes.data_as(u32p))
         h = ctypes.c_void_p()
-        create = _lib.sisu_circuit_create_host if host_only else _lib.sisu_circuit_create
+        if outs is None:
+            create = _lib.sisu_circuit_create_host if host_only else _lib.sisu_circuit_create
+        else:
+            create = _lib.sisu_circuit_create_acc_host if host_only else _lib.sisu_circuit_create_acc
         _check(create(layers, d, int(widths[d]), int(n_copies), ctypes.byref(h)))
         self._keep = None
         self.h = h
@@ -203,8 +226,12 @@ class Circuit:
 
     @classmethod
     def from_spec(cls, spec, host_only: bool = False):
-        """From any object with widths, types, in1, in2 and n_copies."""
-        return cls(spec.widths, spec.types, spec.in1, spec.in2, spec.n_copies, host_only=host_only)
+        """From any object with widths, types, in1, in2 and n_copies (and
+        outs, for accumulation gates)."""
+        outs = getattr(spec, "outs", None)
+        if outs is not None and all(o is None for o in outs):
+            outs = None
+        return cls(spec.widths, spec.types, spec.in1, spec.in2, spec.n_copies, host_only=host_only, outs=outs)
 
     def __del__(self):
         if getattr(self, "h", None):

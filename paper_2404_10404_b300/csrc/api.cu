@@ -167,38 +167,48 @@ static const char kDefaultDomain[] = "SISU-GKR-v1";
 // ---------------------------------------------------------------------------
 // circuit creation
 
-// Wiring bytes: for each gate layer i and padded gate g:
-//   u8 type || u32le in1 || u32le in2   (type 2 = absent padding gate)
+// Wiring bytes: for each gate layer i and padded gate g in turn,
+//   one entry:   u8 type || u32le in1 || u32le in2
+//   no entry:    u8 2 || u32le 0 || u32le 0          (a padding gate)
+//   k >= 2:      u8 3 || u32le k, then k times u8 type || u32le in1 || u32le in2
+// (a plain circuit, one entry a gate, keeps the one-record-a-gate bytes)
 static void wiring_digest(const HostCircuit& hc, uint32_t out[8]) {
   size_t n = 0;
-  for (uint32_t i = 0; i < hc.d; ++i) n += (size_t)hc.W[i] * 9;
+  for (uint32_t i = 0; i < hc.d; ++i) n += ((size_t)hc.W[i] + hc.out[i].size()) * 9;
   std::vector<uint8_t> buf(n);
   uint8_t* p = buf.data();
   auto put = [&](uint32_t v) {
     p[0] = (uint8_t)v; p[1] = (uint8_t)(v >> 8); p[2] = (uint8_t)(v >> 16); p[3] = (uint8_t)(v >> 24);
     p += 4;
   };
-  for (uint32_t i = 0; i < hc.d; ++i)
+  for (uint32_t i = 0; i < hc.d; ++i) {
+    size_t e = 0;
+    const size_t ne = hc.out[i].size();
     for (uint32_t g = 0; g < hc.W[i]; ++g) {
-      *p++ = hc.type[i][g];
-      put(hc.in1[i][g]);
-      put(hc.in2[i][g]);
+      size_t e1 = e;
+      while (e1 < ne && hc.out[i][e1] == g) ++e1;
+      if (e1 - e == 0) {
+        *p++ = 2; put(0); put(0);
+      } else if (e1 - e == 1) {
+        *p++ = hc.type[i][e]; put(hc.in1[i][e]); put(hc.in2[i][e]);
+      } else {
+        *p++ = 3; put((uint32_t)(e1 - e));
+        for (size_t q = e; q < e1; ++q) {
+          *p++ = hc.type[i][q]; put(hc.in1[i][q]); put(hc.in2[i][q]);
+        }
+      }
+      e = e1;
     }
-  host_statement_digest(buf.data(), n, out);
+  }
+  host_statement_digest(buf.data(), (size_t)(p - buf.data()), out);
 }
 
-static int circuit_create(const sisu_layer* layers, uint32_t n_gate_layers, uint32_t input_width,
-                          uint32_t n_copies, bool on_device, sisu_circuit** out) {
-  if (!out) return fail(SISU_ERR_INVALID_ARG, "out is NULL");
-  *out = nullptr;
-  if (!layers || n_gate_layers == 0) return fail(SISU_ERR_INVALID_ARG, "need at least one gate layer");
-  if (n_gate_layers > SISU_MAX_LAYERS) return fail(SISU_ERR_TOO_LARGE, "more than %u layers", SISU_MAX_LAYERS);
-  if (n_copies == 0 || input_width == 0) return fail(SISU_ERR_INVALID_ARG, "zero copies or zero input width");
+// the padded shape of a circuit from its d + 1 widths (layer d = inputs)
+static int circuit_shape(const uint32_t* widths, uint32_t d, uint32_t n_copies, HostCircuit& hc) {
+  if (d == 0) return fail(SISU_ERR_INVALID_ARG, "need at least one gate layer");
+  if (d > SISU_MAX_LAYERS) return fail(SISU_ERR_TOO_LARGE, "more than %u layers", SISU_MAX_LAYERS);
+  if (n_copies == 0) return fail(SISU_ERR_INVALID_ARG, "zero copies");
   if (n_copies > SISU_MAX_COPIES) return fail(SISU_ERR_TOO_LARGE, "more than 2^24 copies");
-  const uint32_t d = n_gate_layers;
-  std::unique_ptr<sisu_circuit> cc(new (std::nothrow) sisu_circuit());
-  if (!cc) return fail(SISU_ERR_OOM, "host allocation");
-  HostCircuit& hc = cc->hc;
   hc.d = d;
   hc.Creal = n_copies;
   hc.c = ceil_log2(n_copies);
@@ -207,7 +217,7 @@ static int circuit_create(const sisu_layer* layers, uint32_t n_gate_layers, uint
   hc.W.resize(d + 1);
   hc.wreal.resize(d + 1);
   for (uint32_t i = 0; i <= d; ++i) {
-    uint32_t w = i < d ? layers[i].width : input_width;
+    const uint32_t w = widths[i];
     if (w == 0) return fail(SISU_ERR_INVALID_ARG, "layer %u has zero width", i);
     if (w > SISU_MAX_WIDTH) return fail(SISU_ERR_TOO_LARGE, "layer %u wider than 2^24", i);
     hc.wreal[i] = w;
@@ -215,36 +225,44 @@ static int circuit_create(const sisu_layer* layers, uint32_t n_gate_layers, uint
     hc.W[i] = 1u << hc.s[i];
     if (hc.c + hc.s[i] > 32) return fail(SISU_ERR_TOO_LARGE, "copies x width of layer %u above 2^32", i);
   }
-  hc.type.resize(d);
-  hc.in1.resize(d);
-  hc.in2.resize(d);
-  for (uint32_t i = 0; i < d; ++i) {
-    const sisu_layer& ly = layers[i];
-    if (!ly.type || !ly.in1 || !ly.in2) return fail(SISU_ERR_INVALID_ARG, "layer %u: NULL wiring array", i);
-    hc.type[i].assign(hc.W[i], 2);
-    hc.in1[i].assign(hc.W[i], 0);
-    hc.in2[i].assign(hc.W[i], 0);
-    for (uint32_t g = 0; g < ly.width; ++g) {
-      if (ly.type[g] > 1) return fail(SISU_ERR_INVALID_ARG, "layer %u gate %u: type %u", i, g, ly.type[g]);
-      if (ly.in1[g] >= hc.wreal[i + 1] || ly.in2[g] >= hc.wreal[i + 1])
-        return fail(SISU_ERR_INDEX_OOB, "layer %u gate %u: input index beyond width %u", i, g, hc.wreal[i + 1]);
-      hc.type[i][g] = ly.type[g];
-      hc.in1[i][g] = ly.in1[g];
-      hc.in2[i][g] = ly.in2[g];
-    }
-  }
+  hc.out.assign(d, {});
+  hc.type.assign(d, {});
+  hc.in1.assign(d, {});
+  hc.in2.assign(d, {});
+  return SISU_OK;
+}
+
+// one entry of layer i, validated; entries must arrive in order of gate
+static int add_entry(HostCircuit& hc, uint32_t i, uint32_t g, uint8_t t, uint32_t a, uint32_t b) {
+  if (t > 1) return fail(SISU_ERR_INVALID_ARG, "layer %u gate %u: type %u", i, g, t);
+  if (a >= hc.wreal[i + 1] || b >= hc.wreal[i + 1])
+    return fail(SISU_ERR_INDEX_OOB, "layer %u gate %u: input index beyond width %u", i, g, hc.wreal[i + 1]);
+  hc.out[i].push_back(g);
+  hc.type[i].push_back(t);
+  hc.in1[i].push_back(a);
+  hc.in2[i].push_back(b);
+  return SISU_OK;
+}
+
+// Digest, then (on_device) the device arrays of every layer: the entries
+// grouped by type (mul first), each group sorted by in1, followed by the
+// gates with no entry; the CSR of the entries by in1 and by in2; and for
+// layers where some gate has several entries, the entries by gate.
+static int circuit_finish(std::unique_ptr<sisu_circuit>& cc, bool on_device, sisu_circuit** out) {
+  HostCircuit& hc = cc->hc;
+  const uint32_t d = hc.d;
+  for (uint32_t i = 0; i < d; ++i)
+    if ((uint64_t)hc.C * hc.out[i].size() > (1ull << 32) || hc.out[i].size() > (1ull << 28))
+      return fail(SISU_ERR_TOO_LARGE, "layer %u: copies x entries above 2^32", i);
   wiring_digest(hc, hc.wiring_digest);
   if (!on_device) {
     *out = cc.release();
     return SISU_OK;
   }
-
-  // Device arrays per layer: gate_io (W_i x 8 B), sgate (n_i x 16 B),
-  // off1/off2 ((W_{i+1}+1) x 4 B), pos1/pos2 (n_i x 4 B).
   struct Lay {
-    std::vector<uint2> io;
     std::vector<uint4> sg;
-    std::vector<uint32_t> off1, pos1, off2, pos2;
+    std::vector<uint32_t> off1, pos1, off2, pos2, offo;
+    std::vector<uint2> eo;
     uint32_t nmul, ntot;
   };
   std::vector<Lay> H(d);
@@ -253,28 +271,33 @@ static int circuit_create(const sisu_layer* layers, uint32_t n_gate_layers, uint
   for (uint32_t i = 0; i < d; ++i) {
     Lay& l = H[i];
     const uint32_t W = hc.W[i], Wn = hc.W[i + 1];
-    l.io.resize(W);
-    std::vector<uint32_t> muls, adds;
-    for (uint32_t g = 0; g < W; ++g) {
-      l.io[g] = make_uint2(hc.in1[i][g] | ((uint32_t)hc.type[i][g] << 30), hc.in2[i][g]);
-      if (hc.type[i][g] == 1) muls.push_back(g);
-      else if (hc.type[i][g] == 0) adds.push_back(g);
+    const uint32_t ne = (uint32_t)hc.out[i].size();
+    std::vector<uint32_t> muls, adds, count(W, 0);
+    for (uint32_t e = 0; e < ne; ++e) {
+      (hc.type[i][e] == 1 ? muls : adds).push_back(e);
+      ++count[hc.out[i][e]];
     }
-    // each type group sorted by in1 (then g) for locality of the row gathers
+    // each type group sorted by in1 (then entry) for locality of the row gathers
     auto by_in1 = [&](uint32_t a, uint32_t b) {
       return hc.in1[i][a] != hc.in1[i][b] ? hc.in1[i][a] < hc.in1[i][b] : a < b;
     };
     std::sort(muls.begin(), muls.end(), by_in1);
     std::sort(adds.begin(), adds.end(), by_in1);
     l.nmul = (uint32_t)muls.size();
-    l.ntot = (uint32_t)(muls.size() + adds.size());
-    l.sg.resize(W);  // present gates, then the absent (padding) gates
-    for (uint32_t q = 0; q < l.ntot; ++q) {
-      uint32_t g = q < l.nmul ? muls[q] : adds[q - l.nmul];
-      l.sg[q] = make_uint4(hc.in1[i][g], hc.in2[i][g], g, 0);
+    l.ntot = ne;
+    bool acc = false;
+    uint32_t empty = 0;
+    for (uint32_t g = 0; g < W; ++g) {
+      acc |= count[g] > 1;
+      empty += count[g] == 0;
     }
-    for (uint32_t g = 0, q = l.ntot; g < W; ++g)
-      if (hc.type[i][g] == 2) l.sg[q++] = make_uint4(0, 0, g, 0);
+    l.sg.resize((size_t)ne + empty);
+    for (uint32_t q = 0; q < ne; ++q) {
+      const uint32_t e = q < l.nmul ? muls[q] : adds[q - l.nmul];
+      l.sg[q] = make_uint4(hc.in1[i][e], hc.in2[i][e], hc.out[i][e], 0);
+    }
+    for (uint32_t g = 0, q = ne; g < W; ++g)
+      if (count[g] == 0) l.sg[q++] = make_uint4(0, 0, g, 0);
     auto csr = [&](int which, std::vector<uint32_t>& off, std::vector<uint32_t>& pos) {
       off.assign(Wn + 1, 0);
       pos.resize(l.ntot);
@@ -285,7 +308,14 @@ static int circuit_create(const sisu_layer* layers, uint32_t n_gate_layers, uint
     };
     csr(0, l.off1, l.pos1);
     csr(1, l.off2, l.pos2);
-    bytes += al(l.io.size() * 8) + al(l.sg.size() * 16 + 16) + 2 * al(l.off1.size() * 4) + 2 * al(l.pos1.size() * 4 + 4);
+    if (acc) {  // entries by gate (hc's order is by gate already)
+      l.offo.assign(W + 1, 0);
+      for (uint32_t g = 0; g < W; ++g) l.offo[g + 1] = l.offo[g] + count[g];
+      l.eo.resize(ne);
+      for (uint32_t e = 0; e < ne; ++e) l.eo[e] = make_uint2(hc.in1[i][e] | ((uint32_t)hc.type[i][e] << 30), hc.in2[i][e]);
+    }
+    bytes += al(l.sg.size() * 16 + 16) + 2 * al(l.off1.size() * 4) + 2 * al(l.pos1.size() * 4 + 4) +
+             al(l.offo.size() * 4) + al(l.eo.size() * 8);
   }
   CK(cudaGetDevice(&cc->device), "cudaGetDevice");
   cudaError_t e = cudaMalloc(&cc->dev, bytes);
@@ -304,19 +334,73 @@ static int circuit_create(const sisu_layer* layers, uint32_t n_gate_layers, uint
   for (uint32_t i = 0; i < d; ++i) {
     Lay& l = H[i];
     DevLayer& D = cc->L[i];
-    D.gate_io = (const uint2*)up(l.io.data(), l.io.size() * 8, l.io.size() * 8);
     D.sgate = (const uint4*)up(l.sg.data(), l.sg.size() * 16, l.sg.size() * 16 + 16);
     D.off1 = (const uint32_t*)up(l.off1.data(), l.off1.size() * 4, l.off1.size() * 4);
     D.pos1 = (const uint32_t*)up(l.pos1.data(), l.pos1.size() * 4, l.pos1.size() * 4 + 4);
     D.off2 = (const uint32_t*)up(l.off2.data(), l.off2.size() * 4, l.off2.size() * 4);
     D.pos2 = (const uint32_t*)up(l.pos2.data(), l.pos2.size() * 4, l.pos2.size() * 4 + 4);
-    if (!D.gate_io || !D.sgate || !D.off1 || !D.pos1 || !D.off2 || !D.pos2)
+    D.offo = l.offo.empty() ? nullptr : (const uint32_t*)up(l.offo.data(), l.offo.size() * 4, l.offo.size() * 4);
+    D.eo = l.eo.empty() ? nullptr : (const uint2*)up(l.eo.data(), l.eo.size() * 8, l.eo.size() * 8);
+    if (!D.sgate || !D.off1 || !D.pos1 || !D.off2 || !D.pos2 || (!l.offo.empty() && (!D.offo || !D.eo)))
       return fail(SISU_ERR_CUDA, "upload of the wiring failed");
     D.nmul = l.nmul;
     D.ntot = l.ntot;
   }
   *out = cc.release();
   return SISU_OK;
+}
+
+static int circuit_create(const sisu_layer* layers, uint32_t n_gate_layers, uint32_t input_width,
+                          uint32_t n_copies, bool on_device, sisu_circuit** out) {
+  if (!out) return fail(SISU_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!layers || n_gate_layers == 0) return fail(SISU_ERR_INVALID_ARG, "need at least one gate layer");
+  if (n_gate_layers > SISU_MAX_LAYERS) return fail(SISU_ERR_TOO_LARGE, "more than %u layers", SISU_MAX_LAYERS);
+  std::unique_ptr<sisu_circuit> cc(new (std::nothrow) sisu_circuit());
+  if (!cc) return fail(SISU_ERR_OOM, "host allocation");
+  std::vector<uint32_t> widths(n_gate_layers + 1);
+  for (uint32_t i = 0; i < n_gate_layers; ++i) widths[i] = layers[i].width;
+  widths[n_gate_layers] = input_width;
+  if (int rc = circuit_shape(widths.data(), n_gate_layers, n_copies, cc->hc)) return rc;
+  for (uint32_t i = 0; i < n_gate_layers; ++i) {
+    const sisu_layer& ly = layers[i];
+    if (!ly.type || !ly.in1 || !ly.in2) return fail(SISU_ERR_INVALID_ARG, "layer %u: NULL wiring array", i);
+    for (uint32_t g = 0; g < ly.width; ++g)
+      if (int rc = add_entry(cc->hc, i, g, ly.type[g], ly.in1[g], ly.in2[g])) return rc;
+  }
+  return circuit_finish(cc, on_device, out);
+}
+
+static int circuit_create_acc(const sisu_acc_layer* layers, uint32_t n_gate_layers, uint32_t input_width,
+                              uint32_t n_copies, bool on_device, sisu_circuit** out) {
+  if (!out) return fail(SISU_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!layers || n_gate_layers == 0) return fail(SISU_ERR_INVALID_ARG, "need at least one gate layer");
+  if (n_gate_layers > SISU_MAX_LAYERS) return fail(SISU_ERR_TOO_LARGE, "more than %u layers", SISU_MAX_LAYERS);
+  std::unique_ptr<sisu_circuit> cc(new (std::nothrow) sisu_circuit());
+  if (!cc) return fail(SISU_ERR_OOM, "host allocation");
+  std::vector<uint32_t> widths(n_gate_layers + 1);
+  for (uint32_t i = 0; i < n_gate_layers; ++i) widths[i] = layers[i].width;
+  widths[n_gate_layers] = input_width;
+  if (int rc = circuit_shape(widths.data(), n_gate_layers, n_copies, cc->hc)) return rc;
+  for (uint32_t i = 0; i < n_gate_layers; ++i) {
+    const sisu_acc_layer& ly = layers[i];
+    if (ly.n_entries && (!ly.out || !ly.type || !ly.in1 || !ly.in2))
+      return fail(SISU_ERR_INVALID_ARG, "layer %u: NULL entry array", i);
+    if (ly.n_entries > (1u << 28)) return fail(SISU_ERR_TOO_LARGE, "layer %u: more than 2^28 entries", i);
+    // stable counting sort of the entries by gate
+    std::vector<uint32_t> start(ly.width + 1, 0);
+    for (uint32_t e = 0; e < ly.n_entries; ++e) {
+      if (ly.out[e] >= ly.width) return fail(SISU_ERR_INDEX_OOB, "layer %u entry %u: gate beyond width", i, e);
+      ++start[ly.out[e] + 1];
+    }
+    for (uint32_t g = 0; g < ly.width; ++g) start[g + 1] += start[g];
+    std::vector<uint32_t> order(ly.n_entries);
+    for (uint32_t e = 0; e < ly.n_entries; ++e) order[start[ly.out[e]]++] = e;
+    for (uint32_t e : order)
+      if (int rc = add_entry(cc->hc, i, ly.out[e], ly.type[e], ly.in1[e], ly.in2[e])) return rc;
+  }
+  return circuit_finish(cc, on_device, out);
 }
 
 extern "C" int sisu_circuit_create(const sisu_layer* layers, uint32_t n_gate_layers, uint32_t input_width,
@@ -327,6 +411,16 @@ extern "C" int sisu_circuit_create(const sisu_layer* layers, uint32_t n_gate_lay
 extern "C" int sisu_circuit_create_host(const sisu_layer* layers, uint32_t n_gate_layers, uint32_t input_width,
                                         uint32_t n_copies, sisu_circuit** out) {
   return circuit_create(layers, n_gate_layers, input_width, n_copies, false, out);
+}
+
+extern "C" int sisu_circuit_create_acc(const sisu_acc_layer* layers, uint32_t n_gate_layers, uint32_t input_width,
+                                       uint32_t n_copies, sisu_circuit** out) {
+  return circuit_create_acc(layers, n_gate_layers, input_width, n_copies, true, out);
+}
+
+extern "C" int sisu_circuit_create_acc_host(const sisu_acc_layer* layers, uint32_t n_gate_layers,
+                                            uint32_t input_width, uint32_t n_copies, sisu_circuit** out) {
+  return circuit_create_acc(layers, n_gate_layers, input_width, n_copies, false, out);
 }
 
 static bool has_device(const sisu_circuit* circ) { return circ && circ->dev; }

@@ -66,10 +66,11 @@ int launch_layer_to_canonical(const uint32_t* V, uint32_t* out, uint32_t c, uint
 // forward evaluation of one layer (Sec. 2.2): V_i(b, g) = op_g(V_{i+1}(b, in1 g), V_{i+1}(b, in2 g))
 //
 // Threads walk each copy's gates in the sorted order (mul gates, add gates,
-// then the absent padding gates, whose value is 0), so a warp holds one kind
+// then the gates with no entry, whose value is 0), so a warp holds one kind
 // of gate: with the wiring order nearly every warp mixed the two and all of
 // it waited for the Montgomery products of its mul lanes.  The outputs go
-// to each gate's own position (one 32-byte sector per element).
+// to each gate's own position (one 32-byte sector per element).  Layers
+// where every gate has at most one entry only.
 
 __global__ void k_eval_layer(const uint32_t* __restrict__ Vn, uint32_t* __restrict__ V,
                              const uint4* __restrict__ sg, uint32_t nmul, uint32_t ntot, uint32_t c, uint32_t s,
@@ -90,10 +91,34 @@ __global__ void k_eval_layer(const uint32_t* __restrict__ Vn, uint32_t* __restri
   }
 }
 
+// A layer of accumulation gates (Sec. 3.4.3): gate g of copy b is the sum
+// of its entries eo[offo[g] .. offo[g+1]) (0 when it has none).
+__global__ void k_eval_layer_acc(const uint32_t* __restrict__ Vn, uint32_t* __restrict__ V,
+                                 const uint32_t* __restrict__ offo, const uint2* __restrict__ eo, uint32_t c,
+                                 uint32_t s, uint32_t sn) {
+  const size_t total = (size_t)1 << (c + s);
+  const uint32_t mask = (1u << s) - 1u;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t b = (uint32_t)(idx >> s), g = (uint32_t)(idx & mask);
+    const uint32_t* row = Vn + (((size_t)b << sn) << 3);
+    Fr acc = fr_zero();
+    for (uint32_t e = offo[g], ee = offo[g + 1]; e < ee; ++e) {
+      const uint2 io = eo[e];
+      const Fr x = fr_load(row, io.x & 0x3fffffffu), y = fr_load(row, io.y);
+      acc = fr_add(acc, (io.x >> 30) ? fr_mul(x, y) : fr_add(x, y));
+    }
+    fr_store(V, idx, acc);
+  }
+}
+
 int launch_eval_layer(const uint32_t* Vn, uint32_t* V, const DevLayer& L, uint32_t c, uint32_t s, uint32_t sn,
                       void* stream) {
   size_t n = (size_t)1 << (c + s);
-  k_eval_layer<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(Vn, V, L.sgate, L.nmul, L.ntot, c, s, sn);
+  if (L.offo)
+    k_eval_layer_acc<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(Vn, V, L.offo, L.eo, c, s, sn);
+  else
+    k_eval_layer<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(Vn, V, L.sgate, L.nmul, L.ntot, c, s, sn);
   return post_launch();
 }
 

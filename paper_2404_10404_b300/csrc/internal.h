@@ -48,20 +48,27 @@ struct InitParams {
 
 // Per-layer device views of the circuit.
 struct DevLayer {
-  const uint2* gate_io;  // per padded gate: {in1 | type << 30, in2}; type 2 = absent
-  const uint4* sgate;    // present gates, mul first then add, each sorted by in1: {in1, in2, g, 0};
-                         // then the absent gates {0, 0, g, 0} (W_i entries in all)
+  // accumulation layers (some gate has several entries): per gate g its
+  // entries eo[offo[g] .. offo[g+1]) as {in1 | type << 30, in2}; null otherwise
+  const uint32_t* offo;
+  const uint2* eo;
+  const uint4* sgate;    // entries, mul first then add, each sorted by in1: {in1, in2, out gate, 0};
+                         // then the gates with no entry {0, 0, g, 0}
   const uint32_t* off1;  // CSR over layer i+1 positions x: sgate positions with in1 == x
   const uint32_t* pos1;
   const uint32_t* off2;  // same for in2
   const uint32_t* pos2;
-  uint32_t nmul, ntot;   // number of mul gates, of present gates
+  uint32_t nmul, ntot;   // number of mul entries, of entries
 };
 
 // Host copy of the padded circuit (the verifier and the digests use it).
 struct HostCircuit {
   uint32_t d = 0, c = 0, C = 0, Creal = 0;
   std::vector<uint32_t> s, W, wreal;
+  // gate layer i as fan-in-2 entries sorted by output gate (stable): gate
+  // g's value is the sum of its entries (Sec. 3.4.3); a plain gate has one
+  // entry, a padding gate none
+  std::vector<std::vector<uint32_t>> out;
   std::vector<std::vector<uint8_t>> type;
   std::vector<std::vector<uint32_t>> in1, in2;
   uint32_t wiring_digest[8];

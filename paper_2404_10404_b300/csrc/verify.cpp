@@ -424,10 +424,9 @@ int host_verify(const HostCircuit& hc, const uint8_t* inputs, const uint8_t* out
     }
     HF sum = kZero;
     const HF vsum = add(vx, vy), vprod = mul(vx, vy);
-    for (uint32_t g = 0; g < W; ++g) {
-      uint8_t t = hc.type[i][g];
-      if (t == 2) continue;
-      HF term = mul(om[g], mul(qx[hc.in1[i][g]], qy[hc.in2[i][g]]));
+    for (size_t e = 0; e < hc.out[i].size(); ++e) {  // entries, each weighed by w of its gate
+      const uint8_t t = hc.type[i][e];
+      HF term = mul(om[hc.out[i][e]], mul(qx[hc.in1[i][e]], qy[hc.in2[i][e]]));
       sum = add(sum, mul(term, t == 0 ? vsum : vprod));
     }
     if (!eq(claim, mul(eq_point(zb, rb), sum))) return SISU_ERR_REJECT;

@@ -180,3 +180,36 @@ def test_full_size_golden(S, name):
     assert len(proof) == g["proof_len"]
     assert sha(proof) == g["proof_sha256"]
     assert sha(ev.outputs()) == g["outputs_sha256"]
+
+
+@pytest.mark.parametrize("seed,C,widths,k", [
+    (1, 2, [3, 4, 5], 3), (2, 4, [4, 4, 4], 4), (3, 37, [300, 257, 513], 3),  # padded copies and widths
+    (4, 1, [64, 64, 64], 6),                                                  # one copy: no copy phase
+    (5, 512, [1024, 1024, 1024], 2), (6, 64, [16, 2048, 16], 5),
+    (7, 16, [1, 8, 1], 4),                                                    # one gate: no x, y phases
+])
+def test_accumulation_parity(S, oracle, seed, C, widths, k):
+    """Accumulation gates (Sec. 3.4.3): a gate sums several fan-in-2
+    entries; proofs and every layer's values equal the oracle's."""
+    circ = synth.accumulation_circuit(seed, C, widths, k)
+    _, ev, xb, _ = _case(S, oracle, circ)
+    for layer in range(circ.depth + 1):
+        assert ev.layer(layer) == oracle.eval_layer(circ, xb, layer), layer
+
+
+def test_accumulation_wide_next_layer(S, oracle):
+    """Entries over a layer wider than 2^16 take the one-launch-per-round
+    path of Libra's phases."""
+    _case(S, oracle, synth.accumulation_circuit(8, 2, [512, 1 << 17], 3))
+
+
+def test_one_entry_a_gate_equals_plain(S, oracle):
+    """The plain circuit written as one entry a gate proves the same bytes."""
+    plain = synth.micro(19, 64, [128, 96, 128], 50)
+    outs = [np.arange(w, dtype=np.uint32) for w in plain.widths[:-1]]
+    acc = synth.Circuit(plain.widths, plain.types, plain.in1, plain.in2, plain.n_copies, outs=outs)
+    xb = synth.fr_bytes(synth.inputs_for(plain))
+    gp = S.Circuit.from_spec(plain)
+    p_plain = S.prove(gp, S.Eval(gp, xb))
+    ga = S.Circuit.from_spec(acc)
+    assert S.prove(ga, S.Eval(ga, xb)) == p_plain == oracle.prove(plain, xb)

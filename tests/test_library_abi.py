@@ -71,3 +71,36 @@ def test_host_verifier_rejects_forgeries():
     assert S.verify(hc, xb, b"".join(brute.fe(v) for v in outs), forged) == -7
     honest = brute.prove(circ, x)
     assert S.verify(hc, xb, b"".join(brute.fe(v) for v in outs), honest) == 0
+
+
+def test_host_verifier_accumulation_gates(oracle):
+    """Accumulation gates (Sec. 3.4.3) through sisu_circuit_create_acc_host:
+    the host verifier accepts the oracle's proofs and rejects tampering;
+    invalid entries are refused."""
+    import numpy as np
+
+    import paper_2404_10404_b300 as S
+    if not os.path.exists(S.library_path()):
+        pytest.skip("library not built")
+    for circ in (synth.accumulation_circuit(1, 2, [3, 4, 5], 3), synth.accumulation_circuit(5, 8, [6, 3, 8], 3),
+                 synth.accumulation_circuit(6, 1, [4, 4], 5)):
+        xb = synth.fr_bytes(synth.inputs_for(circ))
+        proof, outs = oracle.prove(circ, xb), oracle.outputs(circ, xb)
+        hc = S.Circuit.from_spec(circ, host_only=True)
+        assert hc.proof_len == len(proof)
+        assert S.verify(hc, xb, outs, proof) == 0
+        hdr = 8 + 4 * (circ.depth + 3)
+        for k in range(0, (len(proof) - hdr) // 32, 4):
+            bad = bytearray(proof)
+            bad[hdr + 32 * k] ^= 1
+            assert S.verify(hc, xb, outs, bytes(bad)) == -7
+    u32 = lambda v: np.array(v, np.uint32)
+    with pytest.raises(S.SisuError) as e:  # entry's gate beyond the layer's width
+        S.Circuit([2, 2], [np.zeros(1, np.uint8)], [u32([0])], [u32([1])], 1, host_only=True, outs=[u32([2])])
+    assert e.value.code == -2
+    with pytest.raises(S.SisuError) as e:  # input index beyond the next layer
+        S.Circuit([2, 2], [np.zeros(1, np.uint8)], [u32([0])], [u32([2])], 1, host_only=True, outs=[u32([0])])
+    assert e.value.code == -2
+    with pytest.raises(S.SisuError) as e:  # type 2
+        S.Circuit([2, 2], [np.full(1, 2, np.uint8)], [u32([0])], [u32([1])], 1, host_only=True, outs=[u32([0])])
+    assert e.value.code == -1
