@@ -284,7 +284,7 @@ def run_ours(args):
            "d2h_bytes_per_step": gc.proof_len}
 
     # per-kernel breakdown of one step (untimed pass)
-    S.profile_enable(0x1FF)
+    S.profile_enable(sum(1 << k for k in S.PROF_KINDS))
     step(inputs)
     torch.cuda.synchronize(dev)
     rounds = S.profile_launches(S.PROF_COPY_ROUND)

@@ -378,24 +378,55 @@ __device__ __forceinline__ uint64_t item_at_cost(uint64_t X, uint32_t nmul, uint
   return j * ntot + min(g, (uint64_t)ntot);
 }
 
+// The split of a round's items over nc CTAs (at most ncmax, and no more than
+// one CTA per `min_items` items): with h <= nc, m CTAs per pair and ranges of
+// per_cta cost units inside a pair; otherwise one contiguous range of per_cta
+// units per CTA (m = 0).
+struct CopySplit {
+  uint32_t nc, m;
+  uint64_t per_cta;
+};
+
+__host__ __device__ __forceinline__ CopySplit copy_split(uint32_t h, uint32_t nmul, uint32_t ntot, uint32_t ncmax,
+                                                         uint32_t min_items) {
+  const uint64_t total = (uint64_t)h * ntot;
+  const uint64_t pair_cost = copy_pair_cost(nmul, ntot);
+  uint64_t nc = (total + min_items - 1) / min_items;
+  if (nc > ncmax) nc = ncmax;
+  if (nc < 1) nc = 1;
+  CopySplit sp;
+  if (h <= nc) {
+    sp.m = (uint32_t)(nc / h);
+    sp.per_cta = (pair_cost + sp.m - 1) / sp.m;
+    sp.nc = h * sp.m;
+  } else {
+    const uint64_t total_cost = (uint64_t)h * pair_cost;
+    sp.m = 0;
+    sp.per_cta = (total_cost + nc - 1) / nc;
+    sp.nc = (uint32_t)((total_cost + sp.per_cta - 1) / sp.per_cta);
+  }
+  return sp;
+}
+
+// The items of CTA `bid` of a round split by (per_cta, m): returns, in lanes
+// t < 4 of warp 0, the CTA's share of g(t) (plain, below 2r).  Called by
+// every thread of the block.
 template <int BD>
-__global__ void __launch_bounds__(BD) k_copy_round(const uint32_t* __restrict__ T, uint32_t sn, uint32_t h,
-                                                   const uint32_t* __restrict__ E, const uint32_t* __restrict__ om,
-                                                   const uint4* __restrict__ sg, uint32_t nmul, uint32_t ntot,
-                                                   uint64_t per_cta, uint32_t m, uint32_t* partials, DevState* S,
-                                                   uint8_t* proof, size_t off, uint32_t k) {
-  __shared__ __align__(16) uint32_t sh_e[16];  // E(j), E(j + h) of the current segment
+__device__ __forceinline__ Fr copy_items(const uint32_t* __restrict__ T, uint32_t sn, uint32_t h,
+                                         const uint32_t* __restrict__ E, const uint32_t* __restrict__ om,
+                                         const uint4* __restrict__ sg, uint32_t nmul, uint32_t ntot,
+                                         uint64_t per_cta, uint32_t m, uint32_t bid, uint32_t* sh_e) {
   const uint64_t pair_cost = copy_pair_cost(nmul, ntot);
   uint64_t c0, c1;  // the CTA's cost range
   if (m) {
-    const uint32_t j = blockIdx.x / m, sub = blockIdx.x - j * m;
+    const uint32_t j = bid / m, sub = bid - j * m;
     const uint64_t base = (uint64_t)j * pair_cost;
     c0 = base + min(pair_cost, (uint64_t)sub * per_cta);
     c1 = base + min(pair_cost, (uint64_t)(sub + 1) * per_cta);
   } else {
     const uint64_t total_cost = (uint64_t)h * pair_cost;
-    c0 = min(total_cost, (uint64_t)blockIdx.x * per_cta);
-    c1 = min(total_cost, (uint64_t)(blockIdx.x + 1) * per_cta);
+    c0 = min(total_cost, (uint64_t)bid * per_cta);
+    c1 = min(total_cost, (uint64_t)(bid + 1) * per_cta);
   }
   const uint64_t q0 = item_at_cost(c0, nmul, ntot, pair_cost);
   const uint64_t q1 = item_at_cost(c1, nmul, ntot, pair_cost);
@@ -465,6 +496,17 @@ __global__ void __launch_bounds__(BD) k_copy_round(const uint32_t* __restrict__ 
     seg = segend;
   }
   if (warp == 0 && lane < 4) tot = fr_mul(tot, fr_mont_2_32());  // undo the reductions' 2^-32
+  return tot;
+}
+
+template <int BD>
+__global__ void __launch_bounds__(BD) k_copy_round(const uint32_t* __restrict__ T, uint32_t sn, uint32_t h,
+                                                   const uint32_t* __restrict__ E, const uint32_t* __restrict__ om,
+                                                   const uint4* __restrict__ sg, uint32_t nmul, uint32_t ntot,
+                                                   uint64_t per_cta, uint32_t m, uint32_t* partials, DevState* S,
+                                                   uint8_t* proof, size_t off, uint32_t k) {
+  __shared__ __align__(16) uint32_t sh_e[16];  // E(j), E(j + h) of the current segment
+  const Fr tot = copy_items<BD>(T, sn, h, E, om, sg, nmul, ntot, per_cta, m, blockIdx.x, sh_e);
   Fr acc[4];
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
@@ -487,25 +529,11 @@ int launch_copy_round(const uint32_t* T, uint32_t sn, uint32_t h, const uint32_t
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_copy_round<BD>, BD, 0) != cudaSuccess || n < 1) n = 1;
     per_sm = n;
   }
-  const uint64_t total = (uint64_t)h * L.ntot;
-  const uint64_t pair_cost = copy_pair_cost(L.nmul, L.ntot);
   // contiguous ranges of equal cost: one wave of CTAs, and for small rounds
   // about one item per thread (short serial chains)
-  uint64_t nc = std::min<uint64_t>((uint64_t)kSMs * per_sm, (total + BD - 1) / BD);
-  nc = std::max<uint64_t>(1, std::min<uint64_t>(nc, kMaxPartials));
-  const uint64_t total_cost = (uint64_t)h * pair_cost;
-  uint64_t per_cta;
-  uint32_t m = 0;
-  if (h <= nc) {  // m CTAs per pair, each range inside one pair
-    m = (uint32_t)(nc / h);
-    per_cta = (pair_cost + m - 1) / m;
-    nc = (uint64_t)h * m;
-  } else {
-    per_cta = (total_cost + nc - 1) / nc;  // cost units per CTA
-    nc = (total_cost + per_cta - 1) / per_cta;
-  }
-  k_copy_round<BD><<<(unsigned)nc, BD, 0, st>>>(T, sn, h, E, omega_s, L.sgate, L.nmul, L.ntot, per_cta, m, partials,
-                                                S, proof, off, k);
+  const CopySplit sp = copy_split(h, L.nmul, L.ntot, std::min<uint32_t>(kSMs * per_sm, kMaxPartials), BD);
+  k_copy_round<BD><<<sp.nc, BD, 0, st>>>(T, sn, h, E, omega_s, L.sgate, L.nmul, L.ntot, sp.per_cta, sp.m, partials,
+                                         S, proof, off, k);
   return post_launch();
 }
 
