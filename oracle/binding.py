@@ -83,6 +83,9 @@ class Oracle:
         lib.so_eval_layer.argtypes = [vp, ctypes.c_char_p, ctypes.c_uint32, ctypes.c_char_p]
         lib.so_outputs.argtypes = [vp, ctypes.c_char_p, ctypes.c_char_p]
         lib.so_wiring_digest.argtypes = [vp, ctypes.c_char_p]
+        lib.so_assoc_F.argtypes = [ctypes.c_char_p, sz, ctypes.c_char_p]
+        lib.so_assoc_hash.argtypes = [ctypes.c_char_p, sz, ctypes.c_char_p, ctypes.c_char_p]
+        lib.so_pairwise_distinct_check.argtypes = [ctypes.c_char_p, ctypes.c_char_p, sz]
         lib.so_circuit_log_copies.restype = ctypes.c_uint32
         lib.so_circuit_log_copies.argtypes = [vp]
         lib.so_circuit_log_width.restype = ctypes.c_uint32
@@ -178,6 +181,30 @@ class Oracle:
         if rc != OK:
             raise ValueError(f"oracle mle failed (code {rc})")
         return out.raw
+
+
+    # -- associative hash (Sec. 3.4.1) and pairwise-distinct check (Sec. 3.4.2)
+    def assoc_F(self, elems: bytes) -> bytes:
+        n = len(elems) // 32
+        out = ctypes.create_string_buffer(max(1, 32 * n))
+        rc = self.lib.so_assoc_F(bytes(elems), n, out)
+        if rc != OK:
+            raise ValueError(f"oracle F failed (code {rc})")
+        return out.raw[:32 * n]
+
+    def assoc_hash(self, elems: bytes, h_pre: bytes | None = None) -> bytes:
+        out = ctypes.create_string_buffer(32)
+        rc = self.lib.so_assoc_hash(bytes(elems), len(elems) // 32, None if h_pre is None else bytes(h_pre), out)
+        if rc != OK:
+            raise ValueError(f"oracle associative hash failed (code {rc})")
+        return out.raw
+
+    def pairwise_distinct_check(self, a: bytes, a_sorted: bytes) -> int:
+        assert len(a) == len(a_sorted)
+        rc = self.lib.so_pairwise_distinct_check(bytes(a), bytes(a_sorted), len(a) // 32)
+        if rc < 0:
+            raise ValueError(f"oracle pairwise-distinct check failed (code {rc})")
+        return rc
 
 
 def ints_to_bytes(vals) -> bytes:

@@ -405,3 +405,36 @@ def forge_vy_one_layer(circ, inputs, domain: bytes | None = None) -> bytes:
     vy = (claim - e * A) * pow(e * B % P, P - 2, P) % P
     out += fe(vx) + fe(vy)
     return bytes(out)
+
+
+# ---------------------------------------------------------------------------
+# Associative hash (Sec. 3.4.1, Algorithm 1) and the pairwise-distinct check
+# (Sec. 3.4.2, Algorithm 2) on Python integers.
+
+ASSOC_ADD = 4294967295  # 2^32 - 1, the constant Algorithm 1 adds every round
+
+
+def assoc_F(e: int) -> int:
+    """Algorithm 1: from r = 0, three times r <- (r + e + 2^32 - 1)^3 mod p."""
+    r = 0
+    for _ in range(3):
+        r = pow(r + e + ASSOC_ADD, 3, P)
+    return r
+
+
+def assoc_hash(elems, h_pre: int = 0) -> int:
+    """h_pre + F(e_1) + ... + F(e_n) mod p (the sum form of Sec. 3.4.1)."""
+    h = h_pre % P
+    for e in elems:
+        h = (h + assoc_F(e)) % P
+    return h
+
+
+def pairwise_distinct_check(A, A_sorted) -> int:
+    """Algorithm 2: equal hashes, then a strictly ascending claimed sort."""
+    if assoc_hash(A) != assoc_hash(A_sorted):
+        return 0
+    for i in range(1, len(A_sorted)):
+        if A_sorted[i] <= A_sorted[i - 1]:
+            return 0
+    return 1

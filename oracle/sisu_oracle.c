@@ -33,6 +33,12 @@
  *     Sec. 3.2.1), the final per-layer identity by summing the wiring
  *     predicates over gates, the output claim from the clear outputs and the
  *     input claims from the clear inputs.
+ *   - Associative hash (Sec. 3.4.1, Algorithm 1) and the pairwise-distinct
+ *     check (Sec. 3.4.2, Algorithm 2), on the same field: F(e) starts from
+ *     0 and three times replaces r by (r + e + 4294967295)^3; the hash of a
+ *     list is the sum of F over it (the form Sec. 3.4.1 settles on), and
+ *     the check compares the hashes of a list and of its claimed sorted
+ *     permutation, then requires the latter strictly ascending.
  *   - Transcript: SHA-256 Fiat-Shamir; statement digests are binary Merkle
  *     trees over 1024-byte chunks.  The paper fixes neither: these are the
  *     project's conventions, pinned by the FIPS 180 vectors and by the
@@ -1126,3 +1132,65 @@ int so_outputs(const so_circuit *cc, const uint8_t *inputs, uint8_t *out) {
 }
 
 void so_wiring_digest(const so_circuit *cc, uint8_t out[32]) { memcpy(out, cc->wiring_digest, 32); }
+
+/* ------------------------------------------------------------------ */
+/* Associative hash (Sec. 3.4.1, Algorithm 1) and the pairwise-distinct */
+/* check (Sec. 3.4.2, Algorithm 2).                                      */
+
+/* Algorithm 1: r = 0, then three times r = (r + e + 4294967295)^3. */
+static fr assoc_F(fr e) {
+    const fr big = fr_u64(4294967295u);
+    fr r = fr_zero();
+    for (int i = 0; i < 3; ++i) {
+        fr t = fr_add(fr_add(r, e), big);
+        r = fr_mul(fr_mul(t, t), t);
+    }
+    return r;
+}
+
+/* F of every element of a list (n canonical elements in, n out). */
+int so_assoc_F(const uint8_t *e, size_t n, uint8_t *out) {
+    so_init();
+    for (size_t i = 0; i < n; ++i) {
+        fr x;
+        if (fr_from_bytes(&x, e + 32 * i) != SO_OK) return SO_ERR_CANON;
+        fr_to_bytes(out + 32 * i, assoc_F(x));
+    }
+    return SO_OK;
+}
+
+/* The associative hash of a list, AH = F(e_1) + ... + F(e_n) (the sum form
+ * of Sec. 3.4.1), continued from h_pre (the running value H_pre of
+ * Sec. 3.4.2; NULL stands for 0): out = h_pre + AH(list). */
+int so_assoc_hash(const uint8_t *e, size_t n, const uint8_t *h_pre, uint8_t out[32]) {
+    so_init();
+    fr h = fr_zero();
+    if (h_pre && fr_from_bytes(&h, h_pre) != SO_OK) return SO_ERR_CANON;
+    for (size_t i = 0; i < n; ++i) {
+        fr x;
+        if (fr_from_bytes(&x, e + 32 * i) != SO_OK) return SO_ERR_CANON;
+        h = fr_add(h, assoc_F(x));
+    }
+    fr_to_bytes(out, h);
+    return SO_OK;
+}
+
+/* Algorithm 2 on lists A and A* of n elements each: 1 when AH(A) = AH(A*)
+ * and A*_i > A*_(i-1) for i = 1 .. n-1 (as integers), else 0;
+ * SO_ERR_CANON when an element is not below r. */
+int so_pairwise_distinct_check(const uint8_t *A, const uint8_t *As, size_t n) {
+    so_init();
+    uint8_t h1[32], h2[32];
+    int rc = so_assoc_hash(A, n, NULL, h1);
+    if (rc != SO_OK) return rc;
+    rc = so_assoc_hash(As, n, NULL, h2);
+    if (rc != SO_OK) return rc;
+    if (memcmp(h1, h2, 32) != 0) return 0;
+    for (size_t i = 1; i < n; ++i) {
+        fr prev, cur;
+        fr_from_bytes(&prev, As + 32 * (i - 1));
+        fr_from_bytes(&cur, As + 32 * i);
+        if (mw_cmp(cur.w, prev.w, 4) <= 0) return 0;
+    }
+    return 1;
+}

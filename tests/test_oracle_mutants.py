@@ -56,6 +56,10 @@ MUTANTS = {
                          "g[0] = sent[0]; g[2] = sent[1]; g[3] = sent[2];\n            g[1] = fr_sub(g[0], claim);"),
     "prover_sends_g1": ("sent[0] = g[0];\n    for (int t = 2; t < n; ++t) sent[t - 1] = g[t];",
                         "sent[0] = g[0];\n    for (int t = 2; t < n; ++t) sent[t - 1] = g[t - 1];"),
+    "assoc_constant": ("const fr big = fr_u64(4294967295u);", "const fr big = fr_u64(4294967296u);"),
+    "assoc_square": ("r = fr_mul(fr_mul(t, t), t);", "r = fr_mul(t, t);"),
+    "assoc_no_chain": ("fr t = fr_add(fr_add(r, e), big);", "fr t = fr_add(e, big);"),
+    "distinct_allows_equal": ("if (mw_cmp(cur.w, prev.w, 4) <= 0) return 0;", "if (mw_cmp(cur.w, prev.w, 4) < 0) return 0;"),
     "interp_wrong_node": ("num = fr_mul(num, fr_sub(x, fr_u64((uint64_t)j)));",
                           "num = fr_mul(num, fr_sub(x, fr_u64((uint64_t)j + 1)));"),
 }
@@ -132,6 +136,18 @@ def _pins(o: Oracle) -> list:
             failed.append("brute-acc")
     except ValueError:
         failed.append("prove-acc-error")
+    # associative hash (Sec. 3.4.1): closed forms at e + 2^32 - 1 = 1 and 2;
+    # pairwise-distinct check (Sec. 3.4.2) on a list with a repeat
+    try:
+        got = bytes_to_ints(o.assoc_F(ints_to_bytes([(1 - (2**32 - 1)) % P, (2 - (2**32 - 1)) % P])))
+        if got != [729, 1006012008]:
+            failed.append("assoc-closed-form")
+        if o.pairwise_distinct_check(ints_to_bytes([7, 3, 7]), ints_to_bytes([3, 7, 7])) != 0:
+            failed.append("distinct-repeat")
+        if o.pairwise_distinct_check(ints_to_bytes([7, 3, 9]), ints_to_bytes([3, 7, 9])) != 1:
+            failed.append("distinct-accept")
+    except ValueError:
+        failed.append("assoc-error")
     return failed
 
 
