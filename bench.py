@@ -7,7 +7,12 @@ transcript, and the GKR layer sumcheck of every layer (copy phase, Libra's
 x and y phases), ending with the proof bytes on the host.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload medium|tiny|slot]
+                    [--workload medium|tiny|slot|batched|served|assoc]
+
+``--workload assoc`` times the second data-parallel workload of the paper:
+the associative hash (Sec. 3.4.1) of every slot's validator indexes and the
+pairwise-distinct check (Sec. 3.4.2) of every epoch, in validator indexes
+per second.
 
 With N > 1 (launched by torchrun, one rank per GPU) every rank proves its
 own instance of the workload: independent proofs, no data-path collective
@@ -40,6 +45,7 @@ UNIT = "gates/s"
 SMS, IMAD_PER_SM_CLK, SM_MAX_MHZ = 148, 64, 2032.0
 IMAD_PER_FR_MUL = 264
 ALU_PEAK_TIMAD = SMS * IMAD_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
+FR_P = 0x30644E72E131A029B85045B68181585D2833E84879B9709143E1F593F0000001
 # DRAM traffic (read + write bytes) per launch of the dominant kernel from
 # an ncu capture (profiles/copy_round_medium.md): the mean over the ten copy
 # rounds of a medium layer (every layer has the same shape, so this is the
@@ -325,6 +331,175 @@ def run_ours(args):
 
 
 # ---------------------------------------------------------------------------
+# associative hash (Sec. 3.4.1, Algorithm 1) and pairwise-distinct check
+# (Sec. 3.4.2, Algorithm 2) over validator indexes
+
+ASSOC_METRIC = "validator indexes/s (associative hash of every slot + pairwise-distinct check of every epoch)"
+ASSOC_UNIT = "indexes/s"
+# multiply-adds per evaluation of F: six Montgomery products and one
+# fixed-multiplier product (82 mad.lo + 80 mad.hi) for e -> e R
+IMAD_PER_F = 6 * IMAD_PER_FR_MUL + 162
+ASSOC_EPOCHS, ASSOC_EPOCH, ASSOC_SLOT, ASSOC_LOG_UNIVERSE = 64, 1 << 20, 1 << 15, 21
+
+
+def assoc_inputs(epochs: int):
+    """Per epoch 2^20 distinct indexes below 2^21 in seeded order, and the
+    same indexes sorted (the prover's claimed permutation A*)."""
+    import numpy as np
+    import synth
+    a = np.empty((epochs * ASSOC_EPOCH, 4), dtype=np.uint64)
+    s = np.empty_like(a)
+    for e in range(epochs):
+        idx = synth.validator_indexes(6 * 2**32 + e, ASSOC_EPOCH, ASSOC_LOG_UNIVERSE)
+        a[e * ASSOC_EPOCH:(e + 1) * ASSOC_EPOCH] = idx
+        s[e * ASSOC_EPOCH:(e + 1) * ASSOC_EPOCH] = idx[np.argsort(idx[:, 0], kind="stable")]
+    return a, s
+
+
+def assoc_describe(epochs: int) -> str:
+    return (f"assoc: {epochs} epochs x 2^20 validator indexes (distinct, below 2^21, seeded order), "
+            f"hash of every slot list of 2^15 (Algorithm 1), Algorithm 2 on every epoch against its sorted list")
+
+
+def time_assoc_oracle(a_bytes: bytes, s_bytes: bytes):
+    from oracle import Oracle
+    o = Oracle()
+    t0 = time.perf_counter()
+    for k in range(0, len(a_bytes), 32 * ASSOC_SLOT):
+        o.assoc_hash(a_bytes[k:k + 32 * ASSOC_SLOT])
+    o.pairwise_distinct_check(a_bytes, s_bytes)
+    return time.perf_counter() - t0
+
+
+def run_assoc_reference(args):
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    a, s = assoc_inputs(1)
+    ab, sb = a.tobytes(), s.tobytes()
+    for _ in range(args.warmup):
+        time_assoc_oracle(ab[:32 * ASSOC_SLOT], sb[:32 * ASSOC_SLOT])
+    total = 0.0
+    for _ in range(args.steps):
+        total += time_assoc_oracle(ab, sb)
+    value = args.steps * ASSOC_EPOCH / total
+    sample = "one epoch (2^20 indexes) per step: its 32 slot hashes and Algorithm 2 on it"
+    line = {"impl": "reference", "metric": ASSOC_METRIC, "value": value, "unit": ASSOC_UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": assoc_describe(ASSOC_EPOCHS), "sample": sample},
+            "cpu_baseline": {"value": value, "unit": ASSOC_UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": ASSOC_UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_assoc(args):
+    import numpy as np
+    import torch
+
+    import paper_2404_10404_b300 as S
+    from oracle import Oracle
+    from paper_2404_10404_b300.build import build
+
+    torch.cuda.set_device(0)
+    build()
+    dev = torch.device("cuda", 0)
+    epochs = ASSOC_EPOCHS
+    n = epochs * ASSOC_EPOCH
+    t0 = time.time()
+    a, s = assoc_inputs(epochs)
+    log(f"[bench] assoc: {n} indexes drawn in {time.time() - t0:.1f} s")
+    host_a = torch.from_numpy(a.view(np.uint8).reshape(-1)).pin_memory()
+    host_s = torch.from_numpy(s.view(np.uint8).reshape(-1)).pin_memory()
+    da, ds = host_a.to(dev), host_s.to(dev)
+    slot_offs = np.arange(0, n + 1, ASSOC_SLOT, dtype=np.uint64)
+    epoch_offs = np.arange(0, n + 1, ASSOC_EPOCH, dtype=np.uint64)
+    stream = torch.cuda.Stream(device=dev)
+    st = stream.cuda_stream
+
+    def step(xa, xs):
+        h = S.assoc_hash_segments(xa, slot_offs, stream=st)
+        res, ha, hs = S.pairwise_distinct_check_segments(xa, xs, epoch_offs, stream=st)
+        return h, res, ha
+
+    h, res, ha = step(da, ds)
+    # parity: every epoch's indexes are distinct (Algorithm 2 must accept
+    # each), two slot hashes and one epoch hash against the oracle, and each
+    # epoch's hash is the sum of its slots' hashes
+    o = Oracle()
+    ab = a.tobytes()
+    ok = all(r == 1 for r in res)
+    for g in (0, len(slot_offs) - 2):
+        ok &= h[g] == o.assoc_hash(ab[32 * g * ASSOC_SLOT:32 * (g + 1) * ASSOC_SLOT])
+    ok &= ha[0] == o.assoc_hash(ab[:32 * ASSOC_EPOCH])
+    per = ASSOC_EPOCH // ASSOC_SLOT
+    ok &= all(sum(int.from_bytes(x, "little") for x in h[e * per:(e + 1) * per]) % FR_P
+              == int.from_bytes(ha[e], "little") for e in range(epochs))
+    for _ in range(max(0, args.warmup - 1)):
+        step(da, ds)
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = Clocks(uuid)
+    time.sleep(0.5)
+    torch.cuda.synchronize(dev)
+    launches0 = S.kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks.mark(True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step(da, ds)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks.mark(False)
+    ms = ev0.elapsed_time(ev1)
+    launches = S.kernel_launches() - launches0
+    clk = clocks.stop()
+    # the two summing kernels timed with events on their stream
+    S.profile_enable((1 << S.PROF_ASSOC_HASH) | (1 << S.PROF_ASSOC_PAIR))
+    for _ in range(min(args.steps, 5)):
+        step(da, ds)
+    torch.cuda.synchronize(dev)
+    kern = {}
+    for kind, name in ((S.PROF_ASSOC_HASH, "k_assoc_chunks<false> (slot hashes)"),
+                       (S.PROF_ASSOC_PAIR, "k_assoc_chunks<true> (pairwise-distinct check)")):
+        kms, kn, kf = S.profile_read(kind)
+        kern[name] = (kms, kn, kf)
+    S.profile_enable(0)
+    dom = max(kern, key=lambda k: kern[k][0])
+    kms, kn, kf = kern[dom]
+    achieved = kf * IMAD_PER_F / (kms / 1e3) / 1e12
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": ALU_PEAK_TIMAD, "unit": "TIMAD/s",
+                "frac": achieved / ALU_PEAK_TIMAD, "traffic": None, "per_launch_ms": kms / kn, "launches_timed": kn,
+                "f_evaluations_per_launch": kf / kn, "imad_per_f": IMAD_PER_F,
+                "peak_source": "derived: 148 SMs x 64 IMAD/clk x 2032 MHz",
+                "kernels_ms_per_step": {k: round(v[0] / v[1], 4) for k, v in kern.items()}}
+    # end to end from pinned host memory: the calls copy the lists in
+    torch.cuda.synchronize(dev)
+    w0 = time.perf_counter()
+    for _ in range(args.steps):
+        step(host_a, host_s)
+    e2e_s = time.perf_counter() - w0
+    e2e = {"value": args.steps * n / e2e_s, "unit": ASSOC_UNIT, "h2d_bytes_per_step": 3 * 32 * n,
+           "d2h_bytes_per_step": 32 * (len(slot_offs) - 1) + 68 * epochs}
+    line = {"metric": ASSOC_METRIC, "value": args.steps * n / (ms / 1e3), "unit": ASSOC_UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": assoc_describe(epochs), "indexes_per_step": n,
+                       "slots_per_step": len(slot_offs) - 1, "epochs_per_step": epochs,
+                       "l2": "inputs larger than L2: 2 GiB of indexes and 2 GiB of sorted indexes"},
+            "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
+            "parity": {"oracle_and_definition": bool(ok)}}
+    if not args.no_cpu_baseline:
+        secs = time_assoc_oracle(ab[:32 * ASSOC_EPOCH], s.tobytes()[:32 * ASSOC_EPOCH])
+        line["cpu_baseline"] = {"value": ASSOC_EPOCH / secs, "unit": ASSOC_UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"one epoch (2^20 indexes): 32 slot hashes and Algorithm 2, {secs:.1f} s, "
+                                          "single-threaded C oracle on the host"}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
 # batched: many independent instances of uneven size
 
 def run_batched(args):
@@ -522,7 +697,7 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["tiny", "medium", "slot", "batched", "served"], default="medium")
+    ap.add_argument("--workload", choices=["tiny", "medium", "slot", "batched", "served", "assoc"], default="medium")
     ap.add_argument("--jobs", type=int, default=200, help="served: number of jobs")
     ap.add_argument("--templates", type=int, default=16, help="served: distinct job instances")
     ap.add_argument("--slots", type=int, default=16, help="served: concurrent jobs")
@@ -533,8 +708,12 @@ def main():
     ap.add_argument("--depth", type=int, default=None,
                     help="keep only the workload's first layers (profiler captures)")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.impl == "reference" and args.workload == "assoc":
+        run_assoc_reference(args)
+    elif args.impl == "reference":
         run_reference(args)
+    elif args.workload == "assoc":
+        run_assoc(args)
     elif args.workload == "batched":
         run_batched(args)
     elif args.workload == "served":

@@ -214,6 +214,47 @@ void sisu_server_destroy(sisu_server* s);
 int sisu_gkr_verify(const sisu_circuit* circ, const uint8_t* inputs, const uint8_t* outputs,
                     const uint8_t* proof, size_t proof_len, const uint8_t* domain, size_t dlen);
 
+/* ---- associative hash (Sec. 3.4.1, Algorithm 1) and the pairwise-distinct
+ * check (Sec. 3.4.2, Algorithm 2) ---------------------------------------------
+ * F(e): r = 0, then three times r = (r + e + 2^32 - 1)^3 in the BN254 scalar
+ * field; the hash of a list is h_pre + F(e_1) + ... + F(e_n), which does not
+ * depend on the order of the list and continues from the hash h_pre of an
+ * earlier list (the running value H_pre of Sec. 3.4.2; NULL stands for 0).
+ *
+ * Elements are 32-byte canonical little-endian values, `elems` holding
+ * offsets[n_segments] of them back to back: host memory (on_device = 0,
+ * copied in by the call) or device memory (on_device != 0, 16-byte
+ * aligned).  Segment g is elements [offsets[g], offsets[g+1]) (host array
+ * of n_segments + 1 values, offsets[0] = 0, not decreasing; empty segments
+ * allowed) and gets out[32 g .. 32 g + 31] (host) = h_pre[g] + sum of F over
+ * it, h_pre a host array of n_segments canonical values or NULL.  The work
+ * is enqueued on `stream` (a cudaStream_t or NULL); the call blocks until
+ * the results are copied out.
+ * Errors: INVALID_ARG (NULL arrays, offsets, misaligned device array),
+ * NOT_CANONICAL (an element or h_pre value not below r), CUDA. */
+int sisu_assoc_hash_segments(const uint8_t* elems, const uint64_t* offsets, uint32_t n_segments,
+                             const uint8_t* h_pre, int on_device, void* stream, uint8_t* out);
+/* One segment of n elements; h_pre: one canonical value or NULL. */
+int sisu_assoc_hash(const uint8_t* elems, uint64_t n, const uint8_t* h_pre, int on_device, void* stream,
+                    uint8_t* out);
+/* Algorithm 2 on lists a and a_sorted of n elements each (same memory kind,
+ * as above): *result = 1 when the two hashes are equal and a_sorted is
+ * strictly ascending as integers (a_sorted[i] > a_sorted[i-1]), else 0.
+ * With a_sorted the sorted permutation of a that the prover supplies, 1
+ * means the elements of a are pairwise distinct.  h_a, h_sorted (host, 32
+ * bytes, may be NULL) receive the two hashes.  n = 0 gives 1.
+ * Errors: INVALID_ARG, NOT_CANONICAL, CUDA. */
+int sisu_pairwise_distinct_check(const uint8_t* a, const uint8_t* a_sorted, uint64_t n, int on_device, void* stream,
+                                 int* result, uint8_t* h_a, uint8_t* h_sorted);
+/* Algorithm 2 on every segment g (elements [offsets[g], offsets[g+1]) of
+ * both arrays; offsets as for sisu_assoc_hash_segments): results[g] (host,
+ * n_segments ints) as above; h_a, h_sorted (host, 32 n_segments bytes each,
+ * may be NULL) receive the segments' hashes.  A segment's order check does
+ * not look across its first element. */
+int sisu_pairwise_distinct_check_segments(const uint8_t* a, const uint8_t* a_sorted, const uint64_t* offsets,
+                                          uint32_t n_segments, int on_device, void* stream, int* results,
+                                          uint8_t* h_a, uint8_t* h_sorted);
+
 /* ---- field core (Sec. 4.1, BN254 scalar field) ----------------------------
  * Elementwise on device arrays of n canonical elements, enqueued on
  * `stream` and awaited: op 0 a+b, 1 a-b, 2 a*b, 3 a^-1 (batched inversion:
@@ -268,7 +309,9 @@ int sisu_microbench(int kind, uint32_t blocks, uint32_t threads, uint32_t iters,
 /* Per-kernel timing with CUDA events on the launching stream.  Bit k of
  * kind_mask enables kind k: 0 copy-phase round, 1 copy-phase fold, 2 layer
  * evaluation, 3 x/y-phase round, 4 statement digests, 5 layer init, 6 x/y
- * phase init, 7 transcript-only kernels, 8 input conversion; 0 disables.
+ * phase init, 7 transcript-only kernels, 8 input conversion, 9 associative
+ * hash sums, 10 pairwise-distinct sums (for 9 and 10 the work counted is
+ * evaluations of F, not field products); 0 disables.
  * sisu_profile_read waits for the recorded events of one kind and returns
  * their summed milliseconds, the launch count and the algorithmic field
  * products of those launches (per copy-phase pair: 5 per mul gate, 2 per

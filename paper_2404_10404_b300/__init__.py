@@ -34,9 +34,12 @@ ENTRY_POINTS = [
     "sisu_profile_enable", "sisu_profile_read", "sisu_profile_launches", "sisu_statement_digest_noalloc",
     "sisu_gkr_prove_batch", "sisu_server_create", "sisu_server_submit", "sisu_server_poll",
     "sisu_server_pending", "sisu_server_destroy",
+    "sisu_assoc_hash", "sisu_assoc_hash_segments", "sisu_pairwise_distinct_check",
+    "sisu_pairwise_distinct_check_segments",
 ]
 PROF_COPY_ROUND, PROF_COPY_FOLD, PROF_EVAL, PROF_GATE_ROUND, PROF_DIGEST = 0, 1, 2, 3, 4
 PROF_LAYER_INIT, PROF_PHASE_INIT, PROF_TRANSCRIPT, PROF_INPUTS = 5, 6, 7, 8
+PROF_ASSOC_HASH, PROF_ASSOC_PAIR = 9, 10
 PROF_KINDS = {0: "copy_round", 1: "copy_fold", 2: "eval_layer", 3: "gate_round", 4: "digest",
               5: "layer_init", 6: "phase_init", 7: "transcript", 8: "inputs"}
 
@@ -96,6 +99,13 @@ def _load():
         "sisu_statement_digest_noalloc": ([vp, sz, vp, vp], ctypes.c_int),
         "sisu_microbench": ([ctypes.c_int, u32, u32, u32, vp, ctypes.POINTER(ctypes.c_double),
                              ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+        "sisu_assoc_hash": ([vp, ctypes.c_uint64, vp, ctypes.c_int, vp, vp], ctypes.c_int),
+        "sisu_assoc_hash_segments": ([vp, ctypes.POINTER(ctypes.c_uint64), u32, vp, ctypes.c_int, vp, vp],
+                                     ctypes.c_int),
+        "sisu_pairwise_distinct_check": ([vp, vp, ctypes.c_uint64, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int),
+                                          vp, vp], ctypes.c_int),
+        "sisu_pairwise_distinct_check_segments": ([vp, vp, ctypes.POINTER(ctypes.c_uint64), u32, ctypes.c_int, vp,
+                                                   ctypes.POINTER(ctypes.c_int), vp, vp], ctypes.c_int),
         "sisu_kernel_launches": ([], ctypes.c_uint64),
         "sisu_free": ([vp], None),
         "sisu_last_error": ([], ctypes.c_char_p),
@@ -399,6 +409,65 @@ def fr_batch(op: int, a, b, out, n: int, stream=None):
     pb, _, kb = _ptr(b)
     po, _, ko = _ptr(out)
     _check(_lib.sisu_fr_batch(op, pa, pb, po, n, _stream(stream)))
+
+
+def assoc_hash(elems, n: int | None = None, h_pre: bytes | None = None, stream=None) -> bytes:
+    """Associative hash (Sec. 3.4.1, Algorithm 1) of n canonical elements
+    (bytes/numpy on the host, or a CUDA tensor), continued from h_pre."""
+    p, dev, keep = _ptr(elems)
+    if n is None:
+        n = (elems.numel() * elems.element_size() if hasattr(elems, "numel") else len(elems)) // 32
+    out = ctypes.create_string_buffer(32)
+    pre = None if h_pre is None else ctypes.create_string_buffer(bytes(h_pre), 32)
+    _check(_lib.sisu_assoc_hash(p, n, ctypes.cast(pre, ctypes.c_void_p) if pre is not None else None, dev,
+                                _stream(stream), ctypes.cast(out, ctypes.c_void_p)))
+    return out.raw
+
+
+def assoc_hash_segments(elems, offsets, h_pre: bytes | None = None, stream=None) -> list:
+    """The hash of every segment [offsets[g], offsets[g+1]) of the elements,
+    each continued from its 32-byte value in h_pre (concatenated) if given."""
+    p, dev, keep = _ptr(elems)
+    m = len(offsets) - 1
+    offs = (ctypes.c_uint64 * len(offsets))(*[int(x) for x in offsets])
+    out = ctypes.create_string_buffer(32 * max(1, m))
+    pre = None if h_pre is None else ctypes.create_string_buffer(bytes(h_pre), 32 * m)
+    _check(_lib.sisu_assoc_hash_segments(p, offs, m, ctypes.cast(pre, ctypes.c_void_p) if pre is not None else None,
+                                         dev, _stream(stream), ctypes.cast(out, ctypes.c_void_p)))
+    raw = out.raw
+    return [raw[32 * g:32 * g + 32] for g in range(m)]
+
+
+def pairwise_distinct_check(a, a_sorted, n: int | None = None, stream=None):
+    """Algorithm 2 (Sec. 3.4.2): (result, hash of a, hash of a_sorted)."""
+    pa, dev, ka = _ptr(a)
+    ps, dev2, ks = _ptr(a_sorted)
+    if dev != dev2:
+        raise ValueError("a and a_sorted must both be host or both be device arrays")
+    if n is None:
+        n = (a.numel() * a.element_size() if hasattr(a, "numel") else len(a)) // 32
+    res = ctypes.c_int(-1)
+    ha, hs = ctypes.create_string_buffer(32), ctypes.create_string_buffer(32)
+    _check(_lib.sisu_pairwise_distinct_check(pa, ps, n, dev, _stream(stream), ctypes.byref(res),
+                                             ctypes.cast(ha, ctypes.c_void_p), ctypes.cast(hs, ctypes.c_void_p)))
+    return res.value, ha.raw, hs.raw
+
+
+def pairwise_distinct_check_segments(a, a_sorted, offsets, stream=None):
+    """Algorithm 2 on every segment: (results, hashes of a, hashes of a_sorted)."""
+    pa, dev, ka = _ptr(a)
+    ps, dev2, ks = _ptr(a_sorted)
+    if dev != dev2:
+        raise ValueError("a and a_sorted must both be host or both be device arrays")
+    m = len(offsets) - 1
+    offs = (ctypes.c_uint64 * len(offsets))(*[int(x) for x in offsets])
+    res = (ctypes.c_int * max(1, m))()
+    ha, hs = ctypes.create_string_buffer(32 * max(1, m)), ctypes.create_string_buffer(32 * max(1, m))
+    _check(_lib.sisu_pairwise_distinct_check_segments(pa, ps, offs, m, dev, _stream(stream), res,
+                                                      ctypes.cast(ha, ctypes.c_void_p),
+                                                      ctypes.cast(hs, ctypes.c_void_p)))
+    ra, rs = ha.raw, hs.raw
+    return list(res)[:m], [ra[32 * g:32 * g + 32] for g in range(m)], [rs[32 * g:32 * g + 32] for g in range(m)]
 
 
 def statement_digest(data, length: int, stream=None) -> bytes:

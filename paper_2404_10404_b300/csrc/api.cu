@@ -88,22 +88,26 @@ cudaEvent_t pool_event() {
   return e;
 }
 
-// Times one launch when its kind is enabled: returns the index of the record.
+// Times one launch when its kind is enabled.
 struct ProfScope {
   long idx = -1;
   cudaStream_t st;
-  ProfScope(uint32_t kind, double work, cudaStream_t s) : st(s) {
-    if (!(g_prof_mask & (1u << kind))) return;
-    ProfRec r{pool_event(), pool_event(), work, kind};
-    cudaEventRecord(r.a, st);
-    g_prof.push_back(r);
-    idx = (long)g_prof.size() - 1;
-  }
-  ~ProfScope() {
-    if (idx >= 0) cudaEventRecord(g_prof[idx].b, st);
-  }
+  ProfScope(uint32_t kind, double work, cudaStream_t s) : st(s) { idx = sisu::prof_begin(kind, work, s); }
+  ~ProfScope() { sisu::prof_end(idx, st); }
 };
 }  // namespace
+
+long sisu::prof_begin(uint32_t kind, double work, void* stream) {
+  if (!(g_prof_mask & (1u << kind))) return -1;
+  ProfRec r{pool_event(), pool_event(), work, kind};
+  cudaEventRecord(r.a, (cudaStream_t)stream);
+  g_prof.push_back(r);
+  return (long)g_prof.size() - 1;
+}
+
+void sisu::prof_end(long idx, void* stream) {
+  if (idx >= 0) cudaEventRecord(g_prof[idx].b, (cudaStream_t)stream);
+}
 
 enum : uint32_t {
   kProfCopyRound = 0, kProfCopyFold = 1, kProfEval = 2, kProfGateRound = 3, kProfDigest = 4,

@@ -1,0 +1,342 @@
+// Associative hash (Sec. 3.4.1, Algorithm 1) and the pairwise-distinct
+// check (Sec. 3.4.2, Algorithm 2) on the device.
+//
+// F(e): r = 0, then three times r = (r + e + 2^32 - 1)^3, in the BN254
+// scalar field.  The hash of a list is the sum of F over it, so it does not
+// depend on the order of the list and a list's hash continues from the hash
+// of an earlier list by addition (the running value H_pre of Sec. 3.4.2).
+// Algorithm 2 accepts a list A and a claimed sorted permutation A* when
+// their hashes agree and A* is strictly ascending.
+//
+// Work layout: the elements of all segments (sub-lists hashed separately,
+// the paper's M sub-circuits) form one array of 32-byte canonical values.
+// The host cuts every segment into chunks of equal size; one CTA sums F over
+// a chunk (threads stride the chunk, so a warp reads 1 KB contiguous per
+// step), and a second launch adds each segment's chunk sums, one warp per
+// segment.  F costs one fixed-multiplier product (e R from the canonical
+// e) and six Montgomery products; the path is bound by the integer
+// multiply-add pipe, not by HBM (32 bytes per element against about 1,700
+// multiply-adds).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "../../include/sisu.h"
+#include "fr_wide.cuh"
+#include "internal.h"
+#include "launch.cuh"
+
+namespace sisu {
+
+constexpr int kAssocBD = 256;
+constexpr uint32_t kAssocAdd = 4294967295u;  // 2^32 - 1, added every round of Algorithm 1
+
+// device error word bits
+constexpr uint32_t kAssocNotCanonical = 1u;
+
+// the CTA's constants: the fixed-multiplier coefficients of R^2 mod p (so
+// that fr_mul_fixed(e, K) = e R, the Montgomery form of a canonical e) and
+// (2^32 - 1) R
+__device__ __forceinline__ void assoc_consts(uint32_t* shK, Fr* sh_c) {
+  if (threadIdx.x < 8) fr_store(shK, threadIdx.x, fr_fixed_coeff(fr_r2(), (int)threadIdx.x));
+  if (threadIdx.x == 8) {
+    Fr c = fr_zero();
+    c.v[0] = kAssocAdd;
+    *sh_c = fr_from_canonical(c);
+  }
+  __syncthreads();
+}
+
+// F(e) in Montgomery form for a canonical e
+__device__ __forceinline__ Fr assoc_F(const Fr& e, const uint32_t* K, const Fr& c) {
+  const Fr a = fr_add(fr_mul_fixed(e, K), c);  // (e + 2^32 - 1) R
+  Fr r = fr_mul(fr_mul(a, a), a);
+  Fr t = fr_add(r, a);
+  r = fr_mul(fr_mul(t, t), t);
+  t = fr_add(r, a);
+  return fr_mul(fr_mul(t, t), t);
+}
+
+// x > y for canonical values (plain 256-bit integers)
+__device__ __forceinline__ bool u256_gt(const Fr& x, const Fr& y) {
+#pragma unroll
+  for (int i = 7; i >= 0; --i)
+    if (x.v[i] != y.v[i]) return x.v[i] > y.v[i];
+  return false;
+}
+
+template <int NV>
+__device__ __forceinline__ void assoc_block_sum(Fr (&v)[NV]) {
+  __shared__ Fr red[NV][kAssocBD / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int t = 0; t < NV; ++t) v[t] = fr_warp_sum(v[t]);
+  if (lane == 0)
+#pragma unroll
+    for (int t = 0; t < NV; ++t) red[t][warp] = v[t];
+  __syncthreads();
+  if (warp == 0)
+#pragma unroll
+    for (int t = 0; t < NV; ++t) v[t] = fr_warp_sum(lane < kAssocBD / 32 ? red[t][lane] : fr_zero());
+  __syncthreads();
+}
+
+// Sums of F over chunk k = elements [chunks[3k], chunks[3k+1]) of `a` (and,
+// with kPair, of `s`) into partials[NV k + t].  With kPair, unordered[k] = 1
+// when some element i of the chunk, other than the first of its segment
+// (chunks[3k+2]), is not above element i - 1 of `s`.
+template <bool kPair>
+__global__ void __launch_bounds__(kAssocBD, 2) k_assoc_chunks(const uint32_t* __restrict__ a,
+                                                          const uint32_t* __restrict__ s,
+                                                          const uint64_t* __restrict__ chunks, uint32_t nchunks,
+                                                          uint32_t* __restrict__ partials,
+                                                          uint32_t* __restrict__ unordered, uint32_t* flag) {
+  constexpr int NV = kPair ? 2 : 1;
+  __shared__ __align__(16) uint32_t shK[64];
+  __shared__ Fr sh_c;
+  assoc_consts(shK, &sh_c);
+  const Fr c = sh_c;
+  uint32_t err = 0;
+  for (uint32_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    const uint64_t b = chunks[3 * (size_t)ch], e = chunks[3 * (size_t)ch + 1], sb = chunks[3 * (size_t)ch + 2];
+    bool unord = false;
+    Fr acc[NV];
+#pragma unroll
+    for (int t = 0; t < NV; ++t) acc[t] = fr_zero();
+    for (uint64_t i = b + threadIdx.x; i < e; i += kAssocBD) {
+      Fr x = fr_load(a, i);
+      if (!fr_lt_modulus(x)) {
+        err |= kAssocNotCanonical;
+        x = fr_zero();
+      }
+      acc[0] = fr_add(acc[0], assoc_F(x, shK, c));
+      if (kPair) {
+        Fr y = fr_load(s, i);
+        if (!fr_lt_modulus(y)) {
+          err |= kAssocNotCanonical;
+          y = fr_zero();
+        }
+        acc[NV - 1] = fr_add(acc[NV - 1], assoc_F(y, shK, c));
+        if (i > sb && !u256_gt(y, fr_load(s, i - 1))) unord = true;
+      }
+    }
+    if (kPair) unord = __syncthreads_or(unord);
+    assoc_block_sum<NV>(acc);
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int t = 0; t < NV; ++t) fr_store(partials, (size_t)NV * ch + t, acc[t]);
+      if (kPair) unordered[ch] = unord ? 1u : 0u;
+    }
+  }
+  if (err) atomicOr(flag, err);
+}
+
+// out[NV g + t] = canonical(h_pre[g] + sum of the chunk sums of segment g),
+// one warp per (segment, value); h_pre canonical (null: 0)
+__global__ void k_assoc_finish(const uint32_t* __restrict__ partials, const uint32_t* __restrict__ seg_chunk,
+                               uint32_t nseg, int NV, const uint32_t* __restrict__ h_pre, uint32_t* __restrict__ out,
+                               uint32_t* flag) {
+  const uint32_t wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (wid >= nseg * (uint32_t)NV) return;
+  const uint32_t g = wid / NV, t = wid - g * NV;
+  Fr x = fr_zero();
+  for (uint32_t k = seg_chunk[g] + lane; k < seg_chunk[g + 1]; k += 32)
+    x = fr_add(x, fr_load(partials, (size_t)NV * k + t));
+  x = fr_warp_sum(x);
+  if (lane == 0) {
+    if (h_pre) {
+      const Fr h = fr_load(h_pre, g);
+      if (!fr_lt_modulus(h)) atomicOr(flag, kAssocNotCanonical);
+      x = fr_add(x, fr_from_canonical(h));
+    }
+    fr_store(out, wid, fr_to_canonical(x));
+  }
+}
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  cudaStream_t st = nullptr;
+  ~DevBuf() {
+    if (p) cudaFreeAsync(p, st);
+  }
+};
+
+int cuda_err(cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  return report_error(SISU_ERR_CUDA, m.c_str());
+}
+
+#define ACK(call, what)                                 \
+  do {                                                  \
+    cudaError_t e_ = (cudaError_t)(call);               \
+    if (e_ != cudaSuccess) return cuda_err(e_, what);   \
+  } while (0)
+
+// Hash the segments of `a` (and, with `pair`, of `s`): out receives
+// NV x nseg canonical values (segment-major); with `pair`, seg_unordered[g]
+// = 1 when segment g of `s` is not strictly ascending.
+int assoc_run(const uint8_t* a, const uint8_t* s, bool pair, const uint64_t* offsets, uint32_t nseg,
+              const uint8_t* h_pre, int on_device, cudaStream_t st, uint8_t* out, uint32_t* host_flag,
+              int* seg_unordered) {
+  const int NV = pair ? 2 : 1;
+  const uint64_t n = offsets[nseg];
+  // chunks: about eight per SM over the whole array, at least 4096 elements,
+  // a multiple of the CTA width, each inside one segment
+  uint64_t ch = std::max<uint64_t>(4096, (n + 8 * kSMs - 1) / (8 * kSMs));
+  ch = (ch + kAssocBD - 1) / kAssocBD * kAssocBD;
+  std::vector<uint64_t> chunks;
+  std::vector<uint32_t> seg_chunk(nseg + 1);
+  for (uint32_t g = 0; g < nseg; ++g) {
+    seg_chunk[g] = (uint32_t)(chunks.size() / 3);
+    for (uint64_t b = offsets[g]; b < offsets[g + 1]; b += ch) {
+      chunks.push_back(b);
+      chunks.push_back(std::min(offsets[g + 1], b + ch));
+      chunks.push_back(offsets[g]);
+    }
+  }
+  seg_chunk[nseg] = (uint32_t)(chunks.size() / 3);
+  const uint32_t nchunks = seg_chunk[nseg];
+  // one device block: chunk table, segment table, partials, h_pre, out,
+  // flag, then (host inputs) the elements
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t b_chunks = al(chunks.size() * 8 + 8), b_seg = al((nseg + 1) * 4), b_part = al((size_t)NV * nchunks * 32 + 32),
+               b_pre = al((size_t)nseg * 32), b_out = al((size_t)NV * nseg * 32),
+               b_flag = al(4 + (size_t)nchunks * 4);
+  const size_t b_in = on_device ? 0 : al((size_t)n * 32) * (pair ? 2 : 1);
+  DevBuf buf;
+  buf.st = st;
+  ACK(cudaMallocAsync(&buf.p, b_chunks + b_seg + b_part + b_pre + b_out + b_flag + b_in, st), "cudaMallocAsync");
+  uint8_t* base = (uint8_t*)buf.p;
+  uint64_t* d_chunks = (uint64_t*)base;
+  uint32_t* d_seg = (uint32_t*)(base + b_chunks);
+  uint32_t* d_part = (uint32_t*)(base + b_chunks + b_seg);
+  uint32_t* d_pre = (uint32_t*)(base + b_chunks + b_seg + b_part);
+  uint32_t* d_out = (uint32_t*)(base + b_chunks + b_seg + b_part + b_pre);
+  uint32_t* d_flag = (uint32_t*)(base + b_chunks + b_seg + b_part + b_pre + b_out);
+  uint8_t* d_in = base + b_chunks + b_seg + b_part + b_pre + b_out + b_flag;
+  const uint8_t* da = a;
+  const uint8_t* ds = s;
+  if (!on_device && n) {
+    ACK(cudaMemcpyAsync(d_in, a, (size_t)n * 32, cudaMemcpyHostToDevice, st), "copy in");
+    da = d_in;
+    if (pair) {
+      ACK(cudaMemcpyAsync(d_in + al((size_t)n * 32), s, (size_t)n * 32, cudaMemcpyHostToDevice, st), "copy in");
+      ds = d_in + al((size_t)n * 32);
+    }
+  }
+  if (!chunks.empty())
+    ACK(cudaMemcpyAsync(d_chunks, chunks.data(), chunks.size() * 8, cudaMemcpyHostToDevice, st), "copy in");
+  ACK(cudaMemcpyAsync(d_seg, seg_chunk.data(), (nseg + 1) * 4, cudaMemcpyHostToDevice, st), "copy in");
+  if (h_pre) ACK(cudaMemcpyAsync(d_pre, h_pre, (size_t)nseg * 32, cudaMemcpyHostToDevice, st), "copy in");
+  uint32_t* d_unord = d_flag + 1;
+  ACK(cudaMemsetAsync(d_flag, 0, 4, st), "memset");
+  if (nchunks) {
+    static int per_sm[2] = {0, 0};
+    int& occ = per_sm[pair];
+    if (occ == 0) {
+      int k = 0;
+      cudaError_t e = pair ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, k_assoc_chunks<true>, kAssocBD, 0)
+                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, k_assoc_chunks<false>, kAssocBD, 0);
+      occ = (e == cudaSuccess && k > 0) ? k : 1;
+    }
+    const unsigned grid = (unsigned)std::min<uint64_t>(nchunks, (uint64_t)kSMs * occ);
+    const long prof = prof_begin(pair ? kProfAssocPair : kProfAssocHash, (double)n * NV, st);
+    if (pair)
+      k_assoc_chunks<true><<<grid, kAssocBD, 0, st>>>((const uint32_t*)da, (const uint32_t*)ds, d_chunks, nchunks,
+                                                      d_part, d_unord, d_flag);
+    else
+      k_assoc_chunks<false><<<grid, kAssocBD, 0, st>>>((const uint32_t*)da, nullptr, d_chunks, nchunks, d_part,
+                                                       nullptr, d_flag);
+    prof_end(prof, st);
+    int rc = post_launch();
+    if (rc) return cuda_err((cudaError_t)rc, "associative hash");
+  }
+  const uint32_t warps = nseg * NV;
+  k_assoc_finish<<<(warps * 32 + 255) / 256, 256, 0, st>>>(d_part, d_seg, nseg, NV, h_pre ? d_pre : nullptr, d_out,
+                                                            d_flag);
+  int rc = post_launch();
+  if (rc) return cuda_err((cudaError_t)rc, "associative hash");
+  ACK(cudaMemcpyAsync(out, d_out, (size_t)NV * nseg * 32, cudaMemcpyDeviceToHost, st), "copy out");
+  ACK(cudaMemcpyAsync(host_flag, d_flag, 4, cudaMemcpyDeviceToHost, st), "copy out");
+  std::vector<uint32_t> unord(pair ? nchunks : 0);
+  if (pair && nchunks)
+    ACK(cudaMemcpyAsync(unord.data(), d_unord, (size_t)nchunks * 4, cudaMemcpyDeviceToHost, st), "copy out");
+  ACK(cudaStreamSynchronize(st), "associative hash");
+  if (pair)
+    for (uint32_t g = 0; g < nseg; ++g) {
+      seg_unordered[g] = 0;
+      for (uint32_t k = seg_chunk[g]; k < seg_chunk[g + 1]; ++k) seg_unordered[g] |= (int)unord[k];
+    }
+  return SISU_OK;
+}
+
+int check_elems(const uint8_t* p, uint64_t n, int on_device) {
+  if (n && !p) return report_error(SISU_ERR_INVALID_ARG, "NULL element array");
+  if (on_device && n && ((uintptr_t)p & 15))
+    return report_error(SISU_ERR_INVALID_ARG, "device element arrays must be 16-byte aligned");
+  return SISU_OK;
+}
+
+}  // namespace
+}  // namespace sisu
+
+using namespace sisu;
+
+extern "C" int sisu_assoc_hash_segments(const uint8_t* elems, const uint64_t* offsets, uint32_t n_segments,
+                                        const uint8_t* h_pre, int on_device, void* stream, uint8_t* out) {
+  if (!offsets || !out || n_segments == 0) return report_error(SISU_ERR_INVALID_ARG, "NULL offsets/out or no segment");
+  if (offsets[0] != 0) return report_error(SISU_ERR_INVALID_ARG, "offsets[0] must be 0");
+  for (uint32_t g = 0; g < n_segments; ++g)
+    if (offsets[g + 1] < offsets[g]) return report_error(SISU_ERR_INVALID_ARG, "offsets must not decrease");
+  int rc = check_elems(elems, offsets[n_segments], on_device);
+  if (rc) return rc;
+  uint32_t flag = 0;
+  rc = assoc_run(elems, nullptr, false, offsets, n_segments, h_pre, on_device, (cudaStream_t)stream, out, &flag,
+                 nullptr);
+  if (rc) return rc;
+  if (flag & kAssocNotCanonical) return report_error(SISU_ERR_NOT_CANONICAL, "an element or h_pre is not below r");
+  return SISU_OK;
+}
+
+extern "C" int sisu_assoc_hash(const uint8_t* elems, uint64_t n, const uint8_t* h_pre, int on_device, void* stream,
+                               uint8_t* out) {
+  const uint64_t offsets[2] = {0, n};
+  return sisu_assoc_hash_segments(elems, offsets, 1, h_pre, on_device, stream, out);
+}
+
+extern "C" int sisu_pairwise_distinct_check_segments(const uint8_t* a, const uint8_t* a_sorted,
+                                                     const uint64_t* offsets, uint32_t n_segments, int on_device,
+                                                     void* stream, int* results, uint8_t* h_a, uint8_t* h_sorted) {
+  if (!offsets || !results || n_segments == 0)
+    return report_error(SISU_ERR_INVALID_ARG, "NULL offsets/results or no segment");
+  if (offsets[0] != 0) return report_error(SISU_ERR_INVALID_ARG, "offsets[0] must be 0");
+  for (uint32_t g = 0; g < n_segments; ++g)
+    if (offsets[g + 1] < offsets[g]) return report_error(SISU_ERR_INVALID_ARG, "offsets must not decrease");
+  int rc = check_elems(a, offsets[n_segments], on_device);
+  if (!rc) rc = check_elems(a_sorted, offsets[n_segments], on_device);
+  if (rc) return rc;
+  std::vector<uint8_t> h((size_t)64 * n_segments);
+  std::vector<int> unord(n_segments);
+  uint32_t flag = 0;
+  rc = assoc_run(a, a_sorted, true, offsets, n_segments, nullptr, on_device, (cudaStream_t)stream, h.data(), &flag,
+                 unord.data());
+  if (rc) return rc;
+  if (flag & kAssocNotCanonical) return report_error(SISU_ERR_NOT_CANONICAL, "an element is not below r");
+  for (uint32_t g = 0; g < n_segments; ++g) {
+    const uint8_t* hg = h.data() + 64 * (size_t)g;
+    if (h_a) memcpy(h_a + 32 * (size_t)g, hg, 32);
+    if (h_sorted) memcpy(h_sorted + 32 * (size_t)g, hg + 32, 32);
+    results[g] = (memcmp(hg, hg + 32, 32) == 0 && !unord[g]) ? 1 : 0;
+  }
+  return SISU_OK;
+}
+
+extern "C" int sisu_pairwise_distinct_check(const uint8_t* a, const uint8_t* a_sorted, uint64_t n, int on_device,
+                                            void* stream, int* result, uint8_t* h_a, uint8_t* h_sorted) {
+  const uint64_t offsets[2] = {0, n};
+  return sisu_pairwise_distinct_check_segments(a, a_sorted, offsets, 1, on_device, stream, result, h_a, h_sorted);
+}

@@ -79,6 +79,11 @@ struct HostCircuit {
 // kernel launch wrappers (kernels.cu); all return cudaError_t as int
 
 uint64_t launches_add(uint64_t n);
+// per-kernel event timing (sisu_profile_enable): the index of the record
+// opened for a launch of `kind` (-1 when the kind is off), closed after it
+long prof_begin(uint32_t kind, double work, void* stream);
+void prof_end(long idx, void* stream);
+constexpr uint32_t kProfAssocHash = 9, kProfAssocPair = 10;
 // sets the calling thread's sisu_last_error() message, returns code
 int report_error(int code, const char* msg);
 

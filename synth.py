@@ -286,6 +286,26 @@ def accumulation_circuit(seed: int, n_copies: int, widths, max_entries: int = 4,
                    outs=outs)
 
 
+def validator_indexes(seed: int, n: int, log_universe: int) -> np.ndarray:
+    """n distinct validator indexes below 2^log_universe (n <= 2^log_universe)
+    in a seeded order, as field elements uint64[n, 4].
+
+    The inputs of the associative hash and of the pairwise-distinct check
+    (Sec. 3.4.1 and 3.4.2) are validator indexes, each below the number of
+    active validators, distinct within an epoch.  Index j is
+    (a j + b) mod 2^log_universe with a odd and b drawn from the stream
+    (seed, b"idx", 0): a bijection, so the n indexes are distinct."""
+    assert 0 <= n <= (1 << log_universe) and log_universe <= 62
+    w = splitmix_words(np.array([stream_seed(seed, b"idx", 0)], dtype=np.uint64), 0, 2)[0]
+    mask = np.uint64((1 << log_universe) - 1)
+    a, b = (w[0] | np.uint64(1)) & mask | np.uint64(1), w[1] & mask
+    j = np.arange(n, dtype=np.uint64)
+    out = np.zeros((n, 4), dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        out[:, 0] = (a * j + b) & mask
+    return out
+
+
 def fr_bytes(elems: np.ndarray) -> bytes:
     """Canonical little-endian bytes of a uint64[..., 4] element array."""
     return np.ascontiguousarray(elems, dtype="<u8").tobytes()
