@@ -336,9 +336,10 @@ def run_ours(args):
 
 ASSOC_METRIC = "validator indexes/s (associative hash of every slot + pairwise-distinct check of every epoch)"
 ASSOC_UNIT = "indexes/s"
-# multiply-adds per evaluation of F: six Montgomery products and one
-# fixed-multiplier product (82 mad.lo + 80 mad.hi) for e -> e R
-IMAD_PER_F = 6 * IMAD_PER_FR_MUL + 162
+# multiply-adds per evaluation of F on a validator index (below 2^32): six
+# Montgomery products and the one-row fixed-multiplier product for e -> e R
+# (8 mad.lo + 8 mad.hi for the row, 9 + 9 for the two reduction steps)
+IMAD_PER_F = 6 * IMAD_PER_FR_MUL + 34
 ASSOC_EPOCHS, ASSOC_EPOCH, ASSOC_SLOT, ASSOC_LOG_UNIVERSE = 64, 1 << 20, 1 << 15, 21
 
 
@@ -462,8 +463,8 @@ def run_assoc(args):
         step(da, ds)
     torch.cuda.synchronize(dev)
     kern = {}
-    for kind, name in ((S.PROF_ASSOC_HASH, "k_assoc_chunks<false> (slot hashes)"),
-                       (S.PROF_ASSOC_PAIR, "k_assoc_chunks<true> (pairwise-distinct check)")):
+    for kind, name in ((S.PROF_ASSOC_HASH, "k_assoc_chunks (slot hashes)"),
+                       (S.PROF_ASSOC_PAIR, "pairwise-distinct check (k_assoc_chunks on A and A*, k_order_chunks)")):
         kms, kn, kf = S.profile_read(kind)
         kern[name] = (kms, kn, kf)
     S.profile_enable(0)

@@ -49,9 +49,19 @@ __device__ __forceinline__ void assoc_consts(uint32_t* shK, Fr* sh_c) {
   __syncthreads();
 }
 
-// F(e) in Montgomery form for a canonical e
-__device__ __forceinline__ Fr assoc_F(const Fr& e, const uint32_t* K, const Fr& c) {
-  const Fr a = fr_add(fr_mul_fixed(e, K), c);  // (e + 2^32 - 1) R
+// e R for a canonical e below 2^32 (a validator index): the one nonzero
+// limb's row of the fixed-multiplier product (16 multiply-adds and the
+// two-word reduction instead of eight rows)
+__device__ __forceinline__ Fr fr_mul_fixed_u32(uint32_t d0, const uint32_t* K8) {
+  Fr d = fr_zero();
+  d.v[0] = d0;
+  return fr_mul_fixed_rows<1>(d, K8);
+}
+
+// F(e) in Montgomery form for a canonical e; `small`: e < 2^32
+__device__ __forceinline__ Fr assoc_F(const Fr& e, bool small, const uint32_t* K, const Fr& c) {
+  const Fr eR = small ? fr_mul_fixed_u32(e.v[0], K) : fr_mul_fixed(e, K);
+  const Fr a = fr_add(eR, c);  // (e + 2^32 - 1) R
   Fr r = fr_mul(fr_mul(a, a), a);
   Fr t = fr_add(r, a);
   r = fr_mul(fr_mul(t, t), t);
@@ -83,54 +93,53 @@ __device__ __forceinline__ void assoc_block_sum(Fr (&v)[NV]) {
   __syncthreads();
 }
 
-// Sums of F over chunk k = elements [chunks[3k], chunks[3k+1]) of `a` (and,
-// with kPair, of `s`) into partials[NV k + t].  With kPair, unordered[k] = 1
-// when some element i of the chunk, other than the first of its segment
-// (chunks[3k+2]), is not above element i - 1 of `s`.
-template <bool kPair>
+// Sum of F over chunk k = elements [chunks[3k], chunks[3k+1]) of `a` into
+// partials[stride k + off].  A warp whose elements are all below 2^32 (the
+// validator indexes of Sec. 3.4.2) converts them with the one-row product.
 __global__ void __launch_bounds__(kAssocBD, 2) k_assoc_chunks(const uint32_t* __restrict__ a,
-                                                          const uint32_t* __restrict__ s,
                                                           const uint64_t* __restrict__ chunks, uint32_t nchunks,
-                                                          uint32_t* __restrict__ partials,
-                                                          uint32_t* __restrict__ unordered, uint32_t* flag) {
-  constexpr int NV = kPair ? 2 : 1;
+                                                          uint32_t* __restrict__ partials, uint32_t stride,
+                                                          uint32_t off, uint32_t* flag) {
   __shared__ __align__(16) uint32_t shK[64];
   __shared__ Fr sh_c;
   assoc_consts(shK, &sh_c);
   const Fr c = sh_c;
   uint32_t err = 0;
   for (uint32_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-    const uint64_t b = chunks[3 * (size_t)ch], e = chunks[3 * (size_t)ch + 1], sb = chunks[3 * (size_t)ch + 2];
-    bool unord = false;
-    Fr acc[NV];
-#pragma unroll
-    for (int t = 0; t < NV; ++t) acc[t] = fr_zero();
-    for (uint64_t i = b + threadIdx.x; i < e; i += kAssocBD) {
-      Fr x = fr_load(a, i);
+    const uint64_t b = chunks[3 * (size_t)ch], e = chunks[3 * (size_t)ch + 1];
+    Fr acc = fr_zero();
+    for (uint64_t i0 = b; i0 < e; i0 += kAssocBD) {  // uniform trip count over the block
+      const uint64_t i = i0 + threadIdx.x;
+      const bool in = i < e;
+      Fr x = in ? fr_load(a, i) : fr_zero();
       if (!fr_lt_modulus(x)) {
         err |= kAssocNotCanonical;
         x = fr_zero();
       }
-      acc[0] = fr_add(acc[0], assoc_F(x, shK, c));
-      if (kPair) {
-        Fr y = fr_load(s, i);
-        if (!fr_lt_modulus(y)) {
-          err |= kAssocNotCanonical;
-          y = fr_zero();
-        }
-        acc[NV - 1] = fr_add(acc[NV - 1], assoc_F(y, shK, c));
-        if (i > sb && !u256_gt(y, fr_load(s, i - 1))) unord = true;
-      }
+      const bool small = __all_sync(0xffffffffu, (x.v[1] | x.v[2] | x.v[3] | x.v[4] | x.v[5] | x.v[6] | x.v[7]) == 0);
+      const Fr f = assoc_F(x, small, shK, c);
+      if (in) acc = fr_add(acc, f);
     }
-    if (kPair) unord = __syncthreads_or(unord);
-    assoc_block_sum<NV>(acc);
-    if (threadIdx.x == 0) {
-#pragma unroll
-      for (int t = 0; t < NV; ++t) fr_store(partials, (size_t)NV * ch + t, acc[t]);
-      if (kPair) unordered[ch] = unord ? 1u : 0u;
-    }
+    Fr v[1] = {acc};
+    assoc_block_sum<1>(v);
+    if (threadIdx.x == 0) fr_store(partials, (size_t)stride * ch + off, v[0]);
   }
   if (err) atomicOr(flag, err);
+}
+
+// unordered[k] = 1 when some element i of chunk k, other than the first of
+// its segment (chunks[3k+2]), is not above element i - 1 (as integers)
+__global__ void __launch_bounds__(kAssocBD) k_order_chunks(const uint32_t* __restrict__ s,
+                                                          const uint64_t* __restrict__ chunks, uint32_t nchunks,
+                                                          uint32_t* __restrict__ unordered) {
+  for (uint32_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    const uint64_t b = chunks[3 * (size_t)ch], e = chunks[3 * (size_t)ch + 1], sb = chunks[3 * (size_t)ch + 2];
+    bool bad = false;
+    for (uint64_t i = b + threadIdx.x; i < e; i += kAssocBD)
+      if (i > sb && !u256_gt(fr_load(s, i), fr_load(s, i - 1))) bad = true;
+    bad = __syncthreads_or(bad);
+    if (threadIdx.x == 0) unordered[ch] = bad ? 1u : 0u;
+  }
 }
 
 // out[NV g + t] = canonical(h_pre[g] + sum of the chunk sums of segment g),
@@ -235,24 +244,26 @@ int assoc_run(const uint8_t* a, const uint8_t* s, bool pair, const uint64_t* off
   uint32_t* d_unord = d_flag + 1;
   ACK(cudaMemsetAsync(d_flag, 0, 4, st), "memset");
   if (nchunks) {
-    static int per_sm[2] = {0, 0};
-    int& occ = per_sm[pair];
+    static int occ = 0;
     if (occ == 0) {
       int k = 0;
-      cudaError_t e = pair ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, k_assoc_chunks<true>, kAssocBD, 0)
-                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, k_assoc_chunks<false>, kAssocBD, 0);
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, k_assoc_chunks, kAssocBD, 0);
       occ = (e == cudaSuccess && k > 0) ? k : 1;
     }
     const unsigned grid = (unsigned)std::min<uint64_t>(nchunks, (uint64_t)kSMs * occ);
     const long prof = prof_begin(pair ? kProfAssocPair : kProfAssocHash, (double)n * NV, st);
-    if (pair)
-      k_assoc_chunks<true><<<grid, kAssocBD, 0, st>>>((const uint32_t*)da, (const uint32_t*)ds, d_chunks, nchunks,
-                                                      d_part, d_unord, d_flag);
-    else
-      k_assoc_chunks<false><<<grid, kAssocBD, 0, st>>>((const uint32_t*)da, nullptr, d_chunks, nchunks, d_part,
-                                                       nullptr, d_flag);
-    prof_end(prof, st);
+    k_assoc_chunks<<<grid, kAssocBD, 0, st>>>((const uint32_t*)da, d_chunks, nchunks, d_part, NV, 0, d_flag);
     int rc = post_launch();
+    if (!rc && pair) {
+      k_assoc_chunks<<<grid, kAssocBD, 0, st>>>((const uint32_t*)ds, d_chunks, nchunks, d_part, NV, 1, d_flag);
+      rc = post_launch();
+      if (!rc) {
+        k_order_chunks<<<(unsigned)std::min<uint64_t>(nchunks, (uint64_t)kSMs * 8), kAssocBD, 0, st>>>(
+            (const uint32_t*)ds, d_chunks, nchunks, d_unord);
+        rc = post_launch();
+      }
+    }
+    prof_end(prof, st);
     if (rc) return cuda_err((cudaError_t)rc, "associative hash");
   }
   const uint32_t warps = nseg * NV;

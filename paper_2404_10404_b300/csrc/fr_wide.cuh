@@ -580,13 +580,15 @@ __device__ __forceinline__ Fr fr_coeff_load(const uint32_t* K8, int i) {
 }
 
 // d rho (Montgomery forms, d < 2p) given the coefficients K_0..K_7 of
-// fr_fixed_coeff as 64 words (16-byte aligned)
-__device__ __forceinline__ Fr fr_mul_fixed(const Fr& d, const uint32_t* K8) {
+// fr_fixed_coeff as 64 words (16-byte aligned); only the rows of the first
+// kRows limbs of d are summed (the others must be zero)
+template <int kRows>
+__device__ __forceinline__ Fr fr_mul_fixed_rows(const Fr& d, const uint32_t* K8) {
   uint32_t a[10];
 #pragma unroll
   for (int i = 0; i < 10; ++i) a[i] = 0;
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
+  for (int i = 0; i < kRows; ++i) {
     const Fr K = fr_coeff_load(K8, i);
     const uint32_t di = d.v[i];
     asm("mad.lo.cc.u32  %0, %11, %10, %0;\n\t"
@@ -663,6 +665,8 @@ __device__ __forceinline__ Fr fr_mul_fixed(const Fr& d, const uint32_t* K8) {
   for (int i = 0; i < 8; ++i) o.v[i] = a[2 + i];
   return o;
 }
+
+__device__ __forceinline__ Fr fr_mul_fixed(const Fr& d, const uint32_t* K8) { return fr_mul_fixed_rows<8>(d, K8); }
 
 #endif  // __CUDACC__
 }  // namespace sisu
