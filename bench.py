@@ -404,7 +404,7 @@ def run_assoc(args):
     torch.cuda.set_device(0)
     build()
     dev = torch.device("cuda", 0)
-    epochs = ASSOC_EPOCHS
+    epochs = args.epochs
     n = epochs * ASSOC_EPOCH
     t0 = time.time()
     a, s = assoc_inputs(epochs)
@@ -489,7 +489,7 @@ def run_assoc(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": assoc_describe(epochs), "indexes_per_step": n,
                        "slots_per_step": len(slot_offs) - 1, "epochs_per_step": epochs,
-                       "l2": "inputs larger than L2: 2 GiB of indexes and 2 GiB of sorted indexes"},
+                       "l2": f"inputs larger than L2: {n * 32 / 2**30:.2f} GiB of indexes and as much sorted"},
             "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
             "parity": {"oracle_and_definition": bool(ok)}}
     if not args.no_cpu_baseline:
@@ -706,6 +706,7 @@ def main():
     ap.add_argument("--instances", type=int, default=64, help="batched: number of instances")
     ap.add_argument("--budget-gb", type=float, default=150.0, help="batched: device memory per wave")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--epochs", type=int, default=ASSOC_EPOCHS, help="assoc: epochs of 2^20 indexes per step")
     ap.add_argument("--depth", type=int, default=None,
                     help="keep only the workload's first layers (profiler captures)")
     args = ap.parse_args()

@@ -10,8 +10,9 @@
 //
 // Work layout: the elements of all segments (sub-lists hashed separately,
 // the paper's M sub-circuits) form one array of 32-byte canonical values.
-// The host cuts every segment into chunks of equal size; one CTA sums F over
-// a chunk (threads stride the chunk, so a warp reads 1 KB contiguous per
+// The host cuts every segment into chunks of 8192 elements; a resident
+// wave of CTAs takes the chunks in order from an atomic counter and sums F
+// over each (threads stride the chunk, so a warp reads 1 KB contiguous per
 // step), and a second launch adds each segment's chunk sums, one warp per
 // segment.  F costs one fixed-multiplier product (e R from the canonical
 // e) and six Montgomery products; the path is bound by the integer
@@ -31,6 +32,7 @@
 namespace sisu {
 
 constexpr int kAssocBD = 256;
+constexpr uint64_t kAssocChunk = 8192;
 constexpr uint32_t kAssocAdd = 4294967295u;  // 2^32 - 1, added every round of Algorithm 1
 
 // device error word bits
@@ -94,18 +96,26 @@ __device__ __forceinline__ void assoc_block_sum(Fr (&v)[NV]) {
 }
 
 // Sum of F over chunk k = elements [chunks[3k], chunks[3k+1]) of `a` into
-// partials[stride k + off].  A warp whose elements are all below 2^32 (the
+// partials[stride k + off].  CTAs take chunks in order from the counter
+// *next (zero at launch), so uneven segments leave no CTA with a whole
+// chunk more than another.  A warp whose elements are all below 2^32 (the
 // validator indexes of Sec. 3.4.2) converts them with the one-row product.
 __global__ void __launch_bounds__(kAssocBD, 2) k_assoc_chunks(const uint32_t* __restrict__ a,
                                                           const uint64_t* __restrict__ chunks, uint32_t nchunks,
                                                           uint32_t* __restrict__ partials, uint32_t stride,
-                                                          uint32_t off, uint32_t* flag) {
+                                                          uint32_t off, uint32_t* next, uint32_t* flag) {
   __shared__ __align__(16) uint32_t shK[64];
   __shared__ Fr sh_c;
+  __shared__ uint32_t sh_ch;
   assoc_consts(shK, &sh_c);
   const Fr c = sh_c;
   uint32_t err = 0;
-  for (uint32_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+  for (;;) {
+    if (threadIdx.x == 0) sh_ch = atomicAdd(next, 1u);
+    __syncthreads();
+    const uint32_t ch = sh_ch;
+    __syncthreads();  // every thread has read sh_ch before thread 0 takes the next chunk
+    if (ch >= nchunks) break;
     const uint64_t b = chunks[3 * (size_t)ch], e = chunks[3 * (size_t)ch + 1];
     Fr acc = fr_zero();
     for (uint64_t i0 = b; i0 < e; i0 += kAssocBD) {  // uniform trip count over the block
@@ -193,10 +203,9 @@ int assoc_run(const uint8_t* a, const uint8_t* s, bool pair, const uint64_t* off
               int* seg_unordered) {
   const int NV = pair ? 2 : 1;
   const uint64_t n = offsets[nseg];
-  // chunks: about eight per SM over the whole array, at least 4096 elements,
-  // a multiple of the CTA width, each inside one segment
-  uint64_t ch = std::max<uint64_t>(4096, (n + 8 * kSMs - 1) / (8 * kSMs));
-  ch = (ch + kAssocBD - 1) / kAssocBD * kAssocBD;
+  // chunks of 8192 elements (32 a thread), each inside one segment, taken
+  // in order by the CTAs
+  const uint64_t ch = kAssocChunk;
   std::vector<uint64_t> chunks;
   std::vector<uint32_t> seg_chunk(nseg + 1);
   for (uint32_t g = 0; g < nseg; ++g) {
@@ -214,7 +223,7 @@ int assoc_run(const uint8_t* a, const uint8_t* s, bool pair, const uint64_t* off
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t b_chunks = al(chunks.size() * 8 + 8), b_seg = al((nseg + 1) * 4), b_part = al((size_t)NV * nchunks * 32 + 32),
                b_pre = al((size_t)nseg * 32), b_out = al((size_t)NV * nseg * 32),
-               b_flag = al(4 + (size_t)nchunks * 4);
+               b_flag = al(12 + (size_t)nchunks * 4);
   const size_t b_in = on_device ? 0 : al((size_t)n * 32) * (pair ? 2 : 1);
   DevBuf buf;
   buf.st = st;
@@ -241,8 +250,9 @@ int assoc_run(const uint8_t* a, const uint8_t* s, bool pair, const uint64_t* off
     ACK(cudaMemcpyAsync(d_chunks, chunks.data(), chunks.size() * 8, cudaMemcpyHostToDevice, st), "copy in");
   ACK(cudaMemcpyAsync(d_seg, seg_chunk.data(), (nseg + 1) * 4, cudaMemcpyHostToDevice, st), "copy in");
   if (h_pre) ACK(cudaMemcpyAsync(d_pre, h_pre, (size_t)nseg * 32, cudaMemcpyHostToDevice, st), "copy in");
-  uint32_t* d_unord = d_flag + 1;
-  ACK(cudaMemsetAsync(d_flag, 0, 4, st), "memset");
+  uint32_t* d_next = d_flag + 1;  // two chunk counters
+  uint32_t* d_unord = d_flag + 3;
+  ACK(cudaMemsetAsync(d_flag, 0, 12, st), "memset");
   if (nchunks) {
     static int occ = 0;
     if (occ == 0) {
@@ -252,10 +262,11 @@ int assoc_run(const uint8_t* a, const uint8_t* s, bool pair, const uint64_t* off
     }
     const unsigned grid = (unsigned)std::min<uint64_t>(nchunks, (uint64_t)kSMs * occ);
     const long prof = prof_begin(pair ? kProfAssocPair : kProfAssocHash, (double)n * NV, st);
-    k_assoc_chunks<<<grid, kAssocBD, 0, st>>>((const uint32_t*)da, d_chunks, nchunks, d_part, NV, 0, d_flag);
+    k_assoc_chunks<<<grid, kAssocBD, 0, st>>>((const uint32_t*)da, d_chunks, nchunks, d_part, NV, 0, d_next, d_flag);
     int rc = post_launch();
     if (!rc && pair) {
-      k_assoc_chunks<<<grid, kAssocBD, 0, st>>>((const uint32_t*)ds, d_chunks, nchunks, d_part, NV, 1, d_flag);
+      k_assoc_chunks<<<grid, kAssocBD, 0, st>>>((const uint32_t*)ds, d_chunks, nchunks, d_part, NV, 1, d_next + 1,
+                                                d_flag);
       rc = post_launch();
       if (!rc) {
         k_order_chunks<<<(unsigned)std::min<uint64_t>(nchunks, (uint64_t)kSMs * 8), kAssocBD, 0, st>>>(
