@@ -336,10 +336,11 @@ def run_ours(args):
 
 ASSOC_METRIC = "validator indexes/s (associative hash of every slot + pairwise-distinct check of every epoch)"
 ASSOC_UNIT = "indexes/s"
-# multiply-adds per evaluation of F on a validator index (below 2^32): six
-# Montgomery products and the one-row fixed-multiplier product for e -> e R
-# (8 mad.lo + 8 mad.hi for the row, 9 + 9 for the two reduction steps)
-IMAD_PER_F = 6 * IMAD_PER_FR_MUL + 34
+# multiply-adds per evaluation of F on a validator index (below 2^32): three
+# Montgomery squares (36 + 36 multiply halves for the square, 8 + 128 for the
+# reduction), three Montgomery products and the one-row fixed-multiplier
+# product for e -> e R (8 + 8 for the row, 9 + 9 for the two reduction steps)
+IMAD_PER_F = 3 * (72 + 136) + 3 * IMAD_PER_FR_MUL + 34
 ASSOC_EPOCHS, ASSOC_EPOCH, ASSOC_SLOT, ASSOC_LOG_UNIVERSE = 64, 1 << 20, 1 << 15, 21
 
 

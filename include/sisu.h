@@ -264,7 +264,11 @@ int sisu_pairwise_distinct_check_segments(const uint8_t* a, const uint8_t* a_sor
  * reduced dot product the copy-phase rounds use: full 512-bit products
  * summed exactly, one reduction per sum), 6 a[i]*b[0] (the product by
  * one fixed multiplier that folds a table by a challenge: eight 32x256-bit
- * rows and a two-word reduction).  b is ignored for op 3.  Errors: INVALID_ARG, NOT_CANONICAL, ZERO_INVERSE. */
+ * rows and a two-word reduction), 7 a^2 by the squaring routine (28
+ * doubled off-diagonal and 8 diagonal partial products, then the
+ * reduction), 8 the same square taken of the representative a R + r of a's
+ * Montgomery form (exercises inputs in [r, 2r)).  b is ignored for ops 3, 7
+ * and 8.  Errors: INVALID_ARG, NOT_CANONICAL, ZERO_INVERSE. */
 int sisu_fr_batch(int op, const uint8_t* a, const uint8_t* b, uint8_t* out, size_t n, void* stream);
 
 /* Merkle statement digest of device bytes (the transcript's digest of

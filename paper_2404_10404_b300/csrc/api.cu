@@ -1036,8 +1036,8 @@ extern "C" int sisu_gkr_verify(const sisu_circuit* circ, const uint8_t* inputs, 
 // field core, digests, microbenchmarks
 
 extern "C" int sisu_fr_batch(int op, const uint8_t* a, const uint8_t* b, uint8_t* out, size_t n, void* stream) {
-  if (op < 0 || op > 6) return fail(SISU_ERR_INVALID_ARG, "op %d", op);
-  if (!a || !out || (op != 3 && !b)) return fail(SISU_ERR_INVALID_ARG, "NULL operand");
+  if (op < 0 || op > 8) return fail(SISU_ERR_INVALID_ARG, "op %d", op);
+  if (!a || !out || (op != 3 && op != 7 && op != 8 && !b)) return fail(SISU_ERR_INVALID_ARG, "NULL operand");
   if (n == 0) return SISU_OK;
   if ((((uintptr_t)a | (uintptr_t)out | (uintptr_t)(b ? b : a)) & 15) != 0)
     return fail(SISU_ERR_INVALID_ARG, "device arrays must be 16-byte aligned");

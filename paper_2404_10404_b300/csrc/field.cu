@@ -18,6 +18,21 @@ __device__ __forceinline__ Fr fr_one_minus_f(const Fr& z) { return fr_sub(fr_one
 
 constexpr int kInvBatch = 8;
 
+// x + r as a plain 256-bit integer (x < r, so the sum is below 2r < 2^255):
+// the other representative of x in the lazily reduced range [0, 2r)
+__device__ __forceinline__ Fr fr_add_modulus(const Fr& x) {
+  const Fr m = fr_modulus();
+  Fr o;
+  uint64_t c = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    c += (uint64_t)x.v[i] + m.v[i];
+    o.v[i] = (uint32_t)c;
+    c >>= 32;
+  }
+  return o;
+}
+
 __global__ void k_fr_batch(int op, const uint32_t* __restrict__ a, const uint32_t* __restrict__ b,
                            uint32_t* __restrict__ out, size_t n, uint32_t* flags) {
   const size_t stride = (size_t)gridDim.x * blockDim.x;
@@ -38,6 +53,8 @@ __global__ void k_fr_batch(int op, const uint32_t* __restrict__ a, const uint32_
         case 1: z = fr_sub(x, y); break;
         case 2: z = fr_mul(x, y); break;
         case 4: z = fr_add(fr_mul(x, y), fr_mul(fr_one_minus_f(x), fr_one_minus_f(y))); break;
+        case 7: z = fr_sqr(x); break;
+        case 8: z = fr_sqr(fr_add_modulus(x)); break;  // the square of a lazy representative in [r, 2r)
         case 6: {  // a * b[0] by the fixed-multiplier product
           Fr b0 = fr_load(b, 0);
           if (!fr_lt_modulus(b0)) b0 = fr_zero();  // reported through element 0

@@ -292,7 +292,47 @@ static __device__ __noinline__ Fr fr_mul_call(Fr a, Fr b) { return fr_mul_inl(a,
 
 __device__ __forceinline__ Fr fr_mul(const Fr& a, const Fr& b) { return fr_mul_call(a, b); }
 
-__device__ __forceinline__ Fr fr_sqr(const Fr& a) { return fr_mul(a, a); }
+// Montgomery square a^2 2^-256 mod p, input and output in [0, 2p): the
+// 512-bit square from its 28 off-diagonal products (doubled) and 8
+// diagonal ones, then eight word-by-word Montgomery steps.  72 multiply
+// halves for the square where a general product takes 128; the bound
+// a^2 + m p < 4p^2 + 2^256 p < 2^511 keeps every carry inside 16 words and
+// the result below 2p (4p < 2^256).
+__device__ __forceinline__ Fr fr_sqr_inl(const Fr& a) {
+  uint32_t t[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) t[i] = 0;
+  asm("mad.lo.cc.u32 %0, %9, %10, %0;\n\t" "madc.lo.cc.u32 %1, %9, %11, %1;\n\t" "madc.lo.cc.u32 %2, %9, %12, %2;\n\t" "madc.lo.cc.u32 %3, %9, %13, %3;\n\t" "madc.lo.cc.u32 %4, %9, %14, %4;\n\t" "madc.lo.cc.u32 %5, %9, %15, %5;\n\t" "madc.lo.cc.u32 %6, %9, %16, %6;\n\t" "addc.cc.u32 %7, %7, 0;\n\t" "addc.u32 %8, %8, 0;\n\t" "mad.hi.cc.u32 %1, %9, %10, %1;\n\t" "madc.hi.cc.u32 %2, %9, %11, %2;\n\t" "madc.hi.cc.u32 %3, %9, %12, %3;\n\t" "madc.hi.cc.u32 %4, %9, %13, %4;\n\t" "madc.hi.cc.u32 %5, %9, %14, %5;\n\t" "madc.hi.cc.u32 %6, %9, %15, %6;\n\t" "madc.hi.cc.u32 %7, %9, %16, %7;\n\t" "addc.u32 %8, %8, 0;\n\t" : "+r"(t[1]), "+r"(t[2]), "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]), "+r"(t[7]), "+r"(t[8]), "+r"(t[9]) : "r"(a.v[0]), "r"(a.v[1]), "r"(a.v[2]), "r"(a.v[3]), "r"(a.v[4]), "r"(a.v[5]), "r"(a.v[6]), "r"(a.v[7]));
+  asm("mad.lo.cc.u32 %0, %8, %9, %0;\n\t" "madc.lo.cc.u32 %1, %8, %10, %1;\n\t" "madc.lo.cc.u32 %2, %8, %11, %2;\n\t" "madc.lo.cc.u32 %3, %8, %12, %3;\n\t" "madc.lo.cc.u32 %4, %8, %13, %4;\n\t" "madc.lo.cc.u32 %5, %8, %14, %5;\n\t" "addc.cc.u32 %6, %6, 0;\n\t" "addc.u32 %7, %7, 0;\n\t" "mad.hi.cc.u32 %1, %8, %9, %1;\n\t" "madc.hi.cc.u32 %2, %8, %10, %2;\n\t" "madc.hi.cc.u32 %3, %8, %11, %3;\n\t" "madc.hi.cc.u32 %4, %8, %12, %4;\n\t" "madc.hi.cc.u32 %5, %8, %13, %5;\n\t" "madc.hi.cc.u32 %6, %8, %14, %6;\n\t" "addc.u32 %7, %7, 0;\n\t" : "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]), "+r"(t[7]), "+r"(t[8]), "+r"(t[9]), "+r"(t[10]) : "r"(a.v[1]), "r"(a.v[2]), "r"(a.v[3]), "r"(a.v[4]), "r"(a.v[5]), "r"(a.v[6]), "r"(a.v[7]));
+  asm("mad.lo.cc.u32 %0, %7, %8, %0;\n\t" "madc.lo.cc.u32 %1, %7, %9, %1;\n\t" "madc.lo.cc.u32 %2, %7, %10, %2;\n\t" "madc.lo.cc.u32 %3, %7, %11, %3;\n\t" "madc.lo.cc.u32 %4, %7, %12, %4;\n\t" "addc.cc.u32 %5, %5, 0;\n\t" "addc.u32 %6, %6, 0;\n\t" "mad.hi.cc.u32 %1, %7, %8, %1;\n\t" "madc.hi.cc.u32 %2, %7, %9, %2;\n\t" "madc.hi.cc.u32 %3, %7, %10, %3;\n\t" "madc.hi.cc.u32 %4, %7, %11, %4;\n\t" "madc.hi.cc.u32 %5, %7, %12, %5;\n\t" "addc.u32 %6, %6, 0;\n\t" : "+r"(t[5]), "+r"(t[6]), "+r"(t[7]), "+r"(t[8]), "+r"(t[9]), "+r"(t[10]), "+r"(t[11]) : "r"(a.v[2]), "r"(a.v[3]), "r"(a.v[4]), "r"(a.v[5]), "r"(a.v[6]), "r"(a.v[7]));
+  asm("mad.lo.cc.u32 %0, %6, %7, %0;\n\t" "madc.lo.cc.u32 %1, %6, %8, %1;\n\t" "madc.lo.cc.u32 %2, %6, %9, %2;\n\t" "madc.lo.cc.u32 %3, %6, %10, %3;\n\t" "addc.cc.u32 %4, %4, 0;\n\t" "addc.u32 %5, %5, 0;\n\t" "mad.hi.cc.u32 %1, %6, %7, %1;\n\t" "madc.hi.cc.u32 %2, %6, %8, %2;\n\t" "madc.hi.cc.u32 %3, %6, %9, %3;\n\t" "madc.hi.cc.u32 %4, %6, %10, %4;\n\t" "addc.u32 %5, %5, 0;\n\t" : "+r"(t[7]), "+r"(t[8]), "+r"(t[9]), "+r"(t[10]), "+r"(t[11]), "+r"(t[12]) : "r"(a.v[3]), "r"(a.v[4]), "r"(a.v[5]), "r"(a.v[6]), "r"(a.v[7]));
+  asm("mad.lo.cc.u32 %0, %5, %6, %0;\n\t" "madc.lo.cc.u32 %1, %5, %7, %1;\n\t" "madc.lo.cc.u32 %2, %5, %8, %2;\n\t" "addc.cc.u32 %3, %3, 0;\n\t" "addc.u32 %4, %4, 0;\n\t" "mad.hi.cc.u32 %1, %5, %6, %1;\n\t" "madc.hi.cc.u32 %2, %5, %7, %2;\n\t" "madc.hi.cc.u32 %3, %5, %8, %3;\n\t" "addc.u32 %4, %4, 0;\n\t" : "+r"(t[9]), "+r"(t[10]), "+r"(t[11]), "+r"(t[12]), "+r"(t[13]) : "r"(a.v[4]), "r"(a.v[5]), "r"(a.v[6]), "r"(a.v[7]));
+  asm("mad.lo.cc.u32 %0, %4, %5, %0;\n\t" "madc.lo.cc.u32 %1, %4, %6, %1;\n\t" "addc.cc.u32 %2, %2, 0;\n\t" "addc.u32 %3, %3, 0;\n\t" "mad.hi.cc.u32 %1, %4, %5, %1;\n\t" "madc.hi.cc.u32 %2, %4, %6, %2;\n\t" "addc.u32 %3, %3, 0;\n\t" : "+r"(t[11]), "+r"(t[12]), "+r"(t[13]), "+r"(t[14]) : "r"(a.v[5]), "r"(a.v[6]), "r"(a.v[7]));
+  asm("mad.lo.cc.u32 %0, %3, %4, %0;\n\t" "addc.cc.u32 %1, %1, 0;\n\t" "addc.u32 %2, %2, 0;\n\t" "mad.hi.cc.u32 %1, %3, %4, %1;\n\t" "addc.u32 %2, %2, 0;\n\t" : "+r"(t[13]), "+r"(t[14]), "+r"(t[15]) : "r"(a.v[6]), "r"(a.v[7]));
+  // doubling, then the diagonal squares
+  asm("add.cc.u32 %0, %0, %0;\n\t" "addc.cc.u32 %1, %1, %1;\n\t" "addc.cc.u32 %2, %2, %2;\n\t" "addc.cc.u32 %3, %3, %3;\n\t" "addc.cc.u32 %4, %4, %4;\n\t" "addc.cc.u32 %5, %5, %5;\n\t" "addc.cc.u32 %6, %6, %6;\n\t" "addc.cc.u32 %7, %7, %7;\n\t" "addc.cc.u32 %8, %8, %8;\n\t" "addc.cc.u32 %9, %9, %9;\n\t" "addc.cc.u32 %10, %10, %10;\n\t" "addc.cc.u32 %11, %11, %11;\n\t" "addc.cc.u32 %12, %12, %12;\n\t" "addc.cc.u32 %13, %13, %13;\n\t" "addc.cc.u32 %14, %14, %14;\n\t" "addc.u32 %15, %15, %15;\n\t" : "+r"(t[0]), "+r"(t[1]), "+r"(t[2]), "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]), "+r"(t[7]), "+r"(t[8]), "+r"(t[9]), "+r"(t[10]), "+r"(t[11]), "+r"(t[12]), "+r"(t[13]), "+r"(t[14]), "+r"(t[15]));
+  asm("mad.lo.cc.u32 %0, %16, %16, %0;\n\t" "madc.hi.cc.u32 %1, %16, %16, %1;\n\t" "madc.lo.cc.u32 %2, %17, %17, %2;\n\t" "madc.hi.cc.u32 %3, %17, %17, %3;\n\t" "madc.lo.cc.u32 %4, %18, %18, %4;\n\t" "madc.hi.cc.u32 %5, %18, %18, %5;\n\t" "madc.lo.cc.u32 %6, %19, %19, %6;\n\t" "madc.hi.cc.u32 %7, %19, %19, %7;\n\t" "madc.lo.cc.u32 %8, %20, %20, %8;\n\t" "madc.hi.cc.u32 %9, %20, %20, %9;\n\t" "madc.lo.cc.u32 %10, %21, %21, %10;\n\t" "madc.hi.cc.u32 %11, %21, %21, %11;\n\t" "madc.lo.cc.u32 %12, %22, %22, %12;\n\t" "madc.hi.cc.u32 %13, %22, %22, %13;\n\t" "madc.lo.cc.u32 %14, %23, %23, %14;\n\t" "madc.hi.u32 %15, %23, %23, %15;\n\t" : "+r"(t[0]), "+r"(t[1]), "+r"(t[2]), "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]), "+r"(t[7]), "+r"(t[8]), "+r"(t[9]), "+r"(t[10]), "+r"(t[11]), "+r"(t[12]), "+r"(t[13]), "+r"(t[14]), "+r"(t[15]) : "r"(a.v[0]), "r"(a.v[1]), "r"(a.v[2]), "r"(a.v[3]), "r"(a.v[4]), "r"(a.v[5]), "r"(a.v[6]), "r"(a.v[7]));
+  // Montgomery steps: m = t_i (-p^-1) mod 2^32, t += m p 2^(32 i); the
+  // carry out of word i + 8 is held in cy and added into word i + 9 by the
+  // next step (at most 2, so no word overflows unseen)
+  uint32_t cy = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    asm("{\n\t" ".reg .u32 m;\n\t" "mul.lo.u32 m, %0, 0xefffffff;\n\t" "mad.lo.cc.u32 %0, m, 0xf0000001, %0;\n\t" "madc.lo.cc.u32 %1, m, 0x43e1f593, %1;\n\t" "madc.lo.cc.u32 %2, m, 0x79b97091, %2;\n\t" "madc.lo.cc.u32 %3, m, 0x2833e848, %3;\n\t" "madc.lo.cc.u32 %4, m, 0x8181585d, %4;\n\t" "madc.lo.cc.u32 %5, m, 0xb85045b6, %5;\n\t" "madc.lo.cc.u32 %6, m, 0xe131a029, %6;\n\t" "madc.lo.cc.u32 %7, m, 0x30644e72, %7;\n\t" "addc.cc.u32 %8, %8, %9;\n\t" "addc.u32 %9, %10, 0;\n\t" "mad.hi.cc.u32 %1, m, 0xf0000001, %1;\n\t" "madc.hi.cc.u32 %2, m, 0x43e1f593, %2;\n\t" "madc.hi.cc.u32 %3, m, 0x79b97091, %3;\n\t" "madc.hi.cc.u32 %4, m, 0x2833e848, %4;\n\t" "madc.hi.cc.u32 %5, m, 0x8181585d, %5;\n\t" "madc.hi.cc.u32 %6, m, 0xb85045b6, %6;\n\t" "madc.hi.cc.u32 %7, m, 0xe131a029, %7;\n\t" "madc.hi.cc.u32 %8, m, 0x30644e72, %8;\n\t" "addc.u32 %9, %9, 0;\n\t" "}"
+        : "+r"(t[i]), "+r"(t[i + 1]), "+r"(t[i + 2]), "+r"(t[i + 3]), "+r"(t[i + 4]), "+r"(t[i + 5]), "+r"(t[i + 6]),
+          "+r"(t[i + 7]), "+r"(t[i + 8]), "+r"(cy)
+        : "r"(0u));
+  }
+  Fr r;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) r.v[i] = t[8 + i];
+  return r;
+}
+
+// one out-of-line copy per translation unit, as for the product
+static __device__ __noinline__ Fr fr_sqr_call(Fr a) { return fr_sqr_inl(a); }
+
+__device__ __forceinline__ Fr fr_sqr(const Fr& a) { return fr_sqr_call(a); }
 
 // ---------------------------------------------------------------------------
 // comparisons and conversions

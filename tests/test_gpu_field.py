@@ -36,6 +36,16 @@ def test_ops_vs_python_ints(S, op, fn):
     assert _run(S, op, a, b) == [fn(x, y) for x, y in zip(a, b)]
 
 
+@pytest.mark.parametrize("op", [7, 8])
+def test_square_vs_python_ints(S, op):
+    """The squaring routine (op 7) and the same on the other representative
+    of each Montgomery form in [r, 2r) (op 8) against a^2 mod r."""
+    rng = random.Random(70 + op)
+    a = [rng.randrange(P) for _ in range(50000)] + EDGE + [P - k for k in range(1, 200)] + list(range(200))
+    a += [(1 << k) % P for k in range(256)] + [((1 << k) - 1) % P for k in range(1, 256)]
+    assert _run(S, op, a, a) == [x * x % P for x in a]
+
+
 def test_million_products_vs_oracle(S, oracle):
     import numpy as np
     rng = np.random.default_rng(12)
