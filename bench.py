@@ -342,6 +342,10 @@ ASSOC_UNIT = "indexes/s"
 # product for e -> e R (8 + 8 for the row, 9 + 9 for the two reduction steps)
 IMAD_PER_F = 3 * (72 + 136) + 3 * IMAD_PER_FR_MUL + 34
 ASSOC_EPOCHS, ASSOC_EPOCH, ASSOC_SLOT, ASSOC_LOG_UNIVERSE = 64, 1 << 20, 1 << 15, 21
+# DRAM read + write bytes per index of k_assoc_chunks (ncu capture of one
+# launch over 2^23 indexes, profiles/assoc_chunks_validator_indexes.md):
+# the 32-byte value read once plus the chunk tables and partial sums
+ASSOC_TRAFFIC_PER_INDEX = (268.550912e6 + 3.135488e6) / 2**23
 
 
 def assoc_inputs(epochs: int):
@@ -469,11 +473,15 @@ def run_assoc(args):
         kms, kn, kf = S.profile_read(kind)
         kern[name] = (kms, kn, kf)
     S.profile_enable(0)
-    dom = max(kern, key=lambda k: kern[k][0])
+    # the dominant kernel is k_assoc_chunks (three of the step's four
+    # launches); the slot-hash scope times exactly one launch of it
+    dom = "k_assoc_chunks (slot hashes)"
     kms, kn, kf = kern[dom]
     achieved = kf * IMAD_PER_F / (kms / 1e3) / 1e12
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": ALU_PEAK_TIMAD, "unit": "TIMAD/s",
-                "frac": achieved / ALU_PEAK_TIMAD, "traffic": None, "per_launch_ms": kms / kn, "launches_timed": kn,
+                "frac": achieved / ALU_PEAK_TIMAD, "traffic": ASSOC_TRAFFIC_PER_INDEX * kf / kn,
+                "traffic_source": "ncu dram bytes of one launch over 2^23 indexes, scaled to the launch's indexes",
+                "per_launch_ms": kms / kn, "launches_timed": kn,
                 "f_evaluations_per_launch": kf / kn, "imad_per_f": IMAD_PER_F,
                 "peak_source": "derived: 148 SMs x 64 IMAD/clk x 2032 MHz",
                 "kernels_ms_per_step": {k: round(v[0] / v[1], 4) for k, v in kern.items()}}
