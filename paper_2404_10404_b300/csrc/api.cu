@@ -628,7 +628,7 @@ extern "C" void sisu_transcript_destroy(sisu_transcript* tr) { delete tr; }
 // ---------------------------------------------------------------------------
 // proving
 
-constexpr int kWsRegions = 13;
+constexpr int kWsRegions = 14;
 
 static void workspace_sizes(const sisu_circuit* cc, size_t sizes[kWsRegions]) {
   const HostCircuit& hc = cc->hc;
@@ -646,7 +646,7 @@ static void workspace_sizes(const sisu_circuit* cc, size_t sizes[kWsRegions]) {
   const size_t v[kWsRegions] = {half, (size_t)hc.C * 32, (size_t)nmax * 32, (size_t)wmax_next * 32,
                                 (size_t)wmax_next * 32, (size_t)wmax_next * 32, (size_t)wmax_next * 32,
                                 (size_t)wmax * 32, (size_t)kMaxPartials * 4 * 32, dig, sizeof(DevState),
-                                hc.proof_len(), eq_half_words(hc.c, smax) * 4};
+                                hc.proof_len(), eq_half_words(hc.c, smax) * 4, (size_t)nmax * 2 * 32};
   for (int k = 0; k < kWsRegions; ++k) sizes[k] = v[k];
 }
 
@@ -686,6 +686,7 @@ static int workspace_init(sisu_eval* ev, Workspace* ws, uint8_t* dev, uint8_t* h
   ws->S = (DevState*)ptrs[10];
   ws->proof = (uint8_t*)ptrs[11];
   ws->eqh = (uint32_t*)ptrs[12];
+  ws->P = (uint32_t*)ptrs[13];
   ws->proof_len = hc.proof_len();
   ws->host = host;
   // the proof header is fixed by the circuit
@@ -796,7 +797,7 @@ static int enqueue_prove(const sisu_circuit* cc, sisu_eval* ev, const sisu_trans
       TailParams tp;
       tp.A = A; tp.E = w.E; tp.om = w.om; tp.sg = L.sgate;
       tp.off1 = L.off1; tp.pos1 = L.pos1; tp.off2 = L.off2; tp.pos2 = L.pos2;
-      tp.nmul = L.nmul; tp.Wn = Wn; tp.s = s;
+      tp.nmul = L.nmul; tp.ntot = L.ntot; tp.Wn = Wn; tp.s = s; tp.P = w.P;
       tp.At = w.At; tp.H1 = w.H1; tp.H2 = w.H2; tp.Ay = w.Ay;
       tp.S = w.S; tp.proof = w.proof; tp.offx = offx; tp.offy = offy; tp.offv = offv; tp.last = i + 1 == d;
       ProfScope ps(kProfGateRound, (double)Wn * (6.0 + s) + 2.0 * L.ntot, st);

@@ -27,7 +27,7 @@ struct sisu_circuit {
 struct Workspace {
   void* dev = nullptr;  // owned allocation (null when placed in caller memory)
   uint32_t *T = nullptr, *E = nullptr, *om = nullptr, *At = nullptr, *H1 = nullptr, *H2 = nullptr,
-           *Ay = nullptr, *Q = nullptr, *partials = nullptr, *dscratch = nullptr, *eqh = nullptr;
+           *Ay = nullptr, *Q = nullptr, *partials = nullptr, *dscratch = nullptr, *eqh = nullptr, *P = nullptr;
   DevState* S = nullptr;
   uint8_t* proof = nullptr;
   uint8_t* host = nullptr;  // pinned: proof bytes followed by the error word

@@ -134,8 +134,9 @@ struct TailParams {
   const uint32_t* om; // gate weights, sorted order
   const uint4* sg;
   const uint32_t *off1, *pos1, *off2, *pos2;
-  uint32_t nmul, Wn, s;
+  uint32_t nmul, ntot, Wn, s;
   uint32_t *At, *H1, *H2, *Ay;
+  uint32_t* P;        // scratch: two values per entry (per-entry terms of the bookkeeping sums)
   DevState* S;
   uint8_t* proof;
   size_t offx, offy, offv;

@@ -915,19 +915,27 @@ __global__ void __cluster_dims__(kTailCTAs, 1, 1) __launch_bounds__(kTailThreads
   const Fr e = fr_load(p.E, 0);
   if (threadIdx.x < 8) sh.st[threadIdx.x] = S->st[threadIdx.x];  // ordered by the cluster barrier below
   // Libra phase 1 bookkeeping: H1(x) = e sum_{in1 g = x} w(g) (mul ? A(in2 g) : 1),
-  // H2(x) = e sum_{in1 g = x, add} w(g) A(in2 g)
+  // H2(x) = e sum_{in1 g = x, add} w(g) A(in2 g).  The per-entry terms are
+  // formed entry-parallel first (one product each, all at once), so that the
+  // sums over the in1 lists are additions only: the lists are a few entries
+  // long, and a product per list step put their longest one on the critical
+  // path.
+  uint32_t* P1 = p.P;
+  uint32_t* P2 = p.P + 8 * (size_t)p.ntot;
+  for (uint32_t g = gtid; g < p.ntot; g += gstride) {
+    const Fr w = fr_load(p.om, g);
+    const Fr wa = fr_mul(w, fr_load(p.A, p.sg[g].y));
+    const bool mul = g < p.nmul;
+    fr_store(P1, g, mul ? wa : w);
+    fr_store(P2, g, mul ? fr_zero() : wa);
+  }
+  cl.sync();  // the terms, for every CTA of the cluster
   for (uint32_t x = gtid; x < p.Wn; x += gstride) {
     Fr a1 = fr_zero(), a2 = fr_zero();
     for (uint32_t q = p.off1[x], qe = p.off1[x + 1]; q < qe; ++q) {
-      uint32_t g = p.pos1[q];
-      Fr w = fr_load(p.om, g);
-      Fr wa = fr_mul(w, fr_load(p.A, p.sg[g].y));
-      if (g < p.nmul) {
-        a1 = fr_add(a1, wa);
-      } else {
-        a1 = fr_add(a1, w);
-        a2 = fr_add(a2, wa);
-      }
+      const uint32_t g = p.pos1[q];
+      a1 = fr_add(a1, fr_load_cg(P1, g));
+      a2 = fr_add(a2, fr_load_cg(P2, g));
     }
     fr_store(p.H1, x, fr_mul(e, a1));
     fr_store(p.H2, x, fr_mul(e, a2));
@@ -983,14 +991,22 @@ __global__ void __cluster_dims__(kTailCTAs, 1, 1) __launch_bounds__(kTailThreads
   // Libra phase 2 bookkeeping: K1(y) = e sum_{in2 g = y} w(g) Q(in1 g) (mul ? v_x : 1),
   // K2(y) = e sum_{in2 g = y, add} w(g) Q(in1 g) v_x,  Q = eq(r_x, .)
   const Fr ev = fr_mul(e, vx);
+  // per-entry terms w(g) Q(in1 g), entry-parallel as in phase 1 (P1: mul
+  // entries, P2: add entries)
+  for (uint32_t g = gtid; g < p.ntot; g += gstride) {
+    const uint32_t x1 = p.sg[g].x;
+    const Fr wq = fr_mul(fr_load(p.om, g), fr_mul(sh.eqh[x1 >> sl], sh.eql[x1 & lmask]));
+    const bool mul = g < p.nmul;
+    fr_store(P1, g, mul ? wq : fr_zero());
+    fr_store(P2, g, mul ? fr_zero() : wq);
+  }
+  cl.sync();
   for (uint32_t y = gtid; y < p.Wn; y += gstride) {
     Fr mu = fr_zero(), ad = fr_zero();
     for (uint32_t q = p.off2[y], qe = p.off2[y + 1]; q < qe; ++q) {
-      uint32_t g = p.pos2[q];
-      const uint32_t x1 = p.sg[g].x;
-      Fr wq = fr_mul(fr_load(p.om, g), fr_mul(sh.eqh[x1 >> sl], sh.eql[x1 & lmask]));
-      if (g < p.nmul) mu = fr_add(mu, wq);
-      else ad = fr_add(ad, wq);
+      const uint32_t g = p.pos2[q];
+      mu = fr_add(mu, fr_load_cg(P1, g));
+      ad = fr_add(ad, fr_load_cg(P2, g));
     }
     fr_store(p.H1, y, fr_add(fr_mul(e, ad), fr_mul(ev, mu)));
     fr_store(p.H2, y, fr_mul(ev, ad));
