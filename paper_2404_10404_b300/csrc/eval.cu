@@ -75,6 +75,7 @@ int launch_layer_to_canonical(const uint32_t* V, uint32_t* out, uint32_t c, uint
 __global__ void k_eval_layer(const uint32_t* __restrict__ Vn, uint32_t* __restrict__ V,
                              const uint4* __restrict__ sg, uint32_t nmul, uint32_t ntot, uint32_t c, uint32_t s,
                              uint32_t sn) {
+  pdl_wait();
   const size_t total = (size_t)1 << (c + s);
   const uint32_t mask = (1u << s) - 1u;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
@@ -118,7 +119,8 @@ int launch_eval_layer(const uint32_t* Vn, uint32_t* V, const DevLayer& L, uint32
   if (L.offo)
     k_eval_layer_acc<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(Vn, V, L.offo, L.eo, c, s, sn);
   else
-    k_eval_layer<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(Vn, V, L.sgate, L.nmul, L.ntot, c, s, sn);
+    return launch_pdl(k_eval_layer, grid_for(n, 256), 256, (cudaStream_t)stream, Vn, V, L.sgate, L.nmul, L.ntot, c, s,
+                      sn);
   return post_launch();
 }
 

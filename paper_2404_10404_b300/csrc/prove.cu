@@ -279,6 +279,7 @@ __device__ __forceinline__ Fr eq_half_entry(const Fr* P, uint32_t k0, uint32_t n
 // then layer 0: z_g high, low; layer i: alpha r_x high, r_x low, beta r_y
 // high, r_y low.
 __global__ void k_eq_halves(DevState* S, uint32_t layer, uint32_t c, uint32_t si, uint32_t* __restrict__ tab) {
+  pdl_wait();
   const uint32_t nE = eq_half_entries(c), nW = eq_half_entries(si);
   const uint32_t total = nE + (layer == 0 ? nW : 2 * nW);
   for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
@@ -298,6 +299,7 @@ __global__ void k_eq_halves(DevState* S, uint32_t layer, uint32_t c, uint32_t si
 
 __global__ void k_layer_init(uint32_t layer, uint32_t c, uint32_t si, const uint4* __restrict__ sg, uint32_t ntot,
                              const uint32_t* __restrict__ tab, uint32_t* __restrict__ E, uint32_t* __restrict__ om) {
+  pdl_wait();
   const uint32_t C = 1u << c;
   const size_t total = (size_t)C + ntot;
   const uint32_t nE = eq_half_entries(c), nW = eq_half_entries(si);
@@ -328,12 +330,11 @@ int launch_layer_init(DevState* S, uint32_t layer, uint32_t c, uint32_t s_i, con
                       uint32_t* omega_s, uint32_t* eqh, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   const uint32_t nh = eq_half_entries(c) + (layer == 0 ? 1 : 2) * eq_half_entries(s_i);
-  k_eq_halves<<<grid_for(nh, 128), 128, 0, st>>>(S, layer, c, s_i, eqh);
-  const int rc = post_launch();
+  const int rc = launch_pdl(k_eq_halves, grid_for(nh, 128), 128, st, S, layer, c, s_i, eqh);
   if (rc) return rc;
   size_t n = ((size_t)1 << c) + L.ntot;
-  k_layer_init<<<grid_for(n, 128), 128, 0, st>>>(layer, c, s_i, L.sgate, L.ntot, eqh, E, omega_s);
-  return post_launch();
+  return launch_pdl(k_layer_init, grid_for(n, 128), 128, st, layer, c, s_i, L.sgate, L.ntot, (const uint32_t*)eqh, E,
+                    omega_s);
 }
 
 // ---------------------------------------------------------------------------
@@ -505,6 +506,7 @@ __global__ void __launch_bounds__(BD) k_copy_round(const uint32_t* __restrict__ 
                                                    const uint4* __restrict__ sg, uint32_t nmul, uint32_t ntot,
                                                    uint64_t per_cta, uint32_t m, uint32_t* partials, DevState* S,
                                                    uint8_t* proof, size_t off, uint32_t k) {
+  pdl_wait();
   __shared__ __align__(16) uint32_t sh_e[16];  // E(j), E(j + h) of the current segment
   const Fr tot = copy_items<BD>(T, sn, h, E, om, sg, nmul, ntot, per_cta, m, blockIdx.x, sh_e);
   Fr acc[4];
@@ -535,9 +537,8 @@ int launch_copy_round(const uint32_t* T, uint32_t sn, uint32_t h, const uint32_t
   // contiguous ranges of equal cost: one wave of CTAs, and for small rounds
   // about one item per thread (short serial chains)
   const CopySplit sp = copy_split(h, L.nmul, L.ntot, std::min<uint32_t>(kSMs * per_sm, kMaxPartials), BD);
-  k_copy_round<BD><<<sp.nc, BD, 0, st>>>(T, sn, h, E, omega_s, L.sgate, L.nmul, L.ntot, sp.per_cta, sp.m, partials,
-                                         S, proof, off, k);
-  return post_launch();
+  return launch_pdl(k_copy_round<BD>, sp.nc, BD, st, T, sn, h, E, omega_s, L.sgate, L.nmul, L.ntot, sp.per_cta, sp.m,
+                    partials, S, proof, off, k);
 }
 
 // fold of the copy rows and of E by the round's challenge r = r_b[k]:
@@ -551,6 +552,7 @@ int launch_copy_round(const uint32_t* T, uint32_t sn, uint32_t h, const uint32_t
 // needs the warps to keep loads in flight).
 __global__ void __launch_bounds__(256, 4) k_copy_fold(const uint32_t* src, uint32_t* dst, uint32_t sn, uint32_t h,
                                                    uint32_t* E, const DevState* S, uint32_t k) {
+  pdl_wait();
   __shared__ __align__(16) uint32_t shK[64];
   if (threadIdx.x < 8) fr_store(shK, threadIdx.x, fr_fixed_coeff(S->rb[k], (int)threadIdx.x));
   __syncthreads();
@@ -571,8 +573,8 @@ int launch_copy_fold(const uint32_t* src, uint32_t* dst, uint32_t sn, uint32_t h
   size_t n = ((size_t)h << sn) + h;
   // one resident wave (four CTAs per SM), so each CTA builds the eight
   // coefficients once for many entries
-  k_copy_fold<<<grid_for(n, 256, 4), 256, 0, (cudaStream_t)stream>>>(src, dst, sn, h, E, S, k);
-  return post_launch();
+  return launch_pdl(k_copy_fold, grid_for(n, 256, 4), 256, (cudaStream_t)stream, src, dst, sn, h, E,
+                    (const DevState*)S, k);
 }
 
 // ---------------------------------------------------------------------------
@@ -907,6 +909,7 @@ __device__ Fr tail_solo(TailShared& sh, const uint32_t* A, const uint32_t* B1, c
 }
 
 __global__ void __cluster_dims__(kTailCTAs, 1, 1) __launch_bounds__(kTailThreads) k_layer_tail(TailParams p) {
+  pdl_wait();
   cg::cluster_group cl = cg::this_cluster();
   __shared__ TailShared sh;
   const uint32_t rank = cl.block_rank();
@@ -1041,8 +1044,7 @@ __global__ void __cluster_dims__(kTailCTAs, 1, 1) __launch_bounds__(kTailThreads
 }
 
 int launch_layer_tail(const TailParams& p, void* stream) {
-  k_layer_tail<<<kTailCTAs, kTailThreads, 0, (cudaStream_t)stream>>>(p);
-  return post_launch();
+  return launch_pdl(k_layer_tail, kTailCTAs, kTailThreads, (cudaStream_t)stream, p);
 }
 
 }  // namespace sisu
