@@ -184,6 +184,27 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# replicas over ranks (torchrun, one process per GPU)
+
+def max_over_ranks(x: float, world: int, dev) -> float:
+    """The largest value over the ranks of the default process group (a
+    time: the job ends with its slowest rank); x itself with one rank."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(world: int, steps: int, units_per_step: int, seconds: float) -> float:
+    """Whole-job throughput of `world` replicas that each processed `steps`
+    steps of `units_per_step` units within `seconds` (the slowest rank's)."""
+    return world * steps * units_per_step / seconds
+
+
+# ---------------------------------------------------------------------------
 # the CUDA path
 
 def run_ours(args):
@@ -260,11 +281,8 @@ def run_ours(args):
     ms = ev0.elapsed_time(ev1)
     launches = S.kernel_launches() - launches0
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * args.steps * gates / (ms / 1e3)
+    ms = max_over_ranks(ms, world, dev)
+    value = aggregate_rate(world, args.steps, gates, ms / 1e3)
     # roofline of the dominant kernel: its launches timed with CUDA events on
     # the launching stream over further steps right after the timed region
     # (per-launch events need launch-by-launch issue instead of graph replay)
@@ -282,11 +300,8 @@ def run_ours(args):
         step(host)
     torch.cuda.synchronize(dev)
     e2e_s = time.perf_counter() - w0
-    if world > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * args.steps * gates / e2e_s, "unit": UNIT, "h2d_bytes_per_step": len(xb),
+    e2e_s = max_over_ranks(e2e_s, world, dev)
+    e2e = {"value": aggregate_rate(world, args.steps, gates, e2e_s), "unit": UNIT, "h2d_bytes_per_step": len(xb),
            "d2h_bytes_per_step": gc.proof_len}
 
     # per-kernel breakdown of one step (untimed pass)
