@@ -458,23 +458,52 @@ int eval_enqueue(sisu_eval* ev, const uint8_t* inputs, int on_device, cudaStream
   const uint32_t d = hc.d;
   const size_t in_bytes = (size_t)hc.Creal * hc.wreal[d] * 32;
   const bool padded = hc.Creal != hc.C || hc.wreal[d] != hc.W[d];
+  // Host inputs of an unpadded circuit arrive in chunks of copies on the
+  // handle's copy stream while the copies already in are converted and
+  // evaluated on `st`: every copy evaluates on its own rows (the circuits
+  // are data-parallel), so the evaluation of chunk k overlaps the transfer
+  // of chunk k + 1 and only the last chunk's evaluation follows the copy.
+  const uint32_t nchunk = (!on_device && !padded && hc.C >= kEvalChunks && in_bytes >= kEvalChunkMin) ? kEvalChunks : 1;
   const uint32_t* src;
   if (on_device) {
     if (((uintptr_t)inputs & 15) != 0) return fail(SISU_ERR_INVALID_ARG, "device inputs not 16-byte aligned");
     src = (const uint32_t*)inputs;
+  } else if (nchunk > 1) {
+    if (!ev->copy_stream) {
+      CK(cudaStreamCreateWithFlags(&ev->copy_stream, cudaStreamNonBlocking), "stream create");
+      for (cudaEvent_t& e : ev->chunk_ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event create");
+    }
+    // the copies overwrite the input layer only after the work queued on st
+    // before this call (a proof may still read it)
+    CK(cudaEventRecord(ev->chunk_ev[kEvalChunks], st), "event record");
+    CK(cudaStreamWaitEvent(ev->copy_stream, ev->chunk_ev[kEvalChunks], 0), "stream wait");
+    const size_t row = (size_t)hc.W[d] * 32;
+    for (uint32_t k = 0; k < nchunk; ++k) {
+      const size_t b0 = (size_t)hc.C * k / nchunk, b1 = (size_t)hc.C * (k + 1) / nchunk;
+      CK(cudaMemcpyAsync((uint8_t*)ev->V[d] + b0 * row, inputs + b0 * row, (b1 - b0) * row, cudaMemcpyHostToDevice,
+                         ev->copy_stream),
+         "input copy");
+      CK(cudaEventRecord(ev->chunk_ev[k], ev->copy_stream), "event record");
+    }
+    src = ev->V[d];
   } else {
     uint32_t* dst = padded ? ev->stage : ev->V[d];
     CK(cudaMemcpyAsync(dst, inputs, in_bytes, cudaMemcpyHostToDevice, st), "input copy");
     src = dst;
   }
   CK(cudaMemsetAsync(ev->flag, 0, 4, st), "memset");
-  {
-    ProfScope ps(kProfInputs, (double)((size_t)hc.C << hc.s[d]), st);
-    CK(launch_inputs_to_mont(src, ev->V[d], hc.c, hc.s[d], hc.Creal, hc.wreal[d], ev->flag, st), "input conversion");
-  }
-  for (int i = (int)d - 1; i >= 0; --i) {
-    ProfScope ps(kProfEval, (double)hc.C * cc->L[i].nmul, st);
-    CK(launch_eval_layer(ev->V[i + 1], ev->V[i], cc->L[i], hc.c, hc.s[i], hc.s[i + 1], st), "eval layer");
+  for (uint32_t k = 0; k < nchunk; ++k) {
+    const uint32_t b0 = (uint32_t)((uint64_t)hc.C * k / nchunk), b1 = (uint32_t)((uint64_t)hc.C * (k + 1) / nchunk);
+    if (nchunk > 1) CK(cudaStreamWaitEvent(st, ev->chunk_ev[k], 0), "stream wait");
+    {
+      ProfScope ps(kProfInputs, (double)((size_t)(b1 - b0) << hc.s[d]), st);
+      CK(launch_inputs_to_mont(src, ev->V[d], b0, b1 - b0, hc.s[d], hc.Creal, hc.wreal[d], ev->flag, st),
+         "input conversion");
+    }
+    for (int i = (int)d - 1; i >= 0; --i) {
+      ProfScope ps(kProfEval, (double)(b1 - b0) * cc->L[i].nmul, st);
+      CK(launch_eval_layer(ev->V[i + 1], ev->V[i], cc->L[i], b0, b1 - b0, hc.s[i], hc.s[i + 1], st), "eval layer");
+    }
   }
   CK(cudaMemcpyAsync(ev->host_flag, ev->flag, 4, cudaMemcpyDeviceToHost, st), "flag copy");
   return SISU_OK;

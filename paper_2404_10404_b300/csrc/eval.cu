@@ -17,12 +17,13 @@ namespace sisu {
 // ---------------------------------------------------------------------------
 // inputs: canonical -> Montgomery, zero padding, canonicity check
 
-__global__ void k_inputs_to_mont(const uint32_t* in, uint32_t* V, uint32_t c, uint32_t s, uint32_t Creal,
-                                 uint32_t wreal, uint32_t* err) {
-  const size_t total = (size_t)1 << (c + s);
+// copies b0 .. b0 + nb - 1 of the input layer
+__global__ void k_inputs_to_mont(const uint32_t* in, uint32_t* V, uint32_t b0, uint32_t nb, uint32_t s,
+                                 uint32_t Creal, uint32_t wreal, uint32_t* err) {
+  const size_t total = (size_t)nb << s;
   const uint32_t mask = (1u << s) - 1u;
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (size_t)gridDim.x * blockDim.x) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < total; k += (size_t)gridDim.x * blockDim.x) {
+    const size_t idx = ((size_t)b0 << s) + k;
     uint32_t b = (uint32_t)(idx >> s), x = (uint32_t)(idx & mask);
     Fr v = fr_zero();
     if (b < Creal && x < wreal) {
@@ -37,10 +38,10 @@ __global__ void k_inputs_to_mont(const uint32_t* in, uint32_t* V, uint32_t c, ui
   }
 }
 
-int launch_inputs_to_mont(const uint32_t* in, uint32_t* V, uint32_t c, uint32_t s, uint32_t Creal,
+int launch_inputs_to_mont(const uint32_t* in, uint32_t* V, uint32_t b0, uint32_t nb, uint32_t s, uint32_t Creal,
                           uint32_t wreal, uint32_t* err, void* stream) {
-  size_t n = (size_t)1 << (c + s);
-  k_inputs_to_mont<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(in, V, c, s, Creal, wreal, err);
+  size_t n = (size_t)nb << s;
+  k_inputs_to_mont<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(in, V, b0, nb, s, Creal, wreal, err);
   return post_launch();
 }
 
@@ -73,13 +74,13 @@ int launch_layer_to_canonical(const uint32_t* V, uint32_t* out, uint32_t c, uint
 // where every gate has at most one entry only.
 
 __global__ void k_eval_layer(const uint32_t* __restrict__ Vn, uint32_t* __restrict__ V,
-                             const uint4* __restrict__ sg, uint32_t nmul, uint32_t ntot, uint32_t c, uint32_t s,
-                             uint32_t sn) {
+                             const uint4* __restrict__ sg, uint32_t nmul, uint32_t ntot, uint32_t b0, uint32_t nb,
+                             uint32_t s, uint32_t sn) {
   pdl_wait();
-  const size_t total = (size_t)1 << (c + s);
+  const size_t total = (size_t)nb << s;
   const uint32_t mask = (1u << s) - 1u;
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (size_t)gridDim.x * blockDim.x) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < total; k += (size_t)gridDim.x * blockDim.x) {
+    const size_t idx = ((size_t)b0 << s) + k;
     const uint32_t b = (uint32_t)(idx >> s), q = (uint32_t)(idx & mask);
     const uint4 gi = sg[q];
     Fr out = fr_zero();
@@ -95,12 +96,12 @@ __global__ void k_eval_layer(const uint32_t* __restrict__ Vn, uint32_t* __restri
 // A layer of accumulation gates (Sec. 3.4.3): gate g of copy b is the sum
 // of its entries eo[offo[g] .. offo[g+1]) (0 when it has none).
 __global__ void k_eval_layer_acc(const uint32_t* __restrict__ Vn, uint32_t* __restrict__ V,
-                                 const uint32_t* __restrict__ offo, const uint2* __restrict__ eo, uint32_t c,
-                                 uint32_t s, uint32_t sn) {
-  const size_t total = (size_t)1 << (c + s);
+                                 const uint32_t* __restrict__ offo, const uint2* __restrict__ eo, uint32_t b0,
+                                 uint32_t nb, uint32_t s, uint32_t sn) {
+  const size_t total = (size_t)nb << s;
   const uint32_t mask = (1u << s) - 1u;
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (size_t)gridDim.x * blockDim.x) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < total; k += (size_t)gridDim.x * blockDim.x) {
+    const size_t idx = ((size_t)b0 << s) + k;
     const uint32_t b = (uint32_t)(idx >> s), g = (uint32_t)(idx & mask);
     const uint32_t* row = Vn + (((size_t)b << sn) << 3);
     Fr acc = fr_zero();
@@ -113,14 +114,14 @@ __global__ void k_eval_layer_acc(const uint32_t* __restrict__ Vn, uint32_t* __re
   }
 }
 
-int launch_eval_layer(const uint32_t* Vn, uint32_t* V, const DevLayer& L, uint32_t c, uint32_t s, uint32_t sn,
-                      void* stream) {
-  size_t n = (size_t)1 << (c + s);
+int launch_eval_layer(const uint32_t* Vn, uint32_t* V, const DevLayer& L, uint32_t b0, uint32_t nb, uint32_t s,
+                      uint32_t sn, void* stream) {
+  size_t n = (size_t)nb << s;
   if (L.offo)
-    k_eval_layer_acc<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(Vn, V, L.offo, L.eo, c, s, sn);
+    k_eval_layer_acc<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(Vn, V, L.offo, L.eo, b0, nb, s, sn);
   else
-    return launch_pdl(k_eval_layer, grid_for(n, 256), 256, (cudaStream_t)stream, Vn, V, L.sgate, L.nmul, L.ntot, c, s,
-                      sn);
+    return launch_pdl(k_eval_layer, grid_for(n, 256), 256, (cudaStream_t)stream, Vn, V, L.sgate, L.nmul, L.ntot, b0,
+                      nb, s, sn);
   return post_launch();
 }
 

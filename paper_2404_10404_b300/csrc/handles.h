@@ -59,7 +59,15 @@ struct sisu_eval {
   uint32_t* host_flag = nullptr;
   std::unique_ptr<Workspace> ws;
   bool placed = false;         // layers, flag and staging live in caller memory
+  // chunked transfer of host inputs (created on first use): the copy stream
+  // and one event per chunk, plus one for the start
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t chunk_ev[sisu::kEvalChunks + 1] = {};
   ~sisu_eval() {
+    if (copy_stream) cudaStreamSynchronize(copy_stream);
+    for (cudaEvent_t e : chunk_ev)
+      if (e) cudaEventDestroy(e);
+    if (copy_stream) cudaStreamDestroy(copy_stream);
     ws.reset();
     if (stage && !placed) cudaFree(stage);
     if (dev) cudaFree(dev);

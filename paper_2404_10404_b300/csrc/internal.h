@@ -22,6 +22,10 @@ namespace sisu {
 constexpr uint32_t kMaxLog = 32;         // bound on c and s_i (sizes <= 2^24 in practice)
 constexpr uint32_t kMaxDomain = 256;     // transcript domain bytes
 constexpr uint32_t kMaxPartials = 8192;  // blocks whose partial sums one round reduces
+// host inputs of at least kEvalChunkMin bytes are copied in kEvalChunks
+// chunks of copies, each evaluated while the next one is in transfer
+constexpr uint32_t kEvalChunks = 4;
+constexpr size_t kEvalChunkMin = (size_t)32 << 20;
 
 // Device-resident prover state: the transcript and every challenge, so that
 // no host round trip is needed inside a proof.  Challenges are stored in
@@ -87,10 +91,12 @@ constexpr uint32_t kProfAssocHash = 9, kProfAssocPair = 10;
 // sets the calling thread's sisu_last_error() message, returns code
 int report_error(int code, const char* msg);
 
-int launch_inputs_to_mont(const uint32_t* in, uint32_t* V, uint32_t c, uint32_t s, uint32_t Creal,
+// the input conversion and the layer evaluation of copies b0 .. b0 + nb - 1
+// (each copy evaluates independently of the others)
+int launch_inputs_to_mont(const uint32_t* in, uint32_t* V, uint32_t b0, uint32_t nb, uint32_t s, uint32_t Creal,
                           uint32_t wreal, uint32_t* err, void* stream);
-int launch_eval_layer(const uint32_t* Vn, uint32_t* V, const DevLayer& L, uint32_t c, uint32_t s, uint32_t sn,
-                      void* stream);
+int launch_eval_layer(const uint32_t* Vn, uint32_t* V, const DevLayer& L, uint32_t b0, uint32_t nb, uint32_t s,
+                      uint32_t sn, void* stream);
 int launch_layer_to_canonical(const uint32_t* V, uint32_t* out, uint32_t c, uint32_t s, uint32_t Creal,
                               uint32_t wreal, void* stream);
 // Merkle statement digests (8 words each): of two Montgomery tables at
