@@ -24,7 +24,7 @@ constexpr uint32_t kMaxDomain = 256;     // transcript domain bytes
 constexpr uint32_t kMaxPartials = 8192;  // blocks whose partial sums one round reduces
 // host inputs of at least kEvalChunkMin bytes are copied in kEvalChunks
 // chunks of copies, each evaluated while the next one is in transfer
-constexpr uint32_t kEvalChunks = 4;
+constexpr uint32_t kEvalChunks = 8;
 constexpr size_t kEvalChunkMin = (size_t)32 << 20;
 
 // Device-resident prover state: the transcript and every challenge, so that
