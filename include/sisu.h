@@ -117,6 +117,11 @@ int sisu_circuit_info(const sisu_circuit* circ, uint32_t* depth, uint32_t* log_c
  * memory (inputs_on_device != 0).  Every layer's values stay resident on
  * the device in the returned handle.  The call returns once the work is
  * enqueued on `stream` and the inputs were found canonical (one wait).
+ * Host inputs of at least 32 MiB (unpadded circuits) are copied in eight
+ * chunks of copies on a stream of the handle while the chunks already
+ * copied are evaluated on `stream` (each copy evaluates independently);
+ * the ordering seen by `stream` is unchanged, and pinned host memory lets
+ * the copies run asynchronously.
  * Errors: INVALID_ARG, NOT_CANONICAL, OOM, CUDA. */
 int sisu_circuit_eval(const sisu_circuit* circ, const uint8_t* inputs, int inputs_on_device,
                       void* stream, sisu_eval** out);
