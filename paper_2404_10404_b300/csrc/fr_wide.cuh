@@ -38,6 +38,10 @@ __device__ __forceinline__ FrAcc fracc_zero() {
 // 2^-32 that fr_redc288 leaves
 SISU_FR_CONST(fr_mont_2_32, 0x15b8b9dau, 0x93e78865u, 0xb05ea154u, 0x16df2426u, 0x302ab839u, 0x1271b743u,
               0xec6c226eu, 0x06bc037eu)
+// 2^-32 in Montgomery form: 2^-32 2^256 mod p is the integer 2^224
+SISU_FR_CONST(fr_mont_2_neg32, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 1u)
+// the plain integer 2^32 (a Montgomery product by it multiplies by 2^32 R^-1)
+SISU_FR_CONST(fr_int_2_32, 0u, 1u, 0u, 0u, 0u, 0u, 0u, 0u)
 
 // acc += a * b (the full 512-bit product, no reduction)
 __device__ __forceinline__ void fracc_mac_inl(FrAcc& acc, const Fr& a, const Fr& b) {

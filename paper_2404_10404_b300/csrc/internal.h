@@ -136,7 +136,7 @@ int launch_layer_end(DevState* S, const uint32_t* Ay, uint32_t s, uint8_t* proof
 constexpr uint32_t kTailMaxWidth = 1u << 16;
 struct TailParams {
   const uint32_t* A;  // row V~(r_b, .) after the copy phase
-  const uint32_t* E;  // E[0] = eq(z_b, r_b)
+  const uint32_t* E;  // E[0] = 2^32 eq(z_b, r_b) (the copy weights carry a factor 2^32)
   const uint32_t* om; // gate weights, sorted order
   const uint4* sg;
   const uint32_t *off1, *pos1, *off2, *pos2;

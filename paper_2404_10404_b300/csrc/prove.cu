@@ -292,7 +292,8 @@ __global__ void k_eq_halves(DevState* S, uint32_t layer, uint32_t c, uint32_t si
     if (!hi) u -= hsize;
     const Fr* P = isE ? (layer == 0 ? S->zb : S->rb) : layer == 0 ? S->zg : which == 0 ? S->rx : S->ry;
     Fr init = fr_one();
-    if (hi) init = isE ? fr_int_one() : layer == 0 ? fr_one() : which == 0 ? S->alpha : S->beta;
+    // the copy weights come out plain and scaled by 2^32 (see the copy round)
+    if (hi) init = isE ? fr_int_2_32() : layer == 0 ? fr_one() : which == 0 ? S->alpha : S->beta;
     fr_store(tab, idx, eq_half_entry(P, hi ? 0 : nh, hi ? nh : n / 2, u, init));
   }
 }
@@ -314,7 +315,7 @@ __global__ void k_layer_init(uint32_t layer, uint32_t c, uint32_t si, const uint
        idx += (size_t)gridDim.x * blockDim.x) {
     if (idx < C) {
       const uint32_t v = (uint32_t)idx;
-      fr_store(E, idx, fr_mul(fr_load(Eh, v >> cl), fr_load(El, v & ((1u << cl) - 1))));  // plain
+      fr_store(E, idx, fr_mul(fr_load(Eh, v >> cl), fr_load(El, v & ((1u << cl) - 1))));  // plain, times 2^32
     } else {
       const uint32_t q = (uint32_t)(idx - C), g = sg[q].z, gh = g >> sl, gl = g & ((1u << sl) - 1);
       Fr w = fr_mul(fr_load(Xh, gh), fr_load(Xl, gl));
@@ -350,7 +351,9 @@ int launch_layer_init(DevState* S, uint32_t layer, uint32_t c, uint32_t s_i, con
 // adds full 512-bit products (fracc_mac) and reduces once per pair segment,
 // so a mul gate costs two Montgomery products and three full products, an
 // add gate two full products.  The reduction leaves a factor 2^-32 in every
-// sum, undone by one product per CTA at the end.
+// sum; the copy weights E are kept scaled by 2^32 (from the layer init on,
+// the folds being linear), so the weighted sums come out exact with no
+// product to undo it.  Consumers of E(r_b) itself multiply by 2^-32 once.
 //
 // Work split: the (pair, gate) items, pair-major, are cut into ranges of
 // equal cost (gates are sorted mul first, so equal item counts would leave
@@ -496,8 +499,7 @@ __device__ __forceinline__ Fr copy_items(const uint32_t* __restrict__ T, uint32_
     }
     seg = segend;
   }
-  if (warp == 0 && lane < 4) tot = fr_mul(tot, fr_mont_2_32());  // undo the reductions' 2^-32
-  return tot;
+  return tot;  // E's factor 2^32 has cancelled the reductions' 2^-32
 }
 
 template <int BD>
@@ -588,7 +590,7 @@ __global__ void k_xinit(const uint32_t* __restrict__ A, const uint32_t* __restri
                         const uint32_t* __restrict__ off1, const uint32_t* __restrict__ pos1, uint32_t Wn,
                         uint32_t* __restrict__ At, uint32_t* __restrict__ H1, uint32_t* __restrict__ H2,
                         uint32_t* __restrict__ Ay) {
-  const Fr e = fr_load(E, 0);
+  const Fr e = fr_mul(fr_load(E, 0), fr_mont_2_neg32());  // E carries a factor 2^32
   for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < Wn; x += gridDim.x * blockDim.x) {
     Fr a1 = fr_zero(), a2 = fr_zero();
     for (uint32_t p = off1[x], pe = off1[x + 1]; p < pe; ++p) {
@@ -637,7 +639,7 @@ __global__ void k_yinit(const uint32_t* __restrict__ E, const uint32_t* __restri
                         const uint4* __restrict__ sg, uint32_t nmul, const uint32_t* __restrict__ off2,
                         const uint32_t* __restrict__ pos2, uint32_t Wn, uint32_t* __restrict__ K1,
                         uint32_t* __restrict__ K2, const DevState* S) {
-  const Fr e = fr_load(E, 0);
+  const Fr e = fr_mul(fr_load(E, 0), fr_mont_2_neg32());  // E carries a factor 2^32
   const Fr ev = fr_mul(e, S->vx);
   for (uint32_t y = blockIdx.x * blockDim.x + threadIdx.x; y < Wn; y += gridDim.x * blockDim.x) {
     Fr m = fr_zero(), a = fr_zero();
@@ -915,7 +917,7 @@ __global__ void __cluster_dims__(kTailCTAs, 1, 1) __launch_bounds__(kTailThreads
   const uint32_t rank = cl.block_rank();
   const uint32_t gtid = rank * kTailThreads + threadIdx.x, gstride = kTailCTAs * kTailThreads;
   DevState* S = p.S;
-  const Fr e = fr_load(p.E, 0);
+  const Fr e = fr_mul(fr_load(p.E, 0), fr_mont_2_neg32());  // E carries a factor 2^32
   if (threadIdx.x < 8) sh.st[threadIdx.x] = S->st[threadIdx.x];  // ordered by the cluster barrier below
   // Libra phase 1 bookkeeping: H1(x) = e sum_{in1 g = x} w(g) (mul ? A(in2 g) : 1),
   // H2(x) = e sum_{in1 g = x, add} w(g) A(in2 g).  The per-entry terms are
