@@ -54,9 +54,11 @@ __device__ __forceinline__ void store_words(uint8_t* base, size_t off, const Fr&
 // where a full SHA-256 of the message and a separate challenge hash took
 // four, and the hash runs on the critical path of every round.
 
-// The compression runs out of line in one of two forms: kSmall for the
-// transcripts at the end of a round kernel, where the code is cold, the
-// unrolled form in the cluster kernel of Libra's phases, where it is warm.
+// The compression runs out of line in one of two forms: the compact loop
+// (kSmall) for the single-thread kernels that run it once, cold (transcript
+// init, layer end of wide layers); the unrolled form everywhere it is warm:
+// the cluster kernel of Libra's phases, and the round kernels, which warm it
+// at their start (warm_transcript_code).
 template <bool kSmall>
 __device__ __forceinline__ ShaWords8 tr_compress(const ShaWords8& h, const ShaWords16& blk) {
   return kSmall ? sha256_compress_small_v(h, blk) : sha256_compress_v(h, blk);
@@ -119,7 +121,23 @@ __device__ __noinline__ Fr tr_challenge_st(uint32_t* st, uint32_t* error, bool f
   return fr_zero();
 }
 
-// the transcripts of the round kernels (cold code)
+// One lane of a round kernel runs the unrolled compression once on scratch
+// words at the start, so that its code is in the SM's instruction caches when
+// the last CTA runs the round's transcript at the end.  Cold, the unrolled
+// form was slower there than the compact loop; warm, it is faster (medium
+// step 19.64 -> 19.35 ms).
+__device__ __forceinline__ void warm_transcript_code(uint32_t a, uint32_t b) {
+  ShaWords8 hw;
+  ShaWords16 bw;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) hw.w[i] = a + i;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) bw.w[i] = b + i;
+  hw = tr_compress<false>(hw, bw);
+  asm volatile("" ::"r"(hw.w[0]));
+}
+
+// the transcripts of the single-thread kernels (transcript init, layer end)
 __device__ __forceinline__ Fr tr_challenge(DevState* S, bool fresh) {
   return tr_challenge_st<true>(S->st, &S->error, fresh);
 }
@@ -152,8 +170,8 @@ __device__ __forceinline__ void round_finalize(DevState* S, const Fr (&v)[NV], u
     Fr canon[NV - 1];
 #pragma unroll
     for (int t = 0; t < NV - 1; ++t) canon[t] = sh[t];
-    tr_absorb_n<NV - 1, true>(S->st, 'R', canon);
-    *rslot = tr_challenge(S, true);
+    tr_absorb_n<NV - 1, false>(S->st, 'R', canon);
+    *rslot = tr_challenge_st<false>(S->st, &S->error, true);
   }
 }
 
@@ -510,6 +528,7 @@ __global__ void __launch_bounds__(BD) k_copy_round(const uint32_t* __restrict__ 
                                                    uint8_t* proof, size_t off, uint32_t k) {
   pdl_wait();
   __shared__ __align__(16) uint32_t sh_e[16];  // E(j), E(j + h) of the current segment
+  if (threadIdx.x == BD - 32) warm_transcript_code(k, h);
   const Fr tot = copy_items<BD>(T, sn, h, E, om, sg, nmul, ntot, per_cta, m, blockIdx.x, sh_e);
   Fr acc[4];
 #pragma unroll
@@ -668,6 +687,7 @@ template <int BD>
 __global__ void __launch_bounds__(BD) k_gate_round(uint32_t* A, uint32_t* B1, uint32_t* B2, uint32_t m, int phase,
                                                    uint32_t k, uint32_t* partials, DevState* S, uint8_t* proof,
                                                    size_t off) {
+  if (threadIdx.x == BD - 32) warm_transcript_code(k, m);
   const uint32_t hq = m / 2;
   Fr* rs = phase == 0 ? S->rx : S->ry;
   const bool fold = k > 0;

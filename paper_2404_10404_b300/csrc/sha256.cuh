@@ -147,10 +147,9 @@ static __device__ __noinline__ ShaWords8 sha256_compress_v(ShaWords8 h, ShaWords
   sha256_compress(h.w, blk.w);
   return h;
 }
-// The compact loop (a quarter of the code) for a transcript that runs cold,
-// once at the end of a kernel whose main loop evicted it: there fetching
-// the unrolled code costs more than the loop saves (measured in the
-// copy-phase rounds).
+// The compact loop (a quarter of the code) for a transcript that runs cold
+// and once: there fetching the unrolled code costs more than the loop saves
+// (measured in the copy-phase rounds before they warmed the unrolled code).
 static __device__ __noinline__ ShaWords8 sha256_compress_small_v(ShaWords8 h, ShaWords16 blk) {
   sha256_compress_compact(h.w, blk.w);
   return h;
