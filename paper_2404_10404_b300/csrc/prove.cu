@@ -393,11 +393,16 @@ __host__ __device__ __forceinline__ uint64_t copy_pair_cost(uint32_t nmul, uint3
 }
 
 // item position of cost position X (rounded up to a gate boundary)
-__device__ __forceinline__ uint64_t item_at_cost(uint64_t X, uint32_t nmul, uint32_t ntot, uint64_t pair_cost) {
-  const uint64_t j = X / pair_cost, r = X - j * pair_cost;
+// gate position inside a pair of cost position r (0 <= r <= pair cost)
+__device__ __forceinline__ uint64_t item_in_pair(uint64_t r, uint32_t nmul, uint32_t ntot) {
   const uint64_t mc = kCostMul * nmul;
   const uint64_t g = r < mc ? (r + kCostMul - 1) / kCostMul : nmul + (r - mc + kCostAdd - 1) / kCostAdd;
-  return j * ntot + min(g, (uint64_t)ntot);
+  return min(g, (uint64_t)ntot);
+}
+
+__device__ __forceinline__ uint64_t item_at_cost(uint64_t X, uint32_t nmul, uint32_t ntot, uint64_t pair_cost) {
+  const uint64_t j = X / pair_cost;
+  return j * ntot + item_in_pair(X - j * pair_cost, nmul, ntot);
 }
 
 // The split of a round's items over nc CTAs (at most ncmax, and no more than
@@ -439,23 +444,23 @@ __device__ __forceinline__ Fr copy_items(const uint32_t* __restrict__ T, uint32_
                                          const uint4* __restrict__ sg, uint32_t nmul, uint32_t ntot,
                                          uint64_t per_cta, uint32_t m, uint32_t bid, uint32_t* sh_e) {
   const uint64_t pair_cost = copy_pair_cost(nmul, ntot);
-  uint64_t c0, c1;  // the CTA's cost range
-  if (m) {
-    const uint32_t j = bid / m, sub = bid - j * m;
-    const uint64_t base = (uint64_t)j * pair_cost;
-    c0 = base + min(pair_cost, (uint64_t)sub * per_cta);
-    c1 = base + min(pair_cost, (uint64_t)(sub + 1) * per_cta);
+  uint64_t q0, q1;  // the CTA's item range
+  uint32_t j;       // the pair of its first item
+  if (m) {  // a range inside pair j: no 64-bit division on the (latency-bound) late rounds
+    j = bid / m;
+    const uint32_t sub = bid - j * m;
+    const uint64_t base = (uint64_t)j * ntot;
+    q0 = base + item_in_pair(min(pair_cost, (uint64_t)sub * per_cta), nmul, ntot);
+    q1 = base + item_in_pair(min(pair_cost, (uint64_t)(sub + 1) * per_cta), nmul, ntot);
   } else {
     const uint64_t total_cost = (uint64_t)h * pair_cost;
-    c0 = min(total_cost, (uint64_t)bid * per_cta);
-    c1 = min(total_cost, (uint64_t)(bid + 1) * per_cta);
+    q0 = item_at_cost(min(total_cost, (uint64_t)bid * per_cta), nmul, ntot, pair_cost);
+    q1 = item_at_cost(min(total_cost, (uint64_t)(bid + 1) * per_cta), nmul, ntot, pair_cost);
+    j = (uint32_t)(q0 / ntot);
   }
-  const uint64_t q0 = item_at_cost(c0, nmul, ntot, pair_cost);
-  const uint64_t q1 = item_at_cost(c1, nmul, ntot, pair_cost);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   Fr tot = fr_zero();  // lane t < 4 of warp 0: sum over segments of E_t(j) S_j(t)
-  for (uint64_t seg = q0; seg < q1;) {
-    const uint32_t j = (uint32_t)(seg / ntot);
+  for (uint64_t seg = q0; seg < q1; ++j) {  // one segment per pair, pairs in order
     const uint64_t segend = min(q1, (uint64_t)(j + 1) * ntot);
     if (threadIdx.x < 4) {  // E(j) -> sh_e[0..7], E(j + h) -> sh_e[8..15], 16 bytes a thread
       __syncwarp(0xfu);     // the previous segment's reads of sh_e are done
