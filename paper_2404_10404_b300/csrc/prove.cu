@@ -584,13 +584,24 @@ __global__ void __launch_bounds__(256, 4) k_copy_fold(const uint32_t* src, uint3
   __syncthreads();
   const size_t nel = (size_t)h << sn;
   const size_t total = nel + h;
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    const bool row = idx < nel;
-    const uint32_t* base = row ? src : E;
-    const size_t i0 = row ? idx : idx - nel, i1 = row ? idx + nel : idx - nel + h;
-    const Fr x = fr_load(base, i0), y = fr_load(base, i1);
-    fr_store(row ? dst : E, i0, fr_add(x, fr_mul_fixed(fr_sub(y, x), shK)));
+  // two entries a thread per step, their four loads issued before either
+  // product (more bytes in flight for the HBM half of this balanced kernel)
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += 2 * stride) {
+    const size_t idy = idx + stride;
+    const bool rowa = idx < nel, rowb = idy < nel, hasb = idy < total;
+    const uint32_t* ba = rowa ? src : E;
+    const uint32_t* bb = rowb ? src : E;
+    const size_t a0 = rowa ? idx : idx - nel, a1 = rowa ? idx + nel : idx - nel + h;
+    const size_t b0 = rowb ? idy : idy - nel, b1 = rowb ? idy + nel : idy - nel + h;
+    const Fr xa = fr_load(ba, a0), ya = fr_load(ba, a1);
+    Fr xb = fr_zero(), yb = fr_zero();
+    if (hasb) {
+      xb = fr_load(bb, b0);
+      yb = fr_load(bb, b1);
+    }
+    fr_store(rowa ? dst : E, a0, fr_add(xa, fr_mul_fixed(fr_sub(ya, xa), shK)));
+    if (hasb) fr_store(rowb ? dst : E, b0, fr_add(xb, fr_mul_fixed(fr_sub(yb, xb), shK)));
   }
 }
 
