@@ -182,6 +182,39 @@ def test_full_size_golden(S, name):
     assert sha(ev.outputs()) == g["outputs_sha256"]
 
 
+def test_chunked_host_inputs(S, oracle):
+    """Host inputs of 32 MiB and more arrive in chunks of copies that are
+    evaluated while the next chunk is in transfer: the proof equals the
+    oracle's, and re-evaluating the handle from host and device inputs in
+    turn on one stream keeps every proof identical."""
+    circ = synth.uniform_circuit(8, 256, [4096, 4096, 4096], 50)
+    xb = synth.fr_bytes(synth.inputs_for(circ))
+    assert len(xb) >= 32 << 20
+    gc = S.Circuit.from_spec(circ)
+    ev = S.Eval(gc, xb)
+    want = oracle.prove(circ, xb)
+    assert S.prove(gc, ev) == want
+    dev = to_device(xb)
+    for src in (dev, xb, xb, dev, xb):
+        ev.update(src)
+        assert S.prove(gc, ev) == want
+
+
+def test_full_size_golden_host_inputs(S):
+    """The medium workload evaluated from host bytes (the chunked transfer)
+    gives the oracle's proof and outputs (stored hashes)."""
+    g = golden("medium")
+    if g is None:
+        pytest.skip("no oracle record for medium")
+    circ = synth.medium()
+    xb = synth.fr_bytes(synth.inputs_for(circ))
+    gc = S.Circuit.from_spec(circ)
+    ev = S.Eval(gc, xb)
+    proof = S.prove(gc, ev)
+    assert sha(proof) == g["proof_sha256"]
+    assert sha(ev.outputs()) == g["outputs_sha256"]
+
+
 @pytest.mark.parametrize("seed,C,widths,k", [
     (1, 2, [3, 4, 5], 3), (2, 4, [4, 4, 4], 4), (3, 37, [300, 257, 513], 3),  # padded copies and widths
     (4, 1, [64, 64, 64], 6),                                                  # one copy: no copy phase
