@@ -351,11 +351,13 @@ def run_ours(args):
 
 ASSOC_METRIC = "validator indexes/s (associative hash of every slot + pairwise-distinct check of every epoch)"
 ASSOC_UNIT = "indexes/s"
-# multiply-adds per evaluation of F on a validator index (below 2^32): three
-# Montgomery squares (36 + 36 multiply halves for the square, 8 + 128 for the
-# reduction), three Montgomery products and the one-row fixed-multiplier
-# product for e -> e R (8 + 8 for the row, 9 + 9 for the two reduction steps)
-IMAD_PER_F = 3 * (72 + 136) + 3 * IMAD_PER_FR_MUL + 34
+# multiply-adds per evaluation of F on a validator index (below 2^32), as the
+# kernel forms it: the first cube and the second base exact in 64-bit
+# integers (about 30 multiply-adds with the second base's square), the
+# second base times R^2 by four fixed-multiplier rows (4 x 16 + 34), one
+# Montgomery product for its cube, a R by two rows (2 x 16 + 34), and the
+# last cube as a Montgomery square (72 + 136) and product
+IMAD_PER_F = 30 + (4 * 16 + 34) + IMAD_PER_FR_MUL + (2 * 16 + 34) + (72 + 136) + IMAD_PER_FR_MUL
 ASSOC_EPOCHS, ASSOC_EPOCH, ASSOC_SLOT, ASSOC_LOG_UNIVERSE = 64, 1 << 20, 1 << 15, 21
 # DRAM read + write bytes per index of k_assoc_chunks (ncu capture of one
 # launch over 2^23 indexes, profiles/assoc_chunks_validator_indexes.md):

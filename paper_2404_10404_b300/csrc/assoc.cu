@@ -38,11 +38,17 @@ constexpr uint32_t kAssocAdd = 4294967295u;  // 2^32 - 1, added every round of A
 // device error word bits
 constexpr uint32_t kAssocNotCanonical = 1u;
 
+// R^3 mod p: a Montgomery product with it multiplies by R^2
+SISU_FR_CONST(fr_r3, 0xb4bf0040u, 0x5e94d8e1u, 0x1cfbb6b8u, 0x2a489cbeu, 0xa19fcfedu, 0x893cc664u, 0x7fcc657cu,
+              0x0cf8594bu)
+
 // the CTA's constants: the fixed-multiplier coefficients of R^2 mod p (so
-// that fr_mul_fixed(e, K) = e R, the Montgomery form of a canonical e) and
+// that fr_mul_fixed(e, K) = e R, the Montgomery form of a canonical e) in
+// shK[0..63], those of R^3 mod p (x -> x R^2) in shK[64..127], and
 // (2^32 - 1) R
 __device__ __forceinline__ void assoc_consts(uint32_t* shK, Fr* sh_c) {
   if (threadIdx.x < 8) fr_store(shK, threadIdx.x, fr_fixed_coeff(fr_r2(), (int)threadIdx.x));
+  if (threadIdx.x >= 32 && threadIdx.x < 40) fr_store(shK, threadIdx.x - 24, fr_fixed_coeff(fr_r3(), (int)threadIdx.x - 32));
   if (threadIdx.x == 8) {
     Fr c = fr_zero();
     c.v[0] = kAssocAdd;
@@ -51,19 +57,56 @@ __device__ __forceinline__ void assoc_consts(uint32_t* shK, Fr* sh_c) {
   __syncthreads();
 }
 
-// e R for a canonical e below 2^32 (a validator index): the one nonzero
-// limb's row of the fixed-multiplier product (16 multiply-adds and the
-// two-word reduction instead of eight rows)
-__device__ __forceinline__ Fr fr_mul_fixed_u32(uint32_t d0, const uint32_t* K8) {
-  Fr d = fr_zero();
-  d.v[0] = d0;
-  return fr_mul_fixed_rows<1>(d, K8);
+__device__ __forceinline__ Fr fr_from_u64x4(uint64_t w0, uint64_t w1, uint64_t w2, uint64_t w3) {
+  Fr x;
+  const uint64_t w[4] = {w0, w1, w2, w3};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    x.v[2 * i] = (uint32_t)w[i];
+    x.v[2 * i + 1] = (uint32_t)(w[i] >> 32);
+  }
+  return x;
 }
 
-// F(e) in Montgomery form for a canonical e; `small`: e < 2^32
+// F(e) in Montgomery form for a canonical e below 2^32 (a validator index).
+// With a = e + 2^32 - 1 < 2^33 the first round's cube a^3 < 2^99 and the
+// second base t = a^3 + a < 2^100 are exact integers, and so is t^2 < 2^200
+// (all below p): the first round needs no modular arithmetic, the second
+// one Montgomery product, t^3 R = MontMul(t^2, t R^2) with t R^2 from the
+// fixed-multiplier rows of t's four limbs (coefficients of R^3).  About 890
+// multiply-adds where the general path takes 1,450.
+__device__ __forceinline__ Fr assoc_F_small(uint32_t e, const uint32_t* K2, const uint32_t* K3) {
+  const uint64_t a = (uint64_t)e + 0xffffffffull;  // < 2^33
+  // a^2 = (s1:s0) < 2^66, a^3 = (c1:c0) < 2^99
+  const uint64_t s0 = a * a, s1 = __umul64hi(a, a);
+  const uint64_t c0 = s0 * a, c1 = __umul64hi(s0, a) + s1 * a;
+  // t = a^3 + a < 2^100 = (t1:t0)
+  const uint64_t t0 = c0 + a, t1 = c1 + (t0 < a ? 1u : 0u);
+  // u = t^2 < 2^200 = (u3:u2:u1:u0)
+  const uint64_t ll = t0 * t0, lh = __umul64hi(t0, t0);
+  const uint64_t m0 = t0 * t1, m1 = __umul64hi(t0, t1);  // t0 t1, counted twice
+  const uint64_t hh = t1 * t1, hh1 = __umul64hi(t1, t1);
+  const uint64_t d0 = m0 << 1, d1 = (m1 << 1) | (m0 >> 63), d2 = m1 >> 63;
+  const uint64_t u0 = ll;
+  const uint64_t u1 = lh + d0;
+  const uint64_t k1 = u1 < d0 ? 1u : 0u;
+  const uint64_t x2 = hh + d1;
+  const uint64_t k2a = x2 < d1 ? 1u : 0u;
+  const uint64_t u2 = x2 + k1;
+  const uint64_t k2b = u2 < k1 ? 1u : 0u;
+  const uint64_t u3 = hh1 + d2 + k2a + k2b;
+  const Fr tR2 = fr_mul_fixed_rows<4>(fr_from_u64x4(t0, t1, 0, 0), K3);  // t R^2
+  const Fr r2 = fr_mul(fr_from_u64x4(u0, u1, u2, u3), tR2);            // t^3 R
+  const Fr aR = fr_mul_fixed_rows<2>(fr_from_u64x4(a, 0, 0, 0), K2);     // a R
+  const Fr t2 = fr_add(r2, aR);
+  return fr_mul(fr_sqr(t2), t2);
+}
+
+// F(e) in Montgomery form for a canonical e; `small`: every lane of the warp
+// holds a value below 2^32
 __device__ __forceinline__ Fr assoc_F(const Fr& e, bool small, const uint32_t* K, const Fr& c) {
-  const Fr eR = small ? fr_mul_fixed_u32(e.v[0], K) : fr_mul_fixed(e, K);
-  const Fr a = fr_add(eR, c);  // (e + 2^32 - 1) R
+  if (small) return assoc_F_small(e.v[0], K, K + 64);
+  const Fr a = fr_add(fr_mul_fixed(e, K), c);  // (e + 2^32 - 1) R
   Fr r = fr_mul(fr_sqr(a), a);
   Fr t = fr_add(r, a);
   r = fr_mul(fr_sqr(t), t);
@@ -104,7 +147,7 @@ __global__ void __launch_bounds__(kAssocBD, 2) k_assoc_chunks(const uint32_t* __
                                                           const uint64_t* __restrict__ chunks, uint32_t nchunks,
                                                           uint32_t* __restrict__ partials, uint32_t stride,
                                                           uint32_t off, uint32_t* next, uint32_t* flag) {
-  __shared__ __align__(16) uint32_t shK[64];
+  __shared__ __align__(16) uint32_t shK[128];
   __shared__ Fr sh_c;
   __shared__ uint32_t sh_ch;
   assoc_consts(shK, &sh_c);
