@@ -362,7 +362,7 @@ ASSOC_EPOCHS, ASSOC_EPOCH, ASSOC_SLOT, ASSOC_LOG_UNIVERSE = 64, 1 << 20, 1 << 15
 # DRAM read + write bytes per index of k_assoc_chunks (ncu capture of one
 # launch over 2^23 indexes, profiles/assoc_chunks_validator_indexes.md):
 # the 32-byte value read once plus the chunk tables and partial sums
-ASSOC_TRAFFIC_PER_INDEX = (268.550912e6 + 3.135488e6) / 2**23
+ASSOC_TRAFFIC_PER_INDEX = (268.816896e6 + 3.927552e6) / 2**23
 
 
 def assoc_inputs(epochs: int):
