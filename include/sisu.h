@@ -259,6 +259,15 @@ int sisu_pairwise_distinct_check(const uint8_t* a, const uint8_t* a_sorted, uint
 int sisu_pairwise_distinct_check_segments(const uint8_t* a, const uint8_t* a_sorted, const uint64_t* offsets,
                                           uint32_t n_segments, int on_device, void* stream, int* results,
                                           uint8_t* h_a, uint8_t* h_sorted);
+/* The prover's side of Algorithm 2: `out` receives the n canonical elements
+ * of `in` in ascending order (as integers), equal values kept.  in and out
+ * are both host or both device memory (on_device; device arrays 16-byte
+ * aligned; in == out allowed).  A least-significant-digit radix sort over
+ * the bytes on which the elements differ; *passes (may be NULL) receives
+ * the number of byte passes run (3 for values below 2^24, up to 32).
+ * Blocks until done.  Errors: INVALID_ARG, NOT_CANONICAL, TOO_LARGE
+ * (n >= 2^32), CUDA. */
+int sisu_sort_elements(const uint8_t* in, uint64_t n, int on_device, void* stream, uint8_t* out, uint32_t* passes);
 
 /* ---- field core (Sec. 4.1, BN254 scalar field) ----------------------------
  * Elementwise on device arrays of n canonical elements, enqueued on

@@ -35,7 +35,7 @@ ENTRY_POINTS = [
     "sisu_gkr_prove_batch", "sisu_server_create", "sisu_server_submit", "sisu_server_poll",
     "sisu_server_pending", "sisu_server_destroy",
     "sisu_assoc_hash", "sisu_assoc_hash_segments", "sisu_pairwise_distinct_check",
-    "sisu_pairwise_distinct_check_segments",
+    "sisu_pairwise_distinct_check_segments", "sisu_sort_elements",
 ]
 PROF_COPY_ROUND, PROF_COPY_FOLD, PROF_EVAL, PROF_GATE_ROUND, PROF_DIGEST = 0, 1, 2, 3, 4
 PROF_LAYER_INIT, PROF_PHASE_INIT, PROF_TRANSCRIPT, PROF_INPUTS = 5, 6, 7, 8
@@ -106,6 +106,8 @@ def _load():
                                           vp, vp], ctypes.c_int),
         "sisu_pairwise_distinct_check_segments": ([vp, vp, ctypes.POINTER(ctypes.c_uint64), u32, ctypes.c_int, vp,
                                                    ctypes.POINTER(ctypes.c_int), vp, vp], ctypes.c_int),
+        "sisu_sort_elements": ([vp, ctypes.c_uint64, ctypes.c_int, vp, vp, ctypes.POINTER(ctypes.c_uint32)],
+                               ctypes.c_int),
         "sisu_kernel_launches": ([], ctypes.c_uint64),
         "sisu_free": ([vp], None),
         "sisu_last_error": ([], ctypes.c_char_p),
@@ -468,6 +470,26 @@ def pairwise_distinct_check_segments(a, a_sorted, offsets, stream=None):
                                                       ctypes.cast(hs, ctypes.c_void_p)))
     ra, rs = ha.raw, hs.raw
     return list(res)[:m], [ra[32 * g:32 * g + 32] for g in range(m)], [rs[32 * g:32 * g + 32] for g in range(m)]
+
+
+def sort_elements(elems, out=None, n: int | None = None, stream=None):
+    """Ascending sort of canonical elements (the prover's A* for Algorithm 2).
+    Host input (bytes/numpy) returns (sorted bytes, passes); for a CUDA
+    tensor, `out` (a CUDA tensor of the same size, may be `elems`) receives
+    the result and (out, passes) is returned."""
+    p, dev, keep = _ptr(elems)
+    if n is None:
+        n = (elems.numel() * elems.element_size() if hasattr(elems, "numel") else len(elems)) // 32
+    passes = ctypes.c_uint32(0)
+    if dev:
+        if out is None:
+            raise ValueError("device input needs a device output buffer")
+        po, dev_o, keep_o = _ptr(out)
+        _check(_lib.sisu_sort_elements(p, n, 1, _stream(stream), po, ctypes.byref(passes)))
+        return out, passes.value
+    buf = ctypes.create_string_buffer(max(1, 32 * n))
+    _check(_lib.sisu_sort_elements(p, n, 0, _stream(stream), ctypes.cast(buf, ctypes.c_void_p), ctypes.byref(passes)))
+    return buf.raw[:32 * n], passes.value
 
 
 def statement_digest(data, length: int, stream=None) -> bytes:

@@ -188,3 +188,55 @@ def test_full_size_sampled(S, oracle):
         assert got[g] == oracle.assoc_hash(x[32 * g * seg:32 * (g + 1) * seg]), g
     epoch = sum(int.from_bytes(h, "little") for h in got[:32]) % P
     assert int.from_bytes(S.assoc_hash(x[:32 * (1 << 20)]), "little") == epoch
+
+
+# ---------------------------------------------------------------------------
+# the prover's sort (A* of Algorithm 2), against the plain definition
+
+def _ints(b):
+    return [int.from_bytes(b[i:i + 32], "little") for i in range(0, len(b), 32)]
+
+
+@pytest.mark.parametrize("n", [1, 2, 255, 256, 257, 4096 + 13, 100000])
+def test_sort_uniform_elements(S, n):
+    x = _elems(300 + n, n)
+    got, passes = S.sort_elements(x)
+    assert _ints(got) == sorted(_ints(x))
+    assert passes == (0 if n == 1 else 32)
+
+
+def test_sort_validator_indexes_and_repeats(S):
+    idx = synth.validator_indexes(17, 300000, 21)
+    x = synth.fr_bytes(idx)
+    got, passes = S.sort_elements(x)
+    assert _ints(got) == sorted(_ints(x)) and passes == 3
+    # repeats, an already sorted list, a reversed one, all equal
+    vals = [v % 1000 for v in _ints(x)[:50000]]
+    for case in (vals, sorted(vals), sorted(vals, reverse=True), [7] * 5000):
+        b = b"".join(v.to_bytes(32, "little") for v in case)
+        got, _ = S.sort_elements(b)
+        assert _ints(got) == sorted(case)
+    # device memory, in place
+    t = to_device(x)
+    S.sort_elements(t, t, len(idx))
+    assert _ints(t[:len(x)].cpu().numpy().tobytes()) == sorted(_ints(x))
+
+
+def test_sort_feeds_the_check(S):
+    """The sorted list the prover produces is accepted by Algorithm 2, and a
+    list with a repeat is rejected."""
+    idx = synth.validator_indexes(18, 1 << 20, 21)
+    a = synth.fr_bytes(idx)
+    s, _ = S.sort_elements(a)
+    assert S.pairwise_distinct_check(a, s)[0] == 1
+    dup = idx.copy()
+    dup[5] = dup[6]
+    a2 = synth.fr_bytes(dup)
+    s2, _ = S.sort_elements(a2)
+    assert S.pairwise_distinct_check(a2, s2)[0] == 0
+
+
+def test_sort_errors(S):
+    with pytest.raises(S.SisuError):
+        S.sort_elements(_elems(19, 3) + (P).to_bytes(32, "little"))
+    assert S.sort_elements(b"")[0] == b""
