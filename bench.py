@@ -502,6 +502,28 @@ def run_assoc(args):
                 "f_evaluations_per_launch": kf / kn, "imad_per_f": IMAD_PER_F,
                 "peak_source": "derived: 148 SMs x 64 IMAD/clk x 2032 MHz",
                 "kernels_ms_per_step": {k: round(v[0] / v[1], 4) for k, v in kern.items()}}
+    # the prover's side (not in the step): sorting one epoch's list on the
+    # device into A*, the input Algorithm 2 checks
+    ep = da[:32 * ASSOC_EPOCH].clone()
+    S.sort_elements(ep.clone(), ep, ASSOC_EPOCH, stream=st)
+    torch.cuda.synchronize(dev)
+    srt0, srt1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    srt0.record(stream)
+    reps = 5
+    passes = 0
+    for _ in range(reps):
+        work = da[:32 * ASSOC_EPOCH].clone()
+        _, passes = S.sort_elements(work, work, ASSOC_EPOCH, stream=st)
+    srt1.record(stream)
+    torch.cuda.synchronize(dev)
+    sort_ms = srt0.elapsed_time(srt1) / reps
+    sort_ok = bool(torch.equal(work, ds[:32 * ASSOC_EPOCH]))
+    # bytes per element: the differing-bytes scan reads it once; every pass
+    # reads it twice (histogram, scatter) and writes it once
+    sort_bytes = ASSOC_EPOCH * 32 * (1 + 3 * passes)
+    prover_sort = {"elements": ASSOC_EPOCH, "ms": sort_ms, "passes": passes,
+                   "GB_s": sort_bytes / (sort_ms / 1e3) / 1e9, "equals_numpy_sort": sort_ok,
+                   "note": "one epoch per call incl. the call's copies in and out of its buffers"}
     # end to end from pinned host memory: the calls copy the lists in
     torch.cuda.synchronize(dev)
     w0 = time.perf_counter()
@@ -517,7 +539,7 @@ def run_assoc(args):
                        "slots_per_step": len(slot_offs) - 1, "epochs_per_step": epochs,
                        "l2": f"inputs larger than L2: {n * 32 / 2**30:.2f} GiB of indexes and as much sorted"},
             "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
-            "parity": {"oracle_and_definition": bool(ok)}}
+            "parity": {"oracle_and_definition": bool(ok)}, "prover_sort": prover_sort}
     if not args.no_cpu_baseline:
         secs = time_assoc_oracle(ab[:32 * ASSOC_EPOCH], s.tobytes()[:32 * ASSOC_EPOCH])
         line["cpu_baseline"] = {"value": ASSOC_EPOCH / secs, "unit": ASSOC_UNIT, "cores": 1, "kind": "oracle",
