@@ -26,6 +26,7 @@ namespace sisu {
 
 constexpr int kSortBD = 256;
 constexpr uint32_t kSortTilesPerSM = 8;
+constexpr uint64_t kSortMinTile = 2048;
 
 __device__ __forceinline__ uint32_t key_byte(const Fr& x, uint32_t d) { return (x.v[d >> 2] >> (8 * (d & 3))) & 0xffu; }
 
@@ -162,7 +163,10 @@ extern "C" int sisu_sort_elements(const uint8_t* in, uint64_t n, int on_device, 
   if (n == 0) return SISU_OK;
   cudaStream_t st = (cudaStream_t)stream;
   const size_t bytes = (size_t)n * 32;
-  const uint32_t G = (uint32_t)std::min<uint64_t>((n + kSortBD - 1) / kSortBD, (uint64_t)kSMs * kSortTilesPerSM);
+  // tiles of at least kSortMinTile elements (fewer counts for the single-CTA
+  // scan), at most kSortTilesPerSM per SM
+  const uint32_t G = (uint32_t)std::max<uint64_t>(
+      1, std::min<uint64_t>((n + kSortMinTile - 1) / kSortMinTile, (uint64_t)kSMs * kSortTilesPerSM));
   const uint64_t tile = (n + G - 1) / G;
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   // two element buffers, the counts, the flag words
