@@ -317,9 +317,10 @@ int sisu_statement_digest_noalloc(const uint8_t* data, size_t len, uint8_t* out,
  * inlined, kind 4 = 32x32+64-bit mad.wide chains, kind 5 = Montgomery
  * products built from 64-bit partial products (mul.wide), kind 6 = kinds 2
  * and 5 run side by side on the same operands, kind 7 = full 512-bit
- * products added into one 544-bit accumulator (no reduction).  Reports the
- * elapsed milliseconds and the number of operations (multiply-adds, or
- * field products for kinds 2, 3, 5 and 7); for kind 6, *ops is minus the number of
+ * products added into one 544-bit accumulator (no reduction), kind 8 =
+ * Montgomery squares by the squaring routine.  Reports the elapsed
+ * milliseconds and the number of operations (multiply-adds, or field
+ * products for kinds 2, 3, 5, 7 and 8); for kind 6, *ops is minus the number of
  * threads whose two products disagreed (0 when they all agree). */
 int sisu_microbench(int kind, uint32_t blocks, uint32_t threads, uint32_t iters, void* stream,
                     double* ms, double* ops);

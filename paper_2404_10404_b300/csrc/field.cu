@@ -235,6 +235,20 @@ __global__ void k_mb_frmac(uint32_t iters, uint32_t* sink) {
   sink[blockIdx.x * blockDim.x + threadIdx.x] = o;
 }
 
+// Montgomery squares (the squaring routine), two chains a thread
+__global__ void k_mb_frsqr(uint32_t iters, uint32_t* sink) {
+  Fr x = fr_one(), z = fr_r2();
+  x.v[0] ^= threadIdx.x;
+  for (uint32_t it = 0; it < iters; ++it) {
+    x = fr_sqr(x);
+    z = fr_sqr(z);
+  }
+  uint32_t o = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) o ^= x.v[i] ^ z.v[i];
+  sink[blockIdx.x * blockDim.x + threadIdx.x] = o;
+}
+
 __global__ void k_mb_madwide(uint32_t iters, uint32_t mul, uint32_t* sink) {
   unsigned long long x[8];
 #pragma unroll
@@ -271,6 +285,7 @@ int run_microbench(int kind, uint32_t blocks, uint32_t threads, uint32_t iters, 
     else if (kind == 4) k_mb_madwide<<<blocks, threads, 0, st>>>(iters, 0x9e3779b9u, sink);
     else if (kind == 5) k_mb_frmul_wide<<<blocks, threads, 0, st>>>(iters, sink);
     else if (kind == 7) k_mb_frmac<<<blocks, threads, 0, st>>>(iters, sink);
+    else if (kind == 8) k_mb_frsqr<<<blocks, threads, 0, st>>>(iters, sink);
     else k_mb_frmul_check<<<blocks, threads, 0, st>>>(iters, sink);
     launches_add(1);
   };
@@ -293,7 +308,7 @@ int run_microbench(int kind, uint32_t blocks, uint32_t threads, uint32_t iters, 
     cudaFree(sink);
     return (int)e;
   }
-  double per = (kind == 2 || kind == 3 || kind == 5 || kind == 7) ? 2.0 : kind == 6 ? 2.0 : 64.0;
+  double per = (kind == 2 || kind == 3 || kind == 5 || kind == 7 || kind == 8) ? 2.0 : kind == 6 ? 2.0 : 64.0;
   *ops = (double)blocks * threads * iters * per;
   cudaEventDestroy(a);
   cudaEventDestroy(b);

@@ -92,7 +92,7 @@ def test_device_digest_vs_oracle(S, oracle, n):
 
 
 def test_microbench_runs(S):
-    for kind in (0, 1, 2, 3, 4, 5, 7):
+    for kind in (0, 1, 2, 3, 4, 5, 7, 8):
         ms, ops = S.microbench(kind, 148, 256, 64)
         assert ms > 0 and ops > 0
 
