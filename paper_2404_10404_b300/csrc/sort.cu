@@ -6,8 +6,10 @@
 // one byte a pass, skipping every byte on which all elements agree (found
 // by one pass over the list first): validator indexes below 2^21 take three
 // passes, uniform field elements all 32.  A pass is a per-CTA histogram of
-// the byte over contiguous tiles, one exclusive scan of the counts in
-// (byte value, tile) order, and a stable scatter: each CTA walks its tile
+// the byte over contiguous tiles (stored tile-major, so that both the
+// histogram's writes and the scan's walks down a byte value's column are
+// coalesced), one exclusive scan of the counts in (byte value, tile) order,
+// and a stable scatter: each CTA walks its tile
 // in chunks of 256, ranks equal bytes inside a warp with a match mask and
 // across warps with per-warp counts in shared memory.  Stability across
 // passes is what makes the byte-at-a-time order the full order.
@@ -27,6 +29,7 @@ namespace sisu {
 constexpr int kSortBD = 256;
 constexpr uint32_t kSortTilesPerSM = 8;
 constexpr uint64_t kSortMinTile = 2048;
+static_assert(kSortBD == 256, "one thread per byte value in the histogram and the scatter");
 
 __device__ __forceinline__ uint32_t key_byte(const Fr& x, uint32_t d) { return (x.v[d >> 2] >> (8 * (d & 3))) & 0xffu; }
 
@@ -54,7 +57,7 @@ __global__ void k_sort_varying(const uint32_t* __restrict__ a, uint64_t n, uint3
   }
 }
 
-// cnt[v * G + c] = elements of tile c whose byte d is v
+// cnt[c * 256 + v] = elements of tile c whose byte d is v
 __global__ void __launch_bounds__(kSortBD) k_sort_hist(const uint32_t* __restrict__ a, uint64_t n, uint64_t tile,
                                                        uint32_t d, uint32_t* __restrict__ cnt) {
   __shared__ uint32_t h[256];
@@ -63,32 +66,59 @@ __global__ void __launch_bounds__(kSortBD) k_sort_hist(const uint32_t* __restric
   const uint64_t b = blockIdx.x * tile, e = min(n, b + tile);
   for (uint64_t i = b + threadIdx.x; i < e; i += kSortBD) atomicAdd(&h[key_byte(fr_load(a, i), d)], 1u);
   __syncthreads();
-  cnt[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
+  cnt[(size_t)blockIdx.x * 256 + threadIdx.x] = h[threadIdx.x];
 }
 
-// in-place exclusive scan of m counts (one CTA of 1024 threads)
-__global__ void __launch_bounds__(1024) k_sort_scan(uint32_t* __restrict__ c, uint32_t m) {
-  __shared__ uint32_t part[1024];
-  const uint32_t per = (m + 1023) / 1024, b = threadIdx.x * per, e = min(m, b + per);
+// In-place exclusive scan of the G x 256 tile-major counts in (byte value,
+// tile) order, by one CTA of 1024 threads: thread (q, v) owns byte value v
+// over the q-th quarter of the tiles.  Its column sum, the per-value
+// totals' exclusive scan over v, then the running offsets written back.
+// A warp reads 32 consecutive counts of one tile per load.
+constexpr int kScanBatch = 8;  // loads in flight per thread
+__global__ void __launch_bounds__(1024) k_sort_scan(uint32_t* __restrict__ c, uint32_t G) {
+  __shared__ uint32_t part[4][256];  // column sum of value v over quarter q
+  __shared__ uint32_t vbase[256];    // elements of byte value below v
+  __shared__ uint32_t wsum[8];
+  const uint32_t v = threadIdx.x & 255u, q = threadIdx.x >> 8;
+  const uint32_t per = (G + 3) / 4, t0 = min(G, q * per), t1 = min(G, t0 + per);
   uint32_t s = 0;
-  for (uint32_t i = b; i < e; ++i) s += c[i];
-  part[threadIdx.x] = s;
-  __syncthreads();
-  for (uint32_t off = 1; off < 1024; off <<= 1) {  // inclusive scan of the thread sums
-    const uint32_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
-    __syncthreads();
-    part[threadIdx.x] += v;
-    __syncthreads();
+  for (uint32_t t = t0; t < t1; t += kScanBatch) {
+    uint32_t x[kScanBatch];
+#pragma unroll
+    for (int u = 0; u < kScanBatch; ++u) x[u] = t + u < t1 ? c[(size_t)(t + u) * 256 + v] : 0u;
+#pragma unroll
+    for (int u = 0; u < kScanBatch; ++u) s += x[u];
   }
-  uint32_t run = threadIdx.x ? part[threadIdx.x - 1] : 0u;
-  for (uint32_t i = b; i < e; ++i) {
-    const uint32_t v = c[i];
-    c[i] = run;
-    run += v;
+  part[q][v] = s;
+  __syncthreads();
+  if (threadIdx.x < 256) {  // exclusive scan of the totals over v
+    const uint32_t tot = part[0][v] + part[1][v] + part[2][v] + part[3][v];
+    uint32_t x = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if ((v & 31u) >= (uint32_t)o) x += y;
+    }
+    if ((v & 31u) == 31u) wsum[v >> 5] = x;
+    vbase[v] = x - tot;
+  }
+  __syncthreads();
+  uint32_t run = vbase[v];
+  for (uint32_t w = 0; w < (v >> 5); ++w) run += wsum[w];
+  for (uint32_t p = 0; p < q; ++p) run += part[p][v];
+  for (uint32_t t = t0; t < t1; t += kScanBatch) {
+    uint32_t x[kScanBatch];
+#pragma unroll
+    for (int u = 0; u < kScanBatch; ++u) x[u] = t + u < t1 ? c[(size_t)(t + u) * 256 + v] : 0u;
+#pragma unroll
+    for (int u = 0; u < kScanBatch; ++u) {
+      if (t + u < t1) c[(size_t)(t + u) * 256 + v] = run;
+      run += x[u];
+    }
   }
 }
 
-// stable scatter of tile c by byte d to dst[off[v * G + c] + rank]
+// stable scatter of tile c by byte d to dst[off[c * 256 + v] + rank]
 __global__ void __launch_bounds__(kSortBD) k_sort_scatter(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst,
                                                           uint64_t n, uint64_t tile, uint32_t d,
                                                           const uint32_t* __restrict__ off) {
@@ -96,7 +126,7 @@ __global__ void __launch_bounds__(kSortBD) k_sort_scatter(const uint32_t* __rest
   __shared__ uint32_t base[256];     // tile offset of byte value v plus the elements placed so far
   __shared__ uint32_t wcnt[NW][256];  // elements of byte value v in warp w of the current chunk
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  base[threadIdx.x] = off[(size_t)threadIdx.x * gridDim.x + blockIdx.x];
+  base[threadIdx.x] = off[(size_t)blockIdx.x * 256 + threadIdx.x];
   const uint64_t b = blockIdx.x * tile, e = min(n, b + tile);
   for (uint64_t c0 = b; c0 < e; c0 += kSortBD) {  // uniform over the block
 #pragma unroll
@@ -193,7 +223,7 @@ extern "C" int sisu_sort_elements(const uint8_t* in, uint64_t n, int on_device, 
     k_sort_hist<<<G, kSortBD, 0, st>>>(A, n, tile, d, cnt);
     rc = post_launch();
     if (!rc) {
-      k_sort_scan<<<1, 1024, 0, st>>>(cnt, 256 * G);
+      k_sort_scan<<<1, 1024, 0, st>>>(cnt, G);
       rc = post_launch();
     }
     if (!rc) {
