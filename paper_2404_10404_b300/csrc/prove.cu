@@ -525,22 +525,130 @@ __device__ __forceinline__ Fr copy_items(const uint32_t* __restrict__ T, uint32_
   return tot;  // E's factor 2^32 has cancelled the reductions' 2^-32
 }
 
+// The round's items of the big rounds (more pairs than CTAs, m = 0), split
+// further: each warp of CTA `bid` owns a contiguous 1/NW of the CTA's cost
+// range, sums every pair segment it touches with warp shuffles and weights
+// it by E_t(j) itself, so the CTA meets no block barrier per segment (in
+// the CTA-wide form every segment ended in a block reduction, where warps
+// that finished early waited).  Returns, in lanes t < 4 of every warp, the
+// warp's share of g(t) (plain, below 2r); sh_e: this warp's 16 words.
 template <int BD>
+__device__ __forceinline__ Fr copy_items_warp(const uint32_t* __restrict__ T, uint32_t sn, uint32_t h,
+                                              const uint32_t* __restrict__ E, const uint32_t* __restrict__ om,
+                                              const uint4* __restrict__ sg, uint32_t nmul, uint32_t ntot,
+                                              uint64_t per_cta, uint32_t m, uint32_t bid, uint32_t* sh_e) {
+  constexpr int NW = BD / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint64_t pair_cost = copy_pair_cost(nmul, ntot);
+  uint64_t c0, c1;  // the CTA's cost range
+  if (m) {  // range `sub` of the m inside pair j
+    const uint32_t j = bid / m, sub = bid - j * m;
+    c0 = (uint64_t)j * pair_cost + min(pair_cost, (uint64_t)sub * per_cta);
+    c1 = (uint64_t)j * pair_cost + min(pair_cost, (uint64_t)(sub + 1) * per_cta);
+  } else {
+    const uint64_t total_cost = (uint64_t)h * pair_cost;
+    c0 = min(total_cost, (uint64_t)bid * per_cta);
+    c1 = min(total_cost, c0 + per_cta);
+  }
+  const uint64_t q0 = item_at_cost(c0 + (c1 - c0) * warp / NW, nmul, ntot, pair_cost);
+  const uint64_t q1 = item_at_cost(c0 + (c1 - c0) * (warp + 1) / NW, nmul, ntot, pair_cost);
+  uint32_t j = (uint32_t)(q0 / ntot);
+  Fr tot = fr_zero();  // lane t < 4: sum over segments of E_t(j) S_j(t)
+  for (uint64_t seg = q0; seg < q1; ++j) {  // one segment per pair, pairs in order
+    const uint64_t segend = min(q1, (uint64_t)(j + 1) * ntot);
+    if (lane < 4) {  // E(j) -> sh_e[0..7], E(j + h) -> sh_e[8..15], 16 bytes a lane
+      __syncwarp(0xfu);  // the previous segment's reads of sh_e are done
+      const uint32_t* src = E + 8 * (size_t)(lane < 2 ? j : j + h) + 4 * (lane & 1);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n\tcp.async.commit_group;" ::"r"(
+                       (uint32_t)__cvta_generic_to_shared(sh_e + 4 * lane)),
+                   "l"(src)
+                   : "memory");
+    }
+    const uint32_t g0 = (uint32_t)(seg - (uint64_t)j * ntot), g1 = (uint32_t)(segend - (uint64_t)j * ntot);
+    const uint32_t* lo = T + (((size_t)j << sn) << 3);
+    const uint32_t* hi = T + (((size_t)(j + h) << sn) << 3);
+    FrAcc a0 = fracc_zero(), a1 = fracc_zero(), ac = fracc_zero();
+    for (uint32_t q = g0 + lane; q < g1; q += 32) {
+      const uint4 gi = sg[q];
+      const Fr w = fr_load(om, q);
+      const Fr x0 = fr_load(lo, gi.x), x1 = fr_load(hi, gi.x);
+      const Fr y0 = fr_load(lo, gi.y), y1 = fr_load(hi, gi.y);
+      if (q < nmul) {
+        const Fr wx0 = fr_mul(w, x0), wx1 = fr_mul(w, x1);
+        fracc_mac(a0, wx0, y0);
+        fracc_mac(a1, wx1, y1);
+        fracc_mac(ac, fr_sub(wx1, wx0), fr_sub(y1, y0));
+      } else {
+        fracc_mac(a0, w, fr_add(x0, y0));
+        fracc_mac(a1, w, fr_add(x1, y1));
+      }
+    }
+    Fr sj[3] = {fr_redc288(a0), fr_redc288(a1), fr_redc288(ac)};
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      sj[t] = fr_warp_sum(sj[t]);  // lane 0: 2^-32 (S_j(0), S_j(1), c_j) over this warp's items
+#pragma unroll
+      for (int i = 0; i < 8; ++i) sj[t].v[i] = __shfl_sync(0xffffffffu, sj[t].v[i], 0);
+    }
+    if (lane < 4) {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+      __syncwarp(0xfu);  // every lane sees all four copies
+      Fr e0, e1;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        e0.v[i] = sh_e[i];
+        e1.v[i] = sh_e[8 + i];
+      }
+      const Fr de = fr_sub(e1, e0);
+      Fr et = e0, st;
+      const Fr d = fr_sub(sj[1], sj[0]);
+      if (lane == 2) {
+        st = fr_add(fr_add(sj[1], d), fr_dbl(sj[2]));  // S(1) + (S(1) - S(0)) + 2c
+      } else if (lane == 3) {
+        st = fr_add(sj[1], fr_dbl(fr_add(d, fr_add(sj[2], fr_dbl(sj[2])))));  // S(1) + 2 (S(1) - S(0) + 3c)
+      } else {
+        st = lane == 0 ? sj[0] : sj[1];
+      }
+      for (int t = 0; t < lane; ++t) et = fr_add(et, de);
+      tot = fr_add(tot, fr_mul(et, st));
+    }
+    seg = segend;
+  }
+  return tot;  // E's factor 2^32 has cancelled the reductions' 2^-32
+}
+
+// kWarp: the big rounds' form (m = 0, segments per warp); else the CTA-wide
+// form (any split; used for m > 0).
+template <int BD, bool kWarp>
 __global__ void __launch_bounds__(BD) k_copy_round(const uint32_t* __restrict__ T, uint32_t sn, uint32_t h,
                                                    const uint32_t* __restrict__ E, const uint32_t* __restrict__ om,
                                                    const uint4* __restrict__ sg, uint32_t nmul, uint32_t ntot,
                                                    uint64_t per_cta, uint32_t m, uint32_t* partials, DevState* S,
                                                    uint8_t* proof, size_t off, uint32_t k) {
   pdl_wait();
-  __shared__ __align__(16) uint32_t sh_e[16];  // E(j), E(j + h) of the current segment
+  __shared__ __align__(16) uint32_t sh_e[BD / 32][16];  // E(j), E(j + h) of a warp's current segment
   if (threadIdx.x == BD - 32) warm_transcript_code(k, h);
-  const Fr tot = copy_items<BD>(T, sn, h, E, om, sg, nmul, ntot, per_cta, m, blockIdx.x, sh_e);
-  Fr acc[4];
+  Fr acc[4];  // thread 0: the CTA's share of g(0..3)
+  if (!kWarp) {  // the CTA-wide form: lanes t < 4 of warp 0
+    const Fr tot = copy_items<BD>(T, sn, h, E, om, sg, nmul, ntot, per_cta, m, blockIdx.x, sh_e[0]);
 #pragma unroll
-  for (int t = 0; t < 4; ++t) {
+    for (int t = 0; t < 4; ++t) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) acc[t].v[i] = __shfl_sync(0xffffffffu, tot.v[i], t);
-    if (threadIdx.x != 0) acc[t] = fr_zero();
+      for (int i = 0; i < 8; ++i) acc[t].v[i] = __shfl_sync(0xffffffffu, tot.v[i], t);
+      if (threadIdx.x != 0) acc[t] = fr_zero();
+    }
+  } else {  // segments per warp, then the warps' sums by a shuffle tree in warp 0
+    __shared__ Fr wtot[BD / 32][4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const Fr tot = copy_items_warp<BD>(T, sn, h, E, om, sg, nmul, ntot, per_cta, m, blockIdx.x, sh_e[warp]);
+    if (lane < 4) wtot[warp][lane] = tot;
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      acc[t] = warp == 0 && lane < BD / 32 ? wtot[lane][t] : fr_zero();
+      if (warp == 0) acc[t] = fr_warp_sum(acc[t]);
+      if (threadIdx.x != 0) acc[t] = fr_zero();
+    }
   }
   if (grid_sum_last_block<BD, 4, true>(acc, partials, S) && threadIdx.x < 32)
     round_finalize<4>(S, acc, proof, off, &S->rb[k]);
@@ -557,14 +665,18 @@ int launch_copy_round(const uint32_t* T, uint32_t sn, uint32_t h, const uint32_t
   static int per_sm = 0;
   if (per_sm == 0) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_copy_round<BD>, BD, 0) != cudaSuccess || n < 1) n = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_copy_round<BD, false>, BD, 0) != cudaSuccess || n < 1)
+      n = 1;
     per_sm = n;
   }
   // contiguous ranges of equal cost: one wave of CTAs, and for small rounds
   // about one item per thread (short serial chains)
   const CopySplit sp = copy_split(h, L.nmul, L.ntot, std::min<uint32_t>(kSMs * per_sm, kMaxPartials), BD);
-  return launch_pdl(k_copy_round<BD>, sp.nc, BD, st, T, sn, h, E, omega_s, L.sgate, L.nmul, L.ntot, sp.per_cta, sp.m,
-                    partials, S, proof, off, k);
+  if (sp.m == 0)  // more pairs than CTAs: segments per warp
+    return launch_pdl(k_copy_round<BD, true>, sp.nc, BD, st, T, sn, h, E, omega_s, L.sgate, L.nmul, L.ntot,
+                      sp.per_cta, sp.m, partials, S, proof, off, k);
+  return launch_pdl(k_copy_round<BD, false>, sp.nc, BD, st, T, sn, h, E, omega_s, L.sgate, L.nmul, L.ntot,
+                    sp.per_cta, sp.m, partials, S, proof, off, k);
 }
 
 // fold of the copy rows and of E by the round's challenge r = r_b[k]:
