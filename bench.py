@@ -51,7 +51,7 @@ FR_P = 0x30644E72E131A029B85045B68181585D2833E84879B9709143E1F593F0000001
 # rounds of a medium layer (every layer has the same shape, so this is the
 # mean over all 200 launches of a step); None when not captured for the
 # current build of the kernel.
-DOMINANT_TRAFFIC_BYTES = 29.90e6
+DOMINANT_TRAFFIC_BYTES = 39.0e6
 
 
 def log(*a):
