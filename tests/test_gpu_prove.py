@@ -66,6 +66,8 @@ def test_micro_parity(S, oracle, C, widths, pct):
     (2, [2048, 8], 50),                 # fan-in from a narrow layer
     (256, [16, 2048, 16], 50),
     (512, [1024] * 4, 100), (512, [1024] * 4, 0),
+    (2048, [3, 5, 2], 50),              # many pairs a warp: segments of a few gates each
+    (600, [70, 33, 9], 40),             # padded copies, more pairs than CTAs, ragged segments
 ])
 def test_shapes_parity(S, oracle, C, widths, pct):
     _case(S, oracle, synth.micro(11, C, widths, pct))
