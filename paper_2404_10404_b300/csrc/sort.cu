@@ -8,8 +8,9 @@
 // passes, uniform field elements all 32.  A pass is a per-CTA histogram of
 // the byte over contiguous tiles (stored tile-major, so that both the
 // histogram's writes and the scan's walks down a byte value's column are
-// coalesced), one exclusive scan of the counts in (byte value, tile) order,
-// and a stable scatter: each CTA walks its tile
+// coalesced; the per-value totals added atomically), one exclusive scan of
+// the counts in (byte value, tile) order by one CTA per byte value, and a
+// stable scatter: each CTA walks its tile
 // in chunks of 256, ranks equal bytes inside a warp with a match mask and
 // across warps with per-warp counts in shared memory.  Stability across
 // passes is what makes the byte-at-a-time order the full order.
@@ -57,9 +58,11 @@ __global__ void k_sort_varying(const uint32_t* __restrict__ a, uint64_t n, uint3
   }
 }
 
-// cnt[c * 256 + v] = elements of tile c whose byte d is v
+// cnt[c * 256 + v] = elements of tile c whose byte d is v; tot[v] += the
+// tile's count (tot zero before the pass)
 __global__ void __launch_bounds__(kSortBD) k_sort_hist(const uint32_t* __restrict__ a, uint64_t n, uint64_t tile,
-                                                       uint32_t d, uint32_t* __restrict__ cnt) {
+                                                       uint32_t d, uint32_t* __restrict__ cnt,
+                                                       uint32_t* __restrict__ tot) {
   __shared__ uint32_t h[256];
   h[threadIdx.x] = 0;
   __syncthreads();
@@ -67,55 +70,43 @@ __global__ void __launch_bounds__(kSortBD) k_sort_hist(const uint32_t* __restric
   for (uint64_t i = b + threadIdx.x; i < e; i += kSortBD) atomicAdd(&h[key_byte(fr_load(a, i), d)], 1u);
   __syncthreads();
   cnt[(size_t)blockIdx.x * 256 + threadIdx.x] = h[threadIdx.x];
+  if (h[threadIdx.x]) atomicAdd(&tot[threadIdx.x], h[threadIdx.x]);
 }
 
 // In-place exclusive scan of the G x 256 tile-major counts in (byte value,
-// tile) order, by one CTA of 1024 threads: thread (q, v) owns byte value v
-// over the q-th quarter of the tiles.  Its column sum, the per-value
-// totals' exclusive scan over v, then the running offsets written back.
-// A warp reads 32 consecutive counts of one tile per load.
-constexpr int kScanBatch = 8;  // loads in flight per thread
-__global__ void __launch_bounds__(1024) k_sort_scan(uint32_t* __restrict__ c, uint32_t G) {
-  __shared__ uint32_t part[4][256];  // column sum of value v over quarter q
-  __shared__ uint32_t vbase[256];    // elements of byte value below v
-  __shared__ uint32_t wsum[8];
-  const uint32_t v = threadIdx.x & 255u, q = threadIdx.x >> 8;
-  const uint32_t per = (G + 3) / 4, t0 = min(G, q * per), t1 = min(G, t0 + per);
+// tile) order: CTA v (one per byte value, 256 threads) starts from the
+// elements of smaller byte values (the totals tot[0..v-1]) and scans its
+// value's column over the tiles, a few consecutive tiles a thread.  CTA 0
+// also clears tot_next, the totals of the next pass.
+__global__ void __launch_bounds__(256) k_sort_scan(uint32_t* __restrict__ c, uint32_t G,
+                                                   const uint32_t* __restrict__ tot, uint32_t* __restrict__ tot_next) {
+  __shared__ uint32_t wbase[8], wscan[8];
+  const uint32_t v = blockIdx.x, lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const uint32_t below = __reduce_add_sync(0xffffffffu, threadIdx.x < v ? tot[threadIdx.x] : 0u);
+  if (lane == 0) wbase[warp] = below;
+  const uint32_t per = (G + 255) / 256, t0 = min(G, threadIdx.x * per), t1 = min(G, t0 + per);
   uint32_t s = 0;
-  for (uint32_t t = t0; t < t1; t += kScanBatch) {
-    uint32_t x[kScanBatch];
+  for (uint32_t t = t0; t < t1; ++t) s += c[(size_t)t * 256 + v];
+  uint32_t incl = s;  // inclusive scan of the thread sums: in the warp, then over the warps
 #pragma unroll
-    for (int u = 0; u < kScanBatch; ++u) x[u] = t + u < t1 ? c[(size_t)(t + u) * 256 + v] : 0u;
-#pragma unroll
-    for (int u = 0; u < kScanBatch; ++u) s += x[u];
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= (uint32_t)o) incl += y;
   }
-  part[q][v] = s;
+  if (lane == 31) wscan[warp] = incl;
   __syncthreads();
-  if (threadIdx.x < 256) {  // exclusive scan of the totals over v
-    const uint32_t tot = part[0][v] + part[1][v] + part[2][v] + part[3][v];
-    uint32_t x = tot;
+  uint32_t run = incl - s;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if ((v & 31u) >= (uint32_t)o) x += y;
-    }
-    if ((v & 31u) == 31u) wsum[v >> 5] = x;
-    vbase[v] = x - tot;
+  for (int w = 0; w < 8; ++w) {
+    run += wbase[w];
+    if ((uint32_t)w < warp) run += wscan[w];
   }
-  __syncthreads();
-  uint32_t run = vbase[v];
-  for (uint32_t w = 0; w < (v >> 5); ++w) run += wsum[w];
-  for (uint32_t p = 0; p < q; ++p) run += part[p][v];
-  for (uint32_t t = t0; t < t1; t += kScanBatch) {
-    uint32_t x[kScanBatch];
-#pragma unroll
-    for (int u = 0; u < kScanBatch; ++u) x[u] = t + u < t1 ? c[(size_t)(t + u) * 256 + v] : 0u;
-#pragma unroll
-    for (int u = 0; u < kScanBatch; ++u) {
-      if (t + u < t1) c[(size_t)(t + u) * 256 + v] = run;
-      run += x[u];
-    }
+  for (uint32_t t = t0; t < t1; ++t) {
+    const uint32_t x = c[(size_t)t * 256 + v];
+    c[(size_t)t * 256 + v] = run;
+    run += x;
   }
+  if (v == 0) tot_next[threadIdx.x] = 0;
 }
 
 // stable scatter of tile c by byte d to dst[off[c * 256 + v] + rank]
@@ -202,14 +193,15 @@ extern "C" int sisu_sort_elements(const uint8_t* in, uint64_t n, int on_device, 
   // two element buffers, the counts, the flag words
   SortBuf buf;
   buf.st = st;
-  SCK(cudaMallocAsync(&buf.p, 2 * al(bytes) + al((size_t)256 * G * 4) + 256, st), "cudaMallocAsync");
+  SCK(cudaMallocAsync(&buf.p, 2 * al(bytes) + al((size_t)256 * G * 4) + 256 + 2048, st), "cudaMallocAsync");
   uint8_t* p = (uint8_t*)buf.p;
   uint32_t* A = (uint32_t*)p;
   uint32_t* B = (uint32_t*)(p + al(bytes));
   uint32_t* cnt = (uint32_t*)(p + 2 * al(bytes));
   uint32_t* flags = (uint32_t*)(p + 2 * al(bytes) + al((size_t)256 * G * 4));
+  uint32_t* tot = flags + 64;  // two sets of 256 per-value totals, by pass parity
   SCK(cudaMemcpyAsync(A, in, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st), "copy in");
-  SCK(cudaMemsetAsync(flags, 0, 8, st), "memset");
+  SCK(cudaMemsetAsync(flags, 0, 256 + 1024, st), "memset");  // the flags and the first pass's totals
   k_sort_varying<<<grid_for(n, kSortBD, 8), kSortBD, 0, st>>>(A, n, flags, flags + 1);
   int rc = post_launch();
   if (rc) return sort_err((cudaError_t)rc, "sort");
@@ -220,10 +212,12 @@ extern "C" int sisu_sort_elements(const uint8_t* in, uint64_t n, int on_device, 
   uint32_t np = 0;
   for (uint32_t d = 0; d < 32; ++d) {
     if (!((hflags[0] >> d) & 1u)) continue;  // every element has the same byte d
-    k_sort_hist<<<G, kSortBD, 0, st>>>(A, n, tile, d, cnt);
+    uint32_t* tot_cur = tot + 256 * (np & 1u);
+    uint32_t* tot_nxt = tot + 256 * ((np + 1u) & 1u);
+    k_sort_hist<<<G, kSortBD, 0, st>>>(A, n, tile, d, cnt, tot_cur);
     rc = post_launch();
     if (!rc) {
-      k_sort_scan<<<1, 1024, 0, st>>>(cnt, G);
+      k_sort_scan<<<256, 256, 0, st>>>(cnt, G, tot_cur, tot_nxt);
       rc = post_launch();
     }
     if (!rc) {
