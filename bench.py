@@ -45,7 +45,6 @@ UNIT = "gates/s"
 SMS, IMAD_PER_SM_CLK, SM_MAX_MHZ = 148, 64, 2032.0
 IMAD_PER_FR_MUL = 264
 ALU_PEAK_TIMAD = SMS * IMAD_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
-FR_P = 0x30644E72E131A029B85045B68181585D2833E84879B9709143E1F593F0000001
 # DRAM traffic (read + write bytes) per launch of the dominant kernel from
 # an ncu capture (profiles/copy_round_medium.md): the mean over the ten copy
 # rounds of a medium layer (every layer has the same shape, so this is the
@@ -381,7 +380,8 @@ def assoc_inputs(epochs: int):
 
 def assoc_describe(epochs: int) -> str:
     return (f"assoc: {epochs} epochs x 2^20 validator indexes (distinct, below 2^21, seeded order), "
-            f"hash of every slot list of 2^15 (Algorithm 1), Algorithm 2 on every epoch against its sorted list")
+            f"hash of every slot list of 2^15 (Algorithm 1), Algorithm 2 on every epoch against its sorted list "
+            f"(the epoch's hash of the list as the sum of its slots' hashes)")
 
 
 def time_assoc_oracle(a_bytes: bytes, s_bytes: bytes):
@@ -435,28 +435,28 @@ def run_assoc(args):
     host_s = torch.from_numpy(s.view(np.uint8).reshape(-1)).pin_memory()
     da, ds = host_a.to(dev), host_s.to(dev)
     slot_offs = np.arange(0, n + 1, ASSOC_SLOT, dtype=np.uint64)
-    epoch_offs = np.arange(0, n + 1, ASSOC_EPOCH, dtype=np.uint64)
     stream = torch.cuda.Stream(device=dev)
     st = stream.cuda_stream
 
-    def step(xa, xs):
-        h = S.assoc_hash_segments(xa, slot_offs, stream=st)
-        res, ha, hs = S.pairwise_distinct_check_segments(xa, xs, epoch_offs, stream=st)
-        return h, res, ha
+    per = ASSOC_EPOCH // ASSOC_SLOT
 
-    h, res, ha = step(da, ds)
+    def step(xa, xs):
+        # every slot's hash (Algorithm 1) and Algorithm 2 on every epoch, the
+        # epoch's hash of A being the sum of its slots' hashes (AH is a sum)
+        return S.assoc_epochs(xa, xs, slot_offs, per, stream=st)
+
+    h, res, ha, hs = step(da, ds)
     # parity: every epoch's indexes are distinct (Algorithm 2 must accept
-    # each), two slot hashes and one epoch hash against the oracle, and each
-    # epoch's hash is the sum of its slots' hashes
+    # each); two slot hashes and the first epoch's hashes of A and of A*
+    # against the oracle; each epoch's hash of A* equals its hash of A
     o = Oracle()
     ab = a.tobytes()
     ok = all(r == 1 for r in res)
     for g in (0, len(slot_offs) - 2):
         ok &= h[g] == o.assoc_hash(ab[32 * g * ASSOC_SLOT:32 * (g + 1) * ASSOC_SLOT])
     ok &= ha[0] == o.assoc_hash(ab[:32 * ASSOC_EPOCH])
-    per = ASSOC_EPOCH // ASSOC_SLOT
-    ok &= all(sum(int.from_bytes(x, "little") for x in h[e * per:(e + 1) * per]) % FR_P
-              == int.from_bytes(ha[e], "little") for e in range(epochs))
+    ok &= hs[0] == o.assoc_hash(s.tobytes()[:32 * ASSOC_EPOCH])
+    ok &= all(ha[e] == hs[e] for e in range(epochs))
     for _ in range(max(0, args.warmup - 1)):
         step(da, ds)
     uuid = None
@@ -486,11 +486,11 @@ def run_assoc(args):
     torch.cuda.synchronize(dev)
     kern = {}
     for kind, name in ((S.PROF_ASSOC_HASH, "k_assoc_chunks (slot hashes)"),
-                       (S.PROF_ASSOC_PAIR, "pairwise-distinct check (k_assoc_chunks on A and A*, k_order_chunks)")):
+                       (S.PROF_ASSOC_PAIR, "pairwise-distinct check (k_assoc_chunks on A*, k_order_chunks)")):
         kms, kn, kf = S.profile_read(kind)
         kern[name] = (kms, kn, kf)
     S.profile_enable(0)
-    # the dominant kernel is k_assoc_chunks (three of the step's four
+    # the dominant kernel is k_assoc_chunks (two of the step's three
     # launches); the slot-hash scope times exactly one launch of it
     dom = "k_assoc_chunks (slot hashes)"
     kms, kn, kf = kern[dom]
@@ -534,7 +534,7 @@ def run_assoc(args):
     for _ in range(args.steps):
         step(host_a, host_s)
     e2e_s = time.perf_counter() - w0
-    e2e = {"value": args.steps * n / e2e_s, "unit": ASSOC_UNIT, "h2d_bytes_per_step": 3 * 32 * n,
+    e2e = {"value": args.steps * n / e2e_s, "unit": ASSOC_UNIT, "h2d_bytes_per_step": 2 * 32 * n,
            "d2h_bytes_per_step": 32 * (len(slot_offs) - 1) + 68 * epochs}
     line = {"metric": ASSOC_METRIC, "value": args.steps * n / (ms / 1e3), "unit": ASSOC_UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,

@@ -259,6 +259,23 @@ int sisu_pairwise_distinct_check(const uint8_t* a, const uint8_t* a_sorted, uint
 int sisu_pairwise_distinct_check_segments(const uint8_t* a, const uint8_t* a_sorted, const uint64_t* offsets,
                                           uint32_t n_segments, int on_device, void* stream, int* results,
                                           uint8_t* h_a, uint8_t* h_sorted);
+/* Slot hashes and Algorithm 2 per epoch in one call (Sec. 3.4.1-3.4.2):
+ * every slot g (elements [slot_offsets[g], slot_offsets[g+1]) of a) is
+ * hashed by Algorithm 1 into slot_hashes (host, 32 n_slots bytes), and
+ * every epoch e (slots e*slots_per_epoch .. (e+1)*slots_per_epoch - 1, and
+ * the same element range of a_sorted) gets Algorithm 2's answer in
+ * results[e] (host, n_slots / slots_per_epoch ints).  Because AH is a sum
+ * of F over the elements, the epoch's hash of a is the sum (mod r) of its
+ * slots' hashes: a is read once, for the slot hashes, and only a_sorted is
+ * hashed again (with its order check).  The answers equal those of
+ * sisu_pairwise_distinct_check_segments on the epochs.  h_a, h_sorted
+ * (host, 32 bytes an epoch, may be NULL) receive the epoch hashes.  Arrays
+ * and memory kinds as for sisu_assoc_hash_segments; slots_per_epoch must
+ * divide n_slots.  Blocks until done.
+ * Errors: INVALID_ARG, NOT_CANONICAL, CUDA. */
+int sisu_assoc_epochs(const uint8_t* a, const uint8_t* a_sorted, const uint64_t* slot_offsets, uint32_t n_slots,
+                      uint32_t slots_per_epoch, int on_device, void* stream, uint8_t* slot_hashes, int* results,
+                      uint8_t* h_a, uint8_t* h_sorted);
 /* The prover's side of Algorithm 2: `out` receives the n canonical elements
  * of `in` in ascending order (as integers), equal values kept.  in and out
  * are both host or both device memory (on_device; device arrays 16-byte

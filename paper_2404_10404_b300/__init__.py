@@ -35,7 +35,7 @@ ENTRY_POINTS = [
     "sisu_gkr_prove_batch", "sisu_server_create", "sisu_server_submit", "sisu_server_poll",
     "sisu_server_pending", "sisu_server_destroy",
     "sisu_assoc_hash", "sisu_assoc_hash_segments", "sisu_pairwise_distinct_check",
-    "sisu_pairwise_distinct_check_segments", "sisu_sort_elements",
+    "sisu_pairwise_distinct_check_segments", "sisu_sort_elements", "sisu_assoc_epochs",
 ]
 PROF_COPY_ROUND, PROF_COPY_FOLD, PROF_EVAL, PROF_GATE_ROUND, PROF_DIGEST = 0, 1, 2, 3, 4
 PROF_LAYER_INIT, PROF_PHASE_INIT, PROF_TRANSCRIPT, PROF_INPUTS = 5, 6, 7, 8
@@ -108,6 +108,8 @@ def _load():
                                                    ctypes.POINTER(ctypes.c_int), vp, vp], ctypes.c_int),
         "sisu_sort_elements": ([vp, ctypes.c_uint64, ctypes.c_int, vp, vp, ctypes.POINTER(ctypes.c_uint32)],
                                ctypes.c_int),
+        "sisu_assoc_epochs": ([vp, vp, ctypes.POINTER(ctypes.c_uint64), u32, u32, ctypes.c_int, vp, vp,
+                               ctypes.POINTER(ctypes.c_int), vp, vp], ctypes.c_int),
         "sisu_kernel_launches": ([], ctypes.c_uint64),
         "sisu_free": ([vp], None),
         "sisu_last_error": ([], ctypes.c_char_p),
@@ -431,7 +433,7 @@ def assoc_hash_segments(elems, offsets, h_pre: bytes | None = None, stream=None)
     each continued from its 32-byte value in h_pre (concatenated) if given."""
     p, dev, keep = _ptr(elems)
     m = len(offsets) - 1
-    offs = (ctypes.c_uint64 * len(offsets))(*[int(x) for x in offsets])
+    offs, _keep_offs = _u64_offsets(offsets)
     out = ctypes.create_string_buffer(32 * max(1, m))
     pre = None if h_pre is None else ctypes.create_string_buffer(bytes(h_pre), 32 * m)
     _check(_lib.sisu_assoc_hash_segments(p, offs, m, ctypes.cast(pre, ctypes.c_void_p) if pre is not None else None,
@@ -455,6 +457,37 @@ def pairwise_distinct_check(a, a_sorted, n: int | None = None, stream=None):
     return res.value, ha.raw, hs.raw
 
 
+def _u64_offsets(offsets):
+    """Offsets as a C uint64 array: a contiguous numpy uint64 array is passed
+    by pointer (the caller keeps the returned array alive), anything else
+    converted first."""
+    arr = np.ascontiguousarray(np.asarray(offsets), dtype=np.uint64)
+    return arr.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), arr
+
+
+def assoc_epochs(a, a_sorted, slot_offsets, slots_per_epoch: int, stream=None):
+    """Every slot's hash (Algorithm 1) and Algorithm 2 on every epoch of
+    `slots_per_epoch` slots, the epoch's hash of `a` taken as the sum of its
+    slots' hashes: (slot hashes, epoch results, epoch hashes of a, epoch
+    hashes of a_sorted)."""
+    pa, dev, ka = _ptr(a)
+    ps, dev2, ks = _ptr(a_sorted)
+    if dev != dev2:
+        raise ValueError("a and a_sorted must both be host or both be device arrays")
+    m = len(slot_offsets) - 1
+    ne = m // slots_per_epoch if slots_per_epoch else 0
+    offs, _keep_offs = _u64_offsets(slot_offsets)
+    sh = ctypes.create_string_buffer(32 * max(1, m))
+    res = (ctypes.c_int * max(1, ne))()
+    ha, hs = ctypes.create_string_buffer(32 * max(1, ne)), ctypes.create_string_buffer(32 * max(1, ne))
+    _check(_lib.sisu_assoc_epochs(pa, ps, offs, m, slots_per_epoch, dev, _stream(stream),
+                                  ctypes.cast(sh, ctypes.c_void_p), res, ctypes.cast(ha, ctypes.c_void_p),
+                                  ctypes.cast(hs, ctypes.c_void_p)))
+    rsh, ra, rs = sh.raw, ha.raw, hs.raw
+    return ([rsh[32 * g:32 * g + 32] for g in range(m)], list(res)[:ne],
+            [ra[32 * e:32 * e + 32] for e in range(ne)], [rs[32 * e:32 * e + 32] for e in range(ne)])
+
+
 def pairwise_distinct_check_segments(a, a_sorted, offsets, stream=None):
     """Algorithm 2 on every segment: (results, hashes of a, hashes of a_sorted)."""
     pa, dev, ka = _ptr(a)
@@ -462,7 +495,7 @@ def pairwise_distinct_check_segments(a, a_sorted, offsets, stream=None):
     if dev != dev2:
         raise ValueError("a and a_sorted must both be host or both be device arrays")
     m = len(offsets) - 1
-    offs = (ctypes.c_uint64 * len(offsets))(*[int(x) for x in offsets])
+    offs, _keep_offs = _u64_offsets(offsets)
     res = (ctypes.c_int * max(1, m))()
     ha, hs = ctypes.create_string_buffer(32 * max(1, m)), ctypes.create_string_buffer(32 * max(1, m))
     _check(_lib.sisu_pairwise_distinct_check_segments(pa, ps, offs, m, dev, _stream(stream), res,

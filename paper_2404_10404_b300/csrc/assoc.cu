@@ -241,26 +241,53 @@ int cuda_err(cudaError_t e, const char* what) {
 // Hash the segments of `a` (and, with `pair`, of `s`): out receives
 // NV x nseg canonical values (segment-major); with `pair`, seg_unordered[g]
 // = 1 when segment g of `s` is not strictly ascending.
-int assoc_run(const uint8_t* a, const uint8_t* s, bool pair, const uint64_t* offsets, uint32_t nseg,
-              const uint8_t* h_pre, int on_device, cudaStream_t st, uint8_t* out, uint32_t* host_flag,
-              int* seg_unordered) {
-  const int NV = pair ? 2 : 1;
-  const uint64_t n = offsets[nseg];
+// One run of the kernels over a list (and, for `pair`, its claimed sort),
+// in three phases so that two runs can share the device without a host
+// round trip between them: prepare (device buffers, the chunk table and, for
+// host lists, the lists themselves copied in: copies from pageable memory
+// wait for the stream, so both runs copy before either launches), launch,
+// collect (results copied out, one stream synchronisation).
+// pair: hash a and s (out: per segment 64 bytes, a's hash then s's) and
+// check the order of s; otherwise hash a (out: 32 bytes a segment) and,
+// with `order`, check the order of a.  seg_unordered (pair or order): per
+// segment, whether two neighbours are not strictly ascending.
+struct AssocJob {
+  DevBuf buf;
+  std::vector<uint32_t> seg_chunk;
+  uint32_t nseg = 0, nchunks = 0;
+  int NV = 1;
+  bool pair = false, ord = false, pre = false;
+  uint64_t n = 0;
+  const uint8_t* da = nullptr;
+  const uint8_t* ds = nullptr;
+  uint64_t* d_chunks = nullptr;
+  uint32_t *d_seg = nullptr, *d_part = nullptr, *d_pre = nullptr, *d_out = nullptr, *d_flag = nullptr;
+};
+
+int assoc_prepare(AssocJob& j, const uint8_t* a, const uint8_t* s, bool pair, bool order, const uint64_t* offsets,
+                  uint32_t nseg, const uint8_t* h_pre, int on_device, cudaStream_t st) {
+  j.NV = pair ? 2 : 1;
+  j.pair = pair;
+  j.ord = pair || order;
+  j.pre = h_pre != nullptr;
+  j.nseg = nseg;
+  const uint64_t n = j.n = offsets[nseg];
+  const int NV = j.NV;
   // chunks of 8192 elements (32 a thread), each inside one segment, taken
   // in order by the CTAs
   const uint64_t ch = kAssocChunk;
   std::vector<uint64_t> chunks;
-  std::vector<uint32_t> seg_chunk(nseg + 1);
+  j.seg_chunk.assign(nseg + 1, 0);
   for (uint32_t g = 0; g < nseg; ++g) {
-    seg_chunk[g] = (uint32_t)(chunks.size() / 3);
+    j.seg_chunk[g] = (uint32_t)(chunks.size() / 3);
     for (uint64_t b = offsets[g]; b < offsets[g + 1]; b += ch) {
       chunks.push_back(b);
       chunks.push_back(std::min(offsets[g + 1], b + ch));
       chunks.push_back(offsets[g]);
     }
   }
-  seg_chunk[nseg] = (uint32_t)(chunks.size() / 3);
-  const uint32_t nchunks = seg_chunk[nseg];
+  j.seg_chunk[nseg] = (uint32_t)(chunks.size() / 3);
+  const uint32_t nchunks = j.nchunks = j.seg_chunk[nseg];
   // one device block: chunk table, segment table, partials, h_pre, out,
   // flag, then (host inputs) the elements
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
@@ -268,34 +295,38 @@ int assoc_run(const uint8_t* a, const uint8_t* s, bool pair, const uint64_t* off
                b_pre = al((size_t)nseg * 32), b_out = al((size_t)NV * nseg * 32),
                b_flag = al(12 + (size_t)nchunks * 4);
   const size_t b_in = on_device ? 0 : al((size_t)n * 32) * (pair ? 2 : 1);
-  DevBuf buf;
-  buf.st = st;
-  ACK(cudaMallocAsync(&buf.p, b_chunks + b_seg + b_part + b_pre + b_out + b_flag + b_in, st), "cudaMallocAsync");
-  uint8_t* base = (uint8_t*)buf.p;
-  uint64_t* d_chunks = (uint64_t*)base;
-  uint32_t* d_seg = (uint32_t*)(base + b_chunks);
-  uint32_t* d_part = (uint32_t*)(base + b_chunks + b_seg);
-  uint32_t* d_pre = (uint32_t*)(base + b_chunks + b_seg + b_part);
-  uint32_t* d_out = (uint32_t*)(base + b_chunks + b_seg + b_part + b_pre);
-  uint32_t* d_flag = (uint32_t*)(base + b_chunks + b_seg + b_part + b_pre + b_out);
+  j.buf.st = st;
+  ACK(cudaMallocAsync(&j.buf.p, b_chunks + b_seg + b_part + b_pre + b_out + b_flag + b_in, st), "cudaMallocAsync");
+  uint8_t* base = (uint8_t*)j.buf.p;
+  j.d_chunks = (uint64_t*)base;
+  j.d_seg = (uint32_t*)(base + b_chunks);
+  j.d_part = (uint32_t*)(base + b_chunks + b_seg);
+  j.d_pre = (uint32_t*)(base + b_chunks + b_seg + b_part);
+  j.d_out = (uint32_t*)(base + b_chunks + b_seg + b_part + b_pre);
+  j.d_flag = (uint32_t*)(base + b_chunks + b_seg + b_part + b_pre + b_out);
   uint8_t* d_in = base + b_chunks + b_seg + b_part + b_pre + b_out + b_flag;
-  const uint8_t* da = a;
-  const uint8_t* ds = s;
+  j.da = a;
+  j.ds = s;
   if (!on_device && n) {
     ACK(cudaMemcpyAsync(d_in, a, (size_t)n * 32, cudaMemcpyHostToDevice, st), "copy in");
-    da = d_in;
+    j.da = d_in;
     if (pair) {
       ACK(cudaMemcpyAsync(d_in + al((size_t)n * 32), s, (size_t)n * 32, cudaMemcpyHostToDevice, st), "copy in");
-      ds = d_in + al((size_t)n * 32);
+      j.ds = d_in + al((size_t)n * 32);
     }
   }
   if (!chunks.empty())
-    ACK(cudaMemcpyAsync(d_chunks, chunks.data(), chunks.size() * 8, cudaMemcpyHostToDevice, st), "copy in");
-  ACK(cudaMemcpyAsync(d_seg, seg_chunk.data(), (nseg + 1) * 4, cudaMemcpyHostToDevice, st), "copy in");
-  if (h_pre) ACK(cudaMemcpyAsync(d_pre, h_pre, (size_t)nseg * 32, cudaMemcpyHostToDevice, st), "copy in");
-  uint32_t* d_next = d_flag + 1;  // two chunk counters
-  uint32_t* d_unord = d_flag + 3;
-  ACK(cudaMemsetAsync(d_flag, 0, 12, st), "memset");
+    ACK(cudaMemcpyAsync(j.d_chunks, chunks.data(), chunks.size() * 8, cudaMemcpyHostToDevice, st), "copy in");
+  ACK(cudaMemcpyAsync(j.d_seg, j.seg_chunk.data(), (nseg + 1) * 4, cudaMemcpyHostToDevice, st), "copy in");
+  if (h_pre) ACK(cudaMemcpyAsync(j.d_pre, h_pre, (size_t)nseg * 32, cudaMemcpyHostToDevice, st), "copy in");
+  ACK(cudaMemsetAsync(j.d_flag, 0, 12, st), "memset");
+  return SISU_OK;
+}
+
+int assoc_launch(AssocJob& j, cudaStream_t st) {
+  const uint32_t nchunks = j.nchunks;
+  uint32_t* d_next = j.d_flag + 1;  // two chunk counters
+  uint32_t* d_unord = j.d_flag + 3;
   if (nchunks) {
     static int occ = 0;
     if (occ == 0) {
@@ -304,39 +335,85 @@ int assoc_run(const uint8_t* a, const uint8_t* s, bool pair, const uint64_t* off
       occ = (e == cudaSuccess && k > 0) ? k : 1;
     }
     const unsigned grid = (unsigned)std::min<uint64_t>(nchunks, (uint64_t)kSMs * occ);
-    const long prof = prof_begin(pair ? kProfAssocPair : kProfAssocHash, (double)n * NV, st);
-    k_assoc_chunks<<<grid, kAssocBD, 0, st>>>((const uint32_t*)da, d_chunks, nchunks, d_part, NV, 0, d_next, d_flag);
+    const long prof = prof_begin(j.ord ? kProfAssocPair : kProfAssocHash, (double)j.n * j.NV, st);
+    k_assoc_chunks<<<grid, kAssocBD, 0, st>>>((const uint32_t*)j.da, j.d_chunks, nchunks, j.d_part, j.NV, 0, d_next,
+                                              j.d_flag);
     int rc = post_launch();
-    if (!rc && pair) {
-      k_assoc_chunks<<<grid, kAssocBD, 0, st>>>((const uint32_t*)ds, d_chunks, nchunks, d_part, NV, 1, d_next + 1,
-                                                d_flag);
+    if (!rc && j.pair) {
+      k_assoc_chunks<<<grid, kAssocBD, 0, st>>>((const uint32_t*)j.ds, j.d_chunks, nchunks, j.d_part, j.NV, 1,
+                                                d_next + 1, j.d_flag);
       rc = post_launch();
-      if (!rc) {
-        k_order_chunks<<<(unsigned)std::min<uint64_t>(nchunks, (uint64_t)kSMs * 8), kAssocBD, 0, st>>>(
-            (const uint32_t*)ds, d_chunks, nchunks, d_unord);
-        rc = post_launch();
-      }
+    }
+    if (!rc && j.ord) {
+      k_order_chunks<<<(unsigned)std::min<uint64_t>(nchunks, (uint64_t)kSMs * 8), kAssocBD, 0, st>>>(
+          (const uint32_t*)(j.pair ? j.ds : j.da), j.d_chunks, nchunks, d_unord);
+      rc = post_launch();
     }
     prof_end(prof, st);
     if (rc) return cuda_err((cudaError_t)rc, "associative hash");
   }
-  const uint32_t warps = nseg * NV;
-  k_assoc_finish<<<(warps * 32 + 255) / 256, 256, 0, st>>>(d_part, d_seg, nseg, NV, h_pre ? d_pre : nullptr, d_out,
-                                                            d_flag);
+  const uint32_t warps = j.nseg * j.NV;
+  k_assoc_finish<<<(warps * 32 + 255) / 256, 256, 0, st>>>(j.d_part, j.d_seg, j.nseg, j.NV, j.pre ? j.d_pre : nullptr,
+                                                            j.d_out, j.d_flag);
   int rc = post_launch();
   if (rc) return cuda_err((cudaError_t)rc, "associative hash");
-  ACK(cudaMemcpyAsync(out, d_out, (size_t)NV * nseg * 32, cudaMemcpyDeviceToHost, st), "copy out");
-  ACK(cudaMemcpyAsync(host_flag, d_flag, 4, cudaMemcpyDeviceToHost, st), "copy out");
-  std::vector<uint32_t> unord(pair ? nchunks : 0);
-  if (pair && nchunks)
-    ACK(cudaMemcpyAsync(unord.data(), d_unord, (size_t)nchunks * 4, cudaMemcpyDeviceToHost, st), "copy out");
+  return SISU_OK;
+}
+
+int assoc_collect(AssocJob& j, cudaStream_t st, uint8_t* out, uint32_t* host_flag, int* seg_unordered) {
+  ACK(cudaMemcpyAsync(out, j.d_out, (size_t)j.NV * j.nseg * 32, cudaMemcpyDeviceToHost, st), "copy out");
+  ACK(cudaMemcpyAsync(host_flag, j.d_flag, 4, cudaMemcpyDeviceToHost, st), "copy out");
+  std::vector<uint32_t> unord(j.ord ? j.nchunks : 0);
+  if (j.ord && j.nchunks)
+    ACK(cudaMemcpyAsync(unord.data(), j.d_flag + 3, (size_t)j.nchunks * 4, cudaMemcpyDeviceToHost, st), "copy out");
   ACK(cudaStreamSynchronize(st), "associative hash");
-  if (pair)
-    for (uint32_t g = 0; g < nseg; ++g) {
+  if (j.ord)
+    for (uint32_t g = 0; g < j.nseg; ++g) {
       seg_unordered[g] = 0;
-      for (uint32_t k = seg_chunk[g]; k < seg_chunk[g + 1]; ++k) seg_unordered[g] |= (int)unord[k];
+      for (uint32_t k = j.seg_chunk[g]; k < j.seg_chunk[g + 1]; ++k) seg_unordered[g] |= (int)unord[k];
     }
   return SISU_OK;
+}
+
+int assoc_run(const uint8_t* a, const uint8_t* s, bool pair, bool order, const uint64_t* offsets, uint32_t nseg,
+              const uint8_t* h_pre, int on_device, cudaStream_t st, uint8_t* out, uint32_t* host_flag,
+              int* seg_unordered) {
+  AssocJob j;
+  int rc = assoc_prepare(j, a, s, pair, order, offsets, nseg, h_pre, on_device, st);
+  if (!rc) rc = assoc_launch(j, st);
+  if (!rc) rc = assoc_collect(j, st, out, host_flag, seg_unordered);
+  return rc;
+}
+
+// acc = (acc + y) mod r for canonical little-endian 256-bit values
+void add_mod_r(uint64_t acc[4], const uint8_t* y) {
+  static const uint64_t r[4] = {0x43e1f593f0000001ull, 0x2833e84879b97091ull, 0xb85045b68181585dull,
+                                0x30644e72e131a029ull};
+  uint64_t b[4];
+  memcpy(b, y, 32);
+  unsigned __int128 c = 0;
+  for (int i = 0; i < 4; ++i) {
+    c += (unsigned __int128)acc[i] + b[i];
+    acc[i] = (uint64_t)c;
+    c >>= 64;
+  }
+  bool ge = c != 0;  // a carry out of 2^256 exceeds r; else compare from the top
+  if (!ge) {
+    ge = true;
+    for (int i = 3; i >= 0; --i)
+      if (acc[i] != r[i]) {
+        ge = acc[i] > r[i];
+        break;
+      }
+  }
+  if (ge) {
+    unsigned __int128 bw = 0;
+    for (int i = 0; i < 4; ++i) {
+      const unsigned __int128 d = (unsigned __int128)acc[i] - r[i] - (uint64_t)bw;
+      acc[i] = (uint64_t)d;
+      bw = (d >> 64) ? 1 : 0;
+    }
+  }
 }
 
 int check_elems(const uint8_t* p, uint64_t n, int on_device) {
@@ -360,8 +437,8 @@ extern "C" int sisu_assoc_hash_segments(const uint8_t* elems, const uint64_t* of
   int rc = check_elems(elems, offsets[n_segments], on_device);
   if (rc) return rc;
   uint32_t flag = 0;
-  rc = assoc_run(elems, nullptr, false, offsets, n_segments, h_pre, on_device, (cudaStream_t)stream, out, &flag,
-                 nullptr);
+  rc = assoc_run(elems, nullptr, false, false, offsets, n_segments, h_pre, on_device, (cudaStream_t)stream, out,
+                 &flag, nullptr);
   if (rc) return rc;
   if (flag & kAssocNotCanonical) return report_error(SISU_ERR_NOT_CANONICAL, "an element or h_pre is not below r");
   return SISU_OK;
@@ -387,8 +464,8 @@ extern "C" int sisu_pairwise_distinct_check_segments(const uint8_t* a, const uin
   std::vector<uint8_t> h((size_t)64 * n_segments);
   std::vector<int> unord(n_segments);
   uint32_t flag = 0;
-  rc = assoc_run(a, a_sorted, true, offsets, n_segments, nullptr, on_device, (cudaStream_t)stream, h.data(), &flag,
-                 unord.data());
+  rc = assoc_run(a, a_sorted, true, false, offsets, n_segments, nullptr, on_device, (cudaStream_t)stream, h.data(),
+                 &flag, unord.data());
   if (rc) return rc;
   if (flag & kAssocNotCanonical) return report_error(SISU_ERR_NOT_CANONICAL, "an element is not below r");
   for (uint32_t g = 0; g < n_segments; ++g) {
@@ -404,4 +481,49 @@ extern "C" int sisu_pairwise_distinct_check(const uint8_t* a, const uint8_t* a_s
                                             void* stream, int* result, uint8_t* h_a, uint8_t* h_sorted) {
   const uint64_t offsets[2] = {0, n};
   return sisu_pairwise_distinct_check_segments(a, a_sorted, offsets, 1, on_device, stream, result, h_a, h_sorted);
+}
+
+extern "C" int sisu_assoc_epochs(const uint8_t* a, const uint8_t* a_sorted, const uint64_t* slot_offsets,
+                                 uint32_t n_slots, uint32_t slots_per_epoch, int on_device, void* stream,
+                                 uint8_t* slot_hashes, int* results, uint8_t* h_a, uint8_t* h_sorted) {
+  if (!slot_offsets || !slot_hashes || !results || n_slots == 0)
+    return report_error(SISU_ERR_INVALID_ARG, "NULL slot offsets/hashes/results or no slot");
+  if (slots_per_epoch == 0 || n_slots % slots_per_epoch)
+    return report_error(SISU_ERR_INVALID_ARG, "the slots must make whole epochs");
+  if (slot_offsets[0] != 0) return report_error(SISU_ERR_INVALID_ARG, "offsets[0] must be 0");
+  for (uint32_t g = 0; g < n_slots; ++g)
+    if (slot_offsets[g + 1] < slot_offsets[g]) return report_error(SISU_ERR_INVALID_ARG, "offsets must not decrease");
+  int rc = check_elems(a, slot_offsets[n_slots], on_device);
+  if (!rc) rc = check_elems(a_sorted, slot_offsets[n_slots], on_device);
+  if (rc) return rc;
+  // Algorithm 1 on every slot of a, and the hash and the order of a_sorted
+  // over every epoch: both runs prepared, then both launched, then both
+  // collected
+  const uint32_t ne = n_slots / slots_per_epoch;
+  std::vector<uint64_t> eoff(ne + 1);
+  for (uint32_t e = 0; e <= ne; ++e) eoff[e] = slot_offsets[(size_t)e * slots_per_epoch];
+  std::vector<uint8_t> hs((size_t)32 * ne);
+  std::vector<int> unord(ne);
+  const cudaStream_t st = (cudaStream_t)stream;
+  AssocJob ja, js;
+  rc = assoc_prepare(ja, a, nullptr, false, false, slot_offsets, n_slots, nullptr, on_device, st);
+  if (!rc) rc = assoc_prepare(js, a_sorted, nullptr, false, true, eoff.data(), ne, nullptr, on_device, st);
+  if (!rc) rc = assoc_launch(ja, st);
+  if (!rc) rc = assoc_launch(js, st);
+  uint32_t flag_a = 0, flag_s = 0;
+  if (!rc) rc = assoc_collect(ja, st, slot_hashes, &flag_a, nullptr);
+  if (!rc) rc = assoc_collect(js, st, hs.data(), &flag_s, unord.data());
+  if (rc) return rc;
+  if ((flag_a | flag_s) & kAssocNotCanonical) return report_error(SISU_ERR_NOT_CANONICAL, "an element is not below r");
+  // the hash of a over an epoch: the sum of its slots' hashes
+  for (uint32_t e = 0; e < ne; ++e) {
+    uint64_t acc[4] = {0, 0, 0, 0};
+    for (uint32_t k = 0; k < slots_per_epoch; ++k) add_mod_r(acc, slot_hashes + 32 * ((size_t)e * slots_per_epoch + k));
+    uint8_t ha[32];
+    memcpy(ha, acc, 32);
+    if (h_a) memcpy(h_a + 32 * (size_t)e, ha, 32);
+    if (h_sorted) memcpy(h_sorted + 32 * (size_t)e, hs.data() + 32 * (size_t)e, 32);
+    results[e] = (memcmp(ha, hs.data() + 32 * (size_t)e, 32) == 0 && !unord[e]) ? 1 : 0;
+  }
+  return SISU_OK;
 }

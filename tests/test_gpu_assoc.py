@@ -240,3 +240,43 @@ def test_sort_errors(S):
     with pytest.raises(S.SisuError):
         S.sort_elements(_elems(19, 3) + (P).to_bytes(32, "little"))
     assert S.sort_elements(b"")[0] == b""
+
+
+def test_assoc_epochs(S, oracle):
+    """Slot hashes and Algorithm 2 per epoch in one call: the slot hashes,
+    every epoch's answer and both epoch hashes equal the oracle's on the
+    same lists, for accepted epochs, repeats, unordered claims and claims
+    that are not permutations; host and device inputs agree."""
+    rng = random.Random(21)
+    spe, nslots = 4, 24
+    lens = [rng.choice([0, 1, 5, 300, 4096, 5000]) for _ in range(nslots)]
+    offs = np.concatenate([[0], np.cumsum(lens)]).astype(np.uint64)
+    A, Srt = [], []
+    for e in range(nslots // spe):
+        n = int(offs[(e + 1) * spe] - offs[e * spe])
+        idx = synth.validator_indexes(300 + e, n, 20)
+        srt = _sorted(idx).copy()
+        kind = e % 4
+        if kind == 1 and n >= 2:      # a repeat
+            idx[-1] = idx[0]
+            srt = _sorted(idx).copy()
+        elif kind == 2 and n >= 2:    # not ascending
+            k = rng.randrange(n - 1)
+            srt[[k, k + 1]] = srt[[k + 1, k]]
+        elif kind == 3 and n >= 1:    # not a permutation
+            srt[-1, 0] += 1 << 21
+        A.append(idx)
+        Srt.append(srt)
+    a, s = synth.fr_bytes(np.concatenate(A)), synth.fr_bytes(np.concatenate(Srt))
+    sh, res, ha, hs = S.assoc_epochs(a, s, offs, spe)
+    for g in range(nslots):
+        assert sh[g] == oracle.assoc_hash(a[32 * int(offs[g]):32 * int(offs[g + 1])]), g
+    for e in range(nslots // spe):
+        lo, hi = int(offs[e * spe]), int(offs[(e + 1) * spe])
+        ae, se = a[32 * lo:32 * hi], s[32 * lo:32 * hi]
+        assert res[e] == oracle.pairwise_distinct_check(ae, se), e
+        assert ha[e] == oracle.assoc_hash(ae) and hs[e] == oracle.assoc_hash(se), e
+    assert 0 < sum(res) < nslots // spe
+    assert S.assoc_epochs(to_device(a), to_device(s), offs, spe) == (sh, res, ha, hs)
+    with pytest.raises(S.SisuError):  # the slots must make whole epochs
+        S.assoc_epochs(a, s, offs, 5)
