@@ -452,6 +452,13 @@ extern "C" int sisu_circuit_info(const sisu_circuit* circ, uint32_t* depth, uint
 // evaluation
 
 namespace sisu {
+// device bytes of the inputs' digest scratch (the two-table launch with an
+// empty second table)
+static size_t eval_digest_scratch_bytes(const HostCircuit& hc) {
+  const size_t words = digest_scratch_words(((size_t)hc.C << hc.s[hc.d]) * 32) + digest_scratch_words(0);
+  return (words * 4 + 255) & ~(size_t)255;
+}
+
 int eval_enqueue(sisu_eval* ev, const uint8_t* inputs, int on_device, cudaStream_t st) {
   const sisu_circuit* cc = ev->circ;
   const HostCircuit& hc = cc->hc;
@@ -464,6 +471,8 @@ int eval_enqueue(sisu_eval* ev, const uint8_t* inputs, int on_device, cudaStream
   // are data-parallel), so the evaluation of chunk k overlaps the transfer
   // of chunk k + 1 and only the last chunk's evaluation follows the copy.
   const uint32_t nchunk = (!on_device && !padded && hc.C >= kEvalChunks && in_bytes >= kEvalChunkMin) ? kEvalChunks : 1;
+  // new inputs land only after the previous inputs' digest has read them
+  if (ev->dig_recorded) CK(cudaStreamWaitEvent(st, ev->dig_ev, 0), "stream wait");
   const uint32_t* src;
   if (on_device) {
     if (((uintptr_t)inputs & 15) != 0) return fail(SISU_ERR_INVALID_ARG, "device inputs not 16-byte aligned");
@@ -492,6 +501,11 @@ int eval_enqueue(sisu_eval* ev, const uint8_t* inputs, int on_device, cudaStream
     src = dst;
   }
   CK(cudaMemsetAsync(ev->flag, 0, 4, st), "memset");
+  if (!ev->dig_stream) {
+    CK(cudaStreamCreateWithFlags(&ev->dig_stream, cudaStreamNonBlocking), "stream create");
+    CK(cudaEventCreateWithFlags(&ev->in_ready, cudaEventDisableTiming), "event create");
+    CK(cudaEventCreateWithFlags(&ev->dig_ev, cudaEventDisableTiming), "event create");
+  }
   for (uint32_t k = 0; k < nchunk; ++k) {
     const uint32_t b0 = (uint32_t)((uint64_t)hc.C * k / nchunk), b1 = (uint32_t)((uint64_t)hc.C * (k + 1) / nchunk);
     if (nchunk > 1) CK(cudaStreamWaitEvent(st, ev->chunk_ev[k], 0), "stream wait");
@@ -499,6 +513,15 @@ int eval_enqueue(sisu_eval* ev, const uint8_t* inputs, int on_device, cudaStream
       ProfScope ps(kProfInputs, (double)((size_t)(b1 - b0) << hc.s[d]), st);
       CK(launch_inputs_to_mont(src, ev->V[d], b0, b1 - b0, hc.s[d], hc.Creal, hc.wreal[d], ev->flag, st),
          "input conversion");
+    }
+    if (k + 1 == nchunk) {  // the input layer is complete: its digest on the side stream
+      CK(cudaEventRecord(ev->in_ready, st), "event record");
+      CK(cudaStreamWaitEvent(ev->dig_stream, ev->in_ready, 0), "stream wait");
+      CK(launch_digest_tables2(ev->V[d], (size_t)hc.C << hc.s[d], nullptr, 0, ev->dscratch, ev->dig, ev->dig + 8,
+                               ev->dig_stream),
+         "input digest");
+      CK(cudaEventRecord(ev->dig_ev, ev->dig_stream), "event record");
+      ev->dig_recorded = true;
     }
     for (int i = (int)d - 1; i >= 0; --i) {
       ProfScope ps(kProfEval, (double)(b1 - b0) * cc->L[i].nmul, st);
@@ -513,9 +536,10 @@ size_t eval_footprint(const sisu_circuit* cc, bool host_inputs) {
   const HostCircuit& hc = cc->hc;
   size_t total = 0;
   for (uint32_t i = 0; i <= hc.d; ++i) total += ((size_t)hc.C << hc.s[i]) * 32;
-  total += 256;  // flag
+  total += 256;  // flag and the inputs' digest
   const bool padded = hc.Creal != hc.C || hc.wreal[hc.d] != hc.W[hc.d];
   if (padded && host_inputs) total += ((size_t)hc.Creal * hc.wreal[hc.d] * 32 + 255) & ~(size_t)255;
+  total += eval_digest_scratch_bytes(hc);
   return total;
 }
 
@@ -530,9 +554,12 @@ void eval_place(sisu_eval* ev, const sisu_circuit* cc, uint8_t* dev, bool host_i
     off += ((size_t)hc.C << hc.s[i]) * 32;
   }
   ev->flag = (uint32_t*)(dev + off);
+  ev->dig = ev->flag + 16;
   off += 256;
   const bool padded = hc.Creal != hc.C || hc.wreal[hc.d] != hc.W[hc.d];
   ev->stage = (padded && host_inputs) ? (uint32_t*)(dev + off) : nullptr;
+  if (padded && host_inputs) off += ((size_t)hc.Creal * hc.wreal[hc.d] * 32 + 255) & ~(size_t)255;
+  ev->dscratch = (uint32_t*)(dev + off);
   ev->host_flag = host_flag;
 }
 }  // namespace sisu
@@ -561,11 +588,13 @@ extern "C" int sisu_circuit_eval(const sisu_circuit* circ, const uint8_t* inputs
     offs[i] = total;
     total += ((size_t)hc.C << hc.s[i]) * 32;
   }
-  if (cudaMalloc(&ev->dev, total + 256) != cudaSuccess)
+  if (cudaMalloc(&ev->dev, total + 256 + eval_digest_scratch_bytes(hc)) != cudaSuccess)
     return fail(SISU_ERR_OOM, "device allocation of %zu bytes for the layer values", total);
   ev->V.resize(hc.d + 1);
   for (uint32_t i = 0; i <= hc.d; ++i) ev->V[i] = (uint32_t*)((uint8_t*)ev->dev + offs[i]);
   ev->flag = (uint32_t*)((uint8_t*)ev->dev + total);
+  ev->dig = ev->flag + 16;
+  ev->dscratch = (uint32_t*)((uint8_t*)ev->dev + total + 256);
   const bool padded = hc.Creal != hc.C || hc.wreal[hc.d] != hc.W[hc.d];
   if (padded && !inputs_on_device) {
     if (cudaMalloc(&ev->stage, (size_t)hc.Creal * hc.wreal[hc.d] * 32) != cudaSuccess)
@@ -768,12 +797,15 @@ static int enqueue_prove(const sisu_circuit* cc, sisu_eval* ev, const sisu_trans
   const HostCircuit& hc = cc->hc;
   Workspace& w = *ev->ws;
   const uint32_t d = hc.d, c = hc.c;
-  // statement digests of the inputs and outputs (the wiring's is cached)
+  // statement digests: the outputs' here, the inputs' formed by the
+  // evaluation on its side stream (the proof's stream waits for it before
+  // this work is enqueued or replayed); the wiring's is cached
   {
     ProfScope ps(kProfDigest, 0, st);
-    CK(launch_digest_tables2(ev->V[d], (size_t)hc.C << hc.s[d], ev->V[0], (size_t)hc.C << hc.s[0], w.dscratch,
-                             w.S->dig_in, w.S->dig_out, st),
+    CK(launch_digest_tables2(ev->V[0], (size_t)hc.C << hc.s[0], nullptr, 0, w.dscratch, w.S->dig_out, ev->dig + 16,
+                             st),
        "statement digests");
+    CK(cudaMemcpyAsync(w.S->dig_in, ev->dig, 32, cudaMemcpyDeviceToDevice, st), "digest copy");
   }
   InitParams ip;
   memset(&ip, 0, sizeof ip);
@@ -869,6 +901,10 @@ int sisu::proof_enqueue(const sisu_circuit* cc, sisu_eval* ev, const sisu_transc
 static int enqueue_proof_and_copy(const sisu_circuit* cc, sisu_eval* ev, const sisu_transcript* tr, cudaStream_t st) {
   Workspace& w = *ev->ws;
   const size_t n = cc->hc.proof_len();
+  // the inputs' digest (outside a capture: launch_proof waits before the replay)
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(st, &cs), "capture status");
+  if (cs == cudaStreamCaptureStatusNone && ev->dig_recorded) CK(cudaStreamWaitEvent(st, ev->dig_ev, 0), "stream wait");
   int rc = enqueue_prove(cc, ev, tr, st);
   if (rc) return rc;
   CK(cudaMemcpyAsync(w.host, w.proof, n, cudaMemcpyDeviceToHost, st), "proof copy");
@@ -921,6 +957,7 @@ static int launch_proof(const sisu_circuit* cc, sisu_eval* ev, const sisu_transc
     w.gdlen = dlen;
     w.gvalid = true;
   }
+  if (ev->dig_recorded) CK(cudaStreamWaitEvent(st, ev->dig_ev, 0), "stream wait");
   CK(cudaGraphLaunch(w.exec, st), "graph launch");
   launches_add(w.graph_kernels);
   return SISU_OK;

@@ -63,11 +63,24 @@ struct sisu_eval {
   // and one event per chunk, plus one for the start
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t chunk_ev[sisu::kEvalChunks + 1] = {};
+  // the inputs' statement digest, formed on its own stream while the layers
+  // evaluate: dig (device, 24 words: the digest, then two unused second
+  // outputs of the two-table digest launches), its scratch, the stream and
+  // two events (inputs converted; digest done, which a proof waits for)
+  uint32_t* dig = nullptr;
+  uint32_t* dscratch = nullptr;
+  cudaStream_t dig_stream = nullptr;
+  cudaEvent_t in_ready = nullptr, dig_ev = nullptr;
+  bool dig_recorded = false;
   ~sisu_eval() {
     if (copy_stream) cudaStreamSynchronize(copy_stream);
+    if (dig_stream) cudaStreamSynchronize(dig_stream);
     for (cudaEvent_t e : chunk_ev)
       if (e) cudaEventDestroy(e);
+    if (in_ready) cudaEventDestroy(in_ready);
+    if (dig_ev) cudaEventDestroy(dig_ev);
     if (copy_stream) cudaStreamDestroy(copy_stream);
+    if (dig_stream) cudaStreamDestroy(dig_stream);
     ws.reset();
     if (stage && !placed) cudaFree(stage);
     if (dev) cudaFree(dev);
