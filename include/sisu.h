@@ -124,7 +124,7 @@ int sisu_circuit_info(const sisu_circuit* circ, uint32_t* depth, uint32_t* log_c
  * the copies run asynchronously.  The statement digest of the inputs is
  * formed on another stream of the handle while the layers evaluate; a
  * proof on this handle waits for it (the handle also holds its scratch,
- * about 1/64 of the input layer's bytes).
+ * about 1/16 of the input layer's bytes).
  * Errors: INVALID_ARG, NOT_CANONICAL, OOM, CUDA. */
 int sisu_circuit_eval(const sisu_circuit* circ, const uint8_t* inputs, int inputs_on_device,
                       void* stream, sisu_eval** out);
