@@ -280,3 +280,18 @@ def test_assoc_epochs(S, oracle):
     assert S.assoc_epochs(to_device(a), to_device(s), offs, spe) == (sh, res, ha, hs)
     with pytest.raises(S.SisuError):  # the slots must make whole epochs
         S.assoc_epochs(a, s, offs, 5)
+
+
+def test_assoc_epochs_errors(S):
+    """Non-canonical elements in either list, and offsets that decrease,
+    are refused; an empty epoch is accepted with the empty hash."""
+    bad = (P).to_bytes(32, "little")
+    good = _elems(22, 4)
+    with pytest.raises(S.SisuError):
+        S.assoc_epochs(good[:96] + bad, good, [0, 2, 4], 2)
+    with pytest.raises(S.SisuError):
+        S.assoc_epochs(good, good[:96] + bad, [0, 2, 4], 2)
+    with pytest.raises(S.SisuError):
+        S.assoc_epochs(good, good, [0, 3, 2, 4], 3)
+    sh, res, ha, hs = S.assoc_epochs(b"", b"", [0, 0, 0], 2)
+    assert res == [1] and ha == hs and sh[0] == sh[1] == ha[0]
