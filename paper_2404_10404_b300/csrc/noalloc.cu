@@ -9,6 +9,7 @@
 // instead, and writes the digest to a device buffer the caller provides.
 #include <cuda_runtime.h>
 
+#include <cstdio>
 #include <mutex>
 
 #include "../../include/sisu.h"
@@ -40,12 +41,36 @@ void* g_noalloc_ptr[256];  // device address of the scratch, per device ordinal
 
 using namespace sisu;
 
+namespace {
+// True when p is device memory (or managed memory) that this device's
+// kernels may read and write.  cudaPointerGetAttributes allocates nothing;
+// an ordinary host pointer comes back as unregistered memory.
+bool device_pointer(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // the error it set is not sticky: clear it
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int launch_fail(int rc, const char* what) {
+  char msg[256];
+  snprintf(msg, sizeof msg, "%s: %s", what, cudaGetErrorString((cudaError_t)rc));
+  return report_error(SISU_ERR_CUDA, msg);
+}
+}  // namespace
+
 extern "C" int sisu_statement_digest_noalloc(const uint8_t* data, size_t len, uint8_t* out, void* stream) {
   if (!out || (len && !data)) return report_error(SISU_ERR_INVALID_ARG, "NULL data or output");
   if (len > kNoAllocMaxLeaves * 1024)
     return report_error(SISU_ERR_TOO_LARGE,
                         "sisu_statement_digest_noalloc serves at most 67108864 bytes (64 MiB) of input; "
                         "use sisu_statement_digest for larger inputs");
+  // both buffers must be device memory: a host address handed to the
+  // kernels would fault the GPU
+  if (!device_pointer(out)) return report_error(SISU_ERR_INVALID_ARG, "out is not device memory");
+  if (len && !device_pointer(data)) return report_error(SISU_ERR_INVALID_ARG, "data is not device memory");
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256)
     return report_error(SISU_ERR_CUDA, "no current CUDA device");
@@ -67,9 +92,10 @@ extern "C" int sisu_statement_digest_noalloc(const uint8_t* data, size_t len, ui
   cudaStream_t st = (cudaStream_t)stream;
   // the tree levels overwrite the scratch before reading it: nothing needs
   // to start at zero
-  if (launch_digest_bytes(data, len, scratch, words, st) != cudaSuccess)
-    return report_error(SISU_ERR_CUDA, "digest kernel launch failed");
+  int rc = launch_digest_bytes(data, len, scratch, words, st);
+  if (rc != (int)cudaSuccess) return launch_fail(rc, "digest tree launch");
   k_digest_words_to_bytes<<<1, 32, 0, st>>>(words, out);
-  if (post_launch() != cudaSuccess) return report_error(SISU_ERR_CUDA, "digest kernel launch failed");
+  rc = post_launch();
+  if (rc != (int)cudaSuccess) return launch_fail(rc, "digest bytes launch");
   return SISU_OK;
 }
