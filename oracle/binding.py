@@ -15,10 +15,11 @@ OK, ERR_ARG, ERR_CANON, ERR_REJECT, ERR_OOM = 0, -1, -2, -3, -4
 
 
 def build_oracle(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain -O2, single thread)."""
+    """Compile the oracle with gcc (plain -O2; OpenMP loops that run on one
+    thread unless Oracle.set_threads asks for more)."""
     if force or not os.path.exists(LIB_PATH) or os.path.getmtime(LIB_PATH) < os.path.getmtime(SRC):
         tmp = LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-shared", "-fPIC",
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-fopenmp", "-shared", "-fPIC",
                                "-o", tmp, SRC])
         os.replace(tmp, LIB_PATH)
     return LIB_PATH
@@ -86,12 +87,19 @@ class Oracle:
         lib.so_assoc_F.argtypes = [ctypes.c_char_p, sz, ctypes.c_char_p]
         lib.so_assoc_hash.argtypes = [ctypes.c_char_p, sz, ctypes.c_char_p, ctypes.c_char_p]
         lib.so_pairwise_distinct_check.argtypes = [ctypes.c_char_p, ctypes.c_char_p, sz]
+        lib.so_set_threads.restype = ctypes.c_int
+        lib.so_set_threads.argtypes = [ctypes.c_int]
         lib.so_circuit_log_copies.restype = ctypes.c_uint32
         lib.so_circuit_log_copies.argtypes = [vp]
         lib.so_circuit_log_width.restype = ctypes.c_uint32
         lib.so_circuit_log_width.argtypes = [vp, ctypes.c_uint32]
         self.lib = lib
         self._handles = {}
+
+    def set_threads(self, n: int) -> int:
+        """Threads of the prover's copy sums, folds and evaluation; returns
+        the number in effect (the proof bytes do not depend on it)."""
+        return int(self.lib.so_set_threads(int(n)))
 
     # -- circuits ---------------------------------------------------------
     def handle(self, circ):

@@ -48,6 +48,11 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* Threads of the copy-phase sums, folds and evaluation (OpenMP over copy
+ * pairs, rows and copies; 1 unless so_set_threads is called).  Field sums
+ * are exact, so the result does not depend on the thread count. */
+static int g_threads = 1;
+
 typedef unsigned __int128 u128;
 
 #define SO_OK 0
@@ -634,6 +639,7 @@ static int eval_all(const so_circuit *cc, const uint8_t *inputs, fr **V) {
         }
     for (int i = (int)d - 1; i >= 0; --i) {
         uint32_t W = cc->W[i], Wn = cc->W[i + 1];
+#pragma omp parallel for num_threads(g_threads) schedule(static)
         for (uint32_t b = 0; b < cc->C; ++b) {
             const fr *in = V[i + 1] + (size_t)b * Wn;
             fr *out = V[i] + (size_t)b * W;
@@ -739,31 +745,39 @@ static void copy_round(const so_circuit *cc, uint32_t i, const fr *T, size_t n, 
     size_t h = n / 2;
     fr prefix = fr_u64(1);
     for (uint32_t m = 1; m < k; ++m) prefix = fr_mul(prefix, eq1(zb[m - 1], rb[m - 1]));
-    fr *row = (fr *)malloc(Wn * sizeof(fr));
     for (int t = 0; t < 4; ++t) out[t] = fr_zero();
-    for (size_t j = 0; j < h; ++j) {
-        fr suffix = fr_u64(1);
-        for (uint32_t m = k + 1; m <= c; ++m)
-            suffix = fr_mul(suffix, eq1(zb[m - 1], fr_u64((uint64_t)bit_msb((uint32_t)j, c - k, m - k))));
-        for (int t = 0; t < 4; ++t) {
-            fr tt = fr_u64((uint64_t)t);
-            for (uint32_t x = 0; x < Wn; ++x) {
-                fr lo = T[j * Wn + x], hi = T[(j + h) * Wn + x];
-                row[x] = fr_add(lo, fr_mul(tt, fr_sub(hi, lo)));
+#pragma omp parallel num_threads(g_threads)
+    {
+        fr part[4] = {fr_zero(), fr_zero(), fr_zero(), fr_zero()}; /* this thread's pairs */
+        fr *row = (fr *)malloc(Wn * sizeof(fr));
+#pragma omp for schedule(static)
+        for (size_t j = 0; j < h; ++j) {
+            fr suffix = fr_u64(1);
+            for (uint32_t m = k + 1; m <= c; ++m)
+                suffix = fr_mul(suffix, eq1(zb[m - 1], fr_u64((uint64_t)bit_msb((uint32_t)j, c - k, m - k))));
+            for (int t = 0; t < 4; ++t) {
+                fr tt = fr_u64((uint64_t)t);
+                for (uint32_t x = 0; x < Wn; ++x) {
+                    fr lo = T[j * Wn + x], hi = T[(j + h) * Wn + x];
+                    row[x] = fr_add(lo, fr_mul(tt, fr_sub(hi, lo)));
+                }
+                fr S = fr_zero();
+                for (uint32_t e = 0; e < cc->ne[i]; ++e) /* entry e weighs w(out e) */
+                    S = fr_add(S, fr_mul(omega[cc->out[i][e]],
+                                         op_gate(cc->type[i][e], row[cc->in1[i][e]], row[cc->in2[i][e]])));
+                fr E = fr_mul(fr_mul(prefix, eq1(zb[k - 1], tt)), suffix);
+                part[t] = fr_add(part[t], fr_mul(E, S));
             }
-            fr S = fr_zero();
-            for (uint32_t e = 0; e < cc->ne[i]; ++e) /* entry e weighs w(out e) */
-                S = fr_add(S, fr_mul(omega[cc->out[i][e]],
-                                     op_gate(cc->type[i][e], row[cc->in1[i][e]], row[cc->in2[i][e]])));
-            fr E = fr_mul(fr_mul(prefix, eq1(zb[k - 1], tt)), suffix);
-            out[t] = fr_add(out[t], fr_mul(E, S));
         }
+        free(row);
+#pragma omp critical
+        for (int t = 0; t < 4; ++t) out[t] = fr_add(out[t], part[t]);
     }
-    free(row);
 }
 
 static void fold_rows(fr *T, size_t n, uint32_t width, fr r) {
     size_t h = n / 2;
+#pragma omp parallel for num_threads(g_threads) schedule(static) if (h * width >= 4096)
     for (size_t j = 0; j < h; ++j)
         for (uint32_t x = 0; x < width; ++x) {
             fr lo = T[j * width + x], hi = T[(j + h) * width + x];
@@ -1039,6 +1053,19 @@ int so_verify(const so_circuit *cc, const uint8_t *inputs, const uint8_t *output
 static void so_init(void) {
     if (!mu_ready) init_mu();
     if (!sha_ready) sha_init_constants();
+}
+
+/* Threads for the parallel loops of the prover (n >= 1); returns the
+ * number in effect.  Without OpenMP the oracle stays single-threaded. */
+int so_set_threads(int n) {
+    so_init();
+#ifdef _OPENMP
+    g_threads = n < 1 ? 1 : n;
+#else
+    (void)n;
+    g_threads = 1;
+#endif
+    return g_threads;
 }
 
 /* op: 0 add, 1 sub, 2 mul, 3 inverse (of a; 0 maps to 0), 4 eq1(a, b).

@@ -268,3 +268,22 @@ def test_accumulation_wiring_is_bound(oracle):
     swapped = _acc([2, 4], 1, [[(0, 1, 2, 3), (0, 0, 0, 1), (1, 0, 1, 2)]])
     d = {oracle.wiring_digest(c) for c in (base, moved, swapped)}
     assert len(d) == 3
+
+
+def test_thread_count_leaves_proofs_unchanged(oracle):
+    """The oracle's OpenMP loops (copy pairs, fold rows, evaluation copies)
+    only regroup exact field sums, so any thread count gives the same bytes;
+    brute force fixes the one-thread proof on a micro circuit."""
+    micro, mx, mi = _mk(8, [16, 8, 16], 50)
+    circ = synth.uniform_circuit(2, 64, [128, 256, 64], 60, name="threads")
+    x = synth.fr_bytes(synth.inputs_for(circ))
+    try:
+        one = oracle.prove(circ, x)
+        micro_one = oracle.prove(micro, mx)
+        for n in (2, 3, 8):
+            assert oracle.set_threads(n) >= 1
+            assert oracle.prove(circ, x) == one
+            assert oracle.prove(micro, mx) == micro_one
+    finally:
+        oracle.set_threads(1)
+    assert micro_one == brute.prove(micro, mi)

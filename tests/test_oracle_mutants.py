@@ -31,8 +31,8 @@ MUTANTS = {
                   "T[j * width + x] = fr_add(lo, fr_mul(r, fr_sub(lo, hi)));"),
     "copy_line_sign": ("row[x] = fr_add(lo, fr_mul(tt, fr_sub(hi, lo)));",
                        "row[x] = fr_add(hi, fr_mul(tt, fr_sub(hi, lo)));"),
-    "copy_drop_add_gates": ("/* entry e weighs w(out e) */\n                S = fr_add(S,",
-                            "/* entry e weighs w(out e) */\n                if (cc->type[i][e]) S = fr_add(S,"),
+    "copy_drop_add_gates": ("/* entry e weighs w(out e) */\n                    S = fr_add(S,",
+                            "/* entry e weighs w(out e) */\n                    if (cc->type[i][e]) S = fr_add(S,"),
     "eval_overwrites": ("out[cc->out[i][e]] = fr_add(out[cc->out[i][e]],", "out[cc->out[i][e]] = fr_add(fr_zero(),"),
     "eq1_dropped_term": ("return fr_add(fr_mul(a, b), fr_mul(fr_sub(one, a), fr_sub(one, b)));",
                          "return fr_add(fr_mul(a, b), fr_mul(fr_sub(one, a), b));"),
