@@ -72,15 +72,18 @@ struct sisu_eval {
   cudaStream_t dig_stream = nullptr;
   cudaEvent_t in_ready = nullptr, dig_ev = nullptr;
   bool dig_recorded = false;
+  bool owns_dig = true;  // false when the digest stream and events belong to a server slot
   ~sisu_eval() {
     if (copy_stream) cudaStreamSynchronize(copy_stream);
     if (dig_stream) cudaStreamSynchronize(dig_stream);
     for (cudaEvent_t e : chunk_ev)
       if (e) cudaEventDestroy(e);
-    if (in_ready) cudaEventDestroy(in_ready);
-    if (dig_ev) cudaEventDestroy(dig_ev);
+    if (owns_dig) {
+      if (in_ready) cudaEventDestroy(in_ready);
+      if (dig_ev) cudaEventDestroy(dig_ev);
+      if (dig_stream) cudaStreamDestroy(dig_stream);
+    }
     if (copy_stream) cudaStreamDestroy(copy_stream);
-    if (dig_stream) cudaStreamDestroy(dig_stream);
     ws.reset();
     if (stage && !placed) cudaFree(stage);
     if (dev) cudaFree(dev);
@@ -109,4 +112,13 @@ int proof_enqueue(const sisu_circuit* cc, sisu_eval* ev, const sisu_transcript* 
 // after the stream work: check the error word, copy the proof out
 int proof_finish(const sisu_circuit* cc, sisu_eval* ev, uint8_t* proof);
 int report_error(int code, const char* msg);
+// Libra's phases and the end of gate layer i from the copy-bound row A and
+// the copy weight E[0], messages from proof offset offx (enqueued on st)
+int enqueue_layer_phases(const HostCircuit& hc, const DevLayer& L, Workspace& w, uint32_t i, const uint32_t* A,
+                         const uint32_t* E, size_t offx, cudaStream_t st);
+// the workspace's regions (kWsRegions of them) in `dev`, the proof header
+// (copy count 2^c_proof) and a zeroed state, set on st
+int workspace_layout(const sisu_circuit* cc, Workspace* ws, uint8_t* dev, uint8_t* host, uint32_t c_proof,
+                     cudaStream_t st);
+size_t workspace_footprint_c(const sisu_circuit* cc, uint32_t c_proof);
 }  // namespace sisu

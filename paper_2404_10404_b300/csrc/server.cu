@@ -1,15 +1,24 @@
 // Proof server: continuous batching of independent proof jobs on one GPU.
 //
 // Jobs (circuit + inputs) queue in arrival order.  A worker thread admits
-// the head of the queue as soon as a slot and enough device memory are free:
-// the job's evaluation and prover workspace are laid out in one device
-// arena (the memory budget, allocated once), and its evaluation and proof
-// are enqueued on the slot's own stream.  Admitted jobs run concurrently,
-// so their rounds interleave on the device.  A finished job (its event has
+// queued jobs as soon as a slot and enough device memory are free: the
+// job's evaluation and prover workspace are laid out in one device arena
+// (the memory budget, allocated once), and its evaluation and proof are
+// enqueued on the slot's own stream.  Admitted jobs run concurrently, so
+// their rounds interleave on the device.  A finished job (its event has
 // completed) releases its slot and memory, which admits the next.
+//
+// Admission takes the oldest queued job that fits in the free memory, so a
+// large job at the head does not hold back smaller ones behind it (jobs of
+// one size keep their arrival order).  To keep the large job from starving,
+// at most kMaxBypass admissions may pass the job at the head; after that
+// nothing else is admitted until it fits, which it does at the latest when
+// the running jobs have finished (its footprint is within the budget).
 #include <cuda_runtime.h>
 
 #include <chrono>
+#include <climits>
+#include <cstdint>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -67,6 +76,7 @@ struct Arena {
 };
 
 constexpr size_t kSlotPinned = 1u << 20;  // proof bytes + error word per slot (proofs are below 600 KB)
+constexpr uint32_t kMaxBypass = 16;       // admissions that may pass the job at the head of the queue
 
 struct Job {
   uint64_t ticket = 0;
@@ -77,6 +87,7 @@ struct Job {
   double t_submit = 0, t_start = 0, t_done = 0;
   size_t off = 0, bytes = 0, eval_bytes = 0;
   int slot = -1;
+  uint64_t admit_order = 0;  // jobs admitted before this one
   std::unique_ptr<sisu_eval> ev;
   std::vector<uint8_t> proof;
 };
@@ -90,13 +101,21 @@ struct sisu_server {
   uint8_t* arena_mem = nullptr;
   Arena arena;
   sisu_transcript domain{};
-  std::vector<cudaStream_t> streams;
-  std::vector<cudaEvent_t> done;
-  std::vector<uint8_t*> pinned;  // per slot: proof bytes, then at +kSlotPinned-256 the evaluation flag
+  // per slot: the job's stream and completion event, the stream and two
+  // events of its inputs' digest (lent to the job's eval handle, so that no
+  // job creates or destroys a stream), and pinned memory for the proof bytes,
+  // then at +kSlotPinned-256 the evaluation flag
+  std::vector<cudaStream_t> streams, dig_streams;
+  std::vector<cudaEvent_t> done, in_ready, dig_done;
+  std::vector<uint8_t*> pinned;
   std::vector<char> busy;
+  uint64_t admitted = 0;          // jobs admitted so far
+  const Job* head = nullptr;      // the job at the head of the queue when last looked at
+  uint32_t head_bypass = 0;       // admissions that passed it
   std::mutex mu;
   std::condition_variable cv;
   bool stop = false;
+  bool paused = false;  // no admissions while set (running jobs continue)
   std::deque<Job*> queue;
   std::vector<Job*> active;
   std::map<uint64_t, std::unique_ptr<Job>> jobs;
@@ -108,31 +127,44 @@ struct sisu_server {
     return *eval_bytes + workspace_footprint(cc);
   }
 
-  // admit and start the head of the queue if a slot and memory are free
+  // admit and start the oldest queued job that fits, if a slot is free
   bool admit_one() {
     Job* j = nullptr;
     {
       std::lock_guard<std::mutex> lock(mu);
-      if (queue.empty() || active.size() >= max_active) return false;
-      Job* h = queue.front();
-      size_t off;
-      if (!arena.alloc(h->bytes, &off)) return false;
+      if (paused || queue.empty() || active.size() >= max_active) return false;
       int slot = -1;
       for (uint32_t k = 0; k < max_active; ++k)
         if (!busy[k]) {
           slot = (int)k;
           break;
         }
-      if (slot < 0) {
-        arena.release(off, h->bytes);
-        return false;
+      if (slot < 0) return false;
+      if (queue.front() != head) {
+        head = queue.front();
+        head_bypass = 0;
       }
-      queue.pop_front();
+      size_t off = 0, failed = SIZE_MAX;  // smallest footprint that did not fit
+      size_t at = queue.size();
+      for (size_t k = 0; k < queue.size(); ++k) {
+        if (k > 0 && head_bypass >= kMaxBypass) break;  // the head waits for memory, nobody passes it
+        if (queue[k]->bytes >= failed) continue;
+        if (arena.alloc(queue[k]->bytes, &off)) {
+          at = k;
+          break;
+        }
+        failed = queue[k]->bytes;
+      }
+      if (at == queue.size()) return false;
+      Job* h = queue[at];
+      queue.erase(queue.begin() + (long)at);
+      if (at > 0) ++head_bypass;
       busy[slot] = 1;
       h->off = off;
       h->slot = slot;
       h->status = 1;
       h->t_start = now_s();
+      h->admit_order = admitted++;
       active.push_back(h);
       j = h;
     }
@@ -141,6 +173,10 @@ struct sisu_server {
     uint32_t* host_flag = (uint32_t*)(pinned[j->slot] + kSlotPinned - 256);
     *host_flag = 0;
     j->ev.reset(new sisu_eval());
+    j->ev->dig_stream = dig_streams[j->slot];
+    j->ev->in_ready = in_ready[j->slot];
+    j->ev->dig_ev = dig_done[j->slot];
+    j->ev->owns_dig = false;
     eval_place(j->ev.get(), j->circ, base, !j->on_device, host_flag);
     int rc = workspace_place(j->ev.get(), base + j->eval_bytes, pinned[j->slot], st);
     if (!rc) rc = eval_enqueue(j->ev.get(), j->inputs, j->on_device, st);
@@ -204,6 +240,24 @@ struct sisu_server {
       if (!progress) cv.wait_for(lock, std::chrono::microseconds(50));
     }
   }
+
+  // frees whatever exists, also after a failed create (the worker, when it
+  // was started, has been joined by sisu_server_destroy)
+  ~sisu_server() {
+    for (size_t k = 0; k < streams.size(); ++k) {
+      if (streams[k]) cudaStreamSynchronize(streams[k]);
+      if (dig_streams[k]) cudaStreamSynchronize(dig_streams[k]);
+    }
+    for (size_t k = 0; k < streams.size(); ++k) {
+      if (streams[k]) cudaStreamDestroy(streams[k]);
+      if (dig_streams[k]) cudaStreamDestroy(dig_streams[k]);
+      if (done[k]) cudaEventDestroy(done[k]);
+      if (in_ready[k]) cudaEventDestroy(in_ready[k]);
+      if (dig_done[k]) cudaEventDestroy(dig_done[k]);
+      if (pinned[k]) cudaFreeHost(pinned[k]);
+    }
+    if (arena_mem) cudaFree(arena_mem);
+  }
 };
 
 extern "C" int sisu_server_create(size_t budget_bytes, uint32_t max_active, const uint8_t* domain, size_t dlen,
@@ -229,19 +283,33 @@ extern "C" int sisu_server_create(size_t budget_bytes, uint32_t max_active, cons
   if (cudaMalloc(&s->arena_mem, s->budget) != cudaSuccess)
     return report_error(SISU_ERR_OOM, "device allocation of the server's memory budget failed");
   s->arena = Arena(s->budget);
-  s->streams.resize(max_active);
-  s->done.resize(max_active);
-  s->pinned.resize(max_active);
+  s->streams.assign(max_active, nullptr);
+  s->dig_streams.assign(max_active, nullptr);
+  s->done.assign(max_active, nullptr);
+  s->in_ready.assign(max_active, nullptr);
+  s->dig_done.assign(max_active, nullptr);
+  s->pinned.assign(max_active, nullptr);
   s->busy.assign(max_active, 0);
   for (uint32_t k = 0; k < max_active; ++k) {
+    // on failure the unique_ptr's destructor frees what was made so far
     if (cudaStreamCreateWithFlags(&s->streams[k], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->dig_streams[k], cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&s->done[k], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->in_ready[k], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->dig_done[k], cudaEventDisableTiming) != cudaSuccess ||
         cudaMallocHost(&s->pinned[k], kSlotPinned) != cudaSuccess)
       return report_error(SISU_ERR_CUDA, "server stream, event or pinned buffer");
   }
   sisu_server* raw = s.get();
   s->worker = std::thread([raw] { raw->run(); });
   *out = s.release();
+  return SISU_OK;
+}
+
+extern "C" int sisu_job_footprint(const sisu_circuit* circ, int inputs_on_device, size_t* bytes) {
+  if (!circ || !bytes) return report_error(SISU_ERR_INVALID_ARG, "NULL argument");
+  if (!circ->dev) return report_error(SISU_ERR_INVALID_ARG, "circuit was created for host verification only");
+  *bytes = ((eval_footprint(circ, !inputs_on_device) + 255) & ~(size_t)255) + workspace_footprint(circ);
   return SISU_OK;
 }
 
@@ -269,7 +337,7 @@ extern "C" int sisu_server_submit(sisu_server* s, const sisu_circuit* circ, cons
 }
 
 extern "C" int sisu_server_poll(sisu_server* s, uint64_t ticket, int* status, uint8_t* proof, size_t cap,
-                                size_t* len, double* latency_ms) {
+                                size_t* len, double* latency_ms, uint64_t* admit_order) {
   if (!s || !status) return report_error(SISU_ERR_INVALID_ARG, "NULL argument");
   std::lock_guard<std::mutex> lock(s->mu);
   auto it = s->jobs.find(ticket);
@@ -278,12 +346,21 @@ extern "C" int sisu_server_poll(sisu_server* s, uint64_t ticket, int* status, ui
   *status = j->status;
   if (j->status == 0 || j->status == 1) return SISU_OK;
   if (latency_ms) *latency_ms = 1e3 * (j->t_done - j->t_submit);
+  if (admit_order) *admit_order = j->status == 2 || j->t_start > 0 ? j->admit_order : UINT64_MAX;
   if (j->status == 2) {
     if (len) *len = j->proof.size();
     if (!proof || cap < j->proof.size()) return report_error(SISU_ERR_BUFFER, "proof buffer too small");
     memcpy(proof, j->proof.data(), j->proof.size());
   }
   s->jobs.erase(it);
+  return SISU_OK;
+}
+
+extern "C" int sisu_server_pause(sisu_server* s, int paused) {
+  if (!s) return report_error(SISU_ERR_INVALID_ARG, "NULL server");
+  std::lock_guard<std::mutex> lock(s->mu);
+  s->paused = paused != 0;
+  s->cv.notify_all();
   return SISU_OK;
 }
 
@@ -308,11 +385,5 @@ extern "C" void sisu_server_destroy(sisu_server* s) {
     s->cv.notify_all();
   }
   if (s->worker.joinable()) s->worker.join();
-  for (uint32_t k = 0; k < s->max_active; ++k) {
-    if (s->streams[k]) cudaStreamDestroy(s->streams[k]);
-    if (s->done[k]) cudaEventDestroy(s->done[k]);
-    if (s->pinned[k]) cudaFreeHost(s->pinned[k]);
-  }
-  if (s->arena_mem) cudaFree(s->arena_mem);
   delete s;
 }

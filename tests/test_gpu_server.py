@@ -86,3 +86,44 @@ def test_server_errors(S):
     assert e.value.code == -9
     srv.close()
     tiny.close()
+
+
+def test_admission_passes_a_blocked_head_without_starving_it(S):
+    """A job at the head that does not fit is passed by smaller jobs that
+    do, at most 16 times; then it runs before the rest (no starvation)."""
+    small = synth.uniform_circuit(5 * (1 << 32) + 50, 8, [32, 32, 32], 60, name="small")
+    big = synth.uniform_circuit(5 * (1 << 32) + 51, 64, [1024, 1024, 1024], 60, name="big")
+    gs, gb = S.Circuit.from_spec(small), S.Circuit.from_spec(big)
+    xs = [synth.fr_bytes(synth.inputs_for(small, seed=2000 + k)) for k in range(40)]
+    xb = synth.fr_bytes(synth.inputs_for(big, seed=2100))
+    alone_s = [S.prove(gs, S.Eval(gs, x)) for x in xs]
+    alone_b = S.prove(gb, S.Eval(gb, xb))
+    fs, fb = S.server_footprint(gs), S.server_footprint(gb)
+    assert fb > 8 * fs
+    # the big job fits only when no small job runs
+    srv = S.Server(budget_bytes=fb + fs - 256, max_active=4)
+    srv.pause(True)
+    tickets = [srv.submit(gs, xs[0]), srv.submit(gs, xs[1]), srv.submit(gb, xb)]
+    tickets += [srv.submit(gs, x) for x in xs[2:]]
+    assert srv.pending() == (len(tickets), 0)
+    srv.pause(False)
+    out = {}
+    t0 = time.time()
+    while len(out) < len(tickets):
+        for t in tickets:
+            if t not in out:
+                r = srv.poll(t, with_order=True)
+                if r[0] not in (srv.QUEUED, srv.RUNNING):
+                    out[t] = r
+        assert time.time() - t0 < 120, "server did not finish"
+        time.sleep(0.001)
+    srv.close()
+    st, proof, lat, order_b = out[tickets[2]]
+    assert st == srv.DONE and proof == alone_b
+    for k, t in enumerate([tickets[0], tickets[1]] + tickets[3:]):
+        assert out[t][0] == srv.DONE and out[t][1] == alone_s[k]
+    # s0, s1 admitted first; 16 small jobs pass the big one; then it runs
+    assert sorted(out[t][3] for t in tickets[:2]) == [0, 1]
+    assert order_b == 2 + 16
+    later = sorted(out[t][3] for t in tickets[3:])
+    assert later == [k for k in range(2, len(tickets)) if k != order_b]
