@@ -7,7 +7,15 @@ transcript, and the GKR layer sumcheck of every layer (copy phase, Libra's
 x and y phases), ending with the proof bytes on the host.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload medium|tiny|slot|batched|served|assoc]
+                    [--workload slot|medium|tiny|batched|served|assoc]
+
+The default workload is the slot-shaped circuit (32768 copies x 1024 gates
+x 24 mixing layers, the largest configuration one GPU holds).  The same
+JSON line carries the batched workload (64 independent instances of uneven
+size, proofs/s against one instance at a time) and a served run (Poisson
+arrivals into the continuous-batching server, p50/p99 latency and proofs/s
+against the plain path measured on the same arrival trace); ``--workload
+batched`` and ``--workload served`` run those alone at full size.
 
 ``--workload assoc`` times the second data-parallel workload of the paper:
 the associative hash (Sec. 3.4.1) of every slot's validator indexes and the
@@ -37,20 +45,25 @@ sys.path.insert(0, ROOT)
 
 METRIC = "gates proved/sec (field mults/s vs roofline); batched proofs/sec and p99 latency vs plain"
 UNIT = "gates/s"
-# Roofline of the integer pipe (the binding unit of this path: exact
-# 256-bit modular products on 32-bit multiply-adds, no tensor cores):
-# 148 SMs x 64 32-bit multiply-adds per SM per clock x 2032 MHz.  One
-# Montgomery product of 8-limb operands (CIOS) is 2*64 multiply halves for
-# a*b plus 8 + 2*64 for the reduction = 264 multiply-adds.
+# The binding unit of this path is the integer pipe: exact 256-bit modular
+# products on 32-bit multiply-adds, no tensor cores.  Its peak is measured
+# in the run (independent mad.lo chains on every SM, best of a second of
+# launches), beside the derived 148 SMs x 64 multiply-adds per SM per clock
+# x 2032 MHz.  One Montgomery product of 8-limb operands (CIOS) counts as
+# 2*64 multiply halves for a*b plus 8 + 2*64 for the reduction = 264
+# multiply-adds.  The copy round's algorithmic work is 2 + 4 f products per
+# (pair, gate) item, f the share of mul gates: a mul gate's three products
+# and three weight products at t = 0, 1, 2, an add gate's two weighted
+# sums (t = 3 follows from the quadratic).
 SMS, IMAD_PER_SM_CLK, SM_MAX_MHZ = 148, 64, 2032.0
 IMAD_PER_FR_MUL = 264
 ALU_PEAK_TIMAD = SMS * IMAD_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
-# DRAM traffic (read + write bytes) per launch of the dominant kernel from
-# an ncu capture (profiles/copy_round_medium.md): the mean over the ten copy
-# rounds of a medium layer (every layer has the same shape, so this is the
-# mean over all 200 launches of a step); None when not captured for the
-# current build of the kernel.
-DOMINANT_TRAFFIC_BYTES = 39.0e6
+# DRAM traffic (read + write bytes) of the dominant kernel per (pair, gate)
+# item, from an ncu capture of the copy rounds of a slot-shaped layer (the
+# first layers of the slot workload: every layer has the same shape, so the
+# per-item traffic of a full-size launch is the same); None when not
+# captured for the current build of the kernel.
+DOMINANT_TRAFFIC_BYTES_PER_ITEM = 3754266112 / 33553408
 
 
 def log(*a):
@@ -73,6 +86,26 @@ def describe(circ) -> str:
 
 def gates_of(circ) -> int:
     return circ.n_copies * circ.gates_per_copy()
+
+
+def gpu_uuid(dev):
+    import torch
+    try:
+        return "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        return None
+
+
+def host_cpu() -> dict:
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "model": model}
 
 
 # ---------------------------------------------------------------------------
@@ -134,30 +167,47 @@ class Clocks:
 # ---------------------------------------------------------------------------
 # CPU oracle (baseline leg and reference arm)
 
-def oracle_sample(layers: int, copies: int):
-    """The workload's first ``layers`` layers with ``copies`` copies."""
+def oracle_sample(name: str, layers: int, copies: int):
+    """The workload's shape cut to ``copies`` copies and its first ``layers``
+    layers (same widths, gate mix and wiring generator)."""
     import synth
-    return synth.uniform_circuit(2, copies, [4096] * (layers + 1), 50,
-                                 name=f"medium-shaped sample: {copies} copies x 4096 gates x {layers} layers")
+    if name == "slot":
+        return synth.mixing_circuit(3, copies, 1024, layers,
+                                    name=f"slot-shaped sample: {copies} copies x 1024 gates x {layers} layers")
+    w = {"tiny": 1024, "medium": 4096}[name]
+    seed = {"tiny": 1, "medium": 2}[name]
+    return synth.uniform_circuit(seed, copies, [w] * (layers + 1), 50,
+                                 name=f"{name}-shaped sample: {copies} copies x {w} gates x {layers} layers")
 
 
-def time_oracle(circ):
+def time_oracle(circ, threads: int = 1):
     import synth
     from oracle import Oracle
     o = Oracle()
+    used = o.set_threads(threads)
     xb = synth.fr_bytes(synth.inputs_for(circ))
     o.proof_len(circ)
     t0 = time.perf_counter()
     o.prove(circ, xb)
-    return time.perf_counter() - t0
+    secs = time.perf_counter() - t0
+    o.set_threads(1)
+    return secs, used
 
 
-def cpu_baseline():
-    circ = oracle_sample(2, 1024)
-    secs = time_oracle(circ)
-    return {"value": gates_of(circ) / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{circ.name} (one proof incl. evaluation, {gates_of(circ)} gates, {secs:.1f} s, "
-                      f"single-threaded C oracle on the host)"}
+def cpu_baseline(name: str):
+    """The oracle on the host cores: all of them (OpenMP over copy pairs,
+    rows and copies), and one thread on a smaller sample."""
+    cores = os.cpu_count() or 1
+    big = oracle_sample(name, 2, 4096 if name == "slot" else 1024)
+    secs, used = time_oracle(big, cores)
+    small = oracle_sample(name, 1, 1024 if name == "slot" else 256)
+    secs1, _ = time_oracle(small, 1)
+    return {"value": gates_of(big) / secs, "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": f"{big.name} (one proof incl. evaluation, {gates_of(big)} gates, {secs:.1f} s on {used} "
+                      f"threads of the host's {cores})",
+            "single_thread": {"value": gates_of(small) / secs1, "unit": UNIT, "cores": 1,
+                              "sample": f"{small.name} ({gates_of(small)} gates, {secs1:.1f} s)"},
+            "host": host_cpu()}
 
 
 def run_reference(args):
@@ -165,19 +215,22 @@ def run_reference(args):
     if rank != 0:
         return
     circ_full = workload(args.workload)
-    circ = oracle_sample(1, 256)
+    cores = os.cpu_count() or 1
+    circ = oracle_sample(args.workload, 1, 1024 if args.workload == "slot" else 256)
     for _ in range(args.warmup):
-        time_oracle(circ)
-    total = 0.0
+        time_oracle(circ, cores)
+    total, used = 0.0, 1
     for _ in range(args.steps):
-        total += time_oracle(circ)
+        secs, used = time_oracle(circ, cores)
+        total += secs
     value = args.steps * gates_of(circ) / total
+    sample = f"{circ.name} per step ({gates_of(circ)} gates, one proof incl. evaluation, {used} threads)"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic", "config": {"workload": describe(circ_full), "sample": circ.name},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{circ.name} per step ({gates_of(circ)} gates)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample,
+                             "host": host_cpu()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -206,8 +259,27 @@ def aggregate_rate(world: int, steps: int, units_per_step: int, seconds: float) 
 # ---------------------------------------------------------------------------
 # the CUDA path
 
+def measure_imad_peak(S, stream, uuid):
+    """The integer pipe's multiply-add rate on this GPU: independent mad.lo
+    chains on every SM, the best launch of about a second of them, with the
+    SM clocks sampled meanwhile."""
+    clocks = Clocks(uuid)
+    time.sleep(0.3)
+    clocks.mark(True)
+    best, t_end, n = 0.0, time.time() + 1.2, 0
+    while time.time() < t_end or n < 3:
+        ms, ops = S.microbench(0, SMS * 8, 256, 16384, stream.cuda_stream)
+        best = max(best, ops / (ms / 1e3) / 1e12)
+        n += 1
+    clocks.mark(False)
+    clk = clocks.stop()
+    ms_fr, ops_fr = S.microbench(2, SMS * 8, 256, 256, stream.cuda_stream)
+    return {"tops": best, "launches": n, "clocks": clk, "fr_mul_gops": ops_fr / (ms_fr / 1e3) / 1e9,
+            "how": "k_mb_madlo: 1184 CTAs x 256 threads, 8 independent mad.lo.u32 chains a thread, "
+                   "best of the launches in about a second (CUDA events)"}
+
+
 def run_ours(args):
-    import numpy as np
     import torch
     import torch.distributed as dist
 
@@ -231,6 +303,7 @@ def run_ours(args):
     xb = synth.fr_bytes(synth.inputs_for(circ))
     log(f"[bench] {circ.name}: inputs drawn in {time.time() - t0:.1f} s")
     host = torch.frombuffer(bytearray(xb), dtype=torch.uint8).pin_memory()
+    del xb
     inputs = host.to(dev)
     stream = torch.cuda.Stream(device=dev)
     gc = S.Circuit.from_spec(circ)
@@ -251,18 +324,12 @@ def run_ours(args):
     for _ in range(max(0, args.warmup - 1)):
         step(inputs)
 
-    # integer-pipe microbenchmark (reported beside the derived peak)
-    ms_lo, ops_lo = S.microbench(0, SMS * 8, 256, 256, stream.cuda_stream)
-    ms_fr, ops_fr = S.microbench(2, SMS * 8, 256, 64, stream.cuda_stream)
-
-    uuid = None
-    try:
-        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
-    except Exception:
-        pass
+    uuid = gpu_uuid(dev)
+    imad = measure_imad_peak(S, stream, uuid)
     clocks = Clocks(uuid)
     time.sleep(0.5)
-    # timed region: no per-kernel events, so the proofs replay their CUDA graphs
+    # timed region: no per-kernel events, so the proofs replay their CUDA graphs;
+    # the layer values (GiBs) are far larger than L2 and every step re-reads them
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
@@ -300,7 +367,7 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     e2e_s = time.perf_counter() - w0
     e2e_s = max_over_ranks(e2e_s, world, dev)
-    e2e = {"value": aggregate_rate(world, args.steps, gates, e2e_s), "unit": UNIT, "h2d_bytes_per_step": len(xb),
+    e2e = {"value": aggregate_rate(world, args.steps, gates, e2e_s), "unit": UNIT, "h2d_bytes_per_step": host.numel(),
            "d2h_bytes_per_step": gc.proof_len}
 
     # per-kernel breakdown of one step (untimed pass)
@@ -316,18 +383,26 @@ def run_ours(args):
         breakdown[name] = {"ms": round(kms, 4), "launches": kn, "fr_mults": kw}
     S.profile_enable(0)
 
+    # algorithmic work of the timed copy rounds: 2 + 4 f products per (pair, gate) item
+    items = sum(circ.n_copies // 2 ** (k + 1) * circ.widths[i] for i in range(circ.depth)
+                for k in range((circ.n_copies - 1).bit_length()))
     achieved = prof_work * IMAD_PER_FR_MUL / (prof_ms / 1e3) / 1e12 if prof_ms else None
-    # kernel launches counted inside the timed region (graph replay launches the same kernels)
+    peak = imad["tops"]
+    per_launch_items = items / max(1, len(rounds)) if rounds else None
+    traffic = (DOMINANT_TRAFFIC_BYTES_PER_ITEM * per_launch_items
+               if DOMINANT_TRAFFIC_BYTES_PER_ITEM and per_launch_items else None)
     roofline = {"bound": "alu", "kernel": "k_copy_round (copy-phase round)", "achieved": achieved,
-                "peak": ALU_PEAK_TIMAD, "unit": "TIMAD/s", "frac": achieved / ALU_PEAK_TIMAD if achieved else None,
-                "traffic": DOMINANT_TRAFFIC_BYTES,
+                "peak": peak, "unit": "TIMAD/s", "frac": achieved / peak if achieved else None,
+                "traffic": traffic,
+                "peak_source": "measured in this run (mad.lo stream, integer pipe) of measured",
+                "peak_measurement": imad,
+                "frac_of_derived_peak": achieved / ALU_PEAK_TIMAD if achieved else None,
+                "derived_peak": {"tops": ALU_PEAK_TIMAD, "how": "148 SMs x 64 IMAD/clk x 2032 MHz"},
+                "work_counted": "2 + 4 f Montgomery products per (pair, gate) item (f = share of mul gates), "
+                                "264 multiply-adds per product",
                 "per_launch_ms": prof_ms / prof_n if prof_n else None, "launches_timed": prof_n,
                 "fr_mults_per_launch": prof_work / prof_n if prof_n else None,
-                "peak_source": "derived: 148 SMs x 64 IMAD/clk x 2032 MHz; 264 IMAD per 8x32-bit Montgomery product",
-                "imad_measured_tops": ops_lo / (ms_lo / 1e3) / 1e12,
-                "fr_mul_measured_gops": ops_fr / (ms_fr / 1e3) / 1e9}
-    if rank != 0:
-        return
+                "items_per_launch": per_launch_items}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
@@ -339,8 +414,25 @@ def run_ours(args):
             "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
             "parity": {"proof_matches_oracle_sha256": parity},
             "breakdown_ms_per_step": breakdown, "copy_rounds_first_layer": per_round}
+    del ev, gc, inputs
+    torch.cuda.synchronize(dev)
+    torch.cuda.empty_cache()
+    if world == 1 and not args.no_extra:
+        # the rest of the metric: batched proofs/s and served p50/p99 against
+        # the plain one-at-a-time path, on the batched workload's instances
+        try:
+            specs, pins = batched_setup(args.instances)
+            bres, singles = batched_core(S, dev, stream, specs, pins, args.budget_gb)
+            line["batched"] = bres
+            line["served"] = served_core(S, dev, specs, pins, singles, args.extra_jobs, args.loads,
+                                         args.budget_gb, args.slots)
+            del pins
+        except Exception as e:  # the headline stands without them
+            line["batched_or_served_error"] = repr(e)
+    if rank != 0:
+        return
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"] = cpu_baseline(args.workload)
     print(json.dumps(line), flush=True)
 
 
@@ -359,8 +451,8 @@ ASSOC_UNIT = "indexes/s"
 IMAD_PER_F = 30 + (4 * 16 + 34) + IMAD_PER_FR_MUL + (2 * 16 + 34) + (72 + 136) + IMAD_PER_FR_MUL
 ASSOC_EPOCHS, ASSOC_EPOCH, ASSOC_SLOT, ASSOC_LOG_UNIVERSE = 64, 1 << 20, 1 << 15, 21
 # DRAM read + write bytes per index of k_assoc_chunks (ncu capture of one
-# launch over 2^23 indexes, profiles/assoc_chunks_validator_indexes.md):
-# the 32-byte value read once plus the chunk tables and partial sums
+# launch over 2^23 indexes): the 32-byte value read once plus the chunk
+# tables and partial sums
 ASSOC_TRAFFIC_PER_INDEX = (268.816896e6 + 3.927552e6) / 2**23
 
 
@@ -555,66 +647,63 @@ def run_assoc(args):
 # ---------------------------------------------------------------------------
 # batched: many independent instances of uneven size
 
-def run_batched(args):
+def batched_setup(n: int):
+    """The first n instances of the batched workload and their inputs in
+    pinned host memory."""
     import torch
-
-    import paper_2404_10404_b300 as S
     import synth
-    from paper_2404_10404_b300.build import build
+    t0 = time.time()
+    specs = [synth.batched_instance(j) for j in range(n)]
+    pins = [torch.frombuffer(bytearray(synth.fr_bytes(synth.inputs_for(c))), dtype=torch.uint8).pin_memory()
+            for c in specs]
+    log(f"[bench] batched: {n} instances drawn in {time.time() - t0:.1f} s")
+    return specs, pins
 
-    torch.cuda.set_device(0)
-    build()
-    dev = torch.device("cuda", 0)
-    stream = torch.cuda.Stream(device=dev)
-    specs = [synth.batched_instance(j) for j in range(args.instances)]
-    budget = int(args.budget_gb * 2**30)
 
-    def footprint(c):
-        Cp = 1 << max(0, (c.n_copies - 1).bit_length())
-        W = 1 << max(0, (max(c.widths) - 1).bit_length())
-        eval_b = sum(Cp * (1 << max(0, (w - 1).bit_length())) * 32 for w in c.widths)
-        return eval_b + (Cp // 2) * W * 32 + (64 << 20)
-
+def batched_core(S, dev, stream, specs, pins, budget_gb: float):
+    """Proofs/s of the instances proved by sisu_gkr_prove_batch against one
+    at a time, admitted in waves that fit the budget; the concurrency is
+    tuned on the first wave.  Returns (result, the single-instance proofs)."""
+    import torch
+    budget = int(budget_gb * 2**30)
+    gcs_all = [S.Circuit.from_spec(c) for c in specs]
+    foot = [S.server_footprint(g, True) for g in gcs_all]
     waves, cur, used = [], [], 0
-    for c in specs:
-        f = footprint(c)
-        if cur and used + f > budget:
+    for k in range(len(specs)):
+        if cur and used + foot[k] > budget:
             waves.append(cur)
             cur, used = [], 0
-        cur.append(c)
-        used += f
+        cur.append(k)
+        used += foot[k]
     if cur:
         waves.append(cur)
     gates = sum(gates_of(c) for c in specs)
     t_plain = t_batch = 0.0
-    tuned = None
-    tune_log = {}
+    tuned, tune_log, singles = None, {}, [None] * len(specs)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for wi, wave in enumerate(waves):
-        t0 = time.time()
-        gcs = [S.Circuit.from_spec(c) for c in wave]
-        evs = []
-        for c, g in zip(wave, gcs):
-            evs.append(S.Eval(g, synth.fr_bytes(synth.inputs_for(c)), stream))
-        log(f"[bench] batched wave {wi}: {len(wave)} instances set up in {time.time() - t0:.1f} s")
+    for wave in waves:
+        gcs = [gcs_all[k] for k in wave]
+        evs = [S.Eval(gcs_all[k], pins[k], stream) for k in wave]
         # warm-up: workspace allocation, first proof, graph capture
         single = [S.prove(g, e, None, stream) for g, e in zip(gcs, evs)]
         for g, e in zip(gcs, evs):
             S.prove(g, e, None, stream)
-        if tuned is None:  # pick the concurrency on the first wave
+        for k, p in zip(wave, single):
+            singles[k] = p
+        if tuned is None:  # the concurrency, on the first wave
             best = None
-            for k in (1, 2, 4, 8, 16, 32):
-                S.prove_batch(gcs, evs, None, stream, k)
+            for kc in (1, 2, 4, 8, 16, 32):
+                S.prove_batch(gcs, evs, None, stream, kc)
                 torch.cuda.synchronize(dev)
                 ev0.record(stream)
-                out = S.prove_batch(gcs, evs, None, stream, k)
+                out = S.prove_batch(gcs, evs, None, stream, kc)
                 ev1.record(stream)
                 torch.cuda.synchronize(dev)
                 ms = ev0.elapsed_time(ev1)
-                tune_log[k] = round(ms, 3)
+                tune_log[kc] = round(ms, 3)
                 assert out == single, "batched proofs differ from single-instance proofs"
                 if best is None or ms < best[1]:
-                    best = (k, ms)
+                    best = (kc, ms)
             tuned = best[0]
         torch.cuda.synchronize(dev)
         ev0.record(stream)
@@ -629,135 +718,171 @@ def run_batched(args):
         torch.cuda.synchronize(dev)
         t_batch += ev0.elapsed_time(ev1) / 1e3
         assert out == single, "batched proofs differ from single-instance proofs"
-        del evs, gcs
+        del evs
         torch.cuda.synchronize(dev)
     n = len(specs)
-    line = {"metric": "batched proofs/sec", "value": n / t_batch, "unit": "proofs/s", "n_gpus": 1, "steps": 1,
-            "warmup": 2, "ms_per_step": 1e3 * t_batch, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": f"batched: {n} instances, C = 2^U{{6..14}}, W = 2^U{{8..12}}, d = U{{8..24}}, "
-                                   f"60% mul, uniform wiring, seeds 4*2^32+j",
-                       "waves": [len(w) for w in waves], "budget_gb": args.budget_gb, "gates": gates,
-                       "timed": "proving only; each instance evaluated once before"},
-            "plain_one_at_a_time": {"value": n / t_plain, "unit": "proofs/s", "seconds": t_plain},
-            "speedup_vs_plain": t_plain / t_batch, "gates_per_s_batched": gates / t_batch,
-            "autotune": {"concurrency": tuned, "ms_first_wave": tune_log},
-            "parity": "every batched proof equals the single-instance proof"}
-    print(json.dumps(line), flush=True)
+    res = {"value": n / t_batch, "unit": "proofs/s", "ms": 1e3 * t_batch,
+           "workload": f"batched: {n} instances, C = 2^U{{6..14}}, W = 2^U{{8..12}}, d = U{{8..24}}, "
+                       f"60% mul, uniform wiring, seeds 4*2^32+j",
+           "waves": [len(w) for w in waves], "budget_gb": budget_gb, "gates": gates,
+           "timed": "proving only (statement digests, transcript, every layer's sumcheck, proof bytes to the "
+                    "host); each instance evaluated once before",
+           "plain_one_at_a_time": {"value": n / t_plain, "unit": "proofs/s", "seconds": t_plain},
+           "speedup_vs_plain": t_plain / t_batch, "gates_per_s_batched": gates / t_batch,
+           "autotune": {"concurrency": tuned, "ms_first_wave": tune_log},
+           "parity": "every batched proof equals the single-instance proof"}
+    return res, singles
 
 
-# ---------------------------------------------------------------------------
-# served: Poisson arrivals into the continuous-batching server
-
-def run_served(args):
-    import numpy as np
+def run_batched(args):
     import torch
 
     import paper_2404_10404_b300 as S
-    import synth
     from paper_2404_10404_b300.build import build
 
     torch.cuda.set_device(0)
     build()
     dev = torch.device("cuda", 0)
-    rng = np.random.default_rng(5)
-    # job templates: instances drawn as in the batched workload; each job is
-    # one template with its own inputs stored once (pinned host memory)
-    templates = [synth.batched_instance(j) for j in range(args.templates)]
-    gcs = [S.Circuit.from_spec(c) for c in templates]
-    pins = []
-    for c in templates:
-        xb = synth.fr_bytes(synth.inputs_for(c))
-        pins.append(torch.frombuffer(bytearray(xb), dtype=torch.uint8).pin_memory())
-    log(f"[bench] served: {len(templates)} templates ready")
-    # plain path, one job at a time: evaluation from pinned host inputs + proof
     stream = torch.cuda.Stream(device=dev)
-    plain_s, alone = [], []
-    for g, x in zip(gcs, pins):
-        ev = S.Eval(g, x, stream)
-        p = S.prove(g, ev, None, stream)
-        S.prove(g, ev, None, stream)
-        t0 = time.perf_counter()
-        for _ in range(2):
-            ev.update(x, stream)
-            S.prove(g, ev, None, stream)
-        plain_s.append((time.perf_counter() - t0) / 2)
-        alone.append(hashlib.sha256(p).hexdigest())
-        del ev
-    torch.cuda.synchronize(dev)
-    jobs = rng.integers(0, len(templates), size=args.jobs)
-    budget = int(args.budget_gb * 2**30)
+    specs, pins = batched_setup(args.instances)
+    res, _ = batched_core(S, dev, stream, specs, pins, args.budget_gb)
+    line = {"metric": "batched proofs/sec", "value": res["value"], "unit": "proofs/s", "n_gpus": 1, "steps": 1,
+            "warmup": 2, "ms_per_step": res["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": res["workload"], "waves": res["waves"], "budget_gb": args.budget_gb,
+                       "gates": res["gates"], "timed": res["timed"]},
+            **{k: res[k] for k in ("plain_one_at_a_time", "speedup_vs_plain", "gates_per_s_batched", "autotune",
+                                   "parity")}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# served: Poisson arrivals into the continuous-batching server, against the
+# plain path (evaluation + proof, one job at a time) on the same arrivals
+
+def served_core(S, dev, specs, pins, singles, njobs: int, loads, budget_gb: float, slots: int, seed: int = 5):
+    """Jobs pick one of the instances uniformly (sizes drawn as in the
+    batched workload) with that instance's inputs; every proof is compared
+    with the instance's single-instance proof."""
+    import numpy as np
+    import torch
+    rng = np.random.default_rng(seed)
+    gcs = [S.Circuit.from_spec(c) for c in specs]
+    alone = [hashlib.sha256(p).hexdigest() for p in singles]
+    jobs = rng.integers(0, len(specs), size=njobs)
+    budget = int(budget_gb * 2**30)
+    stream = torch.cuda.Stream(device=dev)
+
+    def summary(lat, done_at, arrivals, bad):
+        ls = np.array(lat)
+        span = max(done_at) - float(arrivals[0])
+        return {"p50_ms": float(np.percentile(ls, 50)), "p99_ms": float(np.percentile(ls, 99)),
+                "proofs_per_s": len(lat) / span, "mismatches": bad}
 
     def serve(arrivals):
-        srv = S.Server(budget, args.slots)
+        srv = S.Server(budget, slots)
         t0 = time.perf_counter()
-        tickets, lat, done_at, bad = [], {}, {}, 0
-        k = 0
-        while len(lat) < len(jobs):
+        pending, lat, done_at, bad, k = {}, [0.0] * njobs, [0.0] * njobs, 0, 0
+        finished = 0
+        while finished < njobs:
             now = time.perf_counter() - t0
-            while k < len(jobs) and arrivals[k] <= now:
-                tickets.append((srv.submit(gcs[jobs[k]], pins[jobs[k]]), k))
+            while k < njobs and arrivals[k] <= now:
+                pending[srv.submit(gcs[jobs[k]], pins[jobs[k]])] = k
                 k += 1
-            for t, jk in tickets:
-                if jk in lat:
-                    continue
+            for t in list(pending):
                 st, proof, ms = srv.poll(t)
                 if st in (srv.QUEUED, srv.RUNNING):
                     continue
+                jk = pending.pop(t)
                 if st != srv.DONE or hashlib.sha256(proof).hexdigest() != alone[jobs[jk]]:
                     bad += 1
                 lat[jk] = ms
                 done_at[jk] = time.perf_counter() - t0
-            tickets = [(t, jk) for t, jk in tickets if jk not in lat]
+                finished += 1
             time.sleep(0.0002)
         srv.close()
-        ls = np.array([lat[j] for j in range(len(jobs))])
-        span = max(done_at.values()) - float(arrivals[0])
-        return {"p50_ms": float(np.percentile(ls, 50)), "p99_ms": float(np.percentile(ls, 99)),
-                "proofs_per_s": len(jobs) / span, "mismatches": bad}
+        return summary(lat, done_at, arrivals, bad)
 
-    def plain_fifo(arrivals):
-        t, ls = 0.0, []
-        for a, j in zip(arrivals, jobs):
-            t = max(t, a) + plain_s[j]
-            ls.append(1e3 * (t - a))
-        ls = np.array(ls)
-        return {"p50_ms": float(np.percentile(ls, 50)), "p99_ms": float(np.percentile(ls, 99)),
-                "proofs_per_s": len(jobs) / (t - float(arrivals[0]))}
+    def plain(arrivals):
+        # the plain path one job at a time in arrival order: evaluation from
+        # the pinned host inputs and the proof, a fresh eval handle per job
+        t0 = time.perf_counter()
+        lat, done_at, bad = [], [], 0
+        for k in range(njobs):
+            now = time.perf_counter() - t0
+            if arrivals[k] > now:
+                time.sleep(arrivals[k] - now)
+            j = jobs[k]
+            ev = S.Eval(gcs[j], pins[j], stream)
+            p = S.prove(gcs[j], ev, None, stream)
+            del ev
+            t = time.perf_counter() - t0
+            bad += hashlib.sha256(p).hexdigest() != alone[j]
+            lat.append(1e3 * (t - arrivals[k]))
+            done_at.append(t)
+        return summary(lat, done_at, arrivals, bad)
 
-    peak = serve(np.zeros(len(jobs)))
+    zeros = np.zeros(njobs)
+    peak = serve(zeros)
+    peak_plain = plain(zeros)
     rate = peak["proofs_per_s"]
-    loads = {}
-    for load in args.loads:
-        gaps = rng.exponential(1.0 / (load * rate), size=len(jobs))
+    by_load = {}
+    for load in loads:
+        gaps = rng.exponential(1.0 / (load * rate), size=njobs)
         arrivals = np.cumsum(gaps) - gaps[0]
-        loads[str(load)] = {"offered_proofs_per_s": load * rate, "served": serve(arrivals),
-                            "plain_one_at_a_time": plain_fifo(arrivals)}
-    line = {"metric": "served p50/p99 proof latency and proofs/sec", "value": peak["proofs_per_s"],
-            "unit": "proofs/s", "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": 1e3 * args.jobs / rate,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": f"served: {args.jobs} jobs drawn from {len(templates)} instances of the batched "
-                                   f"workload, Poisson arrivals, {args.budget_gb:g} GB budget, {args.slots} slots",
-                       "loads": args.loads},
-            "peak": peak, "plain_peak_proofs_per_s": len(jobs) / float(sum(plain_s[j] for j in jobs)),
-            "by_load": loads, "parity": "each served proof is compared with the same job proved alone"}
+        by_load[str(load)] = {"offered_proofs_per_s": load * rate, "served": serve(arrivals),
+                              "plain_one_at_a_time": plain(arrivals)}
+    return {"value": rate, "unit": "proofs/s",
+            "workload": f"served: {njobs} jobs, each one of the {len(specs)} batched instances drawn uniformly "
+                        f"with its inputs (pinned host memory), Poisson arrivals at the offered loads, "
+                        f"{budget_gb:g} GB budget, {slots} slots",
+            "peak": peak, "plain_peak": peak_plain, "by_load": by_load,
+            "plain": "evaluation + proof per job through the public API, one at a time in arrival order, "
+                     "measured on the same arrival times",
+            "parity": "every proof (served and plain) equals the instance's single-instance proof"}
+
+
+def run_served(args):
+    import torch
+
+    import paper_2404_10404_b300 as S
+    from paper_2404_10404_b300.build import build
+
+    torch.cuda.set_device(0)
+    build()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    specs, pins = batched_setup(args.instances)
+    singles = []
+    for c, x in zip(specs, pins):
+        g = S.Circuit.from_spec(c)
+        singles.append(S.prove(g, S.Eval(g, x, stream), None, stream))
+        torch.cuda.synchronize(dev)
+    res = served_core(S, dev, specs, pins, singles, args.jobs, args.loads, args.budget_gb, args.slots)
+    line = {"metric": "served p50/p99 proof latency and proofs/sec", "value": res["value"], "unit": "proofs/s",
+            "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": 1e3 * args.jobs / res["value"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic", "config": {"workload": res["workload"], "loads": args.loads},
+            **{k: res[k] for k in ("peak", "plain_peak", "by_load", "plain", "parity")}}
     print(json.dumps(line), flush=True)
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["tiny", "medium", "slot", "batched", "served", "assoc"], default="medium")
-    ap.add_argument("--jobs", type=int, default=200, help="served: number of jobs")
-    ap.add_argument("--templates", type=int, default=16, help="served: distinct job instances")
+    ap.add_argument("--workload", choices=["slot", "medium", "tiny", "batched", "served", "assoc"], default="slot")
+    ap.add_argument("--jobs", type=int, default=2000, help="served: number of jobs")
+    ap.add_argument("--extra-jobs", type=int, default=200,
+                    help="served jobs in the default run's line (the full configuration: --workload served)")
     ap.add_argument("--slots", type=int, default=16, help="served: concurrent jobs")
     ap.add_argument("--loads", type=float, nargs="+", default=[0.25, 0.5, 0.9], help="served: offered loads")
     ap.add_argument("--instances", type=int, default=64, help="batched: number of instances")
-    ap.add_argument("--budget-gb", type=float, default=150.0, help="batched: device memory per wave")
+    ap.add_argument("--budget-gb", type=float, default=150.0, help="batched and served: device memory")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="leave the batched and served keys out of the line")
     ap.add_argument("--epochs", type=int, default=ASSOC_EPOCHS, help="assoc: epochs of 2^20 indexes per step")
     ap.add_argument("--depth", type=int, default=None,
                     help="keep only the workload's first layers (profiler captures)")
@@ -765,6 +890,8 @@ def main():
     if args.impl == "reference" and args.workload == "assoc":
         run_assoc_reference(args)
     elif args.impl == "reference":
+        if args.workload in ("batched", "served"):
+            args.workload = "slot"
         run_reference(args)
     elif args.workload == "assoc":
         run_assoc(args)

@@ -183,14 +183,17 @@ int sisu_gkr_prove_batch(const sisu_circuit* const* circs, sisu_eval* const* eva
 
 /* ---- serving (continuous batching of proof jobs) --------------------------
  * A server owns one device allocation of `budget_bytes` (its memory budget),
- * `max_active` slots (a stream, an event and a 1 MiB pinned proof buffer
- * each) and a worker thread.  Jobs queue in arrival order; the worker admits
- * the head of the queue as soon as a slot is free and the job's footprint
- * (all layer values plus the prover workspace, see sisu_circuit_info) fits
- * in the free part of the budget, lays the job out there, and enqueues its
- * evaluation and proof on the slot's stream.  Admitted jobs run
- * concurrently, so their rounds interleave on the device; a finished job
- * frees its slot and memory, which admits the next.  Every proof is byte
+ * `max_active` slots (two streams, three events and a 1 MiB pinned proof
+ * buffer each, made once) and a worker thread.  Jobs queue in arrival
+ * order.  Whenever a slot is free the worker admits the oldest queued job
+ * whose footprint (all layer values plus the prover workspace, see
+ * sisu_circuit_info) fits in the free part of the budget, lays the job out
+ * there, and enqueues its evaluation and proof on the slot's stream.  A job
+ * at the head that does not fit is passed by at most 16 admissions; then
+ * nothing else is admitted until it fits (at the latest when the running
+ * jobs finish), so no job starves.  Admitted jobs run concurrently, so
+ * their rounds interleave on the device; a finished job frees its slot and
+ * memory, which admits the next.  Every proof is byte
  * for byte the proof sisu_gkr_prove_into gives for the same inputs and
  * domain (NULL/0 = the default domain).  The server works on the device
  * that is current at creation.  Per-kernel profiling must be off while a
@@ -201,7 +204,11 @@ int sisu_gkr_prove_batch(const sisu_circuit* const* circs, sisu_eval* const* eva
  *   Errors: TOO_LARGE when the footprint exceeds the whole budget.
  * poll: *status = 0 queued, 1 running, 2 done (the proof is copied out and
  *   the ticket released), or a negative SISU_ERR_* (e.g. NOT_CANONICAL
- *   inputs; the ticket is released).  *latency_ms = completion - submission.
+ *   inputs; the ticket is released).  *latency_ms = completion - submission;
+ *   *admit_order (may be NULL) = the number of jobs admitted before this
+ *   one (UINT64_MAX for a job dropped unadmitted).
+ * pause: paused != 0 stops admissions (running jobs continue, submissions
+ *   queue), 0 resumes them.
  * pending: queued and running job counts.
  * destroy: waits for running jobs; queued jobs are dropped. */
 typedef struct sisu_server sisu_server;
@@ -210,7 +217,12 @@ int sisu_server_create(size_t budget_bytes, uint32_t max_active, const uint8_t* 
 int sisu_server_submit(sisu_server* s, const sisu_circuit* circ, const uint8_t* inputs, int inputs_on_device,
                        uint64_t* ticket);
 int sisu_server_poll(sisu_server* s, uint64_t ticket, int* status, uint8_t* proof, size_t cap, size_t* len,
-                     double* latency_ms);
+                     double* latency_ms, uint64_t* admit_order);
+int sisu_server_pause(sisu_server* s, int paused);
+/* The device bytes a server job of this circuit takes from the budget
+ * (layer values, input staging when host inputs need padding, digest
+ * scratch and the prover workspace).  Errors: INVALID_ARG. */
+int sisu_job_footprint(const sisu_circuit* circ, int inputs_on_device, size_t* bytes);
 int sisu_server_pending(sisu_server* s, uint32_t* queued, uint32_t* running);
 void sisu_server_destroy(sisu_server* s);
 
@@ -221,6 +233,83 @@ void sisu_server_destroy(sisu_server* s);
  * Returns SISU_OK or SISU_ERR_REJECT (or INVALID_ARG / NOT_CANONICAL). */
 int sisu_gkr_verify(const sisu_circuit* circ, const uint8_t* inputs, const uint8_t* outputs,
                     const uint8_t* proof, size_t proof_len, const uint8_t* domain, size_t dlen);
+
+/* ---- copy-sharded proving (Sec. 3.2.1, distributed GKR) -------------------
+ * The paper spreads the sumcheck over machines: the variables split into
+ * machine bits and local bits, the machines' partial round polynomials are
+ * summed at a master, and after the local rounds the master continues on a
+ * table of one entry per machine.  Here the machine index is the low part
+ * of the copy index: rank q of `world` (a power of two) holds copies
+ * b = j * world + q, j < 2^c_loc.  Copy bits are bound most significant
+ * first, so rounds 0 .. c_loc - 1 of a layer's copy phase bind rank-local
+ * bits only, and the proof is byte for byte the one-GPU proof of all
+ * world * 2^c_loc copies.
+ *
+ * A rank's evaluation is sisu_circuit_eval of a circuit with the same
+ * wiring and 2^c_loc copies (no padded copies; output and input widths of
+ * at least 32, so that each copy's rows are whole 1 KiB digest chunks) on
+ * its copies' inputs, in the order j = 0, 1, ....  The exchanges between
+ * the calls are the caller's (for example NCCL all-gathers, or device
+ * copies between ranks that share a GPU); every call only enqueues work on
+ * `stream` and reads or writes the device buffers given at creation, each
+ * 16-byte aligned, of the sizes sisu_shard_buffer_sizes reports:
+ *   roots_send  -> all-gather -> roots_recv   (every rank's copy digests)
+ *   sums_send   -> all-gather -> sums_recv    (a copy round's 4 sums)
+ *   row_send    -> gather to rank 0 -> row_recv (rank 0 only; the rank's
+ *                                               copy-bound row and weight)
+ *   state       <- broadcast from rank 0      (transcript and challenges)
+ * "all-gather" puts rank q's send buffer at q * (send size) in recv.
+ * One proof, every rank in step:
+ *   roots; exchange; begin;
+ *   for each layer i < depth:
+ *     layer_begin(i);
+ *     for k < local_rounds: copy_round(i, k); exchange sums; absorb(i, k);
+ *     row(i); gather rows; rank 0: finish(i); broadcast state;
+ *   rank 0: proof.
+ * Errors: INVALID_ARG (shapes, buffers, a layer or round out of range), OOM,
+ * CUDA, TOO_LARGE. */
+typedef struct sisu_shard sisu_shard;
+typedef struct {
+  void* roots_send;
+  void* roots_recv;
+  void* sums_send;
+  void* sums_recv;
+  void* row_send;
+  void* row_recv;  /* rank 0; may be NULL on other ranks */
+  void* state;
+} sisu_shard_buffers;
+/* sizes[7]: bytes of roots_send, roots_recv, sums_send, sums_recv, row_send,
+ * row_recv, state for this rank's evaluation in a world of `world` ranks. */
+int sisu_shard_buffer_sizes(const sisu_eval* local, uint32_t world, size_t* sizes);
+/* Allocates the rank's workspace (the evaluation must outlive the shard).
+ * tr: transcript domain, NULL for the default. */
+int sisu_shard_create(sisu_eval* local, uint32_t rank, uint32_t world, const sisu_transcript* tr,
+                      const sisu_shard_buffers* bufs, sisu_shard** out);
+void sisu_shard_destroy(sisu_shard* sh);
+/* local_rounds = c_loc (copy rounds a rank runs alone each layer),
+ * copy_bits = c_loc + log2(world), proof_len = the whole proof's bytes. */
+int sisu_shard_info(const sisu_shard* sh, uint32_t* local_rounds, uint32_t* copy_bits, size_t* proof_len);
+/* roots_send = the Merkle subtree roots of the rank's input rows, then of
+ * its output rows (the statement digests' trees are perfect: a copy's rows
+ * are a subtree). */
+int sisu_shard_roots(sisu_shard* sh, void* stream);
+/* From roots_recv: the statement digests, the initial transcript state and
+ * the claim point (every rank alike). */
+int sisu_shard_begin(sisu_shard* sh, void* stream);
+/* The rank's copy weights eq(z, j world + q) and the layer's gate weights. */
+int sisu_shard_layer_begin(sisu_shard* sh, uint32_t layer, void* stream);
+/* sums_send = the rank's part g_q(0..3) of copy round k (k < local_rounds). */
+int sisu_shard_copy_round(sisu_shard* sh, uint32_t layer, uint32_t k, void* stream);
+/* From sums_recv: the round message (their sum), its transcript step and
+ * challenge, then the fold of the rank's rows and weights. */
+int sisu_shard_absorb(sisu_shard* sh, uint32_t layer, uint32_t k, void* stream);
+/* row_send = the rank's copy-bound row (W_{layer+1} values) and its weight. */
+int sisu_shard_row(sisu_shard* sh, uint32_t layer, void* stream);
+/* Rank 0, from row_recv: the last log2(world) copy rounds on the table of
+ * one row a rank, Libra's two phases and the end of the layer (into state). */
+int sisu_shard_finish(sisu_shard* sh, uint32_t layer, void* stream);
+/* Waits for `stream`; rank 0's buffer then holds the whole proof. */
+int sisu_shard_proof(sisu_shard* sh, void* stream, uint8_t* proof, size_t cap, size_t* proof_len);
 
 /* ---- associative hash (Sec. 3.4.1, Algorithm 1) and the pairwise-distinct
  * check (Sec. 3.4.2, Algorithm 2) ---------------------------------------------
@@ -328,7 +417,10 @@ int sisu_statement_digest(const uint8_t* data, size_t len, uint8_t* out, void* s
  * different streams, or from different threads) race and must be ordered
  * by the caller.  Nothing in the array needs to start at zero.  No
  * cudaMalloc, cudaFree or other allocating routine is called.
- * Errors: INVALID_ARG, TOO_LARGE, CUDA. */
+ * Both buffers are checked with cudaPointerGetAttributes (which allocates
+ * nothing) before any launch: host memory, pinned or not, is refused.
+ * Errors: INVALID_ARG (NULL, or data / out not device memory), TOO_LARGE,
+ * CUDA (with the runtime's error string). */
 int sisu_statement_digest_noalloc(const uint8_t* data, size_t len, uint8_t* out, void* stream);
 
 /* Integer-pipe microbenchmarks used for the roofline: kind 0 = independent
@@ -353,8 +445,8 @@ int sisu_microbench(int kind, uint32_t blocks, uint32_t threads, uint32_t iters,
  * evaluations of F, not field products); 0 disables.
  * sisu_profile_read waits for the recorded events of one kind and returns
  * their summed milliseconds, the launch count and the algorithmic field
- * products of those launches (per copy-phase pair: 5 per mul gate, 2 per
- * add gate, 4 for the copy weights), then forgets them. */
+ * products of those launches (per copy-phase pair and gate: 2 + 4 f, i.e.
+ * 6 per mul gate and 2 per add gate), then forgets them. */
 int sisu_profile_enable(uint32_t kind_mask);
 int sisu_profile_read(uint32_t kind, double* ms, uint64_t* launches, double* fr_mults);
 /* The recorded launches of one kind one by one, oldest first, without

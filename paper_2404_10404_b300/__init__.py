@@ -33,7 +33,10 @@ ENTRY_POINTS = [
     "sisu_kernel_launches", "sisu_free", "sisu_last_error", "sisu_version",
     "sisu_profile_enable", "sisu_profile_read", "sisu_profile_launches", "sisu_statement_digest_noalloc",
     "sisu_gkr_prove_batch", "sisu_server_create", "sisu_server_submit", "sisu_server_poll",
-    "sisu_server_pending", "sisu_server_destroy",
+    "sisu_server_pending", "sisu_server_pause", "sisu_server_destroy", "sisu_job_footprint",
+    "sisu_shard_buffer_sizes", "sisu_shard_create", "sisu_shard_destroy", "sisu_shard_info", "sisu_shard_roots",
+    "sisu_shard_begin", "sisu_shard_layer_begin", "sisu_shard_copy_round", "sisu_shard_absorb", "sisu_shard_row",
+    "sisu_shard_finish", "sisu_shard_proof",
     "sisu_assoc_hash", "sisu_assoc_hash_segments", "sisu_pairwise_distinct_check",
     "sisu_pairwise_distinct_check_segments", "sisu_sort_elements", "sisu_assoc_epochs",
 ]
@@ -59,6 +62,13 @@ class _AccLayer(ctypes.Structure):
     _fields_ = [("width", ctypes.c_uint32), ("n_entries", ctypes.c_uint32),
                 ("out", ctypes.POINTER(ctypes.c_uint32)), ("type", ctypes.POINTER(ctypes.c_uint8)),
                 ("in1", ctypes.POINTER(ctypes.c_uint32)), ("in2", ctypes.POINTER(ctypes.c_uint32))]
+
+
+SHARD_BUFFERS = ("roots_send", "roots_recv", "sums_send", "sums_recv", "row_send", "row_recv", "state")
+
+
+class _ShardBuffers(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in SHARD_BUFFERS]
 
 
 def _load():
@@ -89,11 +99,25 @@ def _load():
         "sisu_server_create": ([sz, u32, vp, sz, pp], ctypes.c_int),
         "sisu_server_submit": ([vp, vp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
         "sisu_server_poll": ([vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int), vp, sz, ctypes.POINTER(sz),
-                              ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+                              ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
         "sisu_server_pending": ([vp, ctypes.POINTER(u32), ctypes.POINTER(u32)], ctypes.c_int),
+        "sisu_server_pause": ([vp, ctypes.c_int], ctypes.c_int),
+        "sisu_job_footprint": ([vp, ctypes.c_int, ctypes.POINTER(sz)], ctypes.c_int),
         "sisu_server_destroy": ([vp], None),
         "sisu_gkr_prove_batch": ([ctypes.POINTER(vp), ctypes.POINTER(vp), u32, vp, vp, u32, ctypes.POINTER(vp),
                                   ctypes.POINTER(sz), ctypes.POINTER(sz)], ctypes.c_int),
+        "sisu_shard_buffer_sizes": ([vp, u32, ctypes.POINTER(sz)], ctypes.c_int),
+        "sisu_shard_create": ([vp, u32, u32, vp, ctypes.POINTER(_ShardBuffers), pp], ctypes.c_int),
+        "sisu_shard_destroy": ([vp], None),
+        "sisu_shard_info": ([vp, ctypes.POINTER(u32), ctypes.POINTER(u32), ctypes.POINTER(sz)], ctypes.c_int),
+        "sisu_shard_roots": ([vp, vp], ctypes.c_int),
+        "sisu_shard_begin": ([vp, vp], ctypes.c_int),
+        "sisu_shard_layer_begin": ([vp, u32, vp], ctypes.c_int),
+        "sisu_shard_copy_round": ([vp, u32, u32, vp], ctypes.c_int),
+        "sisu_shard_absorb": ([vp, u32, u32, vp], ctypes.c_int),
+        "sisu_shard_row": ([vp, u32, vp], ctypes.c_int),
+        "sisu_shard_finish": ([vp, u32, vp], ctypes.c_int),
+        "sisu_shard_proof": ([vp, vp, vp, sz, ctypes.POINTER(sz)], ctypes.c_int),
         "sisu_fr_batch": ([ctypes.c_int, vp, vp, vp, sz, vp], ctypes.c_int),
         "sisu_statement_digest": ([vp, sz, u8p, vp], ctypes.c_int),
         "sisu_statement_digest_noalloc": ([vp, sz, vp, vp], ctypes.c_int),
@@ -239,13 +263,15 @@ class Circuit:
         self.eval_bytes = int(eb.value)
 
     @classmethod
-    def from_spec(cls, spec, host_only: bool = False):
+    def from_spec(cls, spec, host_only: bool = False, n_copies: int | None = None):
         """From any object with widths, types, in1, in2 and n_copies (and
-        outs, for accumulation gates)."""
+        outs, for accumulation gates); ``n_copies`` overrides the copy count
+        (a rank's share of a copy-sharded proof)."""
         outs = getattr(spec, "outs", None)
         if outs is not None and all(o is None for o in outs):
             outs = None
-        return cls(spec.widths, spec.types, spec.in1, spec.in2, spec.n_copies, host_only=host_only, outs=outs)
+        return cls(spec.widths, spec.types, spec.in1, spec.in2, spec.n_copies if n_copies is None else n_copies,
+                   host_only=host_only, outs=outs)
 
     def __del__(self):
         if getattr(self, "h", None):
@@ -289,6 +315,73 @@ class Eval:
     def __del__(self):
         if getattr(self, "h", None):
             _lib.sisu_eval_destroy(self.h)
+            self.h = None
+
+
+def shard_buffer_sizes(ev: Eval, world: int) -> dict:
+    """Bytes of each exchange buffer of a rank (``sisu_shard_buffer_sizes``)."""
+    sizes = (ctypes.c_size_t * len(SHARD_BUFFERS))()
+    _check(_lib.sisu_shard_buffer_sizes(ev.h, int(world), sizes))
+    return dict(zip(SHARD_BUFFERS, (int(x) for x in sizes)))
+
+
+class Shard:
+    """One rank's part of a copy-sharded proof (``sisu_shard_*``).
+
+    ``buffers`` maps the names of SHARD_BUFFERS to 16-byte aligned device
+    buffers (torch tensors or pointers) of the sizes shard_buffer_sizes
+    gives; they must outlive the shard."""
+
+    def __init__(self, ev: Eval, rank: int, world: int, buffers: dict, transcript=None):
+        keep = []
+        ptrs = {}
+        for n in SHARD_BUFFERS:
+            p, _, k = _ptr(buffers.get(n))
+            ptrs[n] = p
+            keep.append(k)
+        b = _ShardBuffers(**ptrs)
+        h = ctypes.c_void_p()
+        _check(_lib.sisu_shard_create(ev.h, int(rank), int(world), transcript.h if transcript else None,
+                                      ctypes.byref(b), ctypes.byref(h)))
+        self.h = h
+        self._keep = (ev, buffers, transcript)
+        lr, cb, pl = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_size_t()
+        _check(_lib.sisu_shard_info(h, ctypes.byref(lr), ctypes.byref(cb), ctypes.byref(pl)))
+        self.rank, self.world = int(rank), int(world)
+        self.local_rounds, self.copy_bits, self.proof_len = int(lr.value), int(cb.value), int(pl.value)
+        self.depth = ev.circ.depth
+
+    def roots(self, stream=None):
+        _check(_lib.sisu_shard_roots(self.h, _stream(stream)))
+
+    def begin(self, stream=None):
+        _check(_lib.sisu_shard_begin(self.h, _stream(stream)))
+
+    def layer_begin(self, layer: int, stream=None):
+        _check(_lib.sisu_shard_layer_begin(self.h, layer, _stream(stream)))
+
+    def copy_round(self, layer: int, k: int, stream=None):
+        _check(_lib.sisu_shard_copy_round(self.h, layer, k, _stream(stream)))
+
+    def absorb(self, layer: int, k: int, stream=None):
+        _check(_lib.sisu_shard_absorb(self.h, layer, k, _stream(stream)))
+
+    def row(self, layer: int, stream=None):
+        _check(_lib.sisu_shard_row(self.h, layer, _stream(stream)))
+
+    def finish(self, layer: int, stream=None):
+        _check(_lib.sisu_shard_finish(self.h, layer, _stream(stream)))
+
+    def proof(self, stream=None) -> bytes:
+        buf = ctypes.create_string_buffer(self.proof_len)
+        n = ctypes.c_size_t()
+        _check(_lib.sisu_shard_proof(self.h, _stream(stream), ctypes.cast(buf, ctypes.c_void_p), self.proof_len,
+                                     ctypes.byref(n)))
+        return buf.raw[:n.value]
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            _lib.sisu_shard_destroy(self.h)
             self.h = None
 
 
@@ -371,19 +464,26 @@ class Server:
         self._keep[t.value] = (keep, circ, circ.proof_len)
         return t.value
 
-    def poll(self, ticket: int):
-        """(status, proof bytes or None, latency ms or None)."""
+    def poll(self, ticket: int, with_order: bool = False):
+        """(status, proof bytes or None, latency ms or None), plus the job's
+        admission order (jobs admitted before it) when ``with_order``."""
         keep, circ, n = self._keep[ticket]
         st = ctypes.c_int()
         buf = ctypes.create_string_buffer(n)
         ln = ctypes.c_size_t()
         lat = ctypes.c_double()
+        order = ctypes.c_uint64()
         _check(_lib.sisu_server_poll(self.h, ticket, ctypes.byref(st), ctypes.cast(buf, ctypes.c_void_p), n,
-                                     ctypes.byref(ln), ctypes.byref(lat)))
+                                     ctypes.byref(ln), ctypes.byref(lat), ctypes.byref(order)))
         if st.value in (self.QUEUED, self.RUNNING):
-            return st.value, None, None
+            return (st.value, None, None, None) if with_order else (st.value, None, None)
         del self._keep[ticket]
-        return st.value, (buf.raw[:ln.value] if st.value == self.DONE else None), lat.value
+        res = (st.value, (buf.raw[:ln.value] if st.value == self.DONE else None), lat.value)
+        return res + (order.value,) if with_order else res
+
+    def pause(self, paused: bool = True):
+        """Stop (or resume) admissions; running jobs continue."""
+        _check(_lib.sisu_server_pause(self.h, int(bool(paused))))
 
     def pending(self):
         q, r = ctypes.c_uint32(), ctypes.c_uint32()
@@ -397,6 +497,13 @@ class Server:
 
     def __del__(self):
         self.close()
+
+
+def server_footprint(circ: Circuit, inputs_on_device: bool = False) -> int:
+    """Device bytes a server job of ``circ`` takes from the budget."""
+    n = ctypes.c_size_t()
+    _check(_lib.sisu_job_footprint(circ.h, int(inputs_on_device), ctypes.byref(n)))
+    return n.value
 
 
 def verify(circ: Circuit, inputs: bytes, outputs: bytes, proof: bytes, domain: bytes | None = None) -> int:
@@ -536,8 +643,10 @@ def statement_digest_noalloc(data, length: int, out, stream=None):
     """The statement digest written to the 32-byte device buffer ``out``,
     using the library's fixed scratch instead of any allocation (inputs up
     to 64 MiB; see include/sisu.h for who needs this and its limits)."""
-    p, _, keep = _ptr(data)
-    po, _, keep_out = _ptr(out)
+    p, on_dev, keep = _ptr(data)
+    po, out_dev, keep_out = _ptr(out)
+    if (length and not on_dev) or not out_dev:
+        raise SisuError(-1, "data and out must be CUDA device buffers")
     _check(_lib.sisu_statement_digest_noalloc(p, length, po, _stream(stream)))
 
 

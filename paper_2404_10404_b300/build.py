@@ -19,7 +19,7 @@ LIB = os.path.join(HERE, "libsisu.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU = ["eval.cu", "prove.cu", "field.cu", "api.cu", "noalloc.cu", "server.cu", "assoc.cu", "sort.cu"]
+CU = ["eval.cu", "prove.cu", "field.cu", "api.cu", "noalloc.cu", "server.cu", "assoc.cu", "sort.cu", "shard.cu"]
 CPP = ["verify.cpp"]
 HEADERS = ["fr.cuh", "fr_wide.cuh", "sha256.cuh", "internal.h", "launch.cuh", "handles.h"]
 

@@ -688,7 +688,14 @@ extern "C" void sisu_transcript_destroy(sisu_transcript* tr) { delete tr; }
 
 constexpr int kWsRegions = 14;
 
-static void workspace_sizes(const sisu_circuit* cc, size_t sizes[kWsRegions]) {
+// proof bytes of a circuit's shape with 2^c copies
+static size_t proof_len_c(const HostCircuit& hc, uint32_t c) {
+  size_t n = 8 + 4 * ((size_t)hc.d + 3);
+  for (uint32_t i = 0; i < hc.d; ++i) n += 32 * (3 * (size_t)c + 4 * (size_t)hc.s[i + 1] + 2);
+  return n;
+}
+
+static void workspace_sizes(const sisu_circuit* cc, size_t sizes[kWsRegions], uint32_t c_proof) {
   const HostCircuit& hc = cc->hc;
   uint32_t wmax_next = 1, wmax = 1, nmax = 1;
   for (uint32_t i = 0; i < hc.d; ++i) {
@@ -704,7 +711,7 @@ static void workspace_sizes(const sisu_circuit* cc, size_t sizes[kWsRegions]) {
   const size_t v[kWsRegions] = {half, (size_t)hc.C * 32, (size_t)nmax * 32, (size_t)wmax_next * 32,
                                 (size_t)wmax_next * 32, (size_t)wmax_next * 32, (size_t)wmax_next * 32,
                                 (size_t)wmax * 32, (size_t)kMaxPartials * 4 * 32, dig, sizeof(DevState),
-                                hc.proof_len(), eq_half_words(hc.c, smax) * 4, (size_t)nmax * 2 * 32};
+                                proof_len_c(hc, c_proof), eq_half_words(hc.c, smax) * 4, (size_t)nmax * 2 * 32};
   for (int k = 0; k < kWsRegions; ++k) sizes[k] = v[k];
 }
 
@@ -713,18 +720,26 @@ static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 namespace sisu {
 size_t workspace_footprint(const sisu_circuit* cc) {
   size_t sizes[kWsRegions], total = 0;
-  workspace_sizes(cc, sizes);
+  workspace_sizes(cc, sizes, cc->hc.c);
   for (size_t x : sizes) total += al256(x);
   return total;
 }
 
-// Lay out the workspace in `dev` (workspace_footprint bytes) with the pinned
-// proof bytes at `host` (proof_len + 16 bytes), header and state set on `st`.
-static int workspace_init(sisu_eval* ev, Workspace* ws, uint8_t* dev, uint8_t* host, cudaStream_t st) {
-  const sisu_circuit* cc = ev->circ;
+size_t workspace_footprint_c(const sisu_circuit* cc, uint32_t c_proof) {
+  size_t sizes[kWsRegions], total = 0;
+  workspace_sizes(cc, sizes, c_proof);
+  for (size_t x : sizes) total += al256(x);
+  return total;
+}
+
+// Lay out the workspace in `dev` (workspace_footprint_c bytes) with the
+// pinned proof bytes at `host` (proof bytes + 16), the header of a proof
+// over 2^c_proof copies and a zeroed state set on `st`.
+int workspace_layout(const sisu_circuit* cc, Workspace* ws, uint8_t* dev, uint8_t* host, uint32_t c_proof,
+                     cudaStream_t st) {
   const HostCircuit& hc = cc->hc;
   size_t sizes[kWsRegions];
-  workspace_sizes(cc, sizes);
+  workspace_sizes(cc, sizes, c_proof);
   uint8_t* p = dev;
   void* ptrs[kWsRegions];
   for (int k = 0; k < kWsRegions; ++k) {
@@ -745,7 +760,7 @@ static int workspace_init(sisu_eval* ev, Workspace* ws, uint8_t* dev, uint8_t* h
   ws->proof = (uint8_t*)ptrs[11];
   ws->eqh = (uint32_t*)ptrs[12];
   ws->P = (uint32_t*)ptrs[13];
-  ws->proof_len = hc.proof_len();
+  ws->proof_len = proof_len_c(hc, c_proof);
   ws->host = host;
   // the proof header is fixed by the circuit
   std::vector<uint8_t> hdr(8 + 4 * ((size_t)hc.d + 3));
@@ -754,13 +769,17 @@ static int workspace_init(sisu_eval* ev, Workspace* ws, uint8_t* dev, uint8_t* h
     hdr[at] = (uint8_t)v; hdr[at + 1] = (uint8_t)(v >> 8); hdr[at + 2] = (uint8_t)(v >> 16); hdr[at + 3] = (uint8_t)(v >> 24);
   };
   put(8, hc.d);
-  put(12, hc.c);
+  put(12, c_proof);
   for (uint32_t i = 0; i <= hc.d; ++i) put(16 + 4 * (size_t)i, hc.s[i]);
   // staged through the pinned proof buffer so that the copy can stay asynchronous
   memcpy(host, hdr.data(), hdr.size());
   CK(cudaMemcpyAsync(ws->proof, host, hdr.size(), cudaMemcpyHostToDevice, st), "header upload");
   CK(cudaMemsetAsync(ws->S, 0, sizeof(DevState), st), "memset");
   return SISU_OK;
+}
+
+static int workspace_init(sisu_eval* ev, Workspace* ws, uint8_t* dev, uint8_t* host, cudaStream_t st) {
+  return workspace_layout(ev->circ, ws, dev, host, ev->circ->hc.c, st);
 }
 
 int workspace_place(sisu_eval* ev, uint8_t* dev, uint8_t* host_pinned, cudaStream_t st) {
@@ -835,7 +854,10 @@ static int enqueue_prove(const sisu_circuit* cc, sisu_eval* ev, const sisu_trans
     }
     // copy phase: c rounds, each followed by the fold of its challenge
     const uint32_t* A = ev->V[i + 1];
-    const double per_pair = 5.0 * L.nmul + 2.0 * (L.ntot - L.nmul) + 4.0;
+    // algorithmic products per pair: 2 + 4 f per gate (a mul gate's three
+    // products and three weight products at t = 0, 1, 2; an add gate's two
+    // weighted sums), f the share of mul entries
+    const double per_pair = 2.0 * L.ntot + 4.0 * L.nmul;
     for (uint32_t k = 0; k < c; ++k) {
       const uint32_t* tab = k == 0 ? ev->V[i + 1] : w.T;
       const uint32_t h = hc.C >> (k + 1);
@@ -851,46 +873,55 @@ static int enqueue_prove(const sisu_circuit* cc, sisu_eval* ev, const sisu_trans
       A = w.T;
     }
     const size_t offx = off + 32 * 3 * (size_t)c;  // a copy round sends 3 values, an x/y round 2
-    const size_t offy = offx + 32 * 2 * (size_t)s;
-    const size_t offv = offy + 32 * 2 * (size_t)s;
-    if (Wn <= kTailMaxWidth) {
-      // Libra's two phases and the end of the layer in one cluster launch
-      TailParams tp;
-      tp.A = A; tp.E = w.E; tp.om = w.om; tp.sg = L.sgate;
-      tp.off1 = L.off1; tp.pos1 = L.pos1; tp.off2 = L.off2; tp.pos2 = L.pos2;
-      tp.nmul = L.nmul; tp.ntot = L.ntot; tp.Wn = Wn; tp.s = s; tp.P = w.P;
-      tp.At = w.At; tp.H1 = w.H1; tp.H2 = w.H2; tp.Ay = w.Ay;
-      tp.S = w.S; tp.proof = w.proof; tp.offx = offx; tp.offy = offy; tp.offv = offv; tp.last = i + 1 == d;
-      ProfScope ps(kProfGateRound, (double)Wn * (6.0 + s) + 2.0 * L.ntot, st);
-      CK(launch_layer_tail(tp, st), "layer tail");
-      off = offv + 64;
-      continue;
-    }
-    // wide layers: one launch per round over the whole GPU
-    {
-      ProfScope ps(kProfPhaseInit, (double)L.ntot + 2.0 * Wn, st);
-      CK(launch_xinit(A, w.E, w.om, L, Wn, w.At, w.H1, w.H2, w.Ay, st), "x init");
-    }
-    for (uint32_t k = 0; k < s; ++k) {
-      ProfScope ps(kProfGateRound, (double)(Wn >> k) / 2 * (k ? 9.0 : 3.0), st);
-      CK(launch_gate_round(w.At, w.H1, w.H2, Wn >> k, 0, k, w.partials, w.S, w.proof, offx + 64 * (size_t)k, st),
-         "x round");
-    }
-    {
-      ProfScope ps(kProfPhaseInit, (double)Wn * s + L.ntot + 3.0 * Wn, st);
-      CK(launch_eq_rx(w.S, s, Wn, w.Q, w.At, st), "eq(r_x)");
-      CK(launch_yinit(w.E, w.om, w.Q, L, Wn, w.H1, w.H2, w.S, st), "y init");
-    }
-    for (uint32_t k = 0; k < s; ++k) {
-      ProfScope ps(kProfGateRound, (double)(Wn >> k) / 2 * (k ? 9.0 : 3.0), st);
-      CK(launch_gate_round(w.Ay, w.H1, w.H2, Wn >> k, 1, k, w.partials, w.S, w.proof, offy + 64 * (size_t)k, st),
-         "y round");
-    }
-    {
-      ProfScope ps(kProfTranscript, 0, st);
-      CK(launch_layer_end(w.S, w.Ay, s, w.proof, offv, i + 1 == d, st), "layer end");
-    }
-    off = offv + 64;
+    if (int rc = sisu::enqueue_layer_phases(hc, L, w, i, A, w.E, offx, st)) return rc;
+    off = offx + 32 * 4 * (size_t)s + 64;
+  }
+  return SISU_OK;
+}
+
+// Libra's two phases (x, then y) and the end of gate layer i, from the
+// copy-bound row A = V~_{i+1}(r_b, .) and the copy weight E[0] = 2^32
+// eq(z_b, r_b); the phases' messages start at proof offset offx.
+int sisu::enqueue_layer_phases(const HostCircuit& hc, const DevLayer& L, Workspace& w, uint32_t i,
+                               const uint32_t* A, const uint32_t* E, size_t offx, cudaStream_t st) {
+  const uint32_t d = hc.d, s = hc.s[i + 1], Wn = hc.W[i + 1];
+  const size_t offy = offx + 32 * 2 * (size_t)s;
+  const size_t offv = offy + 32 * 2 * (size_t)s;
+  if (Wn <= kTailMaxWidth) {
+    // Libra's two phases and the end of the layer in one cluster launch
+    TailParams tp;
+    tp.A = A; tp.E = E; tp.om = w.om; tp.sg = L.sgate;
+    tp.off1 = L.off1; tp.pos1 = L.pos1; tp.off2 = L.off2; tp.pos2 = L.pos2;
+    tp.nmul = L.nmul; tp.ntot = L.ntot; tp.Wn = Wn; tp.s = s; tp.P = w.P;
+    tp.At = w.At; tp.H1 = w.H1; tp.H2 = w.H2; tp.Ay = w.Ay;
+    tp.S = w.S; tp.proof = w.proof; tp.offx = offx; tp.offy = offy; tp.offv = offv; tp.last = i + 1 == d;
+    ProfScope ps(kProfGateRound, (double)Wn * (6.0 + s) + 2.0 * L.ntot, st);
+    CK(launch_layer_tail(tp, st), "layer tail");
+    return SISU_OK;
+  }
+  // wide layers: one launch per round over the whole GPU
+  {
+    ProfScope ps(kProfPhaseInit, (double)L.ntot + 2.0 * Wn, st);
+    CK(launch_xinit(A, E, w.om, L, Wn, w.At, w.H1, w.H2, w.Ay, st), "x init");
+  }
+  for (uint32_t k = 0; k < s; ++k) {
+    ProfScope ps(kProfGateRound, (double)(Wn >> k) / 2 * (k ? 9.0 : 3.0), st);
+    CK(launch_gate_round(w.At, w.H1, w.H2, Wn >> k, 0, k, w.partials, w.S, w.proof, offx + 64 * (size_t)k, st),
+       "x round");
+  }
+  {
+    ProfScope ps(kProfPhaseInit, (double)Wn * s + L.ntot + 3.0 * Wn, st);
+    CK(launch_eq_rx(w.S, s, Wn, w.Q, w.At, st), "eq(r_x)");
+    CK(launch_yinit(E, w.om, w.Q, L, Wn, w.H1, w.H2, w.S, st), "y init");
+  }
+  for (uint32_t k = 0; k < s; ++k) {
+    ProfScope ps(kProfGateRound, (double)(Wn >> k) / 2 * (k ? 9.0 : 3.0), st);
+    CK(launch_gate_round(w.Ay, w.H1, w.H2, Wn >> k, 1, k, w.partials, w.S, w.proof, offy + 64 * (size_t)k, st),
+       "y round");
+  }
+  {
+    ProfScope ps(kProfTranscript, 0, st);
+    CK(launch_layer_end(w.S, w.Ay, s, w.proof, offv, i + 1 == d, st), "layer end");
   }
   return SISU_OK;
 }

@@ -317,6 +317,82 @@ int launch_digest_tables2(const uint32_t* ta, size_t na, const uint32_t* tb, siz
   return post_launch();
 }
 
+// Copy-sharded statement digests.  With W >= 32 elements a row (a whole
+// number of 1 KiB chunks, a power of two) and a power-of-two copy count,
+// the tree over a table is perfect and copy b's leaves form the subtree
+// whose root is node b of level log2(W / 32): a rank can form the roots of
+// its own copies, and the tree above them needs only those roots.
+
+// The per-copy subtree roots of two tables of nc copies (widths wa, wb
+// elements, both at least 32): roots_a[8 j .. 8 j + 7] for the rank's copy
+// j, then roots_b likewise.  Scratch: digest_scratch_words of each table.
+int launch_digest_copy_roots(const uint32_t* ta, uint32_t wa, const uint32_t* tb, uint32_t wb, uint32_t nc,
+                             uint32_t* scratch, uint32_t* roots_a, uint32_t* roots_b, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t na = (size_t)nc * wa, nb = (size_t)nc * wb;
+  const size_t la = na / 32, lb = nb / 32;
+  uint32_t* a0 = scratch;
+  uint32_t* a1 = a0 + 8 * la + 8;
+  uint32_t* b0 = scratch + digest_scratch_words(na * 32);
+  uint32_t* b1 = b0 + 8 * lb + 8;
+  k_digest_leaves_table2<<<grid_for(la + lb, 128, 32), 128, 0, st>>>(ta, na, a0, tb, nb, b0);
+  if (int e = post_launch()) return e;
+  size_t n_a = la, n_b = lb;
+  while (n_a > nc || n_b > nc) {  // down to one node per copy in each tree
+    const size_t m = (n_a > nc ? n_a / 2 : 0) + (n_b > nc ? n_b / 2 : 0);
+    k_digest_level2<<<grid_for(m, 128), 128, 0, st>>>(a0, n_a > nc ? n_a : 1, a1, b0, n_b > nc ? n_b : 1, b1);
+    if (int e = post_launch()) return e;
+    if (n_a > nc) {
+      std::swap(a0, a1);
+      n_a /= 2;
+    }
+    if (n_b > nc) {
+      std::swap(b0, b1);
+      n_b /= 2;
+    }
+  }
+  cudaError_t e = cudaMemcpyAsync(roots_a, a0, (size_t)nc * 32, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(roots_b, b0, (size_t)nc * 32, cudaMemcpyDeviceToDevice, st);
+  return (int)e;
+}
+
+// roots gathered rank by rank (rank q's part: its nc roots of table a, then
+// of table b) into copy order: copy b = j * world + q
+__global__ void k_roots_to_copy_order(const uint32_t* __restrict__ all, uint32_t nc, uint32_t world,
+                                      uint32_t* __restrict__ ra, uint32_t* __restrict__ rb) {
+  const size_t total = (size_t)nc * world * 16;
+  for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < total; w += (size_t)gridDim.x * blockDim.x) {
+    const size_t q = w / ((size_t)nc * 16), rest = w - q * nc * 16;
+    const size_t tab = rest / ((size_t)nc * 8), r2 = rest - tab * nc * 8, j = r2 / 8, k = r2 - j * 8;
+    (tab == 0 ? ra : rb)[(j * world + q) * 8 + k] = all[w];
+  }
+}
+
+// The two statement digests from every rank's per-copy roots (all: world
+// parts as above, nc copies a rank; tables of nc * world copies of wa and
+// wb elements).  Scratch: 2 * digest_scratch_words(nc * world * 1024).
+int launch_digest_from_roots(const uint32_t* all, uint32_t nc, uint32_t world, uint32_t wa, uint32_t wb,
+                             uint32_t* scratch, uint32_t* out_a, uint32_t* out_b, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t C = (size_t)nc * world;
+  uint32_t* a0 = scratch;
+  uint32_t* a1 = a0 + 8 * C + 8;
+  uint32_t* b0 = scratch + digest_scratch_words(C * 1024);
+  uint32_t* b1 = b0 + 8 * C + 8;
+  k_roots_to_copy_order<<<grid_for(C * 16, 128), 128, 0, st>>>(all, nc, world, a0, b0);
+  if (int e = post_launch()) return e;
+  size_t n = C;
+  while (n > 1) {
+    k_digest_level2<<<grid_for(n, 128), 128, 0, st>>>(a0, n, a1, b0, n, b1);
+    if (int e = post_launch()) return e;
+    std::swap(a0, a1);
+    std::swap(b0, b1);
+    n = (n + 1) / 2;
+  }
+  k_digest_final2<<<1, 32, 0, st>>>(a0, (uint64_t)C * wa * 32, 0, out_a, b0, (uint64_t)C * wb * 32, 0, out_b);
+  return post_launch();
+}
+
 int launch_digest_bytes(const uint8_t* data, size_t len, uint32_t* scratch, uint32_t* out_words, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   size_t nleaf = (len + 1023) / 1024;

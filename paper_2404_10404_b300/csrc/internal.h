@@ -110,16 +110,34 @@ int launch_digest_bytes(const uint8_t* data, size_t len, uint32_t* scratch, uint
 size_t digest_scratch_words(size_t len_bytes);
 
 int launch_transcript_init(const InitParams& p, DevState* S, void* stream);
+// cq, q: the copies are rank q's of 2^cq (copies j 2^cq + q, j < 2^c); 0, 0
+// for all copies
 int launch_layer_init(DevState* S, uint32_t layer, uint32_t c, uint32_t s_i, const DevLayer& L, uint32_t* E,
-                      uint32_t* omega_s, uint32_t* eqh, void* stream);
+                      uint32_t* omega_s, uint32_t* eqh, void* stream, uint32_t cq = 0, uint32_t q = 0);
 // words of the eq half-table scratch of launch_layer_init (copy bits c,
 // largest layer log-width smax)
 size_t eq_half_words(uint32_t c, uint32_t smax);
+// sums_out (not null): the round's sums g(0..3) go there (one rank of a
+// copy-sharded proof) instead of the message and transcript
 int launch_copy_round(const uint32_t* T, uint32_t sn, uint32_t h, const uint32_t* E, const uint32_t* omega_s,
                       const DevLayer& L, uint32_t* partials, DevState* S, uint8_t* proof, size_t off,
-                      uint32_t k, void* stream);
+                      uint32_t k, void* stream, uint32_t* sums_out = nullptr);
 int launch_copy_fold(const uint32_t* src, uint32_t* dst, uint32_t sn, uint32_t h, uint32_t* E,
                      DevState* S, uint32_t k, void* stream);
+// copy-sharded proofs: the round message from the gathered sums of every
+// rank; a rank's copy-bound row and weight as one message; rank 0's table
+// of the gathered rows (stride values apart) and weights
+int launch_shard_absorb(const uint32_t* sums_all, uint32_t world, DevState* S, uint8_t* proof, size_t off,
+                        uint32_t k, void* stream);
+int launch_shard_row(const uint32_t* A, const uint32_t* E, uint32_t Wn, uint32_t* out, void* stream);
+int launch_shard_table(const uint32_t* rows, uint32_t world, uint32_t Wn, uint32_t stride, uint32_t* T, uint32_t* E,
+                       void* stream);
+// per-copy Merkle subtree roots of two tables of nc copies (row widths of at
+// least 32 elements), and the two statement digests from every rank's roots
+int launch_digest_copy_roots(const uint32_t* ta, uint32_t wa, const uint32_t* tb, uint32_t wb, uint32_t nc,
+                             uint32_t* scratch, uint32_t* roots_a, uint32_t* roots_b, void* stream);
+int launch_digest_from_roots(const uint32_t* all, uint32_t nc, uint32_t world, uint32_t wa, uint32_t wb,
+                             uint32_t* scratch, uint32_t* out_a, uint32_t* out_b, void* stream);
 int launch_xinit(const uint32_t* Arow, const uint32_t* E, const uint32_t* omega_s, const DevLayer& L,
                  uint32_t Wn, uint32_t* At, uint32_t* H1, uint32_t* H2, uint32_t* Ay, void* stream);
 int launch_gate_round(uint32_t* A, uint32_t* B1, uint32_t* B2, uint32_t m, int phase, uint32_t k,

@@ -296,7 +296,14 @@ __device__ __forceinline__ Fr eq_half_entry(const Fr* P, uint32_t k0, uint32_t n
 // Half tables, in order: E high (plain: started from the integer 1), E low;
 // then layer 0: z_g high, low; layer i: alpha r_x high, r_x low, beta r_y
 // high, r_y low.
-__global__ void k_eq_halves(DevState* S, uint32_t layer, uint32_t c, uint32_t si, uint32_t* __restrict__ tab) {
+//
+// With cq > 0 the copies are those of one rank of 2^cq holding the copies
+// b = j 2^cq + q (Sec. 3.2.1: the machine index as the low copy bits): E
+// runs over the c high bits of b only, and its high half starts from the
+// rank's factor eq(point bits c .. c + cq - 1, q), so that E(j) is the
+// weight of global copy j 2^cq + q.
+__global__ void k_eq_halves(DevState* S, uint32_t layer, uint32_t c, uint32_t si, uint32_t* __restrict__ tab,
+                            uint32_t cq, uint32_t q) {
   pdl_wait();
   const uint32_t nE = eq_half_entries(c), nW = eq_half_entries(si);
   const uint32_t total = nE + (layer == 0 ? nW : 2 * nW);
@@ -312,6 +319,7 @@ __global__ void k_eq_halves(DevState* S, uint32_t layer, uint32_t c, uint32_t si
     Fr init = fr_one();
     // the copy weights come out plain and scaled by 2^32 (see the copy round)
     if (hi) init = isE ? fr_int_2_32() : layer == 0 ? fr_one() : which == 0 ? S->alpha : S->beta;
+    if (hi && isE && cq) init = eq_half_entry(P, c, cq, q, init);  // the rank's factor
     fr_store(tab, idx, eq_half_entry(P, hi ? 0 : nh, hi ? nh : n / 2, u, init));
   }
 }
@@ -346,10 +354,10 @@ __global__ void k_layer_init(uint32_t layer, uint32_t c, uint32_t si, const uint
 size_t eq_half_words(uint32_t c, uint32_t smax) { return 8 * ((size_t)eq_half_entries(c) + 2 * eq_half_entries(smax)); }
 
 int launch_layer_init(DevState* S, uint32_t layer, uint32_t c, uint32_t s_i, const DevLayer& L, uint32_t* E,
-                      uint32_t* omega_s, uint32_t* eqh, void* stream) {
+                      uint32_t* omega_s, uint32_t* eqh, void* stream, uint32_t cq, uint32_t q) {
   cudaStream_t st = (cudaStream_t)stream;
   const uint32_t nh = eq_half_entries(c) + (layer == 0 ? 1 : 2) * eq_half_entries(s_i);
-  const int rc = launch_pdl(k_eq_halves, grid_for(nh, 128), 128, st, S, layer, c, s_i, eqh);
+  const int rc = launch_pdl(k_eq_halves, grid_for(nh, 128), 128, st, S, layer, c, s_i, eqh, cq, q);
   if (rc) return rc;
   size_t n = ((size_t)1 << c) + L.ntot;
   return launch_pdl(k_layer_init, grid_for(n, 128), 128, st, layer, c, s_i, L.sgate, L.ntot, (const uint32_t*)eqh, E,
@@ -619,12 +627,15 @@ __device__ __forceinline__ Fr copy_items_warp(const uint32_t* __restrict__ T, ui
 
 // kWarp: the big rounds' form (m = 0, segments per warp); else the CTA-wide
 // form (any split; used for m > 0).
+// sums_out: null for a whole proof; for one rank of a copy-sharded proof
+// the rank's round sums g(0..3) (plain, below 2r) go there instead of the
+// round message and the transcript, which wait for every rank's sums.
 template <int BD, bool kWarp>
 __global__ void __launch_bounds__(BD) k_copy_round(const uint32_t* __restrict__ T, uint32_t sn, uint32_t h,
                                                    const uint32_t* __restrict__ E, const uint32_t* __restrict__ om,
                                                    const uint4* __restrict__ sg, uint32_t nmul, uint32_t ntot,
                                                    uint64_t per_cta, uint32_t m, uint32_t* partials, DevState* S,
-                                                   uint8_t* proof, size_t off, uint32_t k) {
+                                                   uint8_t* proof, size_t off, uint32_t k, uint32_t* sums_out) {
   pdl_wait();
   __shared__ __align__(16) uint32_t sh_e[BD / 32][16];  // E(j), E(j + h) of a warp's current segment
   if (threadIdx.x == BD - 32) warm_transcript_code(k, h);
@@ -650,13 +661,20 @@ __global__ void __launch_bounds__(BD) k_copy_round(const uint32_t* __restrict__ 
       if (threadIdx.x != 0) acc[t] = fr_zero();
     }
   }
-  if (grid_sum_last_block<BD, 4, true>(acc, partials, S) && threadIdx.x < 32)
-    round_finalize<4>(S, acc, proof, off, &S->rb[k]);
+  if (grid_sum_last_block<BD, 4, true>(acc, partials, S) && threadIdx.x < 32) {
+    if (sums_out) {
+      if (threadIdx.x == 0)
+#pragma unroll
+        for (int t = 0; t < 4; ++t) fr_store(sums_out, t, acc[t]);
+    } else {
+      round_finalize<4>(S, acc, proof, off, &S->rb[k]);
+    }
+  }
 }
 
 int launch_copy_round(const uint32_t* T, uint32_t sn, uint32_t h, const uint32_t* E, const uint32_t* omega_s,
                       const DevLayer& L, uint32_t* partials, DevState* S, uint8_t* proof, size_t off, uint32_t k,
-                      void* stream) {
+                      void* stream, uint32_t* sums_out) {
   cudaStream_t st = (cudaStream_t)stream;
   // 384 threads: at 168 registers one CTA fills the register file with 12
   // warps (256 threads left a third of it idle; measured: round 1 of a
@@ -674,9 +692,68 @@ int launch_copy_round(const uint32_t* T, uint32_t sn, uint32_t h, const uint32_t
   const CopySplit sp = copy_split(h, L.nmul, L.ntot, std::min<uint32_t>(kSMs * per_sm, kMaxPartials), BD);
   if (sp.m == 0)  // more pairs than CTAs: segments per warp
     return launch_pdl(k_copy_round<BD, true>, sp.nc, BD, st, T, sn, h, E, omega_s, L.sgate, L.nmul, L.ntot,
-                      sp.per_cta, sp.m, partials, S, proof, off, k);
+                      sp.per_cta, sp.m, partials, S, proof, off, k, sums_out);
   return launch_pdl(k_copy_round<BD, false>, sp.nc, BD, st, T, sn, h, E, omega_s, L.sgate, L.nmul, L.ntot,
-                    sp.per_cta, sp.m, partials, S, proof, off, k);
+                    sp.per_cta, sp.m, partials, S, proof, off, k, sums_out);
+}
+
+// ---------------------------------------------------------------------------
+// copy-sharded proofs (Sec. 3.2.1: the machine index is the low part of the
+// copy index, so every rank binds its own copy bits first and the round
+// polynomial of a copy round is the sum of the ranks' polynomials)
+
+// After the ranks' sums of round k are gathered (world x 4 values, rank by
+// rank, plain and below 2r): their sum is the round polynomial, which goes
+// into the proof and the transcript as in a whole proof (every rank runs
+// this, so every rank draws the same challenge).
+__global__ void k_shard_absorb(const uint32_t* __restrict__ sums_all, uint32_t world, DevState* S, uint8_t* proof,
+                               size_t off, uint32_t k) {
+  Fr v[4] = {fr_zero(), fr_zero(), fr_zero(), fr_zero()};
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      for (uint32_t q = 0; q < world; ++q) v[t] = fr_add(v[t], fr_load(sums_all, 4 * (size_t)q + t));
+  round_finalize<4>(S, v, proof, off, &S->rb[k]);
+}
+
+int launch_shard_absorb(const uint32_t* sums_all, uint32_t world, DevState* S, uint8_t* proof, size_t off,
+                        uint32_t k, void* stream) {
+  k_shard_absorb<<<1, 32, 0, (cudaStream_t)stream>>>(sums_all, world, S, proof, off, k);
+  return post_launch();
+}
+
+// the rank's copy-bound row A (Wn values) and its copy weight E[0] into one
+// message of Wn + 1 values
+__global__ void k_shard_row(const uint32_t* __restrict__ A, const uint32_t* __restrict__ E, uint32_t Wn,
+                            uint32_t* __restrict__ out) {
+  for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x <= Wn; x += gridDim.x * blockDim.x)
+    fr_store(out, x, fr_load(x < Wn ? A : E, x < Wn ? x : 0));
+}
+
+int launch_shard_row(const uint32_t* A, const uint32_t* E, uint32_t Wn, uint32_t* out, void* stream) {
+  k_shard_row<<<grid_for(Wn + 1, 128), 128, 0, (cudaStream_t)stream>>>(A, E, Wn, out);
+  return post_launch();
+}
+
+// rank 0: the gathered messages (rank q's at q * stride values) as the
+// table of world rows (row q = rank q's row: the rank is the copy index's
+// low part, the one still unbound) and its copy weights
+__global__ void k_shard_table(const uint32_t* __restrict__ rows, uint32_t world, uint32_t Wn, uint32_t stride,
+                              uint32_t* __restrict__ T, uint32_t* __restrict__ E) {
+  const size_t total = (size_t)world * (Wn + 1);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t q = i / (Wn + 1), x = i - q * (Wn + 1);
+    const Fr v = fr_load(rows, q * stride + x);
+    if (x < Wn) fr_store(T, q * Wn + x, v);
+    else fr_store(E, q, v);
+  }
+}
+
+int launch_shard_table(const uint32_t* rows, uint32_t world, uint32_t Wn, uint32_t stride, uint32_t* T, uint32_t* E,
+                       void* stream) {
+  k_shard_table<<<grid_for((size_t)world * (Wn + 1), 128), 128, 0, (cudaStream_t)stream>>>(rows, world, Wn, stride,
+                                                                                          T, E);
+  return post_launch();
 }
 
 // fold of the copy rows and of E by the round's challenge r = r_b[k]:

@@ -1,5 +1,5 @@
-"""Batched proving of independent instances of uneven size (SURVEY's batched
-configuration, scaled to sizes the oracle finishes quickly): every proof
+"""Batched proving of independent instances of uneven size (the batched
+workload's distribution, scaled to sizes the oracle finishes quickly): every proof
 equals the oracle's and the single-instance GPU proof, at every concurrency,
 on repeated calls (CUDA-graph replay) and in any order."""
 import numpy as np
@@ -64,3 +64,24 @@ def test_batch_domain_and_repeat_rejected(S, batch, oracle):
     with pytest.raises(S.SisuError) as e:
         S.prove_batch([gcs[0], gcs[0]], [evs[0], evs[0]])
     assert e.value.code == -1
+
+
+# instances of the batched workload itself (C = 2^U{6..14}, W = 2^U{8..12},
+# d = U{8..24}, 60% mul, seeds 4*2^32+j): the nine smallest of its first 64,
+# up to 2.9 M gates each, among them the widest width (4096)
+BATCHED_SMALL = [21, 29, 56, 57, 33, 30, 22, 34, 10]
+
+
+def test_batched_workload_instances_equal_oracle(S):
+    import os
+
+    from oracle import Oracle
+    o = Oracle()
+    o.set_threads(os.cpu_count() or 1)  # the proof bytes do not depend on it
+    circs = [synth.batched_instance(j) for j in BATCHED_SMALL]
+    xs = [synth.fr_bytes(synth.inputs_for(c)) for c in circs]
+    gcs = [S.Circuit.from_spec(c) for c in circs]
+    evs = [S.Eval(g, x) for g, x in zip(gcs, xs)]
+    want = [o.prove(c, x) for c, x in zip(circs, xs)]
+    for k in (1, 4, 9):
+        assert S.prove_batch(gcs, evs, concurrency=k) == want
