@@ -423,6 +423,18 @@ int sisu_statement_digest(const uint8_t* data, size_t len, uint8_t* out, void* s
  * CUDA (with the runtime's error string). */
 int sisu_statement_digest_noalloc(const uint8_t* data, size_t len, uint8_t* out, void* stream);
 
+/* Launch shape of the copy-round kernel for layers whose next layer has
+ * 2^log_width positions, in rounds of 2^log_pairs pairs (both < 25), as an
+ * autotuner picks it: cta_threads 128, 256 or 384 (0 restores the
+ * default), form 0 = per-warp pair segments while pairs outnumber CTAs
+ * (the default), 1 = CTA-wide segments, 2 = per-warp segments always,
+ * min_items = (pair, gate) items a CTA at least (0: one per thread).
+ * Proof bytes do not depend on it.  Process-wide; set it before the first
+ * proof of an eval handle (a handle replays the launches it captured).
+ * Errors: INVALID_ARG. */
+int sisu_tune_copy_round(uint32_t log_width, uint32_t log_pairs, uint32_t cta_threads, uint32_t form,
+                         uint32_t min_items);
+
 /* Integer-pipe microbenchmarks used for the roofline: kind 0 = independent
  * 32-bit multiply-add chains (mad.lo), kind 1 = mad.hi chains, kind 2 =
  * Montgomery products as the kernels call them, kind 3 = the same products

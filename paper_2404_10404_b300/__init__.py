@@ -36,7 +36,7 @@ ENTRY_POINTS = [
     "sisu_server_pending", "sisu_server_pause", "sisu_server_destroy", "sisu_job_footprint",
     "sisu_shard_buffer_sizes", "sisu_shard_create", "sisu_shard_destroy", "sisu_shard_info", "sisu_shard_roots",
     "sisu_shard_begin", "sisu_shard_layer_begin", "sisu_shard_copy_round", "sisu_shard_absorb", "sisu_shard_row",
-    "sisu_shard_finish", "sisu_shard_proof",
+    "sisu_shard_finish", "sisu_shard_proof", "sisu_tune_copy_round",
     "sisu_assoc_hash", "sisu_assoc_hash_segments", "sisu_pairwise_distinct_check",
     "sisu_pairwise_distinct_check_segments", "sisu_sort_elements", "sisu_assoc_epochs",
 ]
@@ -118,6 +118,7 @@ def _load():
         "sisu_shard_row": ([vp, u32, vp], ctypes.c_int),
         "sisu_shard_finish": ([vp, u32, vp], ctypes.c_int),
         "sisu_shard_proof": ([vp, vp, vp, sz, ctypes.POINTER(sz)], ctypes.c_int),
+        "sisu_tune_copy_round": ([u32, u32, u32, u32, u32], ctypes.c_int),
         "sisu_fr_batch": ([ctypes.c_int, vp, vp, vp, sz, vp], ctypes.c_int),
         "sisu_statement_digest": ([vp, sz, u8p, vp], ctypes.c_int),
         "sisu_statement_digest_noalloc": ([vp, sz, vp, vp], ctypes.c_int),
@@ -497,6 +498,12 @@ class Server:
 
     def __del__(self):
         self.close()
+
+
+def tune_copy_round(log_width: int, log_pairs: int, cta_threads: int, form: int = 0, min_items: int = 0):
+    """Set the copy round's launch shape for one (layer width, pairs) class
+    (``sisu_tune_copy_round``; cta_threads 0 restores the default)."""
+    _check(_lib.sisu_tune_copy_round(int(log_width), int(log_pairs), int(cta_threads), int(form), int(min_items)))
 
 
 def server_footprint(circ: Circuit, inputs_on_device: bool = False) -> int:

@@ -1183,6 +1183,13 @@ extern "C" int sisu_microbench(int kind, uint32_t blocks, uint32_t threads, uint
   return SISU_OK;
 }
 
+extern "C" int sisu_tune_copy_round(uint32_t log_width, uint32_t log_pairs, uint32_t cta_threads, uint32_t form,
+                                    uint32_t min_items) {
+  if (set_copy_tune(log_width, log_pairs, cta_threads, form, min_items))
+    return fail(SISU_ERR_INVALID_ARG, "copy-round tuning entry out of range");
+  return SISU_OK;
+}
+
 extern "C" uint64_t sisu_kernel_launches(void) { return launches_add(0); }
 extern "C" void sisu_free(void* p) { free(p); }
 extern "C" const char* sisu_last_error(void) { return g_err; }

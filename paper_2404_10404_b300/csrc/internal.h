@@ -117,6 +117,9 @@ int launch_layer_init(DevState* S, uint32_t layer, uint32_t c, uint32_t s_i, con
 // words of the eq half-table scratch of launch_layer_init (copy bits c,
 // largest layer log-width smax)
 size_t eq_half_words(uint32_t c, uint32_t smax);
+// the copy round's launch shape for layers of 2^sn positions and rounds of
+// 2^log_pairs pairs (bd 0: the default); -1 for a value out of range
+int set_copy_tune(uint32_t sn, uint32_t log_pairs, uint32_t bd, uint32_t form, uint32_t min_items);
 // sums_out (not null): the round's sums g(0..3) go there (one rank of a
 // copy-sharded proof) instead of the message and transcript
 int launch_copy_round(const uint32_t* T, uint32_t sn, uint32_t h, const uint32_t* E, const uint32_t* omega_s,

@@ -672,14 +672,24 @@ __global__ void __launch_bounds__(BD) k_copy_round(const uint32_t* __restrict__ 
   }
 }
 
-int launch_copy_round(const uint32_t* T, uint32_t sn, uint32_t h, const uint32_t* E, const uint32_t* omega_s,
-                      const DevLayer& L, uint32_t* partials, DevState* S, uint8_t* proof, size_t off, uint32_t k,
-                      void* stream, uint32_t* sums_out) {
-  cudaStream_t st = (cudaStream_t)stream;
-  // 384 threads: at 168 registers one CTA fills the register file with 12
-  // warps (256 threads left a third of it idle; measured: round 1 of a
-  // medium layer 224 -> 206 us)
-  constexpr int BD = 384;
+// Launch shapes of the copy round, chosen per (log2 W_{i+1}, log2 pairs) by
+// a tuning table the host fills (sisu_tune_copy_round; unset entries keep
+// the default): the CTA width (128, 256 or 384 threads), the form (per-warp
+// pair segments or CTA-wide segments) and the CTA count's granularity (at
+// least `min_items` (pair, gate) items a CTA).  Default: 384 threads (at
+// 168 registers one CTA fills the register file with 12 warps; 256 threads
+// left a third of it idle: round 1 of a medium layer 224 -> 206 us), the
+// per-warp form while pairs outnumber CTAs, about one item a thread.
+struct CopyTune {
+  uint16_t bd;        // 0: unset
+  uint8_t form;       // 0: per-warp segments iff more pairs than CTAs, 1: CTA-wide, 2: per-warp
+  uint32_t min_items;
+};
+constexpr uint32_t kTuneLog = 25;
+static CopyTune g_copy_tune[kTuneLog][kTuneLog];
+
+template <int BD>
+static int copy_round_per_sm() {
   static int per_sm = 0;
   if (per_sm == 0) {
     int n = 0;
@@ -687,14 +697,50 @@ int launch_copy_round(const uint32_t* T, uint32_t sn, uint32_t h, const uint32_t
       n = 1;
     per_sm = n;
   }
+  return per_sm;
+}
+
+template <int BD>
+static int launch_copy_round_bd(int form, uint32_t min_items, const uint32_t* T, uint32_t sn, uint32_t h,
+                                const uint32_t* E, const uint32_t* omega_s, const DevLayer& L, uint32_t* partials,
+                                DevState* S, uint8_t* proof, size_t off, uint32_t k, cudaStream_t st,
+                                uint32_t* sums_out) {
+  const uint32_t ncmax = std::min<uint32_t>(kSMs * copy_round_per_sm<BD>(), kMaxPartials);
   // contiguous ranges of equal cost: one wave of CTAs, and for small rounds
-  // about one item per thread (short serial chains)
-  const CopySplit sp = copy_split(h, L.nmul, L.ntot, std::min<uint32_t>(kSMs * per_sm, kMaxPartials), BD);
-  if (sp.m == 0)  // more pairs than CTAs: segments per warp
+  // about min_items items a CTA (short serial chains)
+  const CopySplit sp = copy_split(h, L.nmul, L.ntot, ncmax, min_items ? min_items : BD);
+  const bool warp = form == 2 || (form == 0 && sp.m == 0);
+  if (warp)
     return launch_pdl(k_copy_round<BD, true>, sp.nc, BD, st, T, sn, h, E, omega_s, L.sgate, L.nmul, L.ntot,
                       sp.per_cta, sp.m, partials, S, proof, off, k, sums_out);
   return launch_pdl(k_copy_round<BD, false>, sp.nc, BD, st, T, sn, h, E, omega_s, L.sgate, L.nmul, L.ntot,
                     sp.per_cta, sp.m, partials, S, proof, off, k, sums_out);
+}
+
+int launch_copy_round(const uint32_t* T, uint32_t sn, uint32_t h, const uint32_t* E, const uint32_t* omega_s,
+                      const DevLayer& L, uint32_t* partials, DevState* S, uint8_t* proof, size_t off, uint32_t k,
+                      void* stream, uint32_t* sums_out) {
+  cudaStream_t st = (cudaStream_t)stream;
+  uint32_t lh = 0;
+  while ((2u << lh) <= h) ++lh;
+  CopyTune t = {384, 0, 0};
+  if (sn < kTuneLog && lh < kTuneLog && g_copy_tune[sn][lh].bd) t = g_copy_tune[sn][lh];
+  if (t.bd == 128)
+    return launch_copy_round_bd<128>(t.form, t.min_items, T, sn, h, E, omega_s, L, partials, S, proof, off, k, st,
+                                     sums_out);
+  if (t.bd == 256)
+    return launch_copy_round_bd<256>(t.form, t.min_items, T, sn, h, E, omega_s, L, partials, S, proof, off, k, st,
+                                     sums_out);
+  return launch_copy_round_bd<384>(t.form, t.min_items, T, sn, h, E, omega_s, L, partials, S, proof, off, k, st,
+                                   sums_out);
+}
+
+int set_copy_tune(uint32_t sn, uint32_t log_pairs, uint32_t bd, uint32_t form, uint32_t min_items) {
+  if (sn >= kTuneLog || log_pairs >= kTuneLog) return -1;
+  if (bd != 0 && bd != 128 && bd != 256 && bd != 384) return -1;
+  if (form > 2) return -1;
+  g_copy_tune[sn][log_pairs] = CopyTune{(uint16_t)bd, (uint8_t)form, min_items};
+  return 0;
 }
 
 // ---------------------------------------------------------------------------
