@@ -59,6 +59,31 @@ class _CircuitHandle:
             self.h = None
 
 
+class _GeneralHandle:
+    def __init__(self, lib, circ):
+        self.lib = lib
+        err = ctypes.c_int(0)
+        u32 = ctypes.POINTER(ctypes.c_uint32)
+        d = circ.depth
+        widths = np.ascontiguousarray(circ.widths, dtype=np.uint32)
+        types = np.ascontiguousarray(np.concatenate([circ.types[i] for i in range(d)]), dtype=np.uint8)
+        in1 = np.ascontiguousarray(np.concatenate([circ.in1[i] for i in range(d)]), dtype=np.uint32)
+        src = np.ascontiguousarray(np.concatenate([circ.layer_src(i) for i in range(d)]), dtype=np.uint32)
+        in2 = np.ascontiguousarray(np.concatenate([circ.in2[i] for i in range(d)]), dtype=np.uint32)
+        self._keep = (widths, types, in1, src, in2)
+        self.h = lib.so_gcircuit_new(ctypes.c_uint32(d), widths.ctypes.data_as(u32),
+                                     types.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), in1.ctypes.data_as(u32),
+                                     src.ctypes.data_as(u32), in2.ctypes.data_as(u32), ctypes.c_uint32(circ.n_copies),
+                                     ctypes.byref(err))
+        if not self.h:
+            raise ValueError(f"oracle rejected the general circuit (code {err.value})")
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            self.lib.so_gcircuit_free(self.h)
+            self.h = None
+
+
 class Oracle:
     """The oracle's entry points, on canonical little-endian byte strings."""
 
@@ -87,6 +112,19 @@ class Oracle:
         lib.so_assoc_F.argtypes = [ctypes.c_char_p, sz, ctypes.c_char_p]
         lib.so_assoc_hash.argtypes = [ctypes.c_char_p, sz, ctypes.c_char_p, ctypes.c_char_p]
         lib.so_pairwise_distinct_check.argtypes = [ctypes.c_char_p, ctypes.c_char_p, sz]
+        lib.so_gcircuit_new.restype = vp
+        lib.so_gcircuit_new.argtypes = [ctypes.c_uint32, u32p, u8p, u32p, u32p, u32p, ctypes.c_uint32,
+                                        ctypes.POINTER(ctypes.c_int)]
+        lib.so_gcircuit_free.argtypes = [vp]
+        lib.so_gproof_len.restype = sz
+        lib.so_gproof_len.argtypes = [vp]
+        lib.so_gprove.argtypes = [vp, ctypes.c_char_p, ctypes.c_char_p, sz, ctypes.c_char_p, sz, ctypes.POINTER(sz)]
+        lib.so_gverify.argtypes = [vp, ctypes.c_char_p, ctypes.c_char_p, ctypes.c_char_p, sz, ctypes.c_char_p, sz]
+        lib.so_goutputs.argtypes = [vp, ctypes.c_char_p, ctypes.c_char_p]
+        lib.so_gcircuit_log_xwidth.restype = ctypes.c_uint32
+        lib.so_gcircuit_log_xwidth.argtypes = [vp, ctypes.c_uint32]
+        lib.so_gcircuit_blocks.restype = ctypes.c_uint32
+        lib.so_gcircuit_blocks.argtypes = [vp, ctypes.c_uint32]
         lib.so_set_threads.restype = ctypes.c_int
         lib.so_set_threads.argtypes = [ctypes.c_int]
         lib.so_circuit_log_copies.restype = ctypes.c_uint32
@@ -95,6 +133,46 @@ class Oracle:
         lib.so_circuit_log_width.argtypes = [vp, ctypes.c_uint32]
         self.lib = lib
         self._handles = {}
+
+    # -- general circuits (Sec. 2.7) ---------------------------------------
+    def ghandle(self, circ):
+        key = ("g", id(circ))
+        h = self._handles.get(key)
+        if h is None or h[0] is not circ:
+            h = (circ, _GeneralHandle(self.lib, circ))
+            self._handles[key] = h
+        return h[1].h
+
+    def general_proof_len(self, circ) -> int:
+        return int(self.lib.so_gproof_len(self.ghandle(circ)))
+
+    def general_shape(self, circ):
+        """Per gate layer: (log2 width of its virtual layer, blocks)."""
+        h = self.ghandle(circ)
+        return [(int(self.lib.so_gcircuit_log_xwidth(h, i)), int(self.lib.so_gcircuit_blocks(h, i)))
+                for i in range(circ.depth)]
+
+    def prove_general(self, circ, inputs: bytes, domain: bytes | None = None) -> bytes:
+        n = self.general_proof_len(circ)
+        buf = ctypes.create_string_buffer(n)
+        ln = ctypes.c_size_t(0)
+        rc = self.lib.so_gprove(self.ghandle(circ), bytes(inputs), domain, len(domain or b""), buf, n,
+                                ctypes.byref(ln))
+        if rc != OK:
+            raise ValueError(f"oracle prove failed (code {rc})")
+        return buf.raw[:ln.value]
+
+    def verify_general(self, circ, inputs: bytes, outputs: bytes, proof: bytes,
+                       domain: bytes | None = None) -> int:
+        return int(self.lib.so_gverify(self.ghandle(circ), bytes(inputs), bytes(outputs), bytes(proof),
+                                       len(proof), domain, len(domain or b"")))
+
+    def outputs_general(self, circ, inputs: bytes) -> bytes:
+        out = ctypes.create_string_buffer(32 * circ.n_copies * circ.widths[0])
+        rc = self.lib.so_goutputs(self.ghandle(circ), bytes(inputs), out)
+        if rc != OK:
+            raise ValueError(f"oracle eval failed (code {rc})")
+        return out.raw
 
     def set_threads(self, n: int) -> int:
         """Threads of the prover's copy sums, folds and evaluation; returns

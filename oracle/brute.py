@@ -438,3 +438,171 @@ def pairwise_distinct_check(A, A_sorted) -> int:
         if A_sorted[i] <= A_sorted[i - 1]:
             return 0
     return 1
+
+# ---------------------------------------------------------------------------
+# General circuits (Sec. 2.7): the second input of a gate of layer i may come
+# from any deeper layer j (i + 1 <= j <= d); the first input stays in layer
+# i + 1.  Layer i's sumcheck runs over a virtual layer X_i: layer i + 1 in
+# full (block 0), then, for each deeper layer j that layer i reads, only the
+# gates of j it uses, in ascending order (the "used gates" indexing of Sec.
+# 2.7: their indexes differ from their positions in layer j), padded to a
+# power of two.  After the sumcheck the prover sends, for both final points
+# r_x and r_y, the part of X~_i(r_b, r) carried by each block:
+#     v_beta(r) = sum_{u in block beta} eq(r, u) X~_i(r_b, u),
+# which are claims on the block's layer (a weighted sum of its values at copy
+# point r_b).  A layer receives such claims from every layer that reads it;
+# they are combined by random coefficients into one claim, each term keeping
+# its own copy point:
+#     sum_T sum_b eq(z_T, b) sum_g M_T(g) V_j(b, g),
+#     M_T(g) = alpha_x eq(r_x, u(g)) + alpha_y eq(r_y, u(g))   (g used by T's block),
+# which is the next layer sumcheck's starting claim.  The input layer's claims
+# are checked against the clear inputs.  With every second input in layer
+# i + 1 this is exactly the layered protocol above (one block, one term).
+
+class GeneralPadded:
+    """A general circuit padded to power-of-two widths and copy count, with
+    the virtual layers X_i of its gate layers."""
+
+    def __init__(self, circ):
+        self.d = circ.depth
+        self.Creal = circ.n_copies
+        self.c = log2_ceil(circ.n_copies)
+        self.C = 1 << self.c
+        self.wreal = list(circ.widths)
+        self.s = [log2_ceil(w) for w in circ.widths]
+        self.W = [1 << s for s in self.s]
+        self.gates, self.blocks, self.sx, self.u2 = [], [], [], []
+        for i in range(self.d):
+            srcs = [int(v) for v in circ.layer_src(i)]
+            gates = [(g, int(t), int(a), int(j), int(b)) for g, (t, a, j, b) in
+                     enumerate(zip(circ.types[i], circ.in1[i], srcs, circ.in2[i]))]
+            blocks = [(i + 1, 0, list(range(self.W[i + 1])))]
+            base = self.W[i + 1]
+            for j in range(i + 2, self.d + 1):
+                used = sorted({b for (_, _, _, jj, b) in gates if jj == j})
+                if used:
+                    blocks.append((j, base, used))
+                    base += len(used)
+            sx = log2_ceil(base)
+            index = {}
+            for j, b0, ys in blocks:
+                for k, y in enumerate(ys):
+                    index[(j, y)] = b0 + k
+            self.gates.append(gates)
+            self.blocks.append(blocks)
+            self.sx.append(sx)
+            self.u2.append([index[(j, b)] for (_, _, _, j, b) in gates])
+
+    def wiring_bytes(self) -> bytes:
+        """Per padded gate: u8 type || u32 in1 || u32 in2 when the second
+        input is in layer i + 1, u8 (4 + type) || u32 in1 || u32 in2 ||
+        u32 layer when it is deeper, (2, 0, 0) for a padding gate."""
+        out = bytearray()
+        for i in range(self.d):
+            by_gate = {g: (t, a, j, b) for g, t, a, j, b in self.gates[i]}
+            for g in range(self.W[i]):
+                if g not in by_gate:
+                    out += struct.pack("<BII", 2, 0, 0)
+                    continue
+                t, a, j, b = by_gate[g]
+                out += struct.pack("<BII", t, a, b) if j == i + 1 else struct.pack("<BIII", 4 + t, a, b, j)
+        return bytes(out)
+
+
+def evaluate_general(pc: GeneralPadded, inputs):
+    d = pc.d
+    V = [None] * (d + 1)
+    V[d] = [0] * (pc.C * pc.W[d])
+    for b in range(pc.Creal):
+        for x in range(pc.wreal[d]):
+            V[d][b * pc.W[d] + x] = inputs[b * pc.wreal[d] + x] % P
+    for i in range(d - 1, -1, -1):
+        V[i] = [0] * (pc.C * pc.W[i])
+        for b in range(pc.C):
+            for g, t, a, j, y in pc.gates[i]:
+                u, v = V[i + 1][b * pc.W[i + 1] + a], V[j][b * pc.W[j] + y]
+                V[i][b * pc.W[i] + g] = ((u + v) if t == 0 else u * v) % P
+    return V
+
+
+def prove_general(circ, inputs, domain: bytes | None = None, check: bool = True) -> bytes:
+    """Proof bytes of a general circuit, every round polynomial by
+    brute-force enumeration over the hypercube."""
+    pc = GeneralPadded(circ)
+    d, c = pc.d, pc.c
+    V = evaluate_general(pc, inputs)
+    tr = Transcript(domain, d, c, pc.s, digest(pc.wiring_bytes()),
+                    digest(b"".join(fe(v) for v in V[d])), digest(b"".join(fe(v) for v in V[0])))
+    out = bytearray(b"SISUGKR2" + struct.pack("<II", d, c) + b"".join(struct.pack("<I", v) for v in pc.s))
+    zb = [tr.challenge() for _ in range(c)]
+    zg = [tr.challenge() for _ in range(pc.s[0])]
+    # terms[j]: the combined claim on layer j as (copy point, gate weights)
+    terms = {0: [(zb, [eq(zg, bits_msb(g, pc.s[0])) for g in range(pc.W[0])])]}
+    claim = mle(V[0], zb + zg)
+    claims = {j: 0 for j in range(d + 1)}
+    for i in range(d):
+        sx, WX = pc.sx[i], 1 << pc.sx[i]
+        X = [0] * (pc.C * WX)
+        for j, b0, ys in pc.blocks[i]:
+            for k, y in enumerate(ys):
+                for b in range(pc.C):
+                    X[b * WX + b0 + k] = V[j][b * pc.W[j] + y]
+        gates = [(g, t, bits_msb(a, sx), bits_msb(u, sx)) for (g, t, a, _, _), u in zip(pc.gates[i], pc.u2[i])]
+        memo = {}
+
+        def Xt(point):
+            key = tuple(point)
+            if key not in memo:
+                memo[key] = mle(X, point)
+            return memo[key]
+
+        def f(point, gates=gates, layer_terms=terms[i], sx=sx):
+            b, x, y = point[:c], point[c:c + sx], point[c + sx:]
+            vx, vy = Xt(b + x), Xt(b + y)
+            acc = 0
+            for zt, M in layer_terms:
+                part = 0
+                for g, t, a1, a2 in gates:
+                    op = (vx + vy) if t == 0 else vx * vy
+                    part += M[g] * eq(x, a1) * eq(y, a2) * op
+                acc += eq(zt, b) * part
+            return acc % P
+
+        if i > 0:
+            claim = claims[i]
+        nvars = c + 2 * sx
+        bound = []
+        for k in range(nvars):
+            nodes = 4 if k < c else 3
+            rest = nvars - k - 1
+            g = [sum(f(bound + [t] + bits_msb(u, rest)) for u in range(1 << rest)) % P for t in range(nodes)]
+            if check:
+                assert (g[0] + g[1]) % P == claim, f"layer {i} round {k}: g(0)+g(1) != claim"
+            sent = [g[0]] + g[2:]
+            out += b"".join(fe(v) for v in sent)
+            tr.absorb(b"R", sent)
+            r = tr.challenge()
+            claim = interpolate(g, r)
+            bound.append(r)
+        rb, rx, ry = bound[:c], bound[c:c + sx], bound[c + sx:]
+        if check:
+            assert claim == f(bound), f"layer {i}: final identity fails"
+        col = [sum(eq(rb, bits_msb(b, c)) * X[b * WX + u] for b in range(pc.C)) % P for u in range(WX)]
+        vb = {}
+        for name, r in (("x", rx), ("y", ry)):
+            vb[name] = [sum(eq(r, bits_msb(b0 + k, sx)) * col[b0 + k] for k in range(len(ys))) % P
+                        for _, b0, ys in pc.blocks[i]]
+            if check:
+                assert sum(vb[name]) % P == Xt(rb + r)
+        out += b"".join(fe(v) for v in vb["x"] + vb["y"])
+        tr.absorb(b"V", vb["x"] + vb["y"])
+        for beta, (j, b0, ys) in enumerate(pc.blocks[i]):
+            if j == d:
+                continue
+            ax, ay = tr.challenge(), tr.challenge()
+            M = [0] * pc.W[j]
+            for k, y in enumerate(ys):
+                M[y] = (ax * eq(rx, bits_msb(b0 + k, sx)) + ay * eq(ry, bits_msb(b0 + k, sx))) % P
+            terms.setdefault(j, []).append((rb, M))
+            claims[j] = (claims[j] + ax * vb["x"][beta] + ay * vb["y"][beta]) % P
+    return bytes(out)

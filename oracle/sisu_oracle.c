@@ -1221,3 +1221,511 @@ int so_pairwise_distinct_check(const uint8_t *A, const uint8_t *As, size_t n) {
     }
     return 1;
 }
+
+/* ------------------------------------------------------------------ */
+/* General circuits (Sec. 2.7).  The second input of a gate of layer i   */
+/* may come from any deeper layer j (i + 1 <= j <= d); the first input    */
+/* stays in layer i + 1.  Layer i's sumcheck runs over a virtual layer    */
+/* X_i: layer i + 1 in full (block 0), then, for each deeper layer j that */
+/* layer i reads, only the gates of j it uses, ascending (the "used       */
+/* gates" indexing of Sec. 2.7), padded to a power of two.  After the     */
+/* rounds the prover sends, for r = r_x and r = r_y, the part of          */
+/* X~_i(r_b, r) that each block carries,                                  */
+/*     v_beta(r) = sum_{u in block beta} eq(r, u) X~_i(r_b, u),          */
+/* a claim on the block's layer.  A layer's claims from every reader are  */
+/* combined by random coefficients, each term keeping its own copy point: */
+/*     sum_T sum_b eq(z_T, b) sum_g M_T(g) V_j(b, g),                     */
+/*     M_T(g) = alpha_x eq(r_x, u(g)) + alpha_y eq(r_y, u(g)),            */
+/* which starts the next layer's sumcheck; the copy rounds sum the terms. */
+/* The input layer's claims are checked against the clear inputs.  With  */
+/* every second input in layer i + 1 this is the layered protocol above.  */
+
+#define SO_MAX_BLOCKS (SO_MAX_DEPTH + 1)
+
+typedef struct so_gcircuit {
+    uint32_t d, c, C, Creal;
+    uint32_t s[SO_MAX_DEPTH + 1], W[SO_MAX_DEPTH + 1], wreal[SO_MAX_DEPTH + 1];
+    uint8_t *type[SO_MAX_DEPTH];            /* one entry per real gate of layer i */
+    uint32_t *in1[SO_MAX_DEPTH], *src[SO_MAX_DEPTH], *in2[SO_MAX_DEPTH];
+    uint32_t sx[SO_MAX_DEPTH], nb[SO_MAX_DEPTH];     /* X_i: log2 width, blocks */
+    uint32_t blayer[SO_MAX_DEPTH][SO_MAX_BLOCKS], bbase[SO_MAX_DEPTH][SO_MAX_BLOCKS];
+    uint32_t bcount[SO_MAX_DEPTH][SO_MAX_BLOCKS];
+    uint32_t *bys[SO_MAX_DEPTH][SO_MAX_BLOCKS];     /* the block's gates in its layer (block 0: all) */
+    uint32_t *u2[SO_MAX_DEPTH];                     /* X_i index of each gate's second input */
+    uint8_t wiring_digest[32];
+} so_gcircuit;
+
+void so_gcircuit_free(so_gcircuit *gc) {
+    if (!gc) return;
+    for (uint32_t i = 0; i < gc->d; ++i) {
+        free(gc->type[i]); free(gc->in1[i]); free(gc->src[i]); free(gc->in2[i]); free(gc->u2[i]);
+        for (uint32_t b = 0; b < gc->nb[i]; ++b) free(gc->bys[i][b]);
+    }
+    free(gc);
+}
+
+/* Wiring bytes: per padded gate of layer i, u8 type || u32le in1 || u32le
+ * in2 when its second input is in layer i + 1, u8 (4 + type) || u32le in1
+ * || u32le in2 || u32le layer when it is deeper, (2, 0, 0) when padding. */
+static int gwiring_digest(so_gcircuit *gc) {
+    size_t n = 0;
+    for (uint32_t i = 0; i < gc->d; ++i) n += (size_t)gc->W[i] * 13;
+    uint8_t *buf = (uint8_t *)malloc(n ? n : 1), *p = buf;
+    if (!buf) return SO_ERR_OOM;
+    for (uint32_t i = 0; i < gc->d; ++i)
+        for (uint32_t g = 0; g < gc->W[i]; ++g) {
+            if (g >= gc->wreal[i]) {
+                *p++ = 2; put_u32(p, 0); p += 4; put_u32(p, 0); p += 4;
+            } else if (gc->src[i][g] == i + 1) {
+                *p++ = gc->type[i][g]; put_u32(p, gc->in1[i][g]); p += 4; put_u32(p, gc->in2[i][g]); p += 4;
+            } else {
+                *p++ = (uint8_t)(4 + gc->type[i][g]); put_u32(p, gc->in1[i][g]); p += 4;
+                put_u32(p, gc->in2[i][g]); p += 4; put_u32(p, gc->src[i][g]); p += 4;
+            }
+        }
+    int rc = statement_digest(buf, (size_t)(p - buf), gc->wiring_digest);
+    free(buf);
+    return rc;
+}
+
+so_gcircuit *so_gcircuit_new(uint32_t d, const uint32_t *widths, const uint8_t *types, const uint32_t *in1,
+                             const uint32_t *src, const uint32_t *in2, uint32_t n_copies, int *err) {
+    so_init();
+    *err = SO_ERR_ARG;
+    if (d < 1 || d > SO_MAX_DEPTH || n_copies < 1 || !widths || !types || !in1 || !src || !in2) return NULL;
+    for (uint32_t i = 0; i <= d; ++i)
+        if (widths[i] < 1 || widths[i] > (1u << 24)) return NULL;
+    so_gcircuit *gc = (so_gcircuit *)calloc(1, sizeof *gc);
+    if (!gc) { *err = SO_ERR_OOM; return NULL; }
+    gc->Creal = n_copies;
+    gc->c = ceil_log2(n_copies);
+    gc->C = 1u << gc->c;
+    for (uint32_t i = 0; i <= d; ++i) {
+        gc->wreal[i] = widths[i];
+        gc->s[i] = ceil_log2(widths[i]);
+        gc->W[i] = 1u << gc->s[i];
+    }
+    size_t off = 0;
+    for (uint32_t i = 0; i < d; ++i) {
+        uint32_t n = widths[i];
+        gc->d = i + 1; /* so that so_gcircuit_free releases what exists */
+        gc->type[i] = (uint8_t *)malloc(n);
+        gc->in1[i] = (uint32_t *)malloc(4 * (size_t)n);
+        gc->src[i] = (uint32_t *)malloc(4 * (size_t)n);
+        gc->in2[i] = (uint32_t *)malloc(4 * (size_t)n);
+        gc->u2[i] = (uint32_t *)malloc(4 * (size_t)n);
+        if (!gc->type[i] || !gc->in1[i] || !gc->src[i] || !gc->in2[i] || !gc->u2[i]) {
+            so_gcircuit_free(gc); *err = SO_ERR_OOM; return NULL;
+        }
+        for (uint32_t g = 0; g < n; ++g) {
+            uint8_t t = types[off + g];
+            uint32_t a = in1[off + g], j = src[off + g], b = in2[off + g];
+            if (t > 1 || a >= widths[i + 1] || j <= i || j > d || b >= widths[j]) { so_gcircuit_free(gc); return NULL; }
+            gc->type[i][g] = t; gc->in1[i][g] = a; gc->src[i][g] = j; gc->in2[i][g] = b;
+        }
+        off += n;
+        /* blocks of X_i: layer i + 1 in full, then the used gates of each deeper layer */
+        gc->nb[i] = 1;
+        gc->blayer[i][0] = i + 1; gc->bbase[i][0] = 0; gc->bcount[i][0] = gc->W[i + 1];
+        gc->bys[i][0] = (uint32_t *)malloc(4 * (size_t)gc->W[i + 1]);
+        if (!gc->bys[i][0]) { so_gcircuit_free(gc); *err = SO_ERR_OOM; return NULL; }
+        for (uint32_t y = 0; y < gc->W[i + 1]; ++y) gc->bys[i][0][y] = y;
+        uint32_t base = gc->W[i + 1];
+        for (uint32_t j = i + 2; j <= d; ++j) {
+            int32_t *pos = (int32_t *)malloc(4 * (size_t)gc->W[j]);
+            if (!pos) { so_gcircuit_free(gc); *err = SO_ERR_OOM; return NULL; }
+            for (uint32_t y = 0; y < gc->W[j]; ++y) pos[y] = -1;
+            for (uint32_t g = 0; g < n; ++g)
+                if (gc->src[i][g] == j) pos[gc->in2[i][g]] = 0;
+            uint32_t cnt = 0;
+            for (uint32_t y = 0; y < gc->W[j]; ++y)
+                if (pos[y] == 0) pos[y] = (int32_t)(base + cnt++);
+            if (cnt) {
+                uint32_t bidx = gc->nb[i]++;
+                gc->blayer[i][bidx] = j; gc->bbase[i][bidx] = base; gc->bcount[i][bidx] = cnt;
+                gc->bys[i][bidx] = (uint32_t *)malloc(4 * (size_t)cnt);
+                if (!gc->bys[i][bidx]) { free(pos); so_gcircuit_free(gc); *err = SO_ERR_OOM; return NULL; }
+                for (uint32_t y = 0, k = 0; y < gc->W[j]; ++y)
+                    if (pos[y] >= 0) gc->bys[i][bidx][k++] = y;
+                for (uint32_t g = 0; g < n; ++g)
+                    if (gc->src[i][g] == j) gc->u2[i][g] = (uint32_t)pos[gc->in2[i][g]];
+                base += cnt;
+            }
+            free(pos);
+        }
+        for (uint32_t g = 0; g < n; ++g)
+            if (gc->src[i][g] == i + 1) gc->u2[i][g] = gc->in2[i][g];
+        gc->sx[i] = ceil_log2(base);
+    }
+    gc->d = d;
+    if (gwiring_digest(gc) != SO_OK) { so_gcircuit_free(gc); *err = SO_ERR_OOM; return NULL; }
+    *err = SO_OK;
+    return gc;
+}
+
+size_t so_gproof_len(const so_gcircuit *gc) {
+    size_t n = 8 + 4 * ((size_t)gc->d + 3);
+    for (uint32_t i = 0; i < gc->d; ++i) n += 32 * (3 * (size_t)gc->c + 4 * (size_t)gc->sx[i] + 2 * (size_t)gc->nb[i]);
+    return n;
+}
+
+uint32_t so_gcircuit_log_xwidth(const so_gcircuit *gc, uint32_t i) { return gc->sx[i]; }
+uint32_t so_gcircuit_blocks(const so_gcircuit *gc, uint32_t i) { return gc->nb[i]; }
+
+static int geval_all(const so_gcircuit *gc, const uint8_t *inputs, fr **V) {
+    uint32_t d = gc->d;
+    for (uint32_t i = 0; i <= d; ++i) V[i] = NULL;
+    for (uint32_t i = 0; i <= d; ++i) {
+        V[i] = (fr *)calloc((size_t)gc->C * gc->W[i], sizeof(fr));
+        if (!V[i]) return SO_ERR_OOM;
+    }
+    for (uint32_t b = 0; b < gc->Creal; ++b)
+        for (uint32_t x = 0; x < gc->wreal[d]; ++x)
+            if (fr_from_bytes(&V[d][(size_t)b * gc->W[d] + x], inputs + 32 * ((size_t)b * gc->wreal[d] + x)) != SO_OK)
+                return SO_ERR_CANON;
+    for (int i = (int)d - 1; i >= 0; --i)
+        for (uint32_t b = 0; b < gc->C; ++b)
+            for (uint32_t g = 0; g < gc->wreal[i]; ++g) {
+                uint32_t j = gc->src[i][g];
+                V[i][(size_t)b * gc->W[i] + g] = op_gate(gc->type[i][g], V[i + 1][(size_t)b * gc->W[i + 1] + gc->in1[i][g]],
+                                                         V[j][(size_t)b * gc->W[j] + gc->in2[i][g]]);
+            }
+    return SO_OK;
+}
+
+/* The copy-round polynomial g(t), t = 0..3, of one weight term (copy point
+ * z, gate weights M) added into out: with T the virtual layer's rows folded
+ * by r_1..r_{k-1} (n rows of WX values),
+ *   sum_{j < n/2} eq(z, (r_1..r_{k-1}, t, bits(j))) sum_g M(g) op_g(T_t(j, in1 g), T_t(j, u2 g)). */
+static void gcopy_round(const so_gcircuit *gc, uint32_t i, const fr *T, size_t n, uint32_t WX, const fr *M,
+                        const fr *z, const fr *rb, uint32_t k, fr out[4]) {
+    uint32_t c = gc->c;
+    size_t h = n / 2;
+    fr prefix = fr_u64(1);
+    for (uint32_t m = 1; m < k; ++m) prefix = fr_mul(prefix, eq1(z[m - 1], rb[m - 1]));
+    fr *row = (fr *)malloc(WX * sizeof(fr));
+    for (size_t j = 0; j < h; ++j) {
+        fr suffix = fr_u64(1);
+        for (uint32_t m = k + 1; m <= c; ++m)
+            suffix = fr_mul(suffix, eq1(z[m - 1], fr_u64((uint64_t)bit_msb((uint32_t)j, c - k, m - k))));
+        for (int t = 0; t < 4; ++t) {
+            fr tt = fr_u64((uint64_t)t);
+            for (uint32_t x = 0; x < WX; ++x) {
+                fr lo = T[j * WX + x], hi = T[(j + h) * WX + x];
+                row[x] = fr_add(lo, fr_mul(fr_sub(hi, lo), tt));
+            }
+            fr S = fr_zero();
+            for (uint32_t g = 0; g < gc->wreal[i]; ++g)
+                S = fr_add(S, fr_mul(M[g], op_gate(gc->type[i][g], row[gc->in1[i][g]], row[gc->u2[i][g]])));
+            out[t] = fr_add(out[t], fr_mul(fr_mul(fr_mul(prefix, eq1(z[k - 1], tt)), suffix), S));
+        }
+    }
+    free(row);
+}
+
+/* Round k of the phase over the first (which = 1) or second (which = 2)
+ * input on the virtual layer, with the combined gate weights om (the copy
+ * weights folded in): A is the copy-bound row folded by the phase's
+ * challenges so far, A0 the unfolded row, pre[g] the eq factor of the bits
+ * already bound (and, in phase 2, eq(r_x, in1 g)). */
+static void ggate_round(const so_gcircuit *gc, uint32_t i, int which, const fr *A, const fr *A0, const fr *om,
+                        const fr *pre, fr vx, uint32_t k, fr out[3]) {
+    uint32_t sx = gc->sx[i];
+    size_t m = (size_t)1 << (sx - k + 1), h = m / 2;
+    uint32_t lomask = (uint32_t)(h - 1);
+    for (int t = 0; t < 3; ++t) {
+        fr tt = fr_u64((uint64_t)t), S = fr_zero();
+        for (uint32_t g = 0; g < gc->wreal[i]; ++g) {
+            uint8_t ty = gc->type[i][g];
+            uint32_t v = which == 1 ? gc->in1[i][g] : gc->u2[i][g];
+            uint32_t lo = v & lomask;
+            fr at = fr_add(A[lo], fr_mul(tt, fr_sub(A[lo + h], A[lo])));
+            fr val = which == 2 ? op_gate(gc->type[i][g], vx, at) : op_gate(ty, at, A0[gc->u2[i][g]]);
+            fr coeff = fr_mul(fr_mul(om[g], pre[g]), eq1(tt, fr_u64((uint64_t)bit_msb(v, sx, k))));
+            S = fr_add(S, fr_mul(coeff, val));
+        }
+        out[t] = S;
+    }
+}
+
+static void gput_hdr(writer *w, const so_gcircuit *gc) {
+    static const char magic[8] = {'S', 'I', 'S', 'U', 'G', 'K', 'R', '2'};
+    uint8_t u[4];
+    if (w->cap >= 8) memcpy(w->buf, magic, 8);
+    w->len = 8;
+    put_u32(u, gc->d); if (w->len + 4 <= w->cap) memcpy(w->buf + w->len, u, 4); w->len += 4;
+    put_u32(u, gc->c); if (w->len + 4 <= w->cap) memcpy(w->buf + w->len, u, 4); w->len += 4;
+    for (uint32_t i = 0; i <= gc->d; ++i) {
+        put_u32(u, gc->s[i]);
+        if (w->len + 4 <= w->cap) memcpy(w->buf + w->len, u, 4);
+        w->len += 4;
+    }
+}
+
+/* weight terms of a layer's combined claim */
+typedef struct {
+    uint32_t n;
+    fr *z[2 * SO_MAX_DEPTH + 2];  /* copy points (c values each) */
+    fr *M[2 * SO_MAX_DEPTH + 2];  /* gate weights (W_j values each) */
+} gterms;
+
+static void gterms_free(gterms *t) {
+    for (uint32_t k = 0; k < t->n; ++k) { free(t->z[k]); free(t->M[k]); }
+    t->n = 0;
+}
+
+/* M(g) of the claims of block b of layer i's virtual layer on its layer:
+ * ax eq(r_x, u) + ay eq(r_y, u) at the block's gates, 0 elsewhere */
+static fr *gblock_weights(const so_gcircuit *gc, uint32_t i, uint32_t b, const fr *rx, const fr *ry, fr ax, fr ay) {
+    uint32_t j = gc->blayer[i][b];
+    fr *M = (fr *)calloc(gc->W[j], sizeof(fr));
+    if (!M) return NULL;
+    for (uint32_t k = 0; k < gc->bcount[i][b]; ++k) {
+        uint32_t u = gc->bbase[i][b] + k;
+        M[gc->bys[i][b][k]] = fr_add(fr_mul(ax, eq_point_index(rx, gc->sx[i], u)),
+                                     fr_mul(ay, eq_point_index(ry, gc->sx[i], u)));
+    }
+    return M;
+}
+
+int so_gprove(const so_gcircuit *gc, const uint8_t *inputs, const uint8_t *domain, size_t dlen,
+              uint8_t *proof, size_t cap, size_t *len_out) {
+    uint32_t d = gc->d, c = gc->c;
+    fr *V[SO_MAX_DEPTH + 1];
+    int rc = geval_all(gc, inputs, V);
+    if (rc != SO_OK) { free_layers(V, d + 1); return rc; }
+    uint8_t dig_in[32], dig_out[32];
+    table_digest(V[d], (size_t)gc->C * gc->W[d], dig_in);
+    table_digest(V[0], (size_t)gc->C * gc->W[0], dig_out);
+    transcript tr;
+    tr_init(&tr, domain, dlen, d, c, gc->s, gc->wiring_digest, dig_in, dig_out);
+    writer w = {proof, 0, cap};
+    gput_hdr(&w, gc);
+    gterms terms[SO_MAX_DEPTH + 1];
+    memset(terms, 0, sizeof terms);
+    fr zg[32], rb[32], rx[32], ry[32];
+    terms[0].n = 1;
+    terms[0].z[0] = (fr *)malloc(32 * sizeof(fr));
+    terms[0].M[0] = (fr *)malloc(gc->W[0] * sizeof(fr));
+    for (uint32_t k = 0; k < c; ++k) terms[0].z[0][k] = tr_challenge(&tr);
+    for (uint32_t k = 0; k < gc->s[0]; ++k) zg[k] = tr_challenge(&tr);
+    for (uint32_t g = 0; g < gc->W[0]; ++g) terms[0].M[0][g] = eq_point_index(zg, gc->s[0], g);
+    for (uint32_t i = 0; i < d; ++i) {
+        uint32_t sx = gc->sx[i], WX = 1u << sx;
+        /* the virtual layer's table, folded in place by the copy rounds */
+        fr *X = (fr *)calloc((size_t)gc->C * WX, sizeof(fr));
+        for (uint32_t b = 0; b < gc->nb[i]; ++b) {
+            uint32_t j = gc->blayer[i][b];
+            for (uint32_t q = 0; q < gc->C; ++q)
+                for (uint32_t k = 0; k < gc->bcount[i][b]; ++k)
+                    X[(size_t)q * WX + gc->bbase[i][b] + k] = V[j][(size_t)q * gc->W[j] + gc->bys[i][b][k]];
+        }
+        size_t n = gc->C;
+        for (uint32_t k = 1; k <= c; ++k) {
+            fr g4[4] = {fr_zero(), fr_zero(), fr_zero(), fr_zero()};
+            for (uint32_t t = 0; t < terms[i].n; ++t) gcopy_round(gc, i, X, n, WX, terms[i].M[t], terms[i].z[t], rb, k, g4);
+            send_round(&tr, &w, g4, 4);
+            rb[k - 1] = tr_challenge(&tr);
+            fold_rows(X, n, WX, rb[k - 1]);
+            n /= 2;
+        }
+        /* the combined gate weights: each term's weights times its copy weight eq(z_T, r_b) */
+        fr *om = (fr *)calloc(gc->W[i], sizeof(fr));
+        for (uint32_t t = 0; t < terms[i].n; ++t) {
+            fr e = fr_u64(1);
+            for (uint32_t m = 0; m < c; ++m) e = fr_mul(e, eq1(terms[i].z[t][m], rb[m]));
+            for (uint32_t g = 0; g < gc->W[i]; ++g) om[g] = fr_add(om[g], fr_mul(e, terms[i].M[t][g]));
+        }
+        fr *A0 = (fr *)malloc(WX * sizeof(fr)), *A = (fr *)malloc(WX * sizeof(fr));
+        fr *pre = (fr *)malloc((gc->wreal[i] ? gc->wreal[i] : 1) * sizeof(fr));
+        memcpy(A0, X, WX * sizeof(fr));
+        memcpy(A, A0, WX * sizeof(fr));
+        for (uint32_t g = 0; g < gc->wreal[i]; ++g) pre[g] = fr_u64(1);
+        for (uint32_t k = 1; k <= sx; ++k) {
+            fr g3[3];
+            ggate_round(gc, i, 1, A, A0, om, pre, fr_zero(), k, g3);
+            send_round(&tr, &w, g3, 3);
+            rx[k - 1] = tr_challenge(&tr);
+            fold_rows(A, (size_t)1 << (sx - k + 1), 1, rx[k - 1]);
+            for (uint32_t g = 0; g < gc->wreal[i]; ++g)
+                pre[g] = fr_mul(pre[g], eq1(rx[k - 1], fr_u64((uint64_t)bit_msb(gc->in1[i][g], sx, k))));
+        }
+        fr vx = A[0];
+        memcpy(A, A0, WX * sizeof(fr));
+        for (uint32_t g = 0; g < gc->wreal[i]; ++g) pre[g] = eq_point_index(rx, sx, gc->in1[i][g]);
+        for (uint32_t k = 1; k <= sx; ++k) {
+            fr g3[3];
+            ggate_round(gc, i, 2, A, A0, om, pre, vx, k, g3);
+            send_round(&tr, &w, g3, 3);
+            ry[k - 1] = tr_challenge(&tr);
+            fold_rows(A, (size_t)1 << (sx - k + 1), 1, ry[k - 1]);
+            for (uint32_t g = 0; g < gc->wreal[i]; ++g)
+                pre[g] = fr_mul(pre[g], eq1(ry[k - 1], fr_u64((uint64_t)bit_msb(gc->u2[i][g], sx, k))));
+        }
+        /* the blocks' parts of X~_i(r_b, r_x) and X~_i(r_b, r_y) */
+        fr vb[2 * SO_MAX_BLOCKS];
+        uint32_t nb = gc->nb[i];
+        for (uint32_t b = 0; b < nb; ++b) {
+            vb[b] = fr_zero();
+            vb[nb + b] = fr_zero();
+            for (uint32_t k = 0; k < gc->bcount[i][b]; ++k) {
+                uint32_t u = gc->bbase[i][b] + k;
+                vb[b] = fr_add(vb[b], fr_mul(eq_point_index(rx, sx, u), A0[u]));
+                vb[nb + b] = fr_add(vb[nb + b], fr_mul(eq_point_index(ry, sx, u), A0[u]));
+            }
+        }
+        absorb_and_put(&tr, &w, 'V', vb, (int)(2 * nb));
+        for (uint32_t b = 0; b < nb; ++b) {
+            uint32_t j = gc->blayer[i][b];
+            if (j == d) continue; /* the input layer: checked by the verifier from the clear inputs */
+            fr ax = tr_challenge(&tr), ay = tr_challenge(&tr);
+            gterms *T = &terms[j];
+            T->z[T->n] = (fr *)malloc(32 * sizeof(fr));
+            memcpy(T->z[T->n], rb, 32 * sizeof(fr));
+            T->M[T->n] = gblock_weights(gc, i, b, rx, ry, ax, ay);
+            T->n++;
+        }
+        free(X); free(om); free(A0); free(A); free(pre);
+    }
+    for (uint32_t j = 0; j <= d; ++j) gterms_free(&terms[j]);
+    free_layers(V, d + 1);
+    *len_out = w.len;
+    return w.len <= cap ? SO_OK : SO_ERR_ARG;
+}
+
+static int gload_table(const so_gcircuit *gc, const uint8_t *bytes, uint32_t layer, fr **out) {
+    fr *T = (fr *)calloc((size_t)gc->C * gc->W[layer], sizeof(fr));
+    if (!T) return SO_ERR_OOM;
+    for (uint32_t b = 0; b < gc->Creal; ++b)
+        for (uint32_t x = 0; x < gc->wreal[layer]; ++x)
+            if (fr_from_bytes(&T[(size_t)b * gc->W[layer] + x],
+                              bytes + 32 * ((size_t)b * gc->wreal[layer] + x)) != SO_OK) {
+                free(T);
+                return SO_ERR_CANON;
+            }
+    *out = T;
+    return SO_OK;
+}
+
+int so_gverify(const so_gcircuit *gc, const uint8_t *inputs, const uint8_t *outputs, const uint8_t *proof,
+               size_t len, const uint8_t *domain, size_t dlen) {
+    uint32_t d = gc->d, c = gc->c;
+    if (len != so_gproof_len(gc)) return SO_ERR_REJECT;
+    {
+        uint8_t hdr[8 + 4 * (SO_MAX_DEPTH + 3)];
+        writer w = {hdr, 0, sizeof hdr};
+        gput_hdr(&w, gc);
+        if (memcmp(hdr, proof, w.len) != 0) return SO_ERR_REJECT;
+    }
+    reader rd = {proof, len, 8 + 4 * ((size_t)d + 3), 0};
+    fr *Vin = NULL, *Vout = NULL;
+    int rc = gload_table(gc, inputs, d, &Vin);
+    if (rc != SO_OK) return rc;
+    rc = gload_table(gc, outputs, 0, &Vout);
+    if (rc != SO_OK) { free(Vin); return rc; }
+    uint8_t dig_in[32], dig_out[32];
+    table_digest(Vin, (size_t)gc->C * gc->W[d], dig_in);
+    table_digest(Vout, (size_t)gc->C * gc->W[0], dig_out);
+    transcript tr;
+    tr_init(&tr, domain, dlen, d, c, gc->s, gc->wiring_digest, dig_in, dig_out);
+    gterms terms[SO_MAX_DEPTH + 1];
+    memset(terms, 0, sizeof terms);
+    fr claims[SO_MAX_DEPTH + 1];
+    for (uint32_t j = 0; j <= d; ++j) claims[j] = fr_zero();
+    fr zg[32], rb[32], rx[32], ry[32], pt[64];
+    terms[0].n = 1;
+    terms[0].z[0] = (fr *)malloc(32 * sizeof(fr));
+    terms[0].M[0] = (fr *)malloc(gc->W[0] * sizeof(fr));
+    for (uint32_t k = 0; k < c; ++k) terms[0].z[0][k] = tr_challenge(&tr);
+    for (uint32_t k = 0; k < gc->s[0]; ++k) zg[k] = tr_challenge(&tr);
+    for (uint32_t g = 0; g < gc->W[0]; ++g) terms[0].M[0][g] = eq_point_index(zg, gc->s[0], g);
+    /* output claim V~_0(z_b, z_g) from the clear outputs */
+    for (uint32_t k = 0; k < c; ++k) pt[k] = terms[0].z[0][k];
+    for (uint32_t k = 0; k < gc->s[0]; ++k) pt[c + k] = zg[k];
+    claims[0] = mle_by_folding(Vout, c + gc->s[0], pt);
+    int ok = 1;
+    for (uint32_t i = 0; i < d && ok; ++i) {
+        uint32_t sx = gc->sx[i], nb = gc->nb[i];
+        fr claim = claims[i];
+        for (uint32_t k = 0; k < c && ok; ++k) {
+            fr g[4], sent[3];
+            for (int t = 0; t < 3; ++t) sent[t] = get_fr(&rd);
+            if (rd.bad) { ok = 0; break; }
+            g[0] = sent[0]; g[1] = fr_sub(claim, sent[0]); g[2] = sent[1]; g[3] = sent[2];
+            tr_absorb(&tr, 'R', sent, 3);
+            rb[k] = tr_challenge(&tr);
+            claim = interpolate(g, 4, rb[k]);
+        }
+        for (int phase = 0; phase < 2 && ok; ++phase)
+            for (uint32_t k = 0; k < sx && ok; ++k) {
+                fr g[3], sent[2];
+                for (int t = 0; t < 2; ++t) sent[t] = get_fr(&rd);
+                if (rd.bad) { ok = 0; break; }
+                g[0] = sent[0]; g[1] = fr_sub(claim, sent[0]); g[2] = sent[1];
+                tr_absorb(&tr, 'R', sent, 2);
+                fr r = tr_challenge(&tr);
+                if (phase == 0) rx[k] = r; else ry[k] = r;
+                claim = interpolate(g, 3, r);
+            }
+        if (!ok) break;
+        fr vb[2 * SO_MAX_BLOCKS], vx = fr_zero(), vy = fr_zero();
+        for (uint32_t b = 0; b < 2 * nb; ++b) vb[b] = get_fr(&rd);
+        if (rd.bad) { ok = 0; break; }
+        for (uint32_t b = 0; b < nb; ++b) { vx = fr_add(vx, vb[b]); vy = fr_add(vy, vb[nb + b]); }
+        /* final identity: claim = sum_T eq(z_T, r_b) sum_g M_T(g) eq(r_x, in1 g) eq(r_y, u2 g) op_g(v_x, v_y) */
+        fr sum = fr_zero();
+        for (uint32_t t = 0; t < terms[i].n; ++t) {
+            fr e = fr_u64(1), part = fr_zero();
+            for (uint32_t m = 0; m < c; ++m) e = fr_mul(e, eq1(terms[i].z[t][m], rb[m]));
+            for (uint32_t g = 0; g < gc->wreal[i]; ++g) {
+                fr pred = fr_mul(eq_point_index(rx, sx, gc->in1[i][g]), eq_point_index(ry, sx, gc->u2[i][g]));
+                part = fr_add(part, fr_mul(fr_mul(terms[i].M[t][g], pred), op_gate(gc->type[i][g], vx, vy)));
+            }
+            sum = fr_add(sum, fr_mul(e, part));
+        }
+        if (!fr_eq(claim, sum)) { ok = 0; break; }
+        tr_absorb(&tr, 'V', vb, (int)(2 * nb));
+        for (uint32_t b = 0; b < nb && ok; ++b) {
+            uint32_t j = gc->blayer[i][b];
+            if (j == d) {
+                /* input check: v(r) = sum_{u in block} eq(r, u) V~_d(r_b, y_u), from the clear inputs */
+                for (int which = 0; which < 2 && ok; ++which) {
+                    const fr *r = which == 0 ? rx : ry;
+                    fr want = fr_zero();
+                    for (uint32_t k = 0; k < gc->bcount[i][b]; ++k) {
+                        fr col = fr_zero();
+                        for (uint32_t q = 0; q < gc->C; ++q)
+                            col = fr_add(col, fr_mul(eq_point_index(rb, c, q),
+                                                     Vin[(size_t)q * gc->W[d] + gc->bys[i][b][k]]));
+                        want = fr_add(want, fr_mul(eq_point_index(r, sx, gc->bbase[i][b] + k), col));
+                    }
+                    if (!fr_eq(want, vb[which * nb + b])) ok = 0;
+                }
+                continue;
+            }
+            fr ax = tr_challenge(&tr), ay = tr_challenge(&tr);
+            gterms *T = &terms[j];
+            T->z[T->n] = (fr *)malloc(32 * sizeof(fr));
+            memcpy(T->z[T->n], rb, 32 * sizeof(fr));
+            T->M[T->n] = gblock_weights(gc, i, b, rx, ry, ax, ay);
+            T->n++;
+            claims[j] = fr_add(claims[j], fr_add(fr_mul(ax, vb[b]), fr_mul(ay, vb[nb + b])));
+        }
+    }
+    if (rd.pos != rd.len) ok = 0;
+    for (uint32_t j = 0; j <= d; ++j) gterms_free(&terms[j]);
+    free(Vin);
+    free(Vout);
+    return ok ? SO_OK : SO_ERR_REJECT;
+}
+
+int so_goutputs(const so_gcircuit *gc, const uint8_t *inputs, uint8_t *out) {
+    fr *V[SO_MAX_DEPTH + 1];
+    int rc = geval_all(gc, inputs, V);
+    if (rc == SO_OK)
+        for (uint32_t b = 0; b < gc->Creal; ++b)
+            for (uint32_t g = 0; g < gc->wreal[0]; ++g)
+                fr_to_bytes(out + 32 * ((size_t)b * gc->wreal[0] + g), V[0][(size_t)b * gc->W[0] + g]);
+    free_layers(V, gc->d + 1);
+    return rc;
+}

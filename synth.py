@@ -121,6 +121,11 @@ class Circuit:
     ``types[i]``, ``in1[i]``, ``in2[i]`` and ``outs[i]`` have one element
     per entry, and gate g's value is the sum over the entries with
     ``outs[i] == g`` (a gate with no entry is 0).
+
+    General circuits (Sec. 2.7): when ``src`` is given and ``src[i]`` is
+    not None, the second input of gate g of layer i is gate ``in2[i][g]``
+    of layer ``src[i][g]`` (any layer below i: i + 1 .. d); the first input
+    always comes from layer i + 1.
     """
     widths: list
     types: list
@@ -131,6 +136,18 @@ class Circuit:
     seed: int = 0
     meta: dict = field(default_factory=dict)
     outs: list | None = None
+    src: list | None = None
+
+    def layer_src(self, i: int):
+        """Layer of every entry's second input (i + 1 unless general)."""
+        if self.src is not None and self.src[i] is not None:
+            return np.asarray(self.src[i], dtype=np.uint32)
+        return np.full(len(self.in1[i]), i + 1, dtype=np.uint32)
+
+    @property
+    def general(self) -> bool:
+        return self.src is not None and any(
+            s is not None and (np.asarray(s) != i + 1).any() for i, s in enumerate(self.src))
 
     def layer_outs(self, i: int):
         """Output gate of every entry of layer i (one entry per gate when plain)."""
@@ -218,6 +235,29 @@ def mixing_circuit(seed: int, n_copies: int, width: int, depth: int, name: str =
         T.append(t); A.append(a); B.append(b)
     return Circuit([width] * (depth + 1), T, A, B, int(n_copies), name=name, seed=seed,
                    meta={"wiring": "mixing", "pct_mul": 70})
+
+
+def general_circuit(seed: int, n_copies: int, widths, pct_mul: int, pct_far: int, name: str = "") -> Circuit:
+    """A general circuit (Sec. 2.7): uniform wiring and gate types as in
+    uniform_circuit, and with probability pct_far % a gate's second input
+    comes from a deeper layer than i + 1, drawn uniformly among layers
+    i + 2 .. d (the gate in it uniform); the first input stays in i + 1."""
+    widths = [int(w) for w in widths]
+    d = len(widths) - 1
+    T, A, B, R = [], [], [], []
+    for i in range(d):
+        t, a, b = uniform_layer(seed, i, widths[i], widths[i + 1], pct_mul)
+        src = np.full(widths[i], i + 1, dtype=np.uint32)
+        if i + 2 <= d:
+            u = splitmix_words(stream_seed(seed, b"far", i), 0, 3 * widths[i]).reshape(widths[i], 3) >> np.uint64(32)
+            far = ((u[:, 0] * np.uint64(100)) >> np.uint64(32)) < np.uint64(pct_far)
+            layer = (i + 2 + ((u[:, 1] * np.uint64(d - i - 1)) >> np.uint64(32))).astype(np.uint32)
+            src = np.where(far, layer, src).astype(np.uint32)
+            wsrc = np.asarray(widths, dtype=np.uint64)[src]
+            b = np.where(far, ((u[:, 2] * wsrc) >> np.uint64(32)).astype(np.uint32), b).astype(np.uint32)
+        T.append(t); A.append(a); B.append(b); R.append(src)
+    return Circuit(widths, T, A, B, int(n_copies), name=name, seed=seed,
+                   meta={"wiring": "general", "pct_mul": pct_mul, "pct_far": pct_far}, src=R)
 
 
 def inputs_for(circ: Circuit, seed: int | None = None) -> np.ndarray:

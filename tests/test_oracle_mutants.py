@@ -62,6 +62,17 @@ MUTANTS = {
     "distinct_allows_equal": ("if (mw_cmp(cur.w, prev.w, 4) <= 0) return 0;", "if (mw_cmp(cur.w, prev.w, 4) < 0) return 0;"),
     "interp_wrong_node": ("num = fr_mul(num, fr_sub(x, fr_u64((uint64_t)j)));",
                           "num = fr_mul(num, fr_sub(x, fr_u64((uint64_t)j + 1)));"),
+    # general circuits (Sec. 2.7)
+    "general_block_base": ("        uint32_t u = gc->bbase[i][b] + k;\n        M[gc->bys[i][b][k]]",
+                           "        uint32_t u = k;\n        M[gc->bys[i][b][k]]"),
+    "general_first_term_only": ("for (uint32_t t = 0; t < terms[i].n; ++t) gcopy_round(",
+                                "for (uint32_t t = 0; t < 1 && t < terms[i].n; ++t) gcopy_round("),
+    "general_copy_weight_dropped": ("om[g] = fr_add(om[g], fr_mul(e, terms[i].M[t][g]));",
+                                    "om[g] = fr_add(om[g], terms[i].M[t][g]);"),
+    "general_used_index": ("if (gc->src[i][g] == j) gc->u2[i][g] = (uint32_t)pos[gc->in2[i][g]];",
+                           "if (gc->src[i][g] == j) gc->u2[i][g] = base - cnt;"),
+    "general_phase2_first_input": ("pre[g] = eq_point_index(rx, sx, gc->in1[i][g]);",
+                                   "pre[g] = eq_point_index(rx, sx, gc->u2[i][g]);"),
 }
 
 
@@ -136,6 +147,33 @@ def _pins(o: Oracle) -> list:
             failed.append("brute-acc")
     except ValueError:
         failed.append("prove-acc-error")
+    # general circuits (Sec. 2.7): against the brute-force prover, accepted,
+    # every tampered element rejected
+    for seed, C, widths, far in ((5, 4, [8, 8, 6, 8], 40), (7, 2, [8, 4, 8, 4], 70)):
+        gcirc = synth.general_circuit(seed, C, widths, 50, far)
+        xg = synth.inputs_for(gcirc)
+        xgb = synth.fr_bytes(xg)
+        try:
+            gp = o.prove_general(gcirc, xgb)
+            gouts = o.outputs_general(gcirc, xgb)
+        except ValueError:
+            failed.append("prove-general-error")
+            continue
+        honest = brute.prove_general(gcirc, synth.fr_ints(xg))
+        if gp != honest:
+            failed.append(f"brute-general{seed}")
+        pg = brute.GeneralPadded(gcirc)
+        vg = brute.evaluate_general(pg, synth.fr_ints(xg))[0]
+        real = b"".join(brute.fe(vg[bb * pg.W[0] + g]) for bb in range(C) for g in range(widths[0]))
+        if o.verify_general(gcirc, xgb, real, honest) != 0:
+            failed.append(f"accept-general{seed}")
+        hdr = 8 + 4 * (gcirc.depth + 3)
+        for k in range(0, (len(honest) - hdr) // 32, 3):
+            bad = bytearray(honest)
+            bad[hdr + 32 * k] ^= 1
+            if o.verify_general(gcirc, xgb, real, bytes(bad)) == 0:
+                failed.append(f"reject-general{seed}")
+                break
     # associative hash (Sec. 3.4.1): closed forms at e + 2^32 - 1 = 1 and 2;
     # pairwise-distinct check (Sec. 3.4.2) on a list with a repeat
     try:
