@@ -389,8 +389,11 @@ def run_ours(args):
     achieved = prof_work * IMAD_PER_FR_MUL / (prof_ms / 1e3) / 1e12 if prof_ms else None
     peak = imad["tops"]
     per_launch_items = items / max(1, len(rounds)) if rounds else None
+    # the per-item traffic was captured on slot-shaped rounds: the other
+    # workloads' rounds have other shapes, so they report none
     traffic = (DOMINANT_TRAFFIC_BYTES_PER_ITEM * per_launch_items
-               if DOMINANT_TRAFFIC_BYTES_PER_ITEM and per_launch_items else None)
+               if DOMINANT_TRAFFIC_BYTES_PER_ITEM and per_launch_items and args.workload == "slot" and not args.depth
+               else None)
     roofline = {"bound": "alu", "kernel": "k_copy_round (copy-phase round)", "achieved": achieved,
                 "peak": peak, "unit": "TIMAD/s", "frac": achieved / peak if achieved else None,
                 "traffic": traffic,

@@ -104,6 +104,38 @@ int sisu_circuit_create_acc(const sisu_acc_layer* layers, uint32_t n_gate_layers
                             uint32_t n_copies, sisu_circuit** out);
 int sisu_circuit_create_acc_host(const sisu_acc_layer* layers, uint32_t n_gate_layers, uint32_t input_width,
                                  uint32_t n_copies, sisu_circuit** out);
+
+/* General circuits (Sec. 2.7): a gate of layer i takes its first input
+ * from layer i + 1 and its second from any deeper layer src (i + 1 .. d),
+ * so values skip layers instead of being forwarded gate by gate.  One
+ * entry per gate: type (0 add, 1 mul), in1 (a gate of layer i + 1), src,
+ * in2 (a gate of layer src).  Layer i is proven over a virtual layer X_i:
+ * layer i + 1 in full, then for each deeper layer it reads only the gates
+ * it uses, ascending (the paper's used-gates indexing), padded to a power
+ * of two of at most 2^16 positions.  Its round messages run over X_i's
+ * bits, and it ends with, for r = r_x and r = r_y, each block's part
+ * v(r) = sum_{u in block} eq(r, u) X~_i(r_b, u) (layer i + 1's block
+ * first): claims on the blocks' layers.  A layer's claims from all its
+ * readers are combined with random coefficients, each keeping its own copy
+ * point, and summed round by round in its copy phase.  A circuit whose
+ * second inputs all come from layer i + 1 gives the layered proof, byte
+ * for byte.  Proof: per layer c x 3, sx_i x 2, sx_i x 2 elements, then 2 x
+ * (blocks of layer i) block values.  Not supported by the server or by
+ * copy-sharded proving.
+ * Errors: INVALID_ARG, INDEX_OOB (an input beyond its layer, or a src not
+ * below the gate's layer), TOO_LARGE (a virtual layer above 2^16), OOM,
+ * CUDA. */
+typedef struct {
+  uint32_t width;
+  const uint8_t* type;
+  const uint32_t* in1;
+  const uint32_t* src;
+  const uint32_t* in2;
+} sisu_general_layer;
+int sisu_circuit_create_general(const sisu_general_layer* layers, uint32_t n_gate_layers, uint32_t input_width,
+                                uint32_t n_copies, sisu_circuit** out);
+int sisu_circuit_create_general_host(const sisu_general_layer* layers, uint32_t n_gate_layers,
+                                     uint32_t input_width, uint32_t n_copies, sisu_circuit** out);
 void sisu_circuit_destroy(sisu_circuit* circ);
 
 /* Padded shape: log2 of the copy count, log2 widths of layers 0..d (array

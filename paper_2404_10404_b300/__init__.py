@@ -26,6 +26,7 @@ ERRORS = {
 FR_ADD, FR_SUB, FR_MUL, FR_INV, FR_EQ1 = 0, 1, 2, 3, 4
 ENTRY_POINTS = [
     "sisu_circuit_create", "sisu_circuit_create_host", "sisu_circuit_create_acc", "sisu_circuit_create_acc_host",
+    "sisu_circuit_create_general", "sisu_circuit_create_general_host",
     "sisu_circuit_destroy", "sisu_circuit_info", "sisu_circuit_eval",
     "sisu_eval_update", "sisu_eval_outputs", "sisu_eval_layer", "sisu_eval_destroy",
     "sisu_transcript_create", "sisu_transcript_destroy", "sisu_gkr_prove", "sisu_gkr_prove_into",
@@ -58,6 +59,12 @@ class _Layer(ctypes.Structure):
                 ("in1", ctypes.POINTER(ctypes.c_uint32)), ("in2", ctypes.POINTER(ctypes.c_uint32))]
 
 
+class _GeneralLayer(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_uint32), ("type", ctypes.POINTER(ctypes.c_uint8)),
+                ("in1", ctypes.POINTER(ctypes.c_uint32)), ("src", ctypes.POINTER(ctypes.c_uint32)),
+                ("in2", ctypes.POINTER(ctypes.c_uint32))]
+
+
 class _AccLayer(ctypes.Structure):
     _fields_ = [("width", ctypes.c_uint32), ("n_entries", ctypes.c_uint32),
                 ("out", ctypes.POINTER(ctypes.c_uint32)), ("type", ctypes.POINTER(ctypes.c_uint8)),
@@ -83,6 +90,8 @@ def _load():
         "sisu_circuit_create_host": ([ctypes.POINTER(_Layer), u32, u32, u32, pp], ctypes.c_int),
         "sisu_circuit_create_acc": ([ctypes.POINTER(_AccLayer), u32, u32, u32, pp], ctypes.c_int),
         "sisu_circuit_create_acc_host": ([ctypes.POINTER(_AccLayer), u32, u32, u32, pp], ctypes.c_int),
+        "sisu_circuit_create_general": ([ctypes.POINTER(_GeneralLayer), u32, u32, u32, pp], ctypes.c_int),
+        "sisu_circuit_create_general_host": ([ctypes.POINTER(_GeneralLayer), u32, u32, u32, pp], ctypes.c_int),
         "sisu_circuit_destroy": ([vp], None),
         "sisu_circuit_info": ([vp, ctypes.POINTER(u32), ctypes.POINTER(u32), ctypes.POINTER(u32),
                                ctypes.POINTER(sz), ctypes.POINTER(sz)], ctypes.c_int),
@@ -219,10 +228,27 @@ class Circuit:
     arrays of a layer list its entries and ``outs[i]`` the gate of each.
     """
 
-    def __init__(self, widths, types, in1, in2, n_copies: int, host_only: bool = False, outs=None):
+    def __init__(self, widths, types, in1, in2, n_copies: int, host_only: bool = False, outs=None, src=None):
         d = len(widths) - 1
         self._keep = []
         u32p, u8p = ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint8)
+        if src is not None:  # general circuit (Sec. 2.7): second inputs from layer src
+            layers = (_GeneralLayer * d)()
+            for i in range(d):
+                t = np.ascontiguousarray(types[i], dtype=np.uint8)
+                a = np.ascontiguousarray(in1[i], dtype=np.uint32)
+                r = np.ascontiguousarray(src[i] if src[i] is not None else np.full(len(a), i + 1), dtype=np.uint32)
+                b = np.ascontiguousarray(in2[i], dtype=np.uint32)
+                if not (len(t) == len(a) == len(r) == len(b) == int(widths[i])):
+                    raise SisuError(-1, f"layer {i}: wiring arrays must have {widths[i]} entries")
+                self._keep += [t, a, r, b]
+                layers[i] = _GeneralLayer(int(widths[i]), t.ctypes.data_as(u8p), a.ctypes.data_as(u32p),
+                                          r.ctypes.data_as(u32p), b.ctypes.data_as(u32p))
+            h = ctypes.c_void_p()
+            create = _lib.sisu_circuit_create_general_host if host_only else _lib.sisu_circuit_create_general
+            _check(create(layers, d, int(widths[d]), int(n_copies), ctypes.byref(h)))
+            self._finish(h, widths, n_copies)
+            return
         layers = (_Layer * d)() if outs is None else (_AccLayer * d)()
         for i in range(d):
             t = np.ascontiguousarray(types[i], dtype=np.uint8)
@@ -248,6 +274,10 @@ class Circuit:
         else:
             create = _lib.sisu_circuit_create_acc_host if host_only else _lib.sisu_circuit_create_acc
         _check(create(layers, d, int(widths[d]), int(n_copies), ctypes.byref(h)))
+        self._finish(h, widths, n_copies)
+
+    def _finish(self, h, widths, n_copies):
+        d = len(widths) - 1
         self._keep = None
         self.h = h
         self.widths = [int(w) for w in widths]
@@ -272,7 +302,7 @@ class Circuit:
         if outs is not None and all(o is None for o in outs):
             outs = None
         return cls(spec.widths, spec.types, spec.in1, spec.in2, spec.n_copies if n_copies is None else n_copies,
-                   host_only=host_only, outs=outs)
+                   host_only=host_only, outs=outs, src=getattr(spec, "src", None))
 
     def __del__(self):
         if getattr(self, "h", None):

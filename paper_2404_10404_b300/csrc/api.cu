@@ -59,7 +59,9 @@ static uint32_t ceil_log2(uint64_t v) {
 namespace sisu {
 size_t HostCircuit::proof_len() const {
   size_t n = 8 + 4 * ((size_t)d + 3);
-  for (uint32_t i = 0; i < d; ++i) n += 32 * (3 * (size_t)c + 4 * (size_t)s[i + 1] + 2);
+  for (uint32_t i = 0; i < d; ++i)
+    n += general ? 32 * (3 * (size_t)c + 4 * (size_t)sx[i] + 2 * blocks[i].size())
+                 : 32 * (3 * (size_t)c + 4 * (size_t)s[i + 1] + 2);
   return n;
 }
 }  // namespace sisu
@@ -178,7 +180,7 @@ static const char kDefaultDomain[] = "SISU-GKR-v1";
 // (a plain circuit, one entry a gate, keeps the one-record-a-gate bytes)
 static void wiring_digest(const HostCircuit& hc, uint32_t out[8]) {
   size_t n = 0;
-  for (uint32_t i = 0; i < hc.d; ++i) n += ((size_t)hc.W[i] + hc.out[i].size()) * 9;
+  for (uint32_t i = 0; i < hc.d; ++i) n += ((size_t)hc.W[i] + hc.out[i].size()) * 13;
   std::vector<uint8_t> buf(n);
   uint8_t* p = buf.data();
   auto put = [&](uint32_t v) {
@@ -194,7 +196,11 @@ static void wiring_digest(const HostCircuit& hc, uint32_t out[8]) {
       if (e1 - e == 0) {
         *p++ = 2; put(0); put(0);
       } else if (e1 - e == 1) {
-        *p++ = hc.type[i][e]; put(hc.in1[i][e]); put(hc.in2[i][e]);
+        // a general circuit's gate reading a deeper layer (Sec. 2.7):
+        // u8 4 + type || u32le in1 || u32le in2 || u32le layer
+        const bool far = hc.general && hc.src[i][e] != i + 1;
+        *p++ = (uint8_t)(far ? 4 + hc.type[i][e] : hc.type[i][e]); put(hc.in1[i][e]); put(hc.in2[i][e]);
+        if (far) put(hc.src[i][e]);
       } else {
         *p++ = 3; put((uint32_t)(e1 - e));
         for (size_t q = e; q < e1; ++q) {
@@ -274,7 +280,9 @@ static int circuit_finish(std::unique_ptr<sisu_circuit>& cc, bool on_device, sis
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
   for (uint32_t i = 0; i < d; ++i) {
     Lay& l = H[i];
-    const uint32_t W = hc.W[i], Wn = hc.W[i + 1];
+    // a general layer's wiring reads its virtual layer: second inputs at their X positions
+    const uint32_t W = hc.W[i], Wn = hc.general ? (1u << hc.sx[i]) : hc.W[i + 1];
+    const std::vector<uint32_t>& IN2 = hc.general ? hc.u2[i] : hc.in2[i];
     const uint32_t ne = (uint32_t)hc.out[i].size();
     std::vector<uint32_t> muls, adds, count(W, 0);
     for (uint32_t e = 0; e < ne; ++e) {
@@ -298,7 +306,7 @@ static int circuit_finish(std::unique_ptr<sisu_circuit>& cc, bool on_device, sis
     l.sg.resize((size_t)ne + empty);
     for (uint32_t q = 0; q < ne; ++q) {
       const uint32_t e = q < l.nmul ? muls[q] : adds[q - l.nmul];
-      l.sg[q] = make_uint4(hc.in1[i][e], hc.in2[i][e], hc.out[i][e], 0);
+      l.sg[q] = make_uint4(hc.in1[i][e], IN2[e], hc.out[i][e], 0);
     }
     for (uint32_t g = 0, q = ne; g < W; ++g)
       if (count[g] == 0) l.sg[q++] = make_uint4(0, 0, g, 0);
@@ -316,10 +324,30 @@ static int circuit_finish(std::unique_ptr<sisu_circuit>& cc, bool on_device, sis
       l.offo.assign(W + 1, 0);
       for (uint32_t g = 0; g < W; ++g) l.offo[g + 1] = l.offo[g] + count[g];
       l.eo.resize(ne);
-      for (uint32_t e = 0; e < ne; ++e) l.eo[e] = make_uint2(hc.in1[i][e] | ((uint32_t)hc.type[i][e] << 30), hc.in2[i][e]);
+      for (uint32_t e = 0; e < ne; ++e) l.eo[e] = make_uint2(hc.in1[i][e] | ((uint32_t)hc.type[i][e] << 30), IN2[e]);
     }
     bytes += al(l.sg.size() * 16 + 16) + 2 * al(l.off1.size() * 4) + 2 * al(l.pos1.size() * 4 + 4) +
              al(l.offo.size() * 4) + al(l.eo.size() * 8);
+  }
+  // general circuits: per layer the gather map of X_i past layer i + 1, the
+  // blocks' (base, count), and per block the X position of each gate of its
+  // layer (~0 when not used)
+  std::vector<std::vector<uint2>> gmap(d), blk(d);
+  std::vector<std::vector<std::vector<uint32_t>>> pmap(d);
+  if (hc.general) {
+    for (uint32_t i = 0; i < d; ++i) {
+      for (size_t b = 0; b < hc.blocks[i].size(); ++b) {
+        const HostCircuit::Block& B = hc.blocks[i][b];
+        blk[i].push_back(make_uint2(B.base, B.count));
+        std::vector<uint32_t> pm(hc.W[B.layer], 0xffffffffu);
+        for (uint32_t k = 0; k < B.count; ++k) pm[b == 0 ? k : B.ys[k]] = B.base + k;
+        if (b > 0)
+          for (uint32_t k = 0; k < B.count; ++k) gmap[i].push_back(make_uint2(B.layer, B.ys[k]));
+        pmap[i].push_back(std::move(pm));
+      }
+      bytes += al(gmap[i].size() * 8 + 8) + al(blk[i].size() * 8);
+      for (auto& pm : pmap[i]) bytes += al(pm.size() * 4);
+    }
   }
   CK(cudaGetDevice(&cc->device), "cudaGetDevice");
   cudaError_t e = cudaMalloc(&cc->dev, bytes);
@@ -349,6 +377,19 @@ static int circuit_finish(std::unique_ptr<sisu_circuit>& cc, bool on_device, sis
       return fail(SISU_ERR_CUDA, "upload of the wiring failed");
     D.nmul = l.nmul;
     D.ntot = l.ntot;
+  }
+  if (hc.general) {
+    cc->gmap.resize(d);
+    cc->blk.resize(d);
+    cc->pmap.resize(d);
+    for (uint32_t i = 0; i < d; ++i) {
+      cc->gmap[i] = (const uint2*)up(gmap[i].data(), gmap[i].size() * 8, gmap[i].size() * 8 + 8);
+      cc->blk[i] = (const uint2*)up(blk[i].data(), blk[i].size() * 8, blk[i].size() * 8);
+      for (auto& pm : pmap[i]) cc->pmap[i].push_back((const uint32_t*)up(pm.data(), pm.size() * 4, pm.size() * 4));
+      if (!cc->gmap[i] || !cc->blk[i]) return fail(SISU_ERR_CUDA, "upload of the general wiring failed");
+      for (auto* q : cc->pmap[i])
+        if (!q) return fail(SISU_ERR_CUDA, "upload of the general wiring failed");
+    }
   }
   *out = cc.release();
   return SISU_OK;
@@ -407,6 +448,84 @@ static int circuit_create_acc(const sisu_acc_layer* layers, uint32_t n_gate_laye
   return circuit_finish(cc, on_device, out);
 }
 
+// General circuits (Sec. 2.7): one entry per gate, its second input from
+// layer src (i + 1 .. d); the virtual layers X_i and their blocks.
+static int circuit_create_general(const sisu_general_layer* layers, uint32_t n_gate_layers, uint32_t input_width,
+                                  uint32_t n_copies, bool on_device, sisu_circuit** out) {
+  if (!out) return fail(SISU_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!layers || n_gate_layers == 0) return fail(SISU_ERR_INVALID_ARG, "need at least one gate layer");
+  if (n_gate_layers > SISU_MAX_LAYERS) return fail(SISU_ERR_TOO_LARGE, "more than %u layers", SISU_MAX_LAYERS);
+  std::unique_ptr<sisu_circuit> cc(new (std::nothrow) sisu_circuit());
+  if (!cc) return fail(SISU_ERR_OOM, "host allocation");
+  std::vector<uint32_t> widths(n_gate_layers + 1);
+  for (uint32_t i = 0; i < n_gate_layers; ++i) widths[i] = layers[i].width;
+  widths[n_gate_layers] = input_width;
+  HostCircuit& hc = cc->hc;
+  if (int rc = circuit_shape(widths.data(), n_gate_layers, n_copies, hc)) return rc;
+  const uint32_t d = n_gate_layers;
+  hc.general = true;
+  hc.src.assign(d, {});
+  hc.u2.assign(d, {});
+  hc.sx.assign(d, 0);
+  hc.blocks.assign(d, {});
+  for (uint32_t i = 0; i < d; ++i) {
+    const sisu_general_layer& ly = layers[i];
+    if (!ly.type || !ly.in1 || !ly.src || !ly.in2) return fail(SISU_ERR_INVALID_ARG, "layer %u: NULL wiring array", i);
+    for (uint32_t g = 0; g < ly.width; ++g) {
+      const uint32_t j = ly.src[g];
+      if (j <= i || j > d) return fail(SISU_ERR_INDEX_OOB, "layer %u gate %u: second input's layer %u", i, g, j);
+      if (ly.type[g] > 1) return fail(SISU_ERR_INVALID_ARG, "layer %u gate %u: type %u", i, g, ly.type[g]);
+      if (ly.in1[g] >= hc.wreal[i + 1] || ly.in2[g] >= hc.wreal[j])
+        return fail(SISU_ERR_INDEX_OOB, "layer %u gate %u: input index beyond its layer's width", i, g);
+      hc.out[i].push_back(g);
+      hc.type[i].push_back(ly.type[g]);
+      hc.in1[i].push_back(ly.in1[g]);
+      hc.in2[i].push_back(ly.in2[g]);
+      hc.src[i].push_back(j);
+    }
+    // X_i: layer i + 1 in full, then the used gates of each deeper layer, ascending
+    HostCircuit::Block b0{i + 1, 0, hc.W[i + 1], {}};
+    hc.blocks[i].push_back(b0);
+    uint32_t base = hc.W[i + 1];
+    std::vector<uint32_t> u2(ly.width);
+    for (uint32_t g = 0; g < ly.width; ++g)
+      if (hc.src[i][g] == i + 1) u2[g] = hc.in2[i][g];
+    for (uint32_t j = i + 2; j <= d; ++j) {
+      std::vector<uint32_t> pos(hc.W[j], 0xffffffffu);
+      for (uint32_t g = 0; g < ly.width; ++g)
+        if (hc.src[i][g] == j) pos[hc.in2[i][g]] = 0;
+      HostCircuit::Block B{j, base, 0, {}};
+      for (uint32_t y = 0; y < hc.W[j]; ++y)
+        if (pos[y] == 0) {
+          pos[y] = base + B.count++;
+          B.ys.push_back(y);
+        }
+      if (!B.count) continue;
+      for (uint32_t g = 0; g < ly.width; ++g)
+        if (hc.src[i][g] == j) u2[g] = pos[hc.in2[i][g]];
+      base += B.count;
+      hc.blocks[i].push_back(std::move(B));
+    }
+    hc.u2[i] = std::move(u2);
+    hc.sx[i] = ceil_log2(base);
+    if (hc.sx[i] > 16)
+      return fail(SISU_ERR_TOO_LARGE, "layer %u: virtual layer wider than 2^16 (general circuits)", i);
+    if (hc.c + hc.sx[i] > 32) return fail(SISU_ERR_TOO_LARGE, "copies x virtual width of layer %u above 2^32", i);
+  }
+  return circuit_finish(cc, on_device, out);
+}
+
+extern "C" int sisu_circuit_create_general(const sisu_general_layer* layers, uint32_t n_gate_layers,
+                                           uint32_t input_width, uint32_t n_copies, sisu_circuit** out) {
+  return circuit_create_general(layers, n_gate_layers, input_width, n_copies, true, out);
+}
+
+extern "C" int sisu_circuit_create_general_host(const sisu_general_layer* layers, uint32_t n_gate_layers,
+                                                uint32_t input_width, uint32_t n_copies, sisu_circuit** out) {
+  return circuit_create_general(layers, n_gate_layers, input_width, n_copies, false, out);
+}
+
 extern "C" int sisu_circuit_create(const sisu_layer* layers, uint32_t n_gate_layers, uint32_t input_width,
                                    uint32_t n_copies, sisu_circuit** out) {
   return circuit_create(layers, n_gate_layers, input_width, n_copies, true, out);
@@ -452,6 +571,17 @@ extern "C" int sisu_circuit_info(const sisu_circuit* circ, uint32_t* depth, uint
 // evaluation
 
 namespace sisu {
+// general circuits: positions of X_i past layer i + 1 (the used gates of
+// deeper layers), and whether X_i needs a table of its own
+static uint32_t gather_count(const HostCircuit& hc, uint32_t i) {
+  uint32_t n = 0;
+  for (size_t b = 1; b < hc.blocks[i].size(); ++b) n += hc.blocks[i][b].count;
+  return n;
+}
+static bool own_x(const HostCircuit& hc, uint32_t i) {
+  return hc.general && (hc.blocks[i].size() > 1 || hc.sx[i] != hc.s[i + 1]);
+}
+
 // device bytes of the inputs' digest scratch (the two-table launch with an
 // empty second table)
 static size_t eval_digest_scratch_bytes(const HostCircuit& hc) {
@@ -470,7 +600,8 @@ int eval_enqueue(sisu_eval* ev, const uint8_t* inputs, int on_device, cudaStream
   // evaluated on `st`: every copy evaluates on its own rows (the circuits
   // are data-parallel), so the evaluation of chunk k overlaps the transfer
   // of chunk k + 1 and only the last chunk's evaluation follows the copy.
-  const uint32_t nchunk = (!on_device && !padded && hc.C >= kEvalChunks && in_bytes >= kEvalChunkMin) ? kEvalChunks : 1;
+  const uint32_t nchunk =
+      (!on_device && !padded && !hc.general && hc.C >= kEvalChunks && in_bytes >= kEvalChunkMin) ? kEvalChunks : 1;
   // new inputs land only after the previous inputs' digest has read them
   if (ev->dig_recorded) CK(cudaStreamWaitEvent(st, ev->dig_ev, 0), "stream wait");
   const uint32_t* src;
@@ -525,7 +656,22 @@ int eval_enqueue(sisu_eval* ev, const uint8_t* inputs, int on_device, cudaStream
     }
     for (int i = (int)d - 1; i >= 0; --i) {
       ProfScope ps(kProfEval, (double)(b1 - b0) * cc->L[i].nmul, st);
-      CK(launch_eval_layer(ev->V[i + 1], ev->V[i], cc->L[i], b0, b1 - b0, hc.s[i], hc.s[i + 1], st), "eval layer");
+      const uint32_t* from = ev->V[i + 1];
+      uint32_t sn = hc.s[i + 1];
+      if (hc.general) {  // a general layer reads its virtual layer, gathered first
+        if (ev->X[i] != ev->V[i + 1]) {
+          GatherLayers gl;
+          for (uint32_t l = 0; l <= d; ++l) {
+            gl.V[l] = ev->V[l];
+            gl.s[l] = hc.s[l];
+          }
+          CK(launch_gather_x(gl, i + 1, cc->gmap[i], gather_count(hc, i), ev->X[i], hc.C, hc.s[i + 1], hc.sx[i], st),
+             "virtual layer");
+        }
+        from = ev->X[i];
+        sn = hc.sx[i];
+      }
+      CK(launch_eval_layer(from, ev->V[i], cc->L[i], b0, b1 - b0, hc.s[i], sn, st), "eval layer");
     }
   }
   CK(cudaMemcpyAsync(ev->host_flag, ev->flag, 4, cudaMemcpyDeviceToHost, st), "flag copy");
@@ -583,15 +729,25 @@ extern "C" int sisu_circuit_eval(const sisu_circuit* circ, const uint8_t* inputs
   if (!ev) return fail(SISU_ERR_OOM, "host allocation");
   ev->circ = circ;
   size_t total = 0;
-  std::vector<size_t> offs(hc.d + 1);
+  std::vector<size_t> offs(hc.d + 1), xoffs(hc.d, 0);
   for (uint32_t i = 0; i <= hc.d; ++i) {
     offs[i] = total;
     total += ((size_t)hc.C << hc.s[i]) * 32;
   }
+  for (uint32_t i = 0; i < hc.d; ++i)
+    if (own_x(hc, i)) {
+      xoffs[i] = total;
+      total += ((size_t)hc.C << hc.sx[i]) * 32;
+    }
   if (cudaMalloc(&ev->dev, total + 256 + eval_digest_scratch_bytes(hc)) != cudaSuccess)
     return fail(SISU_ERR_OOM, "device allocation of %zu bytes for the layer values", total);
   ev->V.resize(hc.d + 1);
   for (uint32_t i = 0; i <= hc.d; ++i) ev->V[i] = (uint32_t*)((uint8_t*)ev->dev + offs[i]);
+  if (hc.general) {
+    ev->X.resize(hc.d);
+    for (uint32_t i = 0; i < hc.d; ++i)
+      ev->X[i] = own_x(hc, i) ? (uint32_t*)((uint8_t*)ev->dev + xoffs[i]) : ev->V[i + 1];
+  }
   ev->flag = (uint32_t*)((uint8_t*)ev->dev + total);
   ev->dig = ev->flag + 16;
   ev->dscratch = (uint32_t*)((uint8_t*)ev->dev + total + 256);
@@ -686,21 +842,42 @@ extern "C" void sisu_transcript_destroy(sisu_transcript* tr) { delete tr; }
 // ---------------------------------------------------------------------------
 // proving
 
-constexpr int kWsRegions = 14;
+constexpr int kWsRegions = 22;
 
 // proof bytes of a circuit's shape with 2^c copies
 static size_t proof_len_c(const HostCircuit& hc, uint32_t c) {
+  if (hc.general) return hc.proof_len();
   size_t n = 8 + 4 * ((size_t)hc.d + 3);
   for (uint32_t i = 0; i < hc.d; ++i) n += 32 * (3 * (size_t)c + 4 * (size_t)hc.s[i + 1] + 2);
   return n;
 }
 
+// general circuits: the readers (layer i, block b) of each layer's claims,
+// in the order the prover meets them (the input layer's are checked by the
+// verifier, so it has none)
+static std::vector<std::vector<std::pair<uint32_t, uint32_t>>> general_readers(const HostCircuit& hc) {
+  std::vector<std::vector<std::pair<uint32_t, uint32_t>>> r(hc.d + 1);
+  if (!hc.general) return r;
+  for (uint32_t i = 0; i < hc.d; ++i)
+    for (uint32_t b = 0; b < hc.blocks[i].size(); ++b)
+      if (hc.blocks[i][b].layer < hc.d) r[hc.blocks[i][b].layer].push_back({i, b});
+  return r;
+}
+
 static void workspace_sizes(const sisu_circuit* cc, size_t sizes[kWsRegions], uint32_t c_proof) {
   const HostCircuit& hc = cc->hc;
-  uint32_t wmax_next = 1, wmax = 1, nmax = 1;
+  uint32_t wmax_next = 1, wmax = 1, nmax = 1, sxmax = 0, nbmax = 0, lmax = 0, nterms = 0;
   for (uint32_t i = 0; i < hc.d; ++i) {
-    wmax_next = std::max(wmax_next, hc.W[i + 1]);
+    wmax_next = std::max(wmax_next, hc.general ? 1u << hc.sx[i] : hc.W[i + 1]);
     nmax = std::max(nmax, cc->L[i].ntot);
+    if (hc.general) {
+      sxmax = std::max(sxmax, hc.sx[i]);
+      nbmax = std::max(nbmax, (uint32_t)hc.blocks[i].size());
+    }
+  }
+  for (const auto& rd : general_readers(hc)) {
+    lmax = std::max(lmax, (uint32_t)rd.size());
+    nterms += (uint32_t)rd.size();
   }
   for (uint32_t i = 0; i <= hc.d; ++i) wmax = std::max(wmax, hc.W[i]);
   const size_t half = hc.C >= 2 ? (size_t)(hc.C / 2) * wmax_next * 32 : 32;
@@ -708,10 +885,16 @@ static void workspace_sizes(const sisu_circuit* cc, size_t sizes[kWsRegions], ui
                       digest_scratch_words((size_t)hc.C * hc.W[0] * 32)) * 4;
   uint32_t smax = 0;
   for (uint32_t i = 0; i < hc.d; ++i) smax = std::max(smax, hc.s[i]);
+  const size_t hstride = hc.c + 2 * (size_t)sxmax + 2 * (size_t)nbmax;
+  const bool g = hc.general;
   const size_t v[kWsRegions] = {half, (size_t)hc.C * 32, (size_t)nmax * 32, (size_t)wmax_next * 32,
                                 (size_t)wmax_next * 32, (size_t)wmax_next * 32, (size_t)wmax_next * 32,
                                 (size_t)wmax * 32, (size_t)kMaxPartials * 4 * 32, dig, sizeof(DevState),
-                                proof_len_c(hc, c_proof), eq_half_words(hc.c, smax) * 4, (size_t)nmax * 2 * 32};
+                                proof_len_c(hc, c_proof), eq_half_words(hc.c, smax) * 4, (size_t)nmax * 2 * 32,
+                                g ? (size_t)lmax * hc.C * 32 : 0, g ? (size_t)lmax * nmax * 32 : 0,
+                                g ? (size_t)lmax * 128 : 0, g ? (size_t)nmax * 32 : 0, g ? (size_t)32 : 0,
+                                g ? (size_t)hc.d * hstride * 32 : 0, g ? (size_t)2 * nbmax * 32 : 0,
+                                g ? (size_t)nterms * sizeof(GeneralTerm) : 0};
   for (int k = 0; k < kWsRegions; ++k) sizes[k] = v[k];
 }
 
@@ -760,6 +943,45 @@ int workspace_layout(const sisu_circuit* cc, Workspace* ws, uint8_t* dev, uint8_
   ws->proof = (uint8_t*)ptrs[11];
   ws->eqh = (uint32_t*)ptrs[12];
   ws->P = (uint32_t*)ptrs[13];
+  if (hc.general) {
+    ws->Et = (uint32_t*)ptrs[14];
+    ws->omt = (uint32_t*)ptrs[15];
+    ws->sums = (uint32_t*)ptrs[16];
+    ws->omc = (uint32_t*)ptrs[17];
+    ws->Ec = (uint32_t*)ptrs[18];
+    ws->hist = (uint32_t*)ptrs[19];
+    ws->vals = (uint32_t*)ptrs[20];
+    ws->gterms = ptrs[21];
+    uint32_t sxmax = 0, nbmax = 0;
+    for (uint32_t i = 0; i < hc.d; ++i) {
+      sxmax = std::max(sxmax, hc.sx[i]);
+      nbmax = std::max(nbmax, (uint32_t)hc.blocks[i].size());
+    }
+    ws->hstride = hc.c + 2 * sxmax + 2 * nbmax;
+    // the terms of every layer's claims: their challenges in the reading
+    // layer's history record, their alphas, the gate positions
+    std::vector<GeneralTerm> terms;
+    ws->term_off.assign(hc.d + 1, 0);
+    const auto readers = general_readers(hc);
+    for (uint32_t j = 0; j <= hc.d; ++j) {
+      ws->term_off[j] = (uint32_t)terms.size();
+      if (j == hc.d) break;
+      for (auto [i, b] : readers[j]) {
+        const Fr* h = (const Fr*)(ws->hist + 8 * (size_t)i * ws->hstride);
+        GeneralTerm t;
+        t.rb = h;
+        t.rx = h + hc.c;
+        t.ry = h + hc.c + hc.sx[i];
+        t.alpha = h + hc.c + 2 * hc.sx[i] + 2 * b;
+        t.pos = cc->pmap[i][b];
+        t.sxr = hc.sx[i];
+        terms.push_back(t);
+      }
+    }
+    if (!terms.empty())
+      CK(cudaMemcpy(ws->gterms, terms.data(), terms.size() * sizeof(GeneralTerm), cudaMemcpyHostToDevice),
+         "term descriptors");
+  }
   ws->proof_len = proof_len_c(hc, c_proof);
   ws->host = host;
   // the proof header is fixed by the circuit
@@ -811,6 +1033,8 @@ static int workspace_alloc(sisu_eval* ev) {
   return SISU_OK;
 }
 
+static int enqueue_general_layer(const sisu_circuit* cc, sisu_eval* ev, uint32_t i, size_t& off, cudaStream_t st);
+
 // Enqueue one whole proof on `st` (no host synchronisation).
 static int enqueue_prove(const sisu_circuit* cc, sisu_eval* ev, const sisu_transcript* tr, cudaStream_t st) {
   const HostCircuit& hc = cc->hc;
@@ -846,6 +1070,10 @@ static int enqueue_prove(const sisu_circuit* cc, sisu_eval* ev, const sisu_trans
 
   size_t off = 8 + 4 * ((size_t)d + 3);
   for (uint32_t i = 0; i < d; ++i) {
+    if (hc.general) {
+      if (int rc = enqueue_general_layer(cc, ev, i, off, st)) return rc;
+      continue;
+    }
     const DevLayer& L = cc->L[i];
     const uint32_t s = hc.s[i + 1], Wn = hc.W[i + 1], sn = hc.s[i + 1];
     {
@@ -873,36 +1101,108 @@ static int enqueue_prove(const sisu_circuit* cc, sisu_eval* ev, const sisu_trans
       A = w.T;
     }
     const size_t offx = off + 32 * 3 * (size_t)c;  // a copy round sends 3 values, an x/y round 2
-    if (int rc = sisu::enqueue_layer_phases(hc, L, w, i, A, w.E, offx, st)) return rc;
+    if (int rc = sisu::enqueue_layer_phases(hc, L, w, i, A, w.E, w.om, hc.s[i + 1], offx, false, st)) return rc;
     off = offx + 32 * 4 * (size_t)s + 64;
   }
   return SISU_OK;
 }
 
+// Gate layer i of a general circuit (Sec. 2.7), over its virtual layer X_i
+// (2^sx positions): layer 0 starts from the claim point (z_b, z_g) as in a
+// layered proof; a deeper layer from the terms of its readers' claims (each
+// with its own copy point), whose round sums are added in every copy round
+// and whose weights, times their copy weights at r_b, are the phases' gate
+// weights.  The layer ends with the blocks' values, their transcript step
+// and the alphas of the blocks' claims.
+static int enqueue_general_layer(const sisu_circuit* cc, sisu_eval* ev, uint32_t i, size_t& off, cudaStream_t st) {
+  const HostCircuit& hc = cc->hc;
+  Workspace& w = *ev->ws;
+  const DevLayer& L = cc->L[i];
+  const uint32_t c = hc.c, sx = hc.sx[i], WX = 1u << sx;
+  const uint32_t nt = i == 0 ? 1 : w.term_off[i + 1] - w.term_off[i];
+  const size_t Cw = 8 * (size_t)hc.C, Nw = 8 * (size_t)L.ntot;
+  uint32_t *E = w.E, *om = w.om;
+  if (i == 0) {
+    CK(launch_layer_init(w.S, 0, c, hc.s[0], L, w.E, w.om, w.eqh, st), "layer init");
+  } else {
+    CK(launch_general_terms((const GeneralTerm*)w.gterms + w.term_off[i], nt, c, L.sgate, L.ntot, w.Et, w.omt, st),
+       "claim terms");
+    E = w.Et;
+    om = w.omt;
+  }
+  const double per_pair = 2.0 * L.ntot + 4.0 * L.nmul;
+  const uint32_t* A = ev->X[i];
+  for (uint32_t k = 0; k < c; ++k) {
+    const uint32_t* tab = k == 0 ? ev->X[i] : w.T;
+    const uint32_t h = hc.C >> (k + 1);
+    const size_t offk = off + 96 * (size_t)k;
+    {
+      ProfScope ps(kProfCopyRound, per_pair * h * nt, st);
+      if (nt == 1) {
+        CK(launch_copy_round(tab, sx, h, E, om, L, w.partials, w.S, w.proof, offk, k, st), "copy round");
+      } else {  // each term's sums, then their sum is the round message
+        for (uint32_t t = 0; t < nt; ++t)
+          CK(launch_copy_round(tab, sx, h, E + t * Cw, om + t * Nw, L, w.partials, w.S, w.proof, offk, k, st,
+                               w.sums + 32 * (size_t)t),
+             "copy round");
+        CK(launch_shard_absorb(w.sums, nt, w.S, w.proof, offk, k, st), "round message");
+      }
+    }
+    {
+      ProfScope ps(kProfCopyFold, (double)h * WX + h * nt, st);
+      CK(launch_copy_fold(tab, w.T, sx, h, E, w.S, k, st), "copy fold");
+      for (uint32_t t = 1; t < nt; ++t) CK(launch_fold_e(E + t * Cw, h, w.S, k, st), "weight fold");
+    }
+    A = w.T;
+  }
+  if (nt > 1) {  // the phases' gate weights: every term's, times its copy weight at r_b
+    CK(launch_combine_terms(E, hc.C, om, L.ntot, nt, w.omc, w.Ec, st), "combined weights");
+    E = w.Ec;
+    om = w.omc;
+  }
+  const size_t offx = off + 96 * (size_t)c, offv = offx + 128 * (size_t)sx;
+  if (int rc = sisu::enqueue_layer_phases(hc, L, w, i, A, E, om, sx, offx, true, st)) return rc;
+  const uint32_t nb = (uint32_t)hc.blocks[i].size();
+  uint64_t mask = 0;
+  for (uint32_t b = 0; b < nb; ++b)
+    if (hc.blocks[i][b].layer < hc.d) mask |= 1ull << b;
+  CK(launch_block_values(A, sx, cc->blk[i], nb, w.S, w.vals, st), "block values");
+  CK(launch_block_absorb(w.vals, nb, mask, w.S, w.proof, offv, c, sx, w.hist + 8 * (size_t)i * w.hstride, st),
+     "block absorb");
+  off = offv + 64 * (size_t)nb;
+  return SISU_OK;
+}
+
 // Libra's two phases (x, then y) and the end of gate layer i, from the
-// copy-bound row A = V~_{i+1}(r_b, .) and the copy weight E[0] = 2^32
-// eq(z_b, r_b); the phases' messages start at proof offset offx.
+// copy-bound row A = V~_{i+1}(r_b, .) (general circuits: of the virtual
+// layer) with gate weights om, the copy weight E[0] = 2^32 eq(z_b, r_b)
+// and s = log2 of the row; the phases' messages start at proof offset offx.
+// no_end: the layer's end (v_x, v_y, their transcript step, alpha, beta) is
+// left to the caller.
 int sisu::enqueue_layer_phases(const HostCircuit& hc, const DevLayer& L, Workspace& w, uint32_t i,
-                               const uint32_t* A, const uint32_t* E, size_t offx, cudaStream_t st) {
-  const uint32_t d = hc.d, s = hc.s[i + 1], Wn = hc.W[i + 1];
+                               const uint32_t* A, const uint32_t* E, const uint32_t* om, uint32_t s, size_t offx,
+                               bool no_end, cudaStream_t st) {
+  const uint32_t d = hc.d, Wn = 1u << s;
   const size_t offy = offx + 32 * 2 * (size_t)s;
   const size_t offv = offy + 32 * 2 * (size_t)s;
   if (Wn <= kTailMaxWidth) {
     // Libra's two phases and the end of the layer in one cluster launch
     TailParams tp;
-    tp.A = A; tp.E = E; tp.om = w.om; tp.sg = L.sgate;
+    tp.A = A; tp.E = E; tp.om = om; tp.sg = L.sgate;
     tp.off1 = L.off1; tp.pos1 = L.pos1; tp.off2 = L.off2; tp.pos2 = L.pos2;
     tp.nmul = L.nmul; tp.ntot = L.ntot; tp.Wn = Wn; tp.s = s; tp.P = w.P;
     tp.At = w.At; tp.H1 = w.H1; tp.H2 = w.H2; tp.Ay = w.Ay;
     tp.S = w.S; tp.proof = w.proof; tp.offx = offx; tp.offy = offy; tp.offv = offv; tp.last = i + 1 == d;
+    tp.no_end = no_end;
     ProfScope ps(kProfGateRound, (double)Wn * (6.0 + s) + 2.0 * L.ntot, st);
     CK(launch_layer_tail(tp, st), "layer tail");
     return SISU_OK;
   }
+  if (no_end) return fail(SISU_ERR_TOO_LARGE, "general layers wider than 2^16");
   // wide layers: one launch per round over the whole GPU
   {
     ProfScope ps(kProfPhaseInit, (double)L.ntot + 2.0 * Wn, st);
-    CK(launch_xinit(A, E, w.om, L, Wn, w.At, w.H1, w.H2, w.Ay, st), "x init");
+    CK(launch_xinit(A, E, om, L, Wn, w.At, w.H1, w.H2, w.Ay, st), "x init");
   }
   for (uint32_t k = 0; k < s; ++k) {
     ProfScope ps(kProfGateRound, (double)(Wn >> k) / 2 * (k ? 9.0 : 3.0), st);
@@ -912,7 +1212,7 @@ int sisu::enqueue_layer_phases(const HostCircuit& hc, const DevLayer& L, Workspa
   {
     ProfScope ps(kProfPhaseInit, (double)Wn * s + L.ntot + 3.0 * Wn, st);
     CK(launch_eq_rx(w.S, s, Wn, w.Q, w.At, st), "eq(r_x)");
-    CK(launch_yinit(E, w.om, w.Q, L, Wn, w.H1, w.H2, w.S, st), "y init");
+    CK(launch_yinit(E, om, w.Q, L, Wn, w.H1, w.H2, w.S, st), "y init");
   }
   for (uint32_t k = 0; k < s; ++k) {
     ProfScope ps(kProfGateRound, (double)(Wn >> k) / 2 * (k ? 9.0 : 3.0), st);

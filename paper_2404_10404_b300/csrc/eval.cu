@@ -125,6 +125,34 @@ int launch_eval_layer(const uint32_t* Vn, uint32_t* V, const DevLayer& L, uint32
   return post_launch();
 }
 
+// General circuits (Sec. 2.7): the virtual layer X_i of gate layer i, row
+// by row: X_i[b][u] = V_{i+1}[b][u] for u < 2^sn, then the used gates of
+// deeper layers (map[u - 2^sn] = {layer, gate}), zero up to 2^sx.
+__global__ void k_gather_x(GatherLayers gl, uint32_t next, const uint2* __restrict__ map, uint32_t nmap,
+                           uint32_t* __restrict__ X, uint32_t C, uint32_t sn, uint32_t sx) {
+  const size_t total = (size_t)C << sx;
+  const uint32_t wn = 1u << sn, mask = (1u << sx) - 1;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t b = idx >> sx;
+    const uint32_t u = (uint32_t)(idx & mask);
+    Fr v = fr_zero();
+    if (u < wn) {
+      v = fr_load(gl.V[next], (b << sn) + u);
+    } else if (u - wn < nmap) {
+      const uint2 m = map[u - wn];
+      v = fr_load(gl.V[m.x], (b << gl.s[m.x]) + m.y);
+    }
+    fr_store(X, idx, v);
+  }
+}
+
+int launch_gather_x(const GatherLayers& gl, uint32_t next, const uint2* map, uint32_t nmap, uint32_t* X, uint32_t C,
+                    uint32_t sn, uint32_t sx, void* stream) {
+  k_gather_x<<<grid_for((size_t)C << sx, 256), 256, 0, (cudaStream_t)stream>>>(gl, next, map, nmap, X, C, sn, sx);
+  return post_launch();
+}
+
 // ---------------------------------------------------------------------------
 // Merkle statement digest over 1024-byte chunks (32 field elements each):
 //   leaf = H(chunk || 0x00), node = H(left || right || 0x01),

@@ -16,9 +16,14 @@ using sisu::kMaxDomain;
 
 struct sisu_circuit {
   HostCircuit hc;
-  std::vector<DevLayer> L;  // device views, gate layers 0..d-1
+  std::vector<DevLayer> L;  // device views, gate layers 0..d-1 (general: over the virtual layers)
   void* dev = nullptr;      // one allocation holding every device array
   int device = 0;
+  // general circuits: per layer the gather map of X_i past layer i + 1
+  // ({layer, gate} per position), the blocks' {base, count}, and per block
+  // the X position of each gate of the block's layer (~0: not used)
+  std::vector<const uint2*> gmap, blk;
+  std::vector<std::vector<const uint32_t*>> pmap;
   ~sisu_circuit() {
     if (dev) cudaFree(dev);
   }
@@ -28,6 +33,14 @@ struct Workspace {
   void* dev = nullptr;  // owned allocation (null when placed in caller memory)
   uint32_t *T = nullptr, *E = nullptr, *om = nullptr, *At = nullptr, *H1 = nullptr, *H2 = nullptr,
            *Ay = nullptr, *Q = nullptr, *partials = nullptr, *dscratch = nullptr, *eqh = nullptr, *P = nullptr;
+  // general circuits: the claim terms' copy and gate weights, their round
+  // sums, the combined weights, every layer's challenges and alphas
+  // (hstride values a layer), the block values, the term descriptors
+  uint32_t *Et = nullptr, *omt = nullptr, *sums = nullptr, *omc = nullptr, *Ec = nullptr, *hist = nullptr,
+           *vals = nullptr;
+  void* gterms = nullptr;
+  uint32_t hstride = 0;
+  std::vector<uint32_t> term_off;  // first descriptor of each layer's terms (d + 1 entries)
   DevState* S = nullptr;
   uint8_t* proof = nullptr;
   uint8_t* host = nullptr;  // pinned: proof bytes followed by the error word
@@ -53,6 +66,7 @@ struct Workspace {
 struct sisu_eval {
   const sisu_circuit* circ = nullptr;
   std::vector<uint32_t*> V;  // layers 0..d, Montgomery, padded
+  std::vector<uint32_t*> X;  // general circuits: the virtual layer of each gate layer (V[i + 1] when it is only that)
   void* dev = nullptr;        // owned allocation (null when placed in caller memory)
   uint32_t* stage = nullptr;  // padded-input staging (only when padding is needed)
   uint32_t* flag = nullptr;   // device error word
@@ -112,10 +126,11 @@ int proof_enqueue(const sisu_circuit* cc, sisu_eval* ev, const sisu_transcript* 
 // after the stream work: check the error word, copy the proof out
 int proof_finish(const sisu_circuit* cc, sisu_eval* ev, uint8_t* proof);
 int report_error(int code, const char* msg);
-// Libra's phases and the end of gate layer i from the copy-bound row A and
-// the copy weight E[0], messages from proof offset offx (enqueued on st)
+// Libra's phases and the end of gate layer i from the copy-bound row A (of
+// 2^s values), gate weights om and the copy weight E[0], messages from
+// proof offset offx (enqueued on st); no_end leaves the layer's end out
 int enqueue_layer_phases(const HostCircuit& hc, const DevLayer& L, Workspace& w, uint32_t i, const uint32_t* A,
-                         const uint32_t* E, size_t offx, cudaStream_t st);
+                         const uint32_t* E, const uint32_t* om, uint32_t s, size_t offx, bool no_end, cudaStream_t st);
 // the workspace's regions (kWsRegions of them) in `dev`, the proof header
 // (copy count 2^c_proof) and a zeroed state, set on st
 int workspace_layout(const sisu_circuit* cc, Workspace* ws, uint8_t* dev, uint8_t* host, uint32_t c_proof,

@@ -76,6 +76,19 @@ struct HostCircuit {
   std::vector<std::vector<uint8_t>> type;
   std::vector<std::vector<uint32_t>> in1, in2;
   uint32_t wiring_digest[8];
+  // General circuits (Sec. 2.7): entry e's second input is gate in2 of
+  // layer src[i][e] (i + 1 .. d).  Layer i's sumcheck runs over a virtual
+  // layer X_i of 2^sx[i] positions: layer i + 1 in full (block 0), then for
+  // each deeper layer it reads the gates it uses, ascending; u2[i][e] is the
+  // X_i position of entry e's second input.
+  bool general = false;
+  struct Block {
+    uint32_t layer, base, count;
+    std::vector<uint32_t> ys;  // the block's gates in its layer (block 0: all of layer i + 1)
+  };
+  std::vector<std::vector<uint32_t>> src, u2;
+  std::vector<uint32_t> sx;
+  std::vector<std::vector<Block>> blocks;
   size_t proof_len() const;
 };
 
@@ -151,6 +164,42 @@ int launch_yinit(const uint32_t* E, const uint32_t* omega_s, const uint32_t* Q, 
 int launch_layer_end(DevState* S, const uint32_t* Ay, uint32_t s, uint8_t* proof, size_t off, int last,
                      void* stream);
 
+// General circuits: X_i[b][u] for every copy b and position u of the
+// virtual layer (u < wn: layer i + 1; then the used gates of deeper
+// layers, map[u - wn] = {layer, gate}; zero padding up to 2^sx)
+struct GatherLayers {
+  const uint32_t* V[65];
+  uint32_t s[65];
+};
+int launch_gather_x(const GatherLayers& gl, uint32_t next, const uint2* map, uint32_t nmap, uint32_t* X,
+                    uint32_t C, uint32_t sn, uint32_t sx, void* stream);
+// the weight terms of a general layer's claims: E_t (2^32 eq(z_t, b), plain)
+// and om_t (M_t of the gate of each sorted entry), t < nt
+struct GeneralTerm {
+  const Fr* rb;        // the reading layer's copy challenges (c)
+  const Fr* rx;        // and its x and y challenges (sxr)
+  const Fr* ry;
+  const Fr* alpha;     // alpha_x, alpha_y of the reading layer's block
+  const uint32_t* pos; // X position in the reading layer of each gate of this layer (~0: not used)
+  uint32_t sxr;
+};
+int launch_general_terms(const GeneralTerm* terms_dev, uint32_t nt, uint32_t c, const uint4* sg, uint32_t ntot,
+                         uint32_t* Et, uint32_t* omt, void* stream);
+int launch_fold_e(uint32_t* E, uint32_t h, const DevState* S, uint32_t k, void* stream);
+// om_c = sum_t e_t om_t (e_t = E_t[0] 2^-32, the copy weight at r_b), E_c[0] = 2^32
+int launch_combine_terms(const uint32_t* Et, uint32_t C, const uint32_t* omt, uint32_t ntot, uint32_t nt,
+                         uint32_t* omc, uint32_t* Ec, void* stream);
+// v_b(r) = sum_{u in block b} eq(r, u) A(u) for r = r_x (vals[b]) and r_y
+// (vals[nb + b]); blocks given as base/count pairs
+int launch_block_values(const uint32_t* A, uint32_t sx, const uint2* blocks, uint32_t nb, const DevState* S,
+                        uint32_t* vals, void* stream);
+// the block values into the proof and the transcript ('V'), then alpha_x,
+// alpha_y of every block whose layer is not the input layer (flags bit b),
+// and the layer's challenges, into the history record hist (rb: c values,
+// rx, ry: sx values each, then 2 nb alphas)
+int launch_block_absorb(const uint32_t* vals, uint32_t nb, uint64_t squeeze_mask, DevState* S, uint8_t* proof,
+                        size_t off, uint32_t c, uint32_t sx, uint32_t* hist, void* stream);
+
 // Libra's two phases of one layer in a single thread-block-cluster launch
 // (tables up to kTailMaxWidth entries): phase-1 init, the x rounds,
 // EQ(r_x), phase-2 init, the y rounds and the end of the layer.
@@ -168,6 +217,7 @@ struct TailParams {
   uint8_t* proof;
   size_t offx, offy, offv;
   int last;
+  int no_end;         // general layers: the block values end the layer instead (v_x, v_y and the state kept)
 };
 int launch_layer_tail(const TailParams& p, void* stream);
 

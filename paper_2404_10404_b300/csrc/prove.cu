@@ -1298,16 +1298,18 @@ __global__ void __cluster_dims__(kTailCTAs, 1, 1) __launch_bounds__(kTailThreads
       Fr v = lane == 0 ? vx : (p.s == 0 ? sh.solo[0][0] : fold2(sh.solo[0][0], sh.solo[0][1], r));
       if (lane == 1) S->vy = v;
       Fr c = fr_to_canonical(v);
-      store_words(p.proof, p.offv + 32 * (size_t)lane, c);
+      if (!p.no_end) store_words(p.proof, p.offv + 32 * (size_t)lane, c);
       sh.canon[lane] = c;
     }
     __syncwarp();
     if (lane == 0) {
-      Fr canon[2] = {sh.canon[0], sh.canon[1]};
-      tr_absorb_n<2, false>(sh.st, 'V', canon);
-      if (!p.last) {
-        S->alpha = tr_challenge_st<false>(sh.st, &S->error, true);
-        S->beta = tr_challenge_st<false>(sh.st, &S->error, false);
+      if (!p.no_end) {
+        Fr canon[2] = {sh.canon[0], sh.canon[1]};
+        tr_absorb_n<2, false>(sh.st, 'V', canon);
+        if (!p.last) {
+          S->alpha = tr_challenge_st<false>(sh.st, &S->error, true);
+          S->beta = tr_challenge_st<false>(sh.st, &S->error, false);
+        }
       }
 #pragma unroll
       for (int i = 0; i < 8; ++i) S->st[i] = sh.st[i];
@@ -1318,6 +1320,164 @@ __global__ void __cluster_dims__(kTailCTAs, 1, 1) __launch_bounds__(kTailThreads
 
 int launch_layer_tail(const TailParams& p, void* stream) {
   return launch_pdl(k_layer_tail, kTailCTAs, kTailThreads, (cudaStream_t)stream, p);
+}
+
+// ---------------------------------------------------------------------------
+// General circuits (Sec. 2.7): layer i's sumcheck runs over a virtual layer
+// X_i (layer i + 1, then the used gates of deeper layers); the claims on a
+// layer from all its readers are weight terms sum_t eq(z_t, b) M_t(g), each
+// with its own copy point z_t, summed round by round in the copy phase.
+
+// the terms' copy weights E_t(b) = 2^32 eq(z_t, b) (plain) over 2^c copies
+// and gate weights om_t(q) = M_t(g_q) = alpha_x eq(r_x, u) + alpha_y eq(r_y,
+// u) at the reading layer's X position u of gate g_q (0 when not used)
+__global__ void k_general_terms(const GeneralTerm* __restrict__ terms, uint32_t nt, uint32_t c,
+                                const uint4* __restrict__ sg, uint32_t ntot, uint32_t* __restrict__ Et,
+                                uint32_t* __restrict__ omt) {
+  const uint32_t C = 1u << c;
+  const size_t per = (size_t)C + ntot, total = per * nt;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t t = (uint32_t)(idx / per);
+    const size_t rest = idx - (size_t)t * per;
+    const GeneralTerm tm = terms[t];
+    if (rest < C) {
+      fr_store(Et, (size_t)t * C + rest, eq_half_entry(tm.rb, 0, c, (uint32_t)rest, fr_int_2_32()));
+    } else {
+      const uint32_t q = (uint32_t)(rest - C), u = tm.pos[sg[q].z];
+      Fr w = fr_zero();
+      if (u != 0xffffffffu)
+        w = fr_add(fr_mul(tm.alpha[0], eq_index(tm.rx, tm.sxr, u)), fr_mul(tm.alpha[1], eq_index(tm.ry, tm.sxr, u)));
+      fr_store(omt, (size_t)t * ntot + q, w);
+    }
+  }
+}
+
+int launch_general_terms(const GeneralTerm* terms_dev, uint32_t nt, uint32_t c, const uint4* sg, uint32_t ntot,
+                         uint32_t* Et, uint32_t* omt, void* stream) {
+  const size_t n = ((size_t)(1u << c) + ntot) * nt;
+  k_general_terms<<<grid_for(n, 128), 128, 0, (cudaStream_t)stream>>>(terms_dev, nt, c, sg, ntot, Et, omt);
+  return post_launch();
+}
+
+// the fold of a copy-weight table alone by the round's challenge r_b[k]
+__global__ void k_fold_e(uint32_t* E, uint32_t h, const DevState* S, uint32_t k) {
+  const Fr r = S->rb[k];
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < h; j += gridDim.x * blockDim.x)
+    fr_store(E, j, fold2(fr_load(E, j), fr_load(E, j + h), r));
+}
+
+int launch_fold_e(uint32_t* E, uint32_t h, const DevState* S, uint32_t k, void* stream) {
+  k_fold_e<<<grid_for(h, 128), 128, 0, (cudaStream_t)stream>>>(E, h, S, k);
+  return post_launch();
+}
+
+// om_c(q) = sum_t e_t om_t(q), with e_t (Montgomery) from E_t[0] = 2^32 e_t
+// (plain): E_t[0] times 2^-32 R^2 is e_t R.  E_c[0] = 2^32, so that the
+// phases' copy weight is 1.
+__global__ void k_combine_terms(const uint32_t* __restrict__ Et, uint32_t C, const uint32_t* __restrict__ omt,
+                                uint32_t ntot, uint32_t nt, uint32_t* __restrict__ omc, uint32_t* __restrict__ Ec) {
+  const Fr scale = fr_mul(fr_mont_2_neg32(), fr_r2());
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < ntot; q += gridDim.x * blockDim.x) {
+    Fr w = fr_zero();
+    for (uint32_t t = 0; t < nt; ++t)
+      w = fr_add(w, fr_mul(fr_mul(fr_load(Et, (size_t)t * C), scale), fr_load(omt, (size_t)t * ntot + q)));
+    fr_store(omc, q, w);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) fr_store(Ec, 0, fr_int_2_32());
+}
+
+int launch_combine_terms(const uint32_t* Et, uint32_t C, const uint32_t* omt, uint32_t ntot, uint32_t nt,
+                         uint32_t* omc, uint32_t* Ec, void* stream) {
+  k_combine_terms<<<grid_for(ntot ? ntot : 1, 128), 128, 0, (cudaStream_t)stream>>>(Et, C, omt, ntot, nt, omc, Ec);
+  return post_launch();
+}
+
+// CTA 2 b + p sums block b of the row A against eq(r, .), r = r_x (p = 0)
+// or r_y (p = 1): eq(r, u) = hi[u >> sl] lo[u mod 2^sl] from half tables in
+// shared memory (sx <= 16)
+constexpr uint32_t kBlockThreads = 256;
+__global__ void __launch_bounds__(kBlockThreads) k_block_values(const uint32_t* __restrict__ A, uint32_t sx,
+                                                                const uint2* __restrict__ blocks, uint32_t nb,
+                                                                const DevState* S, uint32_t* __restrict__ vals) {
+  __shared__ Fr hi[256], lo[256];
+  __shared__ Fr red[kBlockThreads / 32];
+  const uint32_t b = blockIdx.x >> 1, p = blockIdx.x & 1;
+  const Fr* r = p == 0 ? S->rx : S->ry;
+  const uint32_t sl = sx / 2, sh = sx - sl;
+  for (uint32_t e = threadIdx.x; e < (1u << sh) + (1u << sl); e += kBlockThreads) {
+    const bool h = e < (1u << sh);
+    const uint32_t v = h ? e : e - (1u << sh);
+    (h ? hi : lo)[v] = eq_half_entry(r, h ? 0 : sh, h ? sh : sl, v, fr_one());
+  }
+  __syncthreads();
+  const uint2 blk = blocks[b];
+  Fr acc = fr_zero();
+  for (uint32_t u = blk.x + threadIdx.x; u < blk.x + blk.y; u += kBlockThreads)
+    acc = fr_add(acc, fr_mul(fr_mul(hi[u >> sl], lo[u & ((1u << sl) - 1)]), fr_load(A, u)));
+  acc = fr_warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    Fr x = threadIdx.x < kBlockThreads / 32 ? red[threadIdx.x] : fr_zero();
+    x = fr_warp_sum(x);
+    if (threadIdx.x == 0) fr_store(vals, (size_t)p * nb + b, x);
+  }
+}
+
+int launch_block_values(const uint32_t* A, uint32_t sx, const uint2* blocks, uint32_t nb, const DevState* S,
+                        uint32_t* vals, void* stream) {
+  k_block_values<<<2 * nb, kBlockThreads, 0, (cudaStream_t)stream>>>(A, sx, blocks, nb, S, vals);
+  return post_launch();
+}
+
+// absorb of n canonical elements (any n), the transcript's absorb step
+__device__ void tr_absorb_var(uint32_t* st, uint32_t tag, const uint32_t* canon_words, uint32_t n) {
+  ShaWords8 h;
+  for (int i = 0; i < 8; ++i) h.w[i] = st[i];
+  h.w[7] ^= (tag << 8) | n;
+  for (uint32_t b = 0; 16 * b < 8 * n; ++b) {
+    ShaWords16 blk;
+    for (int k = 0; k < 16; ++k) {
+      const uint32_t w = 16 * b + k;
+      blk.w[k] = w < 8 * n ? bswap32(canon_words[w]) : 0u;
+    }
+    h = tr_compress<true>(h, blk);
+  }
+  for (int i = 0; i < 8; ++i) st[i] = h.w[i];
+}
+
+__global__ void k_block_absorb(const uint32_t* __restrict__ vals, uint32_t nb, uint64_t squeeze_mask, DevState* S,
+                               uint8_t* proof, size_t off, uint32_t c, uint32_t sx, uint32_t* __restrict__ hist) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  uint32_t canon[8 * 2 * 64];
+  for (uint32_t k = 0; k < 2 * nb; ++k) {
+    const Fr v = fr_to_canonical(fr_load(vals, k));
+    store_words(proof, off + 32 * (size_t)k, v);
+    for (int i = 0; i < 8; ++i) canon[8 * k + i] = v.v[i];
+  }
+  tr_absorb_var(S->st, 'V', canon, 2 * nb);
+  // the layer's challenges, then the blocks' alphas
+  for (uint32_t k = 0; k < c; ++k) fr_store(hist, k, S->rb[k]);
+  for (uint32_t k = 0; k < sx; ++k) {
+    fr_store(hist, c + k, S->rx[k]);
+    fr_store(hist, c + sx + k, S->ry[k]);
+  }
+  bool fresh = true;
+  for (uint32_t b = 0; b < nb; ++b) {
+    if (!((squeeze_mask >> b) & 1u)) continue;
+    const Fr ax = tr_challenge_st<true>(S->st, &S->error, fresh);
+    const Fr ay = tr_challenge_st<true>(S->st, &S->error, false);
+    fresh = false;
+    fr_store(hist, c + 2 * sx + 2 * b, ax);
+    fr_store(hist, c + 2 * sx + 2 * b + 1, ay);
+  }
+}
+
+int launch_block_absorb(const uint32_t* vals, uint32_t nb, uint64_t squeeze_mask, DevState* S, uint8_t* proof,
+                        size_t off, uint32_t c, uint32_t sx, uint32_t* hist, void* stream) {
+  k_block_absorb<<<1, 32, 0, (cudaStream_t)stream>>>(vals, nb, squeeze_mask, S, proof, off, c, sx, hist);
+  return post_launch();
 }
 
 }  // namespace sisu

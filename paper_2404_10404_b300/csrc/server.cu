@@ -309,6 +309,7 @@ extern "C" int sisu_server_create(size_t budget_bytes, uint32_t max_active, cons
 extern "C" int sisu_job_footprint(const sisu_circuit* circ, int inputs_on_device, size_t* bytes) {
   if (!circ || !bytes) return report_error(SISU_ERR_INVALID_ARG, "NULL argument");
   if (!circ->dev) return report_error(SISU_ERR_INVALID_ARG, "circuit was created for host verification only");
+  if (circ->hc.general) return report_error(SISU_ERR_INVALID_ARG, "the server does not take general circuits");
   *bytes = ((eval_footprint(circ, !inputs_on_device) + 255) & ~(size_t)255) + workspace_footprint(circ);
   return SISU_OK;
 }
@@ -317,6 +318,7 @@ extern "C" int sisu_server_submit(sisu_server* s, const sisu_circuit* circ, cons
                                   int inputs_on_device, uint64_t* ticket) {
   if (!s || !circ || !inputs || !ticket) return report_error(SISU_ERR_INVALID_ARG, "NULL argument");
   if (!circ->dev) return report_error(SISU_ERR_INVALID_ARG, "circuit was created for host verification only");
+  if (circ->hc.general) return report_error(SISU_ERR_INVALID_ARG, "the server does not take general circuits");
   std::unique_ptr<Job> j(new (std::nothrow) Job());
   if (!j) return report_error(SISU_ERR_OOM, "host allocation");
   j->circ = circ;

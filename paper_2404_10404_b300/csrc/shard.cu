@@ -87,6 +87,7 @@ extern "C" int sisu_shard_create(sisu_eval* local, uint32_t rank, uint32_t world
     return report_error(SISU_ERR_INVALID_ARG, "world must be a power of two, at most 2^20");
   if (rank >= world) return report_error(SISU_ERR_INVALID_ARG, "rank beyond world");
   const HostCircuit& hc = local->circ->hc;
+  if (hc.general) return report_error(SISU_ERR_INVALID_ARG, "copy-sharded proving of general circuits is not supported");
   if (hc.Creal != hc.C)
     return report_error(SISU_ERR_INVALID_ARG, "a rank's copy count must be a power of two (no padded copies)");
   if (hc.W[0] < 32 || hc.W[hc.d] < 32)
@@ -255,7 +256,8 @@ extern "C" int sisu_shard_finish(sisu_shard* sh, uint32_t layer, void* stream) {
     rc = launch_copy_fold(sh->T0, sh->T0, sn, h, sh->E0, w.S, k, st);
     if (rc) return cuda_err(rc, "copy fold");
   }
-  return enqueue_layer_phases(hc, L, w, layer, sh->T0, sh->E0, sh->layer_off[layer] + 96 * (size_t)sh->c_full, st);
+  return enqueue_layer_phases(hc, L, w, layer, sh->T0, sh->E0, w.om, hc.s[layer + 1],
+                              sh->layer_off[layer] + 96 * (size_t)sh->c_full, false, st);
 }
 
 extern "C" int sisu_shard_proof(sisu_shard* sh, void* stream, uint8_t* proof, size_t cap, size_t* proof_len) {

@@ -209,13 +209,13 @@ struct Transcript {
   uint32_t st[8];
   bool fresh = true;
   void absorb(uint8_t tag, const HF* e, int n) {
-    uint8_t msg[32 * 4] = {0};
+    std::vector<uint8_t> msg((size_t)64 * ((32 * n + 63) / 64), 0);
     const int nb = (32 * n + 63) / 64;
-    for (int i = 0; i < n; ++i) store(msg + 32 * i, e[i]);
+    for (int i = 0; i < n; ++i) store(msg.data() + 32 * i, e[i]);
     st[7] ^= ((uint32_t)tag << 8) | (uint32_t)n;
     for (int b = 0; b < nb; ++b) {
       uint32_t blk[16];
-      const uint8_t* p = msg + 64 * b;
+      const uint8_t* p = msg.data() + 64 * b;
       for (int k = 0; k < 16; ++k)
         blk[k] = ((uint32_t)p[4 * k] << 24) | ((uint32_t)p[4 * k + 1] << 16) | ((uint32_t)p[4 * k + 2] << 8) | p[4 * k + 3];
       sha256_compress(st, blk);
@@ -330,8 +330,12 @@ void host_statement_digest(const uint8_t* data, size_t len, uint32_t out[8]) {
   s.end(out);
 }
 
+static int host_verify_general(const HostCircuit& hc, const uint8_t* inputs, const uint8_t* outputs,
+                               const uint8_t* proof, size_t proof_len, const uint8_t* domain, size_t dlen);
+
 int host_verify(const HostCircuit& hc, const uint8_t* inputs, const uint8_t* outputs, const uint8_t* proof,
                 size_t proof_len, const uint8_t* domain, size_t dlen) {
+  if (hc.general) return host_verify_general(hc, inputs, outputs, proof, proof_len, domain, dlen);
   const uint32_t d = hc.d, c = hc.c;
   if (proof_len != hc.proof_len()) return SISU_ERR_REJECT;
   // header
@@ -444,6 +448,142 @@ int host_verify(const HostCircuit& hc, const uint8_t* inputs, const uint8_t* out
       p1.insert(p1.end(), rx.begin(), rx.end());
       p2.insert(p2.end(), ry.begin(), ry.end());
       if (!eq(vx, mle(Vin, p1)) || !eq(vy, mle(Vin, p2))) return SISU_ERR_REJECT;
+    }
+  }
+  if (pos != proof_len) return SISU_ERR_REJECT;
+  return SISU_OK;
+}
+
+// General circuits (Sec. 2.7): layer i's rounds run over its virtual layer
+// X_i (2^sx positions); the layer ends with every block's part of
+// X~_i(r_b, r_x) and X~_i(r_b, r_y).  The final identity sums the weight
+// terms of the layer's claims, each with its own copy point; a block on the
+// input layer is checked against the clear inputs, any other becomes a term
+// of its layer's claim with two fresh coefficients.
+static int host_verify_general(const HostCircuit& hc, const uint8_t* inputs, const uint8_t* outputs,
+                               const uint8_t* proof, size_t proof_len, const uint8_t* domain, size_t dlen) {
+  const uint32_t d = hc.d, c = hc.c;
+  if (proof_len != hc.proof_len()) return SISU_ERR_REJECT;
+  {
+    std::vector<uint8_t> hdr(8 + 4 * ((size_t)d + 3));
+    memcpy(hdr.data(), "SISUGKR2", 8);
+    auto put = [&](size_t at, uint32_t v) {
+      for (int k = 0; k < 4; ++k) hdr[at + k] = (uint8_t)(v >> (8 * k));
+    };
+    put(8, d);
+    put(12, c);
+    for (uint32_t i = 0; i <= d; ++i) put(16 + 4 * (size_t)i, hc.s[i]);
+    if (memcmp(hdr.data(), proof, hdr.size()) != 0) return SISU_ERR_REJECT;
+  }
+  size_t pos = 8 + 4 * ((size_t)d + 3);
+  auto next = [&](HF* x) -> bool {
+    if (pos + 32 > proof_len) return false;
+    bool ok = load(proof + pos, x);
+    pos += 32;
+    return ok;
+  };
+  std::vector<uint8_t> in_b = padded_bytes(inputs, hc.C, hc.W[d], hc.Creal, hc.wreal[d]);
+  std::vector<uint8_t> out_b = padded_bytes(outputs, hc.C, hc.W[0], hc.Creal, hc.wreal[0]);
+  std::vector<HF> Vin, Vout;
+  if (!load_table(in_b, &Vin) || !load_table(out_b, &Vout)) return SISU_ERR_NOT_CANONICAL;
+  uint32_t dig_in[8], dig_out[8];
+  host_statement_digest(in_b.data(), in_b.size(), dig_in);
+  host_statement_digest(out_b.data(), out_b.size(), dig_out);
+  Transcript tr;
+  {
+    Sha256Stream h;
+    h.begin();
+    h.bytes(domain, dlen);
+    h.byte(0);
+    h.u32le(d);
+    h.u32le(c);
+    for (uint32_t i = 0; i <= d; ++i) h.u32le(hc.s[i]);
+    h.digest_words(hc.wiring_digest);
+    h.digest_words(dig_in);
+    h.digest_words(dig_out);
+    h.end(tr.st);
+  }
+  struct Term {
+    std::vector<HF> z, M;
+  };
+  std::vector<std::vector<Term>> terms(d + 1);
+  std::vector<HF> claims(d + 1, kZero);
+  std::vector<HF> zb(c), zg(hc.s[0]);
+  for (auto& z : zb) z = tr.challenge();
+  for (auto& z : zg) z = tr.challenge();
+  terms[0].push_back({zb, eq_table(zg)});
+  {
+    std::vector<HF> pt(zb);
+    pt.insert(pt.end(), zg.begin(), zg.end());
+    claims[0] = mle(Vout, pt);
+  }
+  static const Lagrange lag;
+  for (uint32_t i = 0; i < d; ++i) {
+    const uint32_t sx = hc.sx[i], nb = (uint32_t)hc.blocks[i].size();
+    HF claim = claims[i];
+    std::vector<HF> rb(c), rx(sx), ry(sx);
+    for (uint32_t k = 0; k < c; ++k) {
+      HF g[4], sent[3];
+      for (auto& v : sent)
+        if (!next(&v)) return SISU_ERR_REJECT;
+      g[0] = sent[0]; g[1] = sub(claim, sent[0]); g[2] = sent[1]; g[3] = sent[2];
+      tr.absorb('R', sent, 3);
+      rb[k] = tr.challenge();
+      claim = lag.at(g, 4, rb[k]);
+    }
+    for (int phase = 0; phase < 2; ++phase)
+      for (uint32_t k = 0; k < sx; ++k) {
+        HF g[3], sent[2];
+        for (auto& v : sent)
+          if (!next(&v)) return SISU_ERR_REJECT;
+        g[0] = sent[0]; g[1] = sub(claim, sent[0]); g[2] = sent[1];
+        tr.absorb('R', sent, 2);
+        HF r = tr.challenge();
+        (phase == 0 ? rx : ry)[k] = r;
+        claim = lag.at(g, 3, r);
+      }
+    std::vector<HF> vb(2 * (size_t)nb);
+    HF vx = kZero, vy = kZero;
+    for (uint32_t b = 0; b < 2 * nb; ++b)
+      if (!next(&vb[b])) return SISU_ERR_REJECT;
+    for (uint32_t b = 0; b < nb; ++b) {
+      vx = add(vx, vb[b]);
+      vy = add(vy, vb[nb + b]);
+    }
+    // final identity over the layer's weight terms
+    const std::vector<HF> qx = eq_table(rx), qy = eq_table(ry);
+    const HF vsum = add(vx, vy), vprod = mul(vx, vy);
+    HF sum = kZero;
+    for (const Term& T : terms[i]) {
+      HF part = kZero;
+      for (size_t e = 0; e < hc.out[i].size(); ++e) {
+        HF term = mul(T.M[hc.out[i][e]], mul(qx[hc.in1[i][e]], qy[hc.u2[i][e]]));
+        part = add(part, mul(term, hc.type[i][e] == 0 ? vsum : vprod));
+      }
+      sum = add(sum, mul(eq_point(T.z, rb), part));
+    }
+    if (!eq(claim, sum)) return SISU_ERR_REJECT;
+    tr.absorb('V', vb.data(), (int)vb.size());
+    const std::vector<HF> erb = eq_table(rb);
+    for (uint32_t b = 0; b < nb; ++b) {
+      const HostCircuit::Block& B = hc.blocks[i][b];
+      auto gate = [&](uint32_t k) { return b == 0 ? k : B.ys[k]; };
+      if (B.layer == d) {  // against the clear inputs
+        HF wx = kZero, wy = kZero;
+        for (uint32_t k = 0; k < B.count; ++k) {
+          HF col = kZero;
+          for (uint32_t q = 0; q < hc.C; ++q) col = add(col, mul(erb[q], Vin[(size_t)q * hc.W[d] + gate(k)]));
+          wx = add(wx, mul(qx[B.base + k], col));
+          wy = add(wy, mul(qy[B.base + k], col));
+        }
+        if (!eq(wx, vb[b]) || !eq(wy, vb[nb + b])) return SISU_ERR_REJECT;
+        continue;
+      }
+      const HF ax = tr.challenge(), ay = tr.challenge();
+      Term T{rb, std::vector<HF>(hc.W[B.layer], kZero)};
+      for (uint32_t k = 0; k < B.count; ++k) T.M[gate(k)] = add(mul(ax, qx[B.base + k]), mul(ay, qy[B.base + k]));
+      terms[B.layer].push_back(std::move(T));
+      claims[B.layer] = add(claims[B.layer], add(mul(ax, vb[b]), mul(ay, vb[nb + b])));
     }
   }
   if (pos != proof_len) return SISU_ERR_REJECT;
