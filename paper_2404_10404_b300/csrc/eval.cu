@@ -114,9 +114,83 @@ __global__ void k_eval_layer_acc(const uint32_t* __restrict__ Vn, uint32_t* __re
   }
 }
 
+// The same evaluation with each copy's row of layer i + 1 staged in shared
+// memory (rows of at most kRowStageMax elements, 64 KiB): a CTA takes one
+// copy at a time, copies the row in with 16-byte cp.async (a hardware wait,
+// no spin) and gathers both inputs of every gate from shared memory instead
+// of from scattered 32-byte sectors in L2/DRAM; several CTAs per SM keep
+// loads of some copies in flight while others compute.
+constexpr uint32_t kRowStageMax = 2048;
+constexpr uint32_t kRowThreads = 256;
+
+__global__ void __launch_bounds__(kRowThreads) k_eval_layer_row(const uint32_t* __restrict__ Vn,
+                                                                uint32_t* __restrict__ V,
+                                                                const uint4* __restrict__ sg, uint32_t nmul,
+                                                                uint32_t ntot, uint32_t b0, uint32_t nb, uint32_t s,
+                                                                uint32_t sn) {
+  pdl_wait();
+  extern __shared__ __align__(16) uint32_t row[];
+  const uint32_t wn16 = 2u << sn, W = 1u << s;  // the row's 16-byte pieces, the layer's gates
+  for (uint32_t bi = blockIdx.x; bi < nb; bi += gridDim.x) {
+    const size_t b = (size_t)b0 + bi;
+    const uint4* src = reinterpret_cast<const uint4*>(Vn + ((b << sn) << 3));
+    for (uint32_t k = threadIdx.x; k < wn16; k += kRowThreads)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                       (uint32_t)__cvta_generic_to_shared(row + 4 * k)),
+                   "l"(src + k)
+                   : "memory");
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    for (uint32_t q = threadIdx.x; q < W; q += kRowThreads) {
+      const uint4 gi = sg[q];
+      Fr out = fr_zero();
+      if (q < ntot) {
+        const Fr x = fr_load(row, gi.x), y = fr_load(row, gi.y);
+        out = q < nmul ? fr_mul(x, y) : fr_add(x, y);
+      }
+      fr_store(V, (b << s) + gi.z, out);
+    }
+    __syncthreads();  // the row is read before the next copy's lands
+  }
+}
+
 int launch_eval_layer(const uint32_t* Vn, uint32_t* V, const DevLayer& L, uint32_t b0, uint32_t nb, uint32_t s,
                       uint32_t sn, void* stream) {
   size_t n = (size_t)nb << s;
+  if (!L.offo && (1u << sn) <= kRowStageMax && nb >= kSMs) {
+    static int per_sm[12] = {0};
+    const size_t smem = (size_t)32 << sn;
+    if (smem > 48 * 1024) {
+      static bool attr = false;
+      if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_eval_layer_row, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(32 * kRowStageMax));
+        if (e != cudaSuccess) return (int)e;
+        attr = true;
+      }
+    }
+    int& ps = per_sm[sn];
+    if (ps == 0) {
+      int m = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, k_eval_layer_row, kRowThreads, smem) != cudaSuccess || m < 1)
+        m = 1;
+      ps = m;
+    }
+    const unsigned grid = (unsigned)std::min<size_t>(nb, (size_t)kSMs * ps);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = kRowThreads;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = (cudaStream_t)stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_eval_layer_row, Vn, V, L.sgate, L.nmul, L.ntot, b0, nb, s, sn);
+    if (e != cudaSuccess) return (int)e;
+    return post_launch();
+  }
   if (L.offo)
     k_eval_layer_acc<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(Vn, V, L.offo, L.eo, b0, nb, s, sn);
   else
