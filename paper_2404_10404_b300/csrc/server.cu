@@ -110,7 +110,7 @@ struct sisu_server {
   std::vector<uint8_t*> pinned;
   std::vector<char> busy;
   uint64_t admitted = 0;          // jobs admitted so far
-  const Job* head = nullptr;      // the job at the head of the queue when last looked at
+  uint64_t head = 0;              // ticket of the job at the head of the queue when last looked at
   uint32_t head_bypass = 0;       // admissions that passed it
   std::mutex mu;
   std::condition_variable cv;
@@ -140,8 +140,8 @@ struct sisu_server {
           break;
         }
       if (slot < 0) return false;
-      if (queue.front() != head) {
-        head = queue.front();
+      if (queue.front()->ticket != head) {
+        head = queue.front()->ticket;
         head_bypass = 0;
       }
       size_t off = 0, failed = SIZE_MAX;  // smallest footprint that did not fit
