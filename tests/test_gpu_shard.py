@@ -89,3 +89,34 @@ def test_refused_shapes(S):
         S.shard_buffer_sizes(ep, 3)
     with pytest.raises(S.SisuError):  # rank beyond world
         S.Shard(ep, 2, 2, bufs)
+
+
+def test_nccl_exchange_one_rank(S, oracle):
+    """The torch.distributed exchange over NCCL on device buffers, in a
+    one-rank process group (the only multi-process form one GPU allows):
+    the sharded driver's all-gathers and broadcast run through NCCL and the
+    proof equals the oracle's."""
+    import socket
+
+    import torch
+    import torch.distributed as dist
+    from paper_2404_10404_b300.shard import DistExchange, GpuRank, prove_sharded
+    import os
+    if dist.is_initialized():
+        pytest.skip("a process group already exists")
+    os.environ.setdefault("NCCL_NVLS_ENABLE", "0")
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    dist.init_process_group("nccl", init_method=f"tcp://127.0.0.1:{port}", rank=0, world_size=1,
+                            device_id=torch.device("cuda", torch.cuda.current_device()))
+    try:
+        spec = synth.uniform_circuit(29, 64, [64, 32, 64], 60, name="gs-nccl")
+        xb = synth.fr_bytes(synth.inputs_for(spec))
+        stream = torch.cuda.current_stream()
+        rank = GpuRank(spec, xb, 0, 1, None, stream)
+        with torch.cuda.stream(stream):
+            proof = prove_sharded([rank], DistExchange(), stream)
+        assert proof == oracle.prove(spec, xb)
+    finally:
+        dist.destroy_process_group()
