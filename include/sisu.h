@@ -444,8 +444,7 @@ int sisu_statement_digest(const uint8_t* data, size_t len, uint8_t* out, void* s
  * Scratch: a fixed 4 MiB array in the library's device memory, which every
  * GPU that loads the library holds until the process exits.  The first call
  * on a device looks up that array's device address (cudaGetSymbolAddress)
- * and caches it, so make the first call on each device before any stream
- * capture.  All calls share the array: calls that overlap on the GPU (on
+ * and caches it for later calls.  All calls share the array: calls that overlap on the GPU (on
  * different streams, or from different threads) race and must be ordered
  * by the caller.  Nothing in the array needs to start at zero.  No
  * cudaMalloc, cudaFree or other allocating routine is called.
