@@ -29,11 +29,12 @@ inline int post_launch() {
 // the launch gap between the short kernels of a proof.  Such a kernel must
 // begin with pdl_wait().
 template <typename... K, typename... A>
-inline int launch_pdl(void (*kernel)(K...), dim3 grid, dim3 block, cudaStream_t st, A&&... args) {
+inline int launch_pdl_smem(void (*kernel)(K...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                           A&&... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = block;
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -43,6 +44,11 @@ inline int launch_pdl(void (*kernel)(K...), dim3 grid, dim3 block, cudaStream_t 
   const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
   if (e != cudaSuccess) return (int)e;
   return post_launch();
+}
+
+template <typename... K, typename... A>
+inline int launch_pdl(void (*kernel)(K...), dim3 grid, dim3 block, cudaStream_t st, A&&... args) {
+  return launch_pdl_smem(kernel, grid, block, 0, st, std::forward<A>(args)...);
 }
 
 #ifdef __CUDACC__

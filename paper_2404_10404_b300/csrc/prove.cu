@@ -533,6 +533,40 @@ __device__ __forceinline__ Fr copy_items(const uint32_t* __restrict__ T, uint32_
   return tot;  // E's factor 2^32 has cancelled the reductions' 2^-32
 }
 
+// Gathers of the per-warp item loop staged through shared memory: each
+// lane copies its next item's five elements (w, x0, x1, y0, y1) there with
+// 16-byte cp.async while it computes the current one, so the products never
+// wait on an L2 or DRAM gather.  A warp's area holds two stages of five
+// elements a lane, each element as two 16-byte halves in lane-contiguous
+// rows (conflict-free 16-byte accesses).
+constexpr uint32_t kStageWords4 = 2 * 5 * 2 * 32;  // 16-byte words a warp (10 KiB)
+
+__device__ __forceinline__ uint4* stage_slot(uint4* stg, int st, int f, int half, int lane) {
+  return stg + ((st * 5 + f) * 2 + half) * 32 + lane;
+}
+
+__device__ __forceinline__ void stage_issue(uint4* stg, int st, int lane, const uint32_t* w,
+                                            const uint32_t* x0, const uint32_t* x1, const uint32_t* y0,
+                                            const uint32_t* y1) {
+  const uint32_t* src[5] = {w, x0, x1, y0, y1};
+#pragma unroll
+  for (int f = 0; f < 5; ++f)
+#pragma unroll
+    for (int half = 0; half < 2; ++half)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                       (uint32_t)__cvta_generic_to_shared(stage_slot(stg, st, f, half, lane))),
+                   "l"(src[f] + 4 * half)
+                   : "memory");
+}
+
+__device__ __forceinline__ Fr stage_read(uint4* stg, int st, int f, int lane) {
+  const uint4 a = *stage_slot(stg, st, f, 0, lane), b = *stage_slot(stg, st, f, 1, lane);
+  Fr x;
+  x.v[0] = a.x; x.v[1] = a.y; x.v[2] = a.z; x.v[3] = a.w;
+  x.v[4] = b.x; x.v[5] = b.y; x.v[6] = b.z; x.v[7] = b.w;
+  return x;
+}
+
 // The round's items of the big rounds (more pairs than CTAs, m = 0), split
 // further: each warp of CTA `bid` owns a contiguous 1/NW of the CTA's cost
 // range, sums every pair segment it touches with warp shuffles and weights
@@ -544,7 +578,8 @@ template <int BD>
 __device__ __forceinline__ Fr copy_items_warp(const uint32_t* __restrict__ T, uint32_t sn, uint32_t h,
                                               const uint32_t* __restrict__ E, const uint32_t* __restrict__ om,
                                               const uint4* __restrict__ sg, uint32_t nmul, uint32_t ntot,
-                                              uint64_t per_cta, uint32_t m, uint32_t bid, uint32_t* sh_e) {
+                                              uint64_t per_cta, uint32_t m, uint32_t bid, uint32_t* sh_e,
+                                              uint4* stg) {
   constexpr int NW = BD / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint64_t pair_cost = copy_pair_cost(nmul, ntot);
@@ -576,11 +611,27 @@ __device__ __forceinline__ Fr copy_items_warp(const uint32_t* __restrict__ T, ui
     const uint32_t* lo = T + (((size_t)j << sn) << 3);
     const uint32_t* hi = T + (((size_t)(j + h) << sn) << 3);
     FrAcc a0 = fracc_zero(), a1 = fracc_zero(), ac = fracc_zero();
-    for (uint32_t q = g0 + lane; q < g1; q += 32) {
+    // two-stage pipeline: item q + 32's gathers are in flight while item q
+    // is computed (one cp.async group a lane and item)
+    uint32_t q = g0 + lane;
+    int st = 0;
+    if (q < g1) {
       const uint4 gi = sg[q];
-      const Fr w = fr_load(om, q);
-      const Fr x0 = fr_load(lo, gi.x), x1 = fr_load(hi, gi.x);
-      const Fr y0 = fr_load(lo, gi.y), y1 = fr_load(hi, gi.y);
+      stage_issue(stg, 0, lane, om + 8 * (size_t)q, lo + 8 * (size_t)gi.x, hi + 8 * (size_t)gi.x,
+                  lo + 8 * (size_t)gi.y, hi + 8 * (size_t)gi.y);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    for (; q < g1; q += 32, st ^= 1) {
+      const uint32_t qn = q + 32;
+      if (qn < g1) {
+        const uint4 gi = sg[qn];
+        stage_issue(stg, st ^ 1, lane, om + 8 * (size_t)qn, lo + 8 * (size_t)gi.x, hi + 8 * (size_t)gi.x,
+                    lo + 8 * (size_t)gi.y, hi + 8 * (size_t)gi.y);
+      }
+      asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 1;" ::: "memory");
+      const Fr w = stage_read(stg, st, 0, lane);
+      const Fr x0 = stage_read(stg, st, 1, lane), x1 = stage_read(stg, st, 2, lane);
+      const Fr y0 = stage_read(stg, st, 3, lane), y1 = stage_read(stg, st, 4, lane);
       if (q < nmul) {
         const Fr wx0 = fr_mul(w, x0), wx1 = fr_mul(w, x1);
         fracc_mac(a0, wx0, y0);
@@ -650,8 +701,10 @@ __global__ void __launch_bounds__(BD) k_copy_round(const uint32_t* __restrict__ 
     }
   } else {  // segments per warp, then the warps' sums by a shuffle tree in warp 0
     __shared__ Fr wtot[BD / 32][4];
+    extern __shared__ uint4 cr_stage[];  // kStageWords4 a warp
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const Fr tot = copy_items_warp<BD>(T, sn, h, E, om, sg, nmul, ntot, per_cta, m, blockIdx.x, sh_e[warp]);
+    const Fr tot = copy_items_warp<BD>(T, sn, h, E, om, sg, nmul, ntot, per_cta, m, blockIdx.x, sh_e[warp],
+                                       cr_stage + warp * kStageWords4);
     if (lane < 4) wtot[warp][lane] = tot;
     __syncthreads();
 #pragma unroll
@@ -710,9 +763,18 @@ static int launch_copy_round_bd(int form, uint32_t min_items, const uint32_t* T,
   // about min_items items a CTA (short serial chains)
   const CopySplit sp = copy_split(h, L.nmul, L.ntot, ncmax, min_items ? min_items : BD);
   const bool warp = form == 2 || (form == 0 && sp.m == 0);
-  if (warp)
-    return launch_pdl(k_copy_round<BD, true>, sp.nc, BD, st, T, sn, h, E, omega_s, L.sgate, L.nmul, L.ntot,
-                      sp.per_cta, sp.m, partials, S, proof, off, k, sums_out);
+  if (warp) {
+    const size_t smem = (size_t)(BD / 32) * kStageWords4 * sizeof(uint4);
+    static bool attr = false;
+    if (!attr) {
+      const cudaError_t e = cudaFuncSetAttribute(k_copy_round<BD, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem);
+      if (e != cudaSuccess) return (int)e;
+      attr = true;
+    }
+    return launch_pdl_smem(k_copy_round<BD, true>, sp.nc, BD, smem, st, T, sn, h, E, omega_s, L.sgate, L.nmul,
+                           L.ntot, sp.per_cta, sp.m, partials, S, proof, off, k, sums_out);
+  }
   return launch_pdl(k_copy_round<BD, false>, sp.nc, BD, st, T, sn, h, E, omega_s, L.sgate, L.nmul, L.ntot,
                     sp.per_cta, sp.m, partials, S, proof, off, k, sums_out);
 }
