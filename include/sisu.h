@@ -473,10 +473,13 @@ int sisu_tune_copy_round(uint32_t log_width, uint32_t log_pairs, uint32_t cta_th
  * products built from 64-bit partial products (mul.wide), kind 6 = kinds 2
  * and 5 run side by side on the same operands, kind 7 = full 512-bit
  * products added into one 544-bit accumulator (no reduction), kind 8 =
- * Montgomery squares by the squaring routine.  Reports the elapsed
- * milliseconds and the number of operations (multiply-adds, or field
- * products for kinds 2, 3, 5, 7 and 8); for kind 6, *ops is minus the number of
- * threads whose two products disagreed (0 when they all agree). */
+ * Montgomery squares by the squaring routine, kind 9 = kind 7 with each
+ * product by one level of Karatsuba, kind 10 = kinds 7 and 9 on the same
+ * arbitrary 256-bit operands (all-ones words included).  Reports the
+ * elapsed milliseconds and the number of operations (multiply-adds, or
+ * field products for kinds 2, 3, 5, 7, 8 and 9); for kinds 6 and 10, *ops
+ * is minus the number of threads whose two results disagreed (0 when they
+ * all agree). */
 int sisu_microbench(int kind, uint32_t blocks, uint32_t threads, uint32_t iters, void* stream,
                     double* ms, double* ops);
 

@@ -224,8 +224,8 @@ __global__ void k_mb_frmac(uint32_t iters, uint32_t* sink) {
   x.v[0] ^= threadIdx.x;
   FrAcc acc = fracc_zero();
   for (uint32_t it = 0; it < iters; ++it) {
-    fracc_mac(acc, x, y);
-    fracc_mac(acc, y, x);
+    acc = fracc_mac_school_call(acc, x, y);
+    acc = fracc_mac_school_call(acc, y, x);
     x.v[1] ^= acc.v[4];
   }
   const Fr r = fr_redc288(acc);
@@ -233,6 +233,54 @@ __global__ void k_mb_frmac(uint32_t iters, uint32_t* sink) {
 #pragma unroll
   for (int i = 0; i < 8; ++i) o ^= r.v[i];
   sink[blockIdx.x * blockDim.x + threadIdx.x] = o;
+}
+
+// the same, each product by one level of Karatsuba (kind 9)
+__global__ void k_mb_frmac_kara(uint32_t iters, uint32_t* sink) {
+  Fr x = fr_one(), y = fr_r2();
+  x.v[0] ^= threadIdx.x;
+  FrAcc acc = fracc_zero();
+  for (uint32_t it = 0; it < iters; ++it) {
+    fracc_mac_kara_inl(acc, x, y);
+    fracc_mac_kara_inl(acc, y, x);
+    x.v[1] ^= acc.v[4];
+  }
+  const Fr r = fr_redc288(acc);
+  uint32_t o = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) o ^= r.v[i];
+  sink[blockIdx.x * blockDim.x + threadIdx.x] = o;
+}
+
+// check of the two accumulations against each other on arbitrary 256-bit
+// operands, all-ones words included (kind 10): nonzero where they differ
+__global__ void k_mb_frmac_check(uint32_t iters, uint32_t* sink) {
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t st = 0x9e3779b9u ^ (tid * 0x85ebca6bu);
+  auto next = [&]() {  // xorshift32
+    st ^= st << 13;
+    st ^= st >> 17;
+    st ^= st << 5;
+    return st;
+  };
+  FrAcc s1 = fracc_zero(), s2 = fracc_zero();
+  uint32_t bad = 0;
+  for (uint32_t it = 0; it < iters; ++it) {
+    Fr x, y;
+    const uint32_t mode = next();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      x.v[i] = (mode & 1u) ? 0xffffffffu : next();
+      y.v[i] = (mode & 2u) ? 0xffffffffu : next();
+      if (mode & 4u) x.v[i] = (i < 4) ? 0xffffffffu : x.v[i];
+      if (mode & 8u) y.v[i] = (i >= 4) ? 0xffffffffu : y.v[i];
+    }
+    fracc_mac_inl(s1, x, y);
+    fracc_mac_kara_inl(s2, x, y);
+#pragma unroll
+    for (int i = 0; i < 17; ++i) bad |= s1.v[i] ^ s2.v[i];
+  }
+  sink[tid] = bad;
 }
 
 // Montgomery squares (the squaring routine), two chains a thread
@@ -286,6 +334,8 @@ int run_microbench(int kind, uint32_t blocks, uint32_t threads, uint32_t iters, 
     else if (kind == 5) k_mb_frmul_wide<<<blocks, threads, 0, st>>>(iters, sink);
     else if (kind == 7) k_mb_frmac<<<blocks, threads, 0, st>>>(iters, sink);
     else if (kind == 8) k_mb_frsqr<<<blocks, threads, 0, st>>>(iters, sink);
+    else if (kind == 9) k_mb_frmac_kara<<<blocks, threads, 0, st>>>(iters, sink);
+    else if (kind == 10) k_mb_frmac_check<<<blocks, threads, 0, st>>>(iters, sink);
     else k_mb_frmul_check<<<blocks, threads, 0, st>>>(iters, sink);
     launches_add(1);
   };
@@ -297,7 +347,7 @@ int run_microbench(int kind, uint32_t blocks, uint32_t threads, uint32_t iters, 
   float t = 0;
   cudaEventElapsedTime(&t, a, b);
   *ms = t;
-  if (kind == 6 && e == cudaSuccess) {
+  if ((kind == 6 || kind == 10) && e == cudaSuccess) {
     std::vector<uint32_t> h((size_t)blocks * threads);
     e = cudaMemcpy(h.data(), sink, h.size() * 4, cudaMemcpyDeviceToHost);
     size_t bad = 0;
@@ -308,7 +358,8 @@ int run_microbench(int kind, uint32_t blocks, uint32_t threads, uint32_t iters, 
     cudaFree(sink);
     return (int)e;
   }
-  double per = (kind == 2 || kind == 3 || kind == 5 || kind == 7 || kind == 8) ? 2.0 : kind == 6 ? 2.0 : 64.0;
+  double per = (kind == 2 || kind == 3 || kind == 5 || kind == 7 || kind == 8 || kind == 9) ? 2.0 : kind == 6 ? 2.0
+                                                                                                             : 64.0;
   *ops = (double)blocks * threads * iters * per;
   cudaEventDestroy(a);
   cudaEventDestroy(b);
