@@ -475,11 +475,13 @@ int sisu_tune_copy_round(uint32_t log_width, uint32_t log_pairs, uint32_t cta_th
  * products added into one 544-bit accumulator (no reduction), kind 8 =
  * Montgomery squares by the squaring routine, kind 9 = kind 7 with each
  * product by one level of Karatsuba, kind 10 = kinds 7 and 9 on the same
- * arbitrary 256-bit operands (all-ones words included).  Reports the
- * elapsed milliseconds and the number of operations (multiply-adds, or
- * field products for kinds 2, 3, 5, 7, 8 and 9); for kinds 6 and 10, *ops
- * is minus the number of threads whose two results disagreed (0 when they
- * all agree). */
+ * arbitrary 256-bit operands (all-ones words included), kind 11 =
+ * Montgomery products as a Karatsuba product and a separate reduction,
+ * kind 12 = kinds 2 and 11 on the same operands.  Reports the elapsed
+ * milliseconds and the number of operations (multiply-adds, or field
+ * products for kinds 2, 3, 5, 7, 8, 9 and 11); for kinds 6, 10 and 12,
+ * *ops is minus the number of threads whose two results disagreed (0 when
+ * they all agree). */
 int sisu_microbench(int kind, uint32_t blocks, uint32_t threads, uint32_t iters, void* stream,
                     double* ms, double* ops);
 

@@ -283,6 +283,39 @@ __global__ void k_mb_frmac_check(uint32_t iters, uint32_t* sink) {
   sink[tid] = bad;
 }
 
+static __device__ __noinline__ Fr fr_mul_kara_call(Fr a, Fr b) { return fr_mul_kara_inl(a, b); }
+
+// Montgomery products by the Karatsuba product and a separate reduction,
+// chained as in kind 2 (kind 11)
+__global__ void k_mb_frmul_kara(uint32_t iters, uint32_t* sink) {
+  Fr x = fr_one(), y = fr_r2(), z = fr_one();
+  x.v[0] ^= threadIdx.x;
+  for (uint32_t it = 0; it < iters; ++it) {
+    x = fr_mul_kara_call(x, y);
+    z = fr_mul_kara_call(z, x);
+  }
+  uint32_t acc = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) acc ^= x.v[i] ^ z.v[i];
+  sink[blockIdx.x * blockDim.x + threadIdx.x] = acc;
+}
+
+// kinds 2 and 11 on the same operands below 2r (kind 12): nonzero where the
+// two products differ
+__global__ void k_mb_frmul_kara_check(uint32_t iters, uint32_t* sink) {
+  Fr x = fr_one(), y = fr_r2();
+  x.v[0] ^= threadIdx.x + blockIdx.x * 977u;
+  uint32_t bad = 0;
+  for (uint32_t it = 0; it < iters; ++it) {
+    const Fr p = fr_mul(x, y), q = fr_mul_kara_call(x, y);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) bad |= p.v[i] ^ q.v[i];
+    y = fr_add(y, p);   // both stay below 2r
+    x = fr_sub(x, fr_dbl(q));
+  }
+  sink[blockIdx.x * blockDim.x + threadIdx.x] = bad;
+}
+
 // Montgomery squares (the squaring routine), two chains a thread
 __global__ void k_mb_frsqr(uint32_t iters, uint32_t* sink) {
   Fr x = fr_one(), z = fr_r2();
@@ -336,6 +369,8 @@ int run_microbench(int kind, uint32_t blocks, uint32_t threads, uint32_t iters, 
     else if (kind == 8) k_mb_frsqr<<<blocks, threads, 0, st>>>(iters, sink);
     else if (kind == 9) k_mb_frmac_kara<<<blocks, threads, 0, st>>>(iters, sink);
     else if (kind == 10) k_mb_frmac_check<<<blocks, threads, 0, st>>>(iters, sink);
+    else if (kind == 11) k_mb_frmul_kara<<<blocks, threads, 0, st>>>(iters, sink);
+    else if (kind == 12) k_mb_frmul_kara_check<<<blocks, threads, 0, st>>>(iters, sink);
     else k_mb_frmul_check<<<blocks, threads, 0, st>>>(iters, sink);
     launches_add(1);
   };
@@ -347,7 +382,7 @@ int run_microbench(int kind, uint32_t blocks, uint32_t threads, uint32_t iters, 
   float t = 0;
   cudaEventElapsedTime(&t, a, b);
   *ms = t;
-  if ((kind == 6 || kind == 10) && e == cudaSuccess) {
+  if ((kind == 6 || kind == 10 || kind == 12) && e == cudaSuccess) {
     std::vector<uint32_t> h((size_t)blocks * threads);
     e = cudaMemcpy(h.data(), sink, h.size() * 4, cudaMemcpyDeviceToHost);
     size_t bad = 0;
@@ -358,7 +393,7 @@ int run_microbench(int kind, uint32_t blocks, uint32_t threads, uint32_t iters, 
     cudaFree(sink);
     return (int)e;
   }
-  double per = (kind == 2 || kind == 3 || kind == 5 || kind == 7 || kind == 8 || kind == 9) ? 2.0 : kind == 6 ? 2.0
+  double per = (kind == 2 || kind == 3 || kind == 5 || kind == 7 || kind == 8 || kind == 9 || kind == 11) ? 2.0 : kind == 6 ? 2.0
                                                                                                              : 64.0;
   *ops = (double)blocks * threads * iters * per;
   cudaEventDestroy(a);

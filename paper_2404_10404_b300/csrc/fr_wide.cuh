@@ -683,6 +683,285 @@ __device__ __forceinline__ Fr fr_redc288(const FrAcc& acc) {
   return o;
 }
 
+// T 2^-256 mod r, in [0, 2r), for T < 4 r^2 (a product of two values below
+// 2r): eight Montgomery steps, each adding the multiple m r of r that zeroes
+// the lowest remaining word, with the carries rippling to the top word.
+// The result is words 8..15 (word 16 stays 0).
+__device__ __forceinline__ Fr fr_redc256(const FrAcc& acc) {
+  uint32_t t[17];
+#pragma unroll
+  for (int i = 0; i < 17; ++i) t[i] = acc.v[i];
+  // step 0: zero t[0]
+  asm("{\n\t"
+      ".reg .u32 m;\n\t"
+      "mul.lo.u32 m, %0, 0xefffffff;\n\t"
+      "mad.lo.cc.u32  %0, m, 0xf0000001, %0;\n\t"
+      "madc.lo.cc.u32 %1, m, 0x43e1f593, %1;\n\t"
+      "madc.lo.cc.u32 %2, m, 0x79b97091, %2;\n\t"
+      "madc.lo.cc.u32 %3, m, 0x2833e848, %3;\n\t"
+      "madc.lo.cc.u32 %4, m, 0x8181585d, %4;\n\t"
+      "madc.lo.cc.u32 %5, m, 0xb85045b6, %5;\n\t"
+      "madc.lo.cc.u32 %6, m, 0xe131a029, %6;\n\t"
+      "madc.lo.cc.u32 %7, m, 0x30644e72, %7;\n\t"
+      "addc.cc.u32    %8, %8, 0;\n\t"
+      "addc.cc.u32    %9, %9, 0;\n\t"
+      "addc.cc.u32    %10, %10, 0;\n\t"
+      "addc.cc.u32    %11, %11, 0;\n\t"
+      "addc.cc.u32    %12, %12, 0;\n\t"
+      "addc.cc.u32    %13, %13, 0;\n\t"
+      "addc.cc.u32    %14, %14, 0;\n\t"
+      "addc.cc.u32    %15, %15, 0;\n\t"
+      "addc.u32       %16, %16, 0;\n\t"
+      "mad.hi.cc.u32  %1, m, 0xf0000001, %1;\n\t"
+      "madc.hi.cc.u32 %2, m, 0x43e1f593, %2;\n\t"
+      "madc.hi.cc.u32 %3, m, 0x79b97091, %3;\n\t"
+      "madc.hi.cc.u32 %4, m, 0x2833e848, %4;\n\t"
+      "madc.hi.cc.u32 %5, m, 0x8181585d, %5;\n\t"
+      "madc.hi.cc.u32 %6, m, 0xb85045b6, %6;\n\t"
+      "madc.hi.cc.u32 %7, m, 0xe131a029, %7;\n\t"
+      "madc.hi.cc.u32 %8, m, 0x30644e72, %8;\n\t"
+      "addc.cc.u32    %9, %9, 0;\n\t"
+      "addc.cc.u32    %10, %10, 0;\n\t"
+      "addc.cc.u32    %11, %11, 0;\n\t"
+      "addc.cc.u32    %12, %12, 0;\n\t"
+      "addc.cc.u32    %13, %13, 0;\n\t"
+      "addc.cc.u32    %14, %14, 0;\n\t"
+      "addc.cc.u32    %15, %15, 0;\n\t"
+      "addc.u32       %16, %16, 0;\n\t"
+      "}"
+      : "+r"(t[0]), "+r"(t[1]), "+r"(t[2]), "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]), "+r"(t[7]), "+r"(t[8]), "+r"(t[9]), "+r"(t[10]), "+r"(t[11]), "+r"(t[12]), "+r"(t[13]), "+r"(t[14]), "+r"(t[15]), "+r"(t[16]));
+  // step 1: zero t[1]
+  asm("{\n\t"
+      ".reg .u32 m;\n\t"
+      "mul.lo.u32 m, %0, 0xefffffff;\n\t"
+      "mad.lo.cc.u32  %0, m, 0xf0000001, %0;\n\t"
+      "madc.lo.cc.u32 %1, m, 0x43e1f593, %1;\n\t"
+      "madc.lo.cc.u32 %2, m, 0x79b97091, %2;\n\t"
+      "madc.lo.cc.u32 %3, m, 0x2833e848, %3;\n\t"
+      "madc.lo.cc.u32 %4, m, 0x8181585d, %4;\n\t"
+      "madc.lo.cc.u32 %5, m, 0xb85045b6, %5;\n\t"
+      "madc.lo.cc.u32 %6, m, 0xe131a029, %6;\n\t"
+      "madc.lo.cc.u32 %7, m, 0x30644e72, %7;\n\t"
+      "addc.cc.u32    %8, %8, 0;\n\t"
+      "addc.cc.u32    %9, %9, 0;\n\t"
+      "addc.cc.u32    %10, %10, 0;\n\t"
+      "addc.cc.u32    %11, %11, 0;\n\t"
+      "addc.cc.u32    %12, %12, 0;\n\t"
+      "addc.cc.u32    %13, %13, 0;\n\t"
+      "addc.cc.u32    %14, %14, 0;\n\t"
+      "addc.u32       %15, %15, 0;\n\t"
+      "mad.hi.cc.u32  %1, m, 0xf0000001, %1;\n\t"
+      "madc.hi.cc.u32 %2, m, 0x43e1f593, %2;\n\t"
+      "madc.hi.cc.u32 %3, m, 0x79b97091, %3;\n\t"
+      "madc.hi.cc.u32 %4, m, 0x2833e848, %4;\n\t"
+      "madc.hi.cc.u32 %5, m, 0x8181585d, %5;\n\t"
+      "madc.hi.cc.u32 %6, m, 0xb85045b6, %6;\n\t"
+      "madc.hi.cc.u32 %7, m, 0xe131a029, %7;\n\t"
+      "madc.hi.cc.u32 %8, m, 0x30644e72, %8;\n\t"
+      "addc.cc.u32    %9, %9, 0;\n\t"
+      "addc.cc.u32    %10, %10, 0;\n\t"
+      "addc.cc.u32    %11, %11, 0;\n\t"
+      "addc.cc.u32    %12, %12, 0;\n\t"
+      "addc.cc.u32    %13, %13, 0;\n\t"
+      "addc.cc.u32    %14, %14, 0;\n\t"
+      "addc.u32       %15, %15, 0;\n\t"
+      "}"
+      : "+r"(t[1]), "+r"(t[2]), "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]), "+r"(t[7]), "+r"(t[8]), "+r"(t[9]), "+r"(t[10]), "+r"(t[11]), "+r"(t[12]), "+r"(t[13]), "+r"(t[14]), "+r"(t[15]), "+r"(t[16]));
+  // step 2: zero t[2]
+  asm("{\n\t"
+      ".reg .u32 m;\n\t"
+      "mul.lo.u32 m, %0, 0xefffffff;\n\t"
+      "mad.lo.cc.u32  %0, m, 0xf0000001, %0;\n\t"
+      "madc.lo.cc.u32 %1, m, 0x43e1f593, %1;\n\t"
+      "madc.lo.cc.u32 %2, m, 0x79b97091, %2;\n\t"
+      "madc.lo.cc.u32 %3, m, 0x2833e848, %3;\n\t"
+      "madc.lo.cc.u32 %4, m, 0x8181585d, %4;\n\t"
+      "madc.lo.cc.u32 %5, m, 0xb85045b6, %5;\n\t"
+      "madc.lo.cc.u32 %6, m, 0xe131a029, %6;\n\t"
+      "madc.lo.cc.u32 %7, m, 0x30644e72, %7;\n\t"
+      "addc.cc.u32    %8, %8, 0;\n\t"
+      "addc.cc.u32    %9, %9, 0;\n\t"
+      "addc.cc.u32    %10, %10, 0;\n\t"
+      "addc.cc.u32    %11, %11, 0;\n\t"
+      "addc.cc.u32    %12, %12, 0;\n\t"
+      "addc.cc.u32    %13, %13, 0;\n\t"
+      "addc.u32       %14, %14, 0;\n\t"
+      "mad.hi.cc.u32  %1, m, 0xf0000001, %1;\n\t"
+      "madc.hi.cc.u32 %2, m, 0x43e1f593, %2;\n\t"
+      "madc.hi.cc.u32 %3, m, 0x79b97091, %3;\n\t"
+      "madc.hi.cc.u32 %4, m, 0x2833e848, %4;\n\t"
+      "madc.hi.cc.u32 %5, m, 0x8181585d, %5;\n\t"
+      "madc.hi.cc.u32 %6, m, 0xb85045b6, %6;\n\t"
+      "madc.hi.cc.u32 %7, m, 0xe131a029, %7;\n\t"
+      "madc.hi.cc.u32 %8, m, 0x30644e72, %8;\n\t"
+      "addc.cc.u32    %9, %9, 0;\n\t"
+      "addc.cc.u32    %10, %10, 0;\n\t"
+      "addc.cc.u32    %11, %11, 0;\n\t"
+      "addc.cc.u32    %12, %12, 0;\n\t"
+      "addc.cc.u32    %13, %13, 0;\n\t"
+      "addc.u32       %14, %14, 0;\n\t"
+      "}"
+      : "+r"(t[2]), "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]), "+r"(t[7]), "+r"(t[8]), "+r"(t[9]), "+r"(t[10]), "+r"(t[11]), "+r"(t[12]), "+r"(t[13]), "+r"(t[14]), "+r"(t[15]), "+r"(t[16]));
+  // step 3: zero t[3]
+  asm("{\n\t"
+      ".reg .u32 m;\n\t"
+      "mul.lo.u32 m, %0, 0xefffffff;\n\t"
+      "mad.lo.cc.u32  %0, m, 0xf0000001, %0;\n\t"
+      "madc.lo.cc.u32 %1, m, 0x43e1f593, %1;\n\t"
+      "madc.lo.cc.u32 %2, m, 0x79b97091, %2;\n\t"
+      "madc.lo.cc.u32 %3, m, 0x2833e848, %3;\n\t"
+      "madc.lo.cc.u32 %4, m, 0x8181585d, %4;\n\t"
+      "madc.lo.cc.u32 %5, m, 0xb85045b6, %5;\n\t"
+      "madc.lo.cc.u32 %6, m, 0xe131a029, %6;\n\t"
+      "madc.lo.cc.u32 %7, m, 0x30644e72, %7;\n\t"
+      "addc.cc.u32    %8, %8, 0;\n\t"
+      "addc.cc.u32    %9, %9, 0;\n\t"
+      "addc.cc.u32    %10, %10, 0;\n\t"
+      "addc.cc.u32    %11, %11, 0;\n\t"
+      "addc.cc.u32    %12, %12, 0;\n\t"
+      "addc.u32       %13, %13, 0;\n\t"
+      "mad.hi.cc.u32  %1, m, 0xf0000001, %1;\n\t"
+      "madc.hi.cc.u32 %2, m, 0x43e1f593, %2;\n\t"
+      "madc.hi.cc.u32 %3, m, 0x79b97091, %3;\n\t"
+      "madc.hi.cc.u32 %4, m, 0x2833e848, %4;\n\t"
+      "madc.hi.cc.u32 %5, m, 0x8181585d, %5;\n\t"
+      "madc.hi.cc.u32 %6, m, 0xb85045b6, %6;\n\t"
+      "madc.hi.cc.u32 %7, m, 0xe131a029, %7;\n\t"
+      "madc.hi.cc.u32 %8, m, 0x30644e72, %8;\n\t"
+      "addc.cc.u32    %9, %9, 0;\n\t"
+      "addc.cc.u32    %10, %10, 0;\n\t"
+      "addc.cc.u32    %11, %11, 0;\n\t"
+      "addc.cc.u32    %12, %12, 0;\n\t"
+      "addc.u32       %13, %13, 0;\n\t"
+      "}"
+      : "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]), "+r"(t[7]), "+r"(t[8]), "+r"(t[9]), "+r"(t[10]), "+r"(t[11]), "+r"(t[12]), "+r"(t[13]), "+r"(t[14]), "+r"(t[15]), "+r"(t[16]));
+  // step 4: zero t[4]
+  asm("{\n\t"
+      ".reg .u32 m;\n\t"
+      "mul.lo.u32 m, %0, 0xefffffff;\n\t"
+      "mad.lo.cc.u32  %0, m, 0xf0000001, %0;\n\t"
+      "madc.lo.cc.u32 %1, m, 0x43e1f593, %1;\n\t"
+      "madc.lo.cc.u32 %2, m, 0x79b97091, %2;\n\t"
+      "madc.lo.cc.u32 %3, m, 0x2833e848, %3;\n\t"
+      "madc.lo.cc.u32 %4, m, 0x8181585d, %4;\n\t"
+      "madc.lo.cc.u32 %5, m, 0xb85045b6, %5;\n\t"
+      "madc.lo.cc.u32 %6, m, 0xe131a029, %6;\n\t"
+      "madc.lo.cc.u32 %7, m, 0x30644e72, %7;\n\t"
+      "addc.cc.u32    %8, %8, 0;\n\t"
+      "addc.cc.u32    %9, %9, 0;\n\t"
+      "addc.cc.u32    %10, %10, 0;\n\t"
+      "addc.cc.u32    %11, %11, 0;\n\t"
+      "addc.u32       %12, %12, 0;\n\t"
+      "mad.hi.cc.u32  %1, m, 0xf0000001, %1;\n\t"
+      "madc.hi.cc.u32 %2, m, 0x43e1f593, %2;\n\t"
+      "madc.hi.cc.u32 %3, m, 0x79b97091, %3;\n\t"
+      "madc.hi.cc.u32 %4, m, 0x2833e848, %4;\n\t"
+      "madc.hi.cc.u32 %5, m, 0x8181585d, %5;\n\t"
+      "madc.hi.cc.u32 %6, m, 0xb85045b6, %6;\n\t"
+      "madc.hi.cc.u32 %7, m, 0xe131a029, %7;\n\t"
+      "madc.hi.cc.u32 %8, m, 0x30644e72, %8;\n\t"
+      "addc.cc.u32    %9, %9, 0;\n\t"
+      "addc.cc.u32    %10, %10, 0;\n\t"
+      "addc.cc.u32    %11, %11, 0;\n\t"
+      "addc.u32       %12, %12, 0;\n\t"
+      "}"
+      : "+r"(t[4]), "+r"(t[5]), "+r"(t[6]), "+r"(t[7]), "+r"(t[8]), "+r"(t[9]), "+r"(t[10]), "+r"(t[11]), "+r"(t[12]), "+r"(t[13]), "+r"(t[14]), "+r"(t[15]), "+r"(t[16]));
+  // step 5: zero t[5]
+  asm("{\n\t"
+      ".reg .u32 m;\n\t"
+      "mul.lo.u32 m, %0, 0xefffffff;\n\t"
+      "mad.lo.cc.u32  %0, m, 0xf0000001, %0;\n\t"
+      "madc.lo.cc.u32 %1, m, 0x43e1f593, %1;\n\t"
+      "madc.lo.cc.u32 %2, m, 0x79b97091, %2;\n\t"
+      "madc.lo.cc.u32 %3, m, 0x2833e848, %3;\n\t"
+      "madc.lo.cc.u32 %4, m, 0x8181585d, %4;\n\t"
+      "madc.lo.cc.u32 %5, m, 0xb85045b6, %5;\n\t"
+      "madc.lo.cc.u32 %6, m, 0xe131a029, %6;\n\t"
+      "madc.lo.cc.u32 %7, m, 0x30644e72, %7;\n\t"
+      "addc.cc.u32    %8, %8, 0;\n\t"
+      "addc.cc.u32    %9, %9, 0;\n\t"
+      "addc.cc.u32    %10, %10, 0;\n\t"
+      "addc.u32       %11, %11, 0;\n\t"
+      "mad.hi.cc.u32  %1, m, 0xf0000001, %1;\n\t"
+      "madc.hi.cc.u32 %2, m, 0x43e1f593, %2;\n\t"
+      "madc.hi.cc.u32 %3, m, 0x79b97091, %3;\n\t"
+      "madc.hi.cc.u32 %4, m, 0x2833e848, %4;\n\t"
+      "madc.hi.cc.u32 %5, m, 0x8181585d, %5;\n\t"
+      "madc.hi.cc.u32 %6, m, 0xb85045b6, %6;\n\t"
+      "madc.hi.cc.u32 %7, m, 0xe131a029, %7;\n\t"
+      "madc.hi.cc.u32 %8, m, 0x30644e72, %8;\n\t"
+      "addc.cc.u32    %9, %9, 0;\n\t"
+      "addc.cc.u32    %10, %10, 0;\n\t"
+      "addc.u32       %11, %11, 0;\n\t"
+      "}"
+      : "+r"(t[5]), "+r"(t[6]), "+r"(t[7]), "+r"(t[8]), "+r"(t[9]), "+r"(t[10]), "+r"(t[11]), "+r"(t[12]), "+r"(t[13]), "+r"(t[14]), "+r"(t[15]), "+r"(t[16]));
+  // step 6: zero t[6]
+  asm("{\n\t"
+      ".reg .u32 m;\n\t"
+      "mul.lo.u32 m, %0, 0xefffffff;\n\t"
+      "mad.lo.cc.u32  %0, m, 0xf0000001, %0;\n\t"
+      "madc.lo.cc.u32 %1, m, 0x43e1f593, %1;\n\t"
+      "madc.lo.cc.u32 %2, m, 0x79b97091, %2;\n\t"
+      "madc.lo.cc.u32 %3, m, 0x2833e848, %3;\n\t"
+      "madc.lo.cc.u32 %4, m, 0x8181585d, %4;\n\t"
+      "madc.lo.cc.u32 %5, m, 0xb85045b6, %5;\n\t"
+      "madc.lo.cc.u32 %6, m, 0xe131a029, %6;\n\t"
+      "madc.lo.cc.u32 %7, m, 0x30644e72, %7;\n\t"
+      "addc.cc.u32    %8, %8, 0;\n\t"
+      "addc.cc.u32    %9, %9, 0;\n\t"
+      "addc.u32       %10, %10, 0;\n\t"
+      "mad.hi.cc.u32  %1, m, 0xf0000001, %1;\n\t"
+      "madc.hi.cc.u32 %2, m, 0x43e1f593, %2;\n\t"
+      "madc.hi.cc.u32 %3, m, 0x79b97091, %3;\n\t"
+      "madc.hi.cc.u32 %4, m, 0x2833e848, %4;\n\t"
+      "madc.hi.cc.u32 %5, m, 0x8181585d, %5;\n\t"
+      "madc.hi.cc.u32 %6, m, 0xb85045b6, %6;\n\t"
+      "madc.hi.cc.u32 %7, m, 0xe131a029, %7;\n\t"
+      "madc.hi.cc.u32 %8, m, 0x30644e72, %8;\n\t"
+      "addc.cc.u32    %9, %9, 0;\n\t"
+      "addc.u32       %10, %10, 0;\n\t"
+      "}"
+      : "+r"(t[6]), "+r"(t[7]), "+r"(t[8]), "+r"(t[9]), "+r"(t[10]), "+r"(t[11]), "+r"(t[12]), "+r"(t[13]), "+r"(t[14]), "+r"(t[15]), "+r"(t[16]));
+  // step 7: zero t[7]
+  asm("{\n\t"
+      ".reg .u32 m;\n\t"
+      "mul.lo.u32 m, %0, 0xefffffff;\n\t"
+      "mad.lo.cc.u32  %0, m, 0xf0000001, %0;\n\t"
+      "madc.lo.cc.u32 %1, m, 0x43e1f593, %1;\n\t"
+      "madc.lo.cc.u32 %2, m, 0x79b97091, %2;\n\t"
+      "madc.lo.cc.u32 %3, m, 0x2833e848, %3;\n\t"
+      "madc.lo.cc.u32 %4, m, 0x8181585d, %4;\n\t"
+      "madc.lo.cc.u32 %5, m, 0xb85045b6, %5;\n\t"
+      "madc.lo.cc.u32 %6, m, 0xe131a029, %6;\n\t"
+      "madc.lo.cc.u32 %7, m, 0x30644e72, %7;\n\t"
+      "addc.cc.u32    %8, %8, 0;\n\t"
+      "addc.u32       %9, %9, 0;\n\t"
+      "mad.hi.cc.u32  %1, m, 0xf0000001, %1;\n\t"
+      "madc.hi.cc.u32 %2, m, 0x43e1f593, %2;\n\t"
+      "madc.hi.cc.u32 %3, m, 0x79b97091, %3;\n\t"
+      "madc.hi.cc.u32 %4, m, 0x2833e848, %4;\n\t"
+      "madc.hi.cc.u32 %5, m, 0x8181585d, %5;\n\t"
+      "madc.hi.cc.u32 %6, m, 0xb85045b6, %6;\n\t"
+      "madc.hi.cc.u32 %7, m, 0xe131a029, %7;\n\t"
+      "madc.hi.cc.u32 %8, m, 0x30644e72, %8;\n\t"
+      "addc.u32       %9, %9, 0;\n\t"
+      "}"
+      : "+r"(t[7]), "+r"(t[8]), "+r"(t[9]), "+r"(t[10]), "+r"(t[11]), "+r"(t[12]), "+r"(t[13]), "+r"(t[14]), "+r"(t[15]), "+r"(t[16]));
+  Fr r;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) r.v[i] = t[8 + i];
+  return r;
+}
+
+// Montgomery product a b 2^-256 mod r by the Karatsuba 512-bit product and
+// a separate reduction (inputs and output in [0, 2r))
+__device__ __forceinline__ Fr fr_mul_kara_inl(const Fr& a, const Fr& b) {
+  FrAcc t = fracc_zero();
+  fracc_mac_kara_inl(t, a, b);
+  return fr_redc256(t);
+}
+
+
 // one out-of-line copy per translation unit (see fr_mul_call); operands and
 // result travel in registers
 // The kernels' lazy product: one level of Karatsuba (three 128-bit

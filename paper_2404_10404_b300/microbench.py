@@ -18,7 +18,8 @@ def main():
     for name, kind, iters in (("mad_lo", 0, 512), ("mad_hi", 1, 512), ("fr_mul", 2, 128),
                               ("fr_mul_inline", 3, 128), ("mad_wide", 4, 512), ("fr_mul_wide", 5, 128),
                               ("fr_mul_check", 6, 64), ("fr_mac_512", 7, 128), ("fr_sqr", 8, 128),
-                              ("fr_mac_512_karatsuba", 9, 128), ("fr_mac_check", 10, 256)):
+                              ("fr_mac_512_karatsuba", 9, 128), ("fr_mac_check", 10, 256),
+                              ("fr_mul_karatsuba", 11, 128), ("fr_mul_karatsuba_check", 12, 256)):
         ms, ops = S.microbench(kind, 148 * 8, 256, iters, st)
         out[name] = {"ms": ms, "ops": ops, "per_s": ops / (ms / 1e3)}
     # the product rate at the occupancy of the prover kernels (1 and 2 CTAs of 256 per SM)

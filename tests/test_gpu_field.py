@@ -92,7 +92,7 @@ def test_device_digest_vs_oracle(S, oracle, n):
 
 
 def test_microbench_runs(S):
-    for kind in (0, 1, 2, 3, 4, 5, 7, 8):
+    for kind in (0, 1, 2, 3, 4, 5, 7, 8, 9, 11):
         ms, ops = S.microbench(kind, 148, 256, 64)
         assert ms > 0 and ops > 0
 
@@ -101,6 +101,16 @@ def test_product_formulations_agree(S):
     """The carry-chain and the 64-bit-partial-product Montgomery products
     give identical limbs on chained inputs (every thread of every block)."""
     ms, bad = S.microbench(6, 148 * 4, 256, 256)
+    assert bad == 0
+
+
+def test_karatsuba_forms_agree(S):
+    """The lazy 512-bit product by Karatsuba (the kernels' form) equals the
+    schoolbook product on arbitrary 256-bit operands, all-ones words
+    included; the Karatsuba-based Montgomery product equals the CIOS one."""
+    ms, bad = S.microbench(10, 148 * 4, 256, 256)
+    assert bad == 0
+    ms, bad = S.microbench(12, 148 * 4, 256, 256)
     assert bad == 0
 
 
