@@ -1091,7 +1091,10 @@ static int enqueue_prove(const sisu_circuit* cc, sisu_eval* ev, const sisu_trans
       const uint32_t h = hc.C >> (k + 1);
       {
         ProfScope ps(kProfCopyRound, per_pair * h, st);
-        CK(launch_copy_round(tab, sn, h, w.E, w.om, L, w.partials, w.S, w.proof, off + 32 * 3 * (size_t)k, k, st),
+        // the first round reads the layer's own values (gates of one entry each)
+        const uint32_t* Vg = k == 0 && !L.offo ? ev->V[i] : nullptr;
+        CK(launch_copy_round(tab, sn, h, w.E, w.om, L, w.partials, w.S, w.proof, off + 32 * 3 * (size_t)k, k, st,
+                             nullptr, Vg, hc.s[i]),
            "copy round");
       }
       {

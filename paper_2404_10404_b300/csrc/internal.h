@@ -134,10 +134,14 @@ size_t eq_half_words(uint32_t c, uint32_t smax);
 // 2^log_pairs pairs (bd 0: the default); -1 for a value out of range
 int set_copy_tune(uint32_t sn, uint32_t log_pairs, uint32_t bd, uint32_t form, uint32_t min_items);
 // sums_out (not null): the round's sums g(0..3) go there (one rank of a
-// copy-sharded proof) instead of the message and transcript
+// copy-sharded proof) instead of the message and transcript.  Vg (not
+// null, first round of a layer whose gates have one entry each, T the
+// layer's unfolded input values): the layer's own values, rows of 2^sv,
+// which the round reads in place of recomputing its t = 0, 1 products.
 int launch_copy_round(const uint32_t* T, uint32_t sn, uint32_t h, const uint32_t* E, const uint32_t* omega_s,
                       const DevLayer& L, uint32_t* partials, DevState* S, uint8_t* proof, size_t off,
-                      uint32_t k, void* stream, uint32_t* sums_out = nullptr);
+                      uint32_t k, void* stream, uint32_t* sums_out = nullptr, const uint32_t* Vg = nullptr,
+                      uint32_t sv = 0);
 int launch_copy_fold(const uint32_t* src, uint32_t* dst, uint32_t sn, uint32_t h, uint32_t* E,
                      DevState* S, uint32_t k, void* stream);
 // copy-sharded proofs: the round message from the gathered sums of every
