@@ -887,7 +887,7 @@ static void workspace_sizes(const sisu_circuit* cc, size_t sizes[kWsRegions], ui
   for (uint32_t i = 0; i < hc.d; ++i) smax = std::max(smax, hc.s[i]);
   const size_t hstride = hc.c + 2 * (size_t)sxmax + 2 * (size_t)nbmax;
   const bool g = hc.general;
-  const size_t v[kWsRegions] = {half, (size_t)hc.C * 32, (size_t)nmax * 32, (size_t)wmax_next * 32,
+  const size_t v[kWsRegions] = {half, (size_t)hc.C * 32, ((size_t)nmax + wmax) * 32, (size_t)wmax_next * 32,
                                 (size_t)wmax_next * 32, (size_t)wmax_next * 32, (size_t)wmax_next * 32,
                                 (size_t)wmax * 32, (size_t)kMaxPartials * 4 * 32, dig, sizeof(DevState),
                                 proof_len_c(hc, c_proof), eq_half_words(hc.c, smax) * 4, (size_t)nmax * 2 * 32,
@@ -932,6 +932,11 @@ int workspace_layout(const sisu_circuit* cc, Workspace* ws, uint8_t* dev, uint8_
   ws->T = (uint32_t*)ptrs[0];
   ws->E = (uint32_t*)ptrs[1];
   ws->om = (uint32_t*)ptrs[2];
+  {
+    uint32_t nmax = 1;
+    for (uint32_t i = 0; i < hc.d; ++i) nmax = std::max(nmax, cc->L[i].ntot);
+    ws->omo = ws->om + 8 * (size_t)nmax;
+  }
   ws->At = (uint32_t*)ptrs[3];
   ws->H1 = (uint32_t*)ptrs[4];
   ws->H2 = (uint32_t*)ptrs[5];
@@ -1078,7 +1083,9 @@ static int enqueue_prove(const sisu_circuit* cc, sisu_eval* ev, const sisu_trans
     const uint32_t s = hc.s[i + 1], Wn = hc.W[i + 1], sn = hc.s[i + 1];
     {
       ProfScope ps(kProfLayerInit, (double)hc.C * c + (double)L.ntot * (i == 0 ? hc.s[0] : 2.0 * hc.s[i] + 2), st);
-      CK(launch_layer_init(w.S, i, c, hc.s[i], L, w.E, w.om, w.eqh, st), "layer init");
+      // gate weights in gate order too, for the first copy round (gates of one entry each)
+      CK(launch_layer_init(w.S, i, c, hc.s[i], L, w.E, w.om, w.eqh, st, 0, 0, L.offo ? nullptr : w.omo),
+         "layer init");
     }
     // copy phase: c rounds, each followed by the fold of its challenge
     const uint32_t* A = ev->V[i + 1];
@@ -1094,7 +1101,7 @@ static int enqueue_prove(const sisu_circuit* cc, sisu_eval* ev, const sisu_trans
         // the first round reads the layer's own values (gates of one entry each)
         const uint32_t* Vg = k == 0 && !L.offo ? ev->V[i] : nullptr;
         CK(launch_copy_round(tab, sn, h, w.E, w.om, L, w.partials, w.S, w.proof, off + 32 * 3 * (size_t)k, k, st,
-                             nullptr, Vg, hc.s[i]),
+                             nullptr, Vg, hc.s[i], w.omo),
            "copy round");
       }
       {

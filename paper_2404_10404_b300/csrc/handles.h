@@ -33,6 +33,7 @@ struct Workspace {
   void* dev = nullptr;  // owned allocation (null when placed in caller memory)
   uint32_t *T = nullptr, *E = nullptr, *om = nullptr, *At = nullptr, *H1 = nullptr, *H2 = nullptr,
            *Ay = nullptr, *Q = nullptr, *partials = nullptr, *dscratch = nullptr, *eqh = nullptr, *P = nullptr;
+  uint32_t* omo = nullptr;  // the gate weights in gate order (first copy rounds), after om
   // general circuits: the claim terms' copy and gate weights, their round
   // sums, the combined weights, every layer's challenges and alphas
   // (hstride values a layer), the block values, the term descriptors

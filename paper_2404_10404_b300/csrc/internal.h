@@ -124,9 +124,11 @@ size_t digest_scratch_words(size_t len_bytes);
 
 int launch_transcript_init(const InitParams& p, DevState* S, void* stream);
 // cq, q: the copies are rank q's of 2^cq (copies j 2^cq + q, j < 2^c); 0, 0
-// for all copies
+// for all copies.  omega_o (not null; layers whose gates have one entry
+// each): the gate weights in gate order as well, 2^s_i values.
 int launch_layer_init(DevState* S, uint32_t layer, uint32_t c, uint32_t s_i, const DevLayer& L, uint32_t* E,
-                      uint32_t* omega_s, uint32_t* eqh, void* stream, uint32_t cq = 0, uint32_t q = 0);
+                      uint32_t* omega_s, uint32_t* eqh, void* stream, uint32_t cq = 0, uint32_t q = 0,
+                      uint32_t* omega_o = nullptr);
 // words of the eq half-table scratch of launch_layer_init (copy bits c,
 // largest layer log-width smax)
 size_t eq_half_words(uint32_t c, uint32_t smax);
@@ -137,11 +139,12 @@ int set_copy_tune(uint32_t sn, uint32_t log_pairs, uint32_t bd, uint32_t form, u
 // copy-sharded proof) instead of the message and transcript.  Vg (not
 // null, first round of a layer whose gates have one entry each, T the
 // layer's unfolded input values): the layer's own values, rows of 2^sv,
-// which the round reads in place of recomputing its t = 0, 1 products.
+// which the round reads in place of recomputing its t = 0, 1 products,
+// with omega_o the gate weights in gate order (launch_layer_init).
 int launch_copy_round(const uint32_t* T, uint32_t sn, uint32_t h, const uint32_t* E, const uint32_t* omega_s,
                       const DevLayer& L, uint32_t* partials, DevState* S, uint8_t* proof, size_t off,
                       uint32_t k, void* stream, uint32_t* sums_out = nullptr, const uint32_t* Vg = nullptr,
-                      uint32_t sv = 0);
+                      uint32_t sv = 0, const uint32_t* omega_o = nullptr);
 int launch_copy_fold(const uint32_t* src, uint32_t* dst, uint32_t sn, uint32_t h, uint32_t* E,
                      DevState* S, uint32_t k, void* stream);
 // copy-sharded proofs: the round message from the gathered sums of every
