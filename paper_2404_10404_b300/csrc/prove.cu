@@ -884,6 +884,22 @@ static int launch_copy_round_bd(int form, uint32_t min_items, const uint32_t* T,
                                         nullptr, 0, nullptr);
 }
 
+// The first round's per-warp form at 512 threads: its products need fewer
+// registers (128, no spills), so one CTA of 16 warps fills an SM where the
+// general form's 168 registers allow 12 (slot first round 1.296 -> 1.256
+// ms).  Taken unless the launch-shape table sets the class.
+
+static int launch_copy_round_first512(const uint32_t* T, uint32_t sn, uint32_t h, const uint32_t* E,
+                                      const uint32_t* omega_s, const DevLayer& L, uint32_t* partials, DevState* S,
+                                      uint8_t* proof, size_t off, uint32_t k, cudaStream_t st, uint32_t* sums_out,
+                                      const uint32_t* Vg, uint32_t sv, const uint32_t* omo, bool* launched) {
+  const CopySplit sp = copy_split(h, L.nmul, L.ntot, std::min<uint32_t>(kSMs, kMaxPartials), 512);
+  *launched = sp.m == 0;
+  if (!*launched) return 0;
+  return launch_copy_round_v<512, true>(true, sp, T, sn, h, E, omega_s, L, partials, S, proof, off, k, st, sums_out,
+                                        Vg, sv, omo);
+}
+
 int launch_copy_round(const uint32_t* T, uint32_t sn, uint32_t h, const uint32_t* E, const uint32_t* omega_s,
                       const DevLayer& L, uint32_t* partials, DevState* S, uint8_t* proof, size_t off, uint32_t k,
                       void* stream, uint32_t* sums_out, const uint32_t* Vg, uint32_t sv, const uint32_t* omo) {
@@ -892,6 +908,12 @@ int launch_copy_round(const uint32_t* T, uint32_t sn, uint32_t h, const uint32_t
   while ((2u << lh) <= h) ++lh;
   CopyTune t = {384, 0, 0};
   if (sn < kTuneLog && lh < kTuneLog && g_copy_tune[sn][lh].bd) t = g_copy_tune[sn][lh];
+  if (Vg && omo && t.bd == 384 && t.form == 0 && t.min_items == 0) {
+    bool launched = false;
+    const int rc = launch_copy_round_first512(T, sn, h, E, omega_s, L, partials, S, proof, off, k, st, sums_out, Vg,
+                                              sv, omo, &launched);
+    if (rc || launched) return rc;
+  }
   if (t.bd == 128)
     return launch_copy_round_bd<128>(t.form, t.min_items, T, sn, h, E, omega_s, L, partials, S, proof, off, k, st,
                                      sums_out, Vg, sv, omo);
