@@ -746,10 +746,11 @@ def batched_core(S, dev, stream, specs, pins, budget_gb: float):
                         "copy_round": {"classes": len(classes), "from_cache": sum(c in cached for c in classes),
                                        "seconds": round(t_tune, 1),
                                        "non_default": sum(table[c] != (384, 0, 0) for c in classes),
-                                       "first_round_us_default_vs_tuned": gains,
+                                       "timed_round_us_default_vs_tuned": gains,
                                        "how": "per (log2 W, log2 pairs) class: 27 launch shapes (128/256/384 "
-                                              "threads x 3 forms x 3 CTA granularities) timed on the first copy "
-                                              "round of a one-layer circuit of that shape, best of 3"}},
+                                              "threads x 3 forms x 3 CTA granularities) timed on the second "
+                                              "copy round of a one-layer circuit with that many pairs in it, "
+                                              "best of 3"}},
            "parity": "every batched proof equals the single-instance proof"}
     return res, singles
 

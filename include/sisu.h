@@ -477,11 +477,13 @@ int sisu_tune_copy_round(uint32_t log_width, uint32_t log_pairs, uint32_t cta_th
  * product by one level of Karatsuba, kind 10 = kinds 7 and 9 on the same
  * arbitrary 256-bit operands (all-ones words included), kind 11 =
  * Montgomery products as a Karatsuba product and a separate reduction,
- * kind 12 = kinds 2 and 11 on the same operands.  Reports the elapsed
- * milliseconds and the number of operations (multiply-adds, or field
- * products for kinds 2, 3, 5, 7, 8, 9 and 11); for kinds 6, 10 and 12,
- * *ops is minus the number of threads whose two results disagreed (0 when
- * they all agree). */
+ * kind 12 = kinds 2 and 11 on the same operands, kind 13 = Montgomery
+ * products two a call with their steps interleaved, kind 14 = kind 13
+ * against kind 2 on the same operands.  Reports the elapsed milliseconds
+ * and the number of operations (multiply-adds, or field products for kinds
+ * 2, 3, 5, 7, 8, 9, 11 and 13); for kinds 6, 10, 12 and 14, *ops is minus
+ * the number of threads whose two results disagreed (0 when they all
+ * agree). */
 int sisu_microbench(int kind, uint32_t blocks, uint32_t threads, uint32_t iters, void* stream,
                     double* ms, double* ops);
 

@@ -201,6 +201,44 @@ __global__ void k_mb_frmul_wide(uint32_t iters, uint32_t* sink) {
   sink[blockIdx.x * blockDim.x + threadIdx.x] = acc;
 }
 
+// two independent products a call, four a step (kind 13)
+__global__ void k_mb_frmul2(uint32_t iters, uint32_t* sink) {
+  Fr x = fr_one(), y = fr_r2(), z = fr_one(), u = fr_r2(), w = fr_one();
+  x.v[0] ^= threadIdx.x;
+  u.v[1] ^= threadIdx.x;
+  for (uint32_t it = 0; it < iters; ++it) {
+    Fr2 p = fr_mul2(x, y, u, y);
+    x = p.a;
+    u = p.b;
+    p = fr_mul2(z, x, w, u);
+    z = p.a;
+    w = p.b;
+  }
+  uint32_t acc = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) acc ^= x.v[i] ^ z.v[i] ^ u.v[i] ^ w.v[i];
+  sink[blockIdx.x * blockDim.x + threadIdx.x] = acc;
+}
+
+// the paired product against two single ones (kind 14)
+__global__ void k_mb_frmul2_check(uint32_t iters, uint32_t* sink) {
+  Fr x = fr_one(), y = fr_r2(), u = fr_r2(), v = fr_one();
+  x.v[0] ^= threadIdx.x + blockIdx.x * 977u;
+  u.v[3] ^= threadIdx.x * 31u + blockIdx.x;
+  uint32_t bad = 0;
+  for (uint32_t it = 0; it < iters; ++it) {
+    const Fr2 p = fr_mul2(x, y, u, v);
+    const Fr a = fr_mul(x, y), b = fr_mul(u, v);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) bad |= (p.a.v[i] ^ a.v[i]) | (p.b.v[i] ^ b.v[i]);
+    x = fr_add(p.a, v);
+    y = fr_add(y, p.b);
+    u = fr_sub(u, p.a);
+    v = fr_add(p.b, x);
+  }
+  sink[blockIdx.x * blockDim.x + threadIdx.x] = bad;
+}
+
 // check of the two product formulations against each other (kind 6)
 __global__ void k_mb_frmul_check(uint32_t iters, uint32_t* sink) {
   Fr x = fr_one(), y = fr_r2(), u = fr_one(), v = fr_r2();
@@ -371,6 +409,8 @@ int run_microbench(int kind, uint32_t blocks, uint32_t threads, uint32_t iters, 
     else if (kind == 10) k_mb_frmac_check<<<blocks, threads, 0, st>>>(iters, sink);
     else if (kind == 11) k_mb_frmul_kara<<<blocks, threads, 0, st>>>(iters, sink);
     else if (kind == 12) k_mb_frmul_kara_check<<<blocks, threads, 0, st>>>(iters, sink);
+    else if (kind == 13) k_mb_frmul2<<<blocks, threads, 0, st>>>(iters, sink);
+    else if (kind == 14) k_mb_frmul2_check<<<blocks, threads, 0, st>>>(iters, sink);
     else k_mb_frmul_check<<<blocks, threads, 0, st>>>(iters, sink);
     launches_add(1);
   };
@@ -382,7 +422,7 @@ int run_microbench(int kind, uint32_t blocks, uint32_t threads, uint32_t iters, 
   float t = 0;
   cudaEventElapsedTime(&t, a, b);
   *ms = t;
-  if ((kind == 6 || kind == 10 || kind == 12) && e == cudaSuccess) {
+  if ((kind == 6 || kind == 10 || kind == 12 || kind == 14) && e == cudaSuccess) {
     std::vector<uint32_t> h((size_t)blocks * threads);
     e = cudaMemcpy(h.data(), sink, h.size() * 4, cudaMemcpyDeviceToHost);
     size_t bad = 0;
@@ -393,8 +433,10 @@ int run_microbench(int kind, uint32_t blocks, uint32_t threads, uint32_t iters, 
     cudaFree(sink);
     return (int)e;
   }
-  double per = (kind == 2 || kind == 3 || kind == 5 || kind == 7 || kind == 8 || kind == 9 || kind == 11) ? 2.0 : kind == 6 ? 2.0
-                                                                                                             : 64.0;
+  double per = (kind == 2 || kind == 3 || kind == 5 || kind == 7 || kind == 8 || kind == 9 || kind == 11) ? 2.0
+               : kind == 6                                                                               ? 2.0
+               : kind == 13                                                                              ? 4.0
+                                                                                                         : 64.0;
   *ops = (double)blocks * threads * iters * per;
   cudaEventDestroy(a);
   cudaEventDestroy(b);

@@ -209,6 +209,53 @@ __device__ __forceinline__ Fr fr_dbl(const Fr& a) { return fr_add(a, a); }
         "r"(a.v[6]), "r"(a.v[7]), "r"(BI));                                                  \
   t0 = t1; t1 = t2; t2 = t3; t3 = t4; t4 = t5; t5 = t6; t6 = t7; t7 = t8;
 
+// the same step on named operand and accumulator words
+#define SISU_CIOS_STEP_ON(A, BI, t0, t1, t2, t3, t4, t5, t6, t7, t8)                     \
+  t8 = 0;                                                                                    \
+  asm("{\n\t"                                                                                \
+      ".reg .u32 m;\n\t"                                                                     \
+      "mad.lo.cc.u32  %0, %9,  %17, %0;\n\t"                                                 \
+      "madc.lo.cc.u32 %1, %10, %17, %1;\n\t"                                                 \
+      "madc.lo.cc.u32 %2, %11, %17, %2;\n\t"                                                 \
+      "madc.lo.cc.u32 %3, %12, %17, %3;\n\t"                                                 \
+      "madc.lo.cc.u32 %4, %13, %17, %4;\n\t"                                                 \
+      "madc.lo.cc.u32 %5, %14, %17, %5;\n\t"                                                 \
+      "madc.lo.cc.u32 %6, %15, %17, %6;\n\t"                                                 \
+      "madc.lo.cc.u32 %7, %16, %17, %7;\n\t"                                                 \
+      "addc.u32       %8, %8, 0;\n\t"                                                        \
+      "mad.hi.cc.u32  %1, %9,  %17, %1;\n\t"                                                 \
+      "madc.hi.cc.u32 %2, %10, %17, %2;\n\t"                                                 \
+      "madc.hi.cc.u32 %3, %11, %17, %3;\n\t"                                                 \
+      "madc.hi.cc.u32 %4, %12, %17, %4;\n\t"                                                 \
+      "madc.hi.cc.u32 %5, %13, %17, %5;\n\t"                                                 \
+      "madc.hi.cc.u32 %6, %14, %17, %6;\n\t"                                                 \
+      "madc.hi.cc.u32 %7, %15, %17, %7;\n\t"                                                 \
+      "madc.hi.u32    %8, %16, %17, %8;\n\t"                                                 \
+      "mul.lo.u32 m, %0, 0xefffffff;\n\t"                                                    \
+      "mad.lo.cc.u32  %0, m, 0xf0000001, %0;\n\t"                                            \
+      "madc.lo.cc.u32 %1, m, 0x43e1f593, %1;\n\t"                                            \
+      "madc.lo.cc.u32 %2, m, 0x79b97091, %2;\n\t"                                            \
+      "madc.lo.cc.u32 %3, m, 0x2833e848, %3;\n\t"                                            \
+      "madc.lo.cc.u32 %4, m, 0x8181585d, %4;\n\t"                                            \
+      "madc.lo.cc.u32 %5, m, 0xb85045b6, %5;\n\t"                                            \
+      "madc.lo.cc.u32 %6, m, 0xe131a029, %6;\n\t"                                            \
+      "madc.lo.cc.u32 %7, m, 0x30644e72, %7;\n\t"                                            \
+      "addc.u32       %8, %8, 0;\n\t"                                                        \
+      "mad.hi.cc.u32  %1, m, 0xf0000001, %1;\n\t"                                            \
+      "madc.hi.cc.u32 %2, m, 0x43e1f593, %2;\n\t"                                            \
+      "madc.hi.cc.u32 %3, m, 0x79b97091, %3;\n\t"                                            \
+      "madc.hi.cc.u32 %4, m, 0x2833e848, %4;\n\t"                                            \
+      "madc.hi.cc.u32 %5, m, 0x8181585d, %5;\n\t"                                            \
+      "madc.hi.cc.u32 %6, m, 0xb85045b6, %6;\n\t"                                            \
+      "madc.hi.cc.u32 %7, m, 0xe131a029, %7;\n\t"                                            \
+      "madc.hi.u32    %8, m, 0x30644e72, %8;\n\t"                                            \
+      "}"                                                                                    \
+      : "+r"(t0), "+r"(t1), "+r"(t2), "+r"(t3), "+r"(t4), "+r"(t5), "+r"(t6), "+r"(t7),      \
+        "+r"(t8)                                                                             \
+      : "r"(A.v[0]), "r"(A.v[1]), "r"(A.v[2]), "r"(A.v[3]), "r"(A.v[4]), "r"(A.v[5]),        \
+        "r"(A.v[6]), "r"(A.v[7]), "r"(BI));                                                  \
+  t0 = t1; t1 = t2; t2 = t3; t3 = t4; t4 = t5; t5 = t6; t6 = t7; t7 = t8;
+
 __device__ __forceinline__ Fr fr_mul_inl(const Fr& a, const Fr& b) {
   uint32_t t0 = 0, t1 = 0, t2 = 0, t3 = 0, t4 = 0, t5 = 0, t6 = 0, t7 = 0, t8;
   SISU_CIOS_STEP(b.v[0])
@@ -291,6 +338,53 @@ static __device__ __noinline__ Fr fr_mul_wide_call(Fr a, Fr b) { return fr_mul_w
 static __device__ __noinline__ Fr fr_mul_call(Fr a, Fr b) { return fr_mul_inl(a, b); }
 
 __device__ __forceinline__ Fr fr_mul(const Fr& a, const Fr& b) { return fr_mul_call(a, b); }
+
+// Two independent Montgomery products in one call, their CIOS steps
+// interleaved (each step's carry chain stays inside its own asm block), so
+// that the scheduler can issue one product's chain while the other waits:
+// more instruction-level parallelism for kernels with few warps an SM.
+struct Fr2 {
+  Fr a, b;
+};
+
+__device__ __forceinline__ Fr2 fr_mul2_inl(const Fr& a, const Fr& b, const Fr& c, const Fr& d) {
+  Fr2 o;
+  {
+    uint32_t t0 = 0, t1 = 0, t2 = 0, t3 = 0, t4 = 0, t5 = 0, t6 = 0, t7 = 0, t8;
+    uint32_t u0 = 0, u1 = 0, u2 = 0, u3 = 0, u4 = 0, u5 = 0, u6 = 0, u7 = 0, u8;
+#define SISU_CIOS_PAIR(I)                                                        \
+  {                                                                              \
+    SISU_CIOS_STEP(b.v[I])                                                       \
+  }                                                                              \
+  {                                                                              \
+    uint32_t& q0 = u0; uint32_t& q1 = u1; uint32_t& q2 = u2; uint32_t& q3 = u3;  \
+    uint32_t& q4 = u4; uint32_t& q5 = u5; uint32_t& q6 = u6; uint32_t& q7 = u7;  \
+    uint32_t& q8 = u8;                                                           \
+    SISU_CIOS_STEP_ON(c, d.v[I], q0, q1, q2, q3, q4, q5, q6, q7, q8)             \
+  }
+    SISU_CIOS_PAIR(0)
+    SISU_CIOS_PAIR(1)
+    SISU_CIOS_PAIR(2)
+    SISU_CIOS_PAIR(3)
+    SISU_CIOS_PAIR(4)
+    SISU_CIOS_PAIR(5)
+    SISU_CIOS_PAIR(6)
+    SISU_CIOS_PAIR(7)
+#undef SISU_CIOS_PAIR
+    o.a.v[0] = t0; o.a.v[1] = t1; o.a.v[2] = t2; o.a.v[3] = t3;
+    o.a.v[4] = t4; o.a.v[5] = t5; o.a.v[6] = t6; o.a.v[7] = t7;
+    o.b.v[0] = u0; o.b.v[1] = u1; o.b.v[2] = u2; o.b.v[3] = u3;
+    o.b.v[4] = u4; o.b.v[5] = u5; o.b.v[6] = u6; o.b.v[7] = u7;
+  }
+  return o;
+}
+
+static __device__ __noinline__ Fr2 fr_mul2_call(Fr a, Fr b, Fr c, Fr d) { return fr_mul2_inl(a, b, c, d); }
+
+// a b 2^-256 and c d 2^-256 (mod r), inputs and outputs in [0, 2r)
+__device__ __forceinline__ Fr2 fr_mul2(const Fr& a, const Fr& b, const Fr& c, const Fr& d) {
+  return fr_mul2_call(a, b, c, d);
+}
 
 // Montgomery square a^2 2^-256 mod p, input and output in [0, 2p): the
 // 512-bit square from its 28 off-diagonal products (doubled) and 8
