@@ -479,11 +479,13 @@ int sisu_tune_copy_round(uint32_t log_width, uint32_t log_pairs, uint32_t cta_th
  * Montgomery products as a Karatsuba product and a separate reduction,
  * kind 12 = kinds 2 and 11 on the same operands, kind 13 = Montgomery
  * products two a call with their steps interleaved, kind 14 = kind 13
- * against kind 2 on the same operands.  Reports the elapsed milliseconds
- * and the number of operations (multiply-adds, or field products for kinds
- * 2, 3, 5, 7, 8, 9, 11 and 13); for kinds 6, 10, 12 and 14, *ops is minus
- * the number of threads whose two results disagreed (0 when they all
- * agree). */
+ * against kind 2 on the same operands, kind 15 = Montgomery products with
+ * the reduction's products by the low limb of r as multiply-adds (kind 2
+ * forms them by shifts and subtractions), kind 16 = kind 15 against kind 2
+ * on the same operands.  Reports the elapsed milliseconds and the number of
+ * operations (multiply-adds, or field products for kinds 2, 3, 5, 7, 8, 9,
+ * 11, 13 and 15); for kinds 6, 10, 12, 14 and 16, *ops is minus the number
+ * of threads whose two results disagreed (0 when they all agree). */
 int sisu_microbench(int kind, uint32_t blocks, uint32_t threads, uint32_t iters, void* stream,
                     double* ms, double* ops);
 

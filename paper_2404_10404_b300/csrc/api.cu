@@ -1486,7 +1486,7 @@ extern "C" int sisu_statement_digest(const uint8_t* data, size_t len, uint8_t* o
 
 extern "C" int sisu_microbench(int kind, uint32_t blocks, uint32_t threads, uint32_t iters, void* stream, double* ms,
                                double* ops) {
-  if (kind < 0 || kind > 14 || !blocks || !threads || threads > 1024 || !ms || !ops)
+  if (kind < 0 || kind > 16 || !blocks || !threads || threads > 1024 || !ms || !ops)
     return fail(SISU_ERR_INVALID_ARG, "bad microbenchmark arguments");
   int rc = run_microbench(kind, blocks, threads, iters, stream, ms, ops);
   if (rc) return cuda_fail((cudaError_t)rc, "microbenchmark");

@@ -239,6 +239,39 @@ __global__ void k_mb_frmul2_check(uint32_t iters, uint32_t* sink) {
   sink[blockIdx.x * blockDim.x + threadIdx.x] = bad;
 }
 
+// products with r_0 by multiply-adds, the earlier form (kind 15)
+__global__ void k_mb_frmul_r0(uint32_t iters, uint32_t* sink) {
+  Fr x = fr_one(), y = fr_r2(), z = fr_one();
+  x.v[0] ^= threadIdx.x;
+  for (uint32_t it = 0; it < iters; ++it) {
+    x = fr_mul_madr0_call(x, y);
+    z = fr_mul_madr0_call(z, x);
+  }
+  uint32_t acc = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) acc ^= x.v[i] ^ z.v[i];
+  sink[blockIdx.x * blockDim.x + threadIdx.x] = acc;
+}
+
+// kind 15 against kind 2 on the same operands (kind 16)
+__global__ void k_mb_frmul_r0_check(uint32_t iters, uint32_t* sink) {
+  Fr x = fr_one(), y = fr_r2(), u = fr_r2(), v = fr_one();
+  x.v[0] ^= threadIdx.x + blockIdx.x * 977u;
+  u.v[3] ^= threadIdx.x * 31u + blockIdx.x;
+  uint32_t bad = 0;
+  for (uint32_t it = 0; it < iters; ++it) {
+    const Fr p = fr_mul_madr0_call(x, y), q = fr_mul_madr0_call(u, v);
+    const Fr a = fr_mul(x, y), b = fr_mul(u, v);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) bad |= (p.v[i] ^ a.v[i]) | (q.v[i] ^ b.v[i]);
+    x = fr_add(p, v);
+    y = fr_add(y, q);
+    u = fr_sub(u, p);
+    v = fr_add(q, x);
+  }
+  sink[blockIdx.x * blockDim.x + threadIdx.x] = bad;
+}
+
 // check of the two product formulations against each other (kind 6)
 __global__ void k_mb_frmul_check(uint32_t iters, uint32_t* sink) {
   Fr x = fr_one(), y = fr_r2(), u = fr_one(), v = fr_r2();
@@ -411,6 +444,8 @@ int run_microbench(int kind, uint32_t blocks, uint32_t threads, uint32_t iters, 
     else if (kind == 12) k_mb_frmul_kara_check<<<blocks, threads, 0, st>>>(iters, sink);
     else if (kind == 13) k_mb_frmul2<<<blocks, threads, 0, st>>>(iters, sink);
     else if (kind == 14) k_mb_frmul2_check<<<blocks, threads, 0, st>>>(iters, sink);
+    else if (kind == 15) k_mb_frmul_r0<<<blocks, threads, 0, st>>>(iters, sink);
+    else if (kind == 16) k_mb_frmul_r0_check<<<blocks, threads, 0, st>>>(iters, sink);
     else k_mb_frmul_check<<<blocks, threads, 0, st>>>(iters, sink);
     launches_add(1);
   };
@@ -422,7 +457,7 @@ int run_microbench(int kind, uint32_t blocks, uint32_t threads, uint32_t iters, 
   float t = 0;
   cudaEventElapsedTime(&t, a, b);
   *ms = t;
-  if ((kind == 6 || kind == 10 || kind == 12 || kind == 14) && e == cudaSuccess) {
+  if ((kind == 6 || kind == 10 || kind == 12 || kind == 14 || kind == 16) && e == cudaSuccess) {
     std::vector<uint32_t> h((size_t)blocks * threads);
     e = cudaMemcpy(h.data(), sink, h.size() * 4, cudaMemcpyDeviceToHost);
     size_t bad = 0;
@@ -433,7 +468,9 @@ int run_microbench(int kind, uint32_t blocks, uint32_t threads, uint32_t iters, 
     cudaFree(sink);
     return (int)e;
   }
-  double per = (kind == 2 || kind == 3 || kind == 5 || kind == 7 || kind == 8 || kind == 9 || kind == 11) ? 2.0
+  double per = (kind == 2 || kind == 3 || kind == 5 || kind == 7 || kind == 8 || kind == 9 || kind == 11 ||
+                kind == 15)
+                   ? 2.0
                : kind == 6                                                                               ? 2.0
                : kind == 13                                                                              ? 4.0
                                                                                                          : 64.0;
