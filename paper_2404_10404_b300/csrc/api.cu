@@ -887,7 +887,8 @@ static void workspace_sizes(const sisu_circuit* cc, size_t sizes[kWsRegions], ui
   for (uint32_t i = 0; i < hc.d; ++i) smax = std::max(smax, hc.s[i]);
   const size_t hstride = hc.c + 2 * (size_t)sxmax + 2 * (size_t)nbmax;
   const bool g = hc.general;
-  const size_t v[kWsRegions] = {half, (size_t)hc.C * 32, ((size_t)nmax + wmax) * 32, (size_t)wmax_next * 32,
+  const size_t v[kWsRegions] = {half, (size_t)hc.C * 4 * 32, ((size_t)nmax + wmax) * 32,
+                                (size_t)wmax_next * 32,
                                 (size_t)wmax_next * 32, (size_t)wmax_next * 32, (size_t)wmax_next * 32,
                                 (size_t)wmax * 32, (size_t)kMaxPartials * 4 * 32, dig, sizeof(DevState),
                                 proof_len_c(hc, c_proof), eq_half_words(hc.c, smax) * 4, (size_t)nmax * 2 * 32,
@@ -931,6 +932,11 @@ int workspace_layout(const sisu_circuit* cc, Workspace* ws, uint8_t* dev, uint8_
   }
   ws->T = (uint32_t*)ptrs[0];
   ws->E = (uint32_t*)ptrs[1];
+  ws->Ub[0] = ws->E + 8 * (size_t)hc.C;
+  ws->Ub[1] = ws->Ub[0] + 8 * (size_t)hc.C;
+  ws->cb[0] = ws->Ub[1] + 8 * (size_t)hc.C;
+  ws->cb[1] = ws->cb[0] + 4 * (size_t)hc.C;
+
   ws->om = (uint32_t*)ptrs[2];
   {
     uint32_t nmax = 1;
@@ -943,6 +949,9 @@ int workspace_layout(const sisu_circuit* cc, Workspace* ws, uint8_t* dev, uint8_
   ws->Ay = (uint32_t*)ptrs[6];
   ws->Q = (uint32_t*)ptrs[7];
   ws->partials = (uint32_t*)ptrs[8];
+  // a round's grid sums use at most kMaxPartials / 2 blocks' four values; the
+  // upper half of the region holds the shares of the pairs' coefficients
+  ws->cpart = ws->partials + 8 * 2 * (size_t)kMaxPartials;
   ws->dscratch = (uint32_t*)ptrs[9];
   ws->S = (DevState*)ptrs[10];
   ws->proof = (uint8_t*)ptrs[11];
@@ -1040,6 +1049,10 @@ static int workspace_alloc(sisu_eval* ev) {
 
 static int enqueue_general_layer(const sisu_circuit* cc, sisu_eval* ev, uint32_t i, size_t& off, cudaStream_t st);
 
+// the copy phase of plain layers by the recurrence of its linear part
+// (launch_copy_c) rather than item by item (launch_copy_round)
+constexpr bool kCopyRecurrence = true;
+
 // Enqueue one whole proof on `st` (no host synchronisation).
 static int enqueue_prove(const sisu_circuit* cc, sisu_eval* ev, const sisu_transcript* tr, cudaStream_t st) {
   const HostCircuit& hc = cc->hc;
@@ -1093,16 +1106,30 @@ static int enqueue_prove(const sisu_circuit* cc, sisu_eval* ev, const sisu_trans
     // products and three weight products at t = 0, 1, 2; an add gate's two
     // weighted sums), f the share of mul entries
     const double per_pair = 2.0 * L.ntot + 4.0 * L.nmul;
+    // layers whose gates have one entry each: the copy phase by the
+    // recurrence of its linear part (the rows' gate sums from layer i's
+    // values, then the mul entries' t^2 terms a round)
+    const bool rec = kCopyRecurrence && !L.offo;
+    if (rec) {
+      ProfScope ps(kProfCopyRound, 2.0 * hc.C * L.ntot / 2, st);
+      CK(launch_rowdot(ev->V[i], hc.s[i], w.omo, hc.C, w.Ub[0], st), "row sums");
+    }
     for (uint32_t k = 0; k < c; ++k) {
       const uint32_t* tab = k == 0 ? ev->V[i + 1] : w.T;
       const uint32_t h = hc.C >> (k + 1);
       {
         ProfScope ps(kProfCopyRound, per_pair * h, st);
-        // the first round reads the layer's own values (gates of one entry each)
-        const uint32_t* Vg = k == 0 && !L.offo ? ev->V[i] : nullptr;
-        CK(launch_copy_round(tab, sn, h, w.E, w.om, L, w.partials, w.S, w.proof, off + 32 * 3 * (size_t)k, k, st,
-                             nullptr, Vg, hc.s[i], w.omo),
-           "copy round");
+        if (rec) {
+          CK(launch_copy_c(tab, sn, h, w.E, w.om, L, w.Ub[(k + 1) & 1], w.cb[(k + 1) & 1], w.Ub[k & 1],
+                           w.cb[k & 1], w.cpart, w.partials, w.S, w.proof, off + 32 * 3 * (size_t)k, k, st),
+             "copy round");
+        } else {
+          // the first round reads the layer's own values (gates of one entry each)
+          const uint32_t* Vg = k == 0 && !L.offo ? ev->V[i] : nullptr;
+          CK(launch_copy_round(tab, sn, h, w.E, w.om, L, w.partials, w.S, w.proof, off + 32 * 3 * (size_t)k, k,
+                               st, nullptr, Vg, hc.s[i], w.omo),
+             "copy round");
+        }
       }
       {
         ProfScope ps(kProfCopyFold, (double)h * Wn + h, st);

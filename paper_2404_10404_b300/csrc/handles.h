@@ -34,6 +34,11 @@ struct Workspace {
   uint32_t *T = nullptr, *E = nullptr, *om = nullptr, *At = nullptr, *H1 = nullptr, *H2 = nullptr,
            *Ay = nullptr, *Q = nullptr, *partials = nullptr, *dscratch = nullptr, *eqh = nullptr, *P = nullptr;
   uint32_t* omo = nullptr;  // the gate weights in gate order (first copy rounds), after om
+  // the copy phase by its linear recurrence: the rows' gate sums of two
+  // rounds (C values each), the pairs' t^2 coefficients of two rounds (C/2
+  // each), after E in its region, and the shares of a pair's coefficient
+  // (rounds with few pairs), in the upper half of the partial sums
+  uint32_t *Ub[2] = {nullptr, nullptr}, *cb[2] = {nullptr, nullptr}, *cpart = nullptr;
   // general circuits: the claim terms' copy and gate weights, their round
   // sums, the combined weights, every layer's challenges and alphas
   // (hstride values a layer), the block values, the term descriptors

@@ -145,6 +145,15 @@ int launch_copy_round(const uint32_t* T, uint32_t sn, uint32_t h, const uint32_t
                       const DevLayer& L, uint32_t* partials, DevState* S, uint8_t* proof, size_t off,
                       uint32_t k, void* stream, uint32_t* sums_out = nullptr, const uint32_t* Vg = nullptr,
                       uint32_t sv = 0, const uint32_t* omega_o = nullptr);
+// The copy phase by its linear recurrence: the rows' gate sums U(b) of
+// layer i's values (rows of 2^sv, gate weights omo in gate order), and one
+// round over the mul entries (U and c of the previous round in, of this
+// round out; cpart: kMaxPartials / 2 values of scratch).
+int launch_rowdot(const uint32_t* V, uint32_t sv, const uint32_t* omo, uint32_t C, uint32_t* U, void* stream);
+int launch_copy_c(const uint32_t* T, uint32_t sn, uint32_t h, const uint32_t* E, const uint32_t* omega_s,
+                  const DevLayer& L, const uint32_t* Uprev, const uint32_t* cprev, uint32_t* Ucur, uint32_t* ccur,
+                  uint32_t* cpart, uint32_t* partials, DevState* S, uint8_t* proof, size_t off, uint32_t k,
+                  void* stream);
 int launch_copy_fold(const uint32_t* src, uint32_t* dst, uint32_t sn, uint32_t h, uint32_t* E,
                      DevState* S, uint32_t k, void* stream);
 // copy-sharded proofs: the round message from the gathered sums of every

@@ -933,6 +933,322 @@ int set_copy_tune(uint32_t sn, uint32_t log_pairs, uint32_t bd, uint32_t form, u
 }
 
 // ---------------------------------------------------------------------------
+// The copy phase by the recurrence of its linear part.
+//
+// Write U_k(j) = sum_g w(g) op_g(T_k(j, in1 g), T_k(j, in2 g)) for the gate
+// sum of row j of round k's table (n_k = 2 h_k rows).  A pair's sums are
+// S_j(0) = U_k(j) and S_j(1) = U_k(j + h_k), and the fold by r_k gives row j
+// of the next table, whose gate sum is
+//   U_{k+1}(j) = (1 - r_k) U_k(j) + r_k U_k(j + h_k) + (r_k^2 - r_k) c_j,
+// c_j = sum over the mul entries of w (x1 - x0)(y1 - y0), the pair's t^2
+// coefficient: an add gate's value folds linearly, and the product x' y' of
+// two folded inputs is (1 - r) x0 y0 + r x1 y1 + (r^2 - r)(x1 - x0)(y1 - y0).
+// So the first round's U_0(b) are the dot products of layer i's rows with
+// the gate weights (k_rowdot), every round's items are the mul entries' t^2
+// terms alone (one Montgomery and one full product a mul item, nothing for
+// an add item), and U_{k+1} follows from U_k and the c_j of round k with
+// two products a row.  The messages and the proof bytes are those of the
+// item-by-item form; only the work changes.  U and c are kept as the lazy
+// sums' reductions leave them (Montgomery form times 2^-32), which the copy
+// weights' factor 2^32 cancels in the message.
+
+constexpr uint32_t kRowDotThreads = 256;
+
+// U(b) = sum_g w(g) V(b, g) for the C rows of layer i's values (2^sv a row),
+// w in gate order.  A row goes to tpr = 2^lt consecutive threads (a power
+// of two up to a warp, chosen so that rows of 4096 still fill the GPU);
+// each sums every tpr-th element with inlined full products into two
+// accumulators (independent chains), coalesced, and the row's threads add
+// their sums by shuffles.
+__global__ void __launch_bounds__(kRowDotThreads) k_rowdot(const uint32_t* __restrict__ V, uint32_t sv,
+                                                           const uint32_t* __restrict__ omo, uint32_t C,
+                                                           uint32_t lt, uint32_t* __restrict__ U) {
+  pdl_wait();
+  const uint32_t W = 1u << sv, tpr = 1u << lt;
+  const uint32_t sub = threadIdx.x & (tpr - 1);
+  const size_t nthreads = (size_t)gridDim.x * kRowDotThreads;
+  const size_t first = (size_t)blockIdx.x * kRowDotThreads + threadIdx.x;
+  // every thread of a warp runs the same number of rows (for the shuffles)
+  const size_t rows_per_pass = nthreads >> lt;
+  const size_t passes = ((size_t)C + rows_per_pass - 1) / rows_per_pass;
+  for (size_t pass = 0; pass < passes; ++pass) {
+    const size_t b = pass * rows_per_pass + (first >> lt);
+    FrAcc a0 = fracc_zero(), a1 = fracc_zero();
+    if (b < C) {
+      const uint32_t* row = V + ((b << sv) << 3);
+      uint32_t g = sub;
+      for (; g + tpr < W; g += 2 * tpr) {
+        fracc_mac_kara_inl(a0, fr_load(omo, g), fr_load(row, g));
+        fracc_mac_kara_inl(a1, fr_load(omo, g + tpr), fr_load(row, g + tpr));
+      }
+      if (g < W) fracc_mac_kara_inl(a0, fr_load(omo, g), fr_load(row, g));
+    }
+    fracc_add(a0, a1);
+    Fr u = fr_redc288(a0);
+    for (uint32_t o = tpr >> 1; o > 0; o >>= 1) {
+      Fr v;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) v.v[i] = __shfl_down_sync(0xffffffffu, u.v[i], o);
+      u = fr_add(u, v);
+    }
+    if (b < C && sub == 0) fr_store(U, b, u);
+  }
+}
+
+int launch_rowdot(const uint32_t* V, uint32_t sv, const uint32_t* omo, uint32_t C, uint32_t* U, void* stream) {
+  // threads a row: 32 for rows of 4096 and more, fewer for short rows, so
+  // that C rows give enough threads (and each at least 8 elements)
+  uint32_t lt = 0;
+  while (lt < 5 && (sv > lt + 3) && ((size_t)C << lt) < (size_t)kSMs * 2048) ++lt;
+  const size_t threads = (size_t)C << lt;
+  const unsigned grid = (unsigned)std::max<size_t>(1, std::min<size_t>((threads + kRowDotThreads - 1) / kRowDotThreads,
+                                                                       (size_t)kSMs * 8));
+  return launch_pdl(k_rowdot, grid, kRowDotThreads, (cudaStream_t)stream, V, sv, omo, C, lt, U);
+}
+
+// The work of pair j after its c_j is known, by the four lanes t = 0..3 of
+// a group (mask: the group's lanes, which all call this): round k's gate
+// sums U_k(j), U_k(j + h), formed from the previous round's (k > 0; the
+// four products split over the lanes and stored to Ucur for the next
+// round) or as k_rowdot left them in Ucur; then lane t's message term
+// E_t(j) S_j(t), S_j(t) = U0 + t (U1 - U0) + (t^2 - t) c, added to its
+// running sum.  withU false: the c term alone (t = 2, 3), for a share of
+// c_j whose U terms come from the pair's first share.  rp, qp: r_{k-1} and
+// r_{k-1}^2 - r_{k-1} (Montgomery form).
+__device__ __forceinline__ void pair_group(uint32_t j, uint32_t h, uint32_t t, uint32_t mask, bool upd, bool withU,
+                                           const uint32_t* Uprev, const uint32_t* cprev, uint32_t* Ucur,
+                                           const uint32_t* E, const Fr& rp, const Fr& qp, const Fr& c, Fr& macc) {
+  const uint32_t src0 = (threadIdx.x & 31) & ~3u;  // the group's lane 0
+  Fr U0 = fr_zero(), U1 = fr_zero();
+  if (withU) {
+    Fr u;  // lanes 0, 2: U0, U1 once the shares of the update are in
+    if (upd) {
+      // lane t: rp (hi - lo) of row j + (t >> 1) h (t even), qp c of that row (t odd)
+      const size_t row = j + (size_t)(t >> 1) * h;
+      const Fr lo = fr_load(Uprev, row);
+      const Fr a = (t & 1) ? fr_mul(qp, fr_load(cprev, row)) : fr_mul(rp, fr_sub(fr_load(Uprev, row + 2 * (size_t)h), lo));
+      Fr o;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) o.v[i] = __shfl_xor_sync(mask, a.v[i], 1);
+      u = fr_add(fr_add(lo, a), o);
+      if ((t & 1) == 0) fr_store(Ucur, row, u);
+    } else {
+      u = fr_load(Ucur, j + (size_t)(t >> 1) * h);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      U0.v[i] = __shfl_sync(mask, u.v[i], src0);
+      U1.v[i] = __shfl_sync(mask, u.v[i], src0 + 2);
+    }
+  }
+  if (!withU && t < 2) return;
+  const Fr e0 = fr_load(E, j), e1 = fr_load(E, j + (size_t)h);
+  const Fr de = fr_sub(e1, e0);
+  Fr et = t == 0 ? e0 : t == 1 ? e1 : fr_add(e1, de);
+  if (t == 3) et = fr_add(et, de);
+  const Fr d = fr_sub(U1, U0);
+  const Fr c2 = fr_dbl(c);
+  Fr st;
+  if (t == 0) {
+    st = U0;
+  } else if (t == 1) {
+    st = U1;
+  } else if (t == 2) {
+    st = fr_add(fr_add(U1, d), c2);  // U0 + 2 d + 2 c
+  } else {
+    st = fr_add(fr_add(U1, fr_dbl(d)), fr_dbl(fr_add(c2, c)));  // U0 + 3 d + 6 c
+  }
+  macc = fr_add(macc, fr_mul(et, st));
+}
+
+// One round of the copy phase over its mul entries (pairs j < h of the
+// table T, 2^sn positions a row).  m = 0 (h at least the CTA count): CTA b
+// takes the whole pairs [b h / nc, (b + 1) h / nc), in chunks of at most
+// kCChunk pairs; its warps split a chunk's items evenly, stage each item's
+// gathers in shared memory (as the per-warp copy round does), and sum the
+// t^2 terms of every pair segment; a pair split between warps is combined
+// from their two boundary records.  Then one thread a pair forms U_k from
+// U_{k-1} (k > 0), stores c_j and adds the pair's message terms.  m > 0 (h
+// below the CTA count): CTA b takes a share `sub` of the mul entries of pair
+// j = b / m; it adds the c terms of its share and, for sub = 0, the U terms;
+// the last block sums the shares into c_j.  The grid's sums go to the
+// transcript as a copy round's do.
+constexpr uint32_t kCChunk = 128;
+
+template <int BD>
+__global__ void __launch_bounds__(BD) k_copy_c(const uint32_t* __restrict__ T, uint32_t sn, uint32_t h,
+                                               const uint32_t* __restrict__ E, const uint32_t* __restrict__ om,
+                                               const uint4* __restrict__ sg, uint32_t nmul, uint32_t m,
+                                               uint32_t per, const uint32_t* Uprev, const uint32_t* cprev,
+                                               uint32_t* Ucur, uint32_t* ccur, uint32_t* cpart, uint32_t* partials,
+                                               DevState* S, uint8_t* proof, size_t off, uint32_t k) {
+  pdl_wait();
+  constexpr int NW = BD / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == BD - 32) warm_transcript_code(k, h);
+  const bool upd = k > 0;
+  Fr rp = fr_zero(), qp = fr_zero();
+  if (upd) {
+    rp = S->rb[k - 1];
+    qp = fr_sub(fr_mul(rp, rp), rp);
+  }
+  Fr acc[4] = {fr_zero(), fr_zero(), fr_zero(), fr_zero()};
+  if (m == 0) {
+    __shared__ Fr cpair[kCChunk];
+    __shared__ Fr rec_val[NW][2];
+    __shared__ uint32_t rec_pair[NW][2];
+    extern __shared__ uint4 cc_stage[];  // kStageWords4 a warp
+    uint4* stg = cc_stage + warp * kStageWords4;
+    const uint32_t pb0 = (uint32_t)((uint64_t)blockIdx.x * h / gridDim.x);
+    const uint32_t pb1 = (uint32_t)((uint64_t)(blockIdx.x + 1) * h / gridDim.x);
+    for (uint32_t cb = pb0; cb < pb1; cb += kCChunk) {
+      const uint32_t np = min(pb1 - cb, kCChunk);
+      for (uint32_t p = threadIdx.x; p < np; p += BD) cpair[p] = fr_zero();
+      if (lane < 2) rec_pair[warp][lane] = 0xffffffffu;
+      __syncthreads();
+      const uint64_t ni = (uint64_t)np * nmul;
+      const uint64_t i0 = ni * warp / NW, i1 = ni * (warp + 1) / NW;
+      for (uint64_t seg = i0; seg < i1;) {
+        const uint32_t p = (uint32_t)(seg / nmul);
+        const uint64_t segend = min(i1, (uint64_t)(p + 1) * nmul);
+        const uint32_t g0 = (uint32_t)(seg - (uint64_t)p * nmul), g1 = (uint32_t)(segend - (uint64_t)p * nmul);
+        const uint32_t j = cb + p;
+        const uint32_t* lo = T + (((size_t)j << sn) << 3);
+        const uint32_t* hi = T + (((size_t)(j + h) << sn) << 3);
+        FrAcc ac = fracc_zero();
+        // two-stage pipeline as in the per-warp copy round
+        uint32_t q = g0 + lane;
+        int st = 0;
+        auto issue = [&](int stage, uint32_t qq) {
+          const uint4 gi = sg[qq];
+          stage_issue(stg, stage, lane, om + 8 * (size_t)qq, lo + 8 * (size_t)gi.x, hi + 8 * (size_t)gi.x,
+                      lo + 8 * (size_t)gi.y, hi + 8 * (size_t)gi.y);
+        };
+        if (q < g1) issue(0, q);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        for (; q < g1; q += 32, st ^= 1) {
+          if (q + 32 < g1) issue(st ^ 1, q + 32);
+          asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 1;" ::: "memory");
+          const Fr w = stage_read(stg, st, 0, lane);
+          const Fr x0 = stage_read(stg, st, 1, lane), x1 = stage_read(stg, st, 2, lane);
+          const Fr y0 = stage_read(stg, st, 3, lane), y1 = stage_read(stg, st, 4, lane);
+          fracc_mac(ac, fr_mul(w, fr_sub(x1, x0)), fr_sub(y1, y0));
+        }
+        const Fr cs = fr_warp_sum(fr_redc288(ac));
+        if (lane == 0) {
+          if (g0 == 0 && g1 == nmul) {
+            cpair[p] = cs;
+          } else {
+            const int slot = seg == i0 ? 0 : 1;  // only a warp's first and last segments can be partial
+            rec_pair[warp][slot] = p;
+            rec_val[warp][slot] = cs;
+          }
+        }
+        seg = segend;
+      }
+      __syncthreads();
+      for (uint32_t p = threadIdx.x; p < np; p += BD) {
+        Fr c = cpair[p];
+        for (int w2 = 0; w2 < NW; ++w2)
+#pragma unroll
+          for (int s2 = 0; s2 < 2; ++s2)
+            if (rec_pair[w2][s2] == p) c = fr_add(c, rec_val[w2][s2]);
+        fr_store(ccur, cb + p, c);
+      }
+      __syncthreads();  // the chunk's shared records are read before the next chunk's
+    }
+    // the message terms of the CTA's pairs, a group of four lanes a pair
+    // (their c_j from this block's stores above, visible after the barrier)
+    const uint32_t t = threadIdx.x & 3, mask = 0xfu << ((threadIdx.x & 31) & ~3u);
+    Fr macc = fr_zero();
+    for (uint32_t j = pb0 + (threadIdx.x >> 2); j < pb1; j += BD / 4)
+      pair_group(j, h, t, mask, upd, true, Uprev, cprev, Ucur, E, rp, qp, fr_load(ccur, j), macc);
+#pragma unroll
+    for (int tt = 0; tt < 4; ++tt) acc[tt] = t == (uint32_t)tt ? macc : fr_zero();
+    block_sum<BD, 4>(acc);  // thread 0
+  } else {
+    const uint32_t j = blockIdx.x / m, sub = blockIdx.x - j * m;
+    const uint32_t q0 = min(nmul, sub * per), q1 = min(nmul, q0 + per);
+    const uint32_t* lo = T + (((size_t)j << sn) << 3);
+    const uint32_t* hi = T + (((size_t)(j + h) << sn) << 3);
+    FrAcc ac = fracc_zero();
+    for (uint32_t q = q0 + threadIdx.x; q < q1; q += BD) {
+      const uint4 gi = sg[q];
+      const Fr w = fr_load(om, q);
+      const Fr x0 = fr_load(lo, gi.x), x1 = fr_load(hi, gi.x);
+      const Fr y0 = fr_load(lo, gi.y), y1 = fr_load(hi, gi.y);
+      fracc_mac(ac, fr_mul(w, fr_sub(x1, x0)), fr_sub(y1, y0));
+    }
+    Fr cs[1] = {fr_redc288(ac)};
+    block_sum<BD, 1>(cs);  // thread 0
+    __shared__ Fr cshare;
+    if (threadIdx.x == 0) {
+      fr_store_cg(cpart, blockIdx.x, cs[0]);
+      cshare = cs[0];
+    }
+    __syncthreads();
+    Fr macc = fr_zero();
+    if (threadIdx.x < 4)
+      pair_group(j, h, threadIdx.x, 0xfu, upd, sub == 0, Uprev, cprev, Ucur, E, rp, qp, cshare, macc);
+    // the four lanes' terms to thread 0 (grid_sum_last_block takes thread 0's)
+    __shared__ Fr mterm[4];
+    if (threadIdx.x < 4) mterm[threadIdx.x] = macc;
+    __syncthreads();
+    if (threadIdx.x == 0)
+#pragma unroll
+      for (int tt = 0; tt < 4; ++tt) acc[tt] = mterm[tt];
+  }
+  const bool last = grid_sum_last_block<BD, 4, true>(acc, partials, S);
+  if (!last) return;
+  if (m > 0) {  // c_j from the shares of every pair, for the next round's U
+    for (uint32_t jj = threadIdx.x; jj < h; jj += BD) {
+      Fr c = fr_zero();
+      for (uint32_t s2 = 0; s2 < m; ++s2) c = fr_add(c, fr_load_cg(cpart, (size_t)jj * m + s2));
+      fr_store(ccur, jj, c);
+    }
+  }
+  if (threadIdx.x < 32) round_finalize<4>(S, acc, proof, off, &S->rb[k]);
+}
+
+constexpr int kCThreads = 256;
+
+static int copy_c_per_sm() {
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    const size_t smem = (size_t)(kCThreads / 32) * kStageWords4 * sizeof(uint4);
+    if (cudaFuncSetAttribute(k_copy_c<kCThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_copy_c<kCThreads>, kCThreads, smem) != cudaSuccess ||
+        n < 1)
+      n = 1;
+    per_sm = n;
+  }
+  return per_sm;
+}
+
+int launch_copy_c(const uint32_t* T, uint32_t sn, uint32_t h, const uint32_t* E, const uint32_t* omega_s,
+                  const DevLayer& L, const uint32_t* Uprev, const uint32_t* cprev, uint32_t* Ucur, uint32_t* ccur,
+                  uint32_t* cpart, uint32_t* partials, DevState* S, uint8_t* proof, size_t off, uint32_t k,
+                  void* stream) {
+  const int per_sm = copy_c_per_sm();
+  if (per_sm == 0) return (int)cudaErrorInvalidValue;
+  const uint32_t nc = std::min<uint32_t>(kSMs * per_sm, kMaxPartials / 2);  // the shares use the upper half
+  const size_t smem = (size_t)(kCThreads / 32) * kStageWords4 * sizeof(uint4);
+  uint32_t m = 0, per = 0, grid = nc;
+  if (h < nc) {  // shares of a pair's mul entries, at least half a CTA's threads of items each
+    const uint32_t by_items = std::max<uint32_t>(1, (L.nmul + kCThreads / 2 - 1) / (kCThreads / 2));
+    m = std::max<uint32_t>(1, std::min<uint32_t>(nc / h, by_items));
+    per = (L.nmul + m - 1) / m;
+    grid = h * m;
+  }
+  return launch_pdl_smem(k_copy_c<kCThreads>, grid, kCThreads, m ? 0 : smem, (cudaStream_t)stream, T, sn, h, E,
+                         omega_s, L.sgate, L.nmul, m, per, Uprev, cprev, Ucur, ccur, cpart, partials, S, proof, off,
+                         k);
+}
+
+// ---------------------------------------------------------------------------
 // copy-sharded proofs (Sec. 3.2.1: the machine index is the low part of the
 // copy index, so every rank binds its own copy bits first and the round
 // polynomial of a copy round is the sum of the ranks' polynomials)
