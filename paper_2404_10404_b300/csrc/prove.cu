@@ -957,15 +957,20 @@ constexpr uint32_t kRowDotThreads = 256;
 // U(b) = sum_g w(g) V(b, g) for the C rows of layer i's values (2^sv a row),
 // w in gate order.  A row goes to tpr = 2^lt consecutive threads (a power
 // of two up to a warp, chosen so that rows of 4096 still fill the GPU);
-// each sums every tpr-th element with inlined full products into two
-// accumulators (independent chains), coalesced, and the row's threads add
-// their sums by shuffles.
+// each sums every tpr-th element of it, two a step with inlined full
+// products into two accumulators (independent chains), the next step's row
+// elements copied into shared memory by cp.async meanwhile (two stages; the
+// weights, the same for every row, come through L1), and the row's threads
+// add their sums by shuffles.
 __global__ void __launch_bounds__(kRowDotThreads) k_rowdot(const uint32_t* __restrict__ V, uint32_t sv,
                                                            const uint32_t* __restrict__ omo, uint32_t C,
                                                            uint32_t lt, uint32_t* __restrict__ U) {
   pdl_wait();
+  __shared__ uint4 rd_stage[kRowDotThreads / 32][2 * 2 * 2 * 32];  // [warp][stage, element, half, lane]
   const uint32_t W = 1u << sv, tpr = 1u << lt;
-  const uint32_t sub = threadIdx.x & (tpr - 1);
+  const uint32_t lane = threadIdx.x & 31, sub = threadIdx.x & (tpr - 1);
+  uint4* stg = rd_stage[threadIdx.x >> 5];
+  auto slot = [&](int st, int e, int half) { return stg + ((st * 2 + e) * 2 + half) * 32 + lane; };
   const size_t nthreads = (size_t)gridDim.x * kRowDotThreads;
   const size_t first = (size_t)blockIdx.x * kRowDotThreads + threadIdx.x;
   // every thread of a warp runs the same number of rows (for the shuffles)
@@ -976,12 +981,37 @@ __global__ void __launch_bounds__(kRowDotThreads) k_rowdot(const uint32_t* __res
     FrAcc a0 = fracc_zero(), a1 = fracc_zero();
     if (b < C) {
       const uint32_t* row = V + ((b << sv) << 3);
+      // step g: elements g and g + tpr (the second only while below W)
+      auto issue = [&](int st, uint32_t g) {
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          if (e == 1 && g + tpr >= W) break;
+          const uint32_t* src = row + 8 * (size_t)(g + e * tpr);
+#pragma unroll
+          for (int half = 0; half < 2; ++half)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                             (uint32_t)__cvta_generic_to_shared(slot(st, e, half))),
+                         "l"(src + 4 * half)
+                         : "memory");
+        }
+      };
+      auto staged = [&](int st, int e) {
+        const uint4 lo = *slot(st, e, 0), hi = *slot(st, e, 1);
+        Fr x;
+        x.v[0] = lo.x; x.v[1] = lo.y; x.v[2] = lo.z; x.v[3] = lo.w;
+        x.v[4] = hi.x; x.v[5] = hi.y; x.v[6] = hi.z; x.v[7] = hi.w;
+        return x;
+      };
       uint32_t g = sub;
-      for (; g + tpr < W; g += 2 * tpr) {
-        fracc_mac_kara_inl(a0, fr_load(omo, g), fr_load(row, g));
-        fracc_mac_kara_inl(a1, fr_load(omo, g + tpr), fr_load(row, g + tpr));
+      int st = 0;
+      if (g < W) issue(0, g);
+      asm volatile("cp.async.commit_group;" ::: "memory");
+      for (; g < W; g += 2 * tpr, st ^= 1) {
+        if (g + 2 * tpr < W) issue(st ^ 1, g + 2 * tpr);
+        asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 1;" ::: "memory");
+        fracc_mac_kara_inl(a0, fr_load(omo, g), staged(st, 0));
+        if (g + tpr < W) fracc_mac_kara_inl(a1, fr_load(omo, g + tpr), staged(st, 1));
       }
-      if (g < W) fracc_mac_kara_inl(a0, fr_load(omo, g), fr_load(row, g));
     }
     fracc_add(a0, a1);
     Fr u = fr_redc288(a0);
