@@ -377,6 +377,7 @@ static int circuit_finish(std::unique_ptr<sisu_circuit>& cc, bool on_device, sis
       return fail(SISU_ERR_CUDA, "upload of the wiring failed");
     D.nmul = l.nmul;
     D.ntot = l.ntot;
+    D.nsg = (uint32_t)l.sg.size();
   }
   if (hc.general) {
     cc->gmap.resize(d);
@@ -1049,10 +1050,6 @@ static int workspace_alloc(sisu_eval* ev) {
 
 static int enqueue_general_layer(const sisu_circuit* cc, sisu_eval* ev, uint32_t i, size_t& off, cudaStream_t st);
 
-// the copy phase of plain layers by the recurrence of its linear part
-// (launch_copy_c) rather than item by item (launch_copy_round)
-constexpr bool kCopyRecurrence = true;
-
 // Enqueue one whole proof on `st` (no host synchronisation).
 static int enqueue_prove(const sisu_circuit* cc, sisu_eval* ev, const sisu_transcript* tr, cudaStream_t st) {
   const HostCircuit& hc = cc->hc;
@@ -1096,9 +1093,8 @@ static int enqueue_prove(const sisu_circuit* cc, sisu_eval* ev, const sisu_trans
     const uint32_t s = hc.s[i + 1], Wn = hc.W[i + 1], sn = hc.s[i + 1];
     {
       ProfScope ps(kProfLayerInit, (double)hc.C * c + (double)L.ntot * (i == 0 ? hc.s[0] : 2.0 * hc.s[i] + 2), st);
-      // gate weights in gate order too, for the first copy round (gates of one entry each)
-      CK(launch_layer_init(w.S, i, c, hc.s[i], L, w.E, w.om, w.eqh, st, 0, 0, L.offo ? nullptr : w.omo),
-         "layer init");
+      // gate weights in gate order too, for the rows' gate sums
+      CK(launch_layer_init(w.S, i, c, hc.s[i], L, w.E, w.om, w.eqh, st, 0, 0, w.omo), "layer init");
     }
     // copy phase: c rounds, each followed by the fold of its challenge
     const uint32_t* A = ev->V[i + 1];
@@ -1106,12 +1102,10 @@ static int enqueue_prove(const sisu_circuit* cc, sisu_eval* ev, const sisu_trans
     // products and three weight products at t = 0, 1, 2; an add gate's two
     // weighted sums), f the share of mul entries
     const double per_pair = 2.0 * L.ntot + 4.0 * L.nmul;
-    // layers whose gates have one entry each: the copy phase by the
-    // recurrence of its linear part (the rows' gate sums from layer i's
-    // values, then the mul entries' t^2 terms a round)
-    const bool rec = kCopyRecurrence && !L.offo;
-    if (rec) {
-      ProfScope ps(kProfCopyRound, 2.0 * hc.C * L.ntot / 2, st);
+    // the copy phase by the recurrence of its linear part: the rows' gate
+    // sums from layer i's values, then the mul entries' t^2 terms a round
+    {
+      ProfScope ps(kProfCopyRound, (double)hc.C * hc.W[i], st);
       CK(launch_rowdot(ev->V[i], hc.s[i], w.omo, hc.C, w.Ub[0], st), "row sums");
     }
     for (uint32_t k = 0; k < c; ++k) {
@@ -1119,17 +1113,9 @@ static int enqueue_prove(const sisu_circuit* cc, sisu_eval* ev, const sisu_trans
       const uint32_t h = hc.C >> (k + 1);
       {
         ProfScope ps(kProfCopyRound, per_pair * h, st);
-        if (rec) {
-          CK(launch_copy_c(tab, sn, h, w.E, w.om, L, w.Ub[(k + 1) & 1], w.cb[(k + 1) & 1], w.Ub[k & 1],
-                           w.cb[k & 1], w.cpart, w.partials, w.S, w.proof, off + 32 * 3 * (size_t)k, k, st),
-             "copy round");
-        } else {
-          // the first round reads the layer's own values (gates of one entry each)
-          const uint32_t* Vg = k == 0 && !L.offo ? ev->V[i] : nullptr;
-          CK(launch_copy_round(tab, sn, h, w.E, w.om, L, w.partials, w.S, w.proof, off + 32 * 3 * (size_t)k, k,
-                               st, nullptr, Vg, hc.s[i], w.omo),
-             "copy round");
-        }
+        CK(launch_copy_c(tab, sn, h, w.E, w.om, L, w.Ub[(k + 1) & 1], w.cb[(k + 1) & 1], w.Ub[k & 1], w.cb[k & 1],
+                         w.cpart, w.partials, w.S, w.proof, off + 32 * 3 * (size_t)k, k, st),
+           "copy round");
       }
       {
         ProfScope ps(kProfCopyFold, (double)h * Wn + h, st);

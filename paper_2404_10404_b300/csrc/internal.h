@@ -63,6 +63,7 @@ struct DevLayer {
   const uint32_t* off2;  // same for in2
   const uint32_t* pos2;
   uint32_t nmul, ntot;   // number of mul entries, of entries
+  uint32_t nsg;          // entries of sgate: the entries, then one for each gate with no entry
 };
 
 // Host copy of the padded circuit (the verifier and the digests use it).
@@ -124,8 +125,8 @@ size_t digest_scratch_words(size_t len_bytes);
 
 int launch_transcript_init(const InitParams& p, DevState* S, void* stream);
 // cq, q: the copies are rank q's of 2^cq (copies j 2^cq + q, j < 2^c); 0, 0
-// for all copies.  omega_o (not null; layers whose gates have one entry
-// each): the gate weights in gate order as well, 2^s_i values.
+// for all copies.  omega_o (not null): the gate weights in gate order as
+// well, 2^s_i values (0 for a gate with no entry).
 int launch_layer_init(DevState* S, uint32_t layer, uint32_t c, uint32_t s_i, const DevLayer& L, uint32_t* E,
                       uint32_t* omega_s, uint32_t* eqh, void* stream, uint32_t cq = 0, uint32_t q = 0,
                       uint32_t* omega_o = nullptr);
@@ -136,15 +137,10 @@ size_t eq_half_words(uint32_t c, uint32_t smax);
 // 2^log_pairs pairs (bd 0: the default); -1 for a value out of range
 int set_copy_tune(uint32_t sn, uint32_t log_pairs, uint32_t bd, uint32_t form, uint32_t min_items);
 // sums_out (not null): the round's sums g(0..3) go there (one rank of a
-// copy-sharded proof) instead of the message and transcript.  Vg (not
-// null, first round of a layer whose gates have one entry each, T the
-// layer's unfolded input values): the layer's own values, rows of 2^sv,
-// which the round reads in place of recomputing its t = 0, 1 products,
-// with omega_o the gate weights in gate order (launch_layer_init).
+// copy-sharded proof) instead of the message and transcript
 int launch_copy_round(const uint32_t* T, uint32_t sn, uint32_t h, const uint32_t* E, const uint32_t* omega_s,
                       const DevLayer& L, uint32_t* partials, DevState* S, uint8_t* proof, size_t off,
-                      uint32_t k, void* stream, uint32_t* sums_out = nullptr, const uint32_t* Vg = nullptr,
-                      uint32_t sv = 0, const uint32_t* omega_o = nullptr);
+                      uint32_t k, void* stream, uint32_t* sums_out = nullptr);
 // The copy phase by its linear recurrence: the rows' gate sums U(b) of
 // layer i's values (rows of 2^sv, gate weights omo in gate order), and one
 // round over the mul entries (U and c of the previous round in, of this

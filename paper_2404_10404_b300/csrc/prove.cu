@@ -325,8 +325,8 @@ __global__ void k_eq_halves(DevState* S, uint32_t layer, uint32_t c, uint32_t si
 }
 
 // om: the gate weights in entry order (om[q] = w(gate of entry q)); omo (not
-// null, layers whose gates have one entry each, nsg = the layer's width):
-// also in gate order, 0 for a gate with no entry.
+// null; nsg = the entries of sg): also in gate order, 0 for a gate with no
+// entry (a gate's several entries all write its one weight).
 __global__ void k_layer_init(uint32_t layer, uint32_t c, uint32_t si, const uint4* __restrict__ sg, uint32_t ntot,
                              const uint32_t* __restrict__ tab, uint32_t* __restrict__ E, uint32_t* __restrict__ om,
                              uint32_t* __restrict__ omo, uint32_t nsg) {
@@ -368,11 +368,9 @@ int launch_layer_init(DevState* S, uint32_t layer, uint32_t c, uint32_t s_i, con
   const uint32_t nh = eq_half_entries(c) + (layer == 0 ? 1 : 2) * eq_half_entries(s_i);
   const int rc = launch_pdl(k_eq_halves, grid_for(nh, 128), 128, st, S, layer, c, s_i, eqh, cq, q);
   if (rc) return rc;
-  const uint32_t W = 1u << s_i;
-  if (omega_o && (L.offo || L.ntot > W)) return (int)cudaErrorInvalidValue;  // gates of one entry each only
-  size_t n = ((size_t)1 << c) + (omega_o ? W : L.ntot);
+  size_t n = ((size_t)1 << c) + (omega_o ? L.nsg : L.ntot);
   return launch_pdl(k_layer_init, grid_for(n, 128), 128, st, layer, c, s_i, L.sgate, L.ntot, (const uint32_t*)eqh, E,
-                    omega_s, omega_o, W);
+                    omega_s, omega_o, L.nsg);
 }
 
 // ---------------------------------------------------------------------------
@@ -457,13 +455,11 @@ __host__ __device__ __forceinline__ CopySplit copy_split(uint32_t h, uint32_t nm
 // The items of CTA `bid` of a round split by (per_cta, m): returns, in lanes
 // t < 4 of warp 0, the CTA's share of g(t) (plain, below 2r).  Called by
 // every thread of the block.
-template <int BD, bool kV>
+template <int BD>
 __device__ __forceinline__ Fr copy_items(const uint32_t* __restrict__ T, uint32_t sn, uint32_t h,
                                          const uint32_t* __restrict__ E, const uint32_t* __restrict__ om,
                                          const uint4* __restrict__ sg, uint32_t nmul, uint32_t ntot,
-                                         uint64_t per_cta, uint32_t m, uint32_t bid, uint32_t* sh_e,
-                                         const uint32_t* __restrict__ Vg, uint32_t sv,
-                                         const uint32_t* __restrict__ omo) {
+                                         uint64_t per_cta, uint32_t m, uint32_t bid, uint32_t* sh_e) {
   const uint64_t pair_cost = copy_pair_cost(nmul, ntot);
   uint64_t q0, q1;  // the CTA's item range
   uint32_t j;       // the pair of its first item
@@ -495,41 +491,19 @@ __device__ __forceinline__ Fr copy_items(const uint32_t* __restrict__ T, uint32_
     const uint32_t* lo = T + (((size_t)j << sn) << 3);
     const uint32_t* hi = T + (((size_t)(j + h) << sn) << 3);
     FrAcc a0 = fracc_zero(), a1 = fracc_zero(), ac = fracc_zero();
-    if (kV) {  // the first round: the gate values of copies j and j + h are the evaluation's
-      // S_j(0), S_j(1): gates [g0, g1) in gate order (the last segment of a
-      // pair also takes the gates from ntot up, which have no entry and
-      // value 0), read coalesced
-      const uint32_t* vlo = Vg + (((size_t)j << sv) << 3);
-      const uint32_t* vhi = Vg + (((size_t)(j + h) << sv) << 3);
-      const uint32_t ge = g1 == ntot ? 1u << sv : g1;
-      for (uint32_t g = g0 + threadIdx.x; g < ge; g += BD) {
-        const Fr w = fr_load(omo, g);
-        fracc_mac(a0, w, fr_load(vlo, g));
-        fracc_mac(a1, w, fr_load(vhi, g));
-      }
-      // c_j: the mul entries of [g0, g1)
-      for (uint32_t q = g0 + threadIdx.x; q < min(g1, nmul); q += BD) {
-        const uint4 gi = sg[q];
-        const Fr w = fr_load(om, q);
-        const Fr x0 = fr_load(lo, gi.x), x1 = fr_load(hi, gi.x);
-        const Fr y0 = fr_load(lo, gi.y), y1 = fr_load(hi, gi.y);
-        fracc_mac(ac, fr_mul(w, fr_sub(x1, x0)), fr_sub(y1, y0));
-      }
-    } else {
-      for (uint32_t q = g0 + threadIdx.x; q < g1; q += BD) {
-        const uint4 gi = sg[q];
-        const Fr w = fr_load(om, q);
-        const Fr x0 = fr_load(lo, gi.x), x1 = fr_load(hi, gi.x);
-        const Fr y0 = fr_load(lo, gi.y), y1 = fr_load(hi, gi.y);
-        if (q < nmul) {
-          const Fr wx0 = fr_mul(w, x0), wx1 = fr_mul(w, x1);
-          fracc_mac(a0, wx0, y0);
-          fracc_mac(a1, wx1, y1);
-          fracc_mac(ac, fr_sub(wx1, wx0), fr_sub(y1, y0));
-        } else {
-          fracc_mac(a0, w, fr_add(x0, y0));
-          fracc_mac(a1, w, fr_add(x1, y1));
-        }
+    for (uint32_t q = g0 + threadIdx.x; q < g1; q += BD) {
+      const uint4 gi = sg[q];
+      const Fr w = fr_load(om, q);
+      const Fr x0 = fr_load(lo, gi.x), x1 = fr_load(hi, gi.x);
+      const Fr y0 = fr_load(lo, gi.y), y1 = fr_load(hi, gi.y);
+      if (q < nmul) {
+        const Fr wx0 = fr_mul(w, x0), wx1 = fr_mul(w, x1);
+        fracc_mac(a0, wx0, y0);
+        fracc_mac(a1, wx1, y1);
+        fracc_mac(ac, fr_sub(wx1, wx0), fr_sub(y1, y0));
+      } else {
+        fracc_mac(a0, w, fr_add(x0, y0));
+        fracc_mac(a1, w, fr_add(x1, y1));
       }
     }
     Fr s[3] = {fr_redc288(a0), fr_redc288(a1), fr_redc288(ac)};
@@ -569,25 +543,15 @@ __device__ __forceinline__ Fr copy_items(const uint32_t* __restrict__ T, uint32_
 }
 
 // Gathers of the per-warp item loop staged through shared memory: each
-// lane copies its next item's five elements (w, x0, x1, y0, y1; in the
-// first round's gate-value loop w, v0, v1) there with 16-byte cp.async
-// while it computes the current one, so the products never wait on an L2
-// or DRAM gather.  A warp's area holds two stages of five elements a lane,
-// each element as two 16-byte halves in lane-contiguous rows
-// (conflict-free 16-byte accesses).
+// lane copies its next item's five elements (w, x0, x1, y0, y1) there with
+// 16-byte cp.async while it computes the current one, so the products never
+// wait on an L2 or DRAM gather.  A warp's area holds two stages of five
+// elements a lane, each element as two 16-byte halves in lane-contiguous
+// rows (conflict-free 16-byte accesses).
 constexpr uint32_t kStageWords4 = 2 * 5 * 2 * 32;  // 16-byte words a warp (10 KiB)
 
 __device__ __forceinline__ uint4* stage_slot(uint4* stg, int st, int f, int half, int lane) {
   return stg + ((st * 5 + f) * 2 + half) * 32 + lane;
-}
-
-__device__ __forceinline__ void stage_issue_one(uint4* stg, int st, int f, int lane, const uint32_t* src) {
-#pragma unroll
-  for (int half = 0; half < 2; ++half)
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
-                     (uint32_t)__cvta_generic_to_shared(stage_slot(stg, st, f, half, lane))),
-                 "l"(src + 4 * half)
-                 : "memory");
 }
 
 __device__ __forceinline__ void stage_issue(uint4* stg, int st, int lane, const uint32_t* w,
@@ -595,7 +559,13 @@ __device__ __forceinline__ void stage_issue(uint4* stg, int st, int lane, const 
                                             const uint32_t* y1) {
   const uint32_t* src[5] = {w, x0, x1, y0, y1};
 #pragma unroll
-  for (int f = 0; f < 5; ++f) stage_issue_one(stg, st, f, lane, src[f]);
+  for (int f = 0; f < 5; ++f)
+#pragma unroll
+    for (int half = 0; half < 2; ++half)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                       (uint32_t)__cvta_generic_to_shared(stage_slot(stg, st, f, half, lane))),
+                   "l"(src[f] + 4 * half)
+                   : "memory");
 }
 
 __device__ __forceinline__ Fr stage_read(uint4* stg, int st, int f, int lane) {
@@ -613,13 +583,12 @@ __device__ __forceinline__ Fr stage_read(uint4* stg, int st, int f, int lane) {
 // the CTA-wide form every segment ended in a block reduction, where warps
 // that finished early waited).  Returns, in lanes t < 4 of every warp, the
 // warp's share of g(t) (plain, below 2r); sh_e: this warp's 16 words.
-template <int BD, bool kV>
+template <int BD>
 __device__ __forceinline__ Fr copy_items_warp(const uint32_t* __restrict__ T, uint32_t sn, uint32_t h,
                                               const uint32_t* __restrict__ E, const uint32_t* __restrict__ om,
                                               const uint4* __restrict__ sg, uint32_t nmul, uint32_t ntot,
                                               uint64_t per_cta, uint32_t m, uint32_t bid, uint32_t* sh_e,
-                                              uint4* stg, const uint32_t* __restrict__ Vg, uint32_t sv,
-                                              const uint32_t* __restrict__ omo) {
+                                              uint4* stg) {
   constexpr int NW = BD / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint64_t pair_cost = copy_pair_cost(nmul, ntot);
@@ -653,77 +622,34 @@ __device__ __forceinline__ Fr copy_items_warp(const uint32_t* __restrict__ T, ui
     FrAcc a0 = fracc_zero(), a1 = fracc_zero(), ac = fracc_zero();
     // two-stage pipeline: item q + 32's gathers are in flight while item q
     // is computed (one cp.async group a lane and item)
-    auto pipelined = [&](uint32_t first, uint32_t end, auto&& issue, auto&& compute) {
-      uint32_t q = first + lane;
-      int st = 0;
-      if (q < end) issue(0, q);
-      asm volatile("cp.async.commit_group;" ::: "memory");
-      for (; q < end; q += 32, st ^= 1) {
-        if (q + 32 < end) issue(st ^ 1, q + 32);
-        asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 1;" ::: "memory");
-        compute(st, q);
+    uint32_t q = g0 + lane;
+    int st = 0;
+    if (q < g1) {
+      const uint4 gi = sg[q];
+      stage_issue(stg, 0, lane, om + 8 * (size_t)q, lo + 8 * (size_t)gi.x, hi + 8 * (size_t)gi.x,
+                  lo + 8 * (size_t)gi.y, hi + 8 * (size_t)gi.y);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    for (; q < g1; q += 32, st ^= 1) {
+      const uint32_t qn = q + 32;
+      if (qn < g1) {
+        const uint4 gi = sg[qn];
+        stage_issue(stg, st ^ 1, lane, om + 8 * (size_t)qn, lo + 8 * (size_t)gi.x, hi + 8 * (size_t)gi.x,
+                    lo + 8 * (size_t)gi.y, hi + 8 * (size_t)gi.y);
       }
-    };
-    if (kV) {
-      // the first round: the gate values of copies j and j + h, which the
-      // evaluation wrote, stand for the products at t = 0 and t = 1.
-      // S_j(0), S_j(1) over gates [g0, g1) in gate order (the last segment
-      // of a pair also takes the gates from ntot up, which have no entry
-      // and value 0): w, v0, v1 read coalesced
-      const uint32_t* vlo = Vg + (((size_t)j << sv) << 3);
-      const uint32_t* vhi = Vg + (((size_t)(j + h) << sv) << 3);
-      const uint32_t ge = g1 == ntot ? 1u << sv : g1;
-      pipelined(
-          g0, ge,
-          [&](int stage, uint32_t g) {
-            stage_issue_one(stg, stage, 0, lane, omo + 8 * (size_t)g);
-            stage_issue_one(stg, stage, 1, lane, vlo + 8 * (size_t)g);
-            stage_issue_one(stg, stage, 2, lane, vhi + 8 * (size_t)g);
-          },
-          [&](int stage, uint32_t) {
-            const Fr w = stage_read(stg, stage, 0, lane);
-            fracc_mac(a0, w, stage_read(stg, stage, 1, lane));
-            fracc_mac(a1, w, stage_read(stg, stage, 2, lane));
-          });
-      // c_j over the mul entries of [g0, g1): w (x1 - x0) (y1 - y0)
-      pipelined(
-          g0, min(g1, nmul),
-          [&](int stage, uint32_t q) {
-            const uint4 gi = sg[q];
-            stage_issue_one(stg, stage, 0, lane, om + 8 * (size_t)q);
-            stage_issue_one(stg, stage, 1, lane, lo + 8 * (size_t)gi.x);
-            stage_issue_one(stg, stage, 2, lane, hi + 8 * (size_t)gi.x);
-            stage_issue_one(stg, stage, 3, lane, lo + 8 * (size_t)gi.y);
-            stage_issue_one(stg, stage, 4, lane, hi + 8 * (size_t)gi.y);
-          },
-          [&](int stage, uint32_t) {
-            const Fr w = stage_read(stg, stage, 0, lane);
-            const Fr x0 = stage_read(stg, stage, 1, lane), x1 = stage_read(stg, stage, 2, lane);
-            const Fr y0 = stage_read(stg, stage, 3, lane), y1 = stage_read(stg, stage, 4, lane);
-            fracc_mac(ac, fr_mul(w, fr_sub(x1, x0)), fr_sub(y1, y0));
-          });
-    } else {
-      pipelined(
-          g0, g1,
-          [&](int stage, uint32_t q) {
-            const uint4 gi = sg[q];
-            stage_issue(stg, stage, lane, om + 8 * (size_t)q, lo + 8 * (size_t)gi.x, hi + 8 * (size_t)gi.x,
-                        lo + 8 * (size_t)gi.y, hi + 8 * (size_t)gi.y);
-          },
-          [&](int stage, uint32_t q) {
-            const Fr w = stage_read(stg, stage, 0, lane);
-            const Fr x0 = stage_read(stg, stage, 1, lane), x1 = stage_read(stg, stage, 2, lane);
-            const Fr y0 = stage_read(stg, stage, 3, lane), y1 = stage_read(stg, stage, 4, lane);
-            if (q < nmul) {
-              const Fr wx0 = fr_mul(w, x0), wx1 = fr_mul(w, x1);
-              fracc_mac(a0, wx0, y0);
-              fracc_mac(a1, wx1, y1);
-              fracc_mac(ac, fr_sub(wx1, wx0), fr_sub(y1, y0));
-            } else {
-              fracc_mac(a0, w, fr_add(x0, y0));
-              fracc_mac(a1, w, fr_add(x1, y1));
-            }
-          });
+      asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 1;" ::: "memory");
+      const Fr w = stage_read(stg, st, 0, lane);
+      const Fr x0 = stage_read(stg, st, 1, lane), x1 = stage_read(stg, st, 2, lane);
+      const Fr y0 = stage_read(stg, st, 3, lane), y1 = stage_read(stg, st, 4, lane);
+      if (q < nmul) {
+        const Fr wx0 = fr_mul(w, x0), wx1 = fr_mul(w, x1);
+        fracc_mac(a0, wx0, y0);
+        fracc_mac(a1, wx1, y1);
+        fracc_mac(ac, fr_sub(wx1, wx0), fr_sub(y1, y0));
+      } else {
+        fracc_mac(a0, w, fr_add(x0, y0));
+        fracc_mac(a1, w, fr_add(x1, y1));
+      }
     }
     Fr sj[3] = {fr_redc288(a0), fr_redc288(a1), fr_redc288(ac)};
 #pragma unroll
@@ -764,27 +690,18 @@ __device__ __forceinline__ Fr copy_items_warp(const uint32_t* __restrict__ T, ui
 // sums_out: null for a whole proof; for one rank of a copy-sharded proof
 // the rank's round sums g(0..3) (plain, below 2r) go there instead of the
 // round message and the transcript, which wait for every rank's sums.
-// kV: the first copy round of a layer whose gates have one entry each, with
-// Vg the layer's own values (rows of 2^sv): a gate's value in copy j is
-// op(x_0, y_0) and in copy j + h op(x_1, y_1), so the sums S_j(0) and
-// S_j(1) need only w v_0 and w v_1, and the t^2 coefficient of a mul gate
-// w (x_1 - x_0)(y_1 - y_0) one Montgomery product: one product fewer a mul
-// item, and an add item gathers no inputs.
-template <int BD, bool kWarp, bool kV>
+template <int BD, bool kWarp>
 __global__ void __launch_bounds__(BD) k_copy_round(const uint32_t* __restrict__ T, uint32_t sn, uint32_t h,
                                                    const uint32_t* __restrict__ E, const uint32_t* __restrict__ om,
                                                    const uint4* __restrict__ sg, uint32_t nmul, uint32_t ntot,
                                                    uint64_t per_cta, uint32_t m, uint32_t* partials, DevState* S,
-                                                   uint8_t* proof, size_t off, uint32_t k, uint32_t* sums_out,
-                                                   const uint32_t* __restrict__ Vg, uint32_t sv,
-                                                   const uint32_t* __restrict__ omo) {
+                                                   uint8_t* proof, size_t off, uint32_t k, uint32_t* sums_out) {
   pdl_wait();
   __shared__ __align__(16) uint32_t sh_e[BD / 32][16];  // E(j), E(j + h) of a warp's current segment
   if (threadIdx.x == BD - 32) warm_transcript_code(k, h);
   Fr acc[4];  // thread 0: the CTA's share of g(0..3)
   if (!kWarp) {  // the CTA-wide form: lanes t < 4 of warp 0
-    const Fr tot =
-        copy_items<BD, kV>(T, sn, h, E, om, sg, nmul, ntot, per_cta, m, blockIdx.x, sh_e[0], Vg, sv, omo);
+    const Fr tot = copy_items<BD>(T, sn, h, E, om, sg, nmul, ntot, per_cta, m, blockIdx.x, sh_e[0]);
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
 #pragma unroll
@@ -795,8 +712,8 @@ __global__ void __launch_bounds__(BD) k_copy_round(const uint32_t* __restrict__ 
     __shared__ Fr wtot[BD / 32][4];
     extern __shared__ uint4 cr_stage[];  // kStageWords4 a warp
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const Fr tot = copy_items_warp<BD, kV>(T, sn, h, E, om, sg, nmul, ntot, per_cta, m, blockIdx.x, sh_e[warp],
-                                           cr_stage + warp * kStageWords4, Vg, sv, omo);
+    const Fr tot = copy_items_warp<BD>(T, sn, h, E, om, sg, nmul, ntot, per_cta, m, blockIdx.x, sh_e[warp],
+                                       cr_stage + warp * kStageWords4);
     if (lane < 4) wtot[warp][lane] = tot;
     __syncthreads();
 #pragma unroll
@@ -838,90 +755,55 @@ static int copy_round_per_sm() {
   static int per_sm = 0;
   if (per_sm == 0) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_copy_round<BD, false, false>, BD, 0) != cudaSuccess ||
-        n < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_copy_round<BD, false>, BD, 0) != cudaSuccess || n < 1)
       n = 1;
     per_sm = n;
   }
   return per_sm;
 }
 
-template <int BD, bool kV>
-static int launch_copy_round_v(bool warp, const CopySplit& sp, const uint32_t* T, uint32_t sn, uint32_t h,
-                               const uint32_t* E, const uint32_t* omega_s, const DevLayer& L, uint32_t* partials,
-                               DevState* S, uint8_t* proof, size_t off, uint32_t k, cudaStream_t st,
-                               uint32_t* sums_out, const uint32_t* Vg, uint32_t sv, const uint32_t* omo) {
-  if (warp) {
-    const size_t smem = (size_t)(BD / 32) * kStageWords4 * sizeof(uint4);
-    static bool attr = false;
-    if (!attr) {
-      const cudaError_t e = cudaFuncSetAttribute(k_copy_round<BD, true, kV>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return (int)e;
-      attr = true;
-    }
-    return launch_pdl_smem(k_copy_round<BD, true, kV>, sp.nc, BD, smem, st, T, sn, h, E, omega_s, L.sgate, L.nmul,
-                           L.ntot, sp.per_cta, sp.m, partials, S, proof, off, k, sums_out, Vg, sv, omo);
-  }
-  return launch_pdl(k_copy_round<BD, false, kV>, sp.nc, BD, st, T, sn, h, E, omega_s, L.sgate, L.nmul, L.ntot,
-                    sp.per_cta, sp.m, partials, S, proof, off, k, sums_out, Vg, sv, omo);
-}
-
 template <int BD>
 static int launch_copy_round_bd(int form, uint32_t min_items, const uint32_t* T, uint32_t sn, uint32_t h,
                                 const uint32_t* E, const uint32_t* omega_s, const DevLayer& L, uint32_t* partials,
                                 DevState* S, uint8_t* proof, size_t off, uint32_t k, cudaStream_t st,
-                                uint32_t* sums_out, const uint32_t* Vg, uint32_t sv, const uint32_t* omo) {
+                                uint32_t* sums_out) {
   const uint32_t ncmax = std::min<uint32_t>(kSMs * copy_round_per_sm<BD>(), kMaxPartials);
   // contiguous ranges of equal cost: one wave of CTAs, and for small rounds
   // about min_items items a CTA (short serial chains)
   const CopySplit sp = copy_split(h, L.nmul, L.ntot, ncmax, min_items ? min_items : BD);
   const bool warp = form == 2 || (form == 0 && sp.m == 0);
-  if (Vg && omo)
-    return launch_copy_round_v<BD, true>(warp, sp, T, sn, h, E, omega_s, L, partials, S, proof, off, k, st,
-                                         sums_out, Vg, sv, omo);
-  return launch_copy_round_v<BD, false>(warp, sp, T, sn, h, E, omega_s, L, partials, S, proof, off, k, st, sums_out,
-                                        nullptr, 0, nullptr);
-}
-
-// The first round's per-warp form at 512 threads: its products need fewer
-// registers (128, no spills), so one CTA of 16 warps fills an SM where the
-// general form's 168 registers allow 12 (slot first round 1.296 -> 1.256
-// ms).  Taken unless the launch-shape table sets the class.
-
-static int launch_copy_round_first512(const uint32_t* T, uint32_t sn, uint32_t h, const uint32_t* E,
-                                      const uint32_t* omega_s, const DevLayer& L, uint32_t* partials, DevState* S,
-                                      uint8_t* proof, size_t off, uint32_t k, cudaStream_t st, uint32_t* sums_out,
-                                      const uint32_t* Vg, uint32_t sv, const uint32_t* omo, bool* launched) {
-  const CopySplit sp = copy_split(h, L.nmul, L.ntot, std::min<uint32_t>(kSMs, kMaxPartials), 512);
-  *launched = sp.m == 0;
-  if (!*launched) return 0;
-  return launch_copy_round_v<512, true>(true, sp, T, sn, h, E, omega_s, L, partials, S, proof, off, k, st, sums_out,
-                                        Vg, sv, omo);
+  if (warp) {
+    const size_t smem = (size_t)(BD / 32) * kStageWords4 * sizeof(uint4);
+    static bool attr = false;
+    if (!attr) {
+      const cudaError_t e = cudaFuncSetAttribute(k_copy_round<BD, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem);
+      if (e != cudaSuccess) return (int)e;
+      attr = true;
+    }
+    return launch_pdl_smem(k_copy_round<BD, true>, sp.nc, BD, smem, st, T, sn, h, E, omega_s, L.sgate, L.nmul,
+                           L.ntot, sp.per_cta, sp.m, partials, S, proof, off, k, sums_out);
+  }
+  return launch_pdl(k_copy_round<BD, false>, sp.nc, BD, st, T, sn, h, E, omega_s, L.sgate, L.nmul, L.ntot,
+                    sp.per_cta, sp.m, partials, S, proof, off, k, sums_out);
 }
 
 int launch_copy_round(const uint32_t* T, uint32_t sn, uint32_t h, const uint32_t* E, const uint32_t* omega_s,
                       const DevLayer& L, uint32_t* partials, DevState* S, uint8_t* proof, size_t off, uint32_t k,
-                      void* stream, uint32_t* sums_out, const uint32_t* Vg, uint32_t sv, const uint32_t* omo) {
+                      void* stream, uint32_t* sums_out) {
   cudaStream_t st = (cudaStream_t)stream;
   uint32_t lh = 0;
   while ((2u << lh) <= h) ++lh;
   CopyTune t = {384, 0, 0};
   if (sn < kTuneLog && lh < kTuneLog && g_copy_tune[sn][lh].bd) t = g_copy_tune[sn][lh];
-  if (Vg && omo && t.bd == 384 && t.form == 0 && t.min_items == 0) {
-    bool launched = false;
-    const int rc = launch_copy_round_first512(T, sn, h, E, omega_s, L, partials, S, proof, off, k, st, sums_out, Vg,
-                                              sv, omo, &launched);
-    if (rc || launched) return rc;
-  }
   if (t.bd == 128)
     return launch_copy_round_bd<128>(t.form, t.min_items, T, sn, h, E, omega_s, L, partials, S, proof, off, k, st,
-                                     sums_out, Vg, sv, omo);
+                                     sums_out);
   if (t.bd == 256)
     return launch_copy_round_bd<256>(t.form, t.min_items, T, sn, h, E, omega_s, L, partials, S, proof, off, k, st,
-                                     sums_out, Vg, sv, omo);
+                                     sums_out);
   return launch_copy_round_bd<384>(t.form, t.min_items, T, sn, h, E, omega_s, L, partials, S, proof, off, k, st,
-                                   sums_out, Vg, sv, omo);
+                                   sums_out);
 }
 
 int set_copy_tune(uint32_t sn, uint32_t log_pairs, uint32_t bd, uint32_t form, uint32_t min_items) {
