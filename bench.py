@@ -63,7 +63,7 @@ ALU_PEAK_TIMAD = SMS * IMAD_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
 # first layers of the slot workload: every layer has the same shape, so the
 # per-item traffic of a full-size launch is the same); None when not
 # captured for the current build of the kernel.
-DOMINANT_TRAFFIC_BYTES_PER_ITEM = 4457510400 / 33553408
+DOMINANT_TRAFFIC_BYTES_PER_ITEM = None
 
 
 def log(*a):
@@ -383,7 +383,7 @@ def run_ours(args):
         breakdown[name] = {"ms": round(kms, 4), "launches": kn, "fr_mults": kw}
     S.profile_enable(0)
 
-    # algorithmic work of the timed copy rounds: 2 + 4 f products per (pair, gate) item
+    # (pair, gate) items of the timed copy rounds (the unit of the traffic figure)
     items = sum(circ.n_copies // 2 ** (k + 1) * circ.widths[i] for i in range(circ.depth)
                 for k in range((circ.n_copies - 1).bit_length()))
     achieved = prof_work * IMAD_PER_FR_MUL / (prof_ms / 1e3) / 1e12 if prof_ms else None
@@ -394,15 +394,17 @@ def run_ours(args):
     traffic = (DOMINANT_TRAFFIC_BYTES_PER_ITEM * per_launch_items
                if DOMINANT_TRAFFIC_BYTES_PER_ITEM and per_launch_items and args.workload == "slot" and not args.depth
                else None)
-    roofline = {"bound": "alu", "kernel": "k_copy_round (copy-phase round)", "achieved": achieved,
+    roofline = {"bound": "alu", "kernel": "k_copy_c (copy-phase round: the mul entries' t^2 terms, the pairs' "
+                                          "message terms and row-sum update)", "achieved": achieved,
                 "peak": peak, "unit": "TIMAD/s", "frac": achieved / peak if achieved else None,
                 "traffic": traffic,
                 "peak_source": "measured in this run (mad.lo stream, integer pipe) of measured",
                 "peak_measurement": imad,
                 "frac_of_derived_peak": achieved / ALU_PEAK_TIMAD if achieved else None,
                 "derived_peak": {"tops": ALU_PEAK_TIMAD, "how": "148 SMs x 64 IMAD/clk x 2032 MHz"},
-                "work_counted": "2 + 4 f Montgomery products per (pair, gate) item (f = share of mul gates), "
-                                "264 multiply-adds per product",
+                "work_counted": "per round, one Montgomery product (264 multiply-adds) and one full 512-bit "
+                                "product (128) per mul entry and pair, and 4 (first round) or 8 Montgomery "
+                                "products per pair",
                 "per_launch_ms": prof_ms / prof_n if prof_n else None, "launches_timed": prof_n,
                 "fr_mults_per_launch": prof_work / prof_n if prof_n else None,
                 "items_per_launch": per_launch_items}
@@ -745,12 +747,12 @@ def batched_core(S, dev, stream, specs, pins, budget_gb: float):
            "autotune": {"concurrency": tuned, "ms_first_wave": tune_log,
                         "copy_round": {"classes": len(classes), "from_cache": sum(c in cached for c in classes),
                                        "seconds": round(t_tune, 1),
-                                       "non_default": sum(table[c] != (384, 0, 0) for c in classes),
-                                       "timed_round_us_default_vs_tuned": gains,
+                                       "non_default": sum(table[c] != tune.DEFAULT_SHAPE for c in classes),
+                                       "first_round_us_default_vs_tuned": gains,
                                        "how": "per (log2 W, log2 pairs) class: 27 launch shapes (128/256/384 "
-                                              "threads x 3 forms x 3 CTA granularities) timed on the second "
-                                              "copy round of a one-layer circuit with that many pairs in it, "
-                                              "best of 3"}},
+                                              "threads x 3 splits (whole pairs a CTA or shares of a pair) x 3 "
+                                              "share sizes) timed on the first copy round of a one-layer "
+                                              "circuit of that shape, best of 3"}},
            "parity": "every batched proof equals the single-instance proof"}
     return res, singles
 

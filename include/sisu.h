@@ -454,15 +454,17 @@ int sisu_statement_digest(const uint8_t* data, size_t len, uint8_t* out, void* s
  * CUDA (with the runtime's error string). */
 int sisu_statement_digest_noalloc(const uint8_t* data, size_t len, uint8_t* out, void* stream);
 
-/* Launch shape of the copy-round kernel for layers whose next layer has
- * 2^log_width positions, in rounds of 2^log_pairs pairs (both < 25), as an
- * autotuner picks it: cta_threads 128, 256 or 384 (0 restores the
- * default), form 0 = per-warp pair segments while pairs outnumber CTAs
- * (the default), 1 = CTA-wide segments, 2 = per-warp segments always,
- * min_items = (pair, gate) items a CTA at least (0: one per thread).
- * Proof bytes do not depend on it.  Process-wide; set it before the first
- * proof of an eval handle (a handle replays the launches it captured).
- * Errors: INVALID_ARG. */
+/* Launch shape of a layered circuit's copy-round kernel for layers whose
+ * next layer has 2^log_width positions, in rounds of 2^log_pairs pairs
+ * (both < 25), as an autotuner picks it: cta_threads 128, 256 or 384 (0
+ * restores the default, 256), form 0 = whole pairs a CTA while pairs are
+ * at least the CTAs and shares of a pair's mul entries otherwise (the
+ * default), 1 = shares whenever there are at most 4096 pairs, 2 = whole
+ * pairs always; min_items = mul entries a share at least (0: half a CTA's
+ * threads).  General circuits and copy-sharded ranks keep their own fixed
+ * shape.  Proof bytes do not depend on it.  Process-wide; set it before the
+ * first proof of an eval handle (a handle replays the launches it
+ * captured).  Errors: INVALID_ARG. */
 int sisu_tune_copy_round(uint32_t log_width, uint32_t log_pairs, uint32_t cta_threads, uint32_t form,
                          uint32_t min_items);
 
@@ -494,11 +496,17 @@ int sisu_microbench(int kind, uint32_t blocks, uint32_t threads, uint32_t iters,
  * evaluation, 3 x/y-phase round, 4 statement digests, 5 layer init, 6 x/y
  * phase init, 7 transcript-only kernels, 8 input conversion, 9 associative
  * hash sums, 10 pairwise-distinct sums (for 9 and 10 the work counted is
- * evaluations of F, not field products); 0 disables.
+ * evaluations of F, not field products), 11 the copy phase's row sums of a
+ * layer; 0 disables.
  * sisu_profile_read waits for the recorded events of one kind and returns
  * their summed milliseconds, the launch count and the algorithmic field
- * products of those launches (per copy-phase pair and gate: 2 + 4 f, i.e.
- * 6 per mul gate and 2 per add gate), then forgets them. */
+ * products of those launches, in Montgomery products (264 multiply-adds; a
+ * full 512-bit product counts 128/264 of one): a layered circuit's copy
+ * round forms one Montgomery and one full product per mul entry and pair,
+ * and 4 (first round) or 8 Montgomery products per pair; its row sums one
+ * full product per copy and gate; a general circuit's copy round 2 + 4 f
+ * products per pair and gate (6 per mul gate, 2 per add gate); then forgets
+ * them. */
 int sisu_profile_enable(uint32_t kind_mask);
 int sisu_profile_read(uint32_t kind, double* ms, uint64_t* launches, double* fr_mults);
 /* The recorded launches of one kind one by one, oldest first, without

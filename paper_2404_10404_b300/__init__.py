@@ -43,9 +43,9 @@ ENTRY_POINTS = [
 ]
 PROF_COPY_ROUND, PROF_COPY_FOLD, PROF_EVAL, PROF_GATE_ROUND, PROF_DIGEST = 0, 1, 2, 3, 4
 PROF_LAYER_INIT, PROF_PHASE_INIT, PROF_TRANSCRIPT, PROF_INPUTS = 5, 6, 7, 8
-PROF_ASSOC_HASH, PROF_ASSOC_PAIR = 9, 10
+PROF_ASSOC_HASH, PROF_ASSOC_PAIR, PROF_ROW_SUMS = 9, 10, 11
 PROF_KINDS = {0: "copy_round", 1: "copy_fold", 2: "eval_layer", 3: "gate_round", 4: "digest",
-              5: "layer_init", 6: "phase_init", 7: "transcript", 8: "inputs"}
+              5: "layer_init", 6: "phase_init", 7: "transcript", 8: "inputs", 11: "row_sums"}
 
 
 class SisuError(RuntimeError):

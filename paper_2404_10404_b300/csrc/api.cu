@@ -113,7 +113,7 @@ void sisu::prof_end(long idx, void* stream) {
 
 enum : uint32_t {
   kProfCopyRound = 0, kProfCopyFold = 1, kProfEval = 2, kProfGateRound = 3, kProfDigest = 4,
-  kProfLayerInit = 5, kProfPhaseInit = 6, kProfTranscript = 7, kProfInputs = 8
+  kProfLayerInit = 5, kProfPhaseInit = 6, kProfTranscript = 7, kProfInputs = 8, kProfRowSums = 11
 };
 
 extern "C" int sisu_profile_enable(uint32_t kind_mask) {
@@ -1050,6 +1050,10 @@ static int workspace_alloc(sisu_eval* ev) {
 
 static int enqueue_general_layer(const sisu_circuit* cc, sisu_eval* ev, uint32_t i, size_t& off, cudaStream_t st);
 
+// a full 512-bit product (128 multiply-adds) in units of a Montgomery
+// product (264), for the copy phase's work counts
+constexpr double kFullProduct = 128.0 / 264.0;
+
 // Enqueue one whole proof on `st` (no host synchronisation).
 static int enqueue_prove(const sisu_circuit* cc, sisu_eval* ev, const sisu_transcript* tr, cudaStream_t st) {
   const HostCircuit& hc = cc->hc;
@@ -1098,21 +1102,23 @@ static int enqueue_prove(const sisu_circuit* cc, sisu_eval* ev, const sisu_trans
     }
     // copy phase: c rounds, each followed by the fold of its challenge
     const uint32_t* A = ev->V[i + 1];
-    // algorithmic products per pair: 2 + 4 f per gate (a mul gate's three
-    // products and three weight products at t = 0, 1, 2; an add gate's two
-    // weighted sums), f the share of mul entries
-    const double per_pair = 2.0 * L.ntot + 4.0 * L.nmul;
+
     // the copy phase by the recurrence of its linear part: the rows' gate
-    // sums from layer i's values, then the mul entries' t^2 terms a round
+    // sums from layer i's values, then the mul entries' t^2 terms a round.
+    // Work counted in Montgomery-product units of 264 multiply-adds: a full
+    // 512-bit product is 128 of them (kFullProduct of a unit)
     {
-      ProfScope ps(kProfCopyRound, (double)hc.C * hc.W[i], st);
+      ProfScope ps(kProfRowSums, kFullProduct * hc.C * hc.W[i], st);
       CK(launch_rowdot(ev->V[i], hc.s[i], w.omo, hc.C, w.Ub[0], st), "row sums");
     }
     for (uint32_t k = 0; k < c; ++k) {
       const uint32_t* tab = k == 0 ? ev->V[i + 1] : w.T;
       const uint32_t h = hc.C >> (k + 1);
       {
-        ProfScope ps(kProfCopyRound, per_pair * h, st);
+        // a mul entry of a pair: one Montgomery and one full product; a pair:
+        // its four message terms and (after the first round) the four
+        // products of its two rows' update
+        ProfScope ps(kProfCopyRound, ((1.0 + kFullProduct) * L.nmul + (k ? 8.0 : 4.0)) * h, st);
         CK(launch_copy_c(tab, sn, h, w.E, w.om, L, w.Ub[(k + 1) & 1], w.cb[(k + 1) & 1], w.Ub[k & 1], w.cb[k & 1],
                          w.cpart, w.partials, w.S, w.proof, off + 32 * 3 * (size_t)k, k, st),
            "copy round");

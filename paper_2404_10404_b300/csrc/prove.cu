@@ -734,21 +734,22 @@ __global__ void __launch_bounds__(BD) k_copy_round(const uint32_t* __restrict__ 
   }
 }
 
-// Launch shapes of the copy round, chosen per (log2 W_{i+1}, log2 pairs) by
-// a tuning table the host fills (sisu_tune_copy_round; unset entries keep
-// the default): the CTA width (128, 256 or 384 threads), the form (per-warp
-// pair segments or CTA-wide segments) and the CTA count's granularity (at
-// least `min_items` (pair, gate) items a CTA).  Default: 384 threads (at
-// 168 registers one CTA fills the register file with 12 warps; 256 threads
-// left a third of it idle: round 1 of a medium layer 224 -> 206 us), the
-// per-warp form while pairs outnumber CTAs, about one item a thread.
+// A launch shape of a copy round: the CTA width (128, 256 or 384 threads),
+// the form and the CTA count's granularity (min_items).  The tuning table
+// (sisu_tune_copy_round; unset entries keep the default), per (log2 W_{i+1},
+// log2 pairs), is k_copy_c's, the layered circuits' copy round.  This
+// general form (general circuits, copy-sharded ranks) runs its default: 384
+// threads (at 168 registers one CTA fills the register file with 12 warps;
+// 256 threads left a third of it idle: round 1 of a medium layer 224 -> 206
+// us), per-warp pair segments while pairs outnumber CTAs (else CTA-wide
+// segments), about one (pair, gate) item a thread.
 struct CopyTune {
   uint16_t bd;        // 0: unset
-  uint8_t form;       // 0: per-warp segments iff more pairs than CTAs, 1: CTA-wide, 2: per-warp
+  uint8_t form;       // general form: 0 per-warp segments iff more pairs than CTAs, 1 CTA-wide, 2 per-warp
   uint32_t min_items;
 };
 constexpr uint32_t kTuneLog = 25;
-static CopyTune g_copy_tune[kTuneLog][kTuneLog];
+static CopyTune g_copy_c_tune[kTuneLog][kTuneLog];
 
 template <int BD>
 static int copy_round_per_sm() {
@@ -792,10 +793,7 @@ int launch_copy_round(const uint32_t* T, uint32_t sn, uint32_t h, const uint32_t
                       const DevLayer& L, uint32_t* partials, DevState* S, uint8_t* proof, size_t off, uint32_t k,
                       void* stream, uint32_t* sums_out) {
   cudaStream_t st = (cudaStream_t)stream;
-  uint32_t lh = 0;
-  while ((2u << lh) <= h) ++lh;
-  CopyTune t = {384, 0, 0};
-  if (sn < kTuneLog && lh < kTuneLog && g_copy_tune[sn][lh].bd) t = g_copy_tune[sn][lh];
+  const CopyTune t = {384, 0, 0};
   if (t.bd == 128)
     return launch_copy_round_bd<128>(t.form, t.min_items, T, sn, h, E, omega_s, L, partials, S, proof, off, k, st,
                                      sums_out);
@@ -810,7 +808,7 @@ int set_copy_tune(uint32_t sn, uint32_t log_pairs, uint32_t bd, uint32_t form, u
   if (sn >= kTuneLog || log_pairs >= kTuneLog) return -1;
   if (bd != 0 && bd != 128 && bd != 256 && bd != 384) return -1;
   if (form > 2) return -1;
-  g_copy_tune[sn][log_pairs] = CopyTune{(uint16_t)bd, (uint8_t)form, min_items};
+  g_copy_c_tune[sn][log_pairs] = CopyTune{(uint16_t)bd, (uint8_t)form, min_items};
   return 0;
 }
 
@@ -1122,42 +1120,68 @@ __global__ void __launch_bounds__(BD) k_copy_c(const uint32_t* __restrict__ T, u
   if (threadIdx.x < 32) round_finalize<4>(S, acc, proof, off, &S->rb[k]);
 }
 
-constexpr int kCThreads = 256;
-
+// Launch shapes of k_copy_c, from the copy round's tuning table (the same
+// (log2 W, log2 pairs) classes): the CTA width (128, 256 or 384 threads;
+// default 256), the split (form 0: whole pairs a CTA while pairs are at
+// least the CTAs, shares of a pair otherwise; 1: shares whenever the pairs
+// fit the shares' scratch; 2: whole pairs always) and the items a share
+// takes at least (default half a CTA's threads).
+template <int BD>
 static int copy_c_per_sm() {
   static int per_sm = 0;
   if (per_sm == 0) {
-    const size_t smem = (size_t)(kCThreads / 32) * kStageWords4 * sizeof(uint4);
-    if (cudaFuncSetAttribute(k_copy_c<kCThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
+    const size_t smem = (size_t)(BD / 32) * kStageWords4 * sizeof(uint4);
+    if (cudaFuncSetAttribute(k_copy_c<BD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
       return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_copy_c<kCThreads>, kCThreads, smem) != cudaSuccess ||
-        n < 1)
-      n = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_copy_c<BD>, BD, smem) != cudaSuccess || n < 1) n = 1;
     per_sm = n;
   }
   return per_sm;
+}
+
+template <int BD>
+static int launch_copy_c_bd(int form, uint32_t min_items, const uint32_t* T, uint32_t sn, uint32_t h,
+                            const uint32_t* E, const uint32_t* omega_s, const DevLayer& L, const uint32_t* Uprev,
+                            const uint32_t* cprev, uint32_t* Ucur, uint32_t* ccur, uint32_t* cpart,
+                            uint32_t* partials, DevState* S, uint8_t* proof, size_t off, uint32_t k,
+                            cudaStream_t st) {
+  const int per_sm = copy_c_per_sm<BD>();
+  if (per_sm == 0) return (int)cudaErrorInvalidValue;
+  const uint32_t nc = std::min<uint32_t>(kSMs * per_sm, kMaxPartials / 2);  // the shares use the upper half
+  const size_t smem = (size_t)(BD / 32) * kStageWords4 * sizeof(uint4);
+  uint32_t m = 0, per = 0, grid = nc;
+  const bool shares = form == 2 ? false : form == 1 ? h <= kMaxPartials / 2 : h < nc;
+  if (shares) {  // shares of a pair's mul entries, each at least min_items of them
+    const uint32_t mi = min_items ? min_items : BD / 2;
+    const uint32_t by_items = std::max<uint32_t>(1, (L.nmul + mi - 1) / mi);
+    m = std::max<uint32_t>(1, std::min<uint32_t>(std::max<uint32_t>(1, nc / h), by_items));
+    per = (L.nmul + m - 1) / m;
+    grid = h * m;
+  } else if (h < nc) {
+    grid = h;  // whole pairs, one a CTA
+  }
+  return launch_pdl_smem(k_copy_c<BD>, grid, BD, m ? 0 : smem, st, T, sn, h, E, omega_s, L.sgate, L.nmul, m, per,
+                         Uprev, cprev, Ucur, ccur, cpart, partials, S, proof, off, k);
 }
 
 int launch_copy_c(const uint32_t* T, uint32_t sn, uint32_t h, const uint32_t* E, const uint32_t* omega_s,
                   const DevLayer& L, const uint32_t* Uprev, const uint32_t* cprev, uint32_t* Ucur, uint32_t* ccur,
                   uint32_t* cpart, uint32_t* partials, DevState* S, uint8_t* proof, size_t off, uint32_t k,
                   void* stream) {
-  const int per_sm = copy_c_per_sm();
-  if (per_sm == 0) return (int)cudaErrorInvalidValue;
-  const uint32_t nc = std::min<uint32_t>(kSMs * per_sm, kMaxPartials / 2);  // the shares use the upper half
-  const size_t smem = (size_t)(kCThreads / 32) * kStageWords4 * sizeof(uint4);
-  uint32_t m = 0, per = 0, grid = nc;
-  if (h < nc) {  // shares of a pair's mul entries, at least half a CTA's threads of items each
-    const uint32_t by_items = std::max<uint32_t>(1, (L.nmul + kCThreads / 2 - 1) / (kCThreads / 2));
-    m = std::max<uint32_t>(1, std::min<uint32_t>(nc / h, by_items));
-    per = (L.nmul + m - 1) / m;
-    grid = h * m;
-  }
-  return launch_pdl_smem(k_copy_c<kCThreads>, grid, kCThreads, m ? 0 : smem, (cudaStream_t)stream, T, sn, h, E,
-                         omega_s, L.sgate, L.nmul, m, per, Uprev, cprev, Ucur, ccur, cpart, partials, S, proof, off,
-                         k);
+  cudaStream_t st = (cudaStream_t)stream;
+  uint32_t lh = 0;
+  while ((2u << lh) <= h) ++lh;
+  CopyTune t = {256, 0, 0};
+  if (sn < kTuneLog && lh < kTuneLog && g_copy_c_tune[sn][lh].bd) t = g_copy_c_tune[sn][lh];
+  if (t.bd == 128)
+    return launch_copy_c_bd<128>(t.form, t.min_items, T, sn, h, E, omega_s, L, Uprev, cprev, Ucur, ccur, cpart,
+                                 partials, S, proof, off, k, st);
+  if (t.bd == 384)
+    return launch_copy_c_bd<384>(t.form, t.min_items, T, sn, h, E, omega_s, L, Uprev, cprev, Ucur, ccur, cpart,
+                                 partials, S, proof, off, k, st);
+  return launch_copy_c_bd<256>(t.form, t.min_items, T, sn, h, E, omega_s, L, Uprev, cprev, Ucur, ccur, cpart,
+                               partials, S, proof, off, k, st);
 }
 
 // ---------------------------------------------------------------------------

@@ -1,18 +1,16 @@
 """Autotuner of the copy round's launch shape.
 
 A copy round of a layer whose next layer has 2^sn positions and 2^lh
-pairs can launch with 128, 256 or 384-thread CTAs, in the per-warp or the
-CTA-wide segment form, and with a CTA count set by the items a CTA takes
-at least.  Which is fastest depends on (sn, lh): wide rounds want every
-SM busy and the per-warp form, small ones short chains and few CTAs.  For
+pairs can launch with 128, 256 or 384-thread CTAs, with whole pairs a CTA
+or shares of a pair's mul entries, and with a share's size set by the
+entries it takes at least.  Which is fastest depends on (sn, lh): wide
+rounds want every SM busy on whole pairs, small ones short chains.  For
 each (sn, lh) class asked for, the tuner proves a one-layer circuit of
-that shape (2^(lh+2) copies, 2^sn gates, 60% mul) under every candidate,
-times its second copy round (2^lh pairs) with CUDA events on the
-launching stream (best of three), and keeps the fastest; the table is
-cached on disk per GPU name and loaded into the library with
-``sisu_tune_copy_round``.  The second round is timed because the first
-round of a layer has a form of its own (it reads the layer's gate values);
-the table applies to every round of the class.  Proof bytes do not depend
+that shape (2^(lh+1) copies, 2^sn gates, 60% mul) under every candidate,
+times its first copy round with CUDA events on the launching stream (best
+of three), and keeps the fastest; the table is cached on disk per GPU
+name and loaded into the library with ``sisu_tune_copy_round``, and
+applies to the copy rounds of layered circuits.  Proof bytes do not depend
 on the launch shape (every candidate's proof is compared with the
 default's).
 """
@@ -23,8 +21,9 @@ import os
 import time
 
 CTA_THREADS = (128, 256, 384)
-FORMS = (0, 1, 2)            # 0 per-warp while pairs outnumber CTAs, 1 CTA-wide, 2 per-warp
-MIN_ITEMS = (0, 2, 4)        # 0: one item a thread; k: k items a thread at least
+DEFAULT_SHAPE = (256, 0, 0)  # the kernel's shape with no table entry
+FORMS = (0, 1, 2)            # 0 whole pairs while pairs are at least the CTAs, 1 shares, 2 whole pairs
+MIN_ITEMS = (0, 2, 4)        # 0: half a CTA's threads of entries a share; k: k entries a thread at least
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_tune", "copy_round.json")
 
 
@@ -65,7 +64,7 @@ def reset(classes):
         S.tune_copy_round(sn, lh, 0)
 
 
-def _time_second_round(S, gc, ev, stream, reps: int = 3) -> tuple[float, bytes]:
+def _time_first_round(S, gc, ev, stream, reps: int = 3) -> tuple[float, bytes]:
     import torch
     best, proof = None, None
     for _ in range(reps):
@@ -75,7 +74,7 @@ def _time_second_round(S, gc, ev, stream, reps: int = 3) -> tuple[float, bytes]:
         rounds = S.profile_launches(S.PROF_COPY_ROUND)
         S.profile_read(S.PROF_COPY_ROUND)
         S.profile_enable(0)
-        ms = rounds[1][0]
+        ms = rounds[0][0]
         best = ms if best is None else min(best, ms)
     return best, proof
 
@@ -94,22 +93,22 @@ def tune(classes, path: str = DEFAULT_CACHE, log=None) -> dict:
     stream = torch.cuda.current_stream()
     t0 = time.time()
     for sn, lh in todo:
-        spec = synth.uniform_circuit(7 * (1 << 32) + 64 * sn + lh, 4 << lh, [1 << sn, 1 << sn], 60,
-                                     name=f"tune_W{1 << sn}_C{4 << lh}")
+        spec = synth.uniform_circuit(7 * (1 << 32) + 64 * sn + lh, 2 << lh, [1 << sn, 1 << sn], 60,
+                                     name=f"tune_W{1 << sn}_C{2 << lh}")
         gc = S.Circuit.from_spec(spec)
         # random canonical inputs drawn on the device (below 2^253 < r): the
         # timing does not depend on the values
-        x = torch.randint(0, 256, ((4 << lh) << sn, 32), dtype=torch.uint8, device="cuda")
+        x = torch.randint(0, 256, ((2 << lh) << sn, 32), dtype=torch.uint8, device="cuda")
         x[:, 31] &= 0x1F
         ev = S.Eval(gc, x.reshape(-1), stream)
         del x
         S.tune_copy_round(sn, lh, 0)
-        ref_ms, ref = _time_second_round(S, gc, ev, stream)
-        best = ((384, 0, 0), ref_ms)
+        ref_ms, ref = _time_first_round(S, gc, ev, stream)
+        best = (DEFAULT_SHAPE, ref_ms)
         per = {"default": round(ref_ms * 1e3, 2)}
         for bd, form, mi in candidates():
             S.tune_copy_round(sn, lh, bd, form, mi)
-            ms, proof = _time_second_round(S, gc, ev, stream)
+            ms, proof = _time_first_round(S, gc, ev, stream)
             if proof != ref:
                 raise RuntimeError(f"launch shape {(bd, form, mi)} changed the proof of {spec.name}")
             per[f"{bd},{form},{mi}"] = round(ms * 1e3, 2)
@@ -139,9 +138,8 @@ def tune(classes, path: str = DEFAULT_CACHE, log=None) -> dict:
 
 
 def gains(classes, path: str = DEFAULT_CACHE):
-    """Summed microseconds of the timed (second) rounds over the classes:
-    the default launch shape against the tuned one (from the cached
-    timings)."""
+    """Summed first-round microseconds over the classes: the default launch
+    shape against the tuned one (from the cached timings)."""
     try:
         timings = json.load(open(path))[_gpu_name()]["timings_us"]
     except (OSError, ValueError, KeyError):
