@@ -836,12 +836,12 @@ constexpr uint32_t kRowDotThreads = 256;
 
 // U(b) = sum_g w(g) V(b, g) for the C rows of layer i's values (2^sv a row),
 // w in gate order.  A row goes to tpr = 2^lt consecutive threads (a power
-// of two up to a warp, chosen so that rows of 4096 still fill the GPU);
-// each sums every tpr-th element of it, two a step with inlined full
+// of two up to a CTA, chosen so that few rows still fill the GPU); each
+// sums every tpr-th element of it, two a step with inlined full
 // products into two accumulators (independent chains), the next step's row
 // elements copied into shared memory by cp.async meanwhile (two stages; the
 // weights, the same for every row, come through L1), and the row's threads
-// add their sums by shuffles.
+// add their sums by shuffles (and shared memory across warps).
 __global__ void __launch_bounds__(kRowDotThreads) k_rowdot(const uint32_t* __restrict__ V, uint32_t sv,
                                                            const uint32_t* __restrict__ omo, uint32_t C,
                                                            uint32_t lt, uint32_t* __restrict__ U) {
@@ -895,21 +895,29 @@ __global__ void __launch_bounds__(kRowDotThreads) k_rowdot(const uint32_t* __res
     }
     fracc_add(a0, a1);
     Fr u = fr_redc288(a0);
-    for (uint32_t o = tpr >> 1; o > 0; o >>= 1) {
+    for (uint32_t o = min(tpr, 32u) >> 1; o > 0; o >>= 1) {
       Fr v;
 #pragma unroll
       for (int i = 0; i < 8; ++i) v.v[i] = __shfl_down_sync(0xffffffffu, u.v[i], o);
       u = fr_add(u, v);
+    }
+    if (tpr > 32) {  // a row over several warps of the CTA: their sums through shared memory
+      __shared__ Fr wsum[kRowDotThreads / 32];
+      if (lane == 0) wsum[threadIdx.x >> 5] = u;
+      __syncthreads();
+      if (sub == 0)
+        for (uint32_t w = 1; w < tpr / 32; ++w) u = fr_add(u, wsum[(threadIdx.x >> 5) + w]);
+      __syncthreads();
     }
     if (b < C && sub == 0) fr_store(U, b, u);
   }
 }
 
 int launch_rowdot(const uint32_t* V, uint32_t sv, const uint32_t* omo, uint32_t C, uint32_t* U, void* stream) {
-  // threads a row: 32 for rows of 4096 and more, fewer for short rows, so
-  // that C rows give enough threads (and each at least 8 elements)
+  // threads a row: enough that the C rows give at least 2048 threads an
+  // SM, with at least 16 elements a thread and at most a CTA a row
   uint32_t lt = 0;
-  while (lt < 5 && (sv > lt + 3) && ((size_t)C << lt) < (size_t)kSMs * 2048) ++lt;
+  while ((1u << lt) < kRowDotThreads && sv > lt + 4 && ((size_t)C << lt) < (size_t)kSMs * 2048) ++lt;
   const size_t threads = (size_t)C << lt;
   const unsigned grid = (unsigned)std::max<size_t>(1, std::min<size_t>((threads + kRowDotThreads - 1) / kRowDotThreads,
                                                                        (size_t)kSMs * 8));
