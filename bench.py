@@ -63,7 +63,7 @@ ALU_PEAK_TIMAD = SMS * IMAD_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
 # first layers of the slot workload: every layer has the same shape, so the
 # per-item traffic of a full-size launch is the same); None when not
 # captured for the current build of the kernel.
-DOMINANT_TRAFFIC_BYTES_PER_ITEM = None
+DOMINANT_TRAFFIC_BYTES_PER_ITEM = 4460090368 / 33553408
 
 
 def log(*a):
