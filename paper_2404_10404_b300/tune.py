@@ -79,16 +79,29 @@ def _time_first_round(S, gc, ev, stream, reps: int = 3) -> tuple[float, bytes]:
     return best, proof
 
 
-def tune(classes, path: str = DEFAULT_CACHE, log=None) -> dict:
-    """Tune every (sn, lh) class in ``classes`` (cached entries of this GPU
-    are kept), apply the table and write the cache.  Returns the table."""
+# For one proof at a time, classes with fewer (pair, gate) items a round
+# keep the default shape: their rounds are latency-bound inside a proof,
+# and shapes timed on a lone round there made the medium proof slower
+# (18.5 -> 18.7 ms with every class tuned, 18.4-18.6 with this floor),
+# while the throughput-bound classes gain inside the proof as in isolation
+# (slot 92.8 -> 91.4-91.7 ms).  Concurrent proofs (the batched workload)
+# tune every class: 118.4 proofs/s against 115.2 with the floor.
+MIN_TUNED_ITEMS = 1 << 20
+
+
+def tune(classes, path: str = DEFAULT_CACHE, log=None, min_items: int = MIN_TUNED_ITEMS) -> dict:
+    """Tune every (sn, lh) class in ``classes`` with at least min_items
+    (pair, gate) items a round (cached entries of this GPU are kept; the
+    smaller classes keep the default shape and are not cached), apply the
+    table and write the cache.  Returns the shapes of every class."""
     import torch
 
     import paper_2404_10404_b300 as S
     import synth
     cached = load(path) or {}
-    todo = sorted({c for c in classes if c not in cached})
     table = dict(cached)
+    small = {c: DEFAULT_SHAPE for c in classes if c not in cached and (1 << (c[0] + c[1])) < min_items}
+    todo = sorted({c for c in classes if c not in table and c not in small})
     timings = {}
     stream = torch.cuda.current_stream()
     t0 = time.time()
@@ -121,6 +134,7 @@ def tune(classes, path: str = DEFAULT_CACHE, log=None) -> dict:
         if log:
             log(f"[tune] W 2^{sn}, pairs 2^{lh}: {best[0]} {best[1] * 1e3:.1f} us (default {ref_ms * 1e3:.1f} us)")
     apply(table)
+    reset(small)
     if todo:
         os.makedirs(os.path.dirname(path), exist_ok=True)
         try:
@@ -134,7 +148,7 @@ def tune(classes, path: str = DEFAULT_CACHE, log=None) -> dict:
         tmp = path + f".tmp{os.getpid()}"
         json.dump(data, open(tmp, "w"), indent=1)
         os.replace(tmp, path)
-    return table
+    return {**table, **small}
 
 
 def gains(classes, path: str = DEFAULT_CACHE):

@@ -21,13 +21,16 @@ def test_tune_cache_and_parity(S, oracle, tmp_path):
     assert (6, 5) in classes and (7, 0) in classes
     path = str(tmp_path / "copy_round.json")
     try:
-        table = tune.tune(classes[:4], path)
+        table = tune.tune(classes[:4], path, min_items=0)
         assert set(table) == set(classes[:4])
         for bd, form, mi in table.values():
             assert bd in tune.CTA_THREADS and form in tune.FORMS
         assert tune.load(path) == table
         # a second call finds every class cached and tunes nothing
-        assert tune.tune(classes[:4], path) == table
+        assert tune.tune(classes[:4], path, min_items=0) == table
+        # classes below the item floor keep the default without being timed
+        small = tune.tune(classes[4:], str(tmp_path / "small.json"))
+        assert all(v == tune.DEFAULT_SHAPE for v in small.values())
         # every launch shape on every round of a fresh handle
         for bd in tune.CTA_THREADS:
             for form in tune.FORMS:
