@@ -279,6 +279,30 @@ def measure_imad_peak(S, stream, uuid):
                    "best of the launches in about a second (CUDA events)"}
 
 
+def copy_phase_equivalent(circ, breakdown: dict, peak: float) -> dict:
+    """The copy phase as a whole (row sums, rounds, folds) against the
+    item-by-item count of its work: 2 + 4 f products a (pair, gate) item for
+    the round sums (a mul gate's three products and three weight products at
+    t = 0, 1, 2; an add gate's two weighted sums) and one product a folded
+    row element.  The recurrence form reaches the same sums with fewer
+    products, so this is the rate at which the phase delivers that work, in
+    Montgomery-product units of 264 multiply-adds, not the rate at which its
+    kernels issue products (the dominant kernel's `frac` is that)."""
+    import numpy as np
+    rounds = (circ.n_copies - 1).bit_length()
+    pairs = sum(circ.n_copies >> (k + 1) for k in range(rounds))
+    sums = sum(pairs * (2 * circ.widths[i] + 4 * int(np.count_nonzero(np.asarray(circ.types[i]) == 1)))
+               for i in range(circ.depth))
+    folds = sum(pairs * circ.widths[i + 1] for i in range(circ.depth))
+    ms = sum(breakdown[k]["ms"] for k in ("row_sums", "copy_round", "copy_fold"))
+    if not ms:
+        return None
+    achieved = (sums + folds) * IMAD_PER_FR_MUL / (ms / 1e3) / 1e12
+    return {"kernels": "k_rowdot + k_copy_c + k_copy_fold", "ms_per_step": ms,
+            "item_by_item_products": sums + folds, "achieved": achieved, "unit": "TIMAD/s",
+            "frac_equivalent": achieved / peak, "peak": peak}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -420,7 +444,8 @@ def run_ours(args):
                                 "products per pair",
                 "per_launch_ms": prof_ms / prof_n if prof_n else None, "launches_timed": prof_n,
                 "fr_mults_per_launch": prof_work / prof_n if prof_n else None,
-                "items_per_launch": per_launch_items}
+                "items_per_launch": per_launch_items,
+                "copy_phase": copy_phase_equivalent(circ, breakdown, peak)}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
