@@ -61,9 +61,10 @@ ALU_PEAK_TIMAD = SMS * IMAD_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
 # DRAM traffic (read + write bytes) of the dominant kernel per (pair, gate)
 # item, from an ncu capture of the copy rounds of a slot-shaped layer (the
 # first layers of the slot workload: every layer has the same shape, so the
-# per-item traffic of a full-size launch is the same); None when not
-# captured for the current build of the kernel.
-DOMINANT_TRAFFIC_BYTES_PER_ITEM = 4460090368 / 33553408
+# per-item traffic of a full-size launch is the same), with the launch
+# shapes the tuner picks for those rounds; None when not captured for the
+# current build of the kernel.
+DOMINANT_TRAFFIC_BYTES_PER_ITEM = 3721676544 / 33553408
 
 
 def log(*a):
