@@ -304,6 +304,23 @@ def copy_phase_equivalent(circ, breakdown: dict, peak: float) -> dict:
             "frac_equivalent": achieved / peak, "peak": peak}
 
 
+def step_equivalent(circ, ms_per_step: float, peak: float) -> dict:
+    """The whole step (evaluation and proof) against the per-gate count of
+    the method's work: 3 + 5 f products a (copy, gate) for a layer with a
+    share f of mul gates (2 + 4 f for the copy rounds' sums, one for the
+    fold, f for the evaluation), in Montgomery-product units of 264
+    multiply-adds.  Libra's phases, the digests and the transcript are
+    extra time at no extra count."""
+    import numpy as np
+    products = sum(circ.n_copies * (3 * circ.widths[i] + 5 * int(np.count_nonzero(np.asarray(circ.types[i]) == 1)))
+                   for i in range(circ.depth))
+    if not ms_per_step:
+        return None
+    achieved = products * IMAD_PER_FR_MUL / (ms_per_step / 1e3) / 1e12
+    return {"per_step_products": products, "ms_per_step": ms_per_step, "achieved": achieved, "unit": "TIMAD/s",
+            "frac_equivalent": achieved / peak, "peak": peak}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -446,7 +463,8 @@ def run_ours(args):
                 "per_launch_ms": prof_ms / prof_n if prof_n else None, "launches_timed": prof_n,
                 "fr_mults_per_launch": prof_work / prof_n if prof_n else None,
                 "items_per_launch": per_launch_items,
-                "copy_phase": copy_phase_equivalent(circ, breakdown, peak)}
+                "copy_phase": copy_phase_equivalent(circ, breakdown, peak),
+                "step": step_equivalent(circ, ms / args.steps, peak)}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",

@@ -48,3 +48,23 @@ def test_one_copy_has_no_copy_phase():
     c = _circuit(1, [4, 4], [[1, 0, 1, 0]])
     assert bench.copy_phase_equivalent(c, BD, 10.0)["item_by_item_products"] == 0
     assert bench.copy_phase_equivalent(c, {k: {"ms": 0.0} for k in BD}, 10.0) is None
+
+
+def test_step_count_by_hand():
+    # 4 copies; layer 0: 2 mul + 2 add gates, layer 1: 4 add gates
+    c = _circuit(4, [4, 4, 4], [[1, 1, 0, 0], [0, 0, 0, 0]])
+    r = bench.step_equivalent(c, 2.0, 10.0)
+    assert r["per_step_products"] == 4 * (3 * 4 + 5 * 2) + 4 * (3 * 4)
+    assert r["achieved"] == pytest.approx(r["per_step_products"] * 264 / 2e-3 / 1e12)
+    assert r["frac_equivalent"] == pytest.approx(r["achieved"] / 10.0)
+    assert bench.step_equivalent(c, 0.0, 10.0) is None
+
+
+def test_slot_counts_match_the_per_gate_formula():
+    # the slot-shaped mixing layers alternate 100% and 40% mul: 3 + 5 f a gate
+    c = synth.mixing_circuit(3, 8, 1024, 4)
+    mul = sum(int(np.count_nonzero(np.asarray(t) == 1)) for t in c.types)
+    gates = 8 * 1024 * 4
+    r = bench.step_equivalent(c, 1.0, 1.0)
+    assert r["per_step_products"] == 3 * gates + 5 * 8 * mul
+    assert abs(mul / (1024 * 4) - 0.7) < 0.02
