@@ -21,7 +21,12 @@
  *     padded with absent gates of value 0 and zero inputs (Sec. 2.2).
  *   - Tables of values are copy-major: element (b, g) at index b*width + g.
  *   - "stream" is a cudaStream_t (NULL = the legacy default stream).  Device
- *     pointers must be 16-byte aligned.
+ *     pointers must be 16-byte aligned.  Every buffer that a call hands to
+ *     its kernels as device memory (inputs or outputs flagged on_device,
+ *     sisu_fr_batch's arrays, sisu_statement_digest's data, the shard
+ *     exchange buffers) is checked with cudaPointerGetAttributes before
+ *     anything is launched: host memory there, pageable or page-locked, is
+ *     refused with SISU_ERR_INVALID_ARG instead of reaching a kernel.
  *   - Every call returns SISU_OK (0) or a negative SISU_ERR_* code; the
  *     calling thread's last error message is sisu_last_error().  No call
  *     aborts or exits.  Handles are not thread-safe: one thread (or one

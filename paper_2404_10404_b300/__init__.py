@@ -670,7 +670,11 @@ def sort_elements(elems, out=None, n: int | None = None, stream=None):
 
 
 def statement_digest(data, length: int, stream=None) -> bytes:
-    p, _, keep = _ptr(data)
+    """The statement digest of ``length`` bytes of the CUDA device buffer
+    ``data`` (host arrays are refused: the kernels read ``data`` in place)."""
+    p, on_dev, keep = _ptr(data)
+    if length and not on_dev:
+        raise SisuError(-1, "data must be a CUDA device buffer")
     out = ctypes.create_string_buffer(32)
     _check(_lib.sisu_statement_digest(p, length, ctypes.cast(out, ctypes.c_void_p), _stream(stream)))
     return out.raw

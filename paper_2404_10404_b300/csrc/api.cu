@@ -44,6 +44,19 @@ static int cuda_fail(cudaError_t e, const char* what) {
   return fail(SISU_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+namespace sisu {
+int require_device(const void* p, const char* what) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // not a sticky error: clear it
+    return fail(SISU_ERR_INVALID_ARG, "%s: not an address the CUDA runtime knows", what);
+  }
+  if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+    return fail(SISU_ERR_INVALID_ARG, "%s is not device memory", what);
+  return SISU_OK;
+}
+}  // namespace sisu
+
 #define CK(call, what)                                   \
   do {                                                   \
     cudaError_t e_ = (cudaError_t)(call);                \
@@ -725,6 +738,8 @@ extern "C" int sisu_circuit_eval(const sisu_circuit* circ, const uint8_t* inputs
   *out = nullptr;
   if (!circ || !inputs) return fail(SISU_ERR_INVALID_ARG, "NULL circuit or inputs");
   if (!has_device(circ)) return fail(SISU_ERR_INVALID_ARG, "circuit was created for host verification only");
+  if (inputs_on_device)
+    if (int rc = require_device(inputs, "inputs")) return rc;
   const HostCircuit& hc = circ->hc;
   std::unique_ptr<sisu_eval> ev(new (std::nothrow) sisu_eval());
   if (!ev) return fail(SISU_ERR_OOM, "host allocation");
@@ -766,6 +781,8 @@ extern "C" int sisu_circuit_eval(const sisu_circuit* circ, const uint8_t* inputs
 
 extern "C" int sisu_eval_update(sisu_eval* ev, const uint8_t* inputs, int inputs_on_device, void* stream) {
   if (!ev || !inputs) return fail(SISU_ERR_INVALID_ARG, "NULL eval or inputs");
+  if (inputs_on_device)
+    if (int rc = require_device(inputs, "inputs")) return rc;
   const HostCircuit& hc = ev->circ->hc;
   const bool padded = hc.Creal != hc.C || hc.wreal[hc.d] != hc.W[hc.d];
   if (padded && !inputs_on_device && !ev->stage) {
@@ -783,6 +800,7 @@ extern "C" int sisu_eval_outputs(const sisu_eval* ev, uint8_t* out, size_t cap, 
   cudaStream_t st = (cudaStream_t)stream;
   if (out_on_device) {
     if (((uintptr_t)out & 15) != 0) return fail(SISU_ERR_INVALID_ARG, "device output not 16-byte aligned");
+    if (int rc = require_device(out, "out")) return rc;
     CK(launch_layer_to_canonical(ev->V[0], (uint32_t*)out, hc.c, hc.s[0], hc.Creal, hc.wreal[0], st), "outputs");
     return SISU_OK;
   }
@@ -1468,6 +1486,10 @@ extern "C" int sisu_fr_batch(int op, const uint8_t* a, const uint8_t* b, uint8_t
   if (n == 0) return SISU_OK;
   if ((((uintptr_t)a | (uintptr_t)out | (uintptr_t)(b ? b : a)) & 15) != 0)
     return fail(SISU_ERR_INVALID_ARG, "device arrays must be 16-byte aligned");
+  if (int rc = require_device(a, "a")) return rc;
+  if (b && op != 3 && op != 7 && op != 8)
+    if (int rc = require_device(b, "b")) return rc;
+  if (int rc = require_device(out, "out")) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   uint32_t *flag = nullptr, host_flag = 0;
   CK(cudaMallocAsync(&flag, 4, st), "cudaMallocAsync");
@@ -1485,6 +1507,8 @@ extern "C" int sisu_fr_batch(int op, const uint8_t* a, const uint8_t* b, uint8_t
 
 extern "C" int sisu_statement_digest(const uint8_t* data, size_t len, uint8_t* out, void* stream) {
   if (!out || (len && !data)) return fail(SISU_ERR_INVALID_ARG, "NULL argument");
+  if (len)
+    if (int rc = require_device(data, "data")) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   const size_t words = digest_scratch_words(len) + 8;
   uint32_t* scratch = nullptr;

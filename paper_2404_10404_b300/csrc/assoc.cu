@@ -420,6 +420,7 @@ int check_elems(const uint8_t* p, uint64_t n, int on_device) {
   if (n && !p) return report_error(SISU_ERR_INVALID_ARG, "NULL element array");
   if (on_device && n && ((uintptr_t)p & 15))
     return report_error(SISU_ERR_INVALID_ARG, "device element arrays must be 16-byte aligned");
+  if (on_device && n) return require_device(p, "element array");
   return SISU_OK;
 }
 

@@ -104,6 +104,12 @@ void prof_end(long idx, void* stream);
 constexpr uint32_t kProfAssocHash = 9, kProfAssocPair = 10;
 // sets the calling thread's sisu_last_error() message, returns code
 int report_error(int code, const char* msg);
+// SISU_OK when p is device (or managed) memory that kernels may read and
+// write, else SISU_ERR_INVALID_ARG naming `what`: a host address handed to
+// a kernel would fault the GPU.  cudaPointerGetAttributes allocates nothing
+// and does not synchronise; ordinary and page-locked host memory are both
+// refused.
+int require_device(const void* p, const char* what);
 
 // the input conversion and the layer evaluation of copies b0 .. b0 + nb - 1
 // (each copy evaluates independently of the others)

@@ -319,6 +319,8 @@ extern "C" int sisu_server_submit(sisu_server* s, const sisu_circuit* circ, cons
   if (!s || !circ || !inputs || !ticket) return report_error(SISU_ERR_INVALID_ARG, "NULL argument");
   if (!circ->dev) return report_error(SISU_ERR_INVALID_ARG, "circuit was created for host verification only");
   if (circ->hc.general) return report_error(SISU_ERR_INVALID_ARG, "the server does not take general circuits");
+  if (inputs_on_device)
+    if (int rc = require_device(inputs, "inputs")) return rc;
   std::unique_ptr<Job> j(new (std::nothrow) Job());
   if (!j) return report_error(SISU_ERR_OOM, "host allocation");
   j->circ = circ;

@@ -102,6 +102,9 @@ extern "C" int sisu_shard_create(sisu_eval* local, uint32_t rank, uint32_t world
                              bufs->row_send, bufs->row_recv, bufs->state};
   for (const void* p : ptrs)
     if (((uintptr_t)p & 15) != 0) return report_error(SISU_ERR_INVALID_ARG, "exchange buffers must be 16-byte aligned");
+  for (const void* p : ptrs)
+    if (p)
+      if (int rc = require_device(p, "exchange buffer")) return rc;
   std::unique_ptr<sisu_shard> sh(new (std::nothrow) sisu_shard());
   if (!sh) return report_error(SISU_ERR_OOM, "host allocation");
   sh->ev = local;

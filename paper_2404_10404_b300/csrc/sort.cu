@@ -181,6 +181,10 @@ extern "C" int sisu_sort_elements(const uint8_t* in, uint64_t n, int on_device, 
   if (n >= (1ull << 32)) return report_error(SISU_ERR_TOO_LARGE, "at most 2^32 - 1 elements");
   if (on_device && n && ((((uintptr_t)in) | ((uintptr_t)out)) & 15))
     return report_error(SISU_ERR_INVALID_ARG, "device element arrays must be 16-byte aligned");
+  if (on_device && n) {
+    if (int rc = require_device(in, "in")) return rc;
+    if (int rc = require_device(out, "out")) return rc;
+  }
   if (n == 0) return SISU_OK;
   cudaStream_t st = (cudaStream_t)stream;
   const size_t bytes = (size_t)n * 32;
