@@ -136,7 +136,6 @@ def tune(classes, path: str = DEFAULT_CACHE, log=None, min_items: int = MIN_TUNE
     apply(table)
     reset(small)
     if todo:
-        os.makedirs(os.path.dirname(path), exist_ok=True)
         try:
             data = json.load(open(path))
         except (OSError, ValueError):
@@ -145,9 +144,14 @@ def tune(classes, path: str = DEFAULT_CACHE, log=None, min_items: int = MIN_TUNE
         prev.update(timings)
         data[_gpu_name()] = {"table": {f"{k[0]},{k[1]}": list(v) for k, v in table.items()},
                              "timings_us": prev, "seconds": round(time.time() - t0, 1)}
-        tmp = path + f".tmp{os.getpid()}"
-        json.dump(data, open(tmp, "w"), indent=1)
-        os.replace(tmp, path)
+        try:
+            os.makedirs(os.path.dirname(path), exist_ok=True)
+            tmp = path + f".tmp{os.getpid()}"
+            with open(tmp, "w") as f:
+                json.dump(data, f, indent=1)
+            os.replace(tmp, path)
+        except OSError:
+            pass  # a read-only location: the table applies to this process only
     return {**table, **small}
 
 
