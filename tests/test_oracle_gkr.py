@@ -106,6 +106,26 @@ def test_prover_matches_bruteforce(oracle, C, widths, pct):
     assert oracle.verify(circ, xb, oracle.outputs(circ, xb), p1) == 0
 
 
+def _random_shapes(n, seed=2024):
+    """Seeded random micro shapes: copy counts 1-9 and widths 1-9 (powers of
+    two or not: padding on both), depths 1-4, every mul share."""
+    rng = random.Random(seed)
+    out = []
+    for _ in range(n):
+        C = rng.randint(1, 9)
+        widths = [rng.randint(1, 9) for _ in range(rng.randint(2, 5))]
+        out.append((rng.randrange(1 << 30), C, widths, rng.choice([0, 25, 50, 75, 100])))
+    return out
+
+
+@pytest.mark.parametrize("seed,C,widths,pct", _random_shapes(24))
+def test_prover_matches_bruteforce_random_shapes(oracle, seed, C, widths, pct):
+    circ, xb, xi = _mk(C, widths, pct, seed=seed)
+    p1 = oracle.prove(circ, xb)
+    assert p1 == brute.prove(circ, xi)
+    assert oracle.verify(circ, xb, oracle.outputs(circ, xb), p1) == 0
+
+
 def test_in1_equals_in2_and_domain(oracle):
     circ, xb, xi = _mk(4, [4, 4, 4], 50, seed=21)
     for i in range(circ.depth):
