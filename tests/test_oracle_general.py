@@ -48,6 +48,27 @@ def test_general_proof_equals_brute_force(oracle, seed, C, widths, pct, far):
     assert oracle.verify_general(g, xb, oracle.outputs_general(g, xb), proof) == 0
 
 
+def _random_general(n, seed=4048):
+    """Seeded random general shapes: 1-8 copies, 3-5 layers of widths 1-9,
+    every mul share and share of far second inputs."""
+    import random
+    rng = random.Random(seed)
+    out = []
+    for _ in range(n):
+        widths = [rng.randint(1, 9) for _ in range(rng.randint(3, 5))]
+        out.append((rng.randrange(1 << 30), rng.randint(1, 8), widths, rng.choice([0, 50, 100]),
+                    rng.choice([20, 50, 100])))
+    return out
+
+
+@pytest.mark.parametrize("seed,C,widths,pct,far", _random_general(12))
+def test_general_proof_equals_brute_force_random_shapes(oracle, seed, C, widths, pct, far):
+    g, xb, xi = _case(seed, C, widths, pct, far)
+    proof = oracle.prove_general(g, xb)
+    assert proof == brute.prove_general(g, xi)
+    assert oracle.verify_general(g, xb, oracle.outputs_general(g, xb), proof) == 0
+
+
 def test_used_gates_indexing():
     """The virtual layer: layer i + 1 in full, then the used gates of each
     deeper layer in ascending order; indexes differ from positions."""

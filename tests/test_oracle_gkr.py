@@ -280,6 +280,24 @@ def test_accumulation_prover_matches_bruteforce(oracle, seed, C, widths, k):
         assert oracle.verify(circ, xb, outs, bytes(t)) == ERR_REJECT
 
 
+def _random_accumulation(n, seed=3032):
+    rng = random.Random(seed)
+    return [(rng.randrange(1 << 30), rng.randint(1, 8), [rng.randint(1, 8) for _ in range(rng.randint(2, 4))],
+             rng.randint(1, 5)) for _ in range(n)]
+
+
+@pytest.mark.parametrize("seed,C,widths,k", _random_accumulation(12))
+def test_accumulation_prover_matches_bruteforce_random_shapes(oracle, seed, C, widths, k):
+    """Seeded random accumulation shapes: 1-8 copies, widths 1-8, up to 1-5
+    entries a gate (gates with none are 0)."""
+    circ = synth.accumulation_circuit(seed, C, widths, k)
+    x = synth.inputs_for(circ)
+    xb = synth.fr_bytes(x)
+    proof = oracle.prove(circ, xb)
+    assert proof == brute.prove(circ, synth.fr_ints(x))
+    assert oracle.verify(circ, xb, oracle.outputs(circ, xb), proof) == 0
+
+
 def test_accumulation_wiring_is_bound(oracle):
     """Moving one entry to another gate, or swapping two entries' order
     inside a gate with different types, changes the wiring digest."""
