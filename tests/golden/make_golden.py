@@ -6,6 +6,7 @@ oracle's proof and the SHA-256 of the real outputs, so that GPU tests can
 compare full-size proofs byte for byte without re-running the slow oracle.
 
     python tests/golden/make_golden.py medium slot
+    python tests/golden/make_golden.py batched:36 batched:31   # instances of the batched workload
 """
 import hashlib
 import json
@@ -24,10 +25,20 @@ OUT = os.path.join(HERE, "oracle_full_size.json")
 WORKLOADS = {"tiny": synth.tiny, "medium": synth.medium, "slot": synth.slot}
 
 
+def _circuit(name: str):
+    """A named workload, or instance j of the batched workload as "batched:j"
+    (stored under "batched_j")."""
+    if name.startswith("batched:"):
+        j = int(name.split(":", 1)[1])
+        return f"batched_{j}", synth.batched_instance(j)
+    return name, WORKLOADS[name]()
+
+
 def main(names):
     o = Oracle()
-    for name in names:
-        circ = WORKLOADS[name]()
+    o.set_threads(os.cpu_count() or 1)  # the proof bytes do not depend on it
+    for arg in names:
+        name, circ = _circuit(arg)
         t0 = time.time()
         x = synth.fr_bytes(synth.inputs_for(circ))
         outs = o.outputs(circ, x)

@@ -85,3 +85,28 @@ def test_batched_workload_instances_equal_oracle(S):
     want = [o.prove(c, x) for c, x in zip(circs, xs)]
     for k in (1, 4, 9):
         assert S.prove_batch(gcs, evs, concurrency=k) == want
+
+
+# larger instances of the same workload (8 to 55 M gates, up to its largest
+# copy count, 2^14, and its widest width, 4096), compared with the oracle's
+# proof hashes written by tests/golden/make_golden.py
+BATCHED_MID = [36, 40, 35, 62, 38, 27, 31, 12]
+
+
+def test_batched_workload_mid_size_instances_equal_oracle_hashes(S):
+    from gpu_util import golden, sha
+    gold = [golden(f"batched_{j}") for j in BATCHED_MID]
+    if any(g is None for g in gold):
+        pytest.skip("no oracle record for the batched instances")
+    circs = [synth.batched_instance(j) for j in BATCHED_MID]
+    xs = [synth.fr_bytes(synth.inputs_for(c)) for c in circs]
+    for x, g in zip(xs, gold):
+        assert sha(x) == g["inputs_sha256"]
+    gcs = [S.Circuit.from_spec(c) for c in circs]
+    evs = [S.Eval(g, x) for g, x in zip(gcs, xs)]
+    del xs
+    proofs = S.prove_batch(gcs, evs, concurrency=4)
+    for j, p, ev, g in zip(BATCHED_MID, proofs, evs, gold):
+        assert len(p) == g["proof_len"], j
+        assert sha(p) == g["proof_sha256"], j
+        assert sha(ev.outputs()) == g["outputs_sha256"], j
