@@ -430,9 +430,15 @@ static void tr_compress(uint8_t st[32], const uint8_t blk[64]) {
     }
 }
 
+/* The most elements one absorb takes: a general circuit's layer end sends
+ * two values for each of its blocks, at most one block per layer below it
+ * (SO_MAX_DEPTH + 1); every other absorb takes at most three. */
+#define SO_MAX_ABSORB (2 * (SO_MAX_DEPTH + 1))
+
 static void tr_absorb(transcript *t, uint8_t tag, const fr *e, int n) {
-    uint8_t msg[32 * 8] = {0};
+    uint8_t msg[32 * SO_MAX_ABSORB + 32]; /* n elements, zero-padded to whole 64-byte blocks */
     size_t len = 32 * (size_t)n, nb = (len + 63) / 64;
+    memset(msg, 0, 64 * nb);
     for (int i = 0; i < n; ++i) fr_to_bytes(msg + 32 * i, e[i]);
     t->st[30] ^= tag;           /* word 7 xor (256 tag + n) */
     t->st[31] ^= (uint8_t)n;

@@ -92,3 +92,16 @@ def test_general_errors(S):
     with pytest.raises(S.SisuError):
         srv.submit(gc, synth.fr_bytes(synth.inputs_for(g)))
     srv.close()
+
+
+@pytest.mark.parametrize("seed,C,widths", [(31, 4, [8] * 7), (33, 3, [5] * 10), (34, 64, [256] * 9)])
+def test_layers_reading_many_layers(S, oracle, seed, C, widths):
+    """Every second input far: a layer's end absorbs two values for each of
+    up to d - i blocks (five to nine here) in one message."""
+    g = synth.general_circuit(seed, C, widths, 50, 100)
+    xb = synth.fr_bytes(synth.inputs_for(g))
+    gc = S.Circuit.from_spec(g)
+    ev = S.Eval(gc, xb)
+    want = oracle.prove_general(g, xb)
+    assert S.prove(gc, ev) == want
+    assert S.verify(gc, xb, ev.outputs(), want) == 0

@@ -134,3 +134,15 @@ def test_verifier_rejects(oracle):
     # another domain
     assert oracle.verify_general(g, xb, outs, proof, b"other") != 0
     assert oracle.verify_general(g, xb, outs, oracle.prove_general(g, xb, b"other"), b"other") == 0
+
+
+@pytest.mark.parametrize("seed,C,widths", [(31, 4, [8] * 7), (32, 2, [4, 8, 4, 8, 4, 8, 4, 8]), (33, 3, [5] * 10)])
+def test_layers_reading_many_layers(oracle, seed, C, widths):
+    """Every second input far: a layer reads up to d - i layers, so its end
+    absorbs two values for each of five to nine blocks in one message."""
+    g, xb, xi = _case(seed, C, widths, 50, 100)
+    pc = brute.GeneralPadded(g)
+    assert max(len(b) for b in pc.blocks) >= 5
+    proof = oracle.prove_general(g, xb)
+    assert proof == brute.prove_general(g, xi)
+    assert oracle.verify_general(g, xb, oracle.outputs_general(g, xb), proof) == 0

@@ -15,7 +15,9 @@ def S():
 
 
 @pytest.mark.parametrize("seed,C,widths,far", [(5, 4, [8, 8, 6, 8], 40), (7, 8, [8, 4, 8, 2, 8], 70),
-                                               (9, 4, [5, 3, 6], 50), (8, 1, [4, 4, 4], 100)])
+                                               (9, 4, [5, 3, 6], 50), (8, 1, [4, 4, 4], 100),
+                                               # layers reading five to nine layers: long 'V' absorbs
+                                               (31, 4, [8] * 7, 100), (33, 3, [5] * 10, 100)])
 def test_host_verifier_on_general_proofs(S, oracle, seed, C, widths, far):
     g = synth.general_circuit(seed, C, widths, 50, far)
     xb = synth.fr_bytes(synth.inputs_for(g))
