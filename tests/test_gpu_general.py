@@ -105,3 +105,23 @@ def test_layers_reading_many_layers(S, oracle, seed, C, widths):
     want = oracle.prove_general(g, xb)
     assert S.prove(gc, ev) == want
     assert S.verify(gc, xb, ev.outputs(), want) == 0
+
+
+def test_general_and_accumulation_handles_take_new_inputs(S, oracle):
+    """A handle's later proofs replay its captured graph: after new inputs
+    (host, then device) the virtual layers are gathered again and every
+    proof is the oracle's for the current inputs."""
+    from gpu_util import to_device
+    specs = [(synth.general_circuit(41, 32, [64, 32, 64, 16, 64], 50, 60), oracle.prove_general),
+             (synth.accumulation_circuit(42, 32, [64, 32, 64, 16], 4), oracle.prove)]
+    for circ, prove in specs:
+        x1 = synth.fr_bytes(synth.inputs_for(circ))
+        x2 = synth.fr_bytes(synth.inputs_for(circ, seed=99))
+        gc = S.Circuit.from_spec(circ)
+        ev = S.Eval(gc, x1)
+        p1 = S.prove(gc, ev)
+        assert p1 == prove(circ, x1) == S.prove(gc, ev)
+        ev.update(x2)
+        assert S.prove(gc, ev) == prove(circ, x2)
+        ev.update(to_device(x1))
+        assert S.prove(gc, ev) == p1
