@@ -73,6 +73,11 @@ MUTANTS = {
                            "if (gc->src[i][g] == j) gc->u2[i][g] = base - cnt;"),
     "general_phase2_first_input": ("pre[g] = eq_point_index(rx, sx, gc->in1[i][g]);",
                                    "pre[g] = eq_point_index(rx, sx, gc->u2[i][g]);"),
+    # the transcript: an absorb's count tweak cut to three bits (wrong only
+    # for the long layer-end absorbs of general layers reading many layers)
+    "absorb_count_low_bits": ("t->st[31] ^= (uint8_t)n;", "t->st[31] ^= (uint8_t)(n & 7);"),
+    "general_block_values_swapped": ("vb[b] = fr_add(vb[b], fr_mul(eq_point_index(rx, sx, u), A0[u]));",
+                                     "vb[b] = fr_add(vb[b], fr_mul(eq_point_index(ry, sx, u), A0[u]));"),
 }
 
 
@@ -149,7 +154,7 @@ def _pins(o: Oracle) -> list:
         failed.append("prove-acc-error")
     # general circuits (Sec. 2.7): against the brute-force prover, accepted,
     # every tampered element rejected
-    for seed, C, widths, far in ((5, 4, [8, 8, 6, 8], 40), (7, 2, [8, 4, 8, 4], 70)):
+    for seed, C, widths, far in ((5, 4, [8, 8, 6, 8], 40), (7, 2, [8, 4, 8, 4], 70), (31, 2, [4] * 7, 100)):
         gcirc = synth.general_circuit(seed, C, widths, 50, far)
         xg = synth.inputs_for(gcirc)
         xgb = synth.fr_bytes(xg)
